@@ -1,0 +1,354 @@
+"""Benchmark: Faceted HyperSARA PDFB iterations/s on one GB300 (libfhs).
+
+One step = one PDFB iteration of the whole hot path (primal step, F, the
+single pass over G with the l2-ball dual step, F^H, SARA analysis + weighted
+l21 dual + synthesis, per-facet Gram + FP64 eig + SVT dual) over the
+1024x1024, 16-channel, 16e6-visibility workload with w-projection.
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "vla_1024"
+METRIC = "PDFB iter/s (1024^2 x 16 ch, 16e6 vis, w-projection); Phi/Phi^H vis/s alongside"
+MU, MU_BAR = 1e-2, 1e-1            # regularisation used for timing (cost does not depend on it)
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([v.strip() for v in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 3 + i and r[3 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _profile_traffic(kernel_file: str):
+    """dram bytes per launch of the fused kernel from the committed ncu summary,
+    valid only while the kernel source is unchanged (sha256 recorded there)."""
+    path = os.path.join(ROOT, "profiles", "degrid_grid_fused_vla_1024.md")
+    src = os.path.join(ROOT, "paper_2209_07604_gb300", "csrc", kernel_file)
+    try:
+        txt = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        m_sha = re.search(r"kernel source sha256:\s*([0-9a-f]{64})", txt)
+        m_tr = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", txt)
+        if m_sha and m_tr and m_sha.group(1) == sha:
+            return float(m_tr.group(1))
+    except OSError:
+        pass
+    return None
+
+
+def fused_kernel_bytes(info, L, B, K, M):
+    """Algorithmic HBM bytes of one launch of the single-pass data kernel:
+    G values 8 B/nnz; per row meta 8 B + row pointer 8 B; per visibility y 8 B,
+    dual d read 8 B + write 8 B; the forward grid read once (8 B/cell) and
+    every block grid written back once (8 B/cell/block)."""
+    return info.nnz * 8 + M * (8 + 8 + 8 + 8 + 8) + L * K * 8 + L * B * K * 8
+
+
+def run_gpu(args):
+    import torch
+    import paper_2209_07604_gb300 as fhs
+    from paper_2209_07604_gb300 import synth
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    fhs.load_library()
+    t0 = time.time()
+    P = synth.make_problem(args.workload)
+    gen_s = time.time() - t0
+    L, M = P.omega.shape[:2]
+    Mtot = L * M
+    stream = torch.cuda.current_stream()
+
+    # ---- end-to-end: host buffers -> problem (H2D inside) -> solve -> image D2H
+    torch.cuda.synchronize()
+    omega = np.ascontiguousarray(P.omega.reshape(-1, 2))
+    wv = np.ascontiguousarray(P.w.reshape(-1))
+    yv = np.ascontiguousarray(np.stack([P.y.real, P.y.imag], -1).reshape(-1, 2))
+    vis_off = np.arange(L + 1, dtype=np.int64) * M
+    params = fhs.default_params(ny=P.ny, nx=P.nx, n_channels=L, n_subcubes=P.C, n_blocks=P.B, qy=P.qy, qx=P.qx,
+                                facet_overlap=P.overlap, w_max=P.w_max, pixel_size=P.pixel_size, mu=MU,
+                                mu_bar=MU_BAR)
+    e2e_iters = args.e2e_iters
+    img_host = torch.empty((L, P.ny, P.nx), dtype=torch.float32, pin_memory=True)
+    t_e2e = time.perf_counter()
+    prob = fhs.Problem(params, omega, wv, yv, P.sigma, vis_off, P.block_offsets)
+    setup_s = time.perf_counter() - t_e2e
+    prob.solve(e2e_iters, 0.0, n_reweight=1 if e2e_iters >= 2 else 0, check_every=max(1, e2e_iters))
+    img_host.copy_(prob.image(), non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t_e2e
+    h2d = omega.nbytes + wv.nbytes + yv.nbytes + P.sigma.nbytes + vis_off.nbytes + P.block_offsets.nbytes
+    d2h = img_host.numel() * 4
+    info = prob.info
+
+    # ---- device-resident timing of K iterations (problem already on the GPU)
+    for _ in range(args.warmup):
+        prob.step(1)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    launches0 = fhs.fhs_kernel_launches(prob.handle)
+    fhs.fhs_profile_enable(prob.handle, True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        prob.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    fhs.fhs_profile_enable(prob.handle, False)
+    phases, n_prof = fhs.fhs_profile_read(prob.handle)
+    launches = fhs.fhs_kernel_launches(prob.handle) - launches0
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    ms_step = ms / args.steps
+
+    # roofline of the dominant kernel (single pass over G)
+    K = 4 * P.ny * P.nx
+    peak, peak_kind = _peaks()
+    kbytes = fused_kernel_bytes(info, L, P.B, K, Mtot)
+    k_ms = phases["degrid_grid"] / max(n_prof, 1)
+    achieved = kbytes / (k_ms * 1e-3) / 1e9
+    traffic = _profile_traffic("k_nufft.cu")
+    # visibilities through Phi and Phi^H per second inside the iteration
+    vis_s = Mtot / (ms_step * 1e-3)
+    out = {
+        "metric": METRIC,
+        "value": ws * 1e3 / ms_step,
+        "unit": "iter/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 (FP64 reductions, eig, weights)",
+        "data": "synthetic (seeded VLA-like uv/w, Gaussian-blob sky, 40 dB)",
+        "config": {"workload": args.workload, "image": "%dx%d" % (P.ny, P.nx), "channels": L,
+                   "subcubes": P.C, "vis_per_channel": M, "blocks": P.B, "facets": "%dx%d" % (P.qy, P.qx),
+                   "facet_overlap": P.overlap, "w_max": P.w_max, "nnz_G": info.nnz,
+                   "l2": "inputs larger than L2 (G alone %.1f GB per iteration)" % (info.nnz * 8 / 1e9),
+                   "mu": MU, "mu_bar": MU_BAR},
+        "vis_per_s": ws * vis_s,
+        "e2e": {"value": ws * e2e_iters / e2e_s, "unit": "iter/s", "h2d_bytes_per_step": h2d / e2e_iters,
+                "d2h_bytes_per_step": d2h / e2e_iters,
+                "what": "create from host arrays (sort, G build, power iteration) + %d iterations with one "
+                        "reweighting + image to pinned host" % e2e_iters,
+                "seconds": e2e_s, "setup_seconds": setup_s},
+        "gpu_launches": int(launches),
+        "phases_ms_per_step": {k: v / max(n_prof, 1) for k, v in phases.items()},
+        "roofline": {"kernel": "degrid_grid_fused", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes": kbytes, "peak_source": peak_kind},
+        "clocks": clk.summary(),
+        "device_bytes": info.device_bytes,
+        "generate_seconds": gen_s,
+    }
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        out["cpu_baseline"] = cpu_baseline(P, info)
+    prob.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def _oracle_sample(P, n_vis: int, sara_side: int, n_facets: int):
+    """Time the oracle's own pieces of one PDFB iteration on a bounded sample
+    of the workload and return seconds per unit of work:
+    data term per stored entry of G (2 channels x n_vis visibilities),
+    SARA analysis + l21 + synthesis per pixel-channel (one channel, a
+    sara_side^2 crop), nuclear dual per facet-pixel-channel (n_facets facets
+    of one sub-cube)."""
+    from oracle import nufft as onf, prox as oprox, wavelets as owv
+    Lc = P.omega.shape[0] // P.C
+    ch = [0, P.C]
+    geom = onf.Geometry(P.ny, P.nx, w_max=P.w_max, n_wplanes=64, pixel_size=P.pixel_size)
+    op = onf.Operator(P.omega[ch, :n_vis], P.w[ch, :n_vis], P.sigma[ch], geom)
+    nnz = sum(G.nnz for G in op.G)
+    rng = np.random.default_rng(0)
+    X = rng.uniform(0, 1, (Lc, P.ny, P.nx))
+    t0 = time.perf_counter()
+    for j in range(2):
+        yw = P.y[ch[j], :n_vis] / P.sigma[ch[j]]
+        eps = oprox.eps_blocks(n_vis, [n_vis])[0]
+        v = oprox.l2ball_dual(np.zeros(n_vis, complex), op.forward(X[j], j), yw, eps, 1e-6)
+        op.adjoint(v, j)
+    t_data = (time.perf_counter() - t0) / nnz
+    side = min(sara_side, P.ny, P.nx)
+    S = owv.Sara(side, side)
+    t0 = time.perf_counter()
+    A = S.analysis(X[:1, :side, :side])
+    W = oprox.l21_dual(np.zeros_like(A), A, 1.0, MU, np.ones(A.shape[1]))
+    S.synthesis(W)
+    t_sara = (time.perf_counter() - t0) / (side * side)
+    facets = oprox.nuclear_facets(P.ny, P.nx, P.qy, P.qx, P.overlap)[:n_facets]
+    npx = 0
+    t0 = time.perf_counter()
+    for (y0, y1, x0, x1) in facets:
+        oprox.nuclear_dual(np.zeros((Lc, y1 - y0, x1 - x0)), X[:, y0:y1, x0:x1], 0.25, MU_BAR, np.ones(Lc))
+        npx += (y1 - y0) * (x1 - x0) * Lc
+    t_nuc = (time.perf_counter() - t0) / npx
+    return t_data, t_sara, t_nuc
+
+
+def _full_units(P, nnz_full):
+    from oracle import prox as oprox
+    L = P.omega.shape[0]
+    fac = oprox.nuclear_facets(P.ny, P.nx, P.qy, P.qx, P.overlap)
+    nuc = sum((y1 - y0) * (x1 - x0) for (y0, y1, x0, x1) in fac) * L
+    return nnz_full, P.ny * P.nx * L, nuc
+
+
+def _estimate(P, nnz_full, t_data, t_sara, t_nuc):
+    u_data, u_sara, u_nuc = _full_units(P, nnz_full)
+    return t_data * u_data + t_sara * u_sara + t_nuc * u_nuc
+
+
+def cpu_baseline(P, info):
+    """Oracle seconds per PDFB iteration of the full workload, from a bounded
+    sample (about 20 s of host work) scaled per unit of work."""
+    n_vis, side, nf = min(P.M, 100_000), 512, 4
+    t_data, t_sara, t_nuc = _oracle_sample(P, n_vis, side, nf)
+    t_full = _estimate(P, info.nnz, t_data, t_sara, t_nuc)
+    return {"value": 1.0 / t_full, "unit": "iter/s", "cores": 1, "kind": "oracle",
+            "sample": ("data term on 2 channels x %d visibilities, SARA on one %dx%d channel crop, nuclear "
+                       "dual on %d facets of one sub-cube; each scaled per unit (G entry, pixel-channel, "
+                       "facet-pixel-channel) to the full workload" % (n_vis, side, side, nf)),
+            "seconds_per_iter": t_full}
+
+
+def run_reference(args):
+    """The oracle as the reference arm (rank 0 only; other ranks exit)."""
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    from paper_2209_07604_gb300 import synth
+    from oracle import nufft as onf
+    P = synth.make_problem(args.workload)
+    geom = onf.Geometry(P.ny, P.nx, w_max=P.w_max, n_wplanes=64, pixel_size=P.pixel_size)
+    _, _, h = onf.wplane(P.w.reshape(-1), geom)
+    nnz_full = float(np.sum((geom.J + 2 * h) ** 2))
+    n_vis, side, nf = min(P.M, 20_000), 128, 1
+    per = []
+    for i in range(args.warmup + args.steps):
+        t = _oracle_sample(P, n_vis, side, nf)
+        if i >= args.warmup:
+            per.append(_estimate(P, nnz_full, *t))
+    s_step = float(np.median(per))
+    val = 1.0 / s_step
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "iter/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": s_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded VLA-like uv/w, Gaussian-blob sky, 40 dB)",
+        "config": {"workload": args.workload},
+        "cpu_baseline": {"value": val, "unit": "iter/s", "cores": 1, "kind": "oracle",
+                         "sample": ("each step: data term on 2 channels x %d visibilities, SARA on one %dx%d "
+                                    "crop, nuclear dual on %d facet; scaled per unit of work to the full "
+                                    "workload" % (n_vis, side, side, nf))},
+        "e2e": {"value": val, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="fhs", choices=["fhs", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--e2e-iters", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

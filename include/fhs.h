@@ -1,0 +1,220 @@
+/*
+ * libfhs: Faceted HyperSARA primal-dual forward-backward (PDFB) imaging on one
+ * GPU (sm_103a).  C ABI: plain host/device pointers, sizes and a CUDA stream
+ * passed as `void *` (a cudaStream_t; NULL = legacy default stream).
+ *
+ * The library solves, for C channel-interleaved spectral sub-cubes
+ * (channel l belongs to sub-cube l % C), the problem of Eq. 3 of Thouvenin et
+ * al., "Parallel faceted imaging in radio interferometry via proximal
+ * splitting (Faceted HyperSARA): II", Sec. 2.2:
+ *
+ *   minimise_{X >= 0}  sum_{l,b} iota_{B(y_{l,b}, eps_{l,b})}(Phi_{l,b} x_l)
+ *                      + mu_bar sum_q ||S_q X_c||_{*,w} + mu ||Psi^dagger X_c||_{2,1,w}
+ *
+ * with Phi_l = Theta_l G_l F Z the NUFFT measurement operator of Eq. 1
+ * (Sec. 2.1), the l2-ball data constraints of Eq. 2, the faceted low-rankness
+ * prior and the exactly faceted SARA average-joint-sparsity prior of
+ * Sec. 2.2.2, and log-sum reweighting around PDFB (Sec. 2.2.3).
+ *
+ * Conventions shared by every entry point:
+ *  - images are float32, layout [L][ny][nx] (row-major, channel-major planes);
+ *    pixel (i1, i2) has coordinates n = (i1 - ny/2, i2 - nx/2);
+ *  - visibilities are complex float32 stored as interleaved (re, im) pairs,
+ *    concatenated by channel in the caller's order (vis_offsets);
+ *  - every pointer named *_dev is device memory owned by the caller; every
+ *    other pointer is host memory owned by the caller; the library keeps no
+ *    caller pointer after a call returns;
+ *  - device work is enqueued on `stream` and is asynchronous unless the call
+ *    returns a host scalar (documented per call);
+ *  - every call returns an fhs_status and never aborts; on FHS_ERR_ARG the
+ *    problem is left unchanged; fhs_last_error() describes the last failure
+ *    of the calling thread.
+ */
+#ifndef FHS_H
+#define FHS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fhs_problem fhs_problem;
+
+typedef enum {
+    FHS_OK = 0,
+    FHS_ERR_ARG = 1,      /* invalid argument or size; nothing was changed      */
+    FHS_ERR_OOM = 2,      /* device allocation failed                           */
+    FHS_ERR_CUDA = 3,     /* a CUDA / cuFFT call failed                         */
+    FHS_ERR_TIMEOUT = 4,  /* a bounded device wait gave up                      */
+    FHS_ERR_STATE = 5     /* call not valid in the problem's current state      */
+} fhs_status;
+
+/* Problem parameters.  Mirrors the user parameters and default internal
+ * parameters of the paper's imaging pipeline (Sec. 4.2). */
+typedef struct fhs_params {
+    int32_t ny, nx;          /* image sides in pixels; both even, >= 16            */
+    int32_t n_channels;      /* L                                                  */
+    int32_t n_subcubes;      /* C; L % C == 0 (channel l -> sub-cube l % C, Eq. 3) */
+    int32_t n_blocks;        /* B data blocks per channel (Sec. 2.1)               */
+    int32_t qy, qx;          /* spatial facets of the low-rankness prior (Q=qy*qx) */
+    double  facet_overlap;   /* facet extension on the low side, fraction of tile  */
+    int32_t kb_taps;         /* J: Kaiser-Bessel taps per dimension (7)            */
+    int32_t wavelet_levels;  /* SARA decomposition depth (4); bases Dirac+db1..db8 */
+    double  w_max;           /* w-projection planes span [-w_max, w_max]; 0 = off  */
+    int32_t n_wplanes;       /* planes per sign (>= 2 when w_max > 0)              */
+    double  pixel_size;      /* radians per pixel (w-term chirp, Sec. 3.2)         */
+    double  mu;              /* l21 (joint sparsity) regularisation, >= 0          */
+    double  mu_bar;          /* nuclear (low-rankness) regularisation, >= 0        */
+    double  upsilon;         /* log-sum reweighting constant, l21 (> 0)            */
+    double  upsilon_bar;     /* log-sum reweighting constant, nuclear (> 0)        */
+    double  tau;             /* primal step; <= 0 selects 0.99/3                   */
+    double  sigma0;          /* nuclear dual step; <= 0 selects 1/max facet cover  */
+    double  sigma1;          /* l21 dual step; <= 0 selects 1 (||Psi|| = 1)        */
+    double  sigma2;          /* data dual step; <= 0 selects 1/max_l ||Phi_l||^2   */
+    int32_t power_iters;     /* power iterations for ||Phi_l||^2 (default 100)     */
+    double  power_tol;       /* relative tolerance of the power iteration          */
+} fhs_params;
+
+/* Fill *p with the defaults (J = 7, 4 levels, 64 w-planes, computed steps). */
+void fhs_default_params(fhs_params *p);
+
+/*
+ * Build a problem on the current CUDA device.
+ *  omega        host, [M_tot][2] float64: spatial frequency of each visibility
+ *               in radians per pixel, (along y, along x), each in [-pi, pi).
+ *  w            host, [M_tot] float64 w coordinate in wavelengths, or NULL (0).
+ *  y            host, [M_tot][2] float64 raw (not whitened) visibilities.
+ *  sigma        host, [L] float64 noise standard deviation per channel
+ *               (Theta_l = 1/sigma_l, natural weighting, Eq. 1).
+ *  vis_offsets  host, [L+1] int64: channel l owns visibilities
+ *               [vis_offsets[l], vis_offsets[l+1]); vis_offsets[0] = 0.
+ *  block_offsets host, [L][B+1] int64, relative to the channel start,
+ *               non-decreasing from 0 to M_l: block b of channel l (Sec. 2.1).
+ *  eps          host, [L][B] float64 l2-ball radii, or NULL for Eq. 2 with
+ *               unit-variance whitened noise: eps_{l,b}^2 = (M_l + 2 sqrt(M_l)) M_{l,b}/M_l.
+ * Copies everything it needs; builds G on the device (one row per visibility:
+ * a (J+2h) x (J+2h) box of KB samples convolved with the w-kernel of its
+ * plane); computes ||Phi_l||^2 by power iteration when sigma2 <= 0; sets
+ * X = 0, all duals to 0 and all weights to 1 (Sec. 5.2: zero initialisation).
+ * Synchronises `stream` before returning.
+ */
+fhs_status fhs_create_problem(const fhs_params *params, const double *omega, const double *w,
+                              const double *y, const double *sigma, const int64_t *vis_offsets,
+                              const int64_t *block_offsets, const double *eps, void *stream,
+                              fhs_problem **out);
+
+/* Release every device and host resource of the problem (NULL is a no-op). */
+void fhs_destroy_problem(fhs_problem *prob);
+
+typedef struct fhs_info {
+    int64_t n_vis;           /* M_tot                                              */
+    int64_t nnz;             /* stored entries of G                                */
+    int64_t n_coef;          /* SARA coefficients per channel (Dirac + db1..db8)   */
+    int64_t nuclear_size;    /* floats in the nuclear dual (all sub-cubes, facets) */
+    int64_t device_bytes;    /* device memory held by the problem                  */
+    int32_t n_facets;        /* Q                                                  */
+    int32_t iteration;       /* PDFB iterations done                               */
+    double  tau, sigma0, sigma1, sigma2;
+    double  phi_norm2_max;   /* max_l ||Phi_l||^2 (0 if sigma2 was given)          */
+} fhs_info;
+
+fhs_status fhs_get_info(const fhs_problem *prob, fhs_info *info);
+
+/* vis_dev[M_tot] (complex) = Phi_l x_l per channel (whitened, Eq. 1).
+ * x_dev: [L][ny][nx] float32.  Asynchronous. */
+fhs_status fhs_measure(fhs_problem *prob, const float *x_dev, float *vis_dev, void *stream);
+
+/* x_dev[L][ny][nx] = Re(Phi_l^H v_l), the adjoint of fhs_measure for real
+ * images.  vis_dev: [M_tot] complex in the caller's order.  Asynchronous. */
+fhs_status fhs_adjoint(fhs_problem *prob, const float *vis_dev, float *x_dev, void *stream);
+
+/* coef_dev[L][n_coef] = Psi^dagger x_l (Sec. 2.2.2): (1/3)[x; W_db1 x; ...; W_db8 x].
+ * Per basis, levels 1..J in order, each level the (y-filter, x-filter) =
+ * (lo,hi), (hi,lo), (hi,hi) subbands row-major, then the last (lo,lo) band.
+ * Level sizes n_{j+1} = floor((n_j + 2p - 1)/2) (decimated full convolution,
+ * zero extension).  Equal to the faceted transform on any tiling.  Async. */
+fhs_status fhs_sara_analysis(fhs_problem *prob, const float *x_dev, float *coef_dev, void *stream);
+
+/* x_dev[L][ny][nx] = Psi c_l, the adjoint of fhs_sara_analysis.  Async. */
+fhs_status fhs_sara_synthesis(fhs_problem *prob, const float *coef_dev, float *x_dev, void *stream);
+
+/* Run n_iter PDFB iterations (Sec. 2.2.3):
+ *   x+ = max(0, x - tau (sum_q S_q^T P_q + Psi W + Re Phi^H v)),  xbar = 2 x+ - x,
+ *   P_q <- Z - SVT(Z, mu_bar w_q), Z = P_q + sigma0 S_q xbar    (per sub-cube, facet)
+ *   W   <- Z min(1, mu w_r / ||Z_r||), Z = W + sigma1 Psi^dagger xbar (rows over channels)
+ *   v_b <- (Z - sigma2 y_b)(1 - min(1, sigma2 eps_b / ||Z - sigma2 y_b||)), Z = v_b + sigma2 Phi_b xbar.
+ * rel_change_out (host, may be NULL): ||x+ - x|| / ||x+|| of the last
+ * iteration; when non-NULL the call synchronises `stream`.            */
+fhs_status fhs_pdfb_step(fhs_problem *prob, int32_t n_iter, double *rel_change_out, void *stream);
+
+/* Log-sum reweighting (Sec. 2.2.3): w_r = upsilon/(upsilon + ||(Psi^dagger X)_r||),
+ * w_{q,i} = upsilon_bar/(upsilon_bar + sigma_i(S_q X)); duals are kept. Async. */
+fhs_status fhs_reweight(fhs_problem *prob, void *stream);
+
+/* Outer reweighting loop around PDFB: n_reweight+1 inner runs of at most
+ * max_iter/(n_reweight+1) iterations each (remainder in the last), an inner
+ * run stopping early once ||x+ - x||/||x+|| < rel_tol (tested every
+ * `check_every` iterations; <= 0 means 10), reweighting between runs.
+ * iters_out (host, may be NULL) receives the iterations done.  Synchronises. */
+fhs_status fhs_solve(fhs_problem *prob, int32_t max_iter, double rel_tol, int32_t n_reweight,
+                     int32_t check_every, int32_t *iters_out, void *stream);
+
+/* Image and state transfer (checkpoint / resume).  Device buffers, async. */
+typedef enum {
+    FHS_STATE_IMAGE = 0,       /* X, [L][ny][nx] float32                                 */
+    FHS_STATE_DUAL_DATA = 1,   /* v, [M_tot] complex (float32 pairs), caller's order     */
+    FHS_STATE_DUAL_SARA = 2,   /* W, [L][n_coef] float32, layout of fhs_sara_analysis    */
+    FHS_STATE_DUAL_NUCLEAR = 3,/* P, per sub-cube c, per facet q (row-major facets),
+                                  [L_c][wy_q][wx_q] float32, concatenated                */
+    FHS_STATE_WEIGHTS_SARA = 4,/* w_r, [C][n_coef] float32                               */
+    FHS_STATE_WEIGHTS_NUC = 5  /* w_{q,i}, [C][Q][L_c] float32                           */
+} fhs_state_part;
+
+/* Number of float32 values of one part.  Setting a dual recomputes the
+ * adjoint term it feeds into the next primal step, so get_state of every part
+ * followed by set_state of every part resumes the iteration exactly. */
+fhs_status fhs_state_size(const fhs_problem *prob, int32_t part, int64_t *n_floats);
+fhs_status fhs_get_state(fhs_problem *prob, int32_t part, float *dst_dev, void *stream);
+fhs_status fhs_set_state(fhs_problem *prob, int32_t part, const float *src_dev, void *stream);
+
+/* ||Phi_l||^2 for every channel by power iteration (n_iter steps from a fixed
+ * start; returns into the host array norms[L]).  Synchronises.          */
+fhs_status fhs_operator_norms(fhs_problem *prob, int32_t n_iter, double *norms, void *stream);
+
+/* Tracing: per-phase device time of the PDFB iteration, measured with CUDA
+ * events recorded on the caller's stream around each phase while enabled.
+ * Phases, in iteration order: */
+typedef enum {
+    FHS_PHASE_PRIMAL = 0,        /* primal step + adjoint gathers + zero-pad     */
+    FHS_PHASE_FFT_FWD = 1,       /* F (cuFFT)                                    */
+    FHS_PHASE_DEGRID_GRID = 2,   /* single pass over G: Phi xbar, dual, G^H      */
+    FHS_PHASE_L2BALL = 3,        /* block l2-ball factors + block-grid combine   */
+    FHS_PHASE_FFT_INV = 4,       /* F^H (cuFFT)                                  */
+    FHS_PHASE_SARA = 5,          /* Psi^dagger, weighted l21 dual, Psi           */
+    FHS_PHASE_NUCLEAR = 6,       /* facet Grams, FP64 eig, SVT dual              */
+    FHS_N_PHASES = 7
+} fhs_phase;
+
+/* on != 0 starts recording (and clears the totals); 0 stops. */
+fhs_status fhs_profile_enable(fhs_problem *prob, int32_t on);
+/* Synchronises the recorded events and returns, per phase, the summed
+ * milliseconds (ms_out[FHS_N_PHASES]) and the number of timed iterations
+ * (*iters_out).  Either pointer may be NULL.                             */
+fhs_status fhs_profile_read(fhs_problem *prob, double *ms_out, int64_t *iters_out);
+/* Number of libfhs kernels launched since the problem was created (cuFFT's
+ * own kernels are not counted). */
+fhs_status fhs_kernel_launches(const fhs_problem *prob, int64_t *count_out);
+
+/* Host utility: the library's own db_p low-pass filter (2p taps, minimum
+ * phase, sum sqrt(2)), computed by spectral factorisation (Daubechies 1988). */
+fhs_status fhs_daubechies_filter(int32_t p, double *h_out);
+
+/* Text of the last error on the calling thread ("" if none). */
+const char *fhs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FHS_H */

@@ -1,0 +1,331 @@
+"""Python binding of libfhs (Faceted HyperSARA PDFB on one GB300 GPU).
+
+Argument marshalling only: every entry point forwards to the C ABI declared
+in ``include/fhs.h`` (same names), passing raw pointers of numpy host arrays
+or torch CUDA tensors and the current torch CUDA stream.  There is no CPU
+path: if ``libfhs.so`` is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfhs.so")
+
+FHS_OK, FHS_ERR_ARG, FHS_ERR_OOM, FHS_ERR_CUDA, FHS_ERR_TIMEOUT, FHS_ERR_STATE = range(6)
+STATE_IMAGE, STATE_DUAL_DATA, STATE_DUAL_SARA, STATE_DUAL_NUCLEAR, STATE_WEIGHTS_SARA, STATE_WEIGHTS_NUC = range(6)
+
+EXPORTED = [
+    "fhs_default_params", "fhs_create_problem", "fhs_destroy_problem", "fhs_get_info", "fhs_measure",
+    "fhs_adjoint", "fhs_sara_analysis", "fhs_sara_synthesis", "fhs_pdfb_step", "fhs_reweight", "fhs_solve",
+    "fhs_state_size", "fhs_get_state", "fhs_set_state", "fhs_operator_norms", "fhs_daubechies_filter",
+    "fhs_last_error", "fhs_profile_enable", "fhs_profile_read", "fhs_kernel_launches",
+]
+PHASES = ["primal", "fft_fwd", "degrid_grid", "l2ball", "fft_inv", "sara", "nuclear"]
+
+
+class FhsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("libfhs status %d: %s" % (status, msg))
+        self.status = status
+
+
+class fhs_params(C.Structure):
+    _fields_ = [
+        ("ny", C.c_int32), ("nx", C.c_int32), ("n_channels", C.c_int32), ("n_subcubes", C.c_int32),
+        ("n_blocks", C.c_int32), ("qy", C.c_int32), ("qx", C.c_int32), ("facet_overlap", C.c_double),
+        ("kb_taps", C.c_int32), ("wavelet_levels", C.c_int32), ("w_max", C.c_double), ("n_wplanes", C.c_int32),
+        ("pixel_size", C.c_double), ("mu", C.c_double), ("mu_bar", C.c_double), ("upsilon", C.c_double),
+        ("upsilon_bar", C.c_double), ("tau", C.c_double), ("sigma0", C.c_double), ("sigma1", C.c_double),
+        ("sigma2", C.c_double), ("power_iters", C.c_int32), ("power_tol", C.c_double),
+    ]
+
+
+class fhs_info(C.Structure):
+    _fields_ = [
+        ("n_vis", C.c_int64), ("nnz", C.c_int64), ("n_coef", C.c_int64), ("nuclear_size", C.c_int64),
+        ("device_bytes", C.c_int64), ("n_facets", C.c_int32), ("iteration", C.c_int32), ("tau", C.c_double),
+        ("sigma0", C.c_double), ("sigma1", C.c_double), ("sigma2", C.c_double), ("phi_norm2_max", C.c_double),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    """Load libfhs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libfhs.so not found at %s: run __graft_entry__.build() (needs nvcc)" % path)
+    lib = C.CDLL(path)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    P = C.POINTER
+    sig = {
+        "fhs_default_params": (None, [P(fhs_params)]),
+        "fhs_create_problem": (C.c_int, [P(fhs_params), vp, vp, vp, vp, vp, vp, vp, vp, P(vp)]),
+        "fhs_destroy_problem": (None, [vp]),
+        "fhs_get_info": (C.c_int, [vp, P(fhs_info)]),
+        "fhs_measure": (C.c_int, [vp, vp, vp, vp]),
+        "fhs_adjoint": (C.c_int, [vp, vp, vp, vp]),
+        "fhs_sara_analysis": (C.c_int, [vp, vp, vp, vp]),
+        "fhs_sara_synthesis": (C.c_int, [vp, vp, vp, vp]),
+        "fhs_pdfb_step": (C.c_int, [vp, i32, P(dbl), vp]),
+        "fhs_reweight": (C.c_int, [vp, vp]),
+        "fhs_solve": (C.c_int, [vp, i32, dbl, i32, i32, P(i32), vp]),
+        "fhs_state_size": (C.c_int, [vp, i32, P(i64)]),
+        "fhs_get_state": (C.c_int, [vp, i32, vp, vp]),
+        "fhs_set_state": (C.c_int, [vp, i32, vp, vp]),
+        "fhs_operator_norms": (C.c_int, [vp, i32, vp, vp]),
+        "fhs_daubechies_filter": (C.c_int, [i32, vp]),
+        "fhs_last_error": (C.c_char_p, []),
+        "fhs_profile_enable": (C.c_int, [vp, i32]),
+        "fhs_profile_read": (C.c_int, [vp, vp, P(i64)]),
+        "fhs_kernel_launches": (C.c_int, [vp, P(i64)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != FHS_OK:
+        raise FhsError(status, load_library().fhs_last_error().decode())
+
+
+def _stream(stream):
+    """cudaStream_t handle: the given one, else torch's current stream (NULL, the
+    legacy default stream, when torch sees no CUDA device)."""
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    import torch
+    if not torch.cuda.is_available():
+        return C.c_void_p(0)
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return C.c_void_p(t.ctypes.data)
+    return C.c_void_p(t.data_ptr())
+
+
+def _dev(t, dtype_name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch." + dtype_name):
+        raise TypeError("expected a contiguous CUDA torch.%s tensor" % dtype_name)
+    return C.c_void_p(t.data_ptr())
+
+
+def default_params(**kw) -> fhs_params:
+    p = fhs_params()
+    load_library().fhs_default_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+# --- entry points (same names as the C ABI) ---------------------------------
+
+def fhs_create_problem(params: fhs_params, omega, w, y, sigma, vis_offsets, block_offsets, eps=None, stream=None):
+    omega = np.ascontiguousarray(omega, dtype=np.float64)
+    w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+    yc = np.ascontiguousarray(y)
+    if np.iscomplexobj(yc):
+        yc = np.ascontiguousarray(np.stack([yc.real, yc.imag], axis=-1), dtype=np.float64)
+    else:
+        yc = np.ascontiguousarray(yc, dtype=np.float64)
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    vis_offsets = np.ascontiguousarray(vis_offsets, dtype=np.int64)
+    block_offsets = np.ascontiguousarray(block_offsets, dtype=np.int64)
+    eps = None if eps is None else np.ascontiguousarray(eps, dtype=np.float64)
+    h = C.c_void_p()
+    _check(load_library().fhs_create_problem(C.byref(params), _ptr(omega), _ptr(w), _ptr(yc), _ptr(sigma),
+                                             _ptr(vis_offsets), _ptr(block_offsets), _ptr(eps), _stream(stream),
+                                             C.byref(h)))
+    return h
+
+
+def fhs_destroy_problem(prob):
+    load_library().fhs_destroy_problem(prob)
+
+
+def fhs_get_info(prob) -> fhs_info:
+    info = fhs_info()
+    _check(load_library().fhs_get_info(prob, C.byref(info)))
+    return info
+
+
+def fhs_measure(prob, x, vis, stream=None):
+    _check(load_library().fhs_measure(prob, _dev(x, "float32"), _dev(vis, "complex64"), _stream(stream)))
+
+
+def fhs_adjoint(prob, vis, x, stream=None):
+    _check(load_library().fhs_adjoint(prob, _dev(vis, "complex64"), _dev(x, "float32"), _stream(stream)))
+
+
+def fhs_sara_analysis(prob, x, coef, stream=None):
+    _check(load_library().fhs_sara_analysis(prob, _dev(x, "float32"), _dev(coef, "float32"), _stream(stream)))
+
+
+def fhs_sara_synthesis(prob, coef, x, stream=None):
+    _check(load_library().fhs_sara_synthesis(prob, _dev(coef, "float32"), _dev(x, "float32"), _stream(stream)))
+
+
+def fhs_pdfb_step(prob, n_iter=1, want_rel=False, stream=None):
+    rel = C.c_double(0.0)
+    _check(load_library().fhs_pdfb_step(prob, int(n_iter), C.byref(rel) if want_rel else None, _stream(stream)))
+    return rel.value if want_rel else None
+
+
+def fhs_reweight(prob, stream=None):
+    _check(load_library().fhs_reweight(prob, _stream(stream)))
+
+
+def fhs_solve(prob, max_iter, rel_tol, n_reweight=0, check_every=10, stream=None):
+    it = C.c_int32(0)
+    _check(load_library().fhs_solve(prob, int(max_iter), float(rel_tol), int(n_reweight), int(check_every),
+                                    C.byref(it), _stream(stream)))
+    return it.value
+
+
+def fhs_state_size(prob, part) -> int:
+    n = C.c_int64(0)
+    _check(load_library().fhs_state_size(prob, int(part), C.byref(n)))
+    return n.value
+
+
+def fhs_get_state(prob, part, dst, stream=None):
+    _check(load_library().fhs_get_state(prob, int(part), _dev(dst, "float32"), _stream(stream)))
+
+
+def fhs_set_state(prob, part, src, stream=None):
+    _check(load_library().fhs_set_state(prob, int(part), _dev(src, "float32"), _stream(stream)))
+
+
+def fhs_operator_norms(prob, n_iter, L, stream=None) -> np.ndarray:
+    out = np.zeros(L, dtype=np.float64)
+    _check(load_library().fhs_operator_norms(prob, int(n_iter), _ptr(out), _stream(stream)))
+    return out
+
+
+def fhs_daubechies_filter(p: int) -> np.ndarray:
+    out = np.zeros(2 * p, dtype=np.float64)
+    _check(load_library().fhs_daubechies_filter(int(p), _ptr(out)))
+    return out
+
+
+def fhs_profile_enable(prob, on: bool):
+    _check(load_library().fhs_profile_enable(prob, 1 if on else 0))
+
+
+def fhs_profile_read(prob):
+    """(dict phase -> summed ms, timed iterations)."""
+    ms = np.zeros(len(PHASES), dtype=np.float64)
+    it = C.c_int64(0)
+    _check(load_library().fhs_profile_read(prob, _ptr(ms), C.byref(it)))
+    return dict(zip(PHASES, ms.tolist())), it.value
+
+
+def fhs_kernel_launches(prob) -> int:
+    n = C.c_int64(0)
+    _check(load_library().fhs_kernel_launches(prob, C.byref(n)))
+    return n.value
+
+
+# --- convenience wrapper ----------------------------------------------------
+
+class Problem:
+    """Owns one libfhs problem built from host arrays; device tensors via torch."""
+
+    def __init__(self, params: fhs_params, omega, w, y, sigma, vis_offsets, block_offsets, eps=None, stream=None):
+        self.params = params
+        self.L = int(params.n_channels)
+        self.ny, self.nx = int(params.ny), int(params.nx)
+        self.handle = fhs_create_problem(params, omega, w, y, sigma, vis_offsets, block_offsets, eps, stream)
+        self.info = fhs_get_info(self.handle)
+
+    @classmethod
+    def from_synth(cls, prob, mu, mu_bar, stream=None, **kw):
+        """Build from a ``synth.Problem`` (all channels share one visibility count)."""
+        L, M = prob.omega.shape[:2]
+        params = default_params(ny=prob.ny, nx=prob.nx, n_channels=L, n_subcubes=prob.C, n_blocks=prob.B,
+                                qy=prob.qy, qx=prob.qx, facet_overlap=prob.overlap, w_max=prob.w_max,
+                                pixel_size=prob.pixel_size, mu=mu, mu_bar=mu_bar)
+        for k, v in kw.items():
+            setattr(params, k, v)
+        vis_off = np.arange(L + 1, dtype=np.int64) * M
+        return cls(params, prob.omega.reshape(-1, 2), prob.w.reshape(-1), prob.y.reshape(-1), prob.sigma,
+                   vis_off, prob.block_offsets, None, stream)
+
+    def close(self):
+        if self.handle:
+            fhs_destroy_problem(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _img(self):
+        import torch
+        return torch.empty((self.L, self.ny, self.nx), dtype=torch.float32, device="cuda")
+
+    def measure(self, x):
+        import torch
+        vis = torch.empty(self.info.n_vis, dtype=torch.complex64, device="cuda")
+        fhs_measure(self.handle, x, vis)
+        return vis
+
+    def adjoint(self, vis):
+        x = self._img()
+        fhs_adjoint(self.handle, vis, x)
+        return x
+
+    def sara_analysis(self, x):
+        import torch
+        c = torch.empty((self.L, self.info.n_coef), dtype=torch.float32, device="cuda")
+        fhs_sara_analysis(self.handle, x, c)
+        return c
+
+    def sara_synthesis(self, c):
+        x = self._img()
+        fhs_sara_synthesis(self.handle, c, x)
+        return x
+
+    def step(self, n_iter=1, want_rel=False):
+        return fhs_pdfb_step(self.handle, n_iter, want_rel)
+
+    def reweight(self):
+        fhs_reweight(self.handle)
+
+    def solve(self, max_iter, rel_tol, n_reweight=0, check_every=10):
+        return fhs_solve(self.handle, max_iter, rel_tol, n_reweight, check_every)
+
+    def get_state(self, part):
+        import torch
+        t = torch.empty(fhs_state_size(self.handle, part), dtype=torch.float32, device="cuda")
+        fhs_get_state(self.handle, part, t)
+        return t
+
+    def set_state(self, part, t):
+        fhs_set_state(self.handle, part, t)
+
+    def image(self):
+        return self.get_state(STATE_IMAGE).reshape(self.L, self.ny, self.nx)
+
+    def operator_norms(self, n_iter=100):
+        return fhs_operator_norms(self.handle, n_iter, self.L)

@@ -1,0 +1,883 @@
+// C-ABI of libfhs: problem set-up (visibility sorting, w-kernels, G build,
+// SARA layout, facets, step sizes), the PDFB iteration driver, reweighting,
+// state transfer.  Every device computation is one of the kernels in k_*.cu
+// or a cuFFT transform; the host only orders launches.
+#include "fhs_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+using namespace fhs;
+
+namespace {
+
+thread_local std::string g_err;
+
+fhs_status fail(fhs_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CU(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(e_ == cudaErrorMemoryAllocation ? FHS_ERR_OOM : FHS_ERR_CUDA, "%s: %s (%s:%d)", #call, \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                               \
+    } while (0)
+
+#define CUFFT(call)                                                                                \
+    do {                                                                                           \
+        cufftResult r_ = (call);                                                                   \
+        if (r_ != CUFFT_SUCCESS) return fail(FHS_ERR_CUDA, "%s: cufft error %d", #call, int(r_));  \
+    } while (0)
+
+#define TRY(call)                                                                                  \
+    do {                                                                                           \
+        fhs_status s_ = (call);                                                                    \
+        if (s_ != FHS_OK) return s_;                                                               \
+    } while (0)
+
+template <typename T>
+fhs_status dev_alloc(fhs_problem *p, T **ptr, size_t count, bool zero = true) {
+    *ptr = nullptr;
+    if (count == 0) count = 1;
+    void *q = nullptr;
+    const size_t bytes = count * sizeof(T);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FHS_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    p->allocs.push_back(q);
+    p->bytes += bytes;
+    if (zero) {
+        e = cudaMemset(q, 0, bytes);
+        if (e != cudaSuccess) return fail(FHS_ERR_CUDA, "cudaMemset failed: %s", cudaGetErrorString(e));
+    }
+    *ptr = static_cast<T *>(q);
+    return FHS_OK;
+}
+
+template <typename T>
+fhs_status upload(T *dst, const T *src, size_t count, cudaStream_t s) {
+    if (count == 0) return FHS_OK;
+    CU(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyHostToDevice, s));
+    return FHS_OK;
+}
+
+void free_all(fhs_problem *p) {
+    for (void *q : p->allocs) cudaFree(q);
+    p->allocs.clear();
+    if (p->plan_ok) cufftDestroy(p->plan);
+    p->plan_ok = false;
+}
+
+inline cudaStream_t S(void *s) { return static_cast<cudaStream_t>(s); }
+
+fhs_status check_params(const fhs_params *q) {
+    if (!q) return fail(FHS_ERR_ARG, "params is NULL");
+    if (q->ny < 16 || q->nx < 16 || (q->ny & 1) || (q->nx & 1))
+        return fail(FHS_ERR_ARG, "image sides must be even and >= 16 (got %d x %d)", q->ny, q->nx);
+    if (2LL * q->ny >= 65536 || 2LL * q->nx >= 65536) return fail(FHS_ERR_ARG, "image side too large");
+    if (q->n_channels < 1 || q->n_subcubes < 1 || q->n_channels % q->n_subcubes)
+        return fail(FHS_ERR_ARG, "n_channels must be a positive multiple of n_subcubes");
+    if (q->n_channels / q->n_subcubes > 16)
+        return fail(FHS_ERR_ARG, "at most 16 channels per sub-cube are supported");
+    if (q->n_blocks < 1) return fail(FHS_ERR_ARG, "n_blocks must be >= 1");
+    if (q->qy < 1 || q->qx < 1 || q->qy > q->ny || q->qx > q->nx) return fail(FHS_ERR_ARG, "bad facet grid");
+    if (!(q->facet_overlap >= 0.0 && q->facet_overlap < 1.0)) return fail(FHS_ERR_ARG, "facet_overlap must be in [0, 1)");
+    if (q->kb_taps < 2 || q->kb_taps > 8) return fail(FHS_ERR_ARG, "kb_taps must be in [2, 8]");
+    if (q->wavelet_levels < 1 || q->wavelet_levels > kMaxLevels) return fail(FHS_ERR_ARG, "wavelet_levels must be in [1, 6]");
+    if (q->w_max < 0.0) return fail(FHS_ERR_ARG, "w_max must be >= 0");
+    if (q->w_max > 0.0 && (q->n_wplanes < 2 || q->n_wplanes > 4096)) return fail(FHS_ERR_ARG, "n_wplanes must be in [2, 4096]");
+    if (q->w_max > 0.0 && !(q->pixel_size > 0.0)) return fail(FHS_ERR_ARG, "pixel_size must be > 0 with w-terms");
+    if (!(q->mu >= 0.0) || !(q->mu_bar >= 0.0)) return fail(FHS_ERR_ARG, "mu and mu_bar must be >= 0");
+    if (!(q->upsilon > 0.0) || !(q->upsilon_bar > 0.0)) return fail(FHS_ERR_ARG, "upsilon and upsilon_bar must be > 0");
+    return FHS_OK;
+}
+
+fhs_status fft(fhs_problem *p, float2 *in, float2 *out, int dir, cudaStream_t s) {
+    CUFFT(cufftSetStream(p->plan, s));
+    CUFFT(cufftExecC2C(p->plan, reinterpret_cast<cufftComplex *>(in), reinterpret_cast<cufftComplex *>(out), dir));
+    return FHS_OK;
+}
+
+// Phi^H applied to sorted visibilities `vis`, result as an inverse-FFT'd grid in `grid`.
+fhs_status adjoint_to_grid(fhs_problem *p, const float2 *vis, float2 *grid, cudaStream_t s) {
+    CU(cudaMemsetAsync(grid, 0, sizeof(float2) * p->K * p->L, s));
+    CU(launch_grid(p, vis, grid, s));
+    TRY(fft(p, grid, grid, CUFFT_INVERSE, s));
+    return FHS_OK;
+}
+
+fhs_status forward_from_image(fhs_problem *p, const float *x, float2 *vis_sorted, cudaStream_t s) {
+    CU(launch_zpad(p, x, p->grid_in, s));
+    TRY(fft(p, p->grid_in, p->grid_aux, CUFFT_FORWARD, s));
+    CU(launch_degrid(p, p->grid_aux, vis_sorted, s));
+    return FHS_OK;
+}
+
+fhs_status adjoint_to_image(fhs_problem *p, const float2 *vis_sorted, float *x, cudaStream_t s) {
+    TRY(adjoint_to_grid(p, vis_sorted, p->grid_aux, s));
+    CU(launch_crop(p, p->grid_aux, x, s));
+    return FHS_OK;
+}
+
+// ||Phi_l||^2 by power iteration from a fixed start; uses Xbar and A_sara as work images.
+fhs_status power_iteration(fhs_problem *p, int n_iter, double tol, std::vector<double> &lam, cudaStream_t s) {
+    const long long LN = (long long)p->L * p->N;
+    std::vector<float> x0(LN);
+    unsigned long long st = 0x9E3779B97F4A7C15ull;
+    for (long long i = 0; i < LN; ++i) {
+        st = st * 6364136223846793005ull + 1442695040888963407ull;
+        x0[i] = float(double(st >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+    }
+    double *norms = p->pnorms;
+    float *x = p->Xbar, *y = p->A_sara;
+    TRY(upload(x, x0.data(), LN, s));
+    CU(cudaMemsetAsync(norms, 0, sizeof(double) * 2 * p->L, s));
+    CU(launch_power_dots(p, x, x, norms, s));
+    CU(launch_power_scale(p, x, x, norms, s));
+    lam.assign(p->L, 0.0);
+    std::vector<double> h(2 * p->L), prev(p->L, 0.0);
+    for (int it = 0; it < n_iter; ++it) {
+        TRY(forward_from_image(p, x, p->vis_tmp, s));
+        TRY(adjoint_to_image(p, p->vis_tmp, y, s));
+        CU(cudaMemsetAsync(norms, 0, sizeof(double) * 2 * p->L, s));
+        CU(launch_power_dots(p, x, y, norms, s));
+        CU(launch_power_scale(p, y, x, norms, s));
+        if ((it + 1) % 5 == 0 || it + 1 == n_iter) {
+            CU(cudaMemcpyAsync(h.data(), norms, sizeof(double) * 2 * p->L, cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+            double worst = 0.0;
+            for (int l = 0; l < p->L; ++l) {
+                lam[l] = h[2 * l];
+                worst = std::max(worst, std::fabs(lam[l] - prev[l]) / std::max(std::fabs(lam[l]), 1e-300));
+                prev[l] = lam[l];
+            }
+            if (worst < tol) break;
+        }
+    }
+    CU(cudaMemsetAsync(p->Xbar, 0, sizeof(float) * LN, s));
+    CU(cudaMemsetAsync(p->A_sara, 0, sizeof(float) * LN, s));
+    return FHS_OK;
+}
+
+bool sara_active(const fhs_problem *p) { return p->prm.mu > 0.0; }
+bool nuc_active(const fhs_problem *p) { return p->prm.mu_bar > 0.0; }
+
+// Records an event pair around one phase of the iteration while tracing is on.
+struct Phase {
+    fhs_problem *p;
+    cudaStream_t s;
+    int id;
+    cudaEvent_t a = nullptr, b = nullptr;
+    Phase(fhs_problem *p_, cudaStream_t s_, int id_) : p(p_), s(s_), id(id_) {
+        if (!p->prof_on) return;
+        a = take();
+        b = take();
+        if (a) cudaEventRecord(a, s);
+    }
+    cudaEvent_t take() {
+        if (!p->ev_pool.empty()) {
+            cudaEvent_t e = p->ev_pool.back();
+            p->ev_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+        return e;
+    }
+    ~Phase() {
+        if (!p->prof_on || !a || !b) return;
+        cudaEventRecord(b, s);
+        p->ev_used.push_back({id, {a, b}});
+    }
+};
+
+fhs_status one_iteration(fhs_problem *p, cudaStream_t s) {
+    CU(cudaMemsetAsync(p->red, 0, 2 * sizeof(double), s));
+    {
+        Phase ph(p, s, FHS_PHASE_PRIMAL);
+        CU(launch_primal(p, s));
+    }
+    // data fidelity: F, single pass over G, l2-ball factors, combine, F^H
+    {
+        Phase ph(p, s, FHS_PHASE_FFT_FWD);
+        TRY(fft(p, p->grid_in, p->grid_work, CUFFT_FORWARD, s));
+    }
+    {
+        Phase ph(p, s, FHS_PHASE_DEGRID_GRID);
+        CU(launch_degrid_grid_fused(p, s));
+    }
+    {
+        Phase ph(p, s, FHS_PHASE_L2BALL);
+        CU(launch_block_finalize(p, s));
+        CU(launch_combine(p, s));
+    }
+    {
+        Phase ph(p, s, FHS_PHASE_FFT_INV);
+        TRY(fft(p, p->grid_work, p->grid_work, CUFFT_INVERSE, s));
+    }
+    // average joint sparsity
+    if (sara_active(p)) {
+        Phase ph(p, s, FHS_PHASE_SARA);
+        CU(launch_sara_analysis(p, p->Xbar, p->coef_tmp, s));
+        CU(launch_l21_dual(p, s));
+        CU(launch_sara_synthesis(p, p->W, p->A_sara, s));
+    }
+    // faceted low-rankness
+    if (nuc_active(p)) {
+        Phase ph(p, s, FHS_PHASE_NUCLEAR);
+        CU(launch_nuclear_gram(p, p->Xbar, true, s));
+        CU(launch_nuclear_eig(p, false, s));
+        CU(launch_nuclear_apply(p, s));
+    }
+    if (p->prof_on) p->prof_iters++;
+    p->iteration++;
+    return FHS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fhs_last_error(void) { return g_err.c_str(); }
+
+void fhs_default_params(fhs_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->ny = p->nx = 256;
+    p->n_channels = 1;
+    p->n_subcubes = 1;
+    p->n_blocks = 1;
+    p->qy = p->qx = 1;
+    p->facet_overlap = 0.0;
+    p->kb_taps = 7;
+    p->wavelet_levels = 4;
+    p->w_max = 0.0;
+    p->n_wplanes = 64;
+    p->pixel_size = 0.0;
+    p->mu = 0.0;
+    p->mu_bar = 0.0;
+    p->upsilon = 1e-3;
+    p->upsilon_bar = 1e-3;
+    p->tau = p->sigma0 = p->sigma1 = p->sigma2 = 0.0;
+    p->power_iters = 100;
+    p->power_tol = 1e-7;
+}
+
+fhs_status fhs_daubechies_filter(int32_t p, double *h_out) {
+    if (p < 1 || p > kNumDb || !h_out) return fail(FHS_ERR_ARG, "p must be in [1, 8] and h_out non-NULL");
+    const std::vector<double> h = daubechies(p);
+    std::copy(h.begin(), h.end(), h_out);
+    return FHS_OK;
+}
+
+fhs_status fhs_create_problem(const fhs_params *params, const double *omega, const double *w, const double *y,
+                              const double *sigma, const int64_t *vis_offsets, const int64_t *block_offsets,
+                              const double *eps_in, void *stream, fhs_problem **out) {
+    g_err.clear();
+    if (!out) return fail(FHS_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    TRY(check_params(params));
+    if (!omega || !y || !sigma || !vis_offsets || !block_offsets) return fail(FHS_ERR_ARG, "NULL input array");
+    const fhs_params &q = *params;
+    const int L = q.n_channels, B = q.n_blocks, J = q.kb_taps;
+    if (vis_offsets[0] != 0) return fail(FHS_ERR_ARG, "vis_offsets[0] must be 0");
+    for (int l = 0; l < L; ++l) {
+        if (vis_offsets[l + 1] < vis_offsets[l]) return fail(FHS_ERR_ARG, "vis_offsets must be non-decreasing");
+        if (!(sigma[l] > 0.0)) return fail(FHS_ERR_ARG, "sigma[%d] must be > 0", l);
+        const int64_t Ml = vis_offsets[l + 1] - vis_offsets[l];
+        const int64_t *bo = block_offsets + (int64_t)l * (B + 1);
+        if (bo[0] != 0 || bo[B] != Ml) return fail(FHS_ERR_ARG, "block_offsets of channel %d must run from 0 to M_l", l);
+        for (int b = 0; b < B; ++b)
+            if (bo[b + 1] < bo[b]) return fail(FHS_ERR_ARG, "block_offsets must be non-decreasing");
+    }
+    const long long Mtot = vis_offsets[L];
+    for (long long i = 0; i < Mtot; ++i) {
+        const double a = omega[2 * i], b = omega[2 * i + 1];
+        if (!(a >= -M_PI && a < M_PI && b >= -M_PI && b < M_PI))
+            return fail(FHS_ERR_ARG, "omega[%lld] outside [-pi, pi)", i);
+        if (!std::isfinite(y[2 * i]) || !std::isfinite(y[2 * i + 1])) return fail(FHS_ERR_ARG, "y[%lld] not finite", i);
+        if (w && !std::isfinite(w[i])) return fail(FHS_ERR_ARG, "w[%lld] not finite", i);
+    }
+    cudaStream_t s = S(stream);
+
+    fhs_problem *p = new (std::nothrow) fhs_problem();
+    if (!p) return fail(FHS_ERR_OOM, "host allocation failed");
+    auto guard = [&](fhs_status st) {
+        if (st != FHS_OK) {
+            cudaStreamSynchronize(s);
+            free_all(p);
+            delete p;
+        }
+        return st;
+    };
+    p->prm = q;
+    p->L = L; p->C = q.n_subcubes; p->Lc = L / q.n_subcubes; p->B = B; p->J = J;
+    p->ny = q.ny; p->nx = q.nx; p->K1 = 2 * q.ny; p->K2 = 2 * q.nx;
+    p->N = (long long)q.ny * q.nx;
+    p->K = (long long)p->K1 * p->K2;
+    p->Mtot = Mtot;
+    p->vis_off.assign(vis_offsets, vis_offsets + L + 1);
+    p->n_seg = L * B;
+    p->seg_off.resize(p->n_seg + 1);
+    for (int l = 0; l < L; ++l)
+        for (int b = 0; b < B; ++b) p->seg_off[l * B + b] = vis_offsets[l] + block_offsets[(int64_t)l * (B + 1) + b];
+    p->seg_off[p->n_seg] = Mtot;
+
+    // ---- per-visibility geometry, w-plane, tile key; counting sort per segment
+    const int K1 = p->K1, K2 = p->K2;
+    const int P1 = q.w_max > 0.0 ? q.n_wplanes - 1 : 0;
+    const double dw = q.w_max > 0.0 ? q.w_max / P1 : 0.0;
+    const int ntx = (K2 + kTile - 1) / kTile, nty = (K1 + kTile - 1) / kTile;
+    std::vector<int> key(Mtot), pl(Mtot), corner1(Mtot), corner2(Mtot), Tv(Mtot);
+    for (long long i = 0; i < Mtot; ++i) {
+        const double k1 = omega[2 * i] * K1 / (2.0 * M_PI);
+        const double k2 = omega[2 * i + 1] * K2 / (2.0 * M_PI);
+        const long long p01 = (long long)std::floor(k1 - J / 2.0) + 1;
+        const long long p02 = (long long)std::floor(k2 - J / 2.0) + 1;
+        int pv = 0, h = 0;
+        if (P1 > 0) {
+            const double wv = w ? w[i] : 0.0;
+            long long pa = (long long)std::floor(std::fabs(wv) / dw + 0.5);
+            if (pa > P1) pa = P1;
+            pv = int(wv < 0 ? -pa : pa);
+            h = (8 * std::abs(pv) + P1) / (2 * P1);
+        }
+        const int T = J + 2 * h;
+        long long c1 = (p01 - h) % K1; if (c1 < 0) c1 += K1;
+        long long c2 = (p02 - h) % K2; if (c2 < 0) c2 += K2;
+        corner1[i] = int(c1); corner2[i] = int(c2); Tv[i] = T; pl[i] = pv + P1;
+        key[i] = int(c1 / kTile) * ntx + int(c2 / kTile);
+    }
+    const int nkeys = nty * ntx;
+    std::vector<long long> perm(Mtot);
+    {
+        std::vector<long long> cnt(nkeys + 1);
+        for (int sg = 0; sg < p->n_seg; ++sg) {
+            const long long a = p->seg_off[sg], b = p->seg_off[sg + 1];
+            std::fill(cnt.begin(), cnt.end(), 0);
+            for (long long i = a; i < b; ++i) cnt[key[i] + 1]++;
+            for (int k = 0; k < nkeys; ++k) cnt[k + 1] += cnt[k];
+            for (long long i = a; i < b; ++i) perm[a + cnt[key[i]]++] = i;
+        }
+    }
+    std::vector<int2> meta(Mtot);
+    std::vector<long long> rowptr(Mtot + 1);
+    std::vector<double2> kap(Mtot);
+    std::vector<short> plane(Mtot);
+    std::vector<float2> yw(Mtot);
+    rowptr[0] = 0;
+    for (long long v = 0; v < Mtot; ++v) {
+        const long long i = perm[v];
+        meta[v] = make_int2(corner1[i] | (corner2[i] << 16), Tv[i]);
+        rowptr[v + 1] = rowptr[v] + (long long)Tv[i] * Tv[i];
+        kap[v] = make_double2(omega[2 * i] * K1 / (2.0 * M_PI), omega[2 * i + 1] * K2 / (2.0 * M_PI));
+        plane[v] = short(pl[i]);
+    }
+    for (int l = 0; l < L; ++l)
+        for (long long v = vis_offsets[l]; v < vis_offsets[l + 1]; ++v) {
+            const long long i = perm[v];
+            yw[v] = make_float2(float(y[2 * i] / sigma[l]), float(y[2 * i + 1] / sigma[l]));
+        }
+    p->nnz = rowptr[Mtot];
+    { std::vector<int> t; t.swap(key); } { std::vector<int> t; t.swap(corner1); } { std::vector<int> t; t.swap(corner2); }
+
+    // ---- w-kernel table: planes -P1..P1, per axis up to 2*kMaxWHalf+1 taps
+    const int n_planes = 2 * P1 + 1;
+    std::vector<char> used(n_planes, 0);
+    for (long long i = 0; i < Mtot; ++i) used[pl[i]] = 1;
+    std::vector<double2> wk((size_t)n_planes * 2 * (2 * kMaxWHalf + 1), make_double2(0.0, 0.0));
+    for (int pi = 0; pi < n_planes; ++pi) {
+        if (!used[pi]) continue;
+        const int pv = pi - P1;
+        const int h = P1 > 0 ? (8 * std::abs(pv) + P1) / (2 * P1) : 0;
+        const double wp = pv * dw;
+        std::complex<double> ck[2 * kMaxWHalf + 1];
+        for (int dim = 0; dim < 2; ++dim) {
+            wkernel(wp, dim ? q.nx : q.ny, dim ? K2 : K1, q.pixel_size, h, ck);
+            for (int jj = 0; jj < 2 * h + 1; ++jj)
+                wk[((size_t)pi * 2 + dim) * (2 * kMaxWHalf + 1) + jj] = make_double2(ck[jj].real(), ck[jj].imag());
+        }
+    }
+
+    // ---- chunks of at most CH visibilities inside one segment
+    long long CH = (Mtot + 152 * 8 - 1) / (152 * 8);
+    CH = std::max(32LL, std::min(1024LL, CH));
+    std::vector<long long> cstart;
+    std::vector<int> cseg;
+    for (int sg = 0; sg < p->n_seg; ++sg)
+        for (long long a = p->seg_off[sg]; a < p->seg_off[sg + 1]; a += CH) {
+            cstart.push_back(a);
+            cseg.push_back(sg);
+        }
+    p->n_chunk = int(cseg.size());
+    cstart.push_back(Mtot);
+
+    std::vector<double> eps(p->n_seg), inv_sig(p->n_seg);
+    for (int l = 0; l < L; ++l) {
+        const double Ml = double(vis_offsets[l + 1] - vis_offsets[l]);
+        for (int b = 0; b < B; ++b) {
+            const double Mb = double(block_offsets[(int64_t)l * (B + 1) + b + 1] - block_offsets[(int64_t)l * (B + 1) + b]);
+            eps[l * B + b] = eps_in ? eps_in[l * B + b]
+                                    : (Ml > 0 ? std::sqrt((Ml + 2.0 * std::sqrt(Ml)) * Mb / Ml) : 0.0);
+            inv_sig[l * B + b] = 1.0 / sigma[l];
+        }
+    }
+
+    // ---- device state: data term
+    fhs_status st;
+    double2 *d_kap = nullptr, *d_wk = nullptr;
+    short *d_plane = nullptr;
+    double *d_isg = nullptr;
+    if ((st = guard(dev_alloc(p, &p->meta, Mtot, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->rowptr, Mtot + 1, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->gval, p->nnz, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->y, Mtot, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->dvis, Mtot))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->vis_tmp, Mtot))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->perm, Mtot, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->d_seg_off, p->n_seg + 1, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->blk_norm2, p->n_seg))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->eps, p->n_seg, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->blk_scale, p->n_seg, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->chunk_start, p->n_chunk + 1, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->chunk_seg, p->n_chunk, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &d_kap, Mtot, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &d_plane, Mtot, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &d_wk, wk.size(), false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &d_isg, p->n_seg, false))) != FHS_OK) return st;
+    std::vector<float> ones(p->n_seg, 1.0f);
+    if ((st = guard(upload(p->meta, meta.data(), Mtot, s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->rowptr, rowptr.data(), Mtot + 1, s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->y, yw.data(), Mtot, s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->perm, perm.data(), Mtot, s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->d_seg_off, p->seg_off.data(), p->n_seg + 1, s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->eps, eps.data(), p->n_seg, s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->blk_scale, ones.data(), p->n_seg, s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->chunk_start, cstart.data(), cstart.size(), s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->chunk_seg, cseg.data(), cseg.size(), s))) != FHS_OK) return st;
+    if ((st = guard(upload(d_kap, kap.data(), Mtot, s))) != FHS_OK) return st;
+    if ((st = guard(upload(d_plane, plane.data(), Mtot, s))) != FHS_OK) return st;
+    if ((st = guard(upload(d_wk, wk.data(), wk.size(), s))) != FHS_OK) return st;
+    if ((st = guard(upload(d_isg, inv_sig.data(), p->n_seg, s))) != FHS_OK) return st;
+    {
+        cudaError_t e = launch_build_g(p, d_kap, d_plane, d_wk, nullptr, n_planes, d_isg, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return guard(fail(FHS_ERR_CUDA, "G build failed: %s", cudaGetErrorString(e)));
+    }
+
+    // scaling of Z
+    {
+        const double beta = kb_beta(J, 2.0);
+        std::vector<float> s1(q.ny), s2(q.nx);
+        for (int i = 0; i < q.ny; ++i) s1[i] = float(1.0 / kb_hat(double(i - q.ny / 2) / K1, J, beta));
+        for (int i = 0; i < q.nx; ++i) s2[i] = float(1.0 / kb_hat(double(i - q.nx / 2) / K2, J, beta));
+        if ((st = guard(dev_alloc(p, &p->s1, q.ny, false))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &p->s2, q.nx, false))) != FHS_OK) return st;
+        if ((st = guard(upload(p->s1, s1.data(), q.ny, s))) != FHS_OK) return st;
+        if ((st = guard(upload(p->s2, s2.data(), q.nx, s))) != FHS_OK) return st;
+    }
+    {
+        int n[2] = {K1, K2};
+        if (cufftPlanMany(&p->plan, 2, n, nullptr, 1, int(p->K), nullptr, 1, int(p->K), CUFFT_C2C, L) != CUFFT_SUCCESS)
+            return guard(fail(FHS_ERR_CUDA, "cufftPlanMany failed"));
+        p->plan_ok = true;
+    }
+    if ((st = guard(dev_alloc(p, &p->grid_in, p->K * L))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->grid_work, p->K * L))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->grid_aux, p->K * L))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->grid_blk, p->K * L * B))) != FHS_OK) return st;
+
+    // ---- image domain
+    if ((st = guard(dev_alloc(p, &p->X, p->N * L))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->Xbar, p->N * L))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->A_sara, p->N * L))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->red, 2))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->pnorms, 2 * L))) != FHS_OK) return st;
+
+    // ---- SARA layout
+    {
+        SaraConst &c = p->sara;
+        std::memset(&c, 0, sizeof c);
+        c.levels = q.wavelet_levels;
+        c.img_ny = q.ny;
+        c.img_nx = q.nx;
+        long long pos = p->N, tpos = 0;
+        for (int b = 1; b <= kNumDb; ++b) {
+            const std::vector<double> h = daubechies(b);
+            const int F = 2 * b;
+            c.F[b] = F;
+            for (int k = 0; k < F; ++k) {
+                c.h[b][k] = float(h[k]);
+                c.g[b][k] = float((k & 1) ? -h[F - 1 - k] : h[F - 1 - k]);
+            }
+            c.ny[b][0] = q.ny;
+            c.nx[b][0] = q.nx;
+            for (int j = 1; j <= c.levels; ++j) {
+                c.ny[b][j] = (c.ny[b][j - 1] + F - 1) / 2;
+                c.nx[b][j] = (c.nx[b][j - 1] + F - 1) / 2;
+            }
+        }
+        for (int b = 1; b <= kNumDb; ++b) {
+            for (int j = 1; j <= c.levels; ++j) {
+                c.off_det[b][j] = pos;
+                pos += 3LL * c.ny[b][j] * c.nx[b][j];
+            }
+            c.off_ll[b] = pos;
+            pos += (long long)c.ny[b][c.levels] * c.nx[b][c.levels];
+            for (int j = 1; j < c.levels; ++j) {
+                c.off_tmp[b][j] = tpos;
+                tpos += (long long)c.ny[b][j] * c.nx[b][j];
+            }
+        }
+        c.n_coef = pos;
+        c.n_tmp = std::max(tpos, 1LL);
+        if ((st = guard(dev_alloc(p, &p->W, c.n_coef * L))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &p->coef_tmp, c.n_coef * L))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &p->sara_tmp, c.n_tmp * L))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &p->w21, c.n_coef * p->C, false))) != FHS_OK) return st;
+        std::vector<float> w1(c.n_coef * p->C, 1.0f);
+        if ((st = guard(upload(p->w21, w1.data(), w1.size(), s))) != FHS_OK) return st;
+    }
+
+    // ---- nuclear facets: tiles at floor(i n / Q), low side extended by ceil(overlap * tile)
+    {
+        auto axis = [&](int n, int Qd) {
+            std::vector<std::pair<int, int>> r;
+            for (int i = 0; i < Qd; ++i) {
+                const int b0 = int((long long)i * n / Qd), b1 = int((long long)(i + 1) * n / Qd);
+                const int ext = int(std::ceil(q.facet_overlap * double(b1 - b0)));
+                r.push_back({std::max(0, b0 - ext), b1});
+            }
+            return r;
+        };
+        const auto ay = axis(q.ny, q.qy), ax = axis(q.nx, q.qx);
+        p->Q = q.qy * q.qx;
+        std::vector<int4> fz;
+        for (auto &a : ay)
+            for (auto &b : ax) {
+                p->facets.push_back({a.first, a.second, b.first, b.second});
+                fz.push_back(make_int4(a.first, a.second, b.first, b.second));
+            }
+        auto cover = [&](const std::vector<std::pair<int, int>> &ff, int n, std::vector<short> &first,
+                         std::vector<short> &cnt) {
+            first.assign(n, 0);
+            cnt.assign(n, 0);
+            for (int i = 0; i < n; ++i) {
+                int f0 = -1, c0 = 0;
+                for (int k = 0; k < (int)ff.size(); ++k)
+                    if (ff[k].first <= i && i < ff[k].second) {
+                        if (f0 < 0) f0 = k;
+                        ++c0;
+                    }
+                first[i] = short(f0);
+                cnt[i] = short(c0);
+            }
+        };
+        std::vector<short> rf, rc, cf, cc;
+        cover(ay, q.ny, rf, rc);
+        cover(ax, q.nx, cf, cc);
+        int mr = 0, mc = 0;
+        for (short v : rc) mr = std::max(mr, int(v));
+        for (short v : cc) mc = std::max(mc, int(v));
+        p->max_cover = mr * mc;
+        p->h_nuc_off.resize((size_t)p->C * p->Q);
+        long long off = 0;
+        for (int c = 0; c < p->C; ++c)
+            for (int k = 0; k < p->Q; ++k) {
+                p->h_nuc_off[(size_t)c * p->Q + k] = off;
+                const Facet &f = p->facets[k];
+                off += (long long)p->Lc * (f.y1 - f.y0) * (f.x1 - f.x0);
+            }
+        p->nuc_size = off;
+        if ((st = guard(dev_alloc(p, &p->d_facets, p->Q, false))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &p->nuc_off, p->C * p->Q, false))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &p->P, off))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &p->gram, (size_t)p->C * p->Q * p->Lc * p->Lc))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &p->mix, (size_t)p->C * p->Q * p->Lc * p->Lc))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &p->wnuc, (size_t)p->C * p->Q * p->Lc, false))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &p->cov_row_first, q.ny, false))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &p->cov_row_cnt, q.ny, false))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &p->cov_col_first, q.nx, false))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &p->cov_col_cnt, q.nx, false))) != FHS_OK) return st;
+        std::vector<float> w1((size_t)p->C * p->Q * p->Lc, 1.0f);
+        if ((st = guard(upload(p->wnuc, w1.data(), w1.size(), s))) != FHS_OK) return st;
+        if ((st = guard(upload(p->d_facets, fz.data(), fz.size(), s))) != FHS_OK) return st;
+        if ((st = guard(upload(p->nuc_off, p->h_nuc_off.data(), p->h_nuc_off.size(), s))) != FHS_OK) return st;
+        if ((st = guard(upload(p->cov_row_first, rf.data(), rf.size(), s))) != FHS_OK) return st;
+        if ((st = guard(upload(p->cov_row_cnt, rc.data(), rc.size(), s))) != FHS_OK) return st;
+        if ((st = guard(upload(p->cov_col_first, cf.data(), cf.size(), s))) != FHS_OK) return st;
+        if ((st = guard(upload(p->cov_col_cnt, cc.data(), cc.size(), s))) != FHS_OK) return st;
+    }
+
+    // ---- step sizes (Condat-Vu: tau * sum_i sigma_i ||L_i||^2 < 1)
+    p->tau = q.tau > 0 ? q.tau : 0.99 / 3.0;
+    p->sigma1 = q.sigma1 > 0 ? q.sigma1 : 1.0;
+    p->sigma0 = q.sigma0 > 0 ? q.sigma0 : 1.0 / double(p->max_cover);
+    if (q.sigma2 > 0) {
+        p->sigma2 = q.sigma2;
+    } else {
+        std::vector<double> lam;
+        const int n_it = q.power_iters > 0 ? q.power_iters : 100;
+        const double tol = q.power_tol > 0 ? q.power_tol : 1e-7;
+        if ((st = guard(power_iteration(p, n_it, tol, lam, s))) != FHS_OK) return st;
+        p->phi_norm2_max = *std::max_element(lam.begin(), lam.end());
+        if (!(p->phi_norm2_max > 0)) return guard(fail(FHS_ERR_ARG, "operator norm is zero (no visibilities?)"));
+        p->sigma2 = 1.0 / p->phi_norm2_max;
+    }
+    {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return guard(fail(FHS_ERR_CUDA, "set-up failed: %s", cudaGetErrorString(e)));
+    }
+    // set-up temporaries are no longer needed
+    for (void *t : {(void *)d_kap, (void *)d_plane, (void *)d_wk, (void *)d_isg}) {
+        auto it = std::find(p->allocs.begin(), p->allocs.end(), t);
+        if (it != p->allocs.end()) { cudaFree(t); p->allocs.erase(it); }
+    }
+    p->bytes -= sizeof(double2) * Mtot + sizeof(short) * Mtot + sizeof(double2) * wk.size() + sizeof(double) * p->n_seg;
+    *out = p;
+    return FHS_OK;
+}
+
+void fhs_destroy_problem(fhs_problem *p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    for (auto &u : p->ev_used) { cudaEventDestroy(u.second.first); cudaEventDestroy(u.second.second); }
+    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    free_all(p);
+    delete p;
+}
+
+fhs_status fhs_profile_enable(fhs_problem *p, int32_t on) {
+    if (!p) return fail(FHS_ERR_ARG, "NULL problem");
+    if (on) {
+        for (auto &u : p->ev_used) { p->ev_pool.push_back(u.second.first); p->ev_pool.push_back(u.second.second); }
+        p->ev_used.clear();
+        for (double &v : p->prof_ms) v = 0.0;
+        p->prof_iters = 0;
+    }
+    p->prof_on = on != 0;
+    return FHS_OK;
+}
+
+fhs_status fhs_profile_read(fhs_problem *p, double *ms_out, int64_t *iters_out) {
+    if (!p) return fail(FHS_ERR_ARG, "NULL problem");
+    for (auto &u : p->ev_used) {
+        CU(cudaEventSynchronize(u.second.second));
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, u.second.first, u.second.second));
+        p->prof_ms[u.first] += ms;
+        p->ev_pool.push_back(u.second.first);
+        p->ev_pool.push_back(u.second.second);
+    }
+    p->ev_used.clear();
+    if (ms_out)
+        for (int i = 0; i < FHS_N_PHASES; ++i) ms_out[i] = p->prof_ms[i];
+    if (iters_out) *iters_out = p->prof_iters;
+    return FHS_OK;
+}
+
+fhs_status fhs_kernel_launches(const fhs_problem *p, int64_t *count_out) {
+    if (!p || !count_out) return fail(FHS_ERR_ARG, "NULL argument");
+    *count_out = p->n_launch;
+    return FHS_OK;
+}
+
+fhs_status fhs_get_info(const fhs_problem *p, fhs_info *info) {
+    if (!p || !info) return fail(FHS_ERR_ARG, "NULL argument");
+    info->n_vis = p->Mtot;
+    info->nnz = p->nnz;
+    info->n_coef = p->sara.n_coef;
+    info->nuclear_size = p->nuc_size;
+    info->device_bytes = (int64_t)p->bytes;
+    info->n_facets = p->Q;
+    info->iteration = p->iteration;
+    info->tau = p->tau;
+    info->sigma0 = p->sigma0;
+    info->sigma1 = p->sigma1;
+    info->sigma2 = p->sigma2;
+    info->phi_norm2_max = p->phi_norm2_max;
+    return FHS_OK;
+}
+
+fhs_status fhs_measure(fhs_problem *p, const float *x_dev, float *vis_dev, void *stream) {
+    if (!p || !x_dev || !vis_dev) return fail(FHS_ERR_ARG, "NULL argument");
+    cudaStream_t s = S(stream);
+    TRY(forward_from_image(p, x_dev, p->vis_tmp, s));
+    CU(launch_permute_to_caller(p, p->vis_tmp, reinterpret_cast<float2 *>(vis_dev), nullptr, s));
+    return FHS_OK;
+}
+
+fhs_status fhs_adjoint(fhs_problem *p, const float *vis_dev, float *x_dev, void *stream) {
+    if (!p || !x_dev || !vis_dev) return fail(FHS_ERR_ARG, "NULL argument");
+    cudaStream_t s = S(stream);
+    CU(launch_permute_from_caller(p, reinterpret_cast<const float2 *>(vis_dev), p->vis_tmp, s));
+    TRY(adjoint_to_image(p, p->vis_tmp, x_dev, s));
+    return FHS_OK;
+}
+
+fhs_status fhs_sara_analysis(fhs_problem *p, const float *x_dev, float *coef_dev, void *stream) {
+    if (!p || !x_dev || !coef_dev) return fail(FHS_ERR_ARG, "NULL argument");
+    CU(launch_sara_analysis(p, x_dev, coef_dev, S(stream)));
+    return FHS_OK;
+}
+
+fhs_status fhs_sara_synthesis(fhs_problem *p, const float *coef_dev, float *x_dev, void *stream) {
+    if (!p || !x_dev || !coef_dev) return fail(FHS_ERR_ARG, "NULL argument");
+    CU(launch_sara_synthesis(p, coef_dev, x_dev, S(stream)));
+    return FHS_OK;
+}
+
+fhs_status fhs_pdfb_step(fhs_problem *p, int32_t n_iter, double *rel_change_out, void *stream) {
+    if (!p) return fail(FHS_ERR_ARG, "NULL problem");
+    if (n_iter < 0) return fail(FHS_ERR_ARG, "n_iter must be >= 0");
+    cudaStream_t s = S(stream);
+    for (int it = 0; it < n_iter; ++it) TRY(one_iteration(p, s));
+    if (rel_change_out) {
+        double h[2] = {0, 0};
+        CU(cudaMemcpyAsync(h, p->red, sizeof h, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        *rel_change_out = h[1] > 0 ? std::sqrt(h[0] / h[1]) : INFINITY;
+    }
+    return FHS_OK;
+}
+
+fhs_status fhs_reweight(fhs_problem *p, void *stream) {
+    if (!p) return fail(FHS_ERR_ARG, "NULL problem");
+    cudaStream_t s = S(stream);
+    CU(launch_sara_analysis(p, p->X, p->coef_tmp, s));
+    CU(launch_l21_reweight(p, s));
+    CU(launch_nuclear_gram(p, p->X, false, s));
+    CU(launch_nuclear_eig(p, true, s));
+    return FHS_OK;
+}
+
+fhs_status fhs_solve(fhs_problem *p, int32_t max_iter, double rel_tol, int32_t n_reweight, int32_t check_every,
+                     int32_t *iters_out, void *stream) {
+    if (!p) return fail(FHS_ERR_ARG, "NULL problem");
+    if (max_iter < 0 || n_reweight < 0) return fail(FHS_ERR_ARG, "max_iter and n_reweight must be >= 0");
+    if (check_every <= 0) check_every = 10;
+    const int per = max_iter / (n_reweight + 1);
+    int done = 0;
+    for (int r = 0; r <= n_reweight; ++r) {
+        const int k = (r < n_reweight) ? per : max_iter - per * n_reweight;
+        int it = 0;
+        while (it < k) {
+            const int n = std::min(check_every, k - it);
+            double rel = 0;
+            TRY(fhs_pdfb_step(p, n, &rel, stream));
+            it += n;
+            if (rel < rel_tol) break;
+        }
+        done += it;
+        if (r < n_reweight) TRY(fhs_reweight(p, stream));
+    }
+    CU(cudaStreamSynchronize(S(stream)));
+    if (iters_out) *iters_out = done;
+    return FHS_OK;
+}
+
+fhs_status fhs_state_size(const fhs_problem *p, int32_t part, int64_t *n) {
+    if (!p || !n) return fail(FHS_ERR_ARG, "NULL argument");
+    switch (part) {
+        case FHS_STATE_IMAGE: *n = p->N * p->L; break;
+        case FHS_STATE_DUAL_DATA: *n = 2 * p->Mtot; break;
+        case FHS_STATE_DUAL_SARA: *n = p->sara.n_coef * p->L; break;
+        case FHS_STATE_DUAL_NUCLEAR: *n = p->nuc_size; break;
+        case FHS_STATE_WEIGHTS_SARA: *n = p->sara.n_coef * p->C; break;
+        case FHS_STATE_WEIGHTS_NUC: *n = (int64_t)p->C * p->Q * p->Lc; break;
+        default: return fail(FHS_ERR_ARG, "unknown state part %d", part);
+    }
+    return FHS_OK;
+}
+
+fhs_status fhs_get_state(fhs_problem *p, int32_t part, float *dst, void *stream) {
+    int64_t n = 0;
+    TRY(fhs_state_size(p, part, &n));
+    if (!dst) return fail(FHS_ERR_ARG, "NULL destination");
+    cudaStream_t s = S(stream);
+    const size_t b = sizeof(float) * n;
+    switch (part) {
+        case FHS_STATE_IMAGE: CU(cudaMemcpyAsync(dst, p->X, b, cudaMemcpyDeviceToDevice, s)); break;
+        case FHS_STATE_DUAL_DATA:
+            CU(launch_permute_to_caller(p, p->dvis, reinterpret_cast<float2 *>(dst), p->blk_scale, s));
+            break;
+        case FHS_STATE_DUAL_SARA: CU(cudaMemcpyAsync(dst, p->W, b, cudaMemcpyDeviceToDevice, s)); break;
+        case FHS_STATE_DUAL_NUCLEAR: CU(cudaMemcpyAsync(dst, p->P, b, cudaMemcpyDeviceToDevice, s)); break;
+        case FHS_STATE_WEIGHTS_SARA: CU(cudaMemcpyAsync(dst, p->w21, b, cudaMemcpyDeviceToDevice, s)); break;
+        case FHS_STATE_WEIGHTS_NUC: CU(cudaMemcpyAsync(dst, p->wnuc, b, cudaMemcpyDeviceToDevice, s)); break;
+    }
+    return FHS_OK;
+}
+
+fhs_status fhs_set_state(fhs_problem *p, int32_t part, const float *src, void *stream) {
+    int64_t n = 0;
+    TRY(fhs_state_size(p, part, &n));
+    if (!src) return fail(FHS_ERR_ARG, "NULL source");
+    cudaStream_t s = S(stream);
+    const size_t b = sizeof(float) * n;
+    switch (part) {
+        case FHS_STATE_IMAGE: CU(cudaMemcpyAsync(p->X, src, b, cudaMemcpyDeviceToDevice, s)); break;
+        case FHS_STATE_DUAL_DATA: {
+            CU(launch_permute_from_caller(p, reinterpret_cast<const float2 *>(src), p->dvis, s));
+            std::vector<float> ones(p->n_seg, 1.0f);
+            CU(cudaMemcpyAsync(p->blk_scale, ones.data(), sizeof(float) * p->n_seg, cudaMemcpyHostToDevice, s));
+            TRY(adjoint_to_grid(p, p->dvis, p->grid_work, s));
+            CU(cudaStreamSynchronize(s));
+            break;
+        }
+        case FHS_STATE_DUAL_SARA:
+            if (!sara_active(p))
+                return fail(FHS_ERR_STATE, "SARA dual set while mu = 0: it would not enter the iteration");
+            CU(cudaMemcpyAsync(p->W, src, b, cudaMemcpyDeviceToDevice, s));
+            CU(launch_sara_synthesis(p, p->W, p->A_sara, s));
+            break;
+        case FHS_STATE_DUAL_NUCLEAR:
+            if (!nuc_active(p))
+                return fail(FHS_ERR_STATE, "nuclear dual set while mu_bar = 0: it would not enter the iteration");
+            CU(cudaMemcpyAsync(p->P, src, b, cudaMemcpyDeviceToDevice, s));
+            break;
+        case FHS_STATE_WEIGHTS_SARA: CU(cudaMemcpyAsync(p->w21, src, b, cudaMemcpyDeviceToDevice, s)); break;
+        case FHS_STATE_WEIGHTS_NUC: CU(cudaMemcpyAsync(p->wnuc, src, b, cudaMemcpyDeviceToDevice, s)); break;
+    }
+    return FHS_OK;
+}
+
+fhs_status fhs_operator_norms(fhs_problem *p, int32_t n_iter, double *norms, void *stream) {
+    if (!p || !norms || n_iter < 1) return fail(FHS_ERR_ARG, "bad argument");
+    cudaStream_t s = S(stream);
+    // the work images are part of the iteration state: keep them
+    const long long LN = p->N * p->L;
+    float *save = nullptr;
+    TRY(dev_alloc(p, &save, 2 * LN, false));
+    CU(cudaMemcpyAsync(save, p->Xbar, sizeof(float) * LN, cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(save + LN, p->A_sara, sizeof(float) * LN, cudaMemcpyDeviceToDevice, s));
+    std::vector<double> lam;
+    fhs_status st = power_iteration(p, n_iter, 0.0, lam, s);
+    CU(cudaMemcpyAsync(p->Xbar, save, sizeof(float) * LN, cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(p->A_sara, save + LN, sizeof(float) * LN, cudaMemcpyDeviceToDevice, s));
+    CU(cudaStreamSynchronize(s));
+    auto it = std::find(p->allocs.begin(), p->allocs.end(), (void *)save);
+    if (it != p->allocs.end()) { cudaFree(save); p->allocs.erase(it); p->bytes -= sizeof(float) * 2 * LN; }
+    if (st != FHS_OK) return st;
+    std::copy(lam.begin(), lam.end(), norms);
+    return FHS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,169 @@
+// Internal definitions of libfhs: problem state, device layouts and kernel
+// launchers.  Not part of the public ABI (see include/fhs.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "fhs.h"
+
+namespace fhs {
+
+constexpr int kMaxLevels = 6;      // SARA depth supported
+constexpr int kNumDb = 8;          // db1..db8
+constexpr int kMaxF = 16;          // taps of db8
+constexpr int kMaxLc = 32;         // channels per sub-cube supported
+constexpr int kMaxWHalf = 4;       // largest w-kernel half-width h
+constexpr int kTile = 32;          // grid tile (cells) used to sort visibilities
+constexpr float kSaraScale = 1.0f / 3.0f;   // 1/sqrt(9 bases)
+
+// ---------------------------------------------------------------------------
+// host math (host_math.cpp)
+// ---------------------------------------------------------------------------
+double bessel_i0(double x);
+double kb_beta(int J, double os);
+double kb_hat(double nu, int J, double beta);
+std::vector<double> daubechies(int p);
+double chirp_phase(double n_abs, int N, int K);
+void wkernel(double wp, int N, int K, double pixel_size, int h, std::complex<double> *out);
+
+// ---------------------------------------------------------------------------
+// SARA layout (constant memory in k_sara.cu)
+// ---------------------------------------------------------------------------
+struct SaraConst {
+    int levels;
+    int F[kNumDb + 1];                       // taps per basis (index 1..8)
+    float h[kNumDb + 1][kMaxF];              // low-pass
+    float g[kNumDb + 1][kMaxF];              // high-pass g[k] = (-1)^k h[F-1-k]
+    int ny[kNumDb + 1][kMaxLevels + 1];      // level sizes (j = 0..levels)
+    int nx[kNumDb + 1][kMaxLevels + 1];
+    long long off_det[kNumDb + 1][kMaxLevels + 1];  // coefficient offset of level j details
+    long long off_ll[kNumDb + 1];            // coefficient offset of the last LL band
+    long long off_tmp[kNumDb + 1][kMaxLevels + 1];  // temp offset of approximation a_j
+    long long n_coef;                        // coefficients per channel
+    long long n_tmp;                         // temp floats per channel
+    int img_ny, img_nx;
+};
+
+// ---------------------------------------------------------------------------
+// Problem state
+// ---------------------------------------------------------------------------
+struct Facet {
+    int y0, y1, x0, x1;
+};
+
+}  // namespace fhs
+
+struct fhs_problem {
+    fhs_params prm;
+    int L = 0, C = 0, Lc = 0, B = 0, ny = 0, nx = 0, K1 = 0, K2 = 0, J = 7;
+    long long N = 0, K = 0;                   // pixels and grid cells per channel
+    long long Mtot = 0, nnz = 0;
+    std::vector<long long> vis_off;           // [L+1]
+    std::vector<long long> seg_off;           // [L*B+1] sorted-order offsets of (l,b) segments
+    int n_seg = 0;
+
+    // data term (sorted visibility order)
+    int2 *meta = nullptr;                     // {c1 | c2 << 16, T}
+    long long *rowptr = nullptr;              // [Mtot+1]
+    float2 *gval = nullptr;                   // [nnz] whitened G values
+    float2 *y = nullptr;                      // whitened data
+    float2 *dvis = nullptr;                   // data dual storage d (v = scale_b d)
+    long long *perm = nullptr;                // sorted -> caller index
+    float2 *vis_tmp = nullptr;                // [Mtot] scratch for measure/adjoint
+    int *vis_chan = nullptr;                  // [n_seg] channel of each segment
+    long long *d_seg_off = nullptr;           // [n_seg+1]
+    double *blk_norm2 = nullptr;              // [n_seg]
+    double *eps = nullptr;                    // [n_seg]
+    float *blk_scale = nullptr;               // [n_seg]  (1 - m_b)
+    int n_chunk = 0;
+    long long *chunk_start = nullptr;         // [n_chunk+1]
+    int *chunk_seg = nullptr;                 // [n_chunk]
+    float *s1 = nullptr, *s2 = nullptr;       // Z scaling per axis
+    cufftHandle plan = 0;
+    bool plan_ok = false;
+    float2 *grid_in = nullptr;                // [L][K] zero-padded input (zeros persist)
+    float2 *grid_work = nullptr;              // [L][K] FFT output / data adjoint grid
+    float2 *grid_blk = nullptr;               // [L][B][K] per-block adjoint grids
+    float2 *grid_aux = nullptr;               // [L][K] scratch for measure/adjoint
+
+    // image domain
+    float *X = nullptr, *Xbar = nullptr, *A_sara = nullptr;
+
+    // SARA
+    fhs::SaraConst sara{};
+    float *W = nullptr;                       // [L][n_coef]
+    float *coef_tmp = nullptr;                // [L][n_coef] analysis output
+    float *sara_tmp = nullptr;                // [L][n_tmp] approximations
+    float *w21 = nullptr;                     // [C][n_coef]
+
+    // nuclear
+    std::vector<fhs::Facet> facets;           // Q facets (row-major)
+    int Q = 0;
+    int4 *d_facets = nullptr;                 // [Q]
+    long long *nuc_off = nullptr;             // [C*Q] float offset of P_{c,q}
+    std::vector<long long> h_nuc_off;
+    long long nuc_size = 0;
+    float *P = nullptr;
+    double *gram = nullptr;                   // [C*Q][Lc*Lc]
+    float *mix = nullptr;                     // [C*Q][Lc*Lc]
+    float *wnuc = nullptr;                    // [C*Q][Lc]
+    short *cov_row_first = nullptr, *cov_row_cnt = nullptr;   // [ny]
+    short *cov_col_first = nullptr, *cov_col_cnt = nullptr;   // [nx]
+    int max_cover = 1;
+
+    // reductions
+    double *red = nullptr;                    // [2]: ||x+ - x||^2, ||x+||^2
+
+    double tau = 0, sigma0 = 0, sigma1 = 0, sigma2 = 0, phi_norm2_max = 0;
+    int iteration = 0;
+    long long n_launch = 0;                   // libfhs kernels launched
+    double *pnorms = nullptr;                 // [2L] power-iteration reductions
+
+    // tracing: event pairs per phase per iteration, recycled from a pool
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+    double prof_ms[FHS_N_PHASES] = {0};
+    long long prof_iters = 0;
+    size_t bytes = 0;
+    std::vector<void *> allocs;
+};
+
+namespace fhs {
+
+// kernel launchers --------------------------------------------------------
+// k_nufft.cu
+cudaError_t launch_build_g(fhs_problem *p, const double2 *kap, const short *plane, const double2 *wk_table,
+                           const int *wk_half, int n_planes_total, const double *inv_sigma_seg,
+                           cudaStream_t s);
+cudaError_t launch_zpad(fhs_problem *p, const float *x, float2 *grid, cudaStream_t s);
+cudaError_t launch_degrid(fhs_problem *p, const float2 *grid, float2 *vis_sorted, cudaStream_t s);
+cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s);
+cudaError_t launch_crop(fhs_problem *p, const float2 *grid, float *x, cudaStream_t s);
+cudaError_t launch_degrid_grid_fused(fhs_problem *p, cudaStream_t s);
+cudaError_t launch_block_finalize(fhs_problem *p, cudaStream_t s);
+cudaError_t launch_combine(fhs_problem *p, cudaStream_t s);
+cudaError_t launch_permute_to_caller(fhs_problem *p, const float2 *sorted, float2 *caller, const float *scale_seg,
+                                     cudaStream_t s);
+cudaError_t launch_permute_from_caller(fhs_problem *p, const float2 *caller, float2 *sorted, cudaStream_t s);
+cudaError_t launch_power_dots(fhs_problem *p, const float *x, const float *y, double *out, cudaStream_t s);
+cudaError_t launch_power_scale(fhs_problem *p, const float *y, float *x, const double *norms, cudaStream_t s);
+// k_sara.cu
+cudaError_t launch_sara_analysis(fhs_problem *p, const float *x, float *coef, cudaStream_t s);
+cudaError_t launch_sara_synthesis(fhs_problem *p, const float *coef, float *x, cudaStream_t s);
+cudaError_t launch_l21_dual(fhs_problem *p, cudaStream_t s);
+cudaError_t launch_l21_reweight(fhs_problem *p, cudaStream_t s);
+// k_nuclear.cu
+cudaError_t launch_nuclear_gram(fhs_problem *p, const float *img, bool with_dual, cudaStream_t s);
+cudaError_t launch_nuclear_eig(fhs_problem *p, bool reweight, cudaStream_t s);
+cudaError_t launch_nuclear_apply(fhs_problem *p, cudaStream_t s);
+// k_pdfb.cu
+cudaError_t launch_primal(fhs_problem *p, cudaStream_t s);
+
+}  // namespace fhs

@@ -1,0 +1,452 @@
+// Measurement operator Phi_l = Theta_l G_l F Z (Sec. 2.1, Eq. 1) and the
+// data-fidelity dual step of the l2 balls (Eq. 2) on sm_103a.
+//
+// G is stored as "box CSR": every row's support is a T x T box of the
+// oversampled grid (KB taps convolved with the w-kernel of its plane,
+// Sec. 3.2), so a row keeps its wrapped corner and T instead of T^2 column
+// indices (8 bytes per non-zero instead of 12).  Rows are sorted by grid
+// tile inside each (channel, block) segment, so the warps of one CTA touch
+// neighbouring grid cells (L1/L2 reuse).
+#include "fhs_internal.h"
+
+#include <cstdio>
+
+namespace fhs {
+
+namespace {
+
+constexpr int kWarps = 8;               // warps per CTA for visibility kernels
+
+__device__ __forceinline__ double kb_eval(double t, int J, double beta, double inv_i0b) {
+    const double u = 2.0 * t / double(J);
+    const double r = 1.0 - u * u;
+    if (r < 0.0) return 0.0;
+    const double x = beta * sqrt(r);
+    const double q = 0.25 * x * x;
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 200; ++k) {
+        term *= q / (double(k) * double(k));
+        sum += term;
+        if (term < 1e-17 * sum) break;
+    }
+    return sum * inv_i0b;
+}
+
+__device__ __forceinline__ int seg_of(const long long *seg_off, int n_seg, long long v) {
+    int lo = 0, hi = n_seg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (seg_off[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One warp per row: KB samples (7 per axis, FP64), discrete convolution with
+// the w-kernel of the row's plane, outer product, whitening, store as float2.
+__global__ void __launch_bounds__(256) build_g_kernel(
+    const int2 *__restrict__ meta, const long long *__restrict__ rowptr, float2 *__restrict__ gval,
+    const double2 *__restrict__ kap, const short *__restrict__ plane, const double2 *__restrict__ wk,
+    const long long *__restrict__ seg_off, int n_seg, const double *__restrict__ inv_sigma_seg,
+    long long Mtot, int J, double beta, double inv_i0b) {
+    __shared__ double s_kb[kWarps][2][16];
+    __shared__ double2 s_g[kWarps][2][16];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * kWarps;
+    for (long long v = (long long)blockIdx.x * kWarps + warp; v < Mtot; v += stride) {
+        const int T = meta[v].y;
+        const int h = (T - J) / 2;
+        const int S = 2 * h + 1;
+        const double2 kp = kap[v];
+        const int dim = lane >> 4, i = lane & 15;
+        const double kd = dim ? kp.y : kp.x;
+        const long long p0 = (long long)floor(kd - 0.5 * J) + 1;
+        if (i < J) s_kb[warp][dim][i] = kb_eval(kd - double(p0 + i), J, beta, inv_i0b);
+        __syncwarp();
+        const int pl = plane[v];
+        if (i < T) {
+            double2 acc = make_double2(0.0, 0.0);
+            for (int jj = 0; jj < S; ++jj) {
+                const int ti = i + jj - (S - 1);
+                if (ti < 0 || ti >= J) continue;
+                const double2 c = wk[(pl * 2 + dim) * (2 * kMaxWHalf + 1) + jj];
+                const double k = s_kb[warp][dim][ti];
+                acc.x += c.x * k;
+                acc.y += c.y * k;
+            }
+            s_g[warp][dim][i] = acc;
+        }
+        __syncwarp();
+        const double isg = inv_sigma_seg[seg_of(seg_off, n_seg, v)];
+        const long long base = rowptr[v];
+        for (int e = lane; e < T * T; e += 32) {
+            const int t1 = e / T, t2 = e - t1 * T;
+            const double2 a = s_g[warp][0][t1], b = s_g[warp][1][t2];
+            const double re = (a.x * b.x - a.y * b.y) * isg;
+            const double im = (a.x * b.y + a.y * b.x) * isg;
+            gval[base + e] = make_float2(float(re), float(im));
+        }
+        __syncwarp();
+    }
+}
+
+// Grid cell of entry e of a row with corner (c1, c2) and side T.
+__device__ __forceinline__ int cell_index(int e, int T, float invT, int c1, int c2, int K1, int K2) {
+    const int t1 = __float2int_rz((float(e) + 0.5f) * invT);
+    const int t2 = e - t1 * T;
+    int k1 = c1 + t1;
+    k1 -= (k1 >= K1) ? K1 : 0;
+    int k2 = c2 + t2;
+    k2 -= (k2 >= K2) ? K2 : 0;
+    return k1 * K2 + k2;
+}
+
+__device__ __forceinline__ void red_add_f2(float2 *addr, float2 v) {
+    atomicAdd(addr, v);   // sm_90+: vector float2 reduction (red.global.add.v2.f32)
+}
+
+// Degrid only: vis = G (F Z x) for the measure operator and power iteration.
+__global__ void __launch_bounds__(256) degrid_kernel(
+    const int2 *__restrict__ meta, const long long *__restrict__ rowptr, const float2 *__restrict__ gval,
+    const long long *__restrict__ chunk_start, const int *__restrict__ chunk_seg, int B,
+    const float2 *__restrict__ grid, long long K, int K1, int K2, float2 *__restrict__ vis) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ch = blockIdx.x;
+    const int l = chunk_seg[ch] / B;
+    const float2 *gl = grid + (long long)l * K;
+    const long long v1 = chunk_start[ch + 1];
+    for (long long v = chunk_start[ch] + warp; v < v1; v += kWarps) {
+        const int2 m = meta[v];
+        const int T = m.y, n = T * T;
+        const int c1 = m.x & 0xffff, c2 = (int)((unsigned)m.x >> 16);
+        const float invT = 1.0f / float(T);
+        const float2 *gv = gval + rowptr[v];
+        float ar = 0.f, ai = 0.f;
+        for (int e = lane; e < n; e += 32) {
+            const float2 g = __ldg(gv + e);
+            const float2 x = gl[cell_index(e, T, invT, c1, c2, K1, K2)];
+            ar = fmaf(g.x, x.x, fmaf(-g.y, x.y, ar));
+            ai = fmaf(g.x, x.y, fmaf(g.y, x.x, ai));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ar += __shfl_xor_sync(0xffffffffu, ar, o);
+            ai += __shfl_xor_sync(0xffffffffu, ai, o);
+        }
+        if (lane == 0) vis[v] = make_float2(ar, ai);
+    }
+}
+
+// Grid only: grid += G^H vis (atomics), for the adjoint operator.
+__global__ void __launch_bounds__(256) grid_kernel(
+    const int2 *__restrict__ meta, const long long *__restrict__ rowptr, const float2 *__restrict__ gval,
+    const long long *__restrict__ chunk_start, const int *__restrict__ chunk_seg, int B,
+    const float2 *__restrict__ vis, long long K, int K1, int K2, float2 *__restrict__ grid) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ch = blockIdx.x;
+    const int l = chunk_seg[ch] / B;
+    float2 *gl = grid + (long long)l * K;
+    const long long v1 = chunk_start[ch + 1];
+    for (long long v = chunk_start[ch] + warp; v < v1; v += kWarps) {
+        const int2 m = meta[v];
+        const int T = m.y, n = T * T;
+        const int c1 = m.x & 0xffff, c2 = (int)((unsigned)m.x >> 16);
+        const float invT = 1.0f / float(T);
+        const float2 *gv = gval + rowptr[v];
+        const float2 d = vis[v];
+        for (int e = lane; e < n; e += 32) {
+            const float2 g = __ldg(gv + e);
+            red_add_f2(gl + cell_index(e, T, invT, c1, c2, K1, K2),
+                       make_float2(g.x * d.x + g.y * d.y, g.x * d.y - g.y * d.x));
+        }
+    }
+}
+
+// The data term of one PDFB iteration in a single pass over G (Eq. 2):
+//   phi  = G_m . Xhat                      (gather from the forward grid)
+//   d_m  = s_b d_m + sigma2 (phi - y_m)    (= z - sigma2 y, z = v + sigma2 Phi xbar)
+//   ||d_b||^2 accumulated in FP64 per block
+//   grid_b += conj(G_m) d_m                (scatter into the block's own grid)
+// The block's l2-ball factor (1 - m_b) is known only after the pass; it is
+// applied to grid_b when the block grids are combined, and kept as s_b for d.
+__global__ void __launch_bounds__(256) degrid_grid_fused_kernel(
+    const int2 *__restrict__ meta, const long long *__restrict__ rowptr, const float2 *__restrict__ gval,
+    const float2 *__restrict__ y, float2 *__restrict__ dvis, const long long *__restrict__ chunk_start,
+    const int *__restrict__ chunk_seg, int B, const float *__restrict__ blk_scale,
+    double *__restrict__ blk_norm2, const float2 *__restrict__ grid, float2 *__restrict__ grid_blk,
+    long long K, int K1, int K2, float sigma2) {
+    __shared__ double s_red[kWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ch = blockIdx.x;
+    const int seg = chunk_seg[ch];
+    const int l = seg / B;
+    const float2 *gl = grid + (long long)l * K;
+    float2 *gb = grid_blk + (long long)seg * K;
+    const float sc = blk_scale[seg];
+    double nrm = 0.0;
+    const long long v1 = chunk_start[ch + 1];
+    for (long long v = chunk_start[ch] + warp; v < v1; v += kWarps) {
+        const int2 m = meta[v];
+        const int T = m.y, n = T * T;
+        const int c1 = m.x & 0xffff, c2 = (int)((unsigned)m.x >> 16);
+        const float invT = 1.0f / float(T);
+        const float2 *gv = gval + rowptr[v];
+        float2 g[8];
+        int idx[8];
+        float ar = 0.f, ai = 0.f;
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            const int e = lane + 32 * it;
+            if (e < n) {
+                g[it] = __ldg(gv + e);
+                idx[it] = cell_index(e, T, invT, c1, c2, K1, K2);
+                const float2 x = gl[idx[it]];
+                ar = fmaf(g[it].x, x.x, fmaf(-g[it].y, x.y, ar));
+                ai = fmaf(g[it].x, x.y, fmaf(g[it].y, x.x, ai));
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ar += __shfl_xor_sync(0xffffffffu, ar, o);
+            ai += __shfl_xor_sync(0xffffffffu, ai, o);
+        }
+        const float2 dold = dvis[v];
+        const float2 yv = y[v];
+        const float dr = fmaf(sc, dold.x, sigma2 * (ar - yv.x));
+        const float di = fmaf(sc, dold.y, sigma2 * (ai - yv.y));
+        if (lane == 0) {
+            dvis[v] = make_float2(dr, di);
+            nrm += double(dr) * dr + double(di) * di;
+        }
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            const int e = lane + 32 * it;
+            if (e < n)
+                red_add_f2(gb + idx[it], make_float2(g[it].x * dr + g[it].y * di, g[it].x * di - g[it].y * dr));
+        }
+    }
+    if (lane == 0) s_red[warp] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kWarps; ++w) s += s_red[w];
+        atomicAdd(blk_norm2 + seg, s);
+    }
+}
+
+// l2-ball factor per block: m_b = min(1, sigma2 eps_b / ||d_b||), s_b = 1 - m_b.
+__global__ void block_finalize_kernel(double *blk_norm2, const double *eps, float *blk_scale, int n_seg,
+                                      double sigma2) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_seg) return;
+    const double nr = sqrt(blk_norm2[s]);
+    const double m = nr > 0.0 ? fmin(1.0, sigma2 * eps[s] / nr) : 1.0;
+    blk_scale[s] = float(1.0 - m);
+    blk_norm2[s] = 0.0;
+}
+
+// grid_work[l] = sum_b s_{l,b} grid_blk[l][b]; grid_blk <- 0.  float4 = 2 cells.
+__global__ void __launch_bounds__(256) combine_kernel(float4 *__restrict__ blk, float4 *__restrict__ out,
+                                                      const float *__restrict__ blk_scale, int B,
+                                                      long long K4, int L) {
+    const long long total = K4 * L;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long l = t / K4, k = t - l * K4;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int b = 0; b < B; ++b) {
+            float4 *src = blk + ((l * B + b) * K4 + k);
+            const float4 v = *src;
+            const float s = blk_scale[l * B + b];
+            acc.x = fmaf(s, v.x, acc.x);
+            acc.y = fmaf(s, v.y, acc.y);
+            acc.z = fmaf(s, v.z, acc.z);
+            acc.w = fmaf(s, v.w, acc.w);
+            *src = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        out[t] = acc;
+    }
+}
+
+// Z: grid[(n mod K)] = x_n s1(n1) s2(n2) (zero cells elsewhere are left as is).
+__global__ void zpad_kernel(const float *__restrict__ x, float2 *__restrict__ grid, const float *__restrict__ s1,
+                            const float *__restrict__ s2, int ny, int nx, int K1, int K2, long long K) {
+    const int l = blockIdx.y;
+    const long long N = (long long)ny * nx;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+        const int i1 = int(p / nx), i2 = int(p - (long long)i1 * nx);
+        int k1 = i1 - ny / 2; k1 += (k1 < 0) ? K1 : 0;
+        int k2 = i2 - nx / 2; k2 += (k2 < 0) ? K2 : 0;
+        grid[(long long)l * K + (long long)k1 * K2 + k2] = make_float2(x[(long long)l * N + p] * s1[i1] * s2[i2], 0.f);
+    }
+}
+
+// Z^T, real part: x_n = Re(grid[(n mod K)]) s1(n1) s2(n2).
+__global__ void crop_kernel(const float2 *__restrict__ grid, float *__restrict__ x, const float *__restrict__ s1,
+                            const float *__restrict__ s2, int ny, int nx, int K1, int K2, long long K) {
+    const int l = blockIdx.y;
+    const long long N = (long long)ny * nx;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+        const int i1 = int(p / nx), i2 = int(p - (long long)i1 * nx);
+        int k1 = i1 - ny / 2; k1 += (k1 < 0) ? K1 : 0;
+        int k2 = i2 - nx / 2; k2 += (k2 < 0) ? K2 : 0;
+        x[(long long)l * N + p] = grid[(long long)l * K + (long long)k1 * K2 + k2].x * s1[i1] * s2[i2];
+    }
+}
+
+__global__ void permute_to_caller_kernel(const float2 *__restrict__ sorted, float2 *__restrict__ caller,
+                                         const long long *__restrict__ perm, const long long *__restrict__ chunk_start,
+                                         const int *__restrict__ chunk_seg, const float *__restrict__ scale_seg) {
+    const int ch = blockIdx.x;
+    const float s = scale_seg ? scale_seg[chunk_seg[ch]] : 1.0f;
+    for (long long v = chunk_start[ch] + threadIdx.x; v < chunk_start[ch + 1]; v += blockDim.x) {
+        const float2 a = sorted[v];
+        caller[perm[v]] = make_float2(a.x * s, a.y * s);
+    }
+}
+
+__global__ void permute_from_caller_kernel(const float2 *__restrict__ caller, float2 *__restrict__ sorted,
+                                           const long long *__restrict__ perm, long long M) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < M; v += (long long)gridDim.x * blockDim.x)
+        sorted[v] = caller[perm[v]];
+}
+
+// Power iteration step on every channel: norms[2l] += <x_l, y_l>, norms[2l+1] += ||y_l||^2.
+__global__ void __launch_bounds__(256) dots_kernel(const float *__restrict__ x, const float *__restrict__ y,
+                                                   long long N, double *__restrict__ out) {
+    __shared__ double s_a[8], s_b[8];
+    const int l = blockIdx.y;
+    double a = 0.0, b = 0.0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
+        const double xv = x[(long long)l * N + p], yv = y[(long long)l * N + p];
+        a += xv * yv;
+        b += yv * yv;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) { s_a[threadIdx.x >> 5] = a; s_b[threadIdx.x >> 5] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0, sb = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sa += s_a[w]; sb += s_b[w]; }
+        atomicAdd(out + 2 * l, sa);
+        atomicAdd(out + 2 * l + 1, sb);
+    }
+}
+
+__global__ void scale_kernel(const float *__restrict__ y, float *__restrict__ x, long long N,
+                             const double *__restrict__ norms) {
+    const int l = blockIdx.y;
+    const double nb = norms[2 * l + 1];
+    const float f = nb > 0.0 ? float(1.0 / sqrt(nb)) : 0.f;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x)
+        x[(long long)l * N + p] = y[(long long)l * N + p] * f;
+}
+
+inline int grid_for(long long n, int threads, int cap = 152 * 16) {
+    long long g = (n + threads - 1) / threads;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return int(g);
+}
+
+}  // namespace
+
+cudaError_t launch_build_g(fhs_problem *p, const double2 *kap, const short *plane, const double2 *wk_table,
+                           const int * /*wk_half*/, int /*n_planes_total*/, const double *inv_sigma_seg,
+                           cudaStream_t s) {
+    const double beta = kb_beta(p->J, 2.0);
+    build_g_kernel<<<grid_for(p->Mtot, kWarps, 152 * 64), 256, 0, s>>>(
+        p->meta, p->rowptr, p->gval, kap, plane, wk_table, p->d_seg_off, p->n_seg, inv_sigma_seg, p->Mtot, p->J,
+        beta, 1.0 / bessel_i0(beta));
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zpad(fhs_problem *p, const float *x, float2 *grid, cudaStream_t s) {
+    dim3 g(grid_for(p->N, 256, 512), p->L);
+    zpad_kernel<<<g, 256, 0, s>>>(x, grid, p->s1, p->s2, p->ny, p->nx, p->K1, p->K2, p->K);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_crop(fhs_problem *p, const float2 *grid, float *x, cudaStream_t s) {
+    dim3 g(grid_for(p->N, 256, 512), p->L);
+    crop_kernel<<<g, 256, 0, s>>>(grid, x, p->s1, p->s2, p->ny, p->nx, p->K1, p->K2, p->K);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_degrid(fhs_problem *p, const float2 *grid, float2 *vis_sorted, cudaStream_t s) {
+    if (p->n_chunk == 0) return cudaSuccess;
+    degrid_kernel<<<p->n_chunk, 256, 0, s>>>(p->meta, p->rowptr, p->gval, p->chunk_start, p->chunk_seg, p->B, grid,
+                                             p->K, p->K1, p->K2, vis_sorted);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s) {
+    if (p->n_chunk == 0) return cudaSuccess;
+    grid_kernel<<<p->n_chunk, 256, 0, s>>>(p->meta, p->rowptr, p->gval, p->chunk_start, p->chunk_seg, p->B,
+                                           vis_sorted, p->K, p->K1, p->K2, grid);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_degrid_grid_fused(fhs_problem *p, cudaStream_t s) {
+    if (p->n_chunk == 0) return cudaSuccess;
+    degrid_grid_fused_kernel<<<p->n_chunk, 256, 0, s>>>(p->meta, p->rowptr, p->gval, p->y, p->dvis, p->chunk_start,
+                                                        p->chunk_seg, p->B, p->blk_scale, p->blk_norm2, p->grid_work,
+                                                        p->grid_blk, p->K, p->K1, p->K2, float(p->sigma2));
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_finalize(fhs_problem *p, cudaStream_t s) {
+    block_finalize_kernel<<<(p->n_seg + 127) / 128, 128, 0, s>>>(p->blk_norm2, p->eps, p->blk_scale, p->n_seg,
+                                                                 p->sigma2);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine(fhs_problem *p, cudaStream_t s) {
+    const long long K4 = p->K / 2;
+    combine_kernel<<<grid_for(K4 * p->L, 256, 152 * 16), 256, 0, s>>>(
+        reinterpret_cast<float4 *>(p->grid_blk), reinterpret_cast<float4 *>(p->grid_work), p->blk_scale, p->B, K4,
+        p->L);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute_to_caller(fhs_problem *p, const float2 *sorted, float2 *caller, const float *scale_seg,
+                                     cudaStream_t s) {
+    if (p->n_chunk == 0) return cudaSuccess;
+    permute_to_caller_kernel<<<p->n_chunk, 256, 0, s>>>(sorted, caller, p->perm, p->chunk_start, p->chunk_seg,
+                                                        scale_seg);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute_from_caller(fhs_problem *p, const float2 *caller, float2 *sorted, cudaStream_t s) {
+    if (p->Mtot == 0) return cudaSuccess;
+    permute_from_caller_kernel<<<grid_for(p->Mtot, 256), 256, 0, s>>>(caller, sorted, p->perm, p->Mtot);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_power_dots(fhs_problem *p, const float *x, const float *y, double *out, cudaStream_t s) {
+    dim3 g(grid_for(p->N, 256, 256), p->L);
+    dots_kernel<<<g, 256, 0, s>>>(x, y, p->N, out);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_power_scale(fhs_problem *p, const float *y, float *x, const double *norms, cudaStream_t s) {
+    dim3 g(grid_for(p->N, 256, 512), p->L);
+    scale_kernel<<<g, 256, 0, s>>>(y, x, p->N, norms);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace fhs

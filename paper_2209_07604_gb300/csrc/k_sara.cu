@@ -1,0 +1,330 @@
+// SARA dictionary Psi^dagger = (1/3)[I; W_db1; ...; W_db8] and its adjoint,
+// and the weighted l21 dual step (Sec. 2.2.2, average joint sparsity).
+//
+// The faceted transform of the paper equals the global one exactly (each
+// coefficient is owned by one facet, whose window holds all its inputs); on
+// one GPU the facets become CTA tiles: each CTA stages its tile plus the
+// filter halo in shared memory (zero extension outside the image) and writes
+// only the coefficients it owns, so nothing is computed twice beyond the halo.
+// One level, one axis: c[k] = sum_i f[i] a[2k+1-i], k < floor((n+F-1)/2).
+#include "fhs_internal.h"
+
+namespace fhs {
+
+namespace {
+
+constexpr int ATY = 8, ATX = 32;                    // analysis output tile
+constexpr int AIN_Y = 2 * ATY + kMaxF - 2;          // staged input rows
+constexpr int AIN_X = 2 * ATX + kMaxF - 2;          // staged input cols
+constexpr int STY = 16, STX = 32;                   // synthesis output tile
+constexpr int SB_Y = (STY + kMaxF - 2) / 2;         // staged band rows
+constexpr int SB_X = (STX + kMaxF - 2) / 2;         // staged band cols
+
+// Filter the staged tile along x then y; write the 4 subbands of basis p at
+// level j (details to coef, LL to `ll_out` with row stride mx).
+__device__ __forceinline__ void analysis_tile(const SaraConst &c, int p, int j, int k0y, int k0x,
+                                              float (*sin_)[AIN_X + 1], float (*slo)[ATX + 1],
+                                              float (*shi)[ATX + 1], float *coef_l, float *ll_out,
+                                              float ll_scale) {
+    const int F = c.F[p];
+    const int my = c.ny[p][j], mx = c.nx[p][j];
+    const float *h = c.h[p];
+    const float *g = c.g[p];
+    for (int idx = threadIdx.x; idx < AIN_Y * ATX; idx += blockDim.x) {
+        const int r = idx / ATX, kx = idx - r * ATX;
+        float lo = 0.f, hi = 0.f;
+        const int base = 2 * kx + kMaxF - 1;
+        for (int i = 0; i < F; ++i) {
+            const float a = sin_[r][base - i];
+            lo = fmaf(h[i], a, lo);
+            hi = fmaf(g[i], a, hi);
+        }
+        slo[r][kx] = lo;
+        shi[r][kx] = hi;
+    }
+    __syncthreads();
+    const long long bs = (long long)my * mx;
+    for (int idx = threadIdx.x; idx < ATY * ATX; idx += blockDim.x) {
+        const int ky = idx / ATX, kx = idx - ky * ATX;
+        const int gy = k0y + ky, gx = k0x + kx;
+        const int base = 2 * ky + kMaxF - 1;
+        float ll = 0.f, lh = 0.f, hl = 0.f, hh = 0.f;
+        for (int i = 0; i < F; ++i) {
+            const float lo = slo[base - i][kx], hi = shi[base - i][kx];
+            ll = fmaf(h[i], lo, ll);
+            lh = fmaf(h[i], hi, lh);
+            hl = fmaf(g[i], lo, hl);
+            hh = fmaf(g[i], hi, hh);
+        }
+        if (gy < my && gx < mx) {
+            float *d = coef_l + c.off_det[p][j] + (long long)gy * mx + gx;
+            d[0] = lh * kSaraScale;
+            d[bs] = hl * kSaraScale;
+            d[2 * bs] = hh * kSaraScale;
+            ll_out[(long long)gy * mx + gx] = ll * ll_scale;
+        }
+    }
+    __syncthreads();
+}
+
+// Level 1 of every Daubechies basis (and the Dirac basis) from one staged tile
+// of the image: the image is read once for all nine bases.
+__global__ void __launch_bounds__(256) analysis_l1_kernel(const __grid_constant__ SaraConst c,
+                                                          const float *__restrict__ x, float *__restrict__ coef,
+                                                          float *__restrict__ tmp) {
+    __shared__ float sin_[AIN_Y][AIN_X + 1];
+    __shared__ float slo[AIN_Y][ATX + 1];
+    __shared__ float shi[AIN_Y][ATX + 1];
+    const int l = blockIdx.z;
+    const int k0y = blockIdx.y * ATY, k0x = blockIdx.x * ATX;
+    const int ny = c.img_ny, nx = c.img_nx;
+    const long long N = (long long)ny * nx;
+    const float *xl = x + (long long)l * N;
+    float *coef_l = coef + (long long)l * c.n_coef;
+    const int r0 = 2 * k0y + 2 - kMaxF, c0 = 2 * k0x + 2 - kMaxF;
+    for (int idx = threadIdx.x; idx < AIN_Y * AIN_X; idx += blockDim.x) {
+        const int r = idx / AIN_X, cc = idx - r * AIN_X;
+        const int gy = r0 + r, gx = c0 + cc;
+        sin_[r][cc] = (gy >= 0 && gy < ny && gx >= 0 && gx < nx) ? xl[(long long)gy * nx + gx] : 0.f;
+    }
+    __syncthreads();
+    // Dirac basis: pixels [2 k0, 2 k0 + 2 tile) of this CTA (tiles partition the image).
+    for (int idx = threadIdx.x; idx < 4 * ATY * ATX; idx += blockDim.x) {
+        const int ry = idx / (2 * ATX), rx = idx - ry * (2 * ATX);
+        const int gy = 2 * k0y + ry, gx = 2 * k0x + rx;
+        if (gy < ny && gx < nx) coef_l[(long long)gy * nx + gx] = sin_[ry + kMaxF - 2][rx + kMaxF - 2] * kSaraScale;
+    }
+    for (int p = 1; p <= kNumDb; ++p) {
+        if (k0y >= c.ny[p][1] || k0x >= c.nx[p][1]) continue;
+        float *ll_out = (c.levels == 1) ? coef_l + c.off_ll[p] : tmp + (long long)l * c.n_tmp + c.off_tmp[p][1];
+        analysis_tile(c, p, 1, k0y, k0x, sin_, slo, shi, coef_l, ll_out, c.levels == 1 ? kSaraScale : 1.f);
+    }
+}
+
+// Level j >= 2 of basis p from its level j-1 approximation.
+__global__ void __launch_bounds__(256) analysis_lj_kernel(const __grid_constant__ SaraConst c, int j,
+                                                          float *__restrict__ coef, float *__restrict__ tmp) {
+    __shared__ float sin_[AIN_Y][AIN_X + 1];
+    __shared__ float slo[AIN_Y][ATX + 1];
+    __shared__ float shi[AIN_Y][ATX + 1];
+    const int p = 1 + blockIdx.z % kNumDb;
+    const int l = blockIdx.z / kNumDb;
+    const int k0y = blockIdx.y * ATY, k0x = blockIdx.x * ATX;
+    if (k0y >= c.ny[p][j] || k0x >= c.nx[p][j]) return;
+    const int ny = c.ny[p][j - 1], nx = c.nx[p][j - 1];
+    const float *in = tmp + (long long)l * c.n_tmp + c.off_tmp[p][j - 1];
+    float *coef_l = coef + (long long)l * c.n_coef;
+    const int r0 = 2 * k0y + 2 - kMaxF, c0 = 2 * k0x + 2 - kMaxF;
+    for (int idx = threadIdx.x; idx < AIN_Y * AIN_X; idx += blockDim.x) {
+        const int r = idx / AIN_X, cc = idx - r * AIN_X;
+        const int gy = r0 + r, gx = c0 + cc;
+        sin_[r][cc] = (gy >= 0 && gy < ny && gx >= 0 && gx < nx) ? in[(long long)gy * nx + gx] : 0.f;
+    }
+    __syncthreads();
+    const bool last = (j == c.levels);
+    float *ll_out = last ? coef_l + c.off_ll[p] : tmp + (long long)l * c.n_tmp + c.off_tmp[p][j];
+    analysis_tile(c, p, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, last ? kSaraScale : 1.f);
+}
+
+// Adjoint of one level of basis p: a_{j-1}[m] = sum_k f[2k+1-m] band[k] over the
+// four bands, for an STY x STX tile of a_{j-1} starting at (m0y, m0x).
+// Returns the tile value of this thread's outputs through `acc`.
+__device__ __forceinline__ void synthesis_tile(const SaraConst &c, int p, int j, int m0y, int m0x,
+                                               const float *coef_l, const float *ll_in, float ll_scale,
+                                               float (*sb)[SB_Y][SB_X + 1], float (*su)[SB_Y][STX + 1],
+                                               float *acc) {
+    const int F = c.F[p];
+    const int my = c.ny[p][j], mx = c.nx[p][j];
+    const float *h = c.h[p];
+    const float *g = c.g[p];
+    const long long bs = (long long)my * mx;
+    const int k0y = m0y / 2, k0x = m0x / 2;
+    const float *det = coef_l + c.off_det[p][j];
+    for (int idx = threadIdx.x; idx < SB_Y * SB_X; idx += blockDim.x) {
+        const int r = idx / SB_X, cc = idx - r * SB_X;
+        const int ky = k0y + r, kx = k0x + cc;
+        float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
+        if (ky < my && kx < mx) {
+            const long long o = (long long)ky * mx + kx;
+            v0 = ll_in[o] * ll_scale;
+            v1 = det[o];
+            v2 = det[bs + o];
+            v3 = det[2 * bs + o];
+        }
+        sb[0][r][cc] = v0;   // LL  (y lo, x lo)
+        sb[1][r][cc] = v1;   // LH  (y lo, x hi)
+        sb[2][r][cc] = v2;   // HL  (y hi, x lo)
+        sb[3][r][cc] = v3;   // HH  (y hi, x hi)
+    }
+    __syncthreads();
+    // x: u_lo = synth(LL, h) + synth(LH, g); u_hi = synth(HL, h) + synth(HH, g)
+    for (int idx = threadIdx.x; idx < SB_Y * STX; idx += blockDim.x) {
+        const int r = idx / STX, rx = idx - r * STX;
+        float ulo = 0.f, uhi = 0.f;
+        for (int i = (rx + 1) & 1; i < F; i += 2) {
+            const int kl = (rx - 1 + i) >> 1;
+            ulo = fmaf(h[i], sb[0][r][kl], fmaf(g[i], sb[1][r][kl], ulo));
+            uhi = fmaf(h[i], sb[2][r][kl], fmaf(g[i], sb[3][r][kl], uhi));
+        }
+        su[0][r][rx] = ulo;
+        su[1][r][rx] = uhi;
+    }
+    __syncthreads();
+    int t = 0;
+    for (int idx = threadIdx.x; idx < STY * STX; idx += blockDim.x, ++t) {
+        const int ry = idx / STX, rx = idx - ry * STX;
+        float a = 0.f;
+        for (int i = (ry + 1) & 1; i < F; i += 2) {
+            const int kl = (ry - 1 + i) >> 1;
+            a = fmaf(h[i], su[0][kl][rx], fmaf(g[i], su[1][kl][rx], a));
+        }
+        acc[t] += a;
+    }
+    __syncthreads();
+}
+
+// Levels j >= 2: reconstruct a_{j-1} of basis p into tmp.
+__global__ void __launch_bounds__(256) synthesis_lj_kernel(const __grid_constant__ SaraConst c, int j,
+                                                           const float *__restrict__ coef, float *__restrict__ tmp) {
+    __shared__ float sb[4][SB_Y][SB_X + 1];
+    __shared__ float su[2][SB_Y][STX + 1];
+    const int p = 1 + blockIdx.z % kNumDb;
+    const int l = blockIdx.z / kNumDb;
+    const int m0y = blockIdx.y * STY, m0x = blockIdx.x * STX;
+    const int oy = c.ny[p][j - 1], ox = c.nx[p][j - 1];
+    if (m0y >= oy || m0x >= ox) return;
+    const float *coef_l = coef + (long long)l * c.n_coef;
+    const bool last = (j == c.levels);
+    const float *ll_in = last ? coef_l + c.off_ll[p] : tmp + (long long)l * c.n_tmp + c.off_tmp[p][j];
+    float acc[STY * STX / 256] = {0.f, 0.f};
+    synthesis_tile(c, p, j, m0y, m0x, coef_l, ll_in, 1.f, sb, su, acc);
+    float *out = tmp + (long long)l * c.n_tmp + c.off_tmp[p][j - 1];
+    int t = 0;
+    for (int idx = threadIdx.x; idx < STY * STX; idx += blockDim.x, ++t) {
+        const int ry = idx / STX, rx = idx - ry * STX;
+        const int gy = m0y + ry, gx = m0x + rx;
+        if (gy < oy && gx < ox) out[(long long)gy * ox + gx] = acc[t];
+    }
+}
+
+// Level 1 of all bases plus the Dirac basis, summed into the image: x = (1/3) sum.
+__global__ void __launch_bounds__(256) synthesis_l1_kernel(const __grid_constant__ SaraConst c,
+                                                           const float *__restrict__ coef, const float *__restrict__ tmp,
+                                                           float *__restrict__ x) {
+    __shared__ float sb[4][SB_Y][SB_X + 1];
+    __shared__ float su[2][SB_Y][STX + 1];
+    const int l = blockIdx.z;
+    const int m0y = blockIdx.y * STY, m0x = blockIdx.x * STX;
+    const int ny = c.img_ny, nx = c.img_nx;
+    const float *coef_l = coef + (long long)l * c.n_coef;
+    float acc[STY * STX / 256] = {0.f, 0.f};
+    for (int p = 1; p <= kNumDb; ++p) {
+        const float *ll_in = (c.levels == 1) ? coef_l + c.off_ll[p] : tmp + (long long)l * c.n_tmp + c.off_tmp[p][1];
+        synthesis_tile(c, p, 1, m0y, m0x, coef_l, ll_in, 1.f, sb, su, acc);
+    }
+    int t = 0;
+    for (int idx = threadIdx.x; idx < STY * STX; idx += blockDim.x, ++t) {
+        const int ry = idx / STX, rx = idx - ry * STX;
+        const int gy = m0y + ry, gx = m0x + rx;
+        if (gy < ny && gx < nx) {
+            const long long o = (long long)gy * nx + gx;
+            x[(long long)l * ny * nx + o] = (acc[t] + coef_l[o]) * kSaraScale;
+        }
+    }
+}
+
+// Weighted l21 dual step, one thread per (sub-cube, coefficient):
+// z_l = W_l + sigma1 A_l over the sub-cube's channels, W_l = z_l min(1, mu w / ||z||).
+template <int MAXLC>
+__global__ void __launch_bounds__(256) l21_dual_kernel(float *__restrict__ W, const float *__restrict__ A,
+                                                       const float *__restrict__ w21, long long n_coef, int C, int Lc,
+                                                       float sigma1, float mu) {
+    const int c = blockIdx.y;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n_coef;
+         r += (long long)gridDim.x * blockDim.x) {
+        float z[MAXLC];
+        float n2 = 0.f;
+#pragma unroll
+        for (int jj = 0; jj < MAXLC; ++jj) {
+            if (jj < Lc) {
+                const long long o = (long long)(c + jj * C) * n_coef + r;
+                z[jj] = fmaf(sigma1, A[o], W[o]);
+                n2 = fmaf(z[jj], z[jj], n2);
+            }
+        }
+        const float thr = mu * w21[(long long)c * n_coef + r];
+        const float nr = sqrtf(n2);
+        const float f = (nr > thr) ? thr / nr : 1.f;
+#pragma unroll
+        for (int jj = 0; jj < MAXLC; ++jj)
+            if (jj < Lc) W[(long long)(c + jj * C) * n_coef + r] = z[jj] * f;
+    }
+}
+
+// Log-sum weights w_r = upsilon / (upsilon + ||(Psi^dagger X)_r||) per sub-cube.
+__global__ void __launch_bounds__(256) l21_reweight_kernel(const float *__restrict__ A, float *__restrict__ w21,
+                                                           long long n_coef, int C, int Lc, double upsilon) {
+    const int c = blockIdx.y;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n_coef;
+         r += (long long)gridDim.x * blockDim.x) {
+        double n2 = 0.0;
+        for (int jj = 0; jj < Lc; ++jj) {
+            const double a = A[(long long)(c + jj * C) * n_coef + r];
+            n2 += a * a;
+        }
+        w21[(long long)c * n_coef + r] = float(upsilon / (upsilon + sqrt(n2)));
+    }
+}
+
+inline int cdiv(long long a, long long b) { return int((a + b - 1) / b); }
+
+}  // namespace
+
+cudaError_t launch_sara_analysis(fhs_problem *p, const float *x, float *coef, cudaStream_t s) {
+    const SaraConst &c = p->sara;
+    int my = 0, mx = 0;
+    for (int b = 1; b <= kNumDb; ++b) { my = max(my, c.ny[b][1]); mx = max(mx, c.nx[b][1]); }
+    analysis_l1_kernel<<<dim3(cdiv(mx, ATX), cdiv(my, ATY), p->L), 256, 0, s>>>(c, x, coef, p->sara_tmp);
+    for (int j = 2; j <= c.levels; ++j) {
+        my = mx = 0;
+        for (int b = 1; b <= kNumDb; ++b) { my = max(my, c.ny[b][j]); mx = max(mx, c.nx[b][j]); }
+        analysis_lj_kernel<<<dim3(cdiv(mx, ATX), cdiv(my, ATY), p->L * kNumDb), 256, 0, s>>>(c, j, coef, p->sara_tmp);
+    }
+    p->n_launch += c.levels;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sara_synthesis(fhs_problem *p, const float *coef, float *x, cudaStream_t s) {
+    const SaraConst &c = p->sara;
+    for (int j = c.levels; j >= 2; --j) {
+        int my = 0, mx = 0;
+        for (int b = 1; b <= kNumDb; ++b) { my = max(my, c.ny[b][j - 1]); mx = max(mx, c.nx[b][j - 1]); }
+        synthesis_lj_kernel<<<dim3(cdiv(mx, STX), cdiv(my, STY), p->L * kNumDb), 256, 0, s>>>(c, j, coef, p->sara_tmp);
+    }
+    synthesis_l1_kernel<<<dim3(cdiv(c.img_nx, STX), cdiv(c.img_ny, STY), p->L), 256, 0, s>>>(c, coef, p->sara_tmp, x);
+    p->n_launch += c.levels;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_l21_dual(fhs_problem *p, cudaStream_t s) {
+    const long long n = p->sara.n_coef;
+    dim3 g(min(cdiv(n, 256), 152 * 8), p->C);
+    const float s1 = float(p->sigma1), mu = float(p->prm.mu);
+    if (p->Lc <= 2) l21_dual_kernel<2><<<g, 256, 0, s>>>(p->W, p->coef_tmp, p->w21, n, p->C, p->Lc, s1, mu);
+    else if (p->Lc <= 4) l21_dual_kernel<4><<<g, 256, 0, s>>>(p->W, p->coef_tmp, p->w21, n, p->C, p->Lc, s1, mu);
+    else if (p->Lc <= 8) l21_dual_kernel<8><<<g, 256, 0, s>>>(p->W, p->coef_tmp, p->w21, n, p->C, p->Lc, s1, mu);
+    else if (p->Lc <= 16) l21_dual_kernel<16><<<g, 256, 0, s>>>(p->W, p->coef_tmp, p->w21, n, p->C, p->Lc, s1, mu);
+    else l21_dual_kernel<32><<<g, 256, 0, s>>>(p->W, p->coef_tmp, p->w21, n, p->C, p->Lc, s1, mu);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_l21_reweight(fhs_problem *p, cudaStream_t s) {
+    const long long n = p->sara.n_coef;
+    dim3 g(min(cdiv(n, 256), 152 * 8), p->C);
+    l21_reweight_kernel<<<g, 256, 0, s>>>(p->coef_tmp, p->w21, n, p->C, p->Lc, p->prm.upsilon);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace fhs

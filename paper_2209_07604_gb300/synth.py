@@ -17,6 +17,7 @@ which is not available.
 from __future__ import annotations
 
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -97,13 +98,18 @@ def _draw_uv(rng: np.random.Generator, M: int) -> np.ndarray:
     return out[perm]
 
 
-def _blob_ft_1d(om: np.ndarray, a: np.ndarray, c: float, s: float) -> np.ndarray:
-    """int exp(-(t-c)^2/(2 s^2) + i pi a t^2 - i om t) dt, written around t = c
-    so that no large exponent cancels."""
+def _blob_ft(o1: np.ndarray, o2: np.ndarray, a: np.ndarray, c1: float, c2: float, s: float) -> np.ndarray:
+    """Fourier transform of the blob exp(-|t-c|^2/(2 s^2)) times the w-term
+    chirp exp(i pi a |t|^2), at frequencies (o1, o2):
+    prod_d int exp(-(t-c_d)^2/(2 s^2) + i pi a t^2 - i o_d t) dt
+      = (pi / alpha) exp(-(q1^2 + q2^2)/(4 alpha) + i (pi a |c|^2 - o.c)),
+    alpha = 1/(2 s^2) - i pi a, q_d = 2 pi a c_d - o_d (written around t = c so
+    that no large exponent cancels)."""
     alpha = 1.0 / (2.0 * s * s) - 1j * math.pi * a
-    q = 2.0 * math.pi * a * c - om
-    return np.sqrt(math.pi / alpha) * np.exp(-(q * q) / (4.0 * alpha)
-                                             + 1j * (math.pi * a * c * c - om * c))
+    q1 = 2.0 * math.pi * a * c1 - o1
+    q2 = 2.0 * math.pi * a * c2 - o2
+    return (math.pi / alpha) * np.exp(-(q1 * q1 + q2 * q2) / (4.0 * alpha)
+                                      + 1j * (math.pi * a * (c1 * c1 + c2 * c2) - o1 * c1 - o2 * c2))
 
 
 def make_problem(name: str = "small_128", trial: int = 0, M: int | None = None,
@@ -150,16 +156,27 @@ def make_problem(name: str = "small_128", trial: int = 0, M: int | None = None,
 
     y = np.zeros((L, Mv), dtype=np.complex128)
     sigma = np.zeros(L)
-    chunk = 1 << 18
+    chunk = 1 << 16
+
+    def sky_vis(job):
+        l, s0 = job
+        sl = slice(s0, min(Mv, s0 + chunk))
+        a_l = w[l, sl] * pixel_size ** 2
+        acc = np.zeros(sl.stop - sl.start, dtype=np.complex128)
+        o1, o2 = omega[l, sl, 0], omega[l, sl, 1]
+        for b in range(n_blobs):
+            acc += amp_l[l, b] * _blob_ft(o1, o2, a_l, cy[b], cx[b], s[b])
+        y[l, sl] = acc
+
+    jobs = [(l, s0) for l in range(L) for s0 in range(0, Mv, chunk)]
+    if len(jobs) > 4:      # numpy ufuncs release the GIL: threads share the work
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(max_workers=min(32, os.cpu_count() or 1)) as ex:
+            list(ex.map(sky_vis, jobs))
+    else:
+        for j in jobs:
+            sky_vis(j)
     for l in range(L):
-        a_l = w[l] * pixel_size ** 2
-        for s0 in range(0, Mv, chunk):
-            sl = slice(s0, min(Mv, s0 + chunk))
-            acc = np.zeros(sl.stop - sl.start, dtype=np.complex128)
-            for b in range(n_blobs):
-                acc += amp_l[l, b] * (_blob_ft_1d(omega[l, sl, 0], a_l[sl], cy[b], s[b])
-                                      * _blob_ft_1d(omega[l, sl, 1], a_l[sl], cx[b], s[b]))
-            y[l, sl] = acc
         sigma[l] = np.linalg.norm(y[l]) / math.sqrt(Mv) * 10.0 ** (-snr_db / 20.0)
     noise = (rng.standard_normal((L, Mv)) + 1j * rng.standard_normal((L, Mv))) / math.sqrt(2.0)
     y += sigma[:, None] * noise

@@ -1,0 +1,98 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point declared in include/fhs.h, rejects bad arguments before
+touching the device, and computes its own Daubechies filters (compared with
+the oracle's and with the published closed forms)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2209_07604_gb300 as fhs
+from oracle import wavelets as wv
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2209_07604_gb300 import build
+    build.build()
+    return fhs.load_library()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "fhs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fhs_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_and_binding_agree(lib):
+    decl = declared_symbols()
+    assert decl, "no declarations parsed"
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert sorted(fhs.EXPORTED) == decl
+
+
+def test_library_filters_match_oracle(lib):
+    for p in range(1, 9):
+        np.testing.assert_allclose(fhs.fhs_daubechies_filter(p), wv.daubechies(p), rtol=0, atol=1e-13)
+
+
+def test_bad_filter_order_is_rejected(lib):
+    with pytest.raises(fhs.FhsError) as e:
+        fhs.fhs_daubechies_filter(9)
+    assert e.value.status == fhs.FHS_ERR_ARG
+
+
+def _args(L=2, M=10, B=2):
+    om = np.zeros((L * M, 2))
+    y = np.zeros((L * M, 2))
+    sig = np.ones(L)
+    vo = np.arange(L + 1, dtype=np.int64) * M
+    bo = np.array([[0, M // 2, M]] * L, dtype=np.int64)
+    return om, y, sig, vo, bo
+
+
+@pytest.mark.parametrize("field,value", [("ny", 15), ("nx", 8), ("n_subcubes", 3), ("n_blocks", 0),
+                                         ("facet_overlap", 1.0), ("wavelet_levels", 9), ("mu", -1.0),
+                                         ("upsilon", 0.0), ("qy", 0)])
+def test_invalid_params_rejected_without_device(lib, field, value):
+    p = fhs.default_params(ny=32, nx=32, n_channels=2, n_subcubes=1, n_blocks=2, mu=0.1, mu_bar=0.1)
+    setattr(p, field, value)
+    om, y, sig, vo, bo = _args()
+    with pytest.raises(fhs.FhsError) as e:
+        fhs.fhs_create_problem(p, om, None, y, sig, vo, bo)
+    assert e.value.status == fhs.FHS_ERR_ARG
+    assert lib.fhs_last_error().decode()
+
+
+def test_invalid_inputs_rejected_without_device(lib):
+    p = fhs.default_params(ny=32, nx=32, n_channels=2, n_subcubes=1, n_blocks=2)
+    om, y, sig, vo, bo = _args()
+    om[3, 0] = 4.0                                   # outside [-pi, pi)
+    with pytest.raises(fhs.FhsError):
+        fhs.fhs_create_problem(p, om, None, y, sig, vo, bo)
+    om, y, sig, vo, bo = _args()
+    bo[1, 2] = 9                                     # blocks must end at M_l
+    with pytest.raises(fhs.FhsError):
+        fhs.fhs_create_problem(p, om, None, y, sig, vo, bo)
+    om, y, sig, vo, bo = _args()
+    sig[0] = 0.0
+    with pytest.raises(fhs.FhsError):
+        fhs.fhs_create_problem(p, om, None, y, sig, vo, bo)
+    om, y, sig, vo, bo = _args()
+    y[0, 0] = np.nan
+    with pytest.raises(fhs.FhsError):
+        fhs.fhs_create_problem(p, om, None, y, sig, vo, bo)
+
+
+def test_params_struct_layout(lib):
+    # the ctypes mirror must have the C layout: defaults written by the library read back sanely
+    p = fhs.default_params()
+    assert p.kb_taps == 7 and p.wavelet_levels == 4 and p.n_wplanes == 64 and p.power_iters == 100
+    assert abs(p.upsilon - 1e-3) < 1e-18 and abs(p.power_tol - 1e-7) < 1e-20
+    # 7 int32 + pad, double, 2 int32, double, int32 + pad, 9 doubles, int32 + pad, double
+    assert C.sizeof(fhs.fhs_params) == 152

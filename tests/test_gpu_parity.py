@@ -1,0 +1,230 @@
+"""GPU parity of libfhs against the FP64 oracle, through the C ABI.
+
+Tolerances: Phi / Phi^H and the SARA transforms run in FP32 with FP32
+accumulation over at most a few hundred terms, so the relative error of a
+whole output vector is bounded by ~sqrt(terms) * 2^-24 * (condition of the
+sum) ~ 1e-6; the parity bound is 1e-5 (relative, 2-norm).  A PDFB iterate is
+a non-expansive map of FP32-rounded operators, so after k iterations the
+image error stays at a few 1e-6; the bound is 1e-4 (relative, 2-norm).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+import paper_2209_07604_gb300 as fhs
+from paper_2209_07604_gb300 import synth
+from oracle import nufft as onf, pdfb as opdfb, wavelets as owv
+
+TOL_OP = 1e-5
+TOL_IMG = 1e-4
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2209_07604_gb300 import build
+    build.build()
+    fhs.load_library()
+
+
+def _oracle(P, mu, mu_bar, sigma2, n_wplanes=64, **kw):
+    return opdfb.FHS(P.omega, P.w, P.y, P.sigma, P.block_offsets, P.ny, P.nx, P.C, P.qy, P.qx, P.overlap,
+                     mu=mu, mu_bar=mu_bar, w_max=P.w_max, n_wplanes=n_wplanes, pixel_size=P.pixel_size,
+                     steps=kw.pop("steps", None), **kw)
+
+
+def _steps_from(prob, sigma2):
+    i = prob.info
+    return opdfb.Steps(tau=i.tau, sigma0=i.sigma0, sigma1=i.sigma1, sigma2=sigma2)
+
+
+@pytest.mark.parametrize("name", ["tiny", "small_128", "mid_w"])
+def test_measure_and_adjoint(name):
+    P = synth.make_problem(name)
+    prob = fhs.Problem.from_synth(P, mu=0.0, mu_bar=0.0, sigma2=1.0)
+    geom = onf.Geometry(P.ny, P.nx, w_max=P.w_max, n_wplanes=64, pixel_size=P.pixel_size)
+    op = onf.Operator(P.omega, P.w, P.sigma, geom)
+    x = synth.random_image((P.L, P.ny, P.nx), 1)
+    vis = prob.measure(torch.tensor(x, dtype=torch.float32, device="cuda")).cpu().numpy().reshape(P.L, -1)
+    ref = np.stack(op.forward_all(x))
+    assert rel(vis, ref) < TOL_OP
+    v = synth.random_vis((P.L, P.M), 2)
+    img = prob.adjoint(torch.tensor(v.reshape(-1), dtype=torch.complex64, device="cuda")).cpu().numpy()
+    ref_img = op.adjoint_all(list(v))
+    assert rel(img, ref_img) < TOL_OP
+    # adjoint identity of the GPU pair itself
+    lhs = np.vdot(v.reshape(-1), vis.reshape(-1).astype(np.complex128)).real
+    rhs = float(np.sum(img.astype(np.float64) * x))
+    assert abs(lhs - rhs) < 1e-5 * abs(lhs)
+    prob.close()
+
+
+def test_nnz_and_row_lengths_match_oracle():
+    P = synth.make_problem("mid_w")
+    prob = fhs.Problem.from_synth(P, mu=0.0, mu_bar=0.0, sigma2=1.0)
+    geom = onf.Geometry(P.ny, P.nx, w_max=P.w_max, n_wplanes=64, pixel_size=P.pixel_size)
+    nnz = sum(onf.build_G(P.omega[l], P.w[l], 1.0, geom).nnz for l in range(P.L))
+    assert prob.info.nnz == nnz
+    prob.close()
+
+
+@pytest.mark.parametrize("ny,nx,levels", [(128, 128, 4), (96, 160, 4), (48, 32, 2), (64, 64, 1)])
+def test_sara_analysis_synthesis(ny, nx, levels):
+    P = synth.make_problem("tiny")
+    prob = fhs.Problem.from_synth(P, mu=0.0, mu_bar=0.0, sigma2=1.0, ny=ny, nx=nx, wavelet_levels=levels)
+    S = owv.Sara(ny, nx, levels)
+    assert prob.info.n_coef == S.n_coef
+    x = synth.random_image((P.L, ny, nx), 3, nonneg=False)
+    c = prob.sara_analysis(torch.tensor(x, dtype=torch.float32, device="cuda")).cpu().numpy()
+    assert rel(c, S.analysis(x)) < TOL_OP
+    z = synth.random_image((P.L, S.n_coef), 4, nonneg=False)
+    xs = prob.sara_synthesis(torch.tensor(z, dtype=torch.float32, device="cuda")).cpu().numpy()
+    assert rel(xs, S.synthesis(z)) < TOL_OP
+    prob.close()
+
+
+def test_operator_norms():
+    P = synth.make_problem("small_128")
+    prob = fhs.Problem.from_synth(P, mu=0.0, mu_bar=0.0, sigma2=1.0)
+    geom = onf.Geometry(P.ny, P.nx)
+    op = onf.Operator(P.omega, P.w, P.sigma, geom)
+    gpu = prob.operator_norms(400)
+    for l in range(P.L):
+        ref = op.norm2(l, n_iter=400, tol=0.0)
+        assert abs(gpu[l] - ref) < 1e-4 * ref
+    prob.close()
+
+
+def _run_pair(name, n_iter, n_reweight, mu, mu_bar, **over):
+    P = synth.make_problem(name, **over)
+    geom = onf.Geometry(P.ny, P.nx, w_max=P.w_max, n_wplanes=64, pixel_size=P.pixel_size)
+    op = onf.Operator(P.omega[:1], P.w[:1], P.sigma[:1], geom)
+    sigma2 = 1.0 / (1.02 * op.norm2(0, n_iter=60))
+    prob = fhs.Problem.from_synth(P, mu=mu, mu_bar=mu_bar, sigma2=sigma2)
+    ref = _oracle(P, mu, mu_bar, sigma2, steps=_steps_from(prob, sigma2))
+    ref.run(n_iter, n_reweight)
+    per = n_iter // (n_reweight + 1)
+    for r in range(n_reweight + 1):
+        k = per if r < n_reweight else n_iter - per * n_reweight
+        prob.step(k)
+        if r < n_reweight:
+            prob.reweight()
+    torch.cuda.synchronize()
+    return P, prob, ref
+
+
+@pytest.mark.parametrize("name,n_iter,n_reweight,mu,mu_bar", [
+    ("tiny", 10, 0, 0.02, 0.3),
+    ("small_128", 50, 0, 0.05, 1.0),
+    ("mid_w", 20, 1, 0.05, 0.5),
+])
+def test_pdfb_iterates(name, n_iter, n_reweight, mu, mu_bar):
+    P, prob, ref = _run_pair(name, n_iter, n_reweight, mu, mu_bar)
+    img = prob.image().cpu().numpy()
+    assert rel(img, ref.X) < TOL_IMG
+    # duals
+    v = prob.get_state(fhs.STATE_DUAL_DATA).cpu().numpy().view(np.complex64).reshape(P.L, -1)
+    assert rel(v, np.stack(ref.v)) < TOL_IMG
+    W = prob.get_state(fhs.STATE_DUAL_SARA).cpu().numpy().reshape(P.L, -1)
+    Wref = np.zeros_like(W, dtype=np.float64)
+    for c, ch in enumerate(ref.chans):
+        Wref[ch] = ref.W[c]
+    assert rel(W, Wref) < TOL_IMG
+    Pn = prob.get_state(fhs.STATE_DUAL_NUCLEAR).cpu().numpy()
+    Pref = np.concatenate([ref.P[c][q].ravel() for c in range(P.C) for q in range(len(ref.facets))])
+    assert rel(Pn, Pref) < TOL_IMG
+    if n_reweight:
+        w21 = prob.get_state(fhs.STATE_WEIGHTS_SARA).cpu().numpy().reshape(P.C, -1)
+        assert rel(w21, np.stack(ref.w21)) < TOL_IMG
+        wn = prob.get_state(fhs.STATE_WEIGHTS_NUC).cpu().numpy()
+        wref = np.concatenate([ref.wnuc[c][q] for c in range(P.C) for q in range(len(ref.facets))])
+        assert rel(wn, wref) < TOL_IMG
+    prob.close()
+
+
+def test_relative_change_and_nonnegativity():
+    P = synth.make_problem("tiny")
+    prob = fhs.Problem.from_synth(P, mu=0.02, mu_bar=0.3, sigma2=1e-3)
+    prob.step(3)
+    Xa = prob.image().cpu().numpy().astype(np.float64)
+    r = prob.step(1, want_rel=True)
+    Xb = prob.image().cpu().numpy().astype(np.float64)
+    assert abs(r - np.linalg.norm(Xb - Xa) / np.linalg.norm(Xb)) < 1e-5 * r
+    assert Xb.min() >= 0.0
+    prob.close()
+
+
+def test_checkpoint_resume():
+    P = synth.make_problem("mid_w")
+    prob = fhs.Problem.from_synth(P, mu=0.05, mu_bar=0.5, sigma2=1e-4)
+    prob.step(4)
+    prob.reweight()
+    prob.step(2)
+    parts = [fhs.STATE_IMAGE, fhs.STATE_DUAL_DATA, fhs.STATE_DUAL_SARA, fhs.STATE_DUAL_NUCLEAR,
+             fhs.STATE_WEIGHTS_SARA, fhs.STATE_WEIGHTS_NUC]
+    saved = {k: prob.get_state(k).clone() for k in parts}
+    prob.step(5)
+    Xa = prob.image().cpu().numpy()
+    other = fhs.Problem.from_synth(P, mu=0.05, mu_bar=0.5, sigma2=1e-4)
+    for k in parts:
+        other.set_state(k, saved[k])
+    other.step(5)
+    Xb = other.image().cpu().numpy()
+    assert rel(Xb, Xa) < 1e-5
+    prob.close()
+    other.close()
+
+
+def test_solve_matches_step_schedule():
+    P = synth.make_problem("tiny")
+    a = fhs.Problem.from_synth(P, mu=0.02, mu_bar=0.3, sigma2=1e-3)
+    n = a.solve(12, 0.0, n_reweight=1, check_every=4)
+    assert n == 12
+    b = fhs.Problem.from_synth(P, mu=0.02, mu_bar=0.3, sigma2=1e-3)
+    b.step(6)
+    b.reweight()
+    b.step(6)
+    assert rel(a.image().cpu().numpy(), b.image().cpu().numpy()) < 1e-5
+    a.close()
+    b.close()
+
+
+def test_empty_block_and_uneven_channels():
+    """A block with no visibilities (eps = 0, factor 1) and channels with
+    different visibility counts, against the oracle."""
+    P = synth.make_problem("tiny", L=2, C=1)
+    M = P.M
+    cut = M - 200
+    omega = np.concatenate([P.omega[0], P.omega[1, :cut]])
+    w = np.concatenate([P.w[0], P.w[1, :cut]])
+    y = np.concatenate([P.y[0], P.y[1, :cut]])
+    vo = np.array([0, M, M + cut], dtype=np.int64)
+    bo = np.array([[0, M // 2, M], [0, 0, cut]], dtype=np.int64)
+    params = fhs.default_params(ny=P.ny, nx=P.nx, n_channels=2, n_subcubes=1, n_blocks=2, qy=P.qy, qx=P.qx,
+                                facet_overlap=P.overlap, mu=0.02, mu_bar=0.3, sigma2=1e-3)
+    prob = fhs.Problem(params, omega, w, y, P.sigma, vo, bo)
+    prob.step(6)
+    X = prob.image().cpu().numpy()
+    # oracle per channel: channel 1 with its truncated data, blocks [0,0) and [0,cut)
+    geom = onf.Geometry(P.ny, P.nx)
+    from oracle import prox as oprox
+    ref = opdfb.FHS(P.omega, P.w, P.y, P.sigma, P.block_offsets, P.ny, P.nx, 1, P.qy, P.qx, P.overlap,
+                    mu=0.02, mu_bar=0.3, steps=_steps_from(prob, 1e-3))
+    ref.op.G[1] = onf.build_G(P.omega[1, :cut], P.w[1, :cut], P.sigma[1], geom)
+    ref.yw[1] = P.y[1, :cut] / P.sigma[1]
+    ref.v[1] = np.zeros(cut, dtype=np.complex128)
+    ref.bo = np.array([[0, M // 2, M], [0, 0, cut]])
+    ref.eps = np.stack([oprox.eps_blocks(M, [M // 2, M - M // 2]), oprox.eps_blocks(cut, [0, cut])])
+    ref.run(6)
+    assert rel(X, ref.X) < TOL_IMG
+    prob.close()
