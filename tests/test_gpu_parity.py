@@ -62,10 +62,11 @@ def test_measure_and_adjoint(name):
     img = prob.adjoint(torch.tensor(v.reshape(-1), dtype=torch.complex64, device="cuda")).cpu().numpy()
     ref_img = op.adjoint_all(list(v))
     assert rel(img, ref_img) < TOL_OP
-    # adjoint identity of the GPU pair itself
+    # adjoint identity of the GPU pair itself, on the Cauchy-Schwarz scale
+    # ||v|| ||Phi x|| (the sum itself cancels heavily)
     lhs = np.vdot(v.reshape(-1), vis.reshape(-1).astype(np.complex128)).real
     rhs = float(np.sum(img.astype(np.float64) * x))
-    assert abs(lhs - rhs) < 1e-5 * abs(lhs)
+    assert abs(lhs - rhs) < 1e-5 * np.linalg.norm(v) * np.linalg.norm(vis)
     prob.close()
 
 
@@ -94,14 +95,32 @@ def test_sara_analysis_synthesis(ny, nx, levels):
 
 
 def test_operator_norms():
-    P = synth.make_problem("small_128")
+    """||Phi_l||^2 by the GPU power iteration against the largest singular
+    value of the explicit FP64 matrix (tiny problem), and against the oracle's
+    power iteration at the parity size (both converge from below; real images
+    pair the singular values, so the gap is small and convergence slow)."""
+    P = synth.make_problem("tiny")
     prob = fhs.Problem.from_synth(P, mu=0.0, mu_bar=0.0, sigma2=1.0)
     geom = onf.Geometry(P.ny, P.nx)
     op = onf.Operator(P.omega, P.w, P.sigma, geom)
+    gpu = prob.operator_norms(3000)
+    for l in range(P.L):
+        cols = []
+        for k in range(P.ny * P.nx):
+            e = np.zeros(P.ny * P.nx)
+            e[k] = 1.0
+            cols.append(op.forward(e.reshape(P.ny, P.nx), l))
+        A = np.array(cols).T
+        smax = np.linalg.svd(np.vstack([A.real, A.imag]), compute_uv=False)[0]
+        assert abs(gpu[l] - smax ** 2) < 1e-5 * smax ** 2
+    prob.close()
+    P = synth.make_problem("small_128")
+    prob = fhs.Problem.from_synth(P, mu=0.0, mu_bar=0.0, sigma2=1.0)
+    op = onf.Operator(P.omega, P.w, P.sigma, onf.Geometry(P.ny, P.nx))
     gpu = prob.operator_norms(400)
     for l in range(P.L):
         ref = op.norm2(l, n_iter=400, tol=0.0)
-        assert abs(gpu[l] - ref) < 1e-4 * ref
+        assert abs(gpu[l] - ref) < 1e-3 * ref
     prob.close()
 
 
