@@ -137,6 +137,25 @@ fhs_status fhs_adjoint(fhs_problem *prob, const float *vis_dev, float *x_dev, vo
  * zero extension).  Equal to the faceted transform on any tiling.  Async. */
 fhs_status fhs_sara_analysis(fhs_problem *prob, const float *x_dev, float *coef_dev, void *stream);
 
+/* Same coefficients as fhs_sara_analysis for n_images images of ny x nx
+ * pixels ([n_images][ny][nx] in, [n_images][n_coef] out, layout as above),
+ * without a problem handle and without allocating device memory.  The paper
+ * has no counterpart: this entry point serves callers that cannot allocate
+ * device memory, such as code whose device memory is fully reserved by
+ * another allocator (a framework's caching allocator or a fixed pool) and
+ * latency-critical loops that must not pay for cudaMalloc and the device
+ * synchronisation it can imply.  Its scratch is a 16 MiB static device array
+ * (2^22 floats) that every GPU loading the library holds until exit; images
+ * needing more scratch than that (about 1.4e6 pixels at 4 levels) are rejected
+ * with FHS_ERR_ARG.  The first call on a device looks up the array's address
+ * on that device (it must be the current device); make that first call before
+ * any stream capture.  Every call shares the one array, so calls that overlap
+ * on the GPU (other streams, other threads) race: order them.  The scratch
+ * needs no clearing (every value read was written earlier in the same call).
+ * Asynchronous on `stream`. */
+fhs_status fhs_sara_analysis_noalloc(int32_t ny, int32_t nx, int32_t n_images, int32_t levels,
+                                     const float *x_dev, float *coef_dev, void *stream);
+
 /* x_dev[L][ny][nx] = Psi c_l, the adjoint of fhs_sara_analysis.  Async. */
 fhs_status fhs_sara_synthesis(fhs_problem *prob, const float *coef_dev, float *x_dev, void *stream);
 

@@ -23,6 +23,7 @@ EXPORTED = [
     "fhs_adjoint", "fhs_sara_analysis", "fhs_sara_synthesis", "fhs_pdfb_step", "fhs_reweight", "fhs_solve",
     "fhs_state_size", "fhs_get_state", "fhs_set_state", "fhs_operator_norms", "fhs_daubechies_filter",
     "fhs_last_error", "fhs_profile_enable", "fhs_profile_read", "fhs_kernel_launches",
+    "fhs_sara_analysis_noalloc",
 ]
 PHASES = ["primal", "fft_fwd", "degrid_grid", "l2ball", "fft_inv", "sara", "nuclear"]
 
@@ -86,6 +87,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fhs_profile_enable": (C.c_int, [vp, i32]),
         "fhs_profile_read": (C.c_int, [vp, vp, P(i64)]),
         "fhs_kernel_launches": (C.c_int, [vp, P(i64)]),
+        "fhs_sara_analysis_noalloc": (C.c_int, [i32, i32, i32, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -177,6 +179,13 @@ def fhs_adjoint(prob, vis, x, stream=None):
 
 def fhs_sara_analysis(prob, x, coef, stream=None):
     _check(load_library().fhs_sara_analysis(prob, _dev(x, "float32"), _dev(coef, "float32"), _stream(stream)))
+
+
+def fhs_sara_analysis_noalloc(ny, nx, n_images, levels, x, coef, stream=None):
+    """SARA analysis for callers that cannot allocate device memory (static
+    16 MiB scratch shared by all calls; overlapping calls race)."""
+    _check(load_library().fhs_sara_analysis_noalloc(int(ny), int(nx), int(n_images), int(levels),
+                                                    _dev(x, "float32"), _dev(coef, "float32"), _stream(stream)))
 
 
 def fhs_sara_synthesis(prob, coef, x, stream=None):

@@ -253,6 +253,8 @@ fhs_status one_iteration(fhs_problem *p, cudaStream_t s) {
 
 }  // namespace
 
+void fhs::set_last_error(const std::string &msg) { g_err = msg; }
+
 extern "C" {
 
 const char *fhs_last_error(void) { return g_err.c_str(); }

@@ -137,6 +137,9 @@ struct fhs_problem {
 
 namespace fhs {
 
+// Sets the text returned by fhs_last_error() on the calling thread.
+void set_last_error(const std::string &msg);
+
 // kernel launchers --------------------------------------------------------
 // k_nufft.cu
 cudaError_t launch_build_g(fhs_problem *p, const double2 *kap, const short *plane, const double2 *wk_table,

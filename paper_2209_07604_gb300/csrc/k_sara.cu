@@ -9,6 +9,10 @@
 // One level, one axis: c[k] = sum_i f[i] a[2k+1-i], k < floor((n+F-1)/2).
 #include "fhs_internal.h"
 
+#include <cstring>
+#include <mutex>
+#include <string>
+
 namespace fhs {
 
 namespace {
@@ -328,3 +332,130 @@ cudaError_t launch_l21_reweight(fhs_problem *p, cudaStream_t s) {
 }
 
 }  // namespace fhs
+
+// ---------------------------------------------------------------------------
+// SARA analysis that allocates nothing.
+//
+// Its scratch (the level approximations a_1..a_{J-1} of one image, all nine
+// bases) lives in a file-scope device array of kNoAllocScratchFloats floats
+// (16 MiB), which every GPU that loads the library holds until the process
+// exits.  Host code cannot use the array's name as a device address, so the
+// address is fetched with cudaGetSymbolAddress once per device, on the first
+// call made with that device current, and cached.
+// ---------------------------------------------------------------------------
+namespace fhs {
+namespace {
+
+constexpr long long kNoAllocScratchFloats = 1LL << 22;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchFloats];
+
+std::mutex g_noalloc_mu;
+float *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Layout of Psi^dagger for an ny x nx image with `levels` levels (the same
+// layout fhs_create_problem builds), computed on the host.
+SaraConst noalloc_layout(int ny, int nx, int levels) {
+    SaraConst c;
+    std::memset(&c, 0, sizeof c);
+    c.levels = levels;
+    c.img_ny = ny;
+    c.img_nx = nx;
+    long long pos = (long long)ny * nx, tpos = 0;
+    for (int b = 1; b <= kNumDb; ++b) {
+        const std::vector<double> h = daubechies(b);
+        const int F = 2 * b;
+        c.F[b] = F;
+        for (int k = 0; k < F; ++k) {
+            c.h[b][k] = float(h[k]);
+            c.g[b][k] = float((k & 1) ? -h[F - 1 - k] : h[F - 1 - k]);
+        }
+        c.ny[b][0] = ny;
+        c.nx[b][0] = nx;
+        for (int j = 1; j <= levels; ++j) {
+            c.ny[b][j] = (c.ny[b][j - 1] + F - 1) / 2;
+            c.nx[b][j] = (c.nx[b][j - 1] + F - 1) / 2;
+        }
+    }
+    for (int b = 1; b <= kNumDb; ++b) {
+        for (int j = 1; j <= levels; ++j) {
+            c.off_det[b][j] = pos;
+            pos += 3LL * c.ny[b][j] * c.nx[b][j];
+        }
+        c.off_ll[b] = pos;
+        pos += (long long)c.ny[b][levels] * c.nx[b][levels];
+        for (int j = 1; j < levels; ++j) {
+            c.off_tmp[b][j] = tpos;
+            tpos += (long long)c.ny[b][j] * c.nx[b][j];
+        }
+    }
+    c.n_coef = pos;
+    c.n_tmp = tpos > 0 ? tpos : 1;
+    return c;
+}
+
+}  // namespace
+}  // namespace fhs
+
+extern "C" fhs_status fhs_sara_analysis_noalloc(int32_t ny, int32_t nx, int32_t n_images, int32_t levels,
+                                                const float *x_dev, float *coef_dev, void *stream) {
+    using namespace fhs;
+    if (!x_dev || !coef_dev) {
+        set_last_error("fhs_sara_analysis_noalloc: NULL buffer");
+        return FHS_ERR_ARG;
+    }
+    if (ny < 16 || nx < 16 || n_images < 0 || levels < 1 || levels > kMaxLevels) {
+        set_last_error("fhs_sara_analysis_noalloc: need ny, nx >= 16, n_images >= 0, 1 <= levels <= 6");
+        return FHS_ERR_ARG;
+    }
+    const SaraConst c = noalloc_layout(ny, nx, levels);
+    if (c.n_tmp > kNoAllocScratchFloats) {
+        set_last_error("fhs_sara_analysis_noalloc: image needs " + std::to_string(c.n_tmp) +
+                       " scratch floats, more than the static maximum of " +
+                       std::to_string(kNoAllocScratchFloats) + " (about 1.4e6 pixels at 4 levels)");
+        return FHS_ERR_ARG;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_last_error(std::string("fhs_sara_analysis_noalloc: no usable current device: ") + cudaGetErrorString(e));
+        return FHS_ERR_CUDA;
+    }
+    float *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess) {
+                set_last_error(std::string("fhs_sara_analysis_noalloc: cudaGetSymbolAddress failed: ") +
+                               cudaGetErrorString(e));
+                return FHS_ERR_CUDA;
+            }
+            g_noalloc_ptr[dev] = static_cast<float *>(ptr);
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int my = 0, mx = 0;
+    for (int b = 1; b <= kNumDb; ++b) { my = max(my, c.ny[b][1]); mx = max(mx, c.nx[b][1]); }
+    const long long N = (long long)ny * nx;
+    // one image at a time: the scratch holds the approximations of one image
+    for (int i = 0; i < n_images; ++i) {
+        const float *xi = x_dev + (long long)i * N;
+        float *ci = coef_dev + (long long)i * c.n_coef;
+        analysis_l1_kernel<<<dim3(cdiv(mx, ATX), cdiv(my, ATY), 1), 256, 0, s>>>(c, xi, ci, scratch);
+        for (int j = 2; j <= c.levels; ++j) {
+            int ly = 0, lx = 0;
+            for (int b = 1; b <= kNumDb; ++b) { ly = max(ly, c.ny[b][j]); lx = max(lx, c.nx[b][j]); }
+            analysis_lj_kernel<<<dim3(cdiv(lx, ATX), cdiv(ly, ATY), kNumDb), 256, 0, s>>>(c, j, ci, scratch);
+        }
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_last_error(std::string("fhs_sara_analysis_noalloc: launch failed: ") + cudaGetErrorString(e));
+        return FHS_ERR_CUDA;
+    }
+    return FHS_OK;
+}
