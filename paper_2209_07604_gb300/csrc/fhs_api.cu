@@ -431,6 +431,46 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
     p->n_chunk = int(cseg.size());
     cstart.push_back(Mtot);
 
+    // ---- tile bins for the single-pass data kernel: runs of one tile key of at
+    // least kDenseMin visibilities become shared-memory bins (split at kBinMax);
+    // shorter runs are packed into sparse bins that take the global path.
+    constexpr long long kDenseMin = 48, kBinMax = 384, kSparseMax = 384;   // kBinMax: smem capacity of a bin
+    std::vector<long long> bstart;
+    std::vector<int> bseg, btile;
+    p->ntx = ntx;
+    for (int sg = 0; sg < p->n_seg; ++sg) {
+        const long long a = p->seg_off[sg], b = p->seg_off[sg + 1];
+        long long sp0 = -1;                          // open sparse run start
+        auto flush_sparse = [&](long long end) {
+            for (long long q = sp0; q < end; q += kSparseMax) {
+                bstart.push_back(q);
+                bseg.push_back(sg);
+                btile.push_back(-1);
+            }
+            sp0 = -1;
+        };
+        long long i = a;
+        while (i < b) {
+            const int k = (meta[i].x & 0xffff) / kTile * ntx + (int)((unsigned)meta[i].x >> 16) / kTile;
+            long long j = i + 1;
+            while (j < b && (meta[j].x & 0xffff) / kTile * ntx + (int)((unsigned)meta[j].x >> 16) / kTile == k) ++j;
+            if (j - i >= kDenseMin) {
+                if (sp0 >= 0) flush_sparse(i);
+                for (long long q = i; q < j; q += kBinMax) {
+                    bstart.push_back(q);
+                    bseg.push_back(sg);
+                    btile.push_back(k);
+                }
+            } else if (sp0 < 0) {
+                sp0 = i;
+            }
+            i = j;
+        }
+        if (sp0 >= 0) flush_sparse(b);
+    }
+    p->n_bin = int(bseg.size());
+    bstart.push_back(Mtot);
+
     std::vector<double> eps(p->n_seg), inv_sig(p->n_seg);
     for (int l = 0; l < L; ++l) {
         const double Ml = double(vis_offsets[l + 1] - vis_offsets[l]);
@@ -458,6 +498,9 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
     if ((st = guard(dev_alloc(p, &p->blk_norm2, p->n_seg))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->eps, p->n_seg, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->blk_scale, p->n_seg, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->bin_start, p->n_bin + 1, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->bin_seg, p->n_bin, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->bin_tile, p->n_bin, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->chunk_start, p->n_chunk + 1, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->chunk_seg, p->n_chunk, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &d_kap, Mtot, false))) != FHS_OK) return st;
@@ -472,6 +515,9 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
     if ((st = guard(upload(p->d_seg_off, p->seg_off.data(), p->n_seg + 1, s))) != FHS_OK) return st;
     if ((st = guard(upload(p->eps, eps.data(), p->n_seg, s))) != FHS_OK) return st;
     if ((st = guard(upload(p->blk_scale, ones.data(), p->n_seg, s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->bin_start, bstart.data(), bstart.size(), s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->bin_seg, bseg.data(), bseg.size(), s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->bin_tile, btile.data(), btile.size(), s))) != FHS_OK) return st;
     if ((st = guard(upload(p->chunk_start, cstart.data(), cstart.size(), s))) != FHS_OK) return st;
     if ((st = guard(upload(p->chunk_seg, cseg.data(), cseg.size(), s))) != FHS_OK) return st;
     if ((st = guard(upload(d_kap, kap.data(), Mtot, s))) != FHS_OK) return st;

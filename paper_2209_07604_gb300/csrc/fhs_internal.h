@@ -81,6 +81,10 @@ struct fhs_problem {
     double *blk_norm2 = nullptr;              // [n_seg]
     double *eps = nullptr;                    // [n_seg]
     float *blk_scale = nullptr;               // [n_seg]  (1 - m_b)
+    int n_bin = 0, ntx = 0;                   // tile bins of the single-pass data kernel
+    long long *bin_start = nullptr;           // [n_bin+1]
+    int *bin_seg = nullptr;                   // [n_bin]
+    int *bin_tile = nullptr;                  // [n_bin] tile key, -1 = sparse (global path)
     int n_chunk = 0;
     long long *chunk_start = nullptr;         // [n_chunk+1]
     int *chunk_seg = nullptr;                 // [n_chunk]

@@ -69,78 +69,129 @@ __global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ P, 
             if (threadIdx.x == (k & 255) && i < Lc && j < Lc) atomicAdd(&G[i * Lc + j], s_red[k]);
 }
 
-// Symmetric eigen-decomposition of one Gram per thread (cyclic Jacobi, FP64,
-// bounded sweeps), then either the SVT mixing matrix or the reweighting weights.
-__global__ void eig_kernel(double *__restrict__ gram, float *__restrict__ mix, float *__restrict__ wnuc, int n_mat,
-                           int Lc, double mu_bar, double upsilon_bar, bool reweight) {
-    const int cq = blockIdx.x * blockDim.x + threadIdx.x;
+// Symmetric eigen-decomposition of one L_c x L_c Gram per warp: cyclic Jacobi
+// in FP64 with a round-robin ordering, so each round applies L_c/2 disjoint
+// rotations at once (columns first, then rows: disjoint Givens rotations
+// commute).  Bounded sweeps.  Then either the SVT mixing matrix
+// M = V diag(min(1, mu_bar w_i / s_i)) V^T or the reweighting weights.
+constexpr int kEigWarps = 4;
+
+__global__ void __launch_bounds__(32 * kEigWarps) eig_kernel(double *__restrict__ gram, float *__restrict__ mix,
+                                                            float *__restrict__ wnuc, int n_mat, int Lc,
+                                                            double mu_bar, double upsilon_bar, bool reweight) {
+    __shared__ double s_a[kEigWarps][16][17];
+    __shared__ double s_v[kEigWarps][16][17];
+    __shared__ double s_cs[kEigWarps][8], s_sn[kEigWarps][8];
+    __shared__ int s_p[kEigWarps][8], s_q[kEigWarps][8];
+    __shared__ int s_ord[kEigWarps][16];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cq = blockIdx.x * kEigWarps + w;
     if (cq >= n_mat) return;
-    double a[kMaxLc][kMaxLc], V[kMaxLc][kMaxLc];
+    double(*a)[17] = s_a[w];
+    double(*V)[17] = s_v[w];
     double *G = gram + (long long)cq * Lc * Lc;
-    for (int i = 0; i < Lc; ++i)
-        for (int j = 0; j < Lc; ++j) {
-            a[i][j] = (j >= i) ? G[i * Lc + j] : G[j * Lc + i];
-            V[i][j] = (i == j) ? 1.0 : 0.0;
-        }
-    for (int i = 0; i < Lc * Lc; ++i) G[i] = 0.0;        // ready for the next accumulation
-    for (int sweep = 0; sweep < 64; ++sweep) {
+    const int n = Lc + (Lc & 1);                 // even size: a padded row/column stays zero
+    for (int e = lane; e < n * n; e += 32) {
+        const int i = e / n, j = e - (e / n) * n;
+        double v = 0.0;
+        if (i < Lc && j < Lc) v = (j >= i) ? G[i * Lc + j] : G[j * Lc + i];
+        a[i][j] = v;
+        V[i][j] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    for (int e = lane; e < Lc * Lc; e += 32) G[e] = 0.0;   // ready for the next accumulation
+    const int half = n / 2;
+    for (int sweep = 0; sweep < 40; ++sweep) {
         double off = 0.0, dia = 0.0;
-        for (int i = 0; i < Lc; ++i) {
-            dia += a[i][i] * a[i][i];
-            for (int j = i + 1; j < Lc; ++j) off += a[i][j] * a[i][j];
+        for (int e = lane; e < n * n; e += 32) {
+            const int i = e / n, j = e - (e / n) * n;
+            const double x = a[i][j];
+            if (i == j) dia += x * x; else off += x * x;
         }
-        if (off <= 1e-30 * dia || off == 0.0) break;
-        for (int pp = 0; pp < Lc - 1; ++pp)
-            for (int qq = pp + 1; qq < Lc; ++qq) {
-                const double apq = a[pp][qq];
-                if (apq == 0.0) continue;
-                const double theta = (a[qq][qq] - a[pp][pp]) / (2.0 * apq);
-                const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
-                for (int k = 0; k < Lc; ++k) {
-                    const double akp = a[k][pp], akq = a[k][qq];
-                    a[k][pp] = cs * akp - sn * akq;
-                    a[k][qq] = sn * akp + cs * akq;
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            dia += __shfl_xor_sync(0xffffffffu, dia, o);
+        }
+        if (off <= 1e-28 * dia || off == 0.0) break;
+        for (int round = 0; round < n - 1; ++round) {
+            // round-robin pairing: position 0 fixed, the others rotate
+            if (lane < half) {
+                const int k = lane;
+                int pa = (k == 0) ? 0 : 1 + (k - 1 + round) % (n - 1);
+                int pb = 1 + (n - 2 - k + round) % (n - 1);
+                const int p = min(pa, pb), q = max(pa, pb);
+                const double apq = a[p][q];
+                double cs = 1.0, sn = 0.0;
+                if (apq != 0.0) {
+                    const double theta = (a[q][q] - a[p][p]) / (2.0 * apq);
+                    const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                    cs = 1.0 / sqrt(t * t + 1.0);
+                    sn = t * cs;
                 }
-                for (int k = 0; k < Lc; ++k) {
-                    const double apk = a[pp][k], aqk = a[qq][k];
-                    a[pp][k] = cs * apk - sn * aqk;
-                    a[qq][k] = sn * apk + cs * aqk;
-                }
-                for (int k = 0; k < Lc; ++k) {
-                    const double vkp = V[k][pp], vkq = V[k][qq];
-                    V[k][pp] = cs * vkp - sn * vkq;
-                    V[k][qq] = sn * vkp + cs * vkq;
-                }
+                s_p[w][k] = p;
+                s_q[w][k] = q;
+                s_cs[w][k] = cs;
+                s_sn[w][k] = sn;
             }
-    }
-    // eigenvalues descending with their vectors
-    int order[kMaxLc];
-    for (int i = 0; i < Lc; ++i) order[i] = i;
-    for (int i = 0; i < Lc; ++i)
-        for (int j = i + 1; j < Lc; ++j)
-            if (a[order[j]][order[j]] > a[order[i]][order[i]]) {
-                const int t = order[i]; order[i] = order[j]; order[j] = t;
+            __syncwarp();
+            // columns: A <- A J, V <- V J
+            for (int e = lane; e < half * n; e += 32) {
+                const int k = e / n, r = e - k * n;
+                const int p = s_p[w][k], q = s_q[w][k];
+                const double cs = s_cs[w][k], sn = s_sn[w][k];
+                const double arp = a[r][p], arq = a[r][q];
+                a[r][p] = cs * arp - sn * arq;
+                a[r][q] = sn * arp + cs * arq;
+                const double vrp = V[r][p], vrq = V[r][q];
+                V[r][p] = cs * vrp - sn * vrq;
+                V[r][q] = sn * vrp + cs * vrq;
             }
-    float *w = wnuc + (long long)cq * Lc;
-    double fac[kMaxLc];
-    for (int i = 0; i < Lc; ++i) {
-        const double sv = sqrt(fmax(a[order[i]][order[i]], 0.0));
-        if (reweight) {
-            w[i] = float(upsilon_bar / (upsilon_bar + sv));
-        } else {
-            const double thr = mu_bar * double(w[i]);
-            fac[i] = (sv > thr) ? thr / sv : 1.0;
+            __syncwarp();
+            // rows: A <- J^T A
+            for (int e = lane; e < half * n; e += 32) {
+                const int k = e / n, c = e - k * n;
+                const int p = s_p[w][k], q = s_q[w][k];
+                const double cs = s_cs[w][k], sn = s_sn[w][k];
+                const double apc = a[p][c], aqc = a[q][c];
+                a[p][c] = cs * apc - sn * aqc;
+                a[q][c] = sn * apc + cs * aqc;
+            }
+            __syncwarp();
         }
     }
-    if (reweight) return;
+    if (lane == 0) {                          // eigenvalues descending (padding excluded)
+        int *ord = s_ord[w];
+        for (int i = 0; i < Lc; ++i) ord[i] = i;
+        for (int i = 0; i < Lc; ++i)
+            for (int j = i + 1; j < Lc; ++j)
+                if (a[ord[j]][ord[j]] > a[ord[i]][ord[i]]) {
+                    const int t = ord[i]; ord[i] = ord[j]; ord[j] = t;
+                }
+    }
+    __syncwarp();
+    const int *ord = s_ord[w];
+    float *wv = wnuc + (long long)cq * Lc;
+    if (reweight) {
+        if (lane < Lc) {
+            const double sv = sqrt(fmax(a[ord[lane]][ord[lane]], 0.0));
+            wv[lane] = float(upsilon_bar / (upsilon_bar + sv));
+        }
+        return;
+    }
+    __shared__ double s_f[kEigWarps][16];
+    if (lane < Lc) {
+        const double sv = sqrt(fmax(a[ord[lane]][ord[lane]], 0.0));
+        const double thr = mu_bar * double(wv[lane]);
+        s_f[w][lane] = (sv > thr) ? thr / sv : 1.0;
+    }
+    __syncwarp();
     float *M = mix + (long long)cq * Lc * Lc;
-    for (int i = 0; i < Lc; ++i)
-        for (int j = 0; j < Lc; ++j) {
-            double m = 0.0;
-            for (int k = 0; k < Lc; ++k) m += V[i][order[k]] * fac[k] * V[j][order[k]];
-            M[i * Lc + j] = float(m);
-        }
+    for (int e = lane; e < Lc * Lc; e += 32) {
+        const int i = e / Lc, j = e - (e / Lc) * Lc;
+        double m = 0.0;
+        for (int k = 0; k < Lc; ++k) m += V[i][ord[k]] * s_f[w][k] * V[j][ord[k]];
+        M[e] = float(m);
+    }
 }
 
 // P_q <- (P_q + sigma0 S_q xbar) M_q, one thread per facet pixel.
@@ -204,8 +255,8 @@ cudaError_t launch_nuclear_gram(fhs_problem *p, const float *img, bool with_dual
 
 cudaError_t launch_nuclear_eig(fhs_problem *p, bool reweight, cudaStream_t s) {
     const int n = p->C * p->Q;
-    eig_kernel<<<(n + 63) / 64, 64, 0, s>>>(p->gram, p->mix, p->wnuc, n, p->Lc, p->prm.mu_bar, p->prm.upsilon_bar,
-                                           reweight);
+    eig_kernel<<<(n + kEigWarps - 1) / kEigWarps, 32 * kEigWarps, 0, s>>>(
+        p->gram, p->mix, p->wnuc, n, p->Lc, p->prm.mu_bar, p->prm.upsilon_bar, reweight);
     p->n_launch += 1;
     return cudaGetLastError();
 }

@@ -233,6 +233,194 @@ __global__ void __launch_bounds__(256) degrid_grid_fused_kernel(
     }
 }
 
+// Tile-binned form of the same pass.  A bin holds visibilities of one
+// (channel, block) segment whose box corners fall in one kTile x kTile grid
+// tile; every box then lies inside the kWin x kWin window at the tile origin.
+// The CTA stages the window of the forward grid in shared memory, gathers
+// from it, accumulates conj(G) d with shared-memory atomics, and adds the
+// window to the block grid once at the end (one global reduction per cell
+// instead of one per G entry).  Bins marked -1 (sparse tiles) take the
+// global path.
+constexpr int kWin = kTile + 15;        // boxes have T <= 16
+constexpr int kBinMax = 384;            // visibilities per bin (host splits longer runs)
+
+struct RowRegs {
+    float2 g[8];
+};
+
+// Issue the loads of one row's values (lane e, e + 32, ...); consumed later.
+__device__ __forceinline__ void load_row(RowRegs &r, const float2 *__restrict__ gv, int n, int lane) {
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+        if (32 * it >= n) break;            // warp-uniform: skip unused slots
+        const int e = lane + 32 * it;
+        if (e < n) r.g[it] = __ldcs(gv + e);
+    }
+}
+
+// Compensated (Kahan) FP32 accumulation for the block norms: a warp sums at
+// most kBinMax / kWarps visibilities this way; warps and CTAs combine in FP64.
+struct Kahan {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+// Visibilities i = i0, i0 + kWarps, ... of one bin, for one warp.  DENSE: the
+// box lies in the shared window; otherwise gather/scatter in global memory.
+template <bool DENSE>
+__device__ __forceinline__ void bin_rows(int i0, int nv, int lane, const int2 *s_meta, const int *s_off,
+                                         const float2 *s_y, const float2 *s_d, const float2 *__restrict__ gbin,
+                                         const float2 *s_grid, float *s_re, float *s_im, int wy0, int wx0,
+                                         const float2 *__restrict__ gl, float2 *__restrict__ gb, int K1, int K2,
+                                         float sc, float sigma2, float2 *__restrict__ dvis_bin, Kahan &nrm) {
+    RowRegs cur, nxt;
+    int i = i0;
+    if (i < nv) load_row(cur, gbin + s_off[i], s_meta[i].y * s_meta[i].y, lane);
+    for (; i < nv; i += kWarps) {
+        const int in = i + kWarps;
+        if (in < nv) load_row(nxt, gbin + s_off[in], s_meta[in].y * s_meta[in].y, lane);
+        const int2 m = s_meta[i];
+        const int T = m.y, n = T * T;
+        const int c1 = m.x & 0xffff, c2 = (int)((unsigned)m.x >> 16);
+        const float invT = 1.0f / float(T);
+        int idx[8];
+        float ar = 0.f, ai = 0.f;
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            if (32 * it >= n) break;
+            const int e = lane + 32 * it;
+            if (e < n) {
+                float2 x;
+                if (DENSE) {
+                    const int t1 = __float2int_rz((float(e) + 0.5f) * invT);
+                    const int t2 = e - t1 * T;
+                    idx[it] = (c1 - wy0 + t1) * kWin + (c2 - wx0 + t2);
+                    x = s_grid[idx[it]];
+                } else {
+                    idx[it] = cell_index(e, T, invT, c1, c2, K1, K2);
+                    x = gl[idx[it]];
+                }
+                const float2 g = cur.g[it];
+                ar = fmaf(g.x, x.x, fmaf(-g.y, x.y, ar));
+                ai = fmaf(g.x, x.y, fmaf(g.y, x.x, ai));
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ar += __shfl_xor_sync(0xffffffffu, ar, o);
+            ai += __shfl_xor_sync(0xffffffffu, ai, o);
+        }
+        const float2 dold = s_d[i];
+        const float2 sy = s_y[i];
+        const float dr = fmaf(sc, dold.x, fmaf(sigma2, ar, -sy.x));
+        const float di = fmaf(sc, dold.y, fmaf(sigma2, ai, -sy.y));
+        if (lane == 0) {
+            dvis_bin[i] = make_float2(dr, di);
+            nrm.add(fmaf(dr, dr, di * di));
+        }
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            if (32 * it >= n) break;
+            const int e = lane + 32 * it;
+            if (e < n) {
+                const float2 g = cur.g[it];
+                const float pr = g.x * dr + g.y * di, pi = g.x * di - g.y * dr;
+                if (DENSE) {
+                    atomicAdd(s_re + idx[it], pr);
+                    atomicAdd(s_im + idx[it], pi);
+                } else {
+                    red_add_f2(gb + idx[it], make_float2(pr, pi));
+                }
+            }
+        }
+        cur = nxt;
+    }
+}
+
+__global__ void __launch_bounds__(256) degrid_grid_binned_kernel(
+    const int2 *__restrict__ meta, const long long *__restrict__ rowptr, const float2 *__restrict__ gval,
+    const float2 *__restrict__ y, float2 *__restrict__ dvis, const long long *__restrict__ bin_start,
+    const int *__restrict__ bin_seg, const int *__restrict__ bin_tile, int ntx, int B,
+    const float *__restrict__ blk_scale, double *__restrict__ blk_norm2, const float2 *__restrict__ grid,
+    float2 *__restrict__ grid_blk, long long K, int K1, int K2, float sigma2) {
+    __shared__ float2 s_grid[kWin * kWin];
+    __shared__ float s_re[kWin * kWin];
+    __shared__ float s_im[kWin * kWin];
+    __shared__ int2 s_meta[kBinMax];
+    __shared__ int s_off[kBinMax];        // row offset relative to the bin's first value
+    __shared__ float2 s_y[kBinMax];       // sigma2 * y
+    __shared__ float2 s_d[kBinMax];
+    __shared__ double s_red[kWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bin = blockIdx.x;
+    const int seg = bin_seg[bin];
+    const int tile = bin_tile[bin];
+    const int l = seg / B;
+    const float2 *gl = grid + (long long)l * K;
+    float2 *gb = grid_blk + (long long)seg * K;
+    const float sc = blk_scale[seg];
+    const long long v0 = bin_start[bin];
+    const int nv = int(bin_start[bin + 1] - v0);
+    const long long g0 = rowptr[v0];
+    const float2 *gbin = gval + g0;
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+        s_meta[i] = meta[v0 + i];
+        s_off[i] = int(rowptr[v0 + i] - g0);
+        const float2 yy = y[v0 + i];
+        s_y[i] = make_float2(sigma2 * yy.x, sigma2 * yy.y);
+        s_d[i] = dvis[v0 + i];
+    }
+    const bool dense = tile >= 0;
+    int wy0 = 0, wx0 = 0;
+    if (dense) {
+        wy0 = (tile / ntx) * kTile;
+        wx0 = (tile % ntx) * kTile;
+        for (int i = threadIdx.x; i < kWin * kWin; i += blockDim.x) {
+            const int r = i / kWin, c = i - r * kWin;
+            int k1 = wy0 + r;
+            while (k1 >= K1) k1 -= K1;
+            int k2 = wx0 + c;
+            while (k2 >= K2) k2 -= K2;
+            s_grid[i] = gl[(long long)k1 * K2 + k2];
+            s_re[i] = 0.f;
+            s_im[i] = 0.f;
+        }
+    }
+    __syncthreads();
+    Kahan nrm;
+    if (dense)
+        bin_rows<true>(warp, nv, lane, s_meta, s_off, s_y, s_d, gbin, s_grid, s_re, s_im, wy0, wx0, gl, gb, K1, K2,
+                       sc, sigma2, dvis + v0, nrm);
+    else
+        bin_rows<false>(warp, nv, lane, s_meta, s_off, s_y, s_d, gbin, s_grid, s_re, s_im, wy0, wx0, gl, gb, K1,
+                        K2, sc, sigma2, dvis + v0, nrm);
+    if (lane == 0) s_red[warp] = double(nrm.s) - double(nrm.c);
+    __syncthreads();
+    if (dense) {
+        for (int q = threadIdx.x; q < kWin * kWin; q += blockDim.x) {
+            const float re = s_re[q], im = s_im[q];
+            if (re != 0.f || im != 0.f) {
+                const int r = q / kWin, c = q - r * kWin;
+                int k1 = wy0 + r;
+                while (k1 >= K1) k1 -= K1;
+                int k2 = wx0 + c;
+                while (k2 >= K2) k2 -= K2;
+                red_add_f2(gb + (long long)k1 * K2 + k2, make_float2(re, im));
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kWarps; ++w) t += s_red[w];
+        atomicAdd(blk_norm2 + seg, t);
+    }
+}
+
 // l2-ball factor per block: m_b = min(1, sigma2 eps_b / ||d_b||), s_b = 1 - m_b.
 __global__ void block_finalize_kernel(double *blk_norm2, const double *eps, float *blk_scale, int n_seg,
                                       double sigma2) {
@@ -244,26 +432,35 @@ __global__ void block_finalize_kernel(double *blk_norm2, const double *eps, floa
     blk_norm2[s] = 0.0;
 }
 
-// grid_work[l] = sum_b s_{l,b} grid_blk[l][b]; grid_blk <- 0.  float4 = 2 cells.
+// grid_work[l] = sum_b s_{l,b} grid_blk[l][b]; grid_blk <- 0.  float4 = 2 cells;
+// blockIdx.y is the channel.  All B loads are issued before any store so they
+// overlap (the zero stores would otherwise order them).
+template <int MAXB>
 __global__ void __launch_bounds__(256) combine_kernel(float4 *__restrict__ blk, float4 *__restrict__ out,
-                                                      const float *__restrict__ blk_scale, int B,
-                                                      long long K4, int L) {
-    const long long total = K4 * L;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        const long long l = t / K4, k = t - l * K4;
+                                                      const float *__restrict__ blk_scale, int B, long long K4) {
+    const int l = blockIdx.y;
+    float sc[MAXB];
+#pragma unroll
+    for (int b = 0; b < MAXB; ++b) sc[b] = (b < B) ? blk_scale[l * B + b] : 0.f;
+    float4 *base = blk + (long long)l * B * K4;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < K4; k += (long long)gridDim.x * blockDim.x) {
+        float4 v[MAXB];
+#pragma unroll
+        for (int b = 0; b < MAXB; ++b)
+            if (b < B) v[b] = __ldcs(base + (long long)b * K4 + k);
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int b = 0; b < B; ++b) {
-            float4 *src = blk + ((l * B + b) * K4 + k);
-            const float4 v = *src;
-            const float s = blk_scale[l * B + b];
-            acc.x = fmaf(s, v.x, acc.x);
-            acc.y = fmaf(s, v.y, acc.y);
-            acc.z = fmaf(s, v.z, acc.z);
-            acc.w = fmaf(s, v.w, acc.w);
-            *src = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        out[t] = acc;
+#pragma unroll
+        for (int b = 0; b < MAXB; ++b)
+            if (b < B) {
+                acc.x = fmaf(sc[b], v[b].x, acc.x);
+                acc.y = fmaf(sc[b], v[b].y, acc.y);
+                acc.z = fmaf(sc[b], v[b].z, acc.z);
+                acc.w = fmaf(sc[b], v[b].w, acc.w);
+            }
+        out[(long long)l * K4 + k] = acc;
+#pragma unroll
+        for (int b = 0; b < MAXB; ++b)
+            if (b < B) __stcs(base + (long long)b * K4 + k, make_float4(0.f, 0.f, 0.f, 0.f));
     }
 }
 
@@ -395,10 +592,11 @@ cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, 
 }
 
 cudaError_t launch_degrid_grid_fused(fhs_problem *p, cudaStream_t s) {
-    if (p->n_chunk == 0) return cudaSuccess;
-    degrid_grid_fused_kernel<<<p->n_chunk, 256, 0, s>>>(p->meta, p->rowptr, p->gval, p->y, p->dvis, p->chunk_start,
-                                                        p->chunk_seg, p->B, p->blk_scale, p->blk_norm2, p->grid_work,
-                                                        p->grid_blk, p->K, p->K1, p->K2, float(p->sigma2));
+    if (p->n_bin == 0) return cudaSuccess;
+    degrid_grid_binned_kernel<<<p->n_bin, 256, 0, s>>>(p->meta, p->rowptr, p->gval, p->y, p->dvis, p->bin_start,
+                                                       p->bin_seg, p->bin_tile, p->ntx, p->B, p->blk_scale,
+                                                       p->blk_norm2, p->grid_work, p->grid_blk, p->K, p->K1, p->K2,
+                                                       float(p->sigma2));
     p->n_launch += 1;
     return cudaGetLastError();
 }
@@ -412,9 +610,13 @@ cudaError_t launch_block_finalize(fhs_problem *p, cudaStream_t s) {
 
 cudaError_t launch_combine(fhs_problem *p, cudaStream_t s) {
     const long long K4 = p->K / 2;
-    combine_kernel<<<grid_for(K4 * p->L, 256, 152 * 16), 256, 0, s>>>(
-        reinterpret_cast<float4 *>(p->grid_blk), reinterpret_cast<float4 *>(p->grid_work), p->blk_scale, p->B, K4,
-        p->L);
+    dim3 g(grid_for(K4, 256, 152 * 8 / p->L + 1), p->L);
+    float4 *blk = reinterpret_cast<float4 *>(p->grid_blk), *out = reinterpret_cast<float4 *>(p->grid_work);
+    if (p->B <= 2) combine_kernel<2><<<g, 256, 0, s>>>(blk, out, p->blk_scale, p->B, K4);
+    else if (p->B <= 4) combine_kernel<4><<<g, 256, 0, s>>>(blk, out, p->blk_scale, p->B, K4);
+    else if (p->B <= 8) combine_kernel<8><<<g, 256, 0, s>>>(blk, out, p->blk_scale, p->B, K4);
+    else if (p->B <= 16) combine_kernel<16><<<g, 256, 0, s>>>(blk, out, p->blk_scale, p->B, K4);
+    else return cudaErrorInvalidValue;
     p->n_launch += 1;
     return cudaGetLastError();
 }

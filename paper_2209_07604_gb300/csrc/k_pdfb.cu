@@ -22,7 +22,8 @@ __global__ void __launch_bounds__(256) primal_kernel(
     const int l = blockIdx.y;
     const int c = l % C, j = l / C;
     const long long N = (long long)ny * nx;
-    double num = 0.0, den = 0.0;
+    // compensated FP32 per thread, FP64 across threads
+    float num = 0.f, cnum = 0.f, den = 0.f, cden = 0.f;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
         const int i1 = int(p / nx), i2 = int(p - (long long)i1 * nx);
         int k1 = i1 - ny / 2; k1 += (k1 < 0) ? K1 : 0;
@@ -48,15 +49,24 @@ __global__ void __launch_bounds__(256) primal_kernel(
         X[o] = xp;
         Xbar[o] = xb;
         grid_in[gk] = make_float2(xb * sc, 0.f);
-        const double dx = double(xp) - double(x);
-        num += dx * dx;
-        den += double(xp) * double(xp);
+        const float dx = xp - x;
+        {
+            const float yv = fmaf(dx, dx, -cnum), t = num + yv;
+            cnum = (t - num) - yv;
+            num = t;
+        }
+        {
+            const float yv = fmaf(xp, xp, -cden), t = den + yv;
+            cden = (t - den) - yv;
+            den = t;
+        }
     }
+    double dn = double(num) - double(cnum), dd = double(den) - double(cden);
     for (int o = 16; o > 0; o >>= 1) {
-        num += __shfl_xor_sync(0xffffffffu, num, o);
-        den += __shfl_xor_sync(0xffffffffu, den, o);
+        dn += __shfl_xor_sync(0xffffffffu, dn, o);
+        dd += __shfl_xor_sync(0xffffffffu, dd, o);
     }
-    if ((threadIdx.x & 31) == 0) { s_a[threadIdx.x >> 5] = num; s_b[threadIdx.x >> 5] = den; }
+    if ((threadIdx.x & 31) == 0) { s_a[threadIdx.x >> 5] = dn; s_b[threadIdx.x >> 5] = dd; }
     __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0.0, b = 0.0;

@@ -17,29 +17,38 @@ namespace fhs {
 
 namespace {
 
-constexpr int ATY = 8, ATX = 32;                    // analysis output tile
+constexpr int ATY = 16, ATX = 32;                   // analysis output tile (coefficients)
 constexpr int AIN_Y = 2 * ATY + kMaxF - 2;          // staged input rows
 constexpr int AIN_X = 2 * ATX + kMaxF - 2;          // staged input cols
-constexpr int STY = 16, STX = 32;                   // synthesis output tile
+constexpr int STY = 32, STX = 64;                   // synthesis output tile (samples, even)
 constexpr int SB_Y = (STY + kMaxF - 2) / 2;         // staged band rows
 constexpr int SB_X = (STX + kMaxF - 2) / 2;         // staged band cols
 
-// Filter the staged tile along x then y; write the 4 subbands of basis p at
-// level j (details to coef, LL to `ll_out` with row stride mx).
-__device__ __forceinline__ void analysis_tile(const SaraConst &c, int p, int j, int k0y, int k0x,
-                                              float (*sin_)[AIN_X + 1], float (*slo)[ATX + 1],
-                                              float (*shi)[ATX + 1], float *coef_l, float *ll_out,
-                                              float ll_scale) {
-    const int F = c.F[p];
-    const int my = c.ny[p][j], mx = c.nx[p][j];
-    const float *h = c.h[p];
-    const float *g = c.g[p];
-    for (int idx = threadIdx.x; idx < AIN_Y * ATX; idx += blockDim.x) {
-        const int r = idx / ATX, kx = idx - r * ATX;
+// One analysis level of basis db_P on the staged tile: x-filter then y-filter
+// with compile-time filter length F = 2P, writing the four subbands at level
+// j (details to coef, LL to `ll_out`, row stride mx).  The staged input row r
+// holds image row 2 k0y + 2 - kMaxF + r, so output k uses rows 2k+kMaxF-1-i.
+template <int P>
+__device__ __forceinline__ void analysis_tile_t(const SaraConst &c, int j, int k0y, int k0x,
+                                                float (*sin_)[AIN_X + 1], float (*slo)[ATX + 1],
+                                                float (*shi)[ATX + 1], float *coef_l, float *ll_out,
+                                                float ll_scale) {
+    constexpr int F = 2 * P;
+    constexpr int R0 = kMaxF - F;                    // first staged row this filter reaches
+    float h[F], g[F];
+#pragma unroll
+    for (int i = 0; i < F; ++i) {
+        h[i] = c.h[P][i];
+        g[i] = c.g[P][i];
+    }
+    const int my = c.ny[P][j], mx = c.nx[P][j];
+    for (int idx = threadIdx.x; idx < (AIN_Y - R0) * ATX; idx += blockDim.x) {
+        const int r = R0 + idx / ATX, kx = idx % ATX;
+        const float *src = &sin_[r][2 * kx + R0];      // src[F-1-i] = input 2kx+kMaxF-1-i
         float lo = 0.f, hi = 0.f;
-        const int base = 2 * kx + kMaxF - 1;
+#pragma unroll
         for (int i = 0; i < F; ++i) {
-            const float a = sin_[r][base - i];
+            const float a = src[F - 1 - i];
             lo = fmaf(h[i], a, lo);
             hi = fmaf(g[i], a, hi);
         }
@@ -49,19 +58,20 @@ __device__ __forceinline__ void analysis_tile(const SaraConst &c, int p, int j, 
     __syncthreads();
     const long long bs = (long long)my * mx;
     for (int idx = threadIdx.x; idx < ATY * ATX; idx += blockDim.x) {
-        const int ky = idx / ATX, kx = idx - ky * ATX;
+        const int ky = idx / ATX, kx = idx % ATX;
         const int gy = k0y + ky, gx = k0x + kx;
-        const int base = 2 * ky + kMaxF - 1;
+        const int r1 = 2 * ky + R0;                    // row of tap i = F-1
         float ll = 0.f, lh = 0.f, hl = 0.f, hh = 0.f;
+#pragma unroll
         for (int i = 0; i < F; ++i) {
-            const float lo = slo[base - i][kx], hi = shi[base - i][kx];
+            const float lo = slo[r1 + F - 1 - i][kx], hi = shi[r1 + F - 1 - i][kx];
             ll = fmaf(h[i], lo, ll);
             lh = fmaf(h[i], hi, lh);
             hl = fmaf(g[i], lo, hl);
             hh = fmaf(g[i], hi, hh);
         }
         if (gy < my && gx < mx) {
-            float *d = coef_l + c.off_det[p][j] + (long long)gy * mx + gx;
+            float *d = coef_l + c.off_det[P][j] + (long long)gy * mx + gx;
             d[0] = lh * kSaraScale;
             d[bs] = hl * kSaraScale;
             d[2 * bs] = hh * kSaraScale;
@@ -73,6 +83,15 @@ __device__ __forceinline__ void analysis_tile(const SaraConst &c, int p, int j, 
 
 // Level 1 of every Daubechies basis (and the Dirac basis) from one staged tile
 // of the image: the image is read once for all nine bases.
+template <int P>
+__device__ __forceinline__ void analysis_l1_basis(const SaraConst &c, int l, int k0y, int k0x,
+                                                  float (*sin_)[AIN_X + 1], float (*slo)[ATX + 1],
+                                                  float (*shi)[ATX + 1], float *coef_l, float *tmp) {
+    if (k0y >= c.ny[P][1] || k0x >= c.nx[P][1]) return;
+    float *ll_out = (c.levels == 1) ? coef_l + c.off_ll[P] : tmp + (long long)l * c.n_tmp + c.off_tmp[P][1];
+    analysis_tile_t<P>(c, 1, k0y, k0x, sin_, slo, shi, coef_l, ll_out, c.levels == 1 ? kSaraScale : 1.f);
+}
+
 __global__ void __launch_bounds__(256) analysis_l1_kernel(const __grid_constant__ SaraConst c,
                                                           const float *__restrict__ x, float *__restrict__ coef,
                                                           float *__restrict__ tmp) {
@@ -98,11 +117,14 @@ __global__ void __launch_bounds__(256) analysis_l1_kernel(const __grid_constant_
         const int gy = 2 * k0y + ry, gx = 2 * k0x + rx;
         if (gy < ny && gx < nx) coef_l[(long long)gy * nx + gx] = sin_[ry + kMaxF - 2][rx + kMaxF - 2] * kSaraScale;
     }
-    for (int p = 1; p <= kNumDb; ++p) {
-        if (k0y >= c.ny[p][1] || k0x >= c.nx[p][1]) continue;
-        float *ll_out = (c.levels == 1) ? coef_l + c.off_ll[p] : tmp + (long long)l * c.n_tmp + c.off_tmp[p][1];
-        analysis_tile(c, p, 1, k0y, k0x, sin_, slo, shi, coef_l, ll_out, c.levels == 1 ? kSaraScale : 1.f);
-    }
+    analysis_l1_basis<1>(c, l, k0y, k0x, sin_, slo, shi, coef_l, tmp);
+    analysis_l1_basis<2>(c, l, k0y, k0x, sin_, slo, shi, coef_l, tmp);
+    analysis_l1_basis<3>(c, l, k0y, k0x, sin_, slo, shi, coef_l, tmp);
+    analysis_l1_basis<4>(c, l, k0y, k0x, sin_, slo, shi, coef_l, tmp);
+    analysis_l1_basis<5>(c, l, k0y, k0x, sin_, slo, shi, coef_l, tmp);
+    analysis_l1_basis<6>(c, l, k0y, k0x, sin_, slo, shi, coef_l, tmp);
+    analysis_l1_basis<7>(c, l, k0y, k0x, sin_, slo, shi, coef_l, tmp);
+    analysis_l1_basis<8>(c, l, k0y, k0x, sin_, slo, shi, coef_l, tmp);
 }
 
 // Level j >= 2 of basis p from its level j-1 approximation.
@@ -127,30 +149,47 @@ __global__ void __launch_bounds__(256) analysis_lj_kernel(const __grid_constant_
     __syncthreads();
     const bool last = (j == c.levels);
     float *ll_out = last ? coef_l + c.off_ll[p] : tmp + (long long)l * c.n_tmp + c.off_tmp[p][j];
-    analysis_tile(c, p, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, last ? kSaraScale : 1.f);
+    const float lls = last ? kSaraScale : 1.f;
+    switch (p) {
+        case 1: analysis_tile_t<1>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls); break;
+        case 2: analysis_tile_t<2>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls); break;
+        case 3: analysis_tile_t<3>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls); break;
+        case 4: analysis_tile_t<4>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls); break;
+        case 5: analysis_tile_t<5>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls); break;
+        case 6: analysis_tile_t<6>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls); break;
+        case 7: analysis_tile_t<7>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls); break;
+        default: analysis_tile_t<8>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls); break;
+    }
 }
 
-// Adjoint of one level of basis p: a_{j-1}[m] = sum_k f[2k+1-m] band[k] over the
-// four bands, for an STY x STX tile of a_{j-1} starting at (m0y, m0x).
-// Returns the tile value of this thread's outputs through `acc`.
-__device__ __forceinline__ void synthesis_tile(const SaraConst &c, int p, int j, int m0y, int m0x,
-                                               const float *coef_l, const float *ll_in, float ll_scale,
-                                               float (*sb)[SB_Y][SB_X + 1], float (*su)[SB_Y][STX + 1],
-                                               float *acc) {
-    const int F = c.F[p];
-    const int my = c.ny[p][j], mx = c.nx[p][j];
-    const float *h = c.h[p];
-    const float *g = c.g[p];
+// Adjoint of one level of db_P for an STY x STX tile of a_{j-1} at (m0y, m0x)
+// (both even).  Polyphase: outputs 2q and 2q+1 use the same band samples
+// k0 + q + t, t < F/2, with the odd and the even taps respectively
+// (a[m] = sum_k f[2k+1-m] band[k]).  Adds this thread's outputs to acc[8]:
+// pairs idx = tid + 256 s, s < 4, each giving rows 2qy and 2qy+1 of column rx.
+template <int P>
+__device__ __forceinline__ void synthesis_tile_t(const SaraConst &c, int j, int m0y, int m0x, const float *coef_l,
+                                                 const float *ll_in, float (*sb)[SB_Y][SB_X + 1],
+                                                 float (*su)[SB_Y][STX + 1], float *acc) {
+    constexpr int F = 2 * P, H = P;
+    float h[F], g[F];
+#pragma unroll
+    for (int i = 0; i < F; ++i) {
+        h[i] = c.h[P][i];
+        g[i] = c.g[P][i];
+    }
+    const int my = c.ny[P][j], mx = c.nx[P][j];
     const long long bs = (long long)my * mx;
     const int k0y = m0y / 2, k0x = m0x / 2;
-    const float *det = coef_l + c.off_det[p][j];
-    for (int idx = threadIdx.x; idx < SB_Y * SB_X; idx += blockDim.x) {
-        const int r = idx / SB_X, cc = idx - r * SB_X;
+    constexpr int NBY = STY / 2 + H - 1, NBX = STX / 2 + H - 1;   // band samples reached
+    const float *det = coef_l + c.off_det[P][j];
+    for (int idx = threadIdx.x; idx < NBY * NBX; idx += blockDim.x) {
+        const int r = idx / NBX, cc = idx - r * NBX;
         const int ky = k0y + r, kx = k0x + cc;
         float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
         if (ky < my && kx < mx) {
             const long long o = (long long)ky * mx + kx;
-            v0 = ll_in[o] * ll_scale;
+            v0 = ll_in[o];
             v1 = det[o];
             v2 = det[bs + o];
             v3 = det[2 * bs + o];
@@ -162,29 +201,61 @@ __device__ __forceinline__ void synthesis_tile(const SaraConst &c, int p, int j,
     }
     __syncthreads();
     // x: u_lo = synth(LL, h) + synth(LH, g); u_hi = synth(HL, h) + synth(HH, g)
-    for (int idx = threadIdx.x; idx < SB_Y * STX; idx += blockDim.x) {
-        const int r = idx / STX, rx = idx - r * STX;
-        float ulo = 0.f, uhi = 0.f;
-        for (int i = (rx + 1) & 1; i < F; i += 2) {
-            const int kl = (rx - 1 + i) >> 1;
-            ulo = fmaf(h[i], sb[0][r][kl], fmaf(g[i], sb[1][r][kl], ulo));
-            uhi = fmaf(h[i], sb[2][r][kl], fmaf(g[i], sb[3][r][kl], uhi));
+    for (int idx = threadIdx.x; idx < NBY * (STX / 2); idx += blockDim.x) {
+        const int r = idx / (STX / 2), q = idx % (STX / 2);
+        float le = 0.f, lo = 0.f, he = 0.f, ho = 0.f;
+#pragma unroll
+        for (int t = 0; t < H; ++t) {
+            const float a0 = sb[0][r][q + t], a1 = sb[1][r][q + t], a2 = sb[2][r][q + t], a3 = sb[3][r][q + t];
+            le = fmaf(h[2 * t + 1], a0, fmaf(g[2 * t + 1], a1, le));
+            lo = fmaf(h[2 * t], a0, fmaf(g[2 * t], a1, lo));
+            he = fmaf(h[2 * t + 1], a2, fmaf(g[2 * t + 1], a3, he));
+            ho = fmaf(h[2 * t], a2, fmaf(g[2 * t], a3, ho));
         }
-        su[0][r][rx] = ulo;
-        su[1][r][rx] = uhi;
+        su[0][r][2 * q] = le;
+        su[0][r][2 * q + 1] = lo;
+        su[1][r][2 * q] = he;
+        su[1][r][2 * q + 1] = ho;
     }
     __syncthreads();
-    int t = 0;
-    for (int idx = threadIdx.x; idx < STY * STX; idx += blockDim.x, ++t) {
-        const int ry = idx / STX, rx = idx - ry * STX;
-        float a = 0.f;
-        for (int i = (ry + 1) & 1; i < F; i += 2) {
-            const int kl = (ry - 1 + i) >> 1;
-            a = fmaf(h[i], su[0][kl][rx], fmaf(g[i], su[1][kl][rx], a));
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const int idx = threadIdx.x + 256 * s;
+        const int qy = idx / STX, rx = idx % STX;
+        float e = 0.f, o = 0.f;
+#pragma unroll
+        for (int t = 0; t < H; ++t) {
+            const float ul = su[0][qy + t][rx], uh = su[1][qy + t][rx];
+            e = fmaf(h[2 * t + 1], ul, fmaf(g[2 * t + 1], uh, e));
+            o = fmaf(h[2 * t], ul, fmaf(g[2 * t], uh, o));
         }
-        acc[t] += a;
+        acc[2 * s] += e;
+        acc[2 * s + 1] += o;
     }
     __syncthreads();
+}
+
+__device__ __forceinline__ void synthesis_tile(const SaraConst &c, int p, int j, int m0y, int m0x,
+                                               const float *coef_l, const float *ll_in,
+                                               float (*sb)[SB_Y][SB_X + 1], float (*su)[SB_Y][STX + 1],
+                                               float *acc) {
+    switch (p) {
+        case 1: synthesis_tile_t<1>(c, j, m0y, m0x, coef_l, ll_in, sb, su, acc); break;
+        case 2: synthesis_tile_t<2>(c, j, m0y, m0x, coef_l, ll_in, sb, su, acc); break;
+        case 3: synthesis_tile_t<3>(c, j, m0y, m0x, coef_l, ll_in, sb, su, acc); break;
+        case 4: synthesis_tile_t<4>(c, j, m0y, m0x, coef_l, ll_in, sb, su, acc); break;
+        case 5: synthesis_tile_t<5>(c, j, m0y, m0x, coef_l, ll_in, sb, su, acc); break;
+        case 6: synthesis_tile_t<6>(c, j, m0y, m0x, coef_l, ll_in, sb, su, acc); break;
+        case 7: synthesis_tile_t<7>(c, j, m0y, m0x, coef_l, ll_in, sb, su, acc); break;
+        default: synthesis_tile_t<8>(c, j, m0y, m0x, coef_l, ll_in, sb, su, acc); break;
+    }
+}
+
+// Output sample of pair slot s of this thread: (row, col) offsets in the tile.
+__device__ __forceinline__ void synth_slot(int s, int &ry, int &rx) {
+    const int idx = threadIdx.x + 256 * (s >> 1);
+    ry = 2 * (idx / STX) + (s & 1);
+    rx = idx % STX;
 }
 
 // Levels j >= 2: reconstruct a_{j-1} of basis p into tmp.
@@ -200,14 +271,15 @@ __global__ void __launch_bounds__(256) synthesis_lj_kernel(const __grid_constant
     const float *coef_l = coef + (long long)l * c.n_coef;
     const bool last = (j == c.levels);
     const float *ll_in = last ? coef_l + c.off_ll[p] : tmp + (long long)l * c.n_tmp + c.off_tmp[p][j];
-    float acc[STY * STX / 256] = {0.f, 0.f};
-    synthesis_tile(c, p, j, m0y, m0x, coef_l, ll_in, 1.f, sb, su, acc);
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    synthesis_tile(c, p, j, m0y, m0x, coef_l, ll_in, sb, su, acc);
     float *out = tmp + (long long)l * c.n_tmp + c.off_tmp[p][j - 1];
-    int t = 0;
-    for (int idx = threadIdx.x; idx < STY * STX; idx += blockDim.x, ++t) {
-        const int ry = idx / STX, rx = idx - ry * STX;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        int ry, rx;
+        synth_slot(s, ry, rx);
         const int gy = m0y + ry, gx = m0x + rx;
-        if (gy < oy && gx < ox) out[(long long)gy * ox + gx] = acc[t];
+        if (gy < oy && gx < ox) out[(long long)gy * ox + gx] = acc[s];
     }
 }
 
@@ -221,18 +293,28 @@ __global__ void __launch_bounds__(256) synthesis_l1_kernel(const __grid_constant
     const int m0y = blockIdx.y * STY, m0x = blockIdx.x * STX;
     const int ny = c.img_ny, nx = c.img_nx;
     const float *coef_l = coef + (long long)l * c.n_coef;
-    float acc[STY * STX / 256] = {0.f, 0.f};
-    for (int p = 1; p <= kNumDb; ++p) {
-        const float *ll_in = (c.levels == 1) ? coef_l + c.off_ll[p] : tmp + (long long)l * c.n_tmp + c.off_tmp[p][1];
-        synthesis_tile(c, p, 1, m0y, m0x, coef_l, ll_in, 1.f, sb, su, acc);
-    }
-    int t = 0;
-    for (int idx = threadIdx.x; idx < STY * STX; idx += blockDim.x, ++t) {
-        const int ry = idx / STX, rx = idx - ry * STX;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#define FHS_SYN_L1(P)                                                                                      \
+    synthesis_tile_t<P>(c, 1, m0y, m0x, coef_l,                                                           \
+                        (c.levels == 1) ? coef_l + c.off_ll[P] : tmp + (long long)l * c.n_tmp + c.off_tmp[P][1], \
+                        sb, su, acc)
+    FHS_SYN_L1(1);
+    FHS_SYN_L1(2);
+    FHS_SYN_L1(3);
+    FHS_SYN_L1(4);
+    FHS_SYN_L1(5);
+    FHS_SYN_L1(6);
+    FHS_SYN_L1(7);
+    FHS_SYN_L1(8);
+#undef FHS_SYN_L1
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        int ry, rx;
+        synth_slot(s, ry, rx);
         const int gy = m0y + ry, gx = m0x + rx;
         if (gy < ny && gx < nx) {
             const long long o = (long long)gy * nx + gx;
-            x[(long long)l * ny * nx + o] = (acc[t] + coef_l[o]) * kSaraScale;
+            x[(long long)l * ny * nx + o] = (acc[s] + coef_l[o]) * kSaraScale;
         }
     }
 }
