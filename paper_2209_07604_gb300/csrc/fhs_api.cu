@@ -434,7 +434,10 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
     // ---- tile bins for the single-pass data kernel: runs of one tile key of at
     // least kDenseMin visibilities become shared-memory bins (split at kBinMax);
     // shorter runs are packed into sparse bins that take the global path.
-    constexpr long long kDenseMin = 48, kBinMax = 384, kSparseMax = 384;   // kBinMax: smem capacity of a bin
+    #ifndef FHS_BIN_MAX
+#define FHS_BIN_MAX 384
+#endif
+    constexpr long long kDenseMin = 48, kBinMax = FHS_BIN_MAX, kSparseMax = FHS_BIN_MAX;   // smem capacity of a bin
     std::vector<long long> bstart;
     std::vector<int> bseg, btile;
     p->ntx = ntx;

@@ -242,7 +242,10 @@ __global__ void __launch_bounds__(256) degrid_grid_fused_kernel(
 // instead of one per G entry).  Bins marked -1 (sparse tiles) take the
 // global path.
 constexpr int kWin = kTile + 15;        // boxes have T <= 16
-constexpr int kBinMax = 384;            // visibilities per bin (host splits longer runs)
+#ifndef FHS_BIN_MAX
+#define FHS_BIN_MAX 384
+#endif
+constexpr int kBinMax = FHS_BIN_MAX;    // visibilities per bin (host splits longer runs)
 
 struct RowRegs {
     float2 g[8];
@@ -342,7 +345,12 @@ __device__ __forceinline__ void bin_rows(int i0, int nv, int lane, const int2 *s
     }
 }
 
-__global__ void __launch_bounds__(256) degrid_grid_binned_kernel(
+// Four CTAs per SM (64 registers, 46 KB shared each): the kernel is latency
+// bound, and occupancy matters more than the registers the cap takes away.
+#ifndef FHS_FUSED_MIN_BLOCKS
+#define FHS_FUSED_MIN_BLOCKS 4
+#endif
+__global__ void __launch_bounds__(256, FHS_FUSED_MIN_BLOCKS) degrid_grid_binned_kernel(
     const int2 *__restrict__ meta, const long long *__restrict__ rowptr, const float2 *__restrict__ gval,
     const float2 *__restrict__ y, float2 *__restrict__ dvis, const long long *__restrict__ bin_start,
     const int *__restrict__ bin_seg, const int *__restrict__ bin_tile, int ntx, int B,
