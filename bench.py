@@ -183,6 +183,28 @@ def run_gpu(args):
         torch.distributed.barrier()
     ms_step = ms / args.steps
 
+    # Phi and Phi^H alone through the C ABI (fhs_measure / fhs_adjoint), device buffers
+    xs = torch.rand((L, P.ny, P.nx), device="cuda", dtype=torch.float32)
+    vis = torch.empty(Mtot, dtype=torch.complex64, device="cuda")
+    img = torch.empty((L, P.ny, P.nx), dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        fhs.fhs_measure(prob.handle, xs, vis)
+        fhs.fhs_adjoint(prob.handle, vis, img)
+    n_op = 10
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    for _ in range(n_op):
+        fhs.fhs_measure(prob.handle, xs, vis)
+    e[1].record(stream)
+    for _ in range(n_op):
+        fhs.fhs_adjoint(prob.handle, vis, img)
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    phi_ms = e[0].elapsed_time(e[1]) / n_op
+    phit_ms = e[1].elapsed_time(e[2]) / n_op
+    del xs, vis, img
+
     # roofline of the dominant kernel (single pass over G)
     K = 4 * P.ny * P.nx
     peak, peak_kind = _peaks()
@@ -190,7 +212,7 @@ def run_gpu(args):
     k_ms = phases["degrid_grid"] / max(n_prof, 1)
     achieved = kbytes / (k_ms * 1e-3) / 1e9
     traffic = _profile_traffic("k_nufft.cu")
-    # visibilities through Phi and Phi^H per second inside the iteration
+    # visibilities through Phi and Phi^H per second inside the PDFB iteration
     vis_s = Mtot / (ms_step * 1e-3)
     out = {
         "metric": METRIC,
@@ -211,6 +233,8 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (G alone %.1f GB per iteration)" % (info.nnz * 8 / 1e9),
                    "mu": MU, "mu_bar": MU_BAR},
         "vis_per_s": ws * vis_s,
+        "phi_vis_per_s": ws * Mtot / (phi_ms * 1e-3),
+        "phi_adjoint_vis_per_s": ws * Mtot / (phit_ms * 1e-3),
         "e2e": {"value": ws * e2e_iters / e2e_s, "unit": "iter/s", "h2d_bytes_per_step": h2d / e2e_iters,
                 "d2h_bytes_per_step": d2h / e2e_iters,
                 "what": "create from host arrays (sort, G build, power iteration) + %d iterations with one "
@@ -335,8 +359,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="fhs", choices=["fhs", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--e2e-iters", type=int, default=200)
