@@ -16,7 +16,11 @@ namespace {
 
 constexpr int kPix = 2048;          // facet pixels per CTA in the Gram / apply kernels
 
-template <int MAXLC>
+// AccT = float in the iteration (FP32 products, FP64 across threads: small
+// singular values are not needed accurately there, they pass the SVT
+// unchanged); AccT = double for the reweighting Gram of x, whose weights
+// upsilon_bar / (upsilon_bar + s_i) need the small singular values too.
+template <int MAXLC, typename AccT>
 __global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ P, const float *__restrict__ img,
                                                    const int4 *__restrict__ facets, const long long *__restrict__ nuc_off,
                                                    int Q, int C, int Lc, int nx, long long N, float s, bool with_dual,
@@ -32,16 +36,16 @@ __global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ P, 
     if (p0 >= npix) return;
     const long long p1 = min(npix, p0 + kPix);
     const float *Pq = P + nuc_off[cq];
-    float acc[NP];
+    AccT acc[NP];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) acc[k] = 0.f;
+    for (int k = 0; k < NP; ++k) acc[k] = AccT(0);
     for (long long pp = p0 + threadIdx.x; pp < p1; pp += blockDim.x) {
         const int py = int(pp / wx), px = int(pp - (long long)py * wx);
         const long long o = (long long)(f.x + py) * nx + (f.z + px);
-        float z[MAXLC];
+        AccT z[MAXLC];
 #pragma unroll
         for (int j = 0; j < MAXLC; ++j) {
-            z[j] = 0.f;
+            z[j] = AccT(0);
             if (j < Lc) {
                 const float xv = img[(long long)(c + j * C) * N + o];
                 z[j] = with_dual ? fmaf(s, xv, Pq[(long long)j * npix + pp]) : xv;
@@ -51,15 +55,15 @@ __global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ P, 
 #pragma unroll
         for (int i = 0; i < MAXLC; ++i)
 #pragma unroll
-            for (int j = i; j < MAXLC; ++j, ++k) acc[k] = fmaf(z[i], z[j], acc[k]);
+            for (int j = i; j < MAXLC; ++j, ++k) acc[k] = fma(z[i], z[j], acc[k]);
     }
     for (int k = threadIdx.x; k < NP; k += blockDim.x) s_red[k] = 0.0;
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-        float v = acc[k];
+        double v = double(acc[k]);
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) atomicAdd(&s_red[k], double(v));
+        if ((threadIdx.x & 31) == 0) atomicAdd(&s_red[k], v);
     }
     __syncthreads();
     int k = 0;
@@ -234,23 +238,27 @@ __global__ void __launch_bounds__(256) apply_kernel(float *__restrict__ P, const
 
 }  // namespace
 
-cudaError_t launch_nuclear_gram(fhs_problem *p, const float *img, bool with_dual, cudaStream_t s) {
+template <typename AccT>
+static cudaError_t gram_dispatch(fhs_problem *p, const float *img, bool with_dual, cudaStream_t s) {
     long long maxpix = 0;
     for (const Facet &f : p->facets) maxpix = std::max<long long>(maxpix, (long long)(f.y1 - f.y0) * (f.x1 - f.x0));
     dim3 g(int((maxpix + kPix - 1) / kPix), p->C * p->Q);
     const float s0 = with_dual ? float(p->sigma0) : 1.f;
-    if (p->Lc <= 2)
-        gram_kernel<2><<<g, 256, 0, s>>>(p->P, img, p->d_facets, p->nuc_off, p->Q, p->C, p->Lc, p->nx, p->N, s0, with_dual, p->gram);
-    else if (p->Lc <= 4)
-        gram_kernel<4><<<g, 256, 0, s>>>(p->P, img, p->d_facets, p->nuc_off, p->Q, p->C, p->Lc, p->nx, p->N, s0, with_dual, p->gram);
-    else if (p->Lc <= 8)
-        gram_kernel<8><<<g, 256, 0, s>>>(p->P, img, p->d_facets, p->nuc_off, p->Q, p->C, p->Lc, p->nx, p->N, s0, with_dual, p->gram);
-    else if (p->Lc <= 16)
-        gram_kernel<16><<<g, 256, 0, s>>>(p->P, img, p->d_facets, p->nuc_off, p->Q, p->C, p->Lc, p->nx, p->N, s0, with_dual, p->gram);
-    else
-        return cudaErrorInvalidValue;
+#define FHS_GRAM(M) gram_kernel<M, AccT><<<g, 256, 0, s>>>(p->P, img, p->d_facets, p->nuc_off, p->Q, p->C, p->Lc, \
+                                                           p->nx, p->N, s0, with_dual, p->gram)
+    if (p->Lc <= 2) FHS_GRAM(2);
+    else if (p->Lc <= 4) FHS_GRAM(4);
+    else if (p->Lc <= 8) FHS_GRAM(8);
+    else if (p->Lc <= 16) FHS_GRAM(16);
+    else return cudaErrorInvalidValue;
+#undef FHS_GRAM
     p->n_launch += 1;
     return cudaGetLastError();
+}
+
+cudaError_t launch_nuclear_gram(fhs_problem *p, const float *img, bool with_dual, cudaStream_t s) {
+    // the dual step's Gram in FP32 products; the reweighting Gram of x in FP64
+    return with_dual ? gram_dispatch<float>(p, img, true, s) : gram_dispatch<double>(p, img, false, s);
 }
 
 cudaError_t launch_nuclear_eig(fhs_problem *p, bool reweight, cudaStream_t s) {

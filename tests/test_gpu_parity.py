@@ -247,3 +247,48 @@ def test_empty_block_and_uneven_channels():
     ref.run(6)
     assert rel(X, ref.X) < TOL_IMG
     prob.close()
+
+
+@pytest.mark.parametrize("name,over,n_iter,mu,mu_bar", [
+    ("small_128", {}, 20, 0.0, 0.0),                          # data fidelity only
+    ("tiny", dict(qy=1, qx=1, overlap=0.0), 8, 0.02, 0.3),     # (C, Q) = (1, 1): HyperSARA
+    ("tiny", dict(L=2, C=2), 8, 0.02, 0.3),                    # one channel per sub-cube
+    ("tiny", dict(L=3, C=1, B=1), 8, 0.02, 0.3),               # odd L_c, one block
+])
+def test_pdfb_degenerate_cases(name, over, n_iter, mu, mu_bar):
+    P, prob, ref = _run_pair(name, n_iter, 0, mu, mu_bar, **over)
+    assert rel(prob.image().cpu().numpy(), ref.X) < TOL_IMG
+    v = prob.get_state(fhs.STATE_DUAL_DATA).cpu().numpy().view(np.complex64).reshape(P.L, -1)
+    assert rel(v, np.stack(ref.v)) < TOL_IMG
+    prob.close()
+
+
+def test_empty_channel():
+    """A channel without visibilities: its data term is zero (Phi_l has no
+    rows, eps = 0); the priors still couple it to the other channel."""
+    import scipy.sparse as sp
+    P = synth.make_problem("tiny", L=2, C=1)
+    M = P.M
+    omega = P.omega[0]
+    w = P.w[0]
+    y = P.y[0]
+    vo = np.array([0, M, M], dtype=np.int64)
+    bo = np.array([[0, M // 2, M], [0, 0, 0]], dtype=np.int64)
+    params = fhs.default_params(ny=P.ny, nx=P.nx, n_channels=2, n_subcubes=1, n_blocks=2, qy=P.qy, qx=P.qx,
+                                facet_overlap=P.overlap, mu=0.02, mu_bar=0.3, sigma2=1e-3)
+    prob = fhs.Problem(params, omega, w, y, P.sigma, vo, bo)
+    prob.step(6)
+    X = prob.image().cpu().numpy()
+    from oracle import prox as oprox
+    ref = opdfb.FHS(P.omega, P.w, P.y, P.sigma, P.block_offsets, P.ny, P.nx, 1, P.qy, P.qx, P.overlap,
+                    mu=0.02, mu_bar=0.3, steps=_steps_from(prob, 1e-3))
+    geom = onf.Geometry(P.ny, P.nx)
+    ref.op.G[1] = sp.csr_matrix((0, geom.K1 * geom.K2), dtype=np.complex128)
+    ref.yw[1] = np.zeros(0, dtype=np.complex128)
+    ref.v[1] = np.zeros(0, dtype=np.complex128)
+    ref.bo = np.array([[0, M // 2, M], [0, 0, 0]])
+    ref.eps = np.stack([oprox.eps_blocks(M, [M // 2, M - M // 2]), np.zeros(2)])
+    ref.run(6)
+    assert rel(X, ref.X) < TOL_IMG
+    assert np.abs(X[1]).max() > 0          # the priors propagate into the empty channel
+    prob.close()
