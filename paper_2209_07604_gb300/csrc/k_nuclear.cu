@@ -61,9 +61,9 @@ __global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ P, 
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-        double v = double(acc[k]);
+        AccT v = acc[k];            // warp sum in the accumulation type, FP64 across warps
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) atomicAdd(&s_red[k], v);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&s_red[k], double(v));
     }
     __syncthreads();
     int k = 0;
