@@ -176,19 +176,24 @@ def run_gpu(args):
     if ws > 1:
         torch.distributed.barrier()
     launches0 = fhs.fhs_kernel_launches(prob.handle)
-    fhs.fhs_profile_enable(prob.handle, True)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         ev0.record(stream)
-        prob.step(args.steps)
+        prob.step(args.steps)            # production path: one CUDA graph per iteration
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
+    launches = fhs.fhs_kernel_launches(prob.handle) - launches0
+    # per-phase device time: the same number of iterations right after, with
+    # event pairs recorded on this stream around every phase (launched kernel
+    # by kernel, since tracing and graph replay exclude each other)
+    fhs.fhs_profile_enable(prob.handle, True)
+    prob.step(args.steps)
+    torch.cuda.synchronize()
     fhs.fhs_profile_enable(prob.handle, False)
     phases, n_prof = fhs.fhs_profile_read(prob.handle)
-    launches = fhs.fhs_kernel_launches(prob.handle) - launches0
     if ws > 1:
         ms = max_over_ranks(ms)
         torch.distributed.barrier()

@@ -168,6 +168,27 @@ fhs_status fhs_sara_synthesis(fhs_problem *prob, const float *coef_dev, float *x
  * iteration; when non-NULL the call synchronises `stream`.            */
 fhs_status fhs_pdfb_step(fhs_problem *prob, int32_t n_iter, double *rel_change_out, void *stream);
 
+/* n_iter PDFB iterations of each of n_prob problems, problem k on
+ * streams[k] (streams may be NULL: legacy default stream).  Iterations are
+ * submitted round-robin, one per problem at a time, so independent problems
+ * (spectral sub-cubes or separate requests, Eq. 3) overlap on the device.
+ * rel_change_out (host, [n_prob], may be NULL) as in fhs_pdfb_step; when
+ * non-NULL the call synchronises every stream.                           */
+fhs_status fhs_pdfb_step_batch(fhs_problem **probs, int32_t n_prob, int32_t n_iter, void **streams,
+                               double *rel_change_out);
+
+/* Replay one PDFB iteration as a CUDA graph (captured on first use for each
+ * stream; on by default; never on the legacy default stream or while
+ * tracing).  on = 0 launches kernel by kernel. */
+fhs_status fhs_use_graphs(fhs_problem *prob, int32_t on);
+
+/* Device bytes a problem with these parameters and n_vis visibilities with
+ * coordinates w (host [n_vis], or NULL for no w-term) will hold after
+ * fhs_create_problem (resident_out) and at most during it (peak_out), for
+ * admission by HBM footprint.  Host only; either output may be NULL.     */
+fhs_status fhs_estimate_bytes(const fhs_params *params, const double *w, int64_t n_vis, int64_t *resident_out,
+                              int64_t *peak_out);
+
 /* Log-sum reweighting (Sec. 2.2.3): w_r = upsilon/(upsilon + ||(Psi^dagger X)_r||),
  * w_{q,i} = upsilon_bar/(upsilon_bar + sigma_i(S_q X)); duals are kept. Async. */
 fhs_status fhs_reweight(fhs_problem *prob, void *stream);

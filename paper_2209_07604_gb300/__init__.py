@@ -23,7 +23,7 @@ EXPORTED = [
     "fhs_adjoint", "fhs_sara_analysis", "fhs_sara_synthesis", "fhs_pdfb_step", "fhs_reweight", "fhs_solve",
     "fhs_state_size", "fhs_get_state", "fhs_set_state", "fhs_operator_norms", "fhs_daubechies_filter",
     "fhs_last_error", "fhs_profile_enable", "fhs_profile_read", "fhs_kernel_launches",
-    "fhs_sara_analysis_noalloc",
+    "fhs_sara_analysis_noalloc", "fhs_pdfb_step_batch", "fhs_use_graphs", "fhs_estimate_bytes",
 ]
 PHASES = ["primal", "fft_fwd", "degrid_grid", "l2ball", "fft_inv", "sara", "nuclear"]
 
@@ -88,6 +88,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fhs_profile_read": (C.c_int, [vp, vp, P(i64)]),
         "fhs_kernel_launches": (C.c_int, [vp, P(i64)]),
         "fhs_sara_analysis_noalloc": (C.c_int, [i32, i32, i32, i32, vp, vp, vp]),
+        "fhs_pdfb_step_batch": (C.c_int, [vp, i32, i32, vp, vp]),
+        "fhs_use_graphs": (C.c_int, [vp, i32]),
+        "fhs_estimate_bytes": (C.c_int, [P(fhs_params), vp, i64, P(i64), P(i64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -233,6 +236,30 @@ def fhs_daubechies_filter(p: int) -> np.ndarray:
     out = np.zeros(2 * p, dtype=np.float64)
     _check(load_library().fhs_daubechies_filter(int(p), _ptr(out)))
     return out
+
+
+def fhs_pdfb_step_batch(probs, n_iter=1, streams=None, want_rel=False):
+    """n_iter iterations of several problems, problem k on streams[k] (ints or torch streams)."""
+    n = len(probs)
+    arr = (C.c_void_p * n)(*[p.value if isinstance(p, C.c_void_p) else p for p in probs])
+    sarr = None
+    if streams is not None:
+        sarr = (C.c_void_p * n)(*[int(getattr(st, "cuda_stream", st)) for st in streams])
+    rel = np.zeros(n, dtype=np.float64)
+    _check(load_library().fhs_pdfb_step_batch(arr, n, int(n_iter), sarr, _ptr(rel) if want_rel else None))
+    return rel if want_rel else None
+
+
+def fhs_use_graphs(prob, on: bool):
+    _check(load_library().fhs_use_graphs(prob, 1 if on else 0))
+
+
+def fhs_estimate_bytes(params: fhs_params, w, n_vis: int):
+    """(resident, peak) device bytes of a problem before creating it."""
+    w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+    r, pk = C.c_int64(0), C.c_int64(0)
+    _check(load_library().fhs_estimate_bytes(C.byref(params), _ptr(w), int(n_vis), C.byref(r), C.byref(pk)))
+    return r.value, pk.value
 
 
 def fhs_profile_enable(prob, on: bool):

@@ -176,6 +176,34 @@ fhs_status power_iteration(fhs_problem *p, int n_iter, double tol, std::vector<d
     return FHS_OK;
 }
 
+// Side T = J + 2h of the G box of a visibility with coordinate w (w-plane rule).
+int row_side(double wv, const fhs_params &q) {
+    if (!(q.w_max > 0.0)) return q.kb_taps;
+    const int P1 = q.n_wplanes - 1;
+    const double dw = q.w_max / P1;
+    long long pa = (long long)std::floor(std::fabs(wv) / dw + 0.5);
+    if (pa > P1) pa = P1;
+    return q.kb_taps + 2 * int((8 * pa + P1) / (2 * P1));
+}
+
+// Facets of the low-rankness prior: tiles at floor(i n / Q), extended on the
+// low side by ceil(overlap * tile) and clipped at 0, row-major.
+std::vector<Facet> facet_list(const fhs_params &q) {
+    auto axis = [&](int n, int Qd) {
+        std::vector<std::pair<int, int>> r;
+        for (int i = 0; i < Qd; ++i) {
+            const int b0 = int((long long)i * n / Qd), b1 = int((long long)(i + 1) * n / Qd);
+            const int ext = int(std::ceil(q.facet_overlap * double(b1 - b0)));
+            r.push_back({std::max(0, b0 - ext), b1});
+        }
+        return r;
+    };
+    std::vector<Facet> f;
+    for (auto &a : axis(q.ny, q.qy))
+        for (auto &b : axis(q.nx, q.qx)) f.push_back({a.first, a.second, b.first, b.second});
+    return f;
+}
+
 bool sara_active(const fhs_problem *p) { return p->prm.mu > 0.0; }
 bool nuc_active(const fhs_problem *p) { return p->prm.mu_bar > 0.0; }
 
@@ -249,6 +277,61 @@ fhs_status one_iteration(fhs_problem *p, cudaStream_t s) {
     if (p->prof_on) p->prof_iters++;
     p->iteration++;
     return FHS_OK;
+}
+
+// n iterations on stream s: replays a CUDA graph of one iteration (captured
+// once per stream) when graphs are enabled, the stream is not the legacy
+// default stream and tracing is off; otherwise launches kernel by kernel.
+// A capture that fails (a library call that cannot be captured) turns graphs
+// off for the problem and falls back to plain launches.
+fhs_status run_iterations(fhs_problem *p, int n, cudaStream_t s) {
+    const bool can = p->use_graphs && !p->prof_on && s != nullptr && n > 0;
+    if (can && (!p->gexec || p->gstream != s)) {
+        if (p->gexec) {
+            cudaGraphExecDestroy(p->gexec);
+            p->gexec = nullptr;
+        }
+        const long long l0 = p->n_launch;
+        const int it0 = p->iteration;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        fhs_status st = FHS_ERR_CUDA;
+        if (e == cudaSuccess) {
+            st = one_iteration(p, s);
+            e = cudaStreamEndCapture(s, &g);
+        }
+        p->iteration = it0;
+        const long long per = p->n_launch - l0;
+        p->n_launch = l0;
+        if (st == FHS_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&p->gexec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (st != FHS_OK || e != cudaSuccess || !p->gexec) {
+            cudaGetLastError();
+            p->gexec = nullptr;
+            p->use_graphs = false;
+        } else {
+            p->gstream = s;
+            p->g_launches = per;
+        }
+    }
+    if (can && p->gexec) {
+        for (int it = 0; it < n; ++it) {
+            CU(cudaGraphLaunch(p->gexec, s));
+            p->iteration++;
+            p->n_launch += p->g_launches;
+        }
+        return FHS_OK;
+    }
+    for (int it = 0; it < n; ++it) TRY(one_iteration(p, s));
+    return FHS_OK;
+}
+
+size_t cufft_workspace(int K1, int K2, int L) {
+    int n[2] = {K1, K2};
+    size_t ws = 0;
+    if (cufftEstimateMany(2, n, nullptr, 1, K1 * K2, nullptr, 1, K1 * K2, CUFFT_C2C, L, &ws) != CUFFT_SUCCESS)
+        return 0;
+    return ws;
 }
 
 }  // namespace
@@ -549,6 +632,8 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
         if (cufftPlanMany(&p->plan, 2, n, nullptr, 1, int(p->K), nullptr, 1, int(p->K), CUFFT_C2C, L) != CUFFT_SUCCESS)
             return guard(fail(FHS_ERR_CUDA, "cufftPlanMany failed"));
         p->plan_ok = true;
+        size_t ws = 0;
+        if (cufftGetSize(p->plan, &ws) == CUFFT_SUCCESS) p->bytes += ws;
     }
     if ((st = guard(dev_alloc(p, &p->grid_in, p->K * L))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->grid_work, p->K * L))) != FHS_OK) return st;
@@ -564,41 +649,8 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
 
     // ---- SARA layout
     {
-        SaraConst &c = p->sara;
-        std::memset(&c, 0, sizeof c);
-        c.levels = q.wavelet_levels;
-        c.img_ny = q.ny;
-        c.img_nx = q.nx;
-        long long pos = p->N, tpos = 0;
-        for (int b = 1; b <= kNumDb; ++b) {
-            const std::vector<double> h = daubechies(b);
-            const int F = 2 * b;
-            c.F[b] = F;
-            for (int k = 0; k < F; ++k) {
-                c.h[b][k] = float(h[k]);
-                c.g[b][k] = float((k & 1) ? -h[F - 1 - k] : h[F - 1 - k]);
-            }
-            c.ny[b][0] = q.ny;
-            c.nx[b][0] = q.nx;
-            for (int j = 1; j <= c.levels; ++j) {
-                c.ny[b][j] = (c.ny[b][j - 1] + F - 1) / 2;
-                c.nx[b][j] = (c.nx[b][j - 1] + F - 1) / 2;
-            }
-        }
-        for (int b = 1; b <= kNumDb; ++b) {
-            for (int j = 1; j <= c.levels; ++j) {
-                c.off_det[b][j] = pos;
-                pos += 3LL * c.ny[b][j] * c.nx[b][j];
-            }
-            c.off_ll[b] = pos;
-            pos += (long long)c.ny[b][c.levels] * c.nx[b][c.levels];
-            for (int j = 1; j < c.levels; ++j) {
-                c.off_tmp[b][j] = tpos;
-                tpos += (long long)c.ny[b][j] * c.nx[b][j];
-            }
-        }
-        c.n_coef = pos;
-        c.n_tmp = std::max(tpos, 1LL);
+        p->sara = sara_layout(q.ny, q.nx, q.wavelet_levels);
+        const SaraConst &c = p->sara;
         if ((st = guard(dev_alloc(p, &p->W, c.n_coef * L))) != FHS_OK) return st;
         if ((st = guard(dev_alloc(p, &p->coef_tmp, c.n_coef * L))) != FHS_OK) return st;
         if ((st = guard(dev_alloc(p, &p->sara_tmp, c.n_tmp * L))) != FHS_OK) return st;
@@ -620,12 +672,9 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
         };
         const auto ay = axis(q.ny, q.qy), ax = axis(q.nx, q.qx);
         p->Q = q.qy * q.qx;
+        p->facets = facet_list(q);
         std::vector<int4> fz;
-        for (auto &a : ay)
-            for (auto &b : ax) {
-                p->facets.push_back({a.first, a.second, b.first, b.second});
-                fz.push_back(make_int4(a.first, a.second, b.first, b.second));
-            }
+        for (const Facet &f : p->facets) fz.push_back(make_int4(f.y0, f.y1, f.x0, f.x1));
         auto cover = [&](const std::vector<std::pair<int, int>> &ff, int n, std::vector<short> &first,
                          std::vector<short> &cnt) {
             first.assign(n, 0);
@@ -711,8 +760,75 @@ void fhs_destroy_problem(fhs_problem *p) {
     cudaDeviceSynchronize();
     for (auto &u : p->ev_used) { cudaEventDestroy(u.second.first); cudaEventDestroy(u.second.second); }
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
     free_all(p);
     delete p;
+}
+
+fhs_status fhs_use_graphs(fhs_problem *p, int32_t on) {
+    if (!p) return fail(FHS_ERR_ARG, "NULL problem");
+    p->use_graphs = on != 0;
+    if (!p->use_graphs && p->gexec) {
+        cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
+    }
+    return FHS_OK;
+}
+
+fhs_status fhs_pdfb_step_batch(fhs_problem **probs, int32_t n_prob, int32_t n_iter, void **streams,
+                               double *rel_change_out) {
+    if (!probs || n_prob < 0 || n_iter < 0) return fail(FHS_ERR_ARG, "bad argument");
+    for (int k = 0; k < n_prob; ++k)
+        if (!probs[k]) return fail(FHS_ERR_ARG, "probs[%d] is NULL", k);
+    // one iteration of every problem in turn, so that their work overlaps on the device
+    for (int it = 0; it < n_iter; ++it)
+        for (int k = 0; k < n_prob; ++k) TRY(run_iterations(probs[k], 1, streams ? S(streams[k]) : nullptr));
+    if (rel_change_out) {
+        std::vector<double> h(2 * (size_t)n_prob, 0.0);
+        for (int k = 0; k < n_prob; ++k)
+            CU(cudaMemcpyAsync(h.data() + 2 * k, probs[k]->red, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                               streams ? S(streams[k]) : nullptr));
+        for (int k = 0; k < n_prob; ++k) CU(cudaStreamSynchronize(streams ? S(streams[k]) : nullptr));
+        for (int k = 0; k < n_prob; ++k)
+            rel_change_out[k] = h[2 * k + 1] > 0 ? std::sqrt(h[2 * k] / h[2 * k + 1]) : INFINITY;
+    }
+    return FHS_OK;
+}
+
+fhs_status fhs_estimate_bytes(const fhs_params *params, const double *w, int64_t n_vis, int64_t *resident_out,
+                              int64_t *peak_out) {
+    TRY(check_params(params));
+    if (n_vis < 0) return fail(FHS_ERR_ARG, "n_vis must be >= 0");
+    const fhs_params &q = *params;
+    const long long L = q.n_channels, B = q.n_blocks, C = q.n_subcubes, Lc = L / C;
+    const long long N = (long long)q.ny * q.nx, K = 4 * N, M = n_vis;
+    long long nnz = 0;
+    for (long long i = 0; i < M; ++i) {
+        const long long T = row_side(w ? w[i] : 0.0, q);
+        nnz += T * T;
+    }
+    const long long nseg = L * B, nchunk = M / 32 + nseg + 1, nbin = M / 32 + 2 * nseg + 1;
+    const SaraConst c = sara_layout(q.ny, q.nx, q.wavelet_levels);
+    long long nuc = 0;
+    const std::vector<Facet> fac = facet_list(q);
+    for (const Facet &f : fac) nuc += Lc * (long long)(f.y1 - f.y0) * (f.x1 - f.x0);
+    nuc *= C;
+    const long long Q = (long long)fac.size();
+    long long r = 0;
+    r += 8 * M + 8 * (M + 1) + 8 * nnz + 8 * M * 4;                  // meta, rowptr, G, y, d, scratch, perm
+    r += 8 * (nseg + 1) + 8 * nseg + 8 * nseg + 4 * nseg;            // segments, norms, eps, scales
+    r += 8 * (nbin + 1) + 8 * nbin + 8 * (nchunk + 1) + 4 * nchunk;  // bins and chunks
+    r += 4 * (q.ny + q.nx);                                          // Z scaling
+    r += 8 * K * L * (3 + B);                                        // grids
+    r += 4 * N * L * 3 + 16 + 16 * L;                                // images, reductions
+    r += 4 * c.n_coef * L * 2 + 4 * c.n_tmp * L + 4 * c.n_coef * C;  // SARA
+    r += 16 * Q + 8 * C * Q + 4 * nuc + 12 * C * Q * Lc * Lc + 4 * C * Q * Lc + 4 * (q.ny + q.nx);
+    r += (long long)cufft_workspace(2 * q.ny, 2 * q.nx, int(L));
+    const long long n_planes = q.w_max > 0.0 ? 2LL * (q.n_wplanes - 1) + 1 : 1;
+    const long long peak = r + 16 * M + 2 * M + 16 * n_planes * 2 * (2 * kMaxWHalf + 1) + 8 * nseg;
+    if (resident_out) *resident_out = r;
+    if (peak_out) *peak_out = peak;
+    return FHS_OK;
 }
 
 fhs_status fhs_profile_enable(fhs_problem *p, int32_t on) {
@@ -799,7 +915,7 @@ fhs_status fhs_pdfb_step(fhs_problem *p, int32_t n_iter, double *rel_change_out,
     if (!p) return fail(FHS_ERR_ARG, "NULL problem");
     if (n_iter < 0) return fail(FHS_ERR_ARG, "n_iter must be >= 0");
     cudaStream_t s = S(stream);
-    for (int it = 0; it < n_iter; ++it) TRY(one_iteration(p, s));
+    TRY(run_iterations(p, n_iter, s));
     if (rel_change_out) {
         double h[2] = {0, 0};
         CU(cudaMemcpyAsync(h, p->red, sizeof h, cudaMemcpyDeviceToHost, s));

@@ -50,6 +50,8 @@ struct SaraConst {
     int img_ny, img_nx;
 };
 
+SaraConst sara_layout(int ny, int nx, int levels);
+
 // ---------------------------------------------------------------------------
 // Problem state
 // ---------------------------------------------------------------------------
@@ -128,6 +130,12 @@ struct fhs_problem {
     int iteration = 0;
     long long n_launch = 0;                   // libfhs kernels launched
     double *pnorms = nullptr;                 // [2L] power-iteration reductions
+
+    // CUDA graph of one iteration, replayed by fhs_pdfb_step on the stream it was captured on
+    bool use_graphs = true;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t gstream = nullptr;
+    long long g_launches = 0;                 // libfhs kernels in one captured iteration
 
     // tracing: event pairs per phase per iteration, recycled from a pool
     bool prof_on = false;

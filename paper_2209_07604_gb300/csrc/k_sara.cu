@@ -366,6 +366,47 @@ inline int cdiv(long long a, long long b) { return int((a + b - 1) / b); }
 
 }  // namespace
 
+// Layout of Psi^dagger for an ny x nx image with `levels` levels: filters,
+// level sizes n_{j+1} = floor((n_j + F - 1)/2) and coefficient/temp offsets.
+SaraConst sara_layout(int ny, int nx, int levels) {
+    SaraConst c;
+    std::memset(&c, 0, sizeof c);
+    c.levels = levels;
+    c.img_ny = ny;
+    c.img_nx = nx;
+    long long pos = (long long)ny * nx, tpos = 0;
+    for (int b = 1; b <= kNumDb; ++b) {
+        const std::vector<double> h = daubechies(b);
+        const int F = 2 * b;
+        c.F[b] = F;
+        for (int k = 0; k < F; ++k) {
+            c.h[b][k] = float(h[k]);
+            c.g[b][k] = float((k & 1) ? -h[F - 1 - k] : h[F - 1 - k]);
+        }
+        c.ny[b][0] = ny;
+        c.nx[b][0] = nx;
+        for (int j = 1; j <= levels; ++j) {
+            c.ny[b][j] = (c.ny[b][j - 1] + F - 1) / 2;
+            c.nx[b][j] = (c.nx[b][j - 1] + F - 1) / 2;
+        }
+    }
+    for (int b = 1; b <= kNumDb; ++b) {
+        for (int j = 1; j <= levels; ++j) {
+            c.off_det[b][j] = pos;
+            pos += 3LL * c.ny[b][j] * c.nx[b][j];
+        }
+        c.off_ll[b] = pos;
+        pos += (long long)c.ny[b][levels] * c.nx[b][levels];
+        for (int j = 1; j < levels; ++j) {
+            c.off_tmp[b][j] = tpos;
+            tpos += (long long)c.ny[b][j] * c.nx[b][j];
+        }
+    }
+    c.n_coef = pos;
+    c.n_tmp = tpos > 0 ? tpos : 1;
+    return c;
+}
+
 cudaError_t launch_sara_analysis(fhs_problem *p, const float *x, float *coef, cudaStream_t s) {
     const SaraConst &c = p->sara;
     int my = 0, mx = 0;
@@ -436,47 +477,6 @@ static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchFloats];
 std::mutex g_noalloc_mu;
 float *g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
-// Layout of Psi^dagger for an ny x nx image with `levels` levels (the same
-// layout fhs_create_problem builds), computed on the host.
-SaraConst noalloc_layout(int ny, int nx, int levels) {
-    SaraConst c;
-    std::memset(&c, 0, sizeof c);
-    c.levels = levels;
-    c.img_ny = ny;
-    c.img_nx = nx;
-    long long pos = (long long)ny * nx, tpos = 0;
-    for (int b = 1; b <= kNumDb; ++b) {
-        const std::vector<double> h = daubechies(b);
-        const int F = 2 * b;
-        c.F[b] = F;
-        for (int k = 0; k < F; ++k) {
-            c.h[b][k] = float(h[k]);
-            c.g[b][k] = float((k & 1) ? -h[F - 1 - k] : h[F - 1 - k]);
-        }
-        c.ny[b][0] = ny;
-        c.nx[b][0] = nx;
-        for (int j = 1; j <= levels; ++j) {
-            c.ny[b][j] = (c.ny[b][j - 1] + F - 1) / 2;
-            c.nx[b][j] = (c.nx[b][j - 1] + F - 1) / 2;
-        }
-    }
-    for (int b = 1; b <= kNumDb; ++b) {
-        for (int j = 1; j <= levels; ++j) {
-            c.off_det[b][j] = pos;
-            pos += 3LL * c.ny[b][j] * c.nx[b][j];
-        }
-        c.off_ll[b] = pos;
-        pos += (long long)c.ny[b][levels] * c.nx[b][levels];
-        for (int j = 1; j < levels; ++j) {
-            c.off_tmp[b][j] = tpos;
-            tpos += (long long)c.ny[b][j] * c.nx[b][j];
-        }
-    }
-    c.n_coef = pos;
-    c.n_tmp = tpos > 0 ? tpos : 1;
-    return c;
-}
-
 }  // namespace
 }  // namespace fhs
 
@@ -491,7 +491,7 @@ extern "C" fhs_status fhs_sara_analysis_noalloc(int32_t ny, int32_t nx, int32_t 
         set_last_error("fhs_sara_analysis_noalloc: need ny, nx >= 16, n_images >= 0, 1 <= levels <= 6");
         return FHS_ERR_ARG;
     }
-    const SaraConst c = noalloc_layout(ny, nx, levels);
+    const SaraConst c = sara_layout(ny, nx, levels);
     if (c.n_tmp > kNoAllocScratchFloats) {
         set_last_error("fhs_sara_analysis_noalloc: image needs " + std::to_string(c.n_tmp) +
                        " scratch floats, more than the static maximum of " +

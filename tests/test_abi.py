@@ -96,3 +96,21 @@ def test_params_struct_layout(lib):
     assert abs(p.upsilon - 1e-3) < 1e-18 and abs(p.power_tol - 1e-7) < 1e-20
     # 7 int32 + pad, double, 2 int32, double, int32 + pad, 9 doubles, int32 + pad, double
     assert C.sizeof(fhs.fhs_params) == 152
+
+
+def test_estimate_bytes_counts_g_entries(lib):
+    """The footprint estimate is host-only; with the same visibility count,
+    w-terms change it by exactly 8 bytes per extra G entry (box side 7 + 2h)."""
+    p = fhs.default_params(ny=64, nx=64, n_channels=2, n_subcubes=1, n_blocks=2, qy=2, qx=2, facet_overlap=0.1,
+                           w_max=2000.0, pixel_size=1e-4)
+    M = 5000
+    w = np.linspace(0.0, 2000.0, M)
+    r0, pk0 = fhs.fhs_estimate_bytes(p, np.zeros(M), M)
+    r1, pk1 = fhs.fhs_estimate_bytes(p, w, M)
+    P1 = p.n_wplanes - 1
+    pa = np.minimum(np.floor(np.abs(w) / (2000.0 / P1) + 0.5).astype(np.int64), P1)
+    T = 7 + 2 * ((8 * pa + P1) // (2 * P1))
+    assert r1 - r0 == 8 * int(np.sum(T * T - 49))
+    assert pk0 > r0 and pk1 > r1
+    r2, _ = fhs.fhs_estimate_bytes(p, np.zeros(2 * M), 2 * M)
+    assert r2 > r0
