@@ -247,6 +247,59 @@ fhs_status fhs_profile_read(fhs_problem *prob, double *ms_out, int64_t *iters_ou
  * own kernels are not counted). */
 fhs_status fhs_kernel_launches(const fhs_problem *prob, int64_t *count_out);
 
+/* ------------------------------------------------------------------------
+ * Serving: imaging requests solved concurrently on one GPU.  Requests are
+ * independent problems (like the spectral sub-cubes of Eq. 3); a server
+ * admits queued requests first-fit while their estimated peak device
+ * footprint (fhs_estimate_bytes) fits its budget and fewer than max_active
+ * run, builds each on a stream of its own, keeps all admitted problems
+ * stepping (CUDA-graph replays of check_every iterations, relative change
+ * read back asynchronously), reweights between stages as fhs_solve does, and
+ * retires a request at its tolerance or iteration budget, copying the image
+ * to host memory and freeing its device memory (stream-ordered), which
+ * admits further requests.  Native threads: one for admission and set-up,
+ * one for stepping.
+ * ------------------------------------------------------------------------ */
+typedef struct fhs_server fhs_server;
+
+typedef enum { FHS_REQ_QUEUED = 0, FHS_REQ_RUNNING = 1, FHS_REQ_DONE = 2, FHS_REQ_FAILED = 3 } fhs_request_state;
+
+typedef struct fhs_request {       /* arrays as in fhs_create_problem; copied by fhs_server_submit */
+    fhs_params params;
+    const double *omega, *w, *y, *sigma;
+    const int64_t *vis_offsets, *block_offsets;
+    const double *eps;
+    int32_t max_iter;              /* iteration budget over all reweighting stages          */
+    int32_t n_reweight;            /* reweightings (stages = n_reweight + 1)                  */
+    double rel_tol;                /* a stage ends once ||x+ - x|| / ||x+|| < rel_tol         */
+    int32_t check_every;           /* iterations between checks (<= 0: the server's default) */
+} fhs_request;
+
+typedef struct fhs_request_result {
+    int32_t state;                 /* fhs_request_state                                       */
+    int32_t status;                /* fhs_status of a failure                                 */
+    int32_t iterations;            /* PDFB iterations done                                    */
+    double rel_change;             /* last relative change read                               */
+    double t_submit, t_start, t_done;   /* seconds since the server started                  */
+    int64_t device_bytes;          /* bytes the problem held                                  */
+} fhs_request_result;
+
+/* Start a server on the current device with a device-memory budget (bytes). */
+fhs_status fhs_server_create(int64_t hbm_budget_bytes, int32_t max_active, int32_t check_every,
+                             fhs_server **out);
+/* Queue a request (returns at once; FHS_ERR_OOM if it can never fit). */
+fhs_status fhs_server_submit(fhs_server *server, const fhs_request *req, int64_t *id_out);
+/* Non-blocking state of a request. */
+fhs_status fhs_server_query(fhs_server *server, int64_t id, fhs_request_result *res_out);
+/* Wait (timeout_s < 0: forever) for a request; image_out (host [L][ny][nx],
+ * may be NULL) receives the image.  Returns the request's status. */
+fhs_status fhs_server_wait(fhs_server *server, int64_t id, double timeout_s, float *image_out,
+                           fhs_request_result *res_out);
+/* Requests running or being set up, queued, and device bytes admitted. */
+fhs_status fhs_server_stats(fhs_server *server, int64_t *active, int64_t *queued, int64_t *bytes_in_use);
+/* Drop queued requests, finish admitted ones, stop the threads. */
+void fhs_server_destroy(fhs_server *server);
+
 /* Host utility: the library's own db_p low-pass filter (2p taps, minimum
  * phase, sum sqrt(2)), computed by spectral factorisation (Daubechies 1988). */
 fhs_status fhs_daubechies_filter(int32_t p, double *h_out);

@@ -24,7 +24,10 @@ EXPORTED = [
     "fhs_state_size", "fhs_get_state", "fhs_set_state", "fhs_operator_norms", "fhs_daubechies_filter",
     "fhs_last_error", "fhs_profile_enable", "fhs_profile_read", "fhs_kernel_launches",
     "fhs_sara_analysis_noalloc", "fhs_pdfb_step_batch", "fhs_use_graphs", "fhs_estimate_bytes",
+    "fhs_server_create", "fhs_server_submit", "fhs_server_query", "fhs_server_wait", "fhs_server_stats",
+    "fhs_server_destroy",
 ]
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 PHASES = ["primal", "fft_fwd", "degrid_grid", "l2ball", "fft_inv", "sara", "nuclear"]
 
 
@@ -50,6 +53,21 @@ class fhs_info(C.Structure):
         ("n_vis", C.c_int64), ("nnz", C.c_int64), ("n_coef", C.c_int64), ("nuclear_size", C.c_int64),
         ("device_bytes", C.c_int64), ("n_facets", C.c_int32), ("iteration", C.c_int32), ("tau", C.c_double),
         ("sigma0", C.c_double), ("sigma1", C.c_double), ("sigma2", C.c_double), ("phi_norm2_max", C.c_double),
+    ]
+
+
+class fhs_request(C.Structure):
+    _fields_ = [
+        ("params", fhs_params), ("omega", C.c_void_p), ("w", C.c_void_p), ("y", C.c_void_p),
+        ("sigma", C.c_void_p), ("vis_offsets", C.c_void_p), ("block_offsets", C.c_void_p), ("eps", C.c_void_p),
+        ("max_iter", C.c_int32), ("n_reweight", C.c_int32), ("rel_tol", C.c_double), ("check_every", C.c_int32),
+    ]
+
+
+class fhs_request_result(C.Structure):
+    _fields_ = [
+        ("state", C.c_int32), ("status", C.c_int32), ("iterations", C.c_int32), ("rel_change", C.c_double),
+        ("t_submit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double), ("device_bytes", C.c_int64),
     ]
 
 
@@ -91,6 +109,12 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fhs_pdfb_step_batch": (C.c_int, [vp, i32, i32, vp, vp]),
         "fhs_use_graphs": (C.c_int, [vp, i32]),
         "fhs_estimate_bytes": (C.c_int, [P(fhs_params), vp, i64, P(i64), P(i64)]),
+        "fhs_server_create": (C.c_int, [i64, i32, i32, P(vp)]),
+        "fhs_server_submit": (C.c_int, [vp, P(fhs_request), P(i64)]),
+        "fhs_server_query": (C.c_int, [vp, i64, P(fhs_request_result)]),
+        "fhs_server_wait": (C.c_int, [vp, i64, dbl, vp, P(fhs_request_result)]),
+        "fhs_server_stats": (C.c_int, [vp, P(i64), P(i64), P(i64)]),
+        "fhs_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -278,6 +302,74 @@ def fhs_kernel_launches(prob) -> int:
     n = C.c_int64(0)
     _check(load_library().fhs_kernel_launches(prob, C.byref(n)))
     return n.value
+
+
+class Server:
+    """Serving loop of libfhs (native threads): submit imaging requests, wait for images."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 8, check_every: int = 10):
+        h = C.c_void_p()
+        _check(load_library().fhs_server_create(int(hbm_budget_bytes), int(max_active), int(check_every),
+                                                C.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, params: fhs_params, omega, w, y, sigma, vis_offsets, block_offsets, max_iter, rel_tol,
+               n_reweight=0, check_every=0, eps=None) -> int:
+        arrs = dict(omega=np.ascontiguousarray(omega, dtype=np.float64),
+                    w=None if w is None else np.ascontiguousarray(w, dtype=np.float64),
+                    y=np.ascontiguousarray(np.stack([np.real(y), np.imag(y)], -1) if np.iscomplexobj(y) else y,
+                                           dtype=np.float64),
+                    sigma=np.ascontiguousarray(sigma, dtype=np.float64),
+                    vis_offsets=np.ascontiguousarray(vis_offsets, dtype=np.int64),
+                    block_offsets=np.ascontiguousarray(block_offsets, dtype=np.int64),
+                    eps=None if eps is None else np.ascontiguousarray(eps, dtype=np.float64))
+        req = fhs_request(params=params, max_iter=int(max_iter), n_reweight=int(n_reweight), rel_tol=float(rel_tol),
+                          check_every=int(check_every))
+        for k, a in arrs.items():
+            setattr(req, k, None if a is None else a.ctypes.data)
+        rid = C.c_int64(0)
+        _check(load_library().fhs_server_submit(self.handle, C.byref(req), C.byref(rid)))   # copies the arrays
+        return rid.value
+
+    def submit_synth(self, prob, mu, mu_bar, max_iter, rel_tol, n_reweight=0, check_every=0, **kw) -> int:
+        L, M = prob.omega.shape[:2]
+        params = default_params(ny=prob.ny, nx=prob.nx, n_channels=L, n_subcubes=prob.C, n_blocks=prob.B,
+                                qy=prob.qy, qx=prob.qx, facet_overlap=prob.overlap, w_max=prob.w_max,
+                                pixel_size=prob.pixel_size, mu=mu, mu_bar=mu_bar)
+        for k, v in kw.items():
+            setattr(params, k, v)
+        return self.submit(params, prob.omega.reshape(-1, 2), prob.w.reshape(-1), prob.y.reshape(-1), prob.sigma,
+                           np.arange(L + 1, dtype=np.int64) * M, prob.block_offsets, max_iter, rel_tol, n_reweight,
+                           check_every)
+
+    def query(self, rid: int) -> fhs_request_result:
+        r = fhs_request_result()
+        _check(load_library().fhs_server_query(self.handle, int(rid), C.byref(r)))
+        return r
+
+    def wait(self, rid: int, shape=None, timeout: float = -1.0):
+        r = fhs_request_result()
+        img = None if shape is None else np.empty(shape, dtype=np.float32)
+        _check(load_library().fhs_server_wait(self.handle, int(rid), float(timeout),
+                                              None if img is None else img.ctypes.data, C.byref(r)))
+        return img, r
+
+    def stats(self):
+        a, q, b = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+        _check(load_library().fhs_server_stats(self.handle, C.byref(a), C.byref(q), C.byref(b)))
+        return a.value, q.value, b.value
+
+    def close(self):
+        if self.handle:
+            load_library().fhs_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # --- convenience wrapper ----------------------------------------------------

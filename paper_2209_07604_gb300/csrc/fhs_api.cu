@@ -50,25 +50,35 @@ fhs_status fail(fhs_status st, const char *fmt, ...) {
         if (s_ != FHS_OK) return s_;                                                               \
     } while (0)
 
+// Stream-ordered device allocation on the problem's home stream (released
+// with cudaFreeAsync, so retiring a problem never synchronises the device).
 template <typename T>
 fhs_status dev_alloc(fhs_problem *p, T **ptr, size_t count, bool zero = true) {
     *ptr = nullptr;
     if (count == 0) count = 1;
     void *q = nullptr;
     const size_t bytes = count * sizeof(T);
-    cudaError_t e = cudaMalloc(&q, bytes);
+    cudaError_t e = cudaMallocAsync(&q, bytes, p->home);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return fail(FHS_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        return fail(FHS_ERR_OOM, "cudaMallocAsync of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
     }
     p->allocs.push_back(q);
     p->bytes += bytes;
     if (zero) {
-        e = cudaMemset(q, 0, bytes);
-        if (e != cudaSuccess) return fail(FHS_ERR_CUDA, "cudaMemset failed: %s", cudaGetErrorString(e));
+        e = cudaMemsetAsync(q, 0, bytes, p->home);
+        if (e != cudaSuccess) return fail(FHS_ERR_CUDA, "cudaMemsetAsync failed: %s", cudaGetErrorString(e));
     }
     *ptr = static_cast<T *>(q);
     return FHS_OK;
+}
+
+void dev_free(fhs_problem *p, void *q) {
+    auto it = std::find(p->allocs.begin(), p->allocs.end(), q);
+    if (it != p->allocs.end()) {
+        cudaFreeAsync(q, p->home);
+        p->allocs.erase(it);
+    }
 }
 
 template <typename T>
@@ -79,8 +89,9 @@ fhs_status upload(T *dst, const T *src, size_t count, cudaStream_t s) {
 }
 
 void free_all(fhs_problem *p) {
-    for (void *q : p->allocs) cudaFree(q);
+    for (void *q : p->allocs) cudaFreeAsync(q, p->home);
     p->allocs.clear();
+    cudaStreamSynchronize(p->home);
     if (p->plan_ok) cufftDestroy(p->plan);
     p->plan_ok = false;
 }
@@ -338,6 +349,17 @@ size_t cufft_workspace(int K1, int K2, int L) {
 
 void fhs::set_last_error(const std::string &msg) { g_err = msg; }
 
+void fhs::destroy_on_stream(fhs_problem *p, cudaStream_t s) {
+    if (!p) return;
+    cudaStreamSynchronize(s);
+    for (auto &u : p->ev_used) { cudaEventDestroy(u.second.first); cudaEventDestroy(u.second.second); }
+    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    p->home = s;
+    free_all(p);
+    delete p;
+}
+
 extern "C" {
 
 const char *fhs_last_error(void) { return g_err.c_str(); }
@@ -413,6 +435,7 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
         return st;
     };
     p->prm = q;
+    p->home = s;
     p->L = L; p->C = q.n_subcubes; p->Lc = L / q.n_subcubes; p->B = B; p->J = J;
     p->ny = q.ny; p->nx = q.nx; p->K1 = 2 * q.ny; p->K2 = 2 * q.nx;
     p->N = (long long)q.ny * q.nx;
@@ -746,10 +769,7 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
         if (e != cudaSuccess) return guard(fail(FHS_ERR_CUDA, "set-up failed: %s", cudaGetErrorString(e)));
     }
     // set-up temporaries are no longer needed
-    for (void *t : {(void *)d_kap, (void *)d_plane, (void *)d_wk, (void *)d_isg}) {
-        auto it = std::find(p->allocs.begin(), p->allocs.end(), t);
-        if (it != p->allocs.end()) { cudaFree(t); p->allocs.erase(it); }
-    }
+    for (void *t : {(void *)d_kap, (void *)d_plane, (void *)d_wk, (void *)d_isg}) dev_free(p, t);
     p->bytes -= sizeof(double2) * Mtot + sizeof(short) * Mtot + sizeof(double2) * wk.size() + sizeof(double) * p->n_seg;
     *out = p;
     return FHS_OK;
@@ -761,6 +781,7 @@ void fhs_destroy_problem(fhs_problem *p) {
     for (auto &u : p->ev_used) { cudaEventDestroy(u.second.first); cudaEventDestroy(u.second.second); }
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    p->home = nullptr;          // the creation stream may be gone; the device is idle
     free_all(p);
     delete p;
 }
@@ -1032,7 +1053,11 @@ fhs_status fhs_operator_norms(fhs_problem *p, int32_t n_iter, double *norms, voi
     // the work images are part of the iteration state: keep them
     const long long LN = p->N * p->L;
     float *save = nullptr;
-    TRY(dev_alloc(p, &save, 2 * LN, false));
+    cudaStream_t home = p->home;
+    p->home = s;                // the work buffer lives on this call's stream
+    fhs_status ast = dev_alloc(p, &save, 2 * LN, false);
+    p->home = home;
+    TRY(ast);
     CU(cudaMemcpyAsync(save, p->Xbar, sizeof(float) * LN, cudaMemcpyDeviceToDevice, s));
     CU(cudaMemcpyAsync(save + LN, p->A_sara, sizeof(float) * LN, cudaMemcpyDeviceToDevice, s));
     std::vector<double> lam;
@@ -1040,8 +1065,10 @@ fhs_status fhs_operator_norms(fhs_problem *p, int32_t n_iter, double *norms, voi
     CU(cudaMemcpyAsync(p->Xbar, save, sizeof(float) * LN, cudaMemcpyDeviceToDevice, s));
     CU(cudaMemcpyAsync(p->A_sara, save + LN, sizeof(float) * LN, cudaMemcpyDeviceToDevice, s));
     CU(cudaStreamSynchronize(s));
-    auto it = std::find(p->allocs.begin(), p->allocs.end(), (void *)save);
-    if (it != p->allocs.end()) { cudaFree(save); p->allocs.erase(it); p->bytes -= sizeof(float) * 2 * LN; }
+    p->home = s;
+    dev_free(p, save);
+    p->home = home;
+    p->bytes -= sizeof(float) * 2 * LN;
     if (st != FHS_OK) return st;
     std::copy(lam.begin(), lam.end(), norms);
     return FHS_OK;

@@ -126,6 +126,7 @@ struct fhs_problem {
     // reductions
     double *red = nullptr;                    // [2]: ||x+ - x||^2, ||x+||^2
 
+    cudaStream_t home = nullptr;              // stream of creation: stream-ordered allocations live on it
     double tau = 0, sigma0 = 0, sigma1 = 0, sigma2 = 0, phi_norm2_max = 0;
     int iteration = 0;
     long long n_launch = 0;                   // libfhs kernels launched
@@ -151,6 +152,10 @@ namespace fhs {
 
 // Sets the text returned by fhs_last_error() on the calling thread.
 void set_last_error(const std::string &msg);
+
+// Releases a problem whose work has all been issued on `s`: waits for s only
+// (no device-wide synchronisation), frees its stream-ordered memory.
+void destroy_on_stream(fhs_problem *p, cudaStream_t s);
 
 // kernel launchers --------------------------------------------------------
 // k_nufft.cu
