@@ -372,6 +372,68 @@ def run_reference(args):
     }))
 
 
+SERVE_MIX = [  # (ny, nx, L, C, M per channel, B, facets, w_max)
+    (256, 256, 4, 1, 100_000, 2, 2, 2000.0),
+    (512, 512, 8, 2, 200_000, 2, 2, 2000.0),
+    (256, 256, 8, 1, 400_000, 4, 2, 0.0),
+    (1024, 1024, 4, 1, 300_000, 4, 4, 2000.0),
+    (512, 512, 4, 2, 1_000_000, 4, 2, 2000.0),
+    (1536, 1024, 4, 1, 200_000, 2, 4, 0.0),
+]
+
+
+def _serve_pass(reqs, arrivals, max_active, budget, check_every):
+    import paper_2209_07604_gb300 as fhs
+    sv = fhs.Server(hbm_budget_bytes=budget, max_active=max_active, check_every=check_every)
+    t0 = time.perf_counter()
+    ids = []
+    for (P, kw), ta in zip(reqs, arrivals):
+        dt = ta - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        ids.append(sv.submit_synth(P, **kw))
+    res = [sv.wait(i)[1] for i in ids]
+    makespan = time.perf_counter() - t0
+    sv.close()
+    lat = np.array([r.t_done - r.t_submit for r in res])
+    vis_iter = sum(P.omega.shape[0] * P.omega.shape[1] * r.iterations for (P, _), r in zip(reqs, res))
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "makespan_s": makespan,
+            "images_per_hour": len(res) * 3600.0 / makespan, "vis_per_s": vis_iter / makespan,
+            "iterations": [int(r.iterations) for r in res],
+            "failed": int(sum(r.state != fhs.REQ_DONE for r in res))}
+
+
+def run_serve(args):
+    """Continuous batching vs one request at a time, same Poisson arrivals."""
+    import torch
+    import paper_2209_07604_gb300 as fhs
+    from paper_2209_07604_gb300 import synth
+    torch.cuda.set_device(0)
+    fhs.load_library()
+    pool = []
+    for k, (ny, nx, L, C, M, B, Q, wmax) in enumerate(SERVE_MIX):
+        pool.append(synth.make_problem("vla_1024", trial=k, ny=ny, nx=nx, L=L, C=C, M=M, B=B, qy=Q, qx=Q,
+                                       w_max=wmax))
+    rng = np.random.default_rng(7604)
+    n = args.serve_requests
+    reqs = [(pool[rng.integers(len(pool))], dict(mu=MU, mu_bar=MU_BAR, max_iter=args.serve_iters,
+                                                   rel_tol=1e-5, n_reweight=1, check_every=10))
+            for _ in range(n)]
+    arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, size=n))
+    budget = int(args.serve_budget_gb * (1 << 30))
+    batched = _serve_pass(reqs, arrivals, args.serve_active, budget, 10)
+    serial = _serve_pass(reqs, arrivals, 1, budget, 10)
+    print(json.dumps({
+        "mode": "serve", "metric": "imaging requests: p50/p99 time to image, images/hour, visibilities/s",
+        "unit": "s", "requests": n, "arrival_rate_per_s": args.serve_rate,
+        "mix": [dict(zip(["ny", "nx", "L", "C", "M_per_channel", "B", "facets", "w_max"], m)) for m in SERVE_MIX],
+        "iterations_per_request": args.serve_iters, "hbm_budget_gb": args.serve_budget_gb,
+        "continuous_batching": batched, "one_at_a_time": serial,
+        "speedup_p99": serial["p99_s"] / batched["p99_s"], "speedup_throughput": batched["images_per_hour"] /
+        serial["images_per_hour"], "data": "synthetic"}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -381,11 +443,19 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--e2e-iters", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="pdfb", choices=["pdfb", "serve"])
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-rate", type=float, default=4.0)
+    ap.add_argument("--serve-iters", type=int, default=200)
+    ap.add_argument("--serve-active", type=int, default=8)
+    ap.add_argument("--serve-budget-gb", type=float, default=200.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 

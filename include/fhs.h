@@ -257,7 +257,7 @@ fhs_status fhs_kernel_launches(const fhs_problem *prob, int64_t *count_out);
  * read back asynchronously), reweights between stages as fhs_solve does, and
  * retires a request at its tolerance or iteration budget, copying the image
  * to host memory and freeing its device memory (stream-ordered), which
- * admits further requests.  Native threads: one for admission and set-up,
+ * admits further requests.  Native threads: three for admission and set-up,
  * one for stepping.
  * ------------------------------------------------------------------------ */
 typedef struct fhs_server fhs_server;

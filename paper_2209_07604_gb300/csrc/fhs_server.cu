@@ -3,8 +3,8 @@
 // A request is a whole imaging problem (Eq. 3) solved to a relative-change
 // tolerance with log-sum reweighting (Sec. 2.2.3).  Requests are independent,
 // like the spectral sub-cubes of the paper, so they overlap freely:
-//  - a setup thread admits queued requests first-fit while their estimated
-//    peak device footprint fits the budget, and builds each problem on a
+//  - set-up threads admit queued requests first-fit while their estimated
+//    peak device footprint fits the budget, and build each problem on a
 //    stream of its own (host sort, G build, power iteration);
 //  - a stepping thread keeps every admitted problem busy: it replays chunks of
 //    PDFB iterations (CUDA graphs) on the problem's stream, reads the
@@ -29,6 +29,7 @@
 namespace {
 
 using Clock = std::chrono::steady_clock;
+constexpr int kSetupThreads = 3;
 
 struct Req {
     long long id = 0;
@@ -65,7 +66,8 @@ struct fhs_server {
     int setting_up = 0;
     bool stop = false;
     int device = 0;
-    std::thread th_setup, th_step;
+    std::vector<std::thread> th_setup;          // set-up is host-heavy (sort, tables): several threads
+    std::thread th_step;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 };
@@ -259,7 +261,7 @@ fhs_status fhs_server_create(int64_t hbm_budget_bytes, int32_t max_active, int32
     sv->max_active = max_active;
     sv->chunk = check_every > 0 ? check_every : 10;
     cudaGetDevice(&sv->device);
-    sv->th_setup = std::thread(setup_loop, sv);
+    for (int k = 0; k < kSetupThreads; ++k) sv->th_setup.emplace_back(setup_loop, sv);
     sv->th_step = std::thread(step_loop, sv);
     *out = sv;
     return FHS_OK;
@@ -359,7 +361,7 @@ void fhs_server_destroy(fhs_server *sv) {
         sv->stop = true;
         sv->cv_setup.notify_all();
     }
-    sv->th_setup.join();
+    for (auto &t : sv->th_setup) t.join();
     sv->th_step.join();
     delete sv;
 }
