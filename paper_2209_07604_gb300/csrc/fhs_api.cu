@@ -5,6 +5,7 @@
 #include "fhs_internal.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -12,6 +13,7 @@
 #include <new>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 using namespace fhs;
@@ -19,6 +21,31 @@ using namespace fhs;
 namespace {
 
 thread_local std::string g_err;
+
+// fn(begin, end) over [0, n) split into contiguous ranges on up to 32 host
+// threads (set-up of 10^7 visibilities is otherwise host bound).  A range whose
+// thread cannot be started runs on the calling thread.
+template <typename F>
+void parallel_for(long long n, F fn, long long min_chunk = 1 << 16) {
+    const long long hc = std::max(1u, std::thread::hardware_concurrency());
+    const long long nt = std::max(1LL, std::min({hc, 32LL, (n + min_chunk - 1) / std::max(1LL, min_chunk)}));
+    if (nt <= 1) {
+        fn(0LL, n);
+        return;
+    }
+    const long long step = (n + nt - 1) / nt;
+    std::vector<std::thread> th;
+    for (long long t = 1; t < nt; ++t) {
+        const long long a = std::min(n, t * step), b = std::min(n, (t + 1) * step);
+        try {
+            th.emplace_back(fn, a, b);
+        } catch (...) {
+            fn(a, b);
+        }
+    }
+    fn(0LL, std::min(n, step));
+    for (auto &x : th) x.join();
+}
 
 fhs_status fail(fhs_status st, const char *fmt, ...) {
     char buf[512];
@@ -89,11 +116,17 @@ fhs_status upload(T *dst, const T *src, size_t count, cudaStream_t s) {
 }
 
 void free_all(fhs_problem *p) {
+    if (p->s_sara) cudaStreamSynchronize(p->s_sara);
+    if (p->s_nuc) cudaStreamSynchronize(p->s_nuc);
     for (void *q : p->allocs) cudaFreeAsync(q, p->home);
     p->allocs.clear();
     cudaStreamSynchronize(p->home);
     if (p->plan_ok) cufftDestroy(p->plan);
     p->plan_ok = false;
+    for (cudaStream_t *t : {&p->s_sara, &p->s_nuc})
+        if (*t) { cudaStreamDestroy(*t); *t = nullptr; }
+    for (cudaEvent_t *e : {&p->ev_fork, &p->ev_sara, &p->ev_nuc})
+        if (*e) { cudaEventDestroy(*e); *e = nullptr; }
 }
 
 inline cudaStream_t S(void *s) { return static_cast<cudaStream_t>(s); }
@@ -253,6 +286,14 @@ fhs_status one_iteration(fhs_problem *p, cudaStream_t s) {
         Phase ph(p, s, FHS_PHASE_PRIMAL);
         CU(launch_primal(p, s));
     }
+    // fork: the prior branches only read xbar; tracing keeps one stream so that
+    // its per-phase event pairs time one phase at a time
+    const bool fork = !p->prof_on && p->s_sara && p->s_nuc && (sara_active(p) || nuc_active(p));
+    if (fork) {
+        CU(cudaEventRecord(p->ev_fork, s));
+        CU(cudaStreamWaitEvent(p->s_sara, p->ev_fork, 0));
+        CU(cudaStreamWaitEvent(p->s_nuc, p->ev_fork, 0));
+    }
     // data fidelity: F, single pass over G, l2-ball factors, combine, F^H
     {
         Phase ph(p, s, FHS_PHASE_FFT_FWD);
@@ -273,17 +314,25 @@ fhs_status one_iteration(fhs_problem *p, cudaStream_t s) {
     }
     // average joint sparsity
     if (sara_active(p)) {
+        cudaStream_t ss = fork ? p->s_sara : s;
         Phase ph(p, s, FHS_PHASE_SARA);
-        CU(launch_sara_analysis(p, p->Xbar, p->coef_tmp, s));
-        CU(launch_l21_dual(p, s));
-        CU(launch_sara_synthesis(p, p->W, p->A_sara, s));
+        CU(launch_sara_analysis(p, p->Xbar, p->coef_tmp, ss));
+        CU(launch_l21_dual(p, ss));
+        CU(launch_sara_synthesis(p, p->W, p->A_sara, ss));
+        if (fork) CU(cudaEventRecord(p->ev_sara, ss));
     }
     // faceted low-rankness
     if (nuc_active(p)) {
+        cudaStream_t sn = fork ? p->s_nuc : s;
         Phase ph(p, s, FHS_PHASE_NUCLEAR);
-        CU(launch_nuclear_gram(p, p->Xbar, true, s));
-        CU(launch_nuclear_eig(p, false, s));
-        CU(launch_nuclear_apply(p, s));
+        CU(launch_nuclear_gram(p, p->Xbar, true, sn));
+        CU(launch_nuclear_eig(p, false, sn));
+        CU(launch_nuclear_apply(p, sn));
+        if (fork) CU(cudaEventRecord(p->ev_nuc, sn));
+    }
+    if (fork) {                                  // join
+        if (sara_active(p)) CU(cudaStreamWaitEvent(s, p->ev_sara, 0));
+        if (nuc_active(p)) CU(cudaStreamWaitEvent(s, p->ev_nuc, 0));
     }
     if (p->prof_on) p->prof_iters++;
     p->iteration++;
@@ -415,12 +464,28 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
             if (bo[b + 1] < bo[b]) return fail(FHS_ERR_ARG, "block_offsets must be non-decreasing");
     }
     const long long Mtot = vis_offsets[L];
-    for (long long i = 0; i < Mtot; ++i) {
-        const double a = omega[2 * i], b = omega[2 * i + 1];
-        if (!(a >= -M_PI && a < M_PI && b >= -M_PI && b < M_PI))
-            return fail(FHS_ERR_ARG, "omega[%lld] outside [-pi, pi)", i);
-        if (!std::isfinite(y[2 * i]) || !std::isfinite(y[2 * i + 1])) return fail(FHS_ERR_ARG, "y[%lld] not finite", i);
-        if (w && !std::isfinite(w[i])) return fail(FHS_ERR_ARG, "w[%lld] not finite", i);
+    {
+        // first invalid visibility (parallel scan), then the message for it
+        std::atomic<long long> first_bad{Mtot};
+        parallel_for(Mtot, [&](long long i0, long long i1) {
+            for (long long i = i0; i < i1 && i < first_bad.load(std::memory_order_relaxed); ++i) {
+                const double a = omega[2 * i], b = omega[2 * i + 1];
+                if (!(a >= -M_PI && a < M_PI && b >= -M_PI && b < M_PI) || !std::isfinite(y[2 * i]) ||
+                    !std::isfinite(y[2 * i + 1]) || (w && !std::isfinite(w[i]))) {
+                    long long cur = first_bad.load();
+                    while (i < cur && !first_bad.compare_exchange_weak(cur, i)) {}
+                    break;
+                }
+            }
+        });
+        const long long i = first_bad.load();
+        if (i < Mtot) {
+            const double a = omega[2 * i], b = omega[2 * i + 1];
+            if (!(a >= -M_PI && a < M_PI && b >= -M_PI && b < M_PI))
+                return fail(FHS_ERR_ARG, "omega[%lld] outside [-pi, pi)", i);
+            if (!std::isfinite(y[2 * i]) || !std::isfinite(y[2 * i + 1])) return fail(FHS_ERR_ARG, "y[%lld] not finite", i);
+            return fail(FHS_ERR_ARG, "w[%lld] not finite", i);
+        }
     }
     cudaStream_t s = S(stream);
 
@@ -454,7 +519,8 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
     const double dw = q.w_max > 0.0 ? q.w_max / P1 : 0.0;
     const int ntx = (K2 + kTile - 1) / kTile, nty = (K1 + kTile - 1) / kTile;
     std::vector<int> key(Mtot), pl(Mtot), corner1(Mtot), corner2(Mtot), Tv(Mtot);
-    for (long long i = 0; i < Mtot; ++i) {
+    parallel_for(Mtot, [&](long long i0, long long i1) {
+    for (long long i = i0; i < i1; ++i) {
         const double k1 = omega[2 * i] * K1 / (2.0 * M_PI);
         const double k2 = omega[2 * i + 1] * K2 / (2.0 * M_PI);
         const long long p01 = (long long)std::floor(k1 - J / 2.0) + 1;
@@ -473,36 +539,39 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
         corner1[i] = int(c1); corner2[i] = int(c2); Tv[i] = T; pl[i] = pv + P1;
         key[i] = int(c1 / kTile) * ntx + int(c2 / kTile);
     }
+    });
     const int nkeys = nty * ntx;
     std::vector<long long> perm(Mtot);
-    {
+    // counting sort by tile key, segments in parallel (each segment is stable)
+    parallel_for(p->n_seg, [&](long long s0, long long s1) {
         std::vector<long long> cnt(nkeys + 1);
-        for (int sg = 0; sg < p->n_seg; ++sg) {
+        for (long long sg = s0; sg < s1; ++sg) {
             const long long a = p->seg_off[sg], b = p->seg_off[sg + 1];
             std::fill(cnt.begin(), cnt.end(), 0);
             for (long long i = a; i < b; ++i) cnt[key[i] + 1]++;
             for (int k = 0; k < nkeys; ++k) cnt[k + 1] += cnt[k];
             for (long long i = a; i < b; ++i) perm[a + cnt[key[i]]++] = i;
         }
-    }
+    }, 1);
     std::vector<int2> meta(Mtot);
     std::vector<long long> rowptr(Mtot + 1);
     std::vector<double2> kap(Mtot);
     std::vector<short> plane(Mtot);
     std::vector<float2> yw(Mtot);
     rowptr[0] = 0;
-    for (long long v = 0; v < Mtot; ++v) {
-        const long long i = perm[v];
-        meta[v] = make_int2(corner1[i] | (corner2[i] << 16), Tv[i]);
-        rowptr[v + 1] = rowptr[v] + (long long)Tv[i] * Tv[i];
-        kap[v] = make_double2(omega[2 * i] * K1 / (2.0 * M_PI), omega[2 * i + 1] * K2 / (2.0 * M_PI));
-        plane[v] = short(pl[i]);
-    }
-    for (int l = 0; l < L; ++l)
-        for (long long v = vis_offsets[l]; v < vis_offsets[l + 1]; ++v) {
+    parallel_for(Mtot, [&](long long v0, long long v1) {
+        int l = int(std::upper_bound(vis_offsets, vis_offsets + L + 1, (int64_t)v0) - vis_offsets) - 1;
+        for (long long v = v0; v < v1; ++v) {
+            while (v >= vis_offsets[l + 1]) ++l;
             const long long i = perm[v];
+            meta[v] = make_int2(corner1[i] | (corner2[i] << 16), Tv[i]);
+            rowptr[v + 1] = (long long)Tv[i] * Tv[i];
+            kap[v] = make_double2(omega[2 * i] * K1 / (2.0 * M_PI), omega[2 * i + 1] * K2 / (2.0 * M_PI));
+            plane[v] = short(pl[i]);
             yw[v] = make_float2(float(y[2 * i] / sigma[l]), float(y[2 * i + 1] / sigma[l]));
         }
+    });
+    for (long long v = 0; v < Mtot; ++v) rowptr[v + 1] += rowptr[v];
     p->nnz = rowptr[Mtot];
     { std::vector<int> t; t.swap(key); } { std::vector<int> t; t.swap(corner1); } { std::vector<int> t; t.swap(corner2); }
 
@@ -748,6 +817,13 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
         if ((st = guard(upload(p->cov_col_first, cf.data(), cf.size(), s))) != FHS_OK) return st;
         if ((st = guard(upload(p->cov_col_cnt, cc.data(), cc.size(), s))) != FHS_OK) return st;
     }
+
+    if (cudaStreamCreateWithFlags(&p->s_sara, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->s_nuc, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_sara, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_nuc, cudaEventDisableTiming) != cudaSuccess)
+        return guard(fail(FHS_ERR_CUDA, "stream/event creation failed"));
 
     // ---- step sizes (Condat-Vu: tau * sum_i sigma_i ||L_i||^2 < 1)
     p->tau = q.tau > 0 ? q.tau : 0.99 / 3.0;

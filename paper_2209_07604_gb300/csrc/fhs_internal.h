@@ -132,6 +132,11 @@ struct fhs_problem {
     long long n_launch = 0;                   // libfhs kernels launched
     double *pnorms = nullptr;                 // [2L] power-iteration reductions
 
+    // the SARA and nuclear dual steps run on their own streams, forked after
+    // the primal step and joined before the iteration ends
+    cudaStream_t s_sara = nullptr, s_nuc = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_sara = nullptr, ev_nuc = nullptr;
+
     // CUDA graph of one iteration, replayed by fhs_pdfb_step on the stream it was captured on
     bool use_graphs = true;
     cudaGraphExec_t gexec = nullptr;

@@ -17,15 +17,21 @@ namespace {
 
 constexpr int kWarps = 8;               // warps per CTA for visibility kernels
 
-__device__ __forceinline__ double kb_eval(double t, int J, double beta, double inv_i0b) {
+// Terms of the I0 power series kept (q = (x/2)^2 <= (beta/2)^2 < 100 for
+// J <= 16 at 2x oversampling; the series has converged to 1e-17 long before).
+constexpr int kI0Terms = 96;
+
+// KB window at offset t: I0(beta sqrt(1 - (2t/J)^2)) / I0(beta), with
+// I0(x) = sum_k q^k / (k!)^2 (q = x^2 / 4) summed in FP64.  inv_k2[k] = 1/k^2
+// turns the FP64 division of each term into a multiplication.
+__device__ __forceinline__ double kb_eval(double t, int J, double beta, double inv_i0b, const double *inv_k2) {
     const double u = 2.0 * t / double(J);
     const double r = 1.0 - u * u;
     if (r < 0.0) return 0.0;
-    const double x = beta * sqrt(r);
-    const double q = 0.25 * x * x;
+    const double q = 0.25 * beta * beta * r;
     double term = 1.0, sum = 1.0;
-    for (int k = 1; k < 200; ++k) {
-        term *= q / (double(k) * double(k));
+    for (int k = 1; k < kI0Terms; ++k) {
+        term *= q * inv_k2[k];
         sum += term;
         if (term < 1e-17 * sum) break;
     }
@@ -50,6 +56,9 @@ __global__ void __launch_bounds__(256) build_g_kernel(
     long long Mtot, int J, double beta, double inv_i0b) {
     __shared__ double s_kb[kWarps][2][16];
     __shared__ double2 s_g[kWarps][2][16];
+    __shared__ double s_inv_k2[kI0Terms];
+    for (int k = threadIdx.x; k < kI0Terms; k += blockDim.x) s_inv_k2[k] = k ? 1.0 / (double(k) * double(k)) : 0.0;
+    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * kWarps;
     for (long long v = (long long)blockIdx.x * kWarps + warp; v < Mtot; v += stride) {
@@ -60,7 +69,7 @@ __global__ void __launch_bounds__(256) build_g_kernel(
         const int dim = lane >> 4, i = lane & 15;
         const double kd = dim ? kp.y : kp.x;
         const long long p0 = (long long)floor(kd - 0.5 * J) + 1;
-        if (i < J) s_kb[warp][dim][i] = kb_eval(kd - double(p0 + i), J, beta, inv_i0b);
+        if (i < J) s_kb[warp][dim][i] = kb_eval(kd - double(p0 + i), J, beta, inv_i0b, s_inv_k2);
         __syncwarp();
         const int pl = plane[v];
         if (i < T) {
@@ -104,135 +113,13 @@ __device__ __forceinline__ void red_add_f2(float2 *addr, float2 v) {
     atomicAdd(addr, v);   // sm_90+: vector float2 reduction (red.global.add.v2.f32)
 }
 
-// Degrid only: vis = G (F Z x) for the measure operator and power iteration.
-__global__ void __launch_bounds__(256) degrid_kernel(
-    const int2 *__restrict__ meta, const long long *__restrict__ rowptr, const float2 *__restrict__ gval,
-    const long long *__restrict__ chunk_start, const int *__restrict__ chunk_seg, int B,
-    const float2 *__restrict__ grid, long long K, int K1, int K2, float2 *__restrict__ vis) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ch = blockIdx.x;
-    const int l = chunk_seg[ch] / B;
-    const float2 *gl = grid + (long long)l * K;
-    const long long v1 = chunk_start[ch + 1];
-    for (long long v = chunk_start[ch] + warp; v < v1; v += kWarps) {
-        const int2 m = meta[v];
-        const int T = m.y, n = T * T;
-        const int c1 = m.x & 0xffff, c2 = (int)((unsigned)m.x >> 16);
-        const float invT = 1.0f / float(T);
-        const float2 *gv = gval + rowptr[v];
-        float ar = 0.f, ai = 0.f;
-        for (int e = lane; e < n; e += 32) {
-            const float2 g = __ldg(gv + e);
-            const float2 x = gl[cell_index(e, T, invT, c1, c2, K1, K2)];
-            ar = fmaf(g.x, x.x, fmaf(-g.y, x.y, ar));
-            ai = fmaf(g.x, x.y, fmaf(g.y, x.x, ai));
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            ar += __shfl_xor_sync(0xffffffffu, ar, o);
-            ai += __shfl_xor_sync(0xffffffffu, ai, o);
-        }
-        if (lane == 0) vis[v] = make_float2(ar, ai);
-    }
-}
-
-// Grid only: grid += G^H vis (atomics), for the adjoint operator.
-__global__ void __launch_bounds__(256) grid_kernel(
-    const int2 *__restrict__ meta, const long long *__restrict__ rowptr, const float2 *__restrict__ gval,
-    const long long *__restrict__ chunk_start, const int *__restrict__ chunk_seg, int B,
-    const float2 *__restrict__ vis, long long K, int K1, int K2, float2 *__restrict__ grid) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ch = blockIdx.x;
-    const int l = chunk_seg[ch] / B;
-    float2 *gl = grid + (long long)l * K;
-    const long long v1 = chunk_start[ch + 1];
-    for (long long v = chunk_start[ch] + warp; v < v1; v += kWarps) {
-        const int2 m = meta[v];
-        const int T = m.y, n = T * T;
-        const int c1 = m.x & 0xffff, c2 = (int)((unsigned)m.x >> 16);
-        const float invT = 1.0f / float(T);
-        const float2 *gv = gval + rowptr[v];
-        const float2 d = vis[v];
-        for (int e = lane; e < n; e += 32) {
-            const float2 g = __ldg(gv + e);
-            red_add_f2(gl + cell_index(e, T, invT, c1, c2, K1, K2),
-                       make_float2(g.x * d.x + g.y * d.y, g.x * d.y - g.y * d.x));
-        }
-    }
-}
-
 // The data term of one PDFB iteration in a single pass over G (Eq. 2):
 //   phi  = G_m . Xhat                      (gather from the forward grid)
 //   d_m  = s_b d_m + sigma2 (phi - y_m)    (= z - sigma2 y, z = v + sigma2 Phi xbar)
-//   ||d_b||^2 accumulated in FP64 per block
+//   ||d_b||^2 accumulated per block (compensated FP32, then FP64)
 //   grid_b += conj(G_m) d_m                (scatter into the block's own grid)
 // The block's l2-ball factor (1 - m_b) is known only after the pass; it is
 // applied to grid_b when the block grids are combined, and kept as s_b for d.
-__global__ void __launch_bounds__(256) degrid_grid_fused_kernel(
-    const int2 *__restrict__ meta, const long long *__restrict__ rowptr, const float2 *__restrict__ gval,
-    const float2 *__restrict__ y, float2 *__restrict__ dvis, const long long *__restrict__ chunk_start,
-    const int *__restrict__ chunk_seg, int B, const float *__restrict__ blk_scale,
-    double *__restrict__ blk_norm2, const float2 *__restrict__ grid, float2 *__restrict__ grid_blk,
-    long long K, int K1, int K2, float sigma2) {
-    __shared__ double s_red[kWarps];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ch = blockIdx.x;
-    const int seg = chunk_seg[ch];
-    const int l = seg / B;
-    const float2 *gl = grid + (long long)l * K;
-    float2 *gb = grid_blk + (long long)seg * K;
-    const float sc = blk_scale[seg];
-    double nrm = 0.0;
-    const long long v1 = chunk_start[ch + 1];
-    for (long long v = chunk_start[ch] + warp; v < v1; v += kWarps) {
-        const int2 m = meta[v];
-        const int T = m.y, n = T * T;
-        const int c1 = m.x & 0xffff, c2 = (int)((unsigned)m.x >> 16);
-        const float invT = 1.0f / float(T);
-        const float2 *gv = gval + rowptr[v];
-        float2 g[8];
-        int idx[8];
-        float ar = 0.f, ai = 0.f;
-#pragma unroll
-        for (int it = 0; it < 8; ++it) {
-            const int e = lane + 32 * it;
-            if (e < n) {
-                g[it] = __ldg(gv + e);
-                idx[it] = cell_index(e, T, invT, c1, c2, K1, K2);
-                const float2 x = gl[idx[it]];
-                ar = fmaf(g[it].x, x.x, fmaf(-g[it].y, x.y, ar));
-                ai = fmaf(g[it].x, x.y, fmaf(g[it].y, x.x, ai));
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            ar += __shfl_xor_sync(0xffffffffu, ar, o);
-            ai += __shfl_xor_sync(0xffffffffu, ai, o);
-        }
-        const float2 dold = dvis[v];
-        const float2 yv = y[v];
-        const float dr = fmaf(sc, dold.x, sigma2 * (ar - yv.x));
-        const float di = fmaf(sc, dold.y, sigma2 * (ai - yv.y));
-        if (lane == 0) {
-            dvis[v] = make_float2(dr, di);
-            nrm += double(dr) * dr + double(di) * di;
-        }
-#pragma unroll
-        for (int it = 0; it < 8; ++it) {
-            const int e = lane + 32 * it;
-            if (e < n)
-                red_add_f2(gb + idx[it], make_float2(g[it].x * dr + g[it].y * di, g[it].x * di - g[it].y * dr));
-        }
-    }
-    if (lane == 0) s_red[warp] = nrm;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < kWarps; ++w) s += s_red[w];
-        atomicAdd(blk_norm2 + seg, s);
-    }
-}
-
 // Tile-binned form of the same pass.  A bin holds visibilities of one
 // (channel, block) segment whose box corners fall in one kTile x kTile grid
 // tile; every box then lies inside the kWin x kWin window at the tile origin.
@@ -275,7 +162,11 @@ struct Kahan {
 
 // Visibilities i = i0, i0 + kWarps, ... of one bin, for one warp.  DENSE: the
 // box lies in the shared window; otherwise gather/scatter in global memory.
-template <bool DENSE>
+// MODE: kFused (the PDFB data term), kGather (Phi only: vis_bin[i] = G_i . Xhat)
+// or kScatter (Phi^H only: grid += conj(G_i) vis_bin[i]).
+enum { kFused = 0, kGather = 1, kScatter = 2 };
+
+template <int MODE, bool DENSE>
 __device__ __forceinline__ void bin_rows(int i0, int nv, int lane, const int2 *s_meta, const int *s_off,
                                          const float2 *s_y, const float2 *s_d, const float2 *__restrict__ gbin,
                                          const float2 *s_grid, float *s_re, float *s_im, int wy0, int wx0,
@@ -298,33 +189,45 @@ __device__ __forceinline__ void bin_rows(int i0, int nv, int lane, const int2 *s
             if (32 * it >= n) break;
             const int e = lane + 32 * it;
             if (e < n) {
-                float2 x;
                 if (DENSE) {
                     const int t1 = __float2int_rz((float(e) + 0.5f) * invT);
                     const int t2 = e - t1 * T;
                     idx[it] = (c1 - wy0 + t1) * kWin + (c2 - wx0 + t2);
-                    x = s_grid[idx[it]];
                 } else {
                     idx[it] = cell_index(e, T, invT, c1, c2, K1, K2);
-                    x = gl[idx[it]];
                 }
-                const float2 g = cur.g[it];
-                ar = fmaf(g.x, x.x, fmaf(-g.y, x.y, ar));
-                ai = fmaf(g.x, x.y, fmaf(g.y, x.x, ai));
+                if (MODE != kScatter) {
+                    const float2 x = DENSE ? s_grid[idx[it]] : gl[idx[it]];
+                    const float2 g = cur.g[it];
+                    ar = fmaf(g.x, x.x, fmaf(-g.y, x.y, ar));
+                    ai = fmaf(g.x, x.y, fmaf(g.y, x.x, ai));
+                }
             }
         }
+        float dr, di;
+        if (MODE != kScatter) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            ar += __shfl_xor_sync(0xffffffffu, ar, o);
-            ai += __shfl_xor_sync(0xffffffffu, ai, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                ar += __shfl_xor_sync(0xffffffffu, ar, o);
+                ai += __shfl_xor_sync(0xffffffffu, ai, o);
+            }
         }
-        const float2 dold = s_d[i];
-        const float2 sy = s_y[i];
-        const float dr = fmaf(sc, dold.x, fmaf(sigma2, ar, -sy.x));
-        const float di = fmaf(sc, dold.y, fmaf(sigma2, ai, -sy.y));
-        if (lane == 0) {
-            dvis_bin[i] = make_float2(dr, di);
-            nrm.add(fmaf(dr, dr, di * di));
+        if (MODE == kFused) {
+            const float2 dold = s_d[i];
+            const float2 sy = s_y[i];
+            dr = fmaf(sc, dold.x, fmaf(sigma2, ar, -sy.x));
+            di = fmaf(sc, dold.y, fmaf(sigma2, ai, -sy.y));
+            if (lane == 0) {
+                dvis_bin[i] = make_float2(dr, di);
+                nrm.add(fmaf(dr, dr, di * di));
+            }
+        } else if (MODE == kGather) {
+            if (lane == 0) dvis_bin[i] = make_float2(ar, ai);
+            cur = nxt;
+            continue;
+        } else {
+            dr = s_d[i].x;
+            di = s_d[i].y;
         }
 #pragma unroll
         for (int it = 0; it < 8; ++it) {
@@ -350,6 +253,11 @@ __device__ __forceinline__ void bin_rows(int i0, int nv, int lane, const int2 *s
 #ifndef FHS_FUSED_MIN_BLOCKS
 #define FHS_FUSED_MIN_BLOCKS 4
 #endif
+// MODE kFused: dvis is the data dual (read and written), grid the forward grid,
+// grid_blk the per-block adjoint grids.  kGather: dvis receives Phi x, grid is
+// the forward grid.  kScatter: dvis holds the visibilities, grid_blk the
+// per-channel output grids (indexed by channel instead of segment).
+template <int MODE>
 __global__ void __launch_bounds__(256, FHS_FUSED_MIN_BLOCKS) degrid_grid_binned_kernel(
     const int2 *__restrict__ meta, const long long *__restrict__ rowptr, const float2 *__restrict__ gval,
     const float2 *__restrict__ y, float2 *__restrict__ dvis, const long long *__restrict__ bin_start,
@@ -370,8 +278,8 @@ __global__ void __launch_bounds__(256, FHS_FUSED_MIN_BLOCKS) degrid_grid_binned_
     const int tile = bin_tile[bin];
     const int l = seg / B;
     const float2 *gl = grid + (long long)l * K;
-    float2 *gb = grid_blk + (long long)seg * K;
-    const float sc = blk_scale[seg];
+    float2 *gb = grid_blk + (long long)(MODE == kScatter ? l : seg) * K;
+    const float sc = MODE == kFused ? blk_scale[seg] : 0.f;
     const long long v0 = bin_start[bin];
     const int nv = int(bin_start[bin + 1] - v0);
     const long long g0 = rowptr[v0];
@@ -379,9 +287,11 @@ __global__ void __launch_bounds__(256, FHS_FUSED_MIN_BLOCKS) degrid_grid_binned_
     for (int i = threadIdx.x; i < nv; i += blockDim.x) {
         s_meta[i] = meta[v0 + i];
         s_off[i] = int(rowptr[v0 + i] - g0);
-        const float2 yy = y[v0 + i];
-        s_y[i] = make_float2(sigma2 * yy.x, sigma2 * yy.y);
-        s_d[i] = dvis[v0 + i];
+        if (MODE == kFused) {
+            const float2 yy = y[v0 + i];
+            s_y[i] = make_float2(sigma2 * yy.x, sigma2 * yy.y);
+        }
+        if (MODE != kGather) s_d[i] = dvis[v0 + i];
     }
     const bool dense = tile >= 0;
     int wy0 = 0, wx0 = 0;
@@ -394,19 +304,38 @@ __global__ void __launch_bounds__(256, FHS_FUSED_MIN_BLOCKS) degrid_grid_binned_
             while (k1 >= K1) k1 -= K1;
             int k2 = wx0 + c;
             while (k2 >= K2) k2 -= K2;
-            s_grid[i] = gl[(long long)k1 * K2 + k2];
-            s_re[i] = 0.f;
-            s_im[i] = 0.f;
+            if (MODE != kScatter) s_grid[i] = gl[(long long)k1 * K2 + k2];
+            if (MODE != kGather) {
+                s_re[i] = 0.f;
+                s_im[i] = 0.f;
+            }
         }
     }
     __syncthreads();
     Kahan nrm;
     if (dense)
-        bin_rows<true>(warp, nv, lane, s_meta, s_off, s_y, s_d, gbin, s_grid, s_re, s_im, wy0, wx0, gl, gb, K1, K2,
-                       sc, sigma2, dvis + v0, nrm);
+        bin_rows<MODE, true>(warp, nv, lane, s_meta, s_off, s_y, s_d, gbin, s_grid, s_re, s_im, wy0, wx0, gl, gb,
+                             K1, K2, sc, sigma2, dvis + v0, nrm);
     else
-        bin_rows<false>(warp, nv, lane, s_meta, s_off, s_y, s_d, gbin, s_grid, s_re, s_im, wy0, wx0, gl, gb, K1,
-                        K2, sc, sigma2, dvis + v0, nrm);
+        bin_rows<MODE, false>(warp, nv, lane, s_meta, s_off, s_y, s_d, gbin, s_grid, s_re, s_im, wy0, wx0, gl, gb,
+                              K1, K2, sc, sigma2, dvis + v0, nrm);
+    if (MODE != kFused) {
+        if (MODE == kScatter && dense) {
+            __syncthreads();
+            for (int q = threadIdx.x; q < kWin * kWin; q += blockDim.x) {
+                const float re = s_re[q], im = s_im[q];
+                if (re != 0.f || im != 0.f) {
+                    const int r = q / kWin, c = q - r * kWin;
+                    int k1 = wy0 + r;
+                    while (k1 >= K1) k1 -= K1;
+                    int k2 = wx0 + c;
+                    while (k2 >= K2) k2 -= K2;
+                    red_add_f2(gb + (long long)k1 * K2 + k2, make_float2(re, im));
+                }
+            }
+        }
+        return;
+    }
     if (lane == 0) s_red[warp] = double(nrm.s) - double(nrm.c);
     __syncthreads();
     if (dense) {
@@ -584,24 +513,26 @@ cudaError_t launch_crop(fhs_problem *p, const float2 *grid, float *x, cudaStream
 }
 
 cudaError_t launch_degrid(fhs_problem *p, const float2 *grid, float2 *vis_sorted, cudaStream_t s) {
-    if (p->n_chunk == 0) return cudaSuccess;
-    degrid_kernel<<<p->n_chunk, 256, 0, s>>>(p->meta, p->rowptr, p->gval, p->chunk_start, p->chunk_seg, p->B, grid,
-                                             p->K, p->K1, p->K2, vis_sorted);
+    if (p->n_bin == 0) return cudaSuccess;
+    degrid_grid_binned_kernel<kGather><<<p->n_bin, 256, 0, s>>>(
+        p->meta, p->rowptr, p->gval, nullptr, vis_sorted, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B,
+        nullptr, nullptr, grid, nullptr, p->K, p->K1, p->K2, 0.f);
     p->n_launch += 1;
     return cudaGetLastError();
 }
 
 cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s) {
-    if (p->n_chunk == 0) return cudaSuccess;
-    grid_kernel<<<p->n_chunk, 256, 0, s>>>(p->meta, p->rowptr, p->gval, p->chunk_start, p->chunk_seg, p->B,
-                                           vis_sorted, p->K, p->K1, p->K2, grid);
+    if (p->n_bin == 0) return cudaSuccess;
+    degrid_grid_binned_kernel<kScatter><<<p->n_bin, 256, 0, s>>>(
+        p->meta, p->rowptr, p->gval, nullptr, const_cast<float2 *>(vis_sorted), p->bin_start, p->bin_seg,
+        p->bin_tile, p->ntx, p->B, nullptr, nullptr, nullptr, grid, p->K, p->K1, p->K2, 0.f);
     p->n_launch += 1;
     return cudaGetLastError();
 }
 
 cudaError_t launch_degrid_grid_fused(fhs_problem *p, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
-    degrid_grid_binned_kernel<<<p->n_bin, 256, 0, s>>>(p->meta, p->rowptr, p->gval, p->y, p->dvis, p->bin_start,
+    degrid_grid_binned_kernel<kFused><<<p->n_bin, 256, 0, s>>>(p->meta, p->rowptr, p->gval, p->y, p->dvis, p->bin_start,
                                                        p->bin_seg, p->bin_tile, p->ntx, p->B, p->blk_scale,
                                                        p->blk_norm2, p->grid_work, p->grid_blk, p->K, p->K1, p->K2,
                                                        float(p->sigma2));
