@@ -253,7 +253,7 @@ def run_gpu(args):
         "phi_adjoint_vis_per_s": ws * Mtot / (phit_ms * 1e-3),
         "e2e": {"value": ws * e2e_iters / e2e_s, "unit": "iter/s", "h2d_bytes_per_step": h2d / e2e_iters,
                 "d2h_bytes_per_step": d2h / e2e_iters,
-                "what": "create from host arrays (sort, G build, power iteration) + %d iterations with one "
+                "what": "create from host arrays (sort, G build, Lanczos norm estimate) + %d iterations with one "
                         "reweighting + image to pinned host" % e2e_iters,
                 "seconds": e2e_s, "setup_seconds": setup_s},
         "gpu_launches": int(launches),

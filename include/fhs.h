@@ -73,8 +73,8 @@ typedef struct fhs_params {
     double  sigma0;          /* nuclear dual step; <= 0 selects 1/max facet cover  */
     double  sigma1;          /* l21 dual step; <= 0 selects 1 (||Psi|| = 1)        */
     double  sigma2;          /* data dual step; <= 0 selects 1/max_l ||Phi_l||^2   */
-    int32_t power_iters;     /* power iterations for ||Phi_l||^2 (default 100)     */
-    double  power_tol;       /* relative tolerance of the power iteration          */
+    int32_t power_iters;     /* Lanczos steps for ||Phi_l||^2 (default 100)        */
+    double  power_tol;       /* relative change of the estimate that stops them    */
 } fhs_params;
 
 /* Fill *p with the defaults (J = 7, 4 levels, 64 w-planes, computed steps). */
@@ -96,7 +96,8 @@ void fhs_default_params(fhs_params *p);
  *               unit-variance whitened noise: eps_{l,b}^2 = (M_l + 2 sqrt(M_l)) M_{l,b}/M_l.
  * Copies everything it needs; builds G on the device (one row per visibility:
  * a (J+2h) x (J+2h) box of KB samples convolved with the w-kernel of its
- * plane); computes ||Phi_l||^2 by power iteration when sigma2 <= 0; sets
+ * plane); computes ||Phi_l||^2 (Lanczos, largest eigenvalue of
+ * Re(Phi_l^H Phi_l)) when sigma2 <= 0; sets
  * X = 0, all duals to 0 and all weights to 1 (Sec. 5.2: zero initialisation).
  * Synchronises `stream` before returning.
  */
@@ -219,8 +220,10 @@ fhs_status fhs_state_size(const fhs_problem *prob, int32_t part, int64_t *n_floa
 fhs_status fhs_get_state(fhs_problem *prob, int32_t part, float *dst_dev, void *stream);
 fhs_status fhs_set_state(fhs_problem *prob, int32_t part, const float *src_dev, void *stream);
 
-/* ||Phi_l||^2 for every channel by power iteration (n_iter steps from a fixed
- * start; returns into the host array norms[L]).  Synchronises.          */
+/* ||Phi_l||^2 for every channel: the largest Ritz value after n_iter Lanczos
+ * steps on Re(Phi_l^H Phi_l) from a fixed start (rises monotonically to the
+ * largest eigenvalue); returns into the host array norms[L].  Uses the
+ * iteration's scratch (the PDFB state is kept).  Synchronises.            */
 fhs_status fhs_operator_norms(fhs_problem *prob, int32_t n_iter, double *norms, void *stream);
 
 /* Tracing: per-phase device time of the PDFB iteration, measured with CUDA

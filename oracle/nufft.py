@@ -239,6 +239,20 @@ class Operator:
     def adjoint_all(self, V: list) -> np.ndarray:
         return np.stack([self.adjoint(V[l], l) for l in range(self.L)])
 
+    def norm2_eigsh(self, l: int, tol: float = 1e-12) -> float:
+        """||Phi_l||^2 as the largest eigenvalue of Re(Phi_l^H Phi_l), by ARPACK's
+        implicitly restarted Lanczos (scipy ``eigsh``) on the FP64 operator."""
+        from scipy.sparse.linalg import LinearOperator, eigsh
+        ny, nx = self.geom.ny, self.geom.nx
+        n = ny * nx
+
+        def mv(x):
+            return np.asarray(self.adjoint(self.forward(np.asarray(x).reshape(ny, nx), l), l)).ravel()
+
+        A = LinearOperator((n, n), matvec=mv, dtype=np.float64)
+        v0 = np.random.default_rng(0).standard_normal(n)
+        return float(eigsh(A, k=1, which="LA", tol=tol, v0=v0, return_eigenvectors=False)[0])
+
     def norm2(self, l: int, n_iter: int = 200, tol: float = 1e-10, seed: int = 0) -> float:
         """||Phi_l||^2 by power iteration on Re(Phi_l^H Phi_l)."""
         rng = np.random.default_rng(seed)

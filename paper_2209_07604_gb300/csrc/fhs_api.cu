@@ -180,9 +180,60 @@ fhs_status adjoint_to_image(fhs_problem *p, const float2 *vis_sorted, float *x, 
     return FHS_OK;
 }
 
-// ||Phi_l||^2 by power iteration from a fixed start; uses Xbar and A_sara as work images.
-fhs_status power_iteration(fhs_problem *p, int n_iter, double tol, std::vector<double> &lam, cudaStream_t s) {
+// y = Re(Phi^H Phi) v for every channel: one pass over G in the normal mode
+// (gather and scatter of each row together) between the two FFTs.  grid_in
+// keeps its zero padding (Z writes the image cells only) and grid_work (Phi^H
+// of the data dual) is iteration state, so the adjoint grids go to the first
+// L grids of grid_blk, which are zero between iterations and zero again after.
+fhs_status apply_normal(fhs_problem *p, const float *v, float *y, cudaStream_t s) {
+    float2 *scratch = p->grid_blk;
+    CU(launch_zpad(p, v, p->grid_in, s));
+    TRY(fft(p, p->grid_in, p->grid_aux, CUFFT_FORWARD, s));
+    CU(launch_normal(p, p->grid_aux, scratch, s));
+    TRY(fft(p, scratch, scratch, CUFFT_INVERSE, s));
+    CU(launch_crop(p, scratch, y, s));
+    CU(cudaMemsetAsync(scratch, 0, sizeof(float2) * p->K * p->L, s));
+    return FHS_OK;
+}
+
+// Largest eigenvalue of the symmetric tridiagonal matrix with diagonal a[0..m)
+// and squared off-diagonal b2[0..m-1), by bisection on the Sturm count (the
+// number of negative pivots of T - x I is the number of eigenvalues below x).
+double tridiag_max_eig(const double *a, const double *b2, int m) {
+    if (m <= 0) return 0.0;
+    double lo = a[0], hi = a[0];
+    for (int i = 0; i < m; ++i) {
+        const double r = (i > 0 ? std::sqrt(b2[i - 1]) : 0.0) + (i + 1 < m ? std::sqrt(b2[i]) : 0.0);
+        lo = std::min(lo, a[i] - r);
+        hi = std::max(hi, a[i] + r);
+    }
+    const double scale = std::max(std::fabs(lo), std::fabs(hi));
+    if (!(scale > 0.0)) return 0.0;
+    auto below = [&](double x) {
+        int c = 0;
+        double q = 1.0;
+        for (int i = 0; i < m; ++i) {
+            q = (a[i] - x) - (i > 0 ? b2[i - 1] / q : 0.0);
+            if (q == 0.0) q = -1e-300 * scale;
+            if (q < 0.0) ++c;
+        }
+        return c;
+    };
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * scale; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (below(mid) == m) hi = mid; else lo = mid;
+    }
+    return hi;
+}
+
+// ||Phi_l||^2 = lambda_max(Re(Phi_l^H Phi_l)) for every channel by the Lanczos
+// recurrence from a fixed random start (the largest Ritz value rises
+// monotonically to lambda_max, far faster than the power method when the top of
+// the spectrum is clustered).  Work vectors: Xbar (v_{j-1}), A_sara (v_j) and the
+// first L*N entries of coef_tmp (w); all three are zero again on return.
+fhs_status norm_estimate(fhs_problem *p, int n_iter, double tol, std::vector<double> &lam, cudaStream_t s) {
     const long long LN = (long long)p->L * p->N;
+    const int L = p->L;
     std::vector<float> x0(LN);
     unsigned long long st = 0x9E3779B97F4A7C15ull;
     for (long long i = 0; i < LN; ++i) {
@@ -190,33 +241,55 @@ fhs_status power_iteration(fhs_problem *p, int n_iter, double tol, std::vector<d
         x0[i] = float(double(st >> 11) * (1.0 / 9007199254740992.0) - 0.5);
     }
     double *norms = p->pnorms;
-    float *x = p->Xbar, *y = p->A_sara;
-    TRY(upload(x, x0.data(), LN, s));
-    CU(cudaMemsetAsync(norms, 0, sizeof(double) * 2 * p->L, s));
-    CU(launch_power_dots(p, x, x, norms, s));
-    CU(launch_power_scale(p, x, x, norms, s));
-    lam.assign(p->L, 0.0);
-    std::vector<double> h(2 * p->L), prev(p->L, 0.0);
-    for (int it = 0; it < n_iter; ++it) {
-        TRY(forward_from_image(p, x, p->vis_tmp, s));
-        TRY(adjoint_to_image(p, p->vis_tmp, y, s));
-        CU(cudaMemsetAsync(norms, 0, sizeof(double) * 2 * p->L, s));
-        CU(launch_power_dots(p, x, y, norms, s));
-        CU(launch_power_scale(p, y, x, norms, s));
-        if ((it + 1) % 5 == 0 || it + 1 == n_iter) {
-            CU(cudaMemcpyAsync(h.data(), norms, sizeof(double) * 2 * p->L, cudaMemcpyDeviceToHost, s));
+    float *vprev = p->Xbar, *v = p->A_sara, *y = p->coef_tmp;
+    double *coef = nullptr;                     // alpha[n_iter][L] then nb2[n_iter + 1][L]
+    const size_t n_coef = (size_t)(2 * n_iter + 1) * L;
+    CU(cudaMallocAsync(reinterpret_cast<void **>(&coef), sizeof(double) * n_coef, s));
+    fhs_status rs = FHS_OK;
+    auto run = [&]() -> fhs_status {
+        double *alpha = coef, *nb2 = coef + (size_t)n_iter * L;
+        CU(cudaMemsetAsync(coef, 0, sizeof(double) * n_coef, s));
+        CU(cudaMemsetAsync(vprev, 0, sizeof(float) * LN, s));
+        TRY(upload(v, x0.data(), LN, s));
+        CU(cudaMemsetAsync(norms, 0, sizeof(double) * 2 * L, s));
+        CU(launch_power_dots(p, v, v, norms, s));
+        CU(launch_power_scale(p, v, v, norms, s));
+        lam.assign(L, 0.0);
+        std::vector<double> ha, hb, prev(L, -1.0), al, bl;
+        for (int j = 0; j < n_iter; ++j) {
+            TRY(apply_normal(p, v, y, s));
+            CU(launch_lanczos_step(p, y, vprev, v, alpha + (size_t)j * L, nb2 + (size_t)j * L, s));
+            std::swap(vprev, v);
+            const bool last = j + 1 == n_iter;
+            if (!last && !(tol > 0.0 && (j + 1) % 5 == 0)) continue;
+            const int m = j + 1;
+            ha.resize((size_t)m * L);
+            hb.resize((size_t)m * L);
+            CU(cudaMemcpyAsync(ha.data(), alpha, sizeof(double) * m * L, cudaMemcpyDeviceToHost, s));
+            CU(cudaMemcpyAsync(hb.data(), nb2 + L, sizeof(double) * m * L, cudaMemcpyDeviceToHost, s));
             CU(cudaStreamSynchronize(s));
             double worst = 0.0;
-            for (int l = 0; l < p->L; ++l) {
-                lam[l] = h[2 * l];
+            al.resize(m);
+            bl.resize(m);
+            for (int l = 0; l < L; ++l) {
+                for (int i = 0; i < m; ++i) {
+                    al[i] = ha[(size_t)i * L + l];
+                    bl[i] = hb[(size_t)i * L + l];
+                }
+                lam[l] = tridiag_max_eig(al.data(), bl.data(), m);
                 worst = std::max(worst, std::fabs(lam[l] - prev[l]) / std::max(std::fabs(lam[l]), 1e-300));
                 prev[l] = lam[l];
             }
-            if (worst < tol) break;
+            if (tol > 0.0 && worst < tol) break;
         }
-    }
+        return FHS_OK;
+    };
+    rs = run();
+    cudaFreeAsync(coef, s);
+    if (rs != FHS_OK) return rs;
     CU(cudaMemsetAsync(p->Xbar, 0, sizeof(float) * LN, s));
     CU(cudaMemsetAsync(p->A_sara, 0, sizeof(float) * LN, s));
+    CU(cudaMemsetAsync(p->coef_tmp, 0, sizeof(float) * LN, s));
     return FHS_OK;
 }
 
@@ -835,7 +908,7 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
         std::vector<double> lam;
         const int n_it = q.power_iters > 0 ? q.power_iters : 100;
         const double tol = q.power_tol > 0 ? q.power_tol : 1e-7;
-        if ((st = guard(power_iteration(p, n_it, tol, lam, s))) != FHS_OK) return st;
+        if ((st = guard(norm_estimate(p, n_it, tol, lam, s))) != FHS_OK) return st;
         p->phi_norm2_max = *std::max_element(lam.begin(), lam.end());
         if (!(p->phi_norm2_max > 0)) return guard(fail(FHS_ERR_ARG, "operator norm is zero (no visibilities?)"));
         p->sigma2 = 1.0 / p->phi_norm2_max;
@@ -1137,7 +1210,7 @@ fhs_status fhs_operator_norms(fhs_problem *p, int32_t n_iter, double *norms, voi
     CU(cudaMemcpyAsync(save, p->Xbar, sizeof(float) * LN, cudaMemcpyDeviceToDevice, s));
     CU(cudaMemcpyAsync(save + LN, p->A_sara, sizeof(float) * LN, cudaMemcpyDeviceToDevice, s));
     std::vector<double> lam;
-    fhs_status st = power_iteration(p, n_iter, 0.0, lam, s);
+    fhs_status st = norm_estimate(p, n_iter, 0.0, lam, s);
     CU(cudaMemcpyAsync(p->Xbar, save, sizeof(float) * LN, cudaMemcpyDeviceToDevice, s));
     CU(cudaMemcpyAsync(p->A_sara, save + LN, sizeof(float) * LN, cudaMemcpyDeviceToDevice, s));
     CU(cudaStreamSynchronize(s));

@@ -172,6 +172,11 @@ cudaError_t launch_degrid(fhs_problem *p, const float2 *grid, float2 *vis_sorted
 cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s);
 cudaError_t launch_crop(fhs_problem *p, const float2 *grid, float *x, cudaStream_t s);
 cudaError_t launch_degrid_grid_fused(fhs_problem *p, cudaStream_t s);
+cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, cudaStream_t s);
+// One Lanczos step after y = A v: y <- w, vprev <- v_{j+1}; alpha_j[l] and
+// nb2_j[L + l] (= beta_{j+1}^2) accumulate, nb2_j[l] = beta_j^2 is read.
+cudaError_t launch_lanczos_step(fhs_problem *p, float *y, float *vprev, const float *v, double *alpha_j,
+                                double *nb2_j, cudaStream_t s);
 cudaError_t launch_block_finalize(fhs_problem *p, cudaStream_t s);
 cudaError_t launch_combine(fhs_problem *p, cudaStream_t s);
 cudaError_t launch_permute_to_caller(fhs_problem *p, const float2 *sorted, float2 *caller, const float *scale_seg,

@@ -162,9 +162,10 @@ struct Kahan {
 
 // Visibilities i = i0, i0 + kWarps, ... of one bin, for one warp.  DENSE: the
 // box lies in the shared window; otherwise gather/scatter in global memory.
-// MODE: kFused (the PDFB data term), kGather (Phi only: vis_bin[i] = G_i . Xhat)
-// or kScatter (Phi^H only: grid += conj(G_i) vis_bin[i]).
-enum { kFused = 0, kGather = 1, kScatter = 2 };
+// MODE: kFused (the PDFB data term), kGather (Phi only: vis_bin[i] = G_i . Xhat),
+// kScatter (Phi^H only: grid += conj(G_i) vis_bin[i]) or kNormal (G^H G in one
+// pass: grid += conj(G_i) (G_i . Xhat), for the operator-norm estimate).
+enum { kFused = 0, kGather = 1, kScatter = 2, kNormal = 3 };
 
 template <int MODE, bool DENSE>
 __device__ __forceinline__ void bin_rows(int i0, int nv, int lane, const int2 *s_meta, const int *s_off,
@@ -225,6 +226,9 @@ __device__ __forceinline__ void bin_rows(int i0, int nv, int lane, const int2 *s
             if (lane == 0) dvis_bin[i] = make_float2(ar, ai);
             cur = nxt;
             continue;
+        } else if (MODE == kNormal) {
+            dr = ar;
+            di = ai;
         } else {
             dr = s_d[i].x;
             di = s_d[i].y;
@@ -256,7 +260,8 @@ __device__ __forceinline__ void bin_rows(int i0, int nv, int lane, const int2 *s
 // MODE kFused: dvis is the data dual (read and written), grid the forward grid,
 // grid_blk the per-block adjoint grids.  kGather: dvis receives Phi x, grid is
 // the forward grid.  kScatter: dvis holds the visibilities, grid_blk the
-// per-channel output grids (indexed by channel instead of segment).
+// per-channel output grids (indexed by channel instead of segment).  kNormal:
+// grid is the forward grid, grid_blk the per-channel output grids, dvis unused.
 template <int MODE>
 __global__ void __launch_bounds__(256, FHS_FUSED_MIN_BLOCKS) degrid_grid_binned_kernel(
     const int2 *__restrict__ meta, const long long *__restrict__ rowptr, const float2 *__restrict__ gval,
@@ -278,7 +283,7 @@ __global__ void __launch_bounds__(256, FHS_FUSED_MIN_BLOCKS) degrid_grid_binned_
     const int tile = bin_tile[bin];
     const int l = seg / B;
     const float2 *gl = grid + (long long)l * K;
-    float2 *gb = grid_blk + (long long)(MODE == kScatter ? l : seg) * K;
+    float2 *gb = grid_blk + (long long)((MODE == kScatter || MODE == kNormal) ? l : seg) * K;
     const float sc = MODE == kFused ? blk_scale[seg] : 0.f;
     const long long v0 = bin_start[bin];
     const int nv = int(bin_start[bin + 1] - v0);
@@ -291,7 +296,7 @@ __global__ void __launch_bounds__(256, FHS_FUSED_MIN_BLOCKS) degrid_grid_binned_
             const float2 yy = y[v0 + i];
             s_y[i] = make_float2(sigma2 * yy.x, sigma2 * yy.y);
         }
-        if (MODE != kGather) s_d[i] = dvis[v0 + i];
+        if (MODE == kFused || MODE == kScatter) s_d[i] = dvis[v0 + i];
     }
     const bool dense = tile >= 0;
     int wy0 = 0, wx0 = 0;
@@ -320,7 +325,7 @@ __global__ void __launch_bounds__(256, FHS_FUSED_MIN_BLOCKS) degrid_grid_binned_
         bin_rows<MODE, false>(warp, nv, lane, s_meta, s_off, s_y, s_d, gbin, s_grid, s_re, s_im, wy0, wx0, gl, gb,
                               K1, K2, sc, sigma2, dvis + v0, nrm);
     if (MODE != kFused) {
-        if (MODE == kScatter && dense) {
+        if ((MODE == kScatter || MODE == kNormal) && dense) {
             __syncthreads();
             for (int q = threadIdx.x; q < kWin * kWin; q += blockDim.x) {
                 const float re = s_re[q], im = s_im[q];
@@ -478,6 +483,63 @@ __global__ void scale_kernel(const float *__restrict__ y, float *__restrict__ x,
         x[(long long)l * N + p] = y[(long long)l * N + p] * f;
 }
 
+// Lanczos three-term recurrence for the largest eigenvalue of
+// A_l = Re(Phi_l^H Phi_l), every channel at once (blockIdx.y = channel):
+//   w = A v_j - beta_j v_{j-1},  alpha_j = <w, v_j>,  w -= alpha_j v_j,
+//   beta_{j+1} = ||w||,  v_{j+1} = w / beta_{j+1}.
+// nb2 holds squared norms (beta^2); reductions are FP64.
+__device__ __forceinline__ void block_add(double v, double *s_part, double *out) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_part[w];
+        atomicAdd(out, t);
+    }
+}
+
+__global__ void __launch_bounds__(256) lanczos_alpha_kernel(float *__restrict__ y, const float *__restrict__ vprev,
+                                                            const float *__restrict__ v, long long N,
+                                                            const double *__restrict__ nb2, double *__restrict__ alpha) {
+    __shared__ double s_part[8];
+    const int l = blockIdx.y;
+    const float beta = float(sqrt(nb2[l]));
+    double a = 0.0;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+        const long long o = (long long)l * N + q;
+        const float w = fmaf(-beta, vprev[o], y[o]);
+        y[o] = w;
+        a += double(w) * double(v[o]);
+    }
+    block_add(a, s_part, alpha + l);
+}
+
+__global__ void __launch_bounds__(256) lanczos_beta_kernel(float *__restrict__ y, const float *__restrict__ v,
+                                                           long long N, const double *__restrict__ alpha,
+                                                           double *__restrict__ nb2_next) {
+    __shared__ double s_part[8];
+    const int l = blockIdx.y;
+    const float a = float(alpha[l]);
+    double b = 0.0;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+        const long long o = (long long)l * N + q;
+        const float w = fmaf(-a, v[o], y[o]);
+        y[o] = w;
+        b += double(w) * double(w);
+    }
+    block_add(b, s_part, nb2_next + l);
+}
+
+__global__ void lanczos_next_kernel(const float *__restrict__ y, float *__restrict__ vnext, long long N,
+                                    const double *__restrict__ nb2_next) {
+    const int l = blockIdx.y;
+    const double nb = nb2_next[l];
+    const float f = nb > 0.0 ? float(1.0 / sqrt(nb)) : 0.f;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x)
+        vnext[(long long)l * N + q] = y[(long long)l * N + q] * f;
+}
+
 inline int grid_for(long long n, int threads, int cap = 152 * 16) {
     long long g = (n + threads - 1) / threads;
     if (g > cap) g = cap;
@@ -526,6 +588,15 @@ cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, 
     degrid_grid_binned_kernel<kScatter><<<p->n_bin, 256, 0, s>>>(
         p->meta, p->rowptr, p->gval, nullptr, const_cast<float2 *>(vis_sorted), p->bin_start, p->bin_seg,
         p->bin_tile, p->ntx, p->B, nullptr, nullptr, nullptr, grid, p->K, p->K1, p->K2, 0.f);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, cudaStream_t s) {
+    if (p->n_bin == 0) return cudaSuccess;
+    degrid_grid_binned_kernel<kNormal><<<p->n_bin, 256, 0, s>>>(
+        p->meta, p->rowptr, p->gval, nullptr, nullptr, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B, nullptr,
+        nullptr, grid, grid_out, p->K, p->K1, p->K2, 0.f);
     p->n_launch += 1;
     return cudaGetLastError();
 }
@@ -587,6 +658,16 @@ cudaError_t launch_power_scale(fhs_problem *p, const float *y, float *x, const d
     dim3 g(grid_for(p->N, 256, 512), p->L);
     scale_kernel<<<g, 256, 0, s>>>(y, x, p->N, norms);
     p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lanczos_step(fhs_problem *p, float *y, float *vprev, const float *v, double *alpha_j,
+                                double *nb2_j, cudaStream_t s) {
+    dim3 g(grid_for(p->N, 256, 256), p->L);
+    lanczos_alpha_kernel<<<g, 256, 0, s>>>(y, vprev, v, p->N, nb2_j, alpha_j);
+    lanczos_beta_kernel<<<g, 256, 0, s>>>(y, v, p->N, alpha_j, nb2_j + p->L);
+    lanczos_next_kernel<<<g, 256, 0, s>>>(y, vprev, p->N, nb2_j + p->L);
+    p->n_launch += 3;
     return cudaGetLastError();
 }
 

@@ -95,15 +95,15 @@ def test_sara_analysis_synthesis(ny, nx, levels):
 
 
 def test_operator_norms():
-    """||Phi_l||^2 by the GPU power iteration against the largest singular
-    value of the explicit FP64 matrix (tiny problem), and against the oracle's
-    power iteration at the parity size (both converge from below; real images
-    pair the singular values, so the gap is small and convergence slow)."""
+    """||Phi_l||^2 by the GPU Lanczos estimate against the largest singular
+    value of the explicit FP64 matrix (tiny problem), and against ARPACK's
+    Lanczos on the FP64 oracle operator at the parity sizes (with and without
+    w-terms)."""
     P = synth.make_problem("tiny")
     prob = fhs.Problem.from_synth(P, mu=0.0, mu_bar=0.0, sigma2=1.0)
     geom = onf.Geometry(P.ny, P.nx)
     op = onf.Operator(P.omega, P.w, P.sigma, geom)
-    gpu = prob.operator_norms(3000)
+    gpu = prob.operator_norms(200)
     for l in range(P.L):
         cols = []
         for k in range(P.ny * P.nx):
@@ -114,14 +114,20 @@ def test_operator_norms():
         smax = np.linalg.svd(np.vstack([A.real, A.imag]), compute_uv=False)[0]
         assert abs(gpu[l] - smax ** 2) < 1e-5 * smax ** 2
     prob.close()
-    P = synth.make_problem("small_128")
-    prob = fhs.Problem.from_synth(P, mu=0.0, mu_bar=0.0, sigma2=1.0)
-    op = onf.Operator(P.omega, P.w, P.sigma, onf.Geometry(P.ny, P.nx))
-    gpu = prob.operator_norms(400)
-    for l in range(P.L):
-        ref = op.norm2(l, n_iter=400, tol=0.0)
-        assert abs(gpu[l] - ref) < 1e-3 * ref
-    prob.close()
+    for name in ("small_128", "mid_w"):
+        P = synth.make_problem(name)
+        prob = fhs.Problem.from_synth(P, mu=0.0, mu_bar=0.0, sigma2=1.0)
+        op = onf.Operator(P.omega, P.w, P.sigma, onf.Geometry(P.ny, P.nx, w_max=P.w_max, n_wplanes=64,
+                                                               pixel_size=P.pixel_size))
+        gpu = prob.operator_norms(80)
+        refs = [op.norm2_eigsh(l) for l in range(P.L)]
+        for l in range(P.L):
+            assert abs(gpu[l] - refs[l]) < 1e-5 * refs[l], (name, l, gpu[l], refs[l])
+        prob.close()
+        # the data step chosen at set-up (sigma2 <= 0): 1 / max_l ||Phi_l||^2
+        prob = fhs.Problem.from_synth(P, mu=0.0, mu_bar=0.0)
+        assert abs(prob.info.sigma2 * max(refs) - 1.0) < 1e-5
+        prob.close()
 
 
 def _run_pair(name, n_iter, n_reweight, mu, mu_bar, **over):

@@ -119,6 +119,8 @@ def test_power_iteration_matches_dense_svd():
     smax = np.linalg.svd(Ar, compute_uv=False)[0]
     # real images pair the singular values, so the gap is small: iterate long
     assert abs(op.norm2(0, n_iter=20000, tol=0.0) - smax ** 2) < 1e-8 * smax ** 2
+    # the Lanczos (ARPACK) estimate reaches the same value directly
+    assert abs(op.norm2_eigsh(0) - smax ** 2) < 1e-10 * smax ** 2
 
 
 def test_psf_peaks_at_phase_centre():
