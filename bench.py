@@ -123,10 +123,11 @@ def _profile_traffic(kernel_file: str):
 
 def fused_kernel_bytes(info, L, B, K, M):
     """Algorithmic HBM bytes of one launch of the single-pass data kernel:
-    G values 8 B/nnz; per row meta 8 B + row pointer 8 B; per visibility y 8 B,
-    dual d read 8 B + write 8 B; the forward grid read once (8 B/cell) and
-    every block grid written back once (8 B/cell/block)."""
-    return info.nnz * 8 + M * (8 + 8 + 8 + 8 + 8) + L * K * 8 + L * B * K * 8
+    G factors 8 B per stored value (2T per row); per row meta 8 B + factor
+    offset 8 B; per visibility y 8 B, dual d read 8 B + write 8 B; the forward
+    grid read once (8 B/cell) and every block grid written back once
+    (8 B/cell/block)."""
+    return info.n_gfac * 8 + M * (8 + 8 + 8 + 8 + 8) + L * K * 8 + L * B * K * 8
 
 
 def run_gpu(args):
@@ -246,7 +247,7 @@ def run_gpu(args):
         "config": {"workload": args.workload, "image": "%dx%d" % (P.ny, P.nx), "channels": L,
                    "subcubes": P.C, "vis_per_channel": M, "blocks": P.B, "facets": "%dx%d" % (P.qy, P.qx),
                    "facet_overlap": P.overlap, "w_max": P.w_max, "nnz_G": info.nnz,
-                   "l2": "inputs larger than L2 (G alone %.1f GB per iteration)" % (info.nnz * 8 / 1e9),
+                   "l2": "inputs larger than L2 (G factors alone %.1f GB per iteration)" % (info.n_gfac * 8 / 1e9),
                    "mu": MU, "mu_bar": MU_BAR},
         "vis_per_s": ws * vis_s,
         "phi_vis_per_s": ws * Mtot / (phi_ms * 1e-3),

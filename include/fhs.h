@@ -111,7 +111,7 @@ void fhs_destroy_problem(fhs_problem *prob);
 
 typedef struct fhs_info {
     int64_t n_vis;           /* M_tot                                              */
-    int64_t nnz;             /* stored entries of G                                */
+    int64_t nnz;             /* entries of G (sum over rows of T^2)                */
     int64_t n_coef;          /* SARA coefficients per channel (Dirac + db1..db8)   */
     int64_t nuclear_size;    /* floats in the nuclear dual (all sub-cubes, facets) */
     int64_t device_bytes;    /* device memory held by the problem                  */
@@ -119,6 +119,8 @@ typedef struct fhs_info {
     int32_t iteration;       /* PDFB iterations done                               */
     double  tau, sigma0, sigma1, sigma2;
     double  phi_norm2_max;   /* max_l ||Phi_l||^2 (0 if sigma2 was given)          */
+    int64_t n_gfac;          /* stored G values: each row is the outer product of
+                                two 1-D factors of T taps, kept as 2T values     */
 } fhs_info;
 
 fhs_status fhs_get_info(const fhs_problem *prob, fhs_info *info);

@@ -53,6 +53,7 @@ class fhs_info(C.Structure):
         ("n_vis", C.c_int64), ("nnz", C.c_int64), ("n_coef", C.c_int64), ("nuclear_size", C.c_int64),
         ("device_bytes", C.c_int64), ("n_facets", C.c_int32), ("iteration", C.c_int32), ("tau", C.c_double),
         ("sigma0", C.c_double), ("sigma1", C.c_double), ("sigma2", C.c_double), ("phi_norm2_max", C.c_double),
+        ("n_gfac", C.c_int64),
     ]
 
 

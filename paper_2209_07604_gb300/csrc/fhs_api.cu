@@ -627,25 +627,29 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
         }
     }, 1);
     std::vector<int2> meta(Mtot);
-    std::vector<long long> rowptr(Mtot + 1);
+    std::vector<long long> fptr(Mtot + 1);
     std::vector<double2> kap(Mtot);
     std::vector<short> plane(Mtot);
     std::vector<float2> yw(Mtot);
-    rowptr[0] = 0;
+    fptr[0] = 0;
     parallel_for(Mtot, [&](long long v0, long long v1) {
         int l = int(std::upper_bound(vis_offsets, vis_offsets + L + 1, (int64_t)v0) - vis_offsets) - 1;
         for (long long v = v0; v < v1; ++v) {
             while (v >= vis_offsets[l + 1]) ++l;
             const long long i = perm[v];
             meta[v] = make_int2(corner1[i] | (corner2[i] << 16), Tv[i]);
-            rowptr[v + 1] = (long long)Tv[i] * Tv[i];
+            fptr[v + 1] = 2LL * Tv[i];
             kap[v] = make_double2(omega[2 * i] * K1 / (2.0 * M_PI), omega[2 * i + 1] * K2 / (2.0 * M_PI));
             plane[v] = short(pl[i]);
             yw[v] = make_float2(float(y[2 * i] / sigma[l]), float(y[2 * i + 1] / sigma[l]));
         }
     });
-    for (long long v = 0; v < Mtot; ++v) rowptr[v + 1] += rowptr[v];
-    p->nnz = rowptr[Mtot];
+    p->nnz = 0;
+    for (long long v = 0; v < Mtot; ++v) {
+        p->nnz += (fptr[v + 1] / 2) * (fptr[v + 1] / 2);
+        fptr[v + 1] += fptr[v];
+    }
+    p->n_fac = fptr[Mtot];
     { std::vector<int> t; t.swap(key); } { std::vector<int> t; t.swap(corner1); } { std::vector<int> t; t.swap(corner2); }
 
     // ---- w-kernel table: planes -P1..P1, per axis up to 2*kMaxWHalf+1 taps
@@ -739,8 +743,8 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
     short *d_plane = nullptr;
     double *d_isg = nullptr;
     if ((st = guard(dev_alloc(p, &p->meta, Mtot, false))) != FHS_OK) return st;
-    if ((st = guard(dev_alloc(p, &p->rowptr, Mtot + 1, false))) != FHS_OK) return st;
-    if ((st = guard(dev_alloc(p, &p->gval, p->nnz, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->fptr, Mtot + 1, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->gfac, p->n_fac, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->y, Mtot, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->dvis, Mtot))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->vis_tmp, Mtot))) != FHS_OK) return st;
@@ -760,7 +764,7 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
     if ((st = guard(dev_alloc(p, &d_isg, p->n_seg, false))) != FHS_OK) return st;
     std::vector<float> ones(p->n_seg, 1.0f);
     if ((st = guard(upload(p->meta, meta.data(), Mtot, s))) != FHS_OK) return st;
-    if ((st = guard(upload(p->rowptr, rowptr.data(), Mtot + 1, s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->fptr, fptr.data(), Mtot + 1, s))) != FHS_OK) return st;
     if ((st = guard(upload(p->y, yw.data(), Mtot, s))) != FHS_OK) return st;
     if ((st = guard(upload(p->perm, perm.data(), Mtot, s))) != FHS_OK) return st;
     if ((st = guard(upload(p->d_seg_off, p->seg_off.data(), p->n_seg + 1, s))) != FHS_OK) return st;
@@ -972,11 +976,8 @@ fhs_status fhs_estimate_bytes(const fhs_params *params, const double *w, int64_t
     const fhs_params &q = *params;
     const long long L = q.n_channels, B = q.n_blocks, C = q.n_subcubes, Lc = L / C;
     const long long N = (long long)q.ny * q.nx, K = 4 * N, M = n_vis;
-    long long nnz = 0;
-    for (long long i = 0; i < M; ++i) {
-        const long long T = row_side(w ? w[i] : 0.0, q);
-        nnz += T * T;
-    }
+    long long n_fac = 0;
+    for (long long i = 0; i < M; ++i) n_fac += 2LL * row_side(w ? w[i] : 0.0, q);
     const long long nseg = L * B, nchunk = M / 32 + nseg + 1, nbin = M / 32 + 2 * nseg + 1;
     const SaraConst c = sara_layout(q.ny, q.nx, q.wavelet_levels);
     long long nuc = 0;
@@ -985,7 +986,7 @@ fhs_status fhs_estimate_bytes(const fhs_params *params, const double *w, int64_t
     nuc *= C;
     const long long Q = (long long)fac.size();
     long long r = 0;
-    r += 8 * M + 8 * (M + 1) + 8 * nnz + 8 * M * 4;                  // meta, rowptr, G, y, d, scratch, perm
+    r += 8 * M + 8 * (M + 1) + 8 * n_fac + 8 * M * 4;                // meta, factor offsets, G factors, y, d, scratch, perm
     r += 8 * (nseg + 1) + 8 * nseg + 8 * nseg + 4 * nseg;            // segments, norms, eps, scales
     r += 8 * (nbin + 1) + 8 * nbin + 8 * (nchunk + 1) + 4 * nchunk;  // bins and chunks
     r += 4 * (q.ny + q.nx);                                          // Z scaling
@@ -1050,6 +1051,7 @@ fhs_status fhs_get_info(const fhs_problem *p, fhs_info *info) {
     info->sigma1 = p->sigma1;
     info->sigma2 = p->sigma2;
     info->phi_norm2_max = p->phi_norm2_max;
+    info->n_gfac = p->n_fac;
     return FHS_OK;
 }
 

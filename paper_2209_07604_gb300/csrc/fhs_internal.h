@@ -65,15 +65,15 @@ struct fhs_problem {
     fhs_params prm;
     int L = 0, C = 0, Lc = 0, B = 0, ny = 0, nx = 0, K1 = 0, K2 = 0, J = 7;
     long long N = 0, K = 0;                   // pixels and grid cells per channel
-    long long Mtot = 0, nnz = 0;
+    long long Mtot = 0, nnz = 0, n_fac = 0;   // nnz: entries of G (sum T^2); n_fac: stored factors (sum 2T)
     std::vector<long long> vis_off;           // [L+1]
     std::vector<long long> seg_off;           // [L*B+1] sorted-order offsets of (l,b) segments
     int n_seg = 0;
 
     // data term (sorted visibility order)
     int2 *meta = nullptr;                     // {c1 | c2 << 16, T}
-    long long *rowptr = nullptr;              // [Mtot+1]
-    float2 *gval = nullptr;                   // [nnz] whitened G values
+    long long *fptr = nullptr;                // [Mtot+1] offsets of the row factors
+    float2 *gfac = nullptr;                   // [n_fac] per row: g1 / sigma (T values), g2 (T values)
     float2 *y = nullptr;                      // whitened data
     float2 *dvis = nullptr;                   // data dual storage d (v = scale_b d)
     long long *perm = nullptr;                // sorted -> caller index

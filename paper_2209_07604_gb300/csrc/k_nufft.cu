@@ -1,12 +1,14 @@
 // Measurement operator Phi_l = Theta_l G_l F Z (Sec. 2.1, Eq. 1) and the
 // data-fidelity dual step of the l2 balls (Eq. 2) on sm_103a.
 //
-// G is stored as "box CSR": every row's support is a T x T box of the
+// G in factored box form: every row's support is a T x T box of the
 // oversampled grid (KB taps convolved with the w-kernel of its plane,
-// Sec. 3.2), so a row keeps its wrapped corner and T instead of T^2 column
-// indices (8 bytes per non-zero instead of 12).  Rows are sorted by grid
-// tile inside each (channel, block) segment, so the warps of one CTA touch
-// neighbouring grid cells (L1/L2 reuse).
+// Sec. 3.2), and both the KB window and the small-field w-chirp separate over
+// the two grid axes, so the row is the outer product g1 (x) g2 of two 1-D
+// rows of T taps.  A row keeps its wrapped box corner, T and the 2T factor
+// values (16 T bytes instead of 8 T^2 for the entries); the kernels form the
+// T^2 products on the fly.  Rows are sorted by grid tile inside each
+// (channel, block) segment, so the warps of one CTA touch neighbouring cells.
 #include "fhs_internal.h"
 
 #include <cstdio>
@@ -47,15 +49,16 @@ __device__ __forceinline__ int seg_of(const long long *seg_off, int n_seg, long 
     return lo;
 }
 
-// One warp per row: KB samples (7 per axis, FP64), discrete convolution with
-// the w-kernel of the row's plane, outer product, whitening, store as float2.
+// One warp per row: KB samples (J per axis, FP64), discrete convolution with
+// the w-kernel of the row's plane, whitening; the row of G is the outer
+// product g1 (x) g2 of the two 1-D factors, stored as T values of g1 (times
+// 1/sigma) followed by T values of g2, in FP32.
 __global__ void __launch_bounds__(256) build_g_kernel(
-    const int2 *__restrict__ meta, const long long *__restrict__ rowptr, float2 *__restrict__ gval,
+    const int2 *__restrict__ meta, const long long *__restrict__ fptr, float2 *__restrict__ gfac,
     const double2 *__restrict__ kap, const short *__restrict__ plane, const double2 *__restrict__ wk,
     const long long *__restrict__ seg_off, int n_seg, const double *__restrict__ inv_sigma_seg,
     long long Mtot, int J, double beta, double inv_i0b) {
     __shared__ double s_kb[kWarps][2][16];
-    __shared__ double2 s_g[kWarps][2][16];
     __shared__ double s_inv_k2[kI0Terms];
     for (int k = threadIdx.x; k < kI0Terms; k += blockDim.x) s_inv_k2[k] = k ? 1.0 / (double(k) * double(k)) : 0.0;
     __syncthreads();
@@ -82,31 +85,11 @@ __global__ void __launch_bounds__(256) build_g_kernel(
                 acc.x += c.x * k;
                 acc.y += c.y * k;
             }
-            s_g[warp][dim][i] = acc;
-        }
-        __syncwarp();
-        const double isg = inv_sigma_seg[seg_of(seg_off, n_seg, v)];
-        const long long base = rowptr[v];
-        for (int e = lane; e < T * T; e += 32) {
-            const int t1 = e / T, t2 = e - t1 * T;
-            const double2 a = s_g[warp][0][t1], b = s_g[warp][1][t2];
-            const double re = (a.x * b.x - a.y * b.y) * isg;
-            const double im = (a.x * b.y + a.y * b.x) * isg;
-            gval[base + e] = make_float2(float(re), float(im));
+            const double f = dim ? 1.0 : inv_sigma_seg[seg_of(seg_off, n_seg, v)];
+            gfac[fptr[v] + dim * T + i] = make_float2(float(acc.x * f), float(acc.y * f));
         }
         __syncwarp();
     }
-}
-
-// Grid cell of entry e of a row with corner (c1, c2) and side T.
-__device__ __forceinline__ int cell_index(int e, int T, float invT, int c1, int c2, int K1, int K2) {
-    const int t1 = __float2int_rz((float(e) + 0.5f) * invT);
-    const int t2 = e - t1 * T;
-    int k1 = c1 + t1;
-    k1 -= (k1 >= K1) ? K1 : 0;
-    int k2 = c2 + t2;
-    k2 -= (k2 >= K2) ? K2 : 0;
-    return k1 * K2 + k2;
 }
 
 __device__ __forceinline__ void red_add_f2(float2 *addr, float2 v) {
@@ -134,18 +117,13 @@ constexpr int kWin = kTile + 15;        // boxes have T <= 16
 #endif
 constexpr int kBinMax = FHS_BIN_MAX;    // visibilities per bin (host splits longer runs)
 
-struct RowRegs {
-    float2 g[8];
-};
-
-// Issue the loads of one row's values (lane e, e + 32, ...); consumed later.
-__device__ __forceinline__ void load_row(RowRegs &r, const float2 *__restrict__ gv, int n, int lane) {
-#pragma unroll
-    for (int it = 0; it < 8; ++it) {
-        if (32 * it >= n) break;            // warp-uniform: skip unused slots
-        const int e = lane + 32 * it;
-        if (e < n) r.g[it] = __ldcs(gv + e);
-    }
+// Factors of one row for one warp: lane t < T holds g1[t], lane 16 + t holds
+// g2[t]; the other lanes hold 0.
+__device__ __forceinline__ float2 load_factors(const float2 *__restrict__ f, int T, int lane) {
+    const int half = lane >> 4, col = lane & 15;
+    float2 r = make_float2(0.f, 0.f);
+    if (col < T) r = __ldcs(f + half * T + col);
+    return r;
 }
 
 // Compensated (Kahan) FP32 accumulation for the block norms: a warp sums at
@@ -165,90 +143,109 @@ struct Kahan {
 // MODE: kFused (the PDFB data term), kGather (Phi only: vis_bin[i] = G_i . Xhat),
 // kScatter (Phi^H only: grid += conj(G_i) vis_bin[i]) or kNormal (G^H G in one
 // pass: grid += conj(G_i) (G_i . Xhat), for the operator-norm estimate).
+//
+// Row G_i = g1 (x) g2 over the T x T box: lane (half, col) = (lane / 16,
+// lane % 16) owns box column col and rows t1 = half, half + 2, ...; it forms
+// b = sum_t1 g1[t1] X[t1][col], and the warp reduces g2[col] b over lanes.
+// The scatter adds conj(g1[t1]) (conj(g2[col]) d) to the same cells.
 enum { kFused = 0, kGather = 1, kScatter = 2, kNormal = 3 };
 
 template <int MODE, bool DENSE>
 __device__ __forceinline__ void bin_rows(int i0, int nv, int lane, const int2 *s_meta, const int *s_off,
-                                         const float2 *s_y, const float2 *s_d, const float2 *__restrict__ gbin,
+                                         const float2 *s_y, const float2 *s_d, const float2 *__restrict__ fbin,
                                          const float2 *s_grid, float *s_re, float *s_im, int wy0, int wx0,
                                          const float2 *__restrict__ gl, float2 *__restrict__ gb, int K1, int K2,
                                          float sc, float sigma2, float2 *__restrict__ dvis_bin, Kahan &nrm) {
-    RowRegs cur, nxt;
-    int i = i0;
-    if (i < nv) load_row(cur, gbin + s_off[i], s_meta[i].y * s_meta[i].y, lane);
-    for (; i < nv; i += kWarps) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int half = lane >> 4, col = lane & 15;
+    float2 fac = make_float2(0.f, 0.f);
+    if (i0 < nv) fac = load_factors(fbin + s_off[i0], s_meta[i0].y, lane);
+    for (int i = i0; i < nv; i += kWarps) {
         const int in = i + kWarps;
-        if (in < nv) load_row(nxt, gbin + s_off[in], s_meta[in].y * s_meta[in].y, lane);
+        float2 fnx = make_float2(0.f, 0.f);
+        if (in < nv) fnx = load_factors(fbin + s_off[in], s_meta[in].y, lane);
         const int2 m = s_meta[i];
-        const int T = m.y, n = T * T;
+        const int T = m.y;
         const int c1 = m.x & 0xffff, c2 = (int)((unsigned)m.x >> 16);
-        const float invT = 1.0f / float(T);
-        int idx[8];
-        float ar = 0.f, ai = 0.f;
+        const bool cin = col < T;
+        const float g2x = __shfl_sync(FULL, fac.x, 16 + col), g2y = __shfl_sync(FULL, fac.y, 16 + col);
+        // this lane's cell in box row t1 = half (rows advance by 2 per step)
+        int ib = 0, k1 = 0, k2 = 0;
+        if (DENSE) {
+            ib = (c1 - wy0 + half) * kWin + (c2 - wx0 + col);
+        } else {
+            k1 = c1 + half;
+            k2 = c2 + col;
+            k2 -= (k2 >= K2) ? K2 : 0;
+        }
+        float dr = 0.f, di = 0.f;
+        if (MODE != kScatter) {
+            float br = 0.f, bi = 0.f;
 #pragma unroll
-        for (int it = 0; it < 8; ++it) {
-            if (32 * it >= n) break;
-            const int e = lane + 32 * it;
-            if (e < n) {
-                if (DENSE) {
-                    const int t1 = __float2int_rz((float(e) + 0.5f) * invT);
-                    const int t2 = e - t1 * T;
-                    idx[it] = (c1 - wy0 + t1) * kWin + (c2 - wx0 + t2);
-                } else {
-                    idx[it] = cell_index(e, T, invT, c1, c2, K1, K2);
-                }
-                if (MODE != kScatter) {
-                    const float2 x = DENSE ? s_grid[idx[it]] : gl[idx[it]];
-                    const float2 g = cur.g[it];
-                    ar = fmaf(g.x, x.x, fmaf(-g.y, x.y, ar));
-                    ai = fmaf(g.x, x.y, fmaf(g.y, x.x, ai));
+            for (int k = 0; k < 8; ++k) {
+                if (2 * k >= T) break;                 // warp-uniform
+                const int t1 = 2 * k + half;
+                const float g1x = __shfl_sync(FULL, fac.x, t1), g1y = __shfl_sync(FULL, fac.y, t1);
+                if (cin && t1 < T) {
+                    float2 x;
+                    if (DENSE) {
+                        x = s_grid[ib + 2 * k * kWin];
+                    } else {
+                        int kk = k1 + 2 * k;
+                        kk -= (kk >= K1) ? K1 : 0;
+                        x = gl[(long long)kk * K2 + k2];
+                    }
+                    br = fmaf(g1x, x.x, fmaf(-g1y, x.y, br));
+                    bi = fmaf(g1x, x.y, fmaf(g1y, x.x, bi));
                 }
             }
-        }
-        float dr, di;
-        if (MODE != kScatter) {
+            float ar = fmaf(br, g2x, -bi * g2y), ai = fmaf(br, g2y, bi * g2x);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                ar += __shfl_xor_sync(0xffffffffu, ar, o);
-                ai += __shfl_xor_sync(0xffffffffu, ai, o);
+                ar += __shfl_xor_sync(FULL, ar, o);
+                ai += __shfl_xor_sync(FULL, ai, o);
             }
-        }
-        if (MODE == kFused) {
-            const float2 dold = s_d[i];
-            const float2 sy = s_y[i];
-            dr = fmaf(sc, dold.x, fmaf(sigma2, ar, -sy.x));
-            di = fmaf(sc, dold.y, fmaf(sigma2, ai, -sy.y));
-            if (lane == 0) {
-                dvis_bin[i] = make_float2(dr, di);
-                nrm.add(fmaf(dr, dr, di * di));
+            if (MODE == kFused) {
+                const float2 dold = s_d[i];
+                const float2 sy = s_y[i];
+                dr = fmaf(sc, dold.x, fmaf(sigma2, ar, -sy.x));
+                di = fmaf(sc, dold.y, fmaf(sigma2, ai, -sy.y));
+                if (lane == 0) {
+                    dvis_bin[i] = make_float2(dr, di);
+                    nrm.add(fmaf(dr, dr, di * di));
+                }
+            } else if (MODE == kGather) {
+                if (lane == 0) dvis_bin[i] = make_float2(ar, ai);
+                fac = fnx;
+                continue;
+            } else {
+                dr = ar;
+                di = ai;
             }
-        } else if (MODE == kGather) {
-            if (lane == 0) dvis_bin[i] = make_float2(ar, ai);
-            cur = nxt;
-            continue;
-        } else if (MODE == kNormal) {
-            dr = ar;
-            di = ai;
         } else {
             dr = s_d[i].x;
             di = s_d[i].y;
         }
+        // e = conj(g2[col]) d; cell (t1, col) += conj(g1[t1]) e
+        const float er = fmaf(g2x, dr, g2y * di), ei = fmaf(g2x, di, -g2y * dr);
 #pragma unroll
-        for (int it = 0; it < 8; ++it) {
-            if (32 * it >= n) break;
-            const int e = lane + 32 * it;
-            if (e < n) {
-                const float2 g = cur.g[it];
-                const float pr = g.x * dr + g.y * di, pi = g.x * di - g.y * dr;
+        for (int k = 0; k < 8; ++k) {
+            if (2 * k >= T) break;
+            const int t1 = 2 * k + half;
+            const float g1x = __shfl_sync(FULL, fac.x, t1), g1y = __shfl_sync(FULL, fac.y, t1);
+            if (cin && t1 < T) {
+                const float pr = fmaf(g1x, er, g1y * ei), pi = fmaf(g1x, ei, -g1y * er);
                 if (DENSE) {
-                    atomicAdd(s_re + idx[it], pr);
-                    atomicAdd(s_im + idx[it], pi);
+                    atomicAdd(s_re + ib + 2 * k * kWin, pr);
+                    atomicAdd(s_im + ib + 2 * k * kWin, pi);
                 } else {
-                    red_add_f2(gb + idx[it], make_float2(pr, pi));
+                    int kk = k1 + 2 * k;
+                    kk -= (kk >= K1) ? K1 : 0;
+                    red_add_f2(gb + (long long)kk * K2 + k2, make_float2(pr, pi));
                 }
             }
         }
-        cur = nxt;
+        fac = fnx;
     }
 }
 
@@ -264,7 +261,7 @@ __device__ __forceinline__ void bin_rows(int i0, int nv, int lane, const int2 *s
 // grid is the forward grid, grid_blk the per-channel output grids, dvis unused.
 template <int MODE>
 __global__ void __launch_bounds__(256, FHS_FUSED_MIN_BLOCKS) degrid_grid_binned_kernel(
-    const int2 *__restrict__ meta, const long long *__restrict__ rowptr, const float2 *__restrict__ gval,
+    const int2 *__restrict__ meta, const long long *__restrict__ fptr, const float2 *__restrict__ gfac,
     const float2 *__restrict__ y, float2 *__restrict__ dvis, const long long *__restrict__ bin_start,
     const int *__restrict__ bin_seg, const int *__restrict__ bin_tile, int ntx, int B,
     const float *__restrict__ blk_scale, double *__restrict__ blk_norm2, const float2 *__restrict__ grid,
@@ -273,7 +270,7 @@ __global__ void __launch_bounds__(256, FHS_FUSED_MIN_BLOCKS) degrid_grid_binned_
     __shared__ float s_re[kWin * kWin];
     __shared__ float s_im[kWin * kWin];
     __shared__ int2 s_meta[kBinMax];
-    __shared__ int s_off[kBinMax];        // row offset relative to the bin's first value
+    __shared__ int s_off[kBinMax];        // factor offset relative to the bin's first row
     __shared__ float2 s_y[kBinMax];       // sigma2 * y
     __shared__ float2 s_d[kBinMax];
     __shared__ double s_red[kWarps];
@@ -287,11 +284,11 @@ __global__ void __launch_bounds__(256, FHS_FUSED_MIN_BLOCKS) degrid_grid_binned_
     const float sc = MODE == kFused ? blk_scale[seg] : 0.f;
     const long long v0 = bin_start[bin];
     const int nv = int(bin_start[bin + 1] - v0);
-    const long long g0 = rowptr[v0];
-    const float2 *gbin = gval + g0;
+    const long long g0 = fptr[v0];
+    const float2 *fbin = gfac + g0;
     for (int i = threadIdx.x; i < nv; i += blockDim.x) {
         s_meta[i] = meta[v0 + i];
-        s_off[i] = int(rowptr[v0 + i] - g0);
+        s_off[i] = int(fptr[v0 + i] - g0);
         if (MODE == kFused) {
             const float2 yy = y[v0 + i];
             s_y[i] = make_float2(sigma2 * yy.x, sigma2 * yy.y);
@@ -319,10 +316,10 @@ __global__ void __launch_bounds__(256, FHS_FUSED_MIN_BLOCKS) degrid_grid_binned_
     __syncthreads();
     Kahan nrm;
     if (dense)
-        bin_rows<MODE, true>(warp, nv, lane, s_meta, s_off, s_y, s_d, gbin, s_grid, s_re, s_im, wy0, wx0, gl, gb,
+        bin_rows<MODE, true>(warp, nv, lane, s_meta, s_off, s_y, s_d, fbin, s_grid, s_re, s_im, wy0, wx0, gl, gb,
                              K1, K2, sc, sigma2, dvis + v0, nrm);
     else
-        bin_rows<MODE, false>(warp, nv, lane, s_meta, s_off, s_y, s_d, gbin, s_grid, s_re, s_im, wy0, wx0, gl, gb,
+        bin_rows<MODE, false>(warp, nv, lane, s_meta, s_off, s_y, s_d, fbin, s_grid, s_re, s_im, wy0, wx0, gl, gb,
                               K1, K2, sc, sigma2, dvis + v0, nrm);
     if (MODE != kFused) {
         if ((MODE == kScatter || MODE == kNormal) && dense) {
@@ -554,7 +551,7 @@ cudaError_t launch_build_g(fhs_problem *p, const double2 *kap, const short *plan
                            cudaStream_t s) {
     const double beta = kb_beta(p->J, 2.0);
     build_g_kernel<<<grid_for(p->Mtot, kWarps, 152 * 64), 256, 0, s>>>(
-        p->meta, p->rowptr, p->gval, kap, plane, wk_table, p->d_seg_off, p->n_seg, inv_sigma_seg, p->Mtot, p->J,
+        p->meta, p->fptr, p->gfac, kap, plane, wk_table, p->d_seg_off, p->n_seg, inv_sigma_seg, p->Mtot, p->J,
         beta, 1.0 / bessel_i0(beta));
     p->n_launch += 1;
     return cudaGetLastError();
@@ -577,7 +574,7 @@ cudaError_t launch_crop(fhs_problem *p, const float2 *grid, float *x, cudaStream
 cudaError_t launch_degrid(fhs_problem *p, const float2 *grid, float2 *vis_sorted, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
     degrid_grid_binned_kernel<kGather><<<p->n_bin, 256, 0, s>>>(
-        p->meta, p->rowptr, p->gval, nullptr, vis_sorted, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B,
+        p->meta, p->fptr, p->gfac, nullptr, vis_sorted, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B,
         nullptr, nullptr, grid, nullptr, p->K, p->K1, p->K2, 0.f);
     p->n_launch += 1;
     return cudaGetLastError();
@@ -586,7 +583,7 @@ cudaError_t launch_degrid(fhs_problem *p, const float2 *grid, float2 *vis_sorted
 cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
     degrid_grid_binned_kernel<kScatter><<<p->n_bin, 256, 0, s>>>(
-        p->meta, p->rowptr, p->gval, nullptr, const_cast<float2 *>(vis_sorted), p->bin_start, p->bin_seg,
+        p->meta, p->fptr, p->gfac, nullptr, const_cast<float2 *>(vis_sorted), p->bin_start, p->bin_seg,
         p->bin_tile, p->ntx, p->B, nullptr, nullptr, nullptr, grid, p->K, p->K1, p->K2, 0.f);
     p->n_launch += 1;
     return cudaGetLastError();
@@ -595,7 +592,7 @@ cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, 
 cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
     degrid_grid_binned_kernel<kNormal><<<p->n_bin, 256, 0, s>>>(
-        p->meta, p->rowptr, p->gval, nullptr, nullptr, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B, nullptr,
+        p->meta, p->fptr, p->gfac, nullptr, nullptr, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B, nullptr,
         nullptr, grid, grid_out, p->K, p->K1, p->K2, 0.f);
     p->n_launch += 1;
     return cudaGetLastError();
@@ -603,7 +600,7 @@ cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, 
 
 cudaError_t launch_degrid_grid_fused(fhs_problem *p, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
-    degrid_grid_binned_kernel<kFused><<<p->n_bin, 256, 0, s>>>(p->meta, p->rowptr, p->gval, p->y, p->dvis, p->bin_start,
+    degrid_grid_binned_kernel<kFused><<<p->n_bin, 256, 0, s>>>(p->meta, p->fptr, p->gfac, p->y, p->dvis, p->bin_start,
                                                        p->bin_seg, p->bin_tile, p->ntx, p->B, p->blk_scale,
                                                        p->blk_norm2, p->grid_work, p->grid_blk, p->K, p->K1, p->K2,
                                                        float(p->sigma2));

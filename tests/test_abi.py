@@ -98,9 +98,10 @@ def test_params_struct_layout(lib):
     assert C.sizeof(fhs.fhs_params) == 152
 
 
-def test_estimate_bytes_counts_g_entries(lib):
+def test_estimate_bytes_counts_g_factors(lib):
     """The footprint estimate is host-only; with the same visibility count,
-    w-terms change it by exactly 8 bytes per extra G entry (box side 7 + 2h)."""
+    w-terms change it by exactly 8 bytes per extra stored G value (each row
+    keeps its two 1-D factors of 7 + 2h taps)."""
     p = fhs.default_params(ny=64, nx=64, n_channels=2, n_subcubes=1, n_blocks=2, qy=2, qx=2, facet_overlap=0.1,
                            w_max=2000.0, pixel_size=1e-4)
     M = 5000
@@ -110,7 +111,7 @@ def test_estimate_bytes_counts_g_entries(lib):
     P1 = p.n_wplanes - 1
     pa = np.minimum(np.floor(np.abs(w) / (2000.0 / P1) + 0.5).astype(np.int64), P1)
     T = 7 + 2 * ((8 * pa + P1) // (2 * P1))
-    assert r1 - r0 == 8 * int(np.sum(T * T - 49))
+    assert r1 - r0 == 8 * int(np.sum(2 * T - 14))
     assert pk0 > r0 and pk1 > r1
     r2, _ = fhs.fhs_estimate_bytes(p, np.zeros(2 * M), 2 * M)
     assert r2 > r0
