@@ -105,8 +105,9 @@ def _peaks():
 
 
 def _profile_traffic(kernel_file: str):
-    """dram bytes per launch of the fused kernel from the committed ncu summary,
-    valid only while the kernel source is unchanged (sha256 recorded there)."""
+    """(dram bytes per launch, limiter) of the fused kernel from the committed
+    ncu summary, valid only while the kernel source is unchanged (sha256
+    recorded there); (None, None) otherwise."""
     path = os.path.join(ROOT, "profiles", "degrid_grid_fused_vla_1024.md")
     src = os.path.join(ROOT, "paper_2209_07604_gb300", "csrc", kernel_file)
     try:
@@ -114,11 +115,12 @@ def _profile_traffic(kernel_file: str):
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
         m_sha = re.search(r"kernel source sha256:\s*([0-9a-f]{64})", txt)
         m_tr = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", txt)
+        m_lim = re.search(r"^limiter:\s*(.+)$", txt, re.M)
         if m_sha and m_tr and m_sha.group(1) == sha:
-            return float(m_tr.group(1))
+            return float(m_tr.group(1)), (m_lim.group(1).strip() if m_lim else None)
     except OSError:
         pass
-    return None
+    return None, None
 
 
 def fused_kernel_bytes(info, L, B, K, M):
@@ -228,7 +230,7 @@ def run_gpu(args):
     kbytes = fused_kernel_bytes(info, L, P.B, K, Mtot)
     k_ms = phases["degrid_grid"] / max(n_prof, 1)
     achieved = kbytes / (k_ms * 1e-3) / 1e9
-    traffic = _profile_traffic("k_nufft.cu")
+    traffic, limiter = _profile_traffic("k_nufft.cu")
     # visibilities through Phi and Phi^H per second inside the PDFB iteration
     vis_s = Mtot / (ms_step * 1e-3)
     out = {
@@ -261,7 +263,7 @@ def run_gpu(args):
         "phases_ms_per_step": {k: v / max(n_prof, 1) for k, v in phases.items()},
         "roofline": {"kernel": "degrid_grid_fused", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                     "algorithmic_bytes": kbytes, "peak_source": peak_kind},
+                     "algorithmic_bytes": kbytes, "peak_source": peak_kind, "limiter": limiter},
         "clocks": clk.summary(),
         "device_bytes": info.device_bytes,
         "generate_seconds": gen_s,
