@@ -230,7 +230,7 @@ def run_gpu(args):
     kbytes = fused_kernel_bytes(info, L, P.B, K, Mtot)
     k_ms = phases["degrid_grid"] / max(n_prof, 1)
     achieved = kbytes / (k_ms * 1e-3) / 1e9
-    traffic, limiter = _profile_traffic("k_nufft.cu")
+    traffic, limiter = _profile_traffic("k_binned.cu")
     # visibilities through Phi and Phi^H per second inside the PDFB iteration
     vis_s = Mtot / (ms_step * 1e-3)
     out = {

@@ -7,8 +7,8 @@
 // the two grid axes, so the row is the outer product g1 (x) g2 of two 1-D
 // rows of T taps.  A row keeps its wrapped box corner, T and the 2T factor
 // values (16 T bytes instead of 8 T^2 for the entries); the kernels form the
-// T^2 products on the fly.  Rows are sorted by grid tile inside each
-// (channel, block) segment, so the warps of one CTA touch neighbouring cells.
+// T^2 products on the fly (the pass over G is in k_binned.cu).  This file
+// builds G and holds the grid, reduction and Lanczos helpers around it.
 #include "fhs_internal.h"
 
 #include <cstdio>
@@ -19,24 +19,22 @@ namespace {
 
 constexpr int kWarps = 8;               // warps per CTA for visibility kernels
 
-// Terms of the I0 power series kept (q = (x/2)^2 <= (beta/2)^2 < 100 for
-// J <= 16 at 2x oversampling; the series has converged to 1e-17 long before).
-constexpr int kI0Terms = 96;
+// Terms of the I0 power series kept: q = (x/2)^2 <= (beta/2)^2 < 87 for
+// J <= 8 at 2x oversampling, where the terms beyond k = 35 are below 1e-18 of
+// the sum.
+constexpr int kI0Terms = 40;
 
 // KB window at offset t: I0(beta sqrt(1 - (2t/J)^2)) / I0(beta), with
-// I0(x) = sum_k q^k / (k!)^2 (q = x^2 / 4) summed in FP64.  inv_k2[k] = 1/k^2
-// turns the FP64 division of each term into a multiplication.
-__device__ __forceinline__ double kb_eval(double t, int J, double beta, double inv_i0b, const double *inv_k2) {
+// I0(x) = sum_k c_k q^k, c_k = 1/(k!)^2, q = x^2/4, by Horner's rule in FP64
+// (all terms positive: no cancellation; one FMA per term, no division).
+__device__ __forceinline__ double kb_eval(double t, int J, double beta, double inv_i0b, const double *c) {
     const double u = 2.0 * t / double(J);
     const double r = 1.0 - u * u;
     if (r < 0.0) return 0.0;
     const double q = 0.25 * beta * beta * r;
-    double term = 1.0, sum = 1.0;
-    for (int k = 1; k < kI0Terms; ++k) {
-        term *= q * inv_k2[k];
-        sum += term;
-        if (term < 1e-17 * sum) break;
-    }
+    double sum = c[kI0Terms - 1];
+#pragma unroll 8
+    for (int k = kI0Terms - 2; k >= 0; --k) sum = fma(sum, q, c[k]);
     return sum * inv_i0b;
 }
 
@@ -59,8 +57,14 @@ __global__ void __launch_bounds__(256) build_g_kernel(
     const long long *__restrict__ seg_off, int n_seg, const double *__restrict__ inv_sigma_seg,
     long long Mtot, int J, double beta, double inv_i0b) {
     __shared__ double s_kb[kWarps][2][16];
-    __shared__ double s_inv_k2[kI0Terms];
-    for (int k = threadIdx.x; k < kI0Terms; k += blockDim.x) s_inv_k2[k] = k ? 1.0 / (double(k) * double(k)) : 0.0;
+    __shared__ double s_c[kI0Terms];          // 1 / (k!)^2
+    if (threadIdx.x == 0) {
+        double ck = 1.0;
+        for (int k = 0; k < kI0Terms; ++k) {
+            if (k) ck /= double(k) * double(k);
+            s_c[k] = ck;
+        }
+    }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * kWarps;
@@ -72,7 +76,7 @@ __global__ void __launch_bounds__(256) build_g_kernel(
         const int dim = lane >> 4, i = lane & 15;
         const double kd = dim ? kp.y : kp.x;
         const long long p0 = (long long)floor(kd - 0.5 * J) + 1;
-        if (i < J) s_kb[warp][dim][i] = kb_eval(kd - double(p0 + i), J, beta, inv_i0b, s_inv_k2);
+        if (i < J) s_kb[warp][dim][i] = kb_eval(kd - double(p0 + i), J, beta, inv_i0b, s_c);
         __syncwarp();
         const int pl = plane[v];
         if (i < T) {
@@ -89,274 +93,6 @@ __global__ void __launch_bounds__(256) build_g_kernel(
             gfac[fptr[v] + dim * T + i] = make_float2(float(acc.x * f), float(acc.y * f));
         }
         __syncwarp();
-    }
-}
-
-__device__ __forceinline__ void red_add_f2(float2 *addr, float2 v) {
-    atomicAdd(addr, v);   // sm_90+: vector float2 reduction (red.global.add.v2.f32)
-}
-
-// The data term of one PDFB iteration in a single pass over G (Eq. 2):
-//   phi  = G_m . Xhat                      (gather from the forward grid)
-//   d_m  = s_b d_m + sigma2 (phi - y_m)    (= z - sigma2 y, z = v + sigma2 Phi xbar)
-//   ||d_b||^2 accumulated per block (compensated FP32, then FP64)
-//   grid_b += conj(G_m) d_m                (scatter into the block's own grid)
-// The block's l2-ball factor (1 - m_b) is known only after the pass; it is
-// applied to grid_b when the block grids are combined, and kept as s_b for d.
-// Tile-binned form of the same pass.  A bin holds visibilities of one
-// (channel, block) segment whose box corners fall in one kTile x kTile grid
-// tile; every box then lies inside the kWin x kWin window at the tile origin.
-// The CTA stages the window of the forward grid in shared memory, gathers
-// from it, accumulates conj(G) d with shared-memory atomics, and adds the
-// window to the block grid once at the end (one global reduction per cell
-// instead of one per G entry).  Bins marked -1 (sparse tiles) take the
-// global path.
-constexpr int kWin = kTile + 15;        // boxes have T <= 16
-#ifndef FHS_BIN_MAX
-#define FHS_BIN_MAX 384
-#endif
-constexpr int kBinMax = FHS_BIN_MAX;    // visibilities per bin (host splits longer runs)
-
-// Factors of one row for one warp: lane t < T holds g1[t], lane 16 + t holds
-// g2[t]; the other lanes hold 0.
-__device__ __forceinline__ float2 load_factors(const float2 *__restrict__ f, int T, int lane) {
-    const int half = lane >> 4, col = lane & 15;
-    float2 r = make_float2(0.f, 0.f);
-    if (col < T) r = __ldcs(f + half * T + col);
-    return r;
-}
-
-// Compensated (Kahan) FP32 accumulation for the block norms: a warp sums at
-// most kBinMax / kWarps visibilities this way; warps and CTAs combine in FP64.
-struct Kahan {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float x) {
-        const float y = x - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-};
-
-// Visibilities i = i0, i0 + kWarps, ... of one bin, for one warp.  DENSE: the
-// box lies in the shared window; otherwise gather/scatter in global memory.
-// MODE: kFused (the PDFB data term), kGather (Phi only: vis_bin[i] = G_i . Xhat),
-// kScatter (Phi^H only: grid += conj(G_i) vis_bin[i]) or kNormal (G^H G in one
-// pass: grid += conj(G_i) (G_i . Xhat), for the operator-norm estimate).
-//
-// Row G_i = g1 (x) g2 over the T x T box: lane (half, col) = (lane / 16,
-// lane % 16) owns box column col and rows t1 = half, half + 2, ...; it forms
-// b = sum_t1 g1[t1] X[t1][col], and the warp reduces g2[col] b over lanes.
-// The scatter adds conj(g1[t1]) (conj(g2[col]) d) to the same cells.
-enum { kFused = 0, kGather = 1, kScatter = 2, kNormal = 3 };
-
-template <int MODE, bool DENSE>
-__device__ __forceinline__ void bin_rows(int i0, int nv, int lane, const int2 *s_meta, const int *s_off,
-                                         const float2 *s_y, const float2 *s_d, const float2 *__restrict__ fbin,
-                                         const float2 *s_grid, float *s_re, float *s_im, int wy0, int wx0,
-                                         const float2 *__restrict__ gl, float2 *__restrict__ gb, int K1, int K2,
-                                         float sc, float sigma2, float2 *__restrict__ dvis_bin, Kahan &nrm) {
-    constexpr unsigned FULL = 0xffffffffu;
-    const int half = lane >> 4, col = lane & 15;
-    float2 fac = make_float2(0.f, 0.f);
-    if (i0 < nv) fac = load_factors(fbin + s_off[i0], s_meta[i0].y, lane);
-    for (int i = i0; i < nv; i += kWarps) {
-        const int in = i + kWarps;
-        float2 fnx = make_float2(0.f, 0.f);
-        if (in < nv) fnx = load_factors(fbin + s_off[in], s_meta[in].y, lane);
-        const int2 m = s_meta[i];
-        const int T = m.y;
-        const int c1 = m.x & 0xffff, c2 = (int)((unsigned)m.x >> 16);
-        const bool cin = col < T;
-        const float g2x = __shfl_sync(FULL, fac.x, 16 + col), g2y = __shfl_sync(FULL, fac.y, 16 + col);
-        // this lane's cell in box row t1 = half (rows advance by 2 per step)
-        int ib = 0, k1 = 0, k2 = 0;
-        if (DENSE) {
-            ib = (c1 - wy0 + half) * kWin + (c2 - wx0 + col);
-        } else {
-            k1 = c1 + half;
-            k2 = c2 + col;
-            k2 -= (k2 >= K2) ? K2 : 0;
-        }
-        float dr = 0.f, di = 0.f;
-        if (MODE != kScatter) {
-            float br = 0.f, bi = 0.f;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                if (2 * k >= T) break;                 // warp-uniform
-                const int t1 = 2 * k + half;
-                const float g1x = __shfl_sync(FULL, fac.x, t1), g1y = __shfl_sync(FULL, fac.y, t1);
-                if (cin && t1 < T) {
-                    float2 x;
-                    if (DENSE) {
-                        x = s_grid[ib + 2 * k * kWin];
-                    } else {
-                        int kk = k1 + 2 * k;
-                        kk -= (kk >= K1) ? K1 : 0;
-                        x = gl[(long long)kk * K2 + k2];
-                    }
-                    br = fmaf(g1x, x.x, fmaf(-g1y, x.y, br));
-                    bi = fmaf(g1x, x.y, fmaf(g1y, x.x, bi));
-                }
-            }
-            float ar = fmaf(br, g2x, -bi * g2y), ai = fmaf(br, g2y, bi * g2x);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                ar += __shfl_xor_sync(FULL, ar, o);
-                ai += __shfl_xor_sync(FULL, ai, o);
-            }
-            if (MODE == kFused) {
-                const float2 dold = s_d[i];
-                const float2 sy = s_y[i];
-                dr = fmaf(sc, dold.x, fmaf(sigma2, ar, -sy.x));
-                di = fmaf(sc, dold.y, fmaf(sigma2, ai, -sy.y));
-                if (lane == 0) {
-                    dvis_bin[i] = make_float2(dr, di);
-                    nrm.add(fmaf(dr, dr, di * di));
-                }
-            } else if (MODE == kGather) {
-                if (lane == 0) dvis_bin[i] = make_float2(ar, ai);
-                fac = fnx;
-                continue;
-            } else {
-                dr = ar;
-                di = ai;
-            }
-        } else {
-            dr = s_d[i].x;
-            di = s_d[i].y;
-        }
-        // e = conj(g2[col]) d; cell (t1, col) += conj(g1[t1]) e
-        const float er = fmaf(g2x, dr, g2y * di), ei = fmaf(g2x, di, -g2y * dr);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            if (2 * k >= T) break;
-            const int t1 = 2 * k + half;
-            const float g1x = __shfl_sync(FULL, fac.x, t1), g1y = __shfl_sync(FULL, fac.y, t1);
-            if (cin && t1 < T) {
-                const float pr = fmaf(g1x, er, g1y * ei), pi = fmaf(g1x, ei, -g1y * er);
-                if (DENSE) {
-                    atomicAdd(s_re + ib + 2 * k * kWin, pr);
-                    atomicAdd(s_im + ib + 2 * k * kWin, pi);
-                } else {
-                    int kk = k1 + 2 * k;
-                    kk -= (kk >= K1) ? K1 : 0;
-                    red_add_f2(gb + (long long)kk * K2 + k2, make_float2(pr, pi));
-                }
-            }
-        }
-        fac = fnx;
-    }
-}
-
-// Four CTAs per SM (64 registers, 46 KB shared each): the kernel is latency
-// bound, and occupancy matters more than the registers the cap takes away.
-#ifndef FHS_FUSED_MIN_BLOCKS
-#define FHS_FUSED_MIN_BLOCKS 4
-#endif
-// MODE kFused: dvis is the data dual (read and written), grid the forward grid,
-// grid_blk the per-block adjoint grids.  kGather: dvis receives Phi x, grid is
-// the forward grid.  kScatter: dvis holds the visibilities, grid_blk the
-// per-channel output grids (indexed by channel instead of segment).  kNormal:
-// grid is the forward grid, grid_blk the per-channel output grids, dvis unused.
-template <int MODE>
-__global__ void __launch_bounds__(256, FHS_FUSED_MIN_BLOCKS) degrid_grid_binned_kernel(
-    const int2 *__restrict__ meta, const long long *__restrict__ fptr, const float2 *__restrict__ gfac,
-    const float2 *__restrict__ y, float2 *__restrict__ dvis, const long long *__restrict__ bin_start,
-    const int *__restrict__ bin_seg, const int *__restrict__ bin_tile, int ntx, int B,
-    const float *__restrict__ blk_scale, double *__restrict__ blk_norm2, const float2 *__restrict__ grid,
-    float2 *__restrict__ grid_blk, long long K, int K1, int K2, float sigma2) {
-    __shared__ float2 s_grid[kWin * kWin];
-    __shared__ float s_re[kWin * kWin];
-    __shared__ float s_im[kWin * kWin];
-    __shared__ int2 s_meta[kBinMax];
-    __shared__ int s_off[kBinMax];        // factor offset relative to the bin's first row
-    __shared__ float2 s_y[kBinMax];       // sigma2 * y
-    __shared__ float2 s_d[kBinMax];
-    __shared__ double s_red[kWarps];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bin = blockIdx.x;
-    const int seg = bin_seg[bin];
-    const int tile = bin_tile[bin];
-    const int l = seg / B;
-    const float2 *gl = grid + (long long)l * K;
-    float2 *gb = grid_blk + (long long)((MODE == kScatter || MODE == kNormal) ? l : seg) * K;
-    const float sc = MODE == kFused ? blk_scale[seg] : 0.f;
-    const long long v0 = bin_start[bin];
-    const int nv = int(bin_start[bin + 1] - v0);
-    const long long g0 = fptr[v0];
-    const float2 *fbin = gfac + g0;
-    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-        s_meta[i] = meta[v0 + i];
-        s_off[i] = int(fptr[v0 + i] - g0);
-        if (MODE == kFused) {
-            const float2 yy = y[v0 + i];
-            s_y[i] = make_float2(sigma2 * yy.x, sigma2 * yy.y);
-        }
-        if (MODE == kFused || MODE == kScatter) s_d[i] = dvis[v0 + i];
-    }
-    const bool dense = tile >= 0;
-    int wy0 = 0, wx0 = 0;
-    if (dense) {
-        wy0 = (tile / ntx) * kTile;
-        wx0 = (tile % ntx) * kTile;
-        for (int i = threadIdx.x; i < kWin * kWin; i += blockDim.x) {
-            const int r = i / kWin, c = i - r * kWin;
-            int k1 = wy0 + r;
-            while (k1 >= K1) k1 -= K1;
-            int k2 = wx0 + c;
-            while (k2 >= K2) k2 -= K2;
-            if (MODE != kScatter) s_grid[i] = gl[(long long)k1 * K2 + k2];
-            if (MODE != kGather) {
-                s_re[i] = 0.f;
-                s_im[i] = 0.f;
-            }
-        }
-    }
-    __syncthreads();
-    Kahan nrm;
-    if (dense)
-        bin_rows<MODE, true>(warp, nv, lane, s_meta, s_off, s_y, s_d, fbin, s_grid, s_re, s_im, wy0, wx0, gl, gb,
-                             K1, K2, sc, sigma2, dvis + v0, nrm);
-    else
-        bin_rows<MODE, false>(warp, nv, lane, s_meta, s_off, s_y, s_d, fbin, s_grid, s_re, s_im, wy0, wx0, gl, gb,
-                              K1, K2, sc, sigma2, dvis + v0, nrm);
-    if (MODE != kFused) {
-        if ((MODE == kScatter || MODE == kNormal) && dense) {
-            __syncthreads();
-            for (int q = threadIdx.x; q < kWin * kWin; q += blockDim.x) {
-                const float re = s_re[q], im = s_im[q];
-                if (re != 0.f || im != 0.f) {
-                    const int r = q / kWin, c = q - r * kWin;
-                    int k1 = wy0 + r;
-                    while (k1 >= K1) k1 -= K1;
-                    int k2 = wx0 + c;
-                    while (k2 >= K2) k2 -= K2;
-                    red_add_f2(gb + (long long)k1 * K2 + k2, make_float2(re, im));
-                }
-            }
-        }
-        return;
-    }
-    if (lane == 0) s_red[warp] = double(nrm.s) - double(nrm.c);
-    __syncthreads();
-    if (dense) {
-        for (int q = threadIdx.x; q < kWin * kWin; q += blockDim.x) {
-            const float re = s_re[q], im = s_im[q];
-            if (re != 0.f || im != 0.f) {
-                const int r = q / kWin, c = q - r * kWin;
-                int k1 = wy0 + r;
-                while (k1 >= K1) k1 -= K1;
-                int k2 = wx0 + c;
-                while (k2 >= K2) k2 -= K2;
-                red_add_f2(gb + (long long)k1 * K2 + k2, make_float2(re, im));
-            }
-        }
-    }
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < kWarps; ++w) t += s_red[w];
-        atomicAdd(blk_norm2 + seg, t);
     }
 }
 
@@ -567,43 +303,6 @@ cudaError_t launch_zpad(fhs_problem *p, const float *x, float2 *grid, cudaStream
 cudaError_t launch_crop(fhs_problem *p, const float2 *grid, float *x, cudaStream_t s) {
     dim3 g(grid_for(p->N, 256, 512), p->L);
     crop_kernel<<<g, 256, 0, s>>>(grid, x, p->s1, p->s2, p->ny, p->nx, p->K1, p->K2, p->K);
-    p->n_launch += 1;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_degrid(fhs_problem *p, const float2 *grid, float2 *vis_sorted, cudaStream_t s) {
-    if (p->n_bin == 0) return cudaSuccess;
-    degrid_grid_binned_kernel<kGather><<<p->n_bin, 256, 0, s>>>(
-        p->meta, p->fptr, p->gfac, nullptr, vis_sorted, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B,
-        nullptr, nullptr, grid, nullptr, p->K, p->K1, p->K2, 0.f);
-    p->n_launch += 1;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s) {
-    if (p->n_bin == 0) return cudaSuccess;
-    degrid_grid_binned_kernel<kScatter><<<p->n_bin, 256, 0, s>>>(
-        p->meta, p->fptr, p->gfac, nullptr, const_cast<float2 *>(vis_sorted), p->bin_start, p->bin_seg,
-        p->bin_tile, p->ntx, p->B, nullptr, nullptr, nullptr, grid, p->K, p->K1, p->K2, 0.f);
-    p->n_launch += 1;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, cudaStream_t s) {
-    if (p->n_bin == 0) return cudaSuccess;
-    degrid_grid_binned_kernel<kNormal><<<p->n_bin, 256, 0, s>>>(
-        p->meta, p->fptr, p->gfac, nullptr, nullptr, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B, nullptr,
-        nullptr, grid, grid_out, p->K, p->K1, p->K2, 0.f);
-    p->n_launch += 1;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_degrid_grid_fused(fhs_problem *p, cudaStream_t s) {
-    if (p->n_bin == 0) return cudaSuccess;
-    degrid_grid_binned_kernel<kFused><<<p->n_bin, 256, 0, s>>>(p->meta, p->fptr, p->gfac, p->y, p->dvis, p->bin_start,
-                                                       p->bin_seg, p->bin_tile, p->ntx, p->B, p->blk_scale,
-                                                       p->blk_norm2, p->grid_work, p->grid_blk, p->K, p->K1, p->K2,
-                                                       float(p->sigma2));
     p->n_launch += 1;
     return cudaGetLastError();
 }
