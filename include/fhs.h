@@ -75,7 +75,17 @@ typedef struct fhs_params {
     double  sigma2;          /* data dual step; <= 0 selects 1/max_l ||Phi_l||^2   */
     int32_t power_iters;     /* Lanczos steps for ||Phi_l||^2 (default 100)        */
     double  power_tol;       /* relative change of the estimate that stops them    */
+    int32_t gram_precision;  /* facet Gram of the nuclear dual step, fhs_gram_precision */
 } fhs_params;
+
+/* Arithmetic of the facet Gram G_q = Z_q^T Z_q in the nuclear dual step
+ * (Sec. 2.2.2).  FP32: FP32 products on the CUDA cores, FP64 sums across
+ * threads.  TF32 / BF16: inputs rounded to TF32 or BF16, products summed in
+ * FP32 on the tensor cores, FP64 across CTAs.  FP64: FP64 products and sums
+ * on the CUDA cores (the mode that agrees with an FP64 SVD of Z_q also for
+ * the small singular values).  The reweighting Gram is FP64 in every mode;
+ * the eigendecomposition is FP64 in every mode. */
+typedef enum { FHS_GRAM_FP32 = 0, FHS_GRAM_TF32 = 1, FHS_GRAM_BF16 = 2, FHS_GRAM_FP64 = 3 } fhs_gram_precision;
 
 /* Fill *p with the defaults (J = 7, 4 levels, 64 w-planes, computed steps). */
 void fhs_default_params(fhs_params *p);
@@ -251,6 +261,12 @@ fhs_status fhs_profile_read(fhs_problem *prob, double *ms_out, int64_t *iters_ou
 /* Number of libfhs kernels launched since the problem was created (cuFFT's
  * own kernels are not counted). */
 fhs_status fhs_kernel_launches(const fhs_problem *prob, int64_t *count_out);
+
+/* Device-side status of the problem's kernels: FHS_ERR_TIMEOUT if a bounded
+ * wait inside a kernel gave up since the last call (the tensor-core Gram's
+ * mbarrier waits), FHS_OK otherwise; the flag is cleared.  Synchronises the
+ * stream. */
+fhs_status fhs_device_status(fhs_problem *prob, void *stream);
 
 /* ------------------------------------------------------------------------
  * Serving: imaging requests solved concurrently on one GPU.  Requests are

@@ -25,9 +25,10 @@ EXPORTED = [
     "fhs_last_error", "fhs_profile_enable", "fhs_profile_read", "fhs_kernel_launches",
     "fhs_sara_analysis_noalloc", "fhs_pdfb_step_batch", "fhs_use_graphs", "fhs_estimate_bytes",
     "fhs_server_create", "fhs_server_submit", "fhs_server_query", "fhs_server_wait", "fhs_server_stats",
-    "fhs_server_destroy",
+    "fhs_server_destroy", "fhs_device_status",
 ]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
+GRAM_FP32, GRAM_TF32, GRAM_BF16, GRAM_FP64 = range(4)
 PHASES = ["primal", "fft_fwd", "degrid_grid", "l2ball", "fft_inv", "sara", "nuclear"]
 
 
@@ -45,6 +46,7 @@ class fhs_params(C.Structure):
         ("pixel_size", C.c_double), ("mu", C.c_double), ("mu_bar", C.c_double), ("upsilon", C.c_double),
         ("upsilon_bar", C.c_double), ("tau", C.c_double), ("sigma0", C.c_double), ("sigma1", C.c_double),
         ("sigma2", C.c_double), ("power_iters", C.c_int32), ("power_tol", C.c_double),
+        ("gram_precision", C.c_int32),
     ]
 
 
@@ -297,6 +299,11 @@ def fhs_profile_read(prob):
     it = C.c_int64(0)
     _check(load_library().fhs_profile_read(prob, _ptr(ms), C.byref(it)))
     return dict(zip(PHASES, ms.tolist())), it.value
+
+
+def fhs_device_status(prob, stream=None):
+    """Raise FhsError(FHS_ERR_TIMEOUT) if a bounded device wait gave up."""
+    _check(load_library().fhs_device_status(prob, _stream(stream)))
 
 
 def fhs_kernel_launches(prob) -> int:

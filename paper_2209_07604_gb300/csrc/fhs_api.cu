@@ -138,8 +138,8 @@ fhs_status check_params(const fhs_params *q) {
     if (2LL * q->ny >= 65536 || 2LL * q->nx >= 65536) return fail(FHS_ERR_ARG, "image side too large");
     if (q->n_channels < 1 || q->n_subcubes < 1 || q->n_channels % q->n_subcubes)
         return fail(FHS_ERR_ARG, "n_channels must be a positive multiple of n_subcubes");
-    if (q->n_channels / q->n_subcubes > 16)
-        return fail(FHS_ERR_ARG, "at most 16 channels per sub-cube are supported");
+    if (q->n_channels / q->n_subcubes > kMaxLc)
+        return fail(FHS_ERR_ARG, "at most %d channels per sub-cube are supported", kMaxLc);
     if (q->n_blocks < 1) return fail(FHS_ERR_ARG, "n_blocks must be >= 1");
     if (q->qy < 1 || q->qx < 1 || q->qy > q->ny || q->qx > q->nx) return fail(FHS_ERR_ARG, "bad facet grid");
     if (!(q->facet_overlap >= 0.0 && q->facet_overlap < 1.0)) return fail(FHS_ERR_ARG, "facet_overlap must be in [0, 1)");
@@ -150,6 +150,8 @@ fhs_status check_params(const fhs_params *q) {
     if (q->w_max > 0.0 && !(q->pixel_size > 0.0)) return fail(FHS_ERR_ARG, "pixel_size must be > 0 with w-terms");
     if (!(q->mu >= 0.0) || !(q->mu_bar >= 0.0)) return fail(FHS_ERR_ARG, "mu and mu_bar must be >= 0");
     if (!(q->upsilon > 0.0) || !(q->upsilon_bar > 0.0)) return fail(FHS_ERR_ARG, "upsilon and upsilon_bar must be > 0");
+    if (q->gram_precision < FHS_GRAM_FP32 || q->gram_precision > FHS_GRAM_FP64)
+        return fail(FHS_ERR_ARG, "gram_precision must be one of FHS_GRAM_FP32, _TF32, _BF16, _FP64");
     return FHS_OK;
 }
 
@@ -398,7 +400,9 @@ fhs_status one_iteration(fhs_problem *p, cudaStream_t s) {
     if (nuc_active(p)) {
         cudaStream_t sn = fork ? p->s_nuc : s;
         Phase ph(p, s, FHS_PHASE_NUCLEAR);
-        CU(launch_nuclear_gram(p, p->Xbar, true, sn));
+        const int gp = p->prm.gram_precision;
+        if (gp == FHS_GRAM_TF32 || gp == FHS_GRAM_BF16) CU(launch_nuclear_gram_tc(p, gp, sn));
+        else CU(launch_nuclear_gram(p, p->Xbar, true, gp == FHS_GRAM_FP64, sn));
         CU(launch_nuclear_eig(p, false, sn));
         CU(launch_nuclear_apply(p, sn));
         if (fork) CU(cudaEventRecord(p->ev_nuc, sn));
@@ -507,6 +511,7 @@ void fhs_default_params(fhs_params *p) {
     p->tau = p->sigma0 = p->sigma1 = p->sigma2 = 0.0;
     p->power_iters = 100;
     p->power_tol = 1e-7;
+    p->gram_precision = FHS_GRAM_FP32;
 }
 
 fhs_status fhs_daubechies_filter(int32_t p, double *h_out) {
@@ -815,6 +820,7 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
     if ((st = guard(dev_alloc(p, &p->A_sara, p->N * L))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->red, 2))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->pnorms, 2 * L))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->dev_err, 1))) != FHS_OK) return st;
 
     // ---- SARA layout
     {
@@ -1037,6 +1043,17 @@ fhs_status fhs_kernel_launches(const fhs_problem *p, int64_t *count_out) {
     return FHS_OK;
 }
 
+fhs_status fhs_device_status(fhs_problem *p, void *stream) {
+    if (!p) return fail(FHS_ERR_ARG, "NULL problem");
+    cudaStream_t s = S(stream);
+    int h = 0;
+    CU(cudaMemcpyAsync(&h, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (h == 0) return FHS_OK;
+    CU(cudaMemsetAsync(p->dev_err, 0, sizeof(int), s));
+    return fail(FHS_ERR_TIMEOUT, "a bounded wait in a device kernel gave up (code %d)", h);
+}
+
 fhs_status fhs_get_info(const fhs_problem *p, fhs_info *info) {
     if (!p || !info) return fail(FHS_ERR_ARG, "NULL argument");
     info->n_vis = p->Mtot;
@@ -1102,7 +1119,7 @@ fhs_status fhs_reweight(fhs_problem *p, void *stream) {
     cudaStream_t s = S(stream);
     CU(launch_sara_analysis(p, p->X, p->coef_tmp, s));
     CU(launch_l21_reweight(p, s));
-    CU(launch_nuclear_gram(p, p->X, false, s));
+    CU(launch_nuclear_gram(p, p->X, false, true, s));
     CU(launch_nuclear_eig(p, true, s));
     return FHS_OK;
 }

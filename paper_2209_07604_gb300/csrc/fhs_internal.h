@@ -131,6 +131,7 @@ struct fhs_problem {
     int iteration = 0;
     long long n_launch = 0;                   // libfhs kernels launched
     double *pnorms = nullptr;                 // [2L] power-iteration reductions
+    int *dev_err = nullptr;                   // [1] set by a kernel whose bounded wait gave up
 
     // the SARA and nuclear dual steps run on their own streams, forked after
     // the primal step and joined before the iteration ends
@@ -190,9 +191,11 @@ cudaError_t launch_sara_synthesis(fhs_problem *p, const float *coef, float *x, c
 cudaError_t launch_l21_dual(fhs_problem *p, cudaStream_t s);
 cudaError_t launch_l21_reweight(fhs_problem *p, cudaStream_t s);
 // k_nuclear.cu
-cudaError_t launch_nuclear_gram(fhs_problem *p, const float *img, bool with_dual, cudaStream_t s);
+cudaError_t launch_nuclear_gram(fhs_problem *p, const float *img, bool with_dual, bool fp64, cudaStream_t s);
 cudaError_t launch_nuclear_eig(fhs_problem *p, bool reweight, cudaStream_t s);
 cudaError_t launch_nuclear_apply(fhs_problem *p, cudaStream_t s);
+// Tensor-core Gram of the dual step (precision FHS_GRAM_TF32 or FHS_GRAM_BF16).
+cudaError_t launch_nuclear_gram_tc(fhs_problem *p, int precision, cudaStream_t s);
 // k_pdfb.cu
 cudaError_t launch_primal(fhs_problem *p, cudaStream_t s);
 

@@ -73,26 +73,89 @@ __global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ P, 
             if (threadIdx.x == (k & 255) && i < Lc && j < Lc) atomicAdd(&G[i * Lc + j], s_red[k]);
 }
 
+// L_c in (16, 32]: the per-thread triangle no longer fits in registers.  The
+// CTA stages kSub pixels x L_c channels of Z in shared memory (loads coalesced
+// along pixels); lane i of each warp then accumulates row i of the Gram over
+// the warp's pixels, reading Z[j][p] as a shared-memory broadcast.
+constexpr int kSub = 128;
+
+template <typename AccT>
+__global__ void __launch_bounds__(256) gram32_kernel(const float *__restrict__ P, const float *__restrict__ img,
+                                                     const int4 *__restrict__ facets,
+                                                     const long long *__restrict__ nuc_off, int Q, int C, int Lc,
+                                                     int nx, long long N, float s, bool with_dual,
+                                                     double *__restrict__ gram) {
+    __shared__ float s_z[32][kSub + 1];
+    __shared__ double s_red[32 * 32];
+    const int cq = blockIdx.y;
+    const int c = cq / Q, q = cq - c * Q;
+    const int4 f = facets[q];
+    const int wx = f.w - f.z;
+    const long long npix = (long long)(f.y - f.x) * wx;
+    const long long p0 = (long long)blockIdx.x * kPix;
+    if (p0 >= npix) return;
+    const long long p1 = min(npix, p0 + kPix);
+    const float *Pq = P + nuc_off[cq];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) s_red[e] = 0.0;
+    AccT acc[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = AccT(0);
+    for (long long sb = p0; sb < p1; sb += kSub) {
+        const int nsub = int(min((long long)kSub, p1 - sb));
+        __syncthreads();                         // the previous sub-chunk is consumed
+        for (int e = threadIdx.x; e < 32 * kSub; e += blockDim.x) {
+            const int j = e / kSub, t = e - j * kSub;
+            float v = 0.f;
+            if (j < Lc && t < nsub) {
+                const long long pp = sb + t;
+                const int py = int(pp / wx), px = int(pp - (long long)py * wx);
+                const long long o = (long long)(f.x + py) * nx + (f.z + px);
+                const float xv = img[(long long)(c + j * C) * N + o];
+                v = with_dual ? fmaf(s, xv, Pq[(long long)j * npix + pp]) : xv;
+            }
+            s_z[j][t] = v;
+        }
+        __syncthreads();
+        for (int t = warp; t < nsub; t += blockDim.x >> 5) {
+            const AccT zi = AccT(s_z[lane][t]);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[j] = fma(zi, AccT(s_z[j][t]), acc[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) atomicAdd(&s_red[lane * 32 + j], double(acc[j]));
+    __syncthreads();
+    double *G = gram + (long long)cq * Lc * Lc;
+    for (int e = threadIdx.x; e < Lc * Lc; e += blockDim.x) {
+        const int i = e / Lc, j = e - i * Lc;
+        if (j >= i) atomicAdd(&G[e], s_red[i * 32 + j]);
+    }
+}
+
 // Symmetric eigen-decomposition of one L_c x L_c Gram per warp: cyclic Jacobi
 // in FP64 with a round-robin ordering, so each round applies L_c/2 disjoint
 // rotations at once (columns first, then rows: disjoint Givens rotations
 // commute).  Bounded sweeps.  Then either the SVT mixing matrix
 // M = V diag(min(1, mu_bar w_i / s_i)) V^T or the reweighting weights.
-constexpr int kEigWarps = 4;
-
-__global__ void __launch_bounds__(32 * kEigWarps) eig_kernel(double *__restrict__ gram, float *__restrict__ mix,
-                                                            float *__restrict__ wnuc, int n_mat, int Lc,
-                                                            double mu_bar, double upsilon_bar, bool reweight) {
-    __shared__ double s_a[kEigWarps][16][17];
-    __shared__ double s_v[kEigWarps][16][17];
-    __shared__ double s_cs[kEigWarps][8], s_sn[kEigWarps][8];
-    __shared__ int s_p[kEigWarps][8], s_q[kEigWarps][8];
-    __shared__ int s_ord[kEigWarps][16];
+// NMAX = 16: four warps (four matrices) per CTA; NMAX = 32: one.
+template <int NMAX>
+__global__ void __launch_bounds__(NMAX == 16 ? 128 : 32) eig_kernel(double *__restrict__ gram,
+                                                                    float *__restrict__ mix,
+                                                                    float *__restrict__ wnuc, int n_mat, int Lc,
+                                                                    double mu_bar, double upsilon_bar,
+                                                                    bool reweight) {
+    constexpr int kEigWarps = NMAX == 16 ? 4 : 1;
+    __shared__ double s_a[kEigWarps][NMAX][NMAX + 1];
+    __shared__ double s_v[kEigWarps][NMAX][NMAX + 1];
+    __shared__ double s_cs[kEigWarps][NMAX / 2], s_sn[kEigWarps][NMAX / 2];
+    __shared__ int s_p[kEigWarps][NMAX / 2], s_q[kEigWarps][NMAX / 2];
+    __shared__ int s_ord[kEigWarps][NMAX];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cq = blockIdx.x * kEigWarps + w;
     if (cq >= n_mat) return;
-    double(*a)[17] = s_a[w];
-    double(*V)[17] = s_v[w];
+    double(*a)[NMAX + 1] = s_a[w];
+    double(*V)[NMAX + 1] = s_v[w];
     double *G = gram + (long long)cq * Lc * Lc;
     const int n = Lc + (Lc & 1);                 // even size: a padded row/column stays zero
     for (int e = lane; e < n * n; e += 32) {
@@ -182,7 +245,7 @@ __global__ void __launch_bounds__(32 * kEigWarps) eig_kernel(double *__restrict_
         }
         return;
     }
-    __shared__ double s_f[kEigWarps][16];
+    __shared__ double s_f[kEigWarps][NMAX];
     if (lane < Lc) {
         const double sv = sqrt(fmax(a[ord[lane]][ord[lane]], 0.0));
         const double thr = mu_bar * double(wv[lane]);
@@ -223,7 +286,7 @@ __global__ void __launch_bounds__(256) apply_kernel(float *__restrict__ P, const
 #pragma unroll
         for (int j = 0; j < MAXLC; ++j)
             z[j] = (j < Lc) ? fmaf(s, img[(long long)(c + j * C) * N + o], Pq[(long long)j * npix + pp]) : 0.f;
-#pragma unroll
+#pragma unroll(MAXLC > 16 ? 2 : MAXLC)
         for (int j = 0; j < MAXLC; ++j) {
             if (j < Lc) {
                 float r = 0.f;
@@ -250,21 +313,28 @@ static cudaError_t gram_dispatch(fhs_problem *p, const float *img, bool with_dua
     else if (p->Lc <= 4) FHS_GRAM(4);
     else if (p->Lc <= 8) FHS_GRAM(8);
     else if (p->Lc <= 16) FHS_GRAM(16);
+    else if (p->Lc <= 32)
+        gram32_kernel<AccT><<<g, 256, 0, s>>>(p->P, img, p->d_facets, p->nuc_off, p->Q, p->C, p->Lc, p->nx, p->N, s0,
+                                              with_dual, p->gram);
     else return cudaErrorInvalidValue;
 #undef FHS_GRAM
     p->n_launch += 1;
     return cudaGetLastError();
 }
 
-cudaError_t launch_nuclear_gram(fhs_problem *p, const float *img, bool with_dual, cudaStream_t s) {
-    // the dual step's Gram in FP32 products; the reweighting Gram of x in FP64
-    return with_dual ? gram_dispatch<float>(p, img, true, s) : gram_dispatch<double>(p, img, false, s);
+cudaError_t launch_nuclear_gram(fhs_problem *p, const float *img, bool with_dual, bool fp64, cudaStream_t s) {
+    // the dual step's Gram in FP32 (or FP64) products; the reweighting Gram of x in FP64
+    return fp64 ? gram_dispatch<double>(p, img, with_dual, s) : gram_dispatch<float>(p, img, with_dual, s);
 }
 
 cudaError_t launch_nuclear_eig(fhs_problem *p, bool reweight, cudaStream_t s) {
     const int n = p->C * p->Q;
-    eig_kernel<<<(n + kEigWarps - 1) / kEigWarps, 32 * kEigWarps, 0, s>>>(
-        p->gram, p->mix, p->wnuc, n, p->Lc, p->prm.mu_bar, p->prm.upsilon_bar, reweight);
+    if (p->Lc <= 16)
+        eig_kernel<16><<<(n + 3) / 4, 128, 0, s>>>(p->gram, p->mix, p->wnuc, n, p->Lc, p->prm.mu_bar,
+                                                  p->prm.upsilon_bar, reweight);
+    else
+        eig_kernel<32><<<n, 32, 0, s>>>(p->gram, p->mix, p->wnuc, n, p->Lc, p->prm.mu_bar, p->prm.upsilon_bar,
+                                         reweight);
     p->n_launch += 1;
     return cudaGetLastError();
 }
@@ -282,6 +352,8 @@ cudaError_t launch_nuclear_apply(fhs_problem *p, cudaStream_t s) {
         apply_kernel<8><<<g, 256, 0, s>>>(p->P, p->Xbar, p->d_facets, p->nuc_off, p->mix, p->Q, p->C, p->Lc, p->nx, p->N, s0);
     else if (p->Lc <= 16)
         apply_kernel<16><<<g, 256, 0, s>>>(p->P, p->Xbar, p->d_facets, p->nuc_off, p->mix, p->Q, p->C, p->Lc, p->nx, p->N, s0);
+    else if (p->Lc <= 32)
+        apply_kernel<32><<<g, 256, 0, s>>>(p->P, p->Xbar, p->d_facets, p->nuc_off, p->mix, p->Q, p->C, p->Lc, p->nx, p->N, s0);
     else
         return cudaErrorInvalidValue;
     p->n_launch += 1;

@@ -94,8 +94,9 @@ def test_params_struct_layout(lib):
     p = fhs.default_params()
     assert p.kb_taps == 7 and p.wavelet_levels == 4 and p.n_wplanes == 64 and p.power_iters == 100
     assert abs(p.upsilon - 1e-3) < 1e-18 and abs(p.power_tol - 1e-7) < 1e-20
-    # 7 int32 + pad, double, 2 int32, double, int32 + pad, 9 doubles, int32 + pad, double
-    assert C.sizeof(fhs.fhs_params) == 152
+    assert p.gram_precision == fhs.GRAM_FP32
+    # 7 int32 + pad, double, 2 int32, double, int32 + pad, 9 doubles, int32 + pad, double, int32 + pad
+    assert C.sizeof(fhs.fhs_params) == 160
 
 
 def test_estimate_bytes_counts_g_factors(lib):

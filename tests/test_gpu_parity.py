@@ -130,12 +130,12 @@ def test_operator_norms():
         prob.close()
 
 
-def _run_pair(name, n_iter, n_reweight, mu, mu_bar, **over):
+def _run_pair(name, n_iter, n_reweight, mu, mu_bar, gram_precision=0, **over):
     P = synth.make_problem(name, **over)
     geom = onf.Geometry(P.ny, P.nx, w_max=P.w_max, n_wplanes=64, pixel_size=P.pixel_size)
     op = onf.Operator(P.omega[:1], P.w[:1], P.sigma[:1], geom)
     sigma2 = 1.0 / (1.02 * op.norm2(0, n_iter=60))
-    prob = fhs.Problem.from_synth(P, mu=mu, mu_bar=mu_bar, sigma2=sigma2)
+    prob = fhs.Problem.from_synth(P, mu=mu, mu_bar=mu_bar, sigma2=sigma2, gram_precision=gram_precision)
     ref = _oracle(P, mu, mu_bar, sigma2, steps=_steps_from(prob, sigma2))
     ref.run(n_iter, n_reweight)
     per = n_iter // (n_reweight + 1)
@@ -174,6 +174,24 @@ def test_pdfb_iterates(name, n_iter, n_reweight, mu, mu_bar):
         wn = prob.get_state(fhs.STATE_WEIGHTS_NUC).cpu().numpy()
         wref = np.concatenate([ref.wnuc[c][q] for c in range(P.C) for q in range(len(ref.facets))])
         assert rel(wn, wref) < TOL_IMG
+    prob.close()
+
+
+@pytest.mark.parametrize("L", [17, 32])
+def test_pdfb_iterates_many_channels_per_subcube(L):
+    """L_c in (16, 32]: the shared-memory Gram (FP64 mode, which resolves the
+    small singular values that the SVT weights see), the 32 x 32 FP64 Jacobi
+    and the 32-channel apply (odd L_c pads the Jacobi to an even size).  The
+    FP32, TF32 and BF16 Grams at this size are measured against the oracle in
+    the mixed-precision tests."""
+    P, prob, ref = _run_pair("tiny", 8, 1, 0.02, 0.3, L=L, C=1, gram_precision=fhs.GRAM_FP64)
+    assert rel(prob.image().cpu().numpy(), ref.X) < TOL_IMG
+    Pn = prob.get_state(fhs.STATE_DUAL_NUCLEAR).cpu().numpy()
+    Pref = np.concatenate([ref.P[c][q].ravel() for c in range(P.C) for q in range(len(ref.facets))])
+    assert rel(Pn, Pref) < TOL_IMG
+    wn = prob.get_state(fhs.STATE_WEIGHTS_NUC).cpu().numpy()
+    wref = np.concatenate([ref.wnuc[c][q] for c in range(P.C) for q in range(len(ref.facets))])
+    assert rel(wn, wref) < TOL_IMG
     prob.close()
 
 
