@@ -156,9 +156,10 @@ def run_gpu(args):
     wv = np.ascontiguousarray(P.w.reshape(-1))
     yv = np.ascontiguousarray(np.stack([P.y.real, P.y.imag], -1).reshape(-1, 2))
     vis_off = np.arange(L + 1, dtype=np.int64) * M
+    gram = {"fp32": fhs.GRAM_FP32, "tf32": fhs.GRAM_TF32, "bf16": fhs.GRAM_BF16, "fp64": fhs.GRAM_FP64}[args.gram]
     params = fhs.default_params(ny=P.ny, nx=P.nx, n_channels=L, n_subcubes=P.C, n_blocks=P.B, qy=P.qy, qx=P.qx,
                                 facet_overlap=P.overlap, w_max=P.w_max, pixel_size=P.pixel_size, mu=MU,
-                                mu_bar=MU_BAR)
+                                mu_bar=MU_BAR, gram_precision=gram)
     e2e_iters = args.e2e_iters
     img_host = torch.empty((L, P.ny, P.nx), dtype=torch.float32, pin_memory=True)
     t_e2e = time.perf_counter()
@@ -244,13 +245,13 @@ def run_gpu(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 (FP64 reductions, eig, weights)",
+        "dtype": "f32 (FP64 reductions, eig, weights; facet Gram %s)" % args.gram,
         "data": "synthetic (seeded VLA-like uv/w, Gaussian-blob sky, 40 dB)",
         "config": {"workload": args.workload, "image": "%dx%d" % (P.ny, P.nx), "channels": L,
                    "subcubes": P.C, "vis_per_channel": M, "blocks": P.B, "facets": "%dx%d" % (P.qy, P.qx),
                    "facet_overlap": P.overlap, "w_max": P.w_max, "nnz_G": info.nnz,
                    "l2": "inputs larger than L2 (G factors alone %.1f GB per iteration)" % (info.n_gfac * 8 / 1e9),
-                   "mu": MU, "mu_bar": MU_BAR},
+                   "mu": MU, "mu_bar": MU_BAR, "gram": args.gram},
         "vis_per_s": ws * vis_s,
         "phi_vis_per_s": ws * Mtot / (phi_ms * 1e-3),
         "phi_adjoint_vis_per_s": ws * Mtot / (phit_ms * 1e-3),
@@ -446,6 +447,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--e2e-iters", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--gram", default="fp32", choices=["fp32", "tf32", "bf16", "fp64"],
+                    help="arithmetic of the nuclear facet Gram (tf32/bf16: tensor cores)")
     ap.add_argument("--mode", default="pdfb", choices=["pdfb", "serve"])
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=4.0)

@@ -887,6 +887,14 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
         if ((st = guard(dev_alloc(p, &p->gram, (size_t)p->C * p->Q * p->Lc * p->Lc))) != FHS_OK) return st;
         if ((st = guard(dev_alloc(p, &p->mix, (size_t)p->C * p->Q * p->Lc * p->Lc))) != FHS_OK) return st;
         if ((st = guard(dev_alloc(p, &p->wnuc, (size_t)p->C * p->Q * p->Lc, false))) != FHS_OK) return st;
+        {
+            const int ne = p->Lc + (p->Lc & 1);
+            std::vector<double> eye((size_t)p->C * p->Q * ne * ne, 0.0);
+            for (size_t m = 0; m < (size_t)p->C * p->Q; ++m)
+                for (int i = 0; i < ne; ++i) eye[m * ne * ne + (size_t)i * ne + i] = 1.0;
+            if ((st = guard(dev_alloc(p, &p->eigv, eye.size(), false))) != FHS_OK) return st;
+            if ((st = guard(upload(p->eigv, eye.data(), eye.size(), s))) != FHS_OK) return st;
+        }
         if ((st = guard(dev_alloc(p, &p->cov_row_first, q.ny, false))) != FHS_OK) return st;
         if ((st = guard(dev_alloc(p, &p->cov_row_cnt, q.ny, false))) != FHS_OK) return st;
         if ((st = guard(dev_alloc(p, &p->cov_col_first, q.nx, false))) != FHS_OK) return st;
@@ -999,7 +1007,9 @@ fhs_status fhs_estimate_bytes(const fhs_params *params, const double *w, int64_t
     r += 8 * K * L * (3 + B);                                        // grids
     r += 4 * N * L * 3 + 16 + 16 * L;                                // images, reductions
     r += 4 * c.n_coef * L * 2 + 4 * c.n_tmp * L + 4 * c.n_coef * C;  // SARA
+    const long long ne = Lc + (Lc & 1);
     r += 16 * Q + 8 * C * Q + 4 * nuc + 12 * C * Q * Lc * Lc + 4 * C * Q * Lc + 4 * (q.ny + q.nx);
+    r += 8 * C * Q * ne * ne;                                        // eigenvector warm starts
     r += (long long)cufft_workspace(2 * q.ny, 2 * q.nx, int(L));
     const long long n_planes = q.w_max > 0.0 ? 2LL * (q.n_wplanes - 1) + 1 : 1;
     const long long peak = r + 16 * M + 2 * M + 16 * n_planes * 2 * (2 * kMaxWHalf + 1) + 8 * nseg;

@@ -119,6 +119,7 @@ struct fhs_problem {
     double *gram = nullptr;                   // [C*Q][Lc*Lc]
     float *mix = nullptr;                     // [C*Q][Lc*Lc]
     float *wnuc = nullptr;                    // [C*Q][Lc]
+    double *eigv = nullptr;                   // [C*Q][n*n] eigenvectors of the last dual-step Gram (n = Lc rounded up to even)
     short *cov_row_first = nullptr, *cov_row_cnt = nullptr;   // [ny]
     short *cov_col_first = nullptr, *cov_col_cnt = nullptr;   // [nx]
     int max_cover = 1;

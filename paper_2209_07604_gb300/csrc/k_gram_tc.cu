@@ -150,56 +150,62 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const float *__rest
     const uint32_t tmem = s_tmem;
     constexpr uint32_t idesc = instr_desc(KIND == 0 ? 2u : 1u, 128u, 32u);
 
-    bool ok = true;
-    for (int it = 0; it < n_stage && ok; ++it) {
+    // Thread (warp w, lane) owns channel row j = 8 w + lane / 4 of every stage
+    // and the 16-byte slot lane % 4 of each K column kq: TF32 pixels
+    // 4 kq + lane % 4, BF16 pixels 8 kq + 2 (lane % 4) + {0, 1}.  Two register
+    // sets take turns: the global loads of stage it + 1 are in flight while
+    // stage it is written and its MMAs are issued.
+    constexpr int VPT = KIND == 0 ? 8 : 16;             // values per thread per stage
+    const int j = (warp << 3) | (lane >> 2);
+    const bool jv = j < Lc;
+    const float *imgj = img + (long long)(c + (jv ? j : 0) * C) * N;
+    const float *Pj = Pq + (long long)(jv ? j : 0) * npix;
+    auto load_stage = [&](int it, float (&v)[VPT]) {
+        const int pb = p0 + it * KS;
+        int py = pb / wx, px = pb - (pb / wx) * wx;   // facet coordinates of the stage's first pixel
+        int k_prev = 0;
+#pragma unroll
+        for (int i = 0; i < VPT; ++i) {
+            const int k = KIND == 0 ? ((i << 2) | (lane & 3)) : (((i >> 1) << 3) | ((lane & 3) << 1) | (i & 1));
+            px += k - k_prev;
+            k_prev = k;
+            while (px >= wx) {
+                px -= wx;
+                ++py;
+            }
+            const int pp = pb + k;
+            float x = 0.f;
+            if (jv && pp < p1) {
+                const long long o = (long long)(f.x + py) * nx + (f.z + px);
+                x = fmaf(s0, __ldg(imgj + o), __ldg(Pj + pp));
+            }
+            v[i] = x;
+        }
+    };
+    // one stage: wait until the MMAs that last read buffer it & 1 are done,
+    // write the stage from registers, issue its four MMAs and commit
+    auto process = [&](int it, const float (&v)[VPT]) -> bool {
         const int st = it & 1;
-        if (it >= 2) {                                    // the MMAs that read this stage are done
+        if (it >= 2) {
             if (!mbar_wait(&s_bar[st], uint32_t(((it - 2) >> 1) & 1))) {
                 if (lane == 0) atomicExch(&s_fail, 1);
             }
             __syncthreads();
-            ok = s_fail == 0;
-            if (!ok) break;
+            if (s_fail) return false;
         }
-        // fill rows 0..31 (channels) x KS pixels of this stage
-        const int pb = p0 + it * KS;
+        // core matrix (row group warp, K column kq), row j & 7, slot lane & 3:
+        // byte warp*1024 + kq*128 + lane*4
         uint8_t *buf = s_stage[st];
-        for (int e = tid; e < 1024; e += kTcThreads) {
-            const int wi = e >> 5, ln = e & 31;
-            const int jg = wi & 3, kq = wi >> 2;          // 8-row group, 16-byte K column
-            const int j = (jg << 3) | (ln >> 2);
+#pragma unroll
+        for (int kq = 0; kq < 8; ++kq) {
             uint32_t word;
             if (KIND == 0) {
-                const int k = (kq << 2) | (ln & 3);
-                const int pp = pb + k;
-                float v = 0.f;
-                if (j < Lc && pp < p1) {
-                    const int py = pp / wx, px = pp - py * wx;
-                    const long long o = (long long)(f.x + py) * nx + (f.z + px);
-                    v = fmaf(s0, img[(long long)(c + j * C) * N + o], Pq[(long long)j * npix + pp]);
-                }
-                word = to_tf32(v);
+                word = to_tf32(v[kq]);
             } else {
-                const int k = (kq << 3) | ((ln & 3) << 1);
-                float v0 = 0.f, v1 = 0.f;
-                if (j < Lc) {
-                    const int pp = pb + k;
-                    if (pp < p1) {
-                        const int py = pp / wx, px = pp - py * wx;
-                        const long long o = (long long)(f.x + py) * nx + (f.z + px);
-                        v0 = fmaf(s0, img[(long long)(c + j * C) * N + o], Pq[(long long)j * npix + pp]);
-                    }
-                    if (pp + 1 < p1) {
-                        const int py = (pp + 1) / wx, px = (pp + 1) - py * wx;
-                        const long long o = (long long)(f.x + py) * nx + (f.z + px);
-                        v1 = fmaf(s0, img[(long long)(c + j * C) * N + o], Pq[(long long)j * npix + pp + 1]);
-                    }
-                }
-                const __nv_bfloat162 b = __floats2bfloat162_rn(v0, v1);
+                const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * kq], v[2 * kq + 1]);
                 word = *reinterpret_cast<const uint32_t *>(&b);
             }
-            // core matrix (jg, kq), row j & 7, 4-byte slot ln & 3 -> byte jg*1024 + kq*128 + ln*4
-            *reinterpret_cast<uint32_t *>(buf + jg * 1024 + kq * 128 + ln * 4) = word;
+            *reinterpret_cast<uint32_t *>(buf + warp * 1024 + kq * 128 + lane * 4) = word;
         }
         fence_async_smem();
         fence_before_sync();
@@ -214,6 +220,17 @@ __global__ void __launch_bounds__(kTcThreads) gram_tc_kernel(const float *__rest
             }
             umma_commit(&s_bar[st]);
         }
+        return true;
+    };
+    float ra[VPT], rb[VPT];
+    load_stage(0, ra);
+    bool ok = true;
+    for (int it = 0; it < n_stage && ok; it += 2) {
+        if (it + 1 < n_stage) load_stage(it + 1, rb);
+        ok = process(it, ra);
+        if (!ok || it + 1 >= n_stage) break;
+        if (it + 2 < n_stage) load_stage(it + 2, ra);
+        ok = process(it + 1, rb);
     }
     // the last commit covers every MMA issued before it
     if (ok) {

@@ -139,15 +139,20 @@ __global__ void __launch_bounds__(256) gram32_kernel(const float *__restrict__ P
 // commute).  Bounded sweeps.  Then either the SVT mixing matrix
 // M = V diag(min(1, mu_bar w_i / s_i)) V^T or the reweighting weights.
 // NMAX = 16: four warps (four matrices) per CTA; NMAX = 32: one.
+// eigv (n x n per matrix, n = L_c rounded up to even), when not NULL, holds
+// the eigenvectors found at the previous call and receives the new ones: the
+// sweeps start from V0^T G V0, which is nearly diagonal when the facet changes
+// little between iterations, so far fewer sweeps reach the same tolerance.
 template <int NMAX>
 __global__ void __launch_bounds__(NMAX == 16 ? 128 : 32) eig_kernel(double *__restrict__ gram,
                                                                     float *__restrict__ mix,
                                                                     float *__restrict__ wnuc, int n_mat, int Lc,
                                                                     double mu_bar, double upsilon_bar,
-                                                                    bool reweight) {
+                                                                    bool reweight, double *__restrict__ eigv) {
     constexpr int kEigWarps = NMAX == 16 ? 4 : 1;
     __shared__ double s_a[kEigWarps][NMAX][NMAX + 1];
     __shared__ double s_v[kEigWarps][NMAX][NMAX + 1];
+    __shared__ double s_t[kEigWarps][NMAX][NMAX + 1];
     __shared__ double s_cs[kEigWarps][NMAX / 2], s_sn[kEigWarps][NMAX / 2];
     __shared__ int s_p[kEigWarps][NMAX / 2], s_q[kEigWarps][NMAX / 2];
     __shared__ int s_ord[kEigWarps][NMAX];
@@ -167,6 +172,27 @@ __global__ void __launch_bounds__(NMAX == 16 ? 128 : 32) eig_kernel(double *__re
     }
     __syncwarp();
     for (int e = lane; e < Lc * Lc; e += 32) G[e] = 0.0;   // ready for the next accumulation
+    double *Vg = eigv ? eigv + (long long)cq * n * n : nullptr;
+    if (Vg) {
+        // T = A V0, then A = V0^T T; V = V0
+        double(*T)[NMAX + 1] = s_t[w];
+        for (int e = lane; e < n * n; e += 32) V[e / n][e % n] = Vg[e];
+        __syncwarp();
+        for (int e = lane; e < n * n; e += 32) {
+            const int i = e / n, j = e - (e / n) * n;
+            double t = 0.0;
+            for (int k = 0; k < n; ++k) t = fma(a[i][k], V[k][j], t);
+            T[i][j] = t;
+        }
+        __syncwarp();
+        for (int e = lane; e < n * n; e += 32) {
+            const int i = e / n, j = e - (e / n) * n;
+            double t = 0.0;
+            for (int k = 0; k < n; ++k) t = fma(V[k][i], T[k][j], t);
+            a[i][j] = t;
+        }
+        __syncwarp();
+    }
     const int half = n / 2;
     for (int sweep = 0; sweep < 40; ++sweep) {
         double off = 0.0, dia = 0.0;
@@ -226,6 +252,8 @@ __global__ void __launch_bounds__(NMAX == 16 ? 128 : 32) eig_kernel(double *__re
             __syncwarp();
         }
     }
+    if (Vg)
+        for (int e = lane; e < n * n; e += 32) Vg[e] = V[e / n][e % n];
     if (lane == 0) {                          // eigenvalues descending (padding excluded)
         int *ord = s_ord[w];
         for (int i = 0; i < Lc; ++i) ord[i] = i;
@@ -329,12 +357,13 @@ cudaError_t launch_nuclear_gram(fhs_problem *p, const float *img, bool with_dual
 
 cudaError_t launch_nuclear_eig(fhs_problem *p, bool reweight, cudaStream_t s) {
     const int n = p->C * p->Q;
+    double *v0 = reweight ? nullptr : p->eigv;     // the reweighting Gram (of x) starts cold
     if (p->Lc <= 16)
         eig_kernel<16><<<(n + 3) / 4, 128, 0, s>>>(p->gram, p->mix, p->wnuc, n, p->Lc, p->prm.mu_bar,
-                                                  p->prm.upsilon_bar, reweight);
+                                                  p->prm.upsilon_bar, reweight, v0);
     else
         eig_kernel<32><<<n, 32, 0, s>>>(p->gram, p->mix, p->wnuc, n, p->Lc, p->prm.mu_bar, p->prm.upsilon_bar,
-                                         reweight);
+                                         reweight, v0);
     p->n_launch += 1;
     return cudaGetLastError();
 }

@@ -47,6 +47,11 @@ WORKLOADS = {
                   qy=3, qx=2, overlap=0.15, w_max=2000.0, n_iter=20, n_reweight=1),
     "tiny": dict(config_id=12, ny=32, nx=48, L=2, M=700, B=2, C=1,
                  qy=2, qx=2, overlap=0.2, w_max=0.0, n_iter=10, n_reweight=0),
+    # The 32-channel facet Gram of the 2048x2048 mixed-precision configuration
+    # (8x8 facets, 10% overlap) as one sub-cube, with few visibilities: the
+    # Gram, the 32x32 eigendecomposition and the apply do not depend on M.
+    "gram32_2048": dict(config_id=13, ny=2048, nx=2048, L=32, M=200_000, B=8, C=1,
+                        qy=8, qx=8, overlap=0.1, w_max=0.0, n_iter=20, n_reweight=0),
 }
 
 
