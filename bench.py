@@ -232,6 +232,8 @@ def run_gpu(args):
     k_ms = phases["degrid_grid"] / max(n_prof, 1)
     achieved = kbytes / (k_ms * 1e-3) / 1e9
     traffic, limiter = _profile_traffic("k_binned.cu")
+    if args.workload != WORKLOAD:
+        traffic = None          # the committed capture is scaled to the default workload only
     # visibilities through Phi and Phi^H per second inside the PDFB iteration
     vis_s = Mtot / (ms_step * 1e-3)
     out = {
