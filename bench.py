@@ -174,6 +174,9 @@ def run_gpu(args):
     info = prob.info
 
     # ---- device-resident timing of K iterations (problem already on the GPU)
+    if args.autotune:
+        prob.autotune_bins()
+    info = prob.info
     for _ in range(args.warmup):
         prob.step(1)
     torch.cuda.synchronize()
@@ -253,7 +256,9 @@ def run_gpu(args):
                    "subcubes": P.C, "vis_per_channel": M, "blocks": P.B, "facets": "%dx%d" % (P.qy, P.qx),
                    "facet_overlap": P.overlap, "w_max": P.w_max, "nnz_G": info.nnz,
                    "l2": "inputs larger than L2 (G factors alone %.1f GB per iteration)" % (info.n_gfac * 8 / 1e9),
-                   "mu": MU, "mu_bar": MU_BAR, "gram": args.gram},
+                   "mu": MU, "mu_bar": MU_BAR, "gram": args.gram,
+                   "bins": {"dense_min": info.bin_dense_min, "split": info.bin_split,
+                            "autotuned": bool(args.autotune)}},
         "vis_per_s": ws * vis_s,
         "phi_vis_per_s": ws * Mtot / (phi_ms * 1e-3),
         "phi_adjoint_vis_per_s": ws * Mtot / (phit_ms * 1e-3),
@@ -449,6 +454,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--e2e-iters", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="measure candidate tile binnings of the pass over G before timing")
     ap.add_argument("--gram", default="fp32", choices=["fp32", "tf32", "bf16", "fp64"],
                     help="arithmetic of the nuclear facet Gram (tf32/bf16: tensor cores)")
     ap.add_argument("--mode", default="pdfb", choices=["pdfb", "serve"])

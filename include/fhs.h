@@ -131,6 +131,8 @@ typedef struct fhs_info {
     double  phi_norm2_max;   /* max_l ||Phi_l||^2 (0 if sigma2 was given)          */
     int64_t n_gfac;          /* stored G values: each row is the outer product of
                                 two 1-D factors of T taps, kept as 2T values     */
+    int32_t bin_dense_min;   /* binning of the pass over G (fhs_autotune_bins)     */
+    int32_t bin_split;
 } fhs_info;
 
 fhs_status fhs_get_info(const fhs_problem *prob, fhs_info *info);
@@ -231,6 +233,18 @@ typedef enum {
 fhs_status fhs_state_size(const fhs_problem *prob, int32_t part, int64_t *n_floats);
 fhs_status fhs_get_state(fhs_problem *prob, int32_t part, float *dst_dev, void *stream);
 fhs_status fhs_set_state(fhs_problem *prob, int32_t part, const float *src_dev, void *stream);
+
+/* Pick the tile binning of the pass over G by measurement (a layout choice of
+ * this library; no passage of the paper defines it).  Times the
+ * normal-mode pass G^H G on a random image under the binning in use and
+ * under candidate binnings (dense-bin minimum 16/32/48/96 rows, bins of at
+ * most 192/288/384 rows cut into equal parts), and keeps a candidate only if
+ * it is at least 3 % faster.  The PDFB state is unchanged; the result of every
+ * operator is the same up to the summation order of the adjoint.  Returns the
+ * binning kept (either out pointer may be NULL).  Allocates the candidate
+ * bins on `stream`; synchronises it.  A captured iteration graph is dropped
+ * and recaptured by the next step. */
+fhs_status fhs_autotune_bins(fhs_problem *prob, void *stream, int32_t *dense_min_out, int32_t *split_out);
 
 /* ||Phi_l||^2 for every channel: the largest Ritz value after n_iter Lanczos
  * steps on Re(Phi_l^H Phi_l) from a fixed start (rises monotonically to the

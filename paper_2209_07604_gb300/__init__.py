@@ -25,7 +25,7 @@ EXPORTED = [
     "fhs_last_error", "fhs_profile_enable", "fhs_profile_read", "fhs_kernel_launches",
     "fhs_sara_analysis_noalloc", "fhs_pdfb_step_batch", "fhs_use_graphs", "fhs_estimate_bytes",
     "fhs_server_create", "fhs_server_submit", "fhs_server_query", "fhs_server_wait", "fhs_server_stats",
-    "fhs_server_destroy", "fhs_device_status",
+    "fhs_server_destroy", "fhs_device_status", "fhs_autotune_bins",
 ]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 GRAM_FP32, GRAM_TF32, GRAM_BF16, GRAM_FP64 = range(4)
@@ -55,7 +55,7 @@ class fhs_info(C.Structure):
         ("n_vis", C.c_int64), ("nnz", C.c_int64), ("n_coef", C.c_int64), ("nuclear_size", C.c_int64),
         ("device_bytes", C.c_int64), ("n_facets", C.c_int32), ("iteration", C.c_int32), ("tau", C.c_double),
         ("sigma0", C.c_double), ("sigma1", C.c_double), ("sigma2", C.c_double), ("phi_norm2_max", C.c_double),
-        ("n_gfac", C.c_int64),
+        ("n_gfac", C.c_int64), ("bin_dense_min", C.c_int32), ("bin_split", C.c_int32),
     ]
 
 
@@ -306,6 +306,14 @@ def fhs_device_status(prob, stream=None):
     _check(load_library().fhs_device_status(prob, _stream(stream)))
 
 
+def fhs_autotune_bins(prob, stream=None):
+    """Time candidate tile binnings of the pass over G and keep the fastest;
+    returns (dense_min, split) of the binning in use afterwards."""
+    dm, sp = C.c_int32(0), C.c_int32(0)
+    _check(load_library().fhs_autotune_bins(prob, _stream(stream), C.byref(dm), C.byref(sp)))
+    return dm.value, sp.value
+
+
 def fhs_kernel_launches(prob) -> int:
     n = C.c_int64(0)
     _check(load_library().fhs_kernel_launches(prob, C.byref(n)))
@@ -465,3 +473,9 @@ class Problem:
 
     def operator_norms(self, n_iter=100):
         return fhs_operator_norms(self.handle, n_iter, self.L)
+
+    def autotune_bins(self, stream=None):
+        """Measure candidate binnings of the pass over G; keep the fastest."""
+        out = fhs_autotune_bins(self.handle, stream)
+        self.info = fhs_get_info(self.handle)
+        return out

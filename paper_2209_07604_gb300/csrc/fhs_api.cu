@@ -131,6 +131,55 @@ void free_all(fhs_problem *p) {
 
 inline cudaStream_t S(void *s) { return static_cast<cudaStream_t>(s); }
 
+// Tile bins of the single-pass data kernel (k_binned.cu): inside each
+// (channel, block) segment, a run of rows whose box corners share one grid tile
+// becomes shared-memory bins when it holds at least dense_min rows, cut into
+// parts of at most `split` rows (equal parts when `even`, else full parts and
+// a remainder); shorter runs are packed in order into sparse bins of at most
+// sparse_max rows, which take the global-memory path.
+void make_bins(const int2 *meta, const std::vector<long long> &seg_off, int n_seg, int ntx, long long dense_min,
+               long long split, bool even, long long sparse_max, std::vector<long long> &bstart,
+               std::vector<int> &bseg, std::vector<int> &btile) {
+    bstart.clear();
+    bseg.clear();
+    btile.clear();
+    auto key = [&](long long i) {
+        return (meta[i].x & 0xffff) / kTile * ntx + (int)((unsigned)meta[i].x >> 16) / kTile;
+    };
+    for (int sg = 0; sg < n_seg; ++sg) {
+        const long long a = seg_off[sg], b = seg_off[sg + 1];
+        long long sp0 = -1;                          // open sparse run start
+        auto flush_sparse = [&](long long end) {
+            for (long long q = sp0; q < end; q += sparse_max) {
+                bstart.push_back(q);
+                bseg.push_back(sg);
+                btile.push_back(-1);
+            }
+            sp0 = -1;
+        };
+        long long i = a;
+        while (i < b) {
+            const int k = key(i);
+            long long j = i + 1;
+            while (j < b && key(j) == k) ++j;
+            if (j - i >= dense_min) {
+                if (sp0 >= 0) flush_sparse(i);
+                const long long n = j - i;
+                const long long parts = (n + split - 1) / split;
+                for (long long t = 0; t < parts; ++t) {
+                    bstart.push_back(even ? i + n * t / parts : i + t * split);
+                    bseg.push_back(sg);
+                    btile.push_back(k);
+                }
+            } else if (sp0 < 0) {
+                sp0 = i;
+            }
+            i = j;
+        }
+        if (sp0 >= 0) flush_sparse(b);
+    }
+}
+
 fhs_status check_params(const fhs_params *q) {
     if (!q) return fail(FHS_ERR_ARG, "params is NULL");
     if (q->ny < 16 || q->nx < 16 || (q->ny & 1) || (q->nx & 1))
@@ -688,46 +737,15 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
     p->n_chunk = int(cseg.size());
     cstart.push_back(Mtot);
 
-    // ---- tile bins for the single-pass data kernel: runs of one tile key of at
-    // least kDenseMin visibilities become shared-memory bins (split at kBinMax);
-    // shorter runs are packed into sparse bins that take the global path.
-    #ifndef FHS_BIN_MAX
-#define FHS_BIN_MAX 384
-#endif
-    constexpr long long kDenseMin = 48, kBinMax = FHS_BIN_MAX, kSparseMax = FHS_BIN_MAX;   // smem capacity of a bin
+    // ---- tile bins for the single-pass data kernel (make_bins); fhs_autotune_bins
+    // may replace them with a measured choice
     std::vector<long long> bstart;
     std::vector<int> bseg, btile;
     p->ntx = ntx;
-    for (int sg = 0; sg < p->n_seg; ++sg) {
-        const long long a = p->seg_off[sg], b = p->seg_off[sg + 1];
-        long long sp0 = -1;                          // open sparse run start
-        auto flush_sparse = [&](long long end) {
-            for (long long q = sp0; q < end; q += kSparseMax) {
-                bstart.push_back(q);
-                bseg.push_back(sg);
-                btile.push_back(-1);
-            }
-            sp0 = -1;
-        };
-        long long i = a;
-        while (i < b) {
-            const int k = (meta[i].x & 0xffff) / kTile * ntx + (int)((unsigned)meta[i].x >> 16) / kTile;
-            long long j = i + 1;
-            while (j < b && (meta[j].x & 0xffff) / kTile * ntx + (int)((unsigned)meta[j].x >> 16) / kTile == k) ++j;
-            if (j - i >= kDenseMin) {
-                if (sp0 >= 0) flush_sparse(i);
-                for (long long q = i; q < j; q += kBinMax) {
-                    bstart.push_back(q);
-                    bseg.push_back(sg);
-                    btile.push_back(k);
-                }
-            } else if (sp0 < 0) {
-                sp0 = i;
-            }
-            i = j;
-        }
-        if (sp0 >= 0) flush_sparse(b);
-    }
+    make_bins(meta.data(), p->seg_off, p->n_seg, ntx, kBinDenseMin, kBinSplitMax, false, kBinSplitMax, bstart, bseg,
+              btile);
+    p->bin_dense_min = int(kBinDenseMin);
+    p->bin_split = int(kBinSplitMax);
     p->n_bin = int(bseg.size());
     bstart.push_back(Mtot);
 
@@ -1079,6 +1097,8 @@ fhs_status fhs_get_info(const fhs_problem *p, fhs_info *info) {
     info->sigma2 = p->sigma2;
     info->phi_norm2_max = p->phi_norm2_max;
     info->n_gfac = p->n_fac;
+    info->bin_dense_min = p->bin_dense_min;
+    info->bin_split = p->bin_split;
     return FHS_OK;
 }
 
@@ -1222,6 +1242,134 @@ fhs_status fhs_set_state(fhs_problem *p, int32_t part, const float *src, void *s
         case FHS_STATE_WEIGHTS_SARA: CU(cudaMemcpyAsync(p->w21, src, b, cudaMemcpyDeviceToDevice, s)); break;
         case FHS_STATE_WEIGHTS_NUC: CU(cudaMemcpyAsync(p->wnuc, src, b, cudaMemcpyDeviceToDevice, s)); break;
     }
+    return FHS_OK;
+}
+
+fhs_status fhs_autotune_bins(fhs_problem *p, void *stream, int32_t *dense_min_out, int32_t *split_out) {
+    if (!p) return fail(FHS_ERR_ARG, "NULL problem");
+    cudaStream_t s = S(stream);
+    if (p->Mtot == 0 || p->n_bin == 0) {
+        if (dense_min_out) *dense_min_out = p->bin_dense_min;
+        if (split_out) *split_out = p->bin_split;
+        return FHS_OK;
+    }
+    CU(cudaStreamSynchronize(s));
+    std::vector<int2> meta(p->Mtot);
+    CU(cudaMemcpyAsync(meta.data(), p->meta, sizeof(int2) * p->Mtot, cudaMemcpyDeviceToHost, s));
+    // a forward grid of a random image (scratch: coef_tmp, grid_in, grid_aux); the
+    // normal-mode pass accumulates into the first L block grids, zero again after
+    const long long LN = (long long)p->L * p->N;
+    std::vector<float> x0(LN);
+    unsigned long long st = 0x2545F4914F6CDD1Dull;
+    for (long long i = 0; i < LN; ++i) {
+        st = st * 6364136223846793005ull + 1442695040888963407ull;
+        x0[i] = float(double(st >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+    }
+    TRY(upload(p->coef_tmp, x0.data(), LN, s));
+    CU(launch_zpad(p, p->coef_tmp, p->grid_in, s));
+    TRY(fft(p, p->grid_in, p->grid_aux, CUFFT_FORWARD, s));
+
+    struct Bins {
+        long long *start = nullptr;
+        int *seg = nullptr, *tile = nullptr;
+        int n = 0, dense_min = 0, split = 0;
+        size_t bytes = 0;
+    };
+    Bins cur{p->bin_start, p->bin_seg, p->bin_tile, p->n_bin, p->bin_dense_min, p->bin_split,
+             sizeof(long long) * (p->n_bin + 1) + 2 * sizeof(int) * p->n_bin};
+    cudaStream_t home = p->home;
+    p->home = s;                                       // candidate arrays live on this call's stream
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    fhs_status rs = FHS_OK;
+    auto time_bins = [&](const Bins &b, float &ms) -> fhs_status {
+        p->bin_start = b.start;
+        p->bin_seg = b.seg;
+        p->bin_tile = b.tile;
+        p->n_bin = b.n;
+        CU(launch_normal(p, p->grid_aux, p->grid_blk, s));          // warm-up
+        CU(cudaEventRecord(e0, s));
+        for (int r = 0; r < 3; ++r) CU(launch_normal(p, p->grid_aux, p->grid_blk, s));
+        CU(cudaEventRecord(e1, s));
+        CU(cudaEventSynchronize(e1));
+        CU(cudaEventElapsedTime(&ms, e0, e1));
+        return FHS_OK;
+    };
+    Bins best = cur;
+    float best_ms = 0.f;
+    auto run = [&]() -> fhs_status {
+        CU(cudaEventCreate(&e0));
+        CU(cudaEventCreate(&e1));
+        TRY(time_bins(cur, best_ms));
+        const long long dmins[] = {16, 32, 48, 96};
+        const long long splits[] = {192, 288, kBinSplitMax};
+        std::vector<long long> bstart;
+        std::vector<int> bseg, btile;
+        for (long long dm : dmins)
+            for (long long sp : splits) {
+                if (sp > kBinSplitMax) continue;
+                make_bins(meta.data(), p->seg_off, p->n_seg, p->ntx, dm, sp, true, kBinSplitMax, bstart, bseg, btile);
+                Bins c;
+                c.n = int(bseg.size());
+                c.dense_min = int(dm);
+                c.split = int(sp);
+                bstart.push_back(p->Mtot);
+                TRY(dev_alloc(p, &c.start, bstart.size(), false));
+                TRY(dev_alloc(p, &c.seg, bseg.size(), false));
+                TRY(dev_alloc(p, &c.tile, btile.size(), false));
+                c.bytes = sizeof(long long) * bstart.size() + sizeof(int) * (bseg.size() + btile.size());
+                TRY(upload(c.start, bstart.data(), bstart.size(), s));
+                TRY(upload(c.seg, bseg.data(), bseg.size(), s));
+                TRY(upload(c.tile, btile.data(), btile.size(), s));
+                float ms = 0.f;
+                TRY(time_bins(c, ms));
+                Bins loser = c;
+                if (ms < 0.97f * best_ms) {            // keep a candidate only for a clear gain
+                    loser = best;
+                    best = c;
+                    best_ms = ms;
+                }
+                if (loser.start != cur.start) {
+                    dev_free(p, loser.start);
+                    dev_free(p, loser.seg);
+                    dev_free(p, loser.tile);
+                    p->bytes -= loser.bytes;
+                }
+            }
+        return FHS_OK;
+    };
+    rs = run();
+    if (rs != FHS_OK && best.start != cur.start) {      // a failed search keeps the original bins
+        dev_free(p, best.start);
+        dev_free(p, best.seg);
+        dev_free(p, best.tile);
+        p->bytes -= best.bytes;
+        best = cur;
+    }
+    p->bin_start = best.start;
+    p->bin_seg = best.seg;
+    p->bin_tile = best.tile;
+    p->n_bin = best.n;
+    p->bin_dense_min = best.dense_min;
+    p->bin_split = best.split;
+    if (best.start != cur.start) {
+        dev_free(p, cur.start);
+        dev_free(p, cur.seg);
+        dev_free(p, cur.tile);
+        p->bytes -= cur.bytes;
+    }
+    p->home = home;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (p->gexec) {                                    // the captured iteration holds the old bins
+        cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
+    }
+    CU(cudaMemsetAsync(p->grid_blk, 0, sizeof(float2) * p->K * p->L, s));
+    CU(cudaMemsetAsync(p->coef_tmp, 0, sizeof(float) * LN, s));
+    CU(cudaStreamSynchronize(s));
+    if (rs != FHS_OK) return rs;
+    if (dense_min_out) *dense_min_out = p->bin_dense_min;
+    if (split_out) *split_out = p->bin_split;
     return FHS_OK;
 }
 

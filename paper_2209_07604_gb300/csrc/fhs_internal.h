@@ -19,7 +19,13 @@ constexpr int kNumDb = 8;          // db1..db8
 constexpr int kMaxF = 16;          // taps of db8
 constexpr int kMaxLc = 32;         // channels per sub-cube supported
 constexpr int kMaxWHalf = 4;       // largest w-kernel half-width h
-constexpr int kTile = 32;          // grid tile (cells) used to sort visibilities
+constexpr int kTile = 32;
+#ifndef FHS_BIN_MAX
+#define FHS_BIN_MAX 384
+#endif
+// Rows per bin of the data kernel: at most kBinSplitMax (its shared-memory
+// staging capacity); tile runs shorter than kBinDenseMin go to sparse bins.
+constexpr long long kBinSplitMax = FHS_BIN_MAX, kBinDenseMin = 48;          // grid tile (cells) used to sort visibilities
 constexpr float kSaraScale = 1.0f / 3.0f;   // 1/sqrt(9 bases)
 
 // ---------------------------------------------------------------------------
@@ -84,6 +90,7 @@ struct fhs_problem {
     double *eps = nullptr;                    // [n_seg]
     float *blk_scale = nullptr;               // [n_seg]  (1 - m_b)
     int n_bin = 0, ntx = 0;                   // tile bins of the single-pass data kernel
+    int bin_dense_min = 0, bin_split = 0;     // binning in use (defaults or fhs_autotune_bins)
     long long *bin_start = nullptr;           // [n_bin+1]
     int *bin_seg = nullptr;                   // [n_bin]
     int *bin_tile = nullptr;                  // [n_bin] tile key, -1 = sparse (global path)
