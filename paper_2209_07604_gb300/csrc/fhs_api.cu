@@ -410,14 +410,11 @@ fhs_status one_iteration(fhs_problem *p, cudaStream_t s) {
         Phase ph(p, s, FHS_PHASE_PRIMAL);
         CU(launch_primal(p, s));
     }
-    // fork: the prior branches only read xbar; tracing keeps one stream so that
-    // its per-phase event pairs time one phase at a time
+    // the prior branches only read xbar and fork off after the pass over G (they
+    // then overlap the combine and F^H; beside the pass itself they take the
+    // shared memory it needs and cost more than they save); tracing keeps one
+    // stream so that its per-phase event pairs time one phase at a time
     const bool fork = !p->prof_on && p->s_sara && p->s_nuc && (sara_active(p) || nuc_active(p));
-    if (fork) {
-        CU(cudaEventRecord(p->ev_fork, s));
-        CU(cudaStreamWaitEvent(p->s_sara, p->ev_fork, 0));
-        CU(cudaStreamWaitEvent(p->s_nuc, p->ev_fork, 0));
-    }
     // data fidelity: F, single pass over G, l2-ball factors, combine, F^H
     {
         Phase ph(p, s, FHS_PHASE_FFT_FWD);
@@ -426,6 +423,11 @@ fhs_status one_iteration(fhs_problem *p, cudaStream_t s) {
     {
         Phase ph(p, s, FHS_PHASE_DEGRID_GRID);
         CU(launch_degrid_grid_fused(p, s));
+    }
+    if (fork) {
+        CU(cudaEventRecord(p->ev_fork, s));
+        CU(cudaStreamWaitEvent(p->s_sara, p->ev_fork, 0));
+        CU(cudaStreamWaitEvent(p->s_nuc, p->ev_fork, 0));
     }
     {
         Phase ph(p, s, FHS_PHASE_L2BALL);
@@ -664,10 +666,10 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
         long long c1 = (p01 - h) % K1; if (c1 < 0) c1 += K1;
         long long c2 = (p02 - h) % K2; if (c2 < 0) c2 += K2;
         corner1[i] = int(c1); corner2[i] = int(c2); Tv[i] = T; pl[i] = pv + P1;
-        key[i] = int(c1 / kTile) * ntx + int(c2 / kTile);
+        key[i] = (int(c1 / kTile) * ntx + int(c2 / kTile)) * 17 + T;   // tile, then box side
     }
     });
-    const int nkeys = nty * ntx;
+    const int nkeys = nty * ntx * 17;
     std::vector<long long> perm(Mtot);
     // counting sort by tile key, segments in parallel (each segment is stable)
     parallel_for(p->n_seg, [&](long long s0, long long s1) {

@@ -169,6 +169,116 @@ __device__ __forceinline__ void bin_rows(int i0, int nv, int lane, const int2 *s
     }
 }
 
+// Columns [C0, C0 + CW) of the gather of one row by one lane:
+// sum_t1 g1[t1] sum_t2 g2[t2] X[c1+t1][c2+t2], with g2 of those columns in
+// registers (zero beyond T).
+template <int C0, int CW, bool DENSE>
+__device__ __forceinline__ void gather_cols(const float2 *__restrict__ f, int T, int c1, int c2,
+                                            const float2 *s_grid, int wy0, int wx0,
+                                            const float2 *__restrict__ gl, int K1, int K2, float &ar, float &ai) {
+    float2 g2[CW];
+#pragma unroll
+    for (int t = 0; t < CW; ++t) g2[t] = (C0 + t < T) ? __ldg(f + T + C0 + t) : make_float2(0.f, 0.f);
+    int k2[DENSE ? 1 : CW];
+    if (!DENSE) {
+#pragma unroll
+        for (int t = 0; t < CW; ++t) {
+            k2[t] = c2 + C0 + t;
+            k2[t] -= (k2[t] >= K2) ? K2 : 0;
+        }
+    }
+    for (int t1 = 0; t1 < T; ++t1) {
+        const float2 a = __ldg(f + t1);
+        float br = 0.f, bi = 0.f;
+        if (DENSE) {
+            const float2 *row = s_grid + (c1 - wy0 + t1) * kWin + (c2 - wx0 + C0);
+#pragma unroll
+            for (int t2 = 0; t2 < CW; ++t2) {
+                const float2 x = row[t2];
+                br = fmaf(g2[t2].x, x.x, fmaf(-g2[t2].y, x.y, br));
+                bi = fmaf(g2[t2].x, x.y, fmaf(g2[t2].y, x.x, bi));
+            }
+        } else {
+            int k1 = c1 + t1;
+            k1 -= (k1 >= K1) ? K1 : 0;
+            const float2 *row = gl + (long long)k1 * K2;
+#pragma unroll
+            for (int t2 = 0; t2 < CW; ++t2) {
+                const float2 x = row[k2[t2]];
+                br = fmaf(g2[t2].x, x.x, fmaf(-g2[t2].y, x.y, br));
+                bi = fmaf(g2[t2].x, x.y, fmaf(g2[t2].y, x.x, bi));
+            }
+        }
+        ar = fmaf(a.x, br, fmaf(-a.y, bi, ar));
+        ai = fmaf(a.x, bi, fmaf(a.y, br, ai));
+    }
+}
+
+// Gather of one row by one lane: phi = sum_t1 g1[t1] sum_t2 g2[t2] X[c1+t1][c2+t2].
+// TT >= T is the warp's largest side rounded to a compiled size; each entry
+// costs one load of X and four FMAs with every lane busy and no reduction
+// across lanes.  Sides above 8 take two passes over the rows (8 columns of
+// g2 in registers at a time, under the 64-register cap).
+template <int TT, bool DENSE>
+__device__ __forceinline__ float2 gather_lane(const float2 *__restrict__ f, int T, int c1, int c2,
+                                              const float2 *s_grid, int wy0, int wx0,
+                                              const float2 *__restrict__ gl, int K1, int K2) {
+    float ar = 0.f, ai = 0.f;
+    if (TT <= 8) {
+        gather_cols<0, TT, DENSE>(f, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2, ar, ai);
+    } else {
+        gather_cols<0, 8, DENSE>(f, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2, ar, ai);
+        gather_cols<8, (TT > 8 ? TT - 8 : 1), DENSE>(f, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2, ar, ai);
+    }
+    return make_float2(ar, ai);
+}
+
+// Phase 1 of a bin: one row per thread (rows are sorted by T inside each tile
+// run, so a warp's rows mostly share T).  kFused: the data-dual pre-update
+// d = s_b d + sigma2 (phi - y) into s_d, the bin's output and the block norm;
+// kGather: phi to the output; kNormal: phi into s_d for the scatter.
+template <int MODE, bool DENSE>
+__device__ __forceinline__ void gather_phase(int nv, const int2 *s_meta, const int *s_off, const float2 *s_y,
+                                             float2 *s_d, const float2 *__restrict__ fbin, const float2 *s_grid,
+                                             int wy0, int wx0, const float2 *__restrict__ gl, int K1, int K2,
+                                             float sc, float sigma2, float2 *__restrict__ dvis_bin, Kahan &nrm) {
+    const int nvr = (nv + 31) & ~31;                 // whole warps: the max below takes every lane
+    for (int i = threadIdx.x; i < nvr; i += blockDim.x) {
+        const bool valid = i < nv;
+        int T = 0, c1 = 0, c2 = 0;
+        const float2 *f = fbin;
+        if (valid) {
+            const int2 m = s_meta[i];
+            T = m.y;
+            c1 = m.x & 0xffff;
+            c2 = (int)((unsigned)m.x >> 16);
+            f = fbin + s_off[i];
+        }
+        const int tm = __reduce_max_sync(0xffffffffu, T);
+        float2 phi;
+        if (tm <= 4) phi = gather_lane<4, DENSE>(f, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
+        else if (tm <= 7) phi = gather_lane<7, DENSE>(f, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
+        else if (tm <= 9) phi = gather_lane<9, DENSE>(f, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
+        else if (tm <= 11) phi = gather_lane<11, DENSE>(f, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
+        else if (tm <= 13) phi = gather_lane<13, DENSE>(f, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
+        else phi = gather_lane<16, DENSE>(f, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
+        if (!valid) continue;
+        if (MODE == kFused) {
+            const float2 dold = s_d[i];
+            const float2 sy = s_y[i];
+            const float dr = fmaf(sc, dold.x, fmaf(sigma2, phi.x, -sy.x));
+            const float di = fmaf(sc, dold.y, fmaf(sigma2, phi.y, -sy.y));
+            dvis_bin[i] = make_float2(dr, di);
+            s_d[i] = make_float2(dr, di);
+            nrm.add(fmaf(dr, dr, di * di));
+        } else if (MODE == kGather) {
+            dvis_bin[i] = phi;
+        } else {
+            s_d[i] = phi;
+        }
+    }
+}
+
 // Four CTAs per SM (64 registers, 46 KB shared each): the kernel is latency
 // bound, and occupancy matters more than the registers the cap takes away.
 #ifndef FHS_FUSED_MIN_BLOCKS
@@ -235,12 +345,26 @@ __global__ void __launch_bounds__(256, FHS_FUSED_MIN_BLOCKS) degrid_grid_binned_
     }
     __syncthreads();
     Kahan nrm;
-    if (dense)
-        bin_rows<MODE, true>(warp, nv, lane, s_meta, s_off, s_y, s_d, fbin, s_grid, s_re, s_im, wy0, wx0, gl, gb,
-                             K1, K2, sc, sigma2, dvis + v0, nrm);
-    else
-        bin_rows<MODE, false>(warp, nv, lane, s_meta, s_off, s_y, s_d, fbin, s_grid, s_re, s_im, wy0, wx0, gl, gb,
-                              K1, K2, sc, sigma2, dvis + v0, nrm);
+    // phase 1: gathers, one row per thread
+    if (MODE != kScatter) {
+        if (dense)
+            gather_phase<MODE, true>(nv, s_meta, s_off, s_y, s_d, fbin, s_grid, wy0, wx0, gl, K1, K2, sc, sigma2,
+                                     dvis + v0, nrm);
+        else
+            gather_phase<MODE, false>(nv, s_meta, s_off, s_y, s_d, fbin, s_grid, wy0, wx0, gl, K1, K2, sc, sigma2,
+                                      dvis + v0, nrm);
+    }
+    // phase 2: scatters of conj(G_i) s_d[i], one row per warp
+    if (MODE != kGather) {
+        if (MODE != kScatter) __syncthreads();       // s_d holds the new values
+        Kahan unused;
+        if (dense)
+            bin_rows<kScatter, true>(warp, nv, lane, s_meta, s_off, s_y, s_d, fbin, s_grid, s_re, s_im, wy0, wx0,
+                                     gl, gb, K1, K2, sc, sigma2, dvis + v0, unused);
+        else
+            bin_rows<kScatter, false>(warp, nv, lane, s_meta, s_off, s_y, s_d, fbin, s_grid, s_re, s_im, wy0, wx0,
+                                      gl, gb, K1, K2, sc, sigma2, dvis + v0, unused);
+    }
     if (MODE != kFused) {
         if ((MODE == kScatter || MODE == kNormal) && dense) {
             __syncthreads();
@@ -258,7 +382,12 @@ __global__ void __launch_bounds__(256, FHS_FUSED_MIN_BLOCKS) degrid_grid_binned_
         }
         return;
     }
-    if (lane == 0) s_red[warp] = double(nrm.s) - double(nrm.c);
+    {
+        double v = double(nrm.s) - double(nrm.c);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_red[warp] = v;
+    }
     __syncthreads();
     if (dense) {
         for (int q = threadIdx.x; q < kWin * kWin; q += blockDim.x) {
