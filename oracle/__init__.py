@@ -8,7 +8,7 @@ matrix-vector products, dense SVD/eigh), written from the paper:
 
 * ``nufft``    measurement operator Phi_l = Theta_l G_l F Z (Sec. 2.1, Eq. 1),
                w-projection rows of G (Sec. 3.2), brute-force NUDFT, power
-               iteration for ||Phi_l||.
+               iteration and ARPACK Lanczos for ||Phi_l||^2.
 * ``wavelets`` Daubechies filters by spectral factorisation, the SARA
                dictionary (Dirac + db1..db8) and its exact faceted form
                (Sec. 2.2.2, spatial faceting).
@@ -16,6 +16,9 @@ matrix-vector products, dense SVD/eigh), written from the paper:
                singular-value soft-thresholding, nuclear facets.
 * ``pdfb``     the primal-dual forward-backward iteration for Eq. 3 with
                reweighting (Sec. 2.2.3).
+* ``defaults`` PSF-peak normalisation, residual and dirty image (Sec. 5.3),
+               dirty-image defaults of mu and mu_bar (a reading: the paper
+               defers the heuristics to Part I).
 
 Nothing here is shared with the CUDA library; the two implementations are
 compared in the tests.  Every function states the passage it follows and,
