@@ -65,8 +65,12 @@ typedef struct fhs_params {
     double  w_max;           /* w-projection planes span [-w_max, w_max]; 0 = off  */
     int32_t n_wplanes;       /* planes per sign (>= 2 when w_max > 0)              */
     double  pixel_size;      /* radians per pixel (w-term chirp, Sec. 3.2)         */
-    double  mu;              /* l21 (joint sparsity) regularisation, >= 0          */
-    double  mu_bar;          /* nuclear (low-rankness) regularisation, >= 0        */
+    double  mu;              /* l21 (joint sparsity) regularisation; 0 switches the
+                                prior off; < 0 selects 1 / sum_c ||Psi^dagger X_c||_{2,1}
+                                of the dirty cube X (see fhs_residual)              */
+    double  mu_bar;          /* nuclear (low-rankness) regularisation; 0 switches it
+                                off; < 0 selects 1 / sum_{c,q} ||S_q X_c||_* of the
+                                dirty cube X                                        */
     double  upsilon;         /* log-sum reweighting constant, l21 (> 0)            */
     double  upsilon_bar;     /* log-sum reweighting constant, nuclear (> 0)        */
     double  tau;             /* primal step; <= 0 selects 0.99/3                   */
@@ -133,6 +137,7 @@ typedef struct fhs_info {
                                 two 1-D factors of T taps, kept as 2T values     */
     int32_t bin_dense_min;   /* binning of the pass over G (fhs_autotune_bins)     */
     int32_t bin_split;
+    double  mu, mu_bar;      /* regularisation in use (the defaults once computed) */
 } fhs_info;
 
 fhs_status fhs_get_info(const fhs_problem *prob, fhs_info *info);
@@ -140,6 +145,14 @@ fhs_status fhs_get_info(const fhs_problem *prob, fhs_info *info);
 /* vis_dev[M_tot] (complex) = Phi_l x_l per channel (whitened, Eq. 1).
  * x_dev: [L][ny][nx] float32.  Asynchronous. */
 fhs_status fhs_measure(fhs_problem *prob, const float *x_dev, float *vis_dev, void *stream);
+
+/* Residual cube of Sec. 5.3: r_dev[L][ny][nx] = eta_l Re(Phi_l^H (y_l - Phi_l x_l))
+ * with the whitened data y_l of the problem and eta_l = 1 / (Phi_l^H Phi_l delta)(centre)
+ * (the point-spread function normalised to peak 1 at the phase centre; computed at
+ * set-up, 0 for a channel without visibilities).  x_dev: [L][ny][nx] float32, or NULL
+ * for x = 0, which gives the dirty image.  Asynchronous; uses the problem's
+ * scratch (not the PDFB state). */
+fhs_status fhs_residual(fhs_problem *prob, const float *x_dev, float *r_dev, void *stream);
 
 /* x_dev[L][ny][nx] = Re(Phi_l^H v_l), the adjoint of fhs_measure for real
  * images.  vis_dev: [M_tot] complex in the caller's order.  Asynchronous. */

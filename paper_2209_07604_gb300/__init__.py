@@ -25,7 +25,7 @@ EXPORTED = [
     "fhs_last_error", "fhs_profile_enable", "fhs_profile_read", "fhs_kernel_launches",
     "fhs_sara_analysis_noalloc", "fhs_pdfb_step_batch", "fhs_use_graphs", "fhs_estimate_bytes",
     "fhs_server_create", "fhs_server_submit", "fhs_server_query", "fhs_server_wait", "fhs_server_stats",
-    "fhs_server_destroy", "fhs_device_status", "fhs_autotune_bins",
+    "fhs_server_destroy", "fhs_device_status", "fhs_autotune_bins", "fhs_residual",
 ]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 GRAM_FP32, GRAM_TF32, GRAM_BF16, GRAM_FP64 = range(4)
@@ -56,6 +56,7 @@ class fhs_info(C.Structure):
         ("device_bytes", C.c_int64), ("n_facets", C.c_int32), ("iteration", C.c_int32), ("tau", C.c_double),
         ("sigma0", C.c_double), ("sigma1", C.c_double), ("sigma2", C.c_double), ("phi_norm2_max", C.c_double),
         ("n_gfac", C.c_int64), ("bin_dense_min", C.c_int32), ("bin_split", C.c_int32),
+        ("mu", C.c_double), ("mu_bar", C.c_double),
     ]
 
 
@@ -205,6 +206,12 @@ def fhs_measure(prob, x, vis, stream=None):
 
 def fhs_adjoint(prob, vis, x, stream=None):
     _check(load_library().fhs_adjoint(prob, _dev(vis, "complex64"), _dev(x, "float32"), _stream(stream)))
+
+
+def fhs_residual(prob, x, r, stream=None):
+    """r = eta Re Phi^H (y - Phi x); x None gives the dirty image."""
+    xp = C.c_void_p(None) if x is None else _dev(x, "float32")
+    _check(load_library().fhs_residual(prob, xp, _dev(r, "float32"), _stream(stream)))
 
 
 def fhs_sara_analysis(prob, x, coef, stream=None):
@@ -438,6 +445,12 @@ class Problem:
         x = self._img()
         fhs_adjoint(self.handle, vis, x)
         return x
+
+    def residual(self, x=None):
+        """eta_l Re Phi_l^H (y_l - Phi_l x_l); the dirty image when x is None."""
+        r = self._img()
+        fhs_residual(self.handle, x, r)
+        return r
 
     def sara_analysis(self, x):
         import torch

@@ -197,7 +197,8 @@ fhs_status check_params(const fhs_params *q) {
     if (q->w_max < 0.0) return fail(FHS_ERR_ARG, "w_max must be >= 0");
     if (q->w_max > 0.0 && (q->n_wplanes < 2 || q->n_wplanes > 4096)) return fail(FHS_ERR_ARG, "n_wplanes must be in [2, 4096]");
     if (q->w_max > 0.0 && !(q->pixel_size > 0.0)) return fail(FHS_ERR_ARG, "pixel_size must be > 0 with w-terms");
-    if (!(q->mu >= 0.0) || !(q->mu_bar >= 0.0)) return fail(FHS_ERR_ARG, "mu and mu_bar must be >= 0");
+    if (!std::isfinite(q->mu) || !std::isfinite(q->mu_bar))
+        return fail(FHS_ERR_ARG, "mu and mu_bar must be finite (>= 0, or < 0 for the dirty-image default)");
     if (!(q->upsilon > 0.0) || !(q->upsilon_bar > 0.0)) return fail(FHS_ERR_ARG, "upsilon and upsilon_bar must be > 0");
     if (q->gram_precision < FHS_GRAM_FP32 || q->gram_precision > FHS_GRAM_FP64)
         return fail(FHS_ERR_ARG, "gram_precision must be one of FHS_GRAM_FP32, _TF32, _BF16, _FP64");
@@ -282,6 +283,76 @@ double tridiag_max_eig(const double *a, const double *b2, int m) {
 // monotonically to lambda_max, far faster than the power method when the top of
 // the spectrum is clustered).  Work vectors: Xbar (v_{j-1}), A_sara (v_j) and the
 // first L*N entries of coef_tmp (w); all three are zero again on return.
+// PSF-peak normalisation (Sec. 5.3): eta_l = 1 / (Re Phi_l^H Phi_l delta)(centre), delta the unit
+// image at the phase centre; 0 for a channel without visibilities.  Scratch: coef_tmp, Xbar
+// (zero again on return).
+fhs_status psf_factors(fhs_problem *p, cudaStream_t s) {
+    const long long LN = (long long)p->L * p->N;
+    const long long centre = (long long)(p->ny / 2) * p->nx + p->nx / 2;
+    std::vector<float> delta(LN, 0.f);
+    for (int l = 0; l < p->L; ++l) delta[(size_t)l * p->N + centre] = 1.f;
+    TRY(upload(p->coef_tmp, delta.data(), LN, s));
+    TRY(apply_normal(p, p->coef_tmp, p->Xbar, s));
+    std::vector<float> peak(p->L), eta(p->L);
+    for (int l = 0; l < p->L; ++l)
+        CU(cudaMemcpyAsync(&peak[l], p->Xbar + (long long)l * p->N + centre, sizeof(float), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    for (int l = 0; l < p->L; ++l) eta[l] = peak[l] > 0.f ? 1.f / peak[l] : 0.f;
+    TRY(upload(p->eta, eta.data(), p->L, s));
+    CU(cudaMemsetAsync(p->Xbar, 0, sizeof(float) * LN, s));
+    CU(cudaMemsetAsync(p->coef_tmp, 0, sizeof(float) * LN, s));
+    return FHS_OK;
+}
+
+// Dirty-image defaults of the regularisation (the paper defers its heuristics to Part I; this
+// is the reading used): with X = eta_l Phi_l^H y_l, mu_bar = 1 / sum_{c,q} ||S_q X_c||_* and
+// mu = 1 / sum_c ||Psi^dagger X_c||_{2,1}.  Each is computed only when its parameter is
+// negative.  Scratch: A_sara, coef_tmp, the Grams (zero again on return).
+fhs_status default_regularisation(fhs_problem *p, cudaStream_t s) {
+    const bool want_mu = p->prm.mu < 0.0, want_mu_bar = p->prm.mu_bar < 0.0;
+    if (!want_mu && !want_mu_bar) return FHS_OK;
+    const long long LN = (long long)p->L * p->N;
+    float *X = p->A_sara;
+    TRY(adjoint_to_image(p, p->y, X, s));
+    CU(launch_chan_scale(p, X, p->eta, s));
+    double *tmp = nullptr;
+    const size_t n_tmp = (size_t)p->C * p->Q * p->Lc + p->C;
+    CU(cudaMallocAsync(reinterpret_cast<void **>(&tmp), sizeof(double) * n_tmp, s));
+    fhs_status rs = FHS_OK;
+    auto run = [&]() -> fhs_status {
+        CU(cudaMemsetAsync(tmp, 0, sizeof(double) * n_tmp, s));
+        double *svals = tmp, *l21 = tmp + (size_t)p->C * p->Q * p->Lc;
+        if (want_mu_bar) {
+            CU(launch_nuclear_gram(p, X, false, true, s));
+            CU(launch_nuclear_svals(p, svals, s));
+        }
+        if (want_mu) {
+            CU(launch_sara_analysis(p, X, p->coef_tmp, s));
+            CU(launch_l21_norm(p, p->coef_tmp, l21, s));
+        }
+        std::vector<double> h(n_tmp);
+        CU(cudaMemcpyAsync(h.data(), tmp, sizeof(double) * n_tmp, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        double nuc = 0.0, l = 0.0;
+        for (size_t i = 0; i < (size_t)p->C * p->Q * p->Lc; ++i) nuc += h[i];
+        for (int c = 0; c < p->C; ++c) l += h[(size_t)p->C * p->Q * p->Lc + c];
+        if (want_mu_bar) {
+            if (!(nuc > 0.0)) return fail(FHS_ERR_ARG, "mu_bar default: the dirty image is zero");
+            p->prm.mu_bar = 1.0 / nuc;
+        }
+        if (want_mu) {
+            if (!(l > 0.0)) return fail(FHS_ERR_ARG, "mu default: the dirty image is zero");
+            p->prm.mu = 1.0 / l;
+        }
+        return FHS_OK;
+    };
+    rs = run();
+    cudaFreeAsync(tmp, s);
+    CU(cudaMemsetAsync(X, 0, sizeof(float) * LN, s));
+    CU(cudaMemsetAsync(p->coef_tmp, 0, sizeof(float) * (size_t)p->sara.n_coef * p->L, s));
+    return rs;
+}
+
 fhs_status norm_estimate(fhs_problem *p, int n_iter, double tol, std::vector<double> &lam, cudaStream_t s) {
     const long long LN = (long long)p->L * p->N;
     const int L = p->L;
@@ -951,6 +1022,9 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
         if (!(p->phi_norm2_max > 0)) return guard(fail(FHS_ERR_ARG, "operator norm is zero (no visibilities?)"));
         p->sigma2 = 1.0 / p->phi_norm2_max;
     }
+    if ((st = guard(dev_alloc(p, &p->eta, L, false))) != FHS_OK) return st;
+    if ((st = guard(psf_factors(p, s))) != FHS_OK) return st;
+    if ((st = guard(default_regularisation(p, s))) != FHS_OK) return st;
     {
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return guard(fail(FHS_ERR_CUDA, "set-up failed: %s", cudaGetErrorString(e)));
@@ -1025,7 +1099,7 @@ fhs_status fhs_estimate_bytes(const fhs_params *params, const double *w, int64_t
     r += 8 * (nbin + 1) + 8 * nbin + 8 * (nchunk + 1) + 4 * nchunk;  // bins and chunks
     r += 4 * (q.ny + q.nx);                                          // Z scaling
     r += 8 * K * L * (3 + B);                                        // grids
-    r += 4 * N * L * 3 + 16 + 16 * L;                                // images, reductions
+    r += 4 * N * L * 3 + 16 + 16 * L + 4 * L;                        // images, reductions, PSF factors
     r += 4 * c.n_coef * L * 2 + 4 * c.n_tmp * L + 4 * c.n_coef * C;  // SARA
     const long long ne = Lc + (Lc & 1);
     r += 16 * Q + 8 * C * Q + 4 * nuc + 12 * C * Q * Lc * Lc + 4 * C * Q * Lc + 4 * (q.ny + q.nx);
@@ -1101,6 +1175,8 @@ fhs_status fhs_get_info(const fhs_problem *p, fhs_info *info) {
     info->n_gfac = p->n_fac;
     info->bin_dense_min = p->bin_dense_min;
     info->bin_split = p->bin_split;
+    info->mu = p->prm.mu;
+    info->mu_bar = p->prm.mu_bar;
     return FHS_OK;
 }
 
@@ -1117,6 +1193,20 @@ fhs_status fhs_adjoint(fhs_problem *p, const float *vis_dev, float *x_dev, void 
     cudaStream_t s = S(stream);
     CU(launch_permute_from_caller(p, reinterpret_cast<const float2 *>(vis_dev), p->vis_tmp, s));
     TRY(adjoint_to_image(p, p->vis_tmp, x_dev, s));
+    return FHS_OK;
+}
+
+fhs_status fhs_residual(fhs_problem *p, const float *x_dev, float *r_dev, void *stream) {
+    if (!p || !r_dev) return fail(FHS_ERR_ARG, "NULL argument");
+    cudaStream_t s = S(stream);
+    if (x_dev) {
+        TRY(forward_from_image(p, x_dev, p->vis_tmp, s));
+        CU(launch_vis_residual(p, p->vis_tmp, p->vis_tmp, s));
+    } else {
+        CU(cudaMemcpyAsync(p->vis_tmp, p->y, sizeof(float2) * p->Mtot, cudaMemcpyDeviceToDevice, s));
+    }
+    TRY(adjoint_to_image(p, p->vis_tmp, r_dev, s));
+    CU(launch_chan_scale(p, r_dev, p->eta, s));
     return FHS_OK;
 }
 

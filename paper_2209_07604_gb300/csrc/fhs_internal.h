@@ -140,6 +140,7 @@ struct fhs_problem {
     long long n_launch = 0;                   // libfhs kernels launched
     double *pnorms = nullptr;                 // [2L] power-iteration reductions
     int *dev_err = nullptr;                   // [1] set by a kernel whose bounded wait gave up
+    float *eta = nullptr;                     // [L] PSF-peak normalisation 1 / (Phi_l^H Phi_l delta)(centre)
 
     // the SARA and nuclear dual steps run on their own streams, forked after
     // the primal step and joined before the iteration ends
@@ -201,6 +202,11 @@ cudaError_t launch_l21_reweight(fhs_problem *p, cudaStream_t s);
 // k_nuclear.cu
 cudaError_t launch_nuclear_gram(fhs_problem *p, const float *img, bool with_dual, bool fp64, cudaStream_t s);
 cudaError_t launch_nuclear_eig(fhs_problem *p, bool reweight, cudaStream_t s);
+// Singular values (descending, FP64) of every facet whose Gram is in p->gram: svals[C*Q][Lc].
+cudaError_t launch_nuclear_svals(fhs_problem *p, double *svals, cudaStream_t s);
+cudaError_t launch_l21_norm(fhs_problem *p, const float *A, double *out, cudaStream_t s);
+cudaError_t launch_vis_residual(fhs_problem *p, const float2 *phi, float2 *r, cudaStream_t s);
+cudaError_t launch_chan_scale(fhs_problem *p, float *x, const float *f, cudaStream_t s);
 cudaError_t launch_nuclear_apply(fhs_problem *p, cudaStream_t s);
 // Tensor-core Gram of the dual step (precision FHS_GRAM_TF32 or FHS_GRAM_BF16).
 cudaError_t launch_nuclear_gram_tc(fhs_problem *p, int precision, cudaStream_t s);

@@ -148,7 +148,8 @@ __global__ void __launch_bounds__(NMAX == 16 ? 128 : 32) eig_kernel(double *__re
                                                                     float *__restrict__ mix,
                                                                     float *__restrict__ wnuc, int n_mat, int Lc,
                                                                     double mu_bar, double upsilon_bar,
-                                                                    bool reweight, double *__restrict__ eigv) {
+                                                                    bool reweight, double *__restrict__ eigv,
+                                                                    double *__restrict__ svals) {
     constexpr int kEigWarps = NMAX == 16 ? 4 : 1;
     __shared__ double s_a[kEigWarps][NMAX][NMAX + 1];
     __shared__ double s_v[kEigWarps][NMAX][NMAX + 1];
@@ -266,6 +267,10 @@ __global__ void __launch_bounds__(NMAX == 16 ? 128 : 32) eig_kernel(double *__re
     __syncwarp();
     const int *ord = s_ord[w];
     float *wv = wnuc + (long long)cq * Lc;
+    if (svals) {                              // singular values only, descending
+        if (lane < Lc) svals[(long long)cq * Lc + lane] = sqrt(fmax(a[ord[lane]][ord[lane]], 0.0));
+        return;
+    }
     if (reweight) {
         if (lane < Lc) {
             const double sv = sqrt(fmax(a[ord[lane]][ord[lane]], 0.0));
@@ -360,10 +365,21 @@ cudaError_t launch_nuclear_eig(fhs_problem *p, bool reweight, cudaStream_t s) {
     double *v0 = reweight ? nullptr : p->eigv;     // the reweighting Gram (of x) starts cold
     if (p->Lc <= 16)
         eig_kernel<16><<<(n + 3) / 4, 128, 0, s>>>(p->gram, p->mix, p->wnuc, n, p->Lc, p->prm.mu_bar,
-                                                  p->prm.upsilon_bar, reweight, v0);
+                                                  p->prm.upsilon_bar, reweight, v0, nullptr);
     else
         eig_kernel<32><<<n, 32, 0, s>>>(p->gram, p->mix, p->wnuc, n, p->Lc, p->prm.mu_bar, p->prm.upsilon_bar,
-                                         reweight, v0);
+                                         reweight, v0, nullptr);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nuclear_svals(fhs_problem *p, double *svals, cudaStream_t s) {
+    const int n = p->C * p->Q;
+    if (p->Lc <= 16)
+        eig_kernel<16><<<(n + 3) / 4, 128, 0, s>>>(p->gram, p->mix, p->wnuc, n, p->Lc, 0.0, 1.0, true, nullptr,
+                                                  svals);
+    else
+        eig_kernel<32><<<n, 32, 0, s>>>(p->gram, p->mix, p->wnuc, n, p->Lc, 0.0, 1.0, true, nullptr, svals);
     p->n_launch += 1;
     return cudaGetLastError();
 }

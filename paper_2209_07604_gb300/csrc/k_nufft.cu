@@ -273,6 +273,22 @@ __global__ void lanczos_next_kernel(const float *__restrict__ y, float *__restri
         vnext[(long long)l * N + q] = y[(long long)l * N + q] * f;
 }
 
+// r_m = y_m - phi_m over the sorted visibilities (phi may alias r).
+__global__ void vis_residual_kernel(const float2 *__restrict__ y, const float2 *phi, float2 *r, long long M) {
+    for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += (long long)gridDim.x * blockDim.x) {
+        const float2 a = y[m], b = phi[m];
+        r[m] = make_float2(a.x - b.x, a.y - b.y);
+    }
+}
+
+// x_l *= f_l on every pixel of channel l (blockIdx.y = channel).
+__global__ void chan_scale_kernel(float *__restrict__ x, long long N, const float *__restrict__ f) {
+    const int l = blockIdx.y;
+    const float a = f[l];
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x)
+        x[(long long)l * N + q] *= a;
+}
+
 inline int grid_for(long long n, int threads, int cap = 152 * 16) {
     long long g = (n + threads - 1) / threads;
     if (g > cap) g = cap;
@@ -353,6 +369,20 @@ cudaError_t launch_power_dots(fhs_problem *p, const float *x, const float *y, do
 cudaError_t launch_power_scale(fhs_problem *p, const float *y, float *x, const double *norms, cudaStream_t s) {
     dim3 g(grid_for(p->N, 256, 512), p->L);
     scale_kernel<<<g, 256, 0, s>>>(y, x, p->N, norms);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vis_residual(fhs_problem *p, const float2 *phi, float2 *r, cudaStream_t s) {
+    if (p->Mtot == 0) return cudaSuccess;
+    vis_residual_kernel<<<grid_for(p->Mtot, 256), 256, 0, s>>>(p->y, phi, r, p->Mtot);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chan_scale(fhs_problem *p, float *x, const float *f, cudaStream_t s) {
+    dim3 g(grid_for(p->N, 256, 512), p->L);
+    chan_scale_kernel<<<g, 256, 0, s>>>(x, p->N, f);
     p->n_launch += 1;
     return cudaGetLastError();
 }

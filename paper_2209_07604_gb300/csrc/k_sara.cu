@@ -367,6 +367,31 @@ __global__ void __launch_bounds__(256) l21_reweight_kernel(const float *__restri
 
 inline int cdiv(long long a, long long b) { return int((a + b - 1) / b); }
 
+// out[c] += sum_r ||(A_l[r])_{l in sub-cube c}||_2 (unweighted l21 norm, FP64).
+__global__ void __launch_bounds__(256) l21_norm_kernel(const float *__restrict__ A, long long n_coef, int C, int Lc,
+                                                       double *__restrict__ out) {
+    __shared__ double s_part[8];
+    const int c = blockIdx.y;
+    double acc = 0.0;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n_coef;
+         r += (long long)gridDim.x * blockDim.x) {
+        double n2 = 0.0;
+        for (int jj = 0; jj < Lc; ++jj) {
+            const double a = A[(long long)(c + jj * C) * n_coef + r];
+            n2 += a * a;
+        }
+        acc += sqrt(n2);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_part[w];
+        atomicAdd(out + c, t);
+    }
+}
+
 }  // namespace
 
 // Layout of Psi^dagger for an ny x nx image with `levels` levels: filters,
@@ -445,6 +470,14 @@ cudaError_t launch_l21_dual(fhs_problem *p, cudaStream_t s) {
     else if (p->Lc <= 8) l21_dual_kernel<8><<<g, 256, 0, s>>>(p->W, p->coef_tmp, p->w21, n, p->C, p->Lc, s1, mu);
     else if (p->Lc <= 16) l21_dual_kernel<16><<<g, 256, 0, s>>>(p->W, p->coef_tmp, p->w21, n, p->C, p->Lc, s1, mu);
     else l21_dual_kernel<32><<<g, 256, 0, s>>>(p->W, p->coef_tmp, p->w21, n, p->C, p->Lc, s1, mu);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_l21_norm(fhs_problem *p, const float *A, double *out, cudaStream_t s) {
+    const long long n = p->sara.n_coef;
+    dim3 g(min(cdiv(n, 256), 152 * 8), p->C);
+    l21_norm_kernel<<<g, 256, 0, s>>>(A, n, p->C, p->Lc, out);
     p->n_launch += 1;
     return cudaGetLastError();
 }

@@ -57,7 +57,7 @@ def _args(L=2, M=10, B=2):
 
 
 @pytest.mark.parametrize("field,value", [("ny", 15), ("nx", 8), ("n_subcubes", 3), ("n_blocks", 0),
-                                         ("facet_overlap", 1.0), ("wavelet_levels", 9), ("mu", -1.0),
+                                         ("facet_overlap", 1.0), ("wavelet_levels", 9), ("mu", float("nan")),
                                          ("upsilon", 0.0), ("qy", 0)])
 def test_invalid_params_rejected_without_device(lib, field, value):
     p = fhs.default_params(ny=32, nx=32, n_channels=2, n_subcubes=1, n_blocks=2, mu=0.1, mu_bar=0.1)

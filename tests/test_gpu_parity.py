@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 import paper_2209_07604_gb300 as fhs
 from paper_2209_07604_gb300 import synth
-from oracle import nufft as onf, pdfb as opdfb, wavelets as owv
+from oracle import nufft as onf, pdfb as opdfb, prox as oprox, wavelets as owv
 
 TOL_OP = 1e-5
 TOL_IMG = 1e-4
@@ -192,6 +192,45 @@ def test_pdfb_iterates_many_channels_per_subcube(L):
     wn = prob.get_state(fhs.STATE_WEIGHTS_NUC).cpu().numpy()
     wref = np.concatenate([ref.wnuc[c][q] for c in range(P.C) for q in range(len(ref.facets))])
     assert rel(wn, wref) < TOL_IMG
+    prob.close()
+
+
+@pytest.mark.parametrize("name", ["tiny", "mid_w"])
+def test_residual_and_dirty_image(name):
+    """eta_l Re Phi_l^H (y_l - Phi_l x_l) (Sec. 5.3) against the oracle, for x = 0
+    (the dirty image) and for a random x; eta from the oracle's PSF peak."""
+    from oracle import defaults as od
+    P = synth.make_problem(name)
+    prob = fhs.Problem.from_synth(P, mu=0.0, mu_bar=0.0, sigma2=1.0)
+    geom = onf.Geometry(P.ny, P.nx, w_max=P.w_max, n_wplanes=64, pixel_size=P.pixel_size)
+    op = onf.Operator(P.omega, P.w, P.sigma, geom)
+    eta = od.psf_peak_factors(op, P.ny, P.nx)
+    yw = [P.y[l] / P.sigma[l] for l in range(P.L)]
+    assert rel(prob.residual().cpu().numpy(), od.residual(op, yw, None, eta)) < TOL_OP
+    x = synth.random_image((P.L, P.ny, P.nx), 12)
+    got = prob.residual(torch.tensor(x, dtype=torch.float32, device="cuda")).cpu().numpy()
+    assert rel(got, od.residual(op, yw, x, eta)) < TOL_OP
+    prob.close()
+
+
+@pytest.mark.parametrize("name", ["small_128", "mid_w"])
+def test_default_regularisation(name):
+    """mu, mu_bar < 0 select 1 / ||Psi^dagger X||_{2,1} and 1 / sum_q ||S_q X||_* of the
+    dirty cube X, summed over sub-cubes, against the oracle; the iteration then runs."""
+    from oracle import defaults as od
+    from oracle import wavelets as owav
+    P = synth.make_problem(name)
+    prob = fhs.Problem.from_synth(P, mu=-1.0, mu_bar=-1.0)
+    geom = onf.Geometry(P.ny, P.nx, w_max=P.w_max, n_wplanes=64, pixel_size=P.pixel_size)
+    op = onf.Operator(P.omega, P.w, P.sigma, geom)
+    eta = od.psf_peak_factors(op, P.ny, P.nx)
+    dirty = od.residual(op, [P.y[l] / P.sigma[l] for l in range(P.L)], None, eta)
+    mu, mu_bar = od.default_regularisation(dirty, P.C, oprox.nuclear_facets(P.ny, P.nx, P.qy, P.qx, P.overlap),
+                                           owav.Sara(P.ny, P.nx, 4))
+    info = prob.info
+    assert abs(info.mu - mu) < 1e-4 * mu and abs(info.mu_bar - mu_bar) < 1e-4 * mu_bar
+    prob.step(3)
+    assert torch.isfinite(prob.image()).all()
     prob.close()
 
 
