@@ -181,18 +181,41 @@ def g_rows(omega: np.ndarray, w: np.ndarray, geom: Geometry, full_wkernel: bool 
     return out
 
 
+DDE_TAPS = 5            # DDE kernels: S x S taps in grid units, centred (offsets -2..2)
+
+
+def dde_convolve(box: np.ndarray, dde: np.ndarray) -> np.ndarray:
+    """Full 2-D convolution of row boxes (n, T1, T2) with DDE kernels (n, S, S):
+    out[a + j1, b + j2] += D[j1, j2] box[a, b] (Sec. 3.1: the row of G is the
+    convolution of the DDE Fourier kernel with the interpolation kernel)."""
+    n, T1, T2 = box.shape
+    S = dde.shape[1]
+    out = np.zeros((n, T1 + S - 1, T2 + S - 1), dtype=np.complex128)
+    for j1 in range(S):
+        for j2 in range(S):
+            out[:, j1:j1 + T1, j2:j2 + T2] += dde[:, j1, j2, None, None] * box
+    return out
+
+
 def build_G(omega: np.ndarray, w: np.ndarray, sigma: float, geom: Geometry,
-            full_wkernel: bool = False) -> sp.csr_matrix:
-    """Whitened degridding matrix Theta G (M x K1*K2, complex128, CSR)."""
+            full_wkernel: bool = False, dde: np.ndarray | None = None) -> sp.csr_matrix:
+    """Whitened degridding matrix Theta G (M x K1*K2, complex128, CSR).  With
+    ``dde`` (M, S, S) every row is further convolved with its visibility's DDE
+    kernel (centred: the box grows by (S-1)/2 on each side)."""
     M = omega.shape[0]
     K1, K2 = geom.K1, geom.K2
     rows, cols, vals = [], [], []
     for idx, c1, c2, g1, g2 in g_rows(omega, w, geom, full_wkernel):
-        T1, T2 = g1.shape[1], g2.shape[1]
+        box = g1[:, :, None] * g2[:, None, :]
+        if dde is not None:
+            box = dde_convolve(box, dde[idx])
+            h = (dde.shape[1] - 1) // 2
+            c1, c2 = c1 - h, c2 - h
+        T1, T2 = box.shape[1], box.shape[2]
         k1 = (c1[:, None] + np.arange(T1)[None, :]) % K1
         k2 = (c2[:, None] + np.arange(T2)[None, :]) % K2
         col = (k1[:, :, None] * K2 + k2[:, None, :]).reshape(len(idx), -1)
-        val = (g1[:, :, None] * g2[:, None, :]).reshape(len(idx), -1)
+        val = box.reshape(len(idx), -1)
         rows.append(np.repeat(idx, T1 * T2))
         cols.append(col.ravel())
         vals.append(val.ravel())
@@ -205,17 +228,18 @@ def build_G(omega: np.ndarray, w: np.ndarray, sigma: float, geom: Geometry,
 class Operator:
     """Phi_l for every channel of a problem: G matrices, scaling, FFT."""
 
-    def __init__(self, omega, w, sigma, geom: Geometry, full_wkernel: bool = False):
+    def __init__(self, omega, w, sigma, geom: Geometry, full_wkernel: bool = False, dde=None):
         self.geom = geom
         self.L = omega.shape[0]
-        self.G = [build_G(omega[l], w[l], float(sigma[l]), geom, full_wkernel) for l in range(self.L)]
+        self.G = [build_G(omega[l], w[l], float(sigma[l]), geom, full_wkernel,
+                          None if dde is None else dde[l]) for l in range(self.L)]
         self.s1 = scaling(geom.ny, geom.K1, geom.J, geom.beta)
         self.s2 = scaling(geom.nx, geom.K2, geom.J, geom.beta)
         self.i1 = (np.arange(geom.ny) - geom.ny // 2) % geom.K1
         self.i2 = (np.arange(geom.nx) - geom.nx // 2) % geom.K2
 
     def fzx(self, x: np.ndarray) -> np.ndarray:
-        """F Z x for one channel image (ny, nx) -> (K1, K2) complex grid."""
+        """F Z x for one channel image (ny, nx), real or complex -> (K1, K2) complex grid."""
         g = np.zeros((self.geom.K1, self.geom.K2), dtype=np.complex128)
         g[np.ix_(self.i1, self.i2)] = x * self.s1[:, None] * self.s2[None, :]
         return np.fft.fft2(g)

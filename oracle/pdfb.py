@@ -46,11 +46,11 @@ class FHS:
     def __init__(self, omega, w, y, sigma, block_offsets, ny, nx, C, qy, qx, overlap,
                  mu, mu_bar, upsilon=1e-3, upsilon_bar=1e-3, w_max=0.0, n_wplanes=64,
                  pixel_size=0.0, levels=4, eps=None, steps: Steps | None = None,
-                 faceted_sara: bool = False, sara_q=(1, 1)):
+                 faceted_sara: bool = False, sara_q=(1, 1), dde=None):
         self.L = omega.shape[0]
         self.ny, self.nx, self.C = ny, nx, C
         self.geom = nufft.Geometry(ny, nx, w_max=w_max, n_wplanes=n_wplanes, pixel_size=pixel_size)
-        self.op = nufft.Operator(omega, w, sigma, self.geom)
+        self.op = nufft.Operator(omega, w, sigma, self.geom, dde=dde)
         self.yw = [y[l] / sigma[l] for l in range(self.L)]                 # Theta_l y_l
         self.bo = np.asarray(block_offsets, dtype=np.int64)
         B = self.bo.shape[1] - 1

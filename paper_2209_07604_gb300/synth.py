@@ -207,3 +207,17 @@ def random_vis(shape, seed: int) -> np.ndarray:
     """Seeded complex standard-normal vector."""
     rng = np.random.Generator(np.random.Philox(seed))
     return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / math.sqrt(2.0)
+
+
+def random_dde(L: int, M: int, seed: int, spread: float = 0.1) -> np.ndarray:
+    """Seeded synthetic DDE kernels (L, M, 5, 5) complex128: the Fourier
+    representation of smooth direction-dependent gains, i.e. 1 at the centre
+    tap plus complex perturbations that decay with the tap distance
+    (spread * exp(-|delta|^2 / 2) standard deviation)."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    d = np.arange(5) - 2
+    env = spread * np.exp(-(d[:, None] ** 2 + d[None, :] ** 2) / 2.0)
+    k = (rng.standard_normal((L, M, 5, 5)) + 1j * rng.standard_normal((L, M, 5, 5))) / math.sqrt(2.0)
+    k *= env[None, None]
+    k[:, :, 2, 2] += 1.0
+    return k

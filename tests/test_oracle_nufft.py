@@ -137,3 +137,33 @@ def test_psf_peaks_at_phase_centre():
     assert abs(psf.max() - np.linalg.norm(op.forward(d, 0)) ** 2) < 1e-9 * psf.max()
     # and the direct transform of delta has unit modulus at every uv point
     assert np.allclose(np.abs(op.forward(d, 0)), 1.0, atol=1e-5)
+
+
+def test_dde_rows_equal_image_modulation():
+    """A row convolved with a centred 5x5 DDE kernel D_m (Sec. 3.1) and applied to
+    F Z x equals the plain row applied to F Z (d_m x), with the image-domain
+    modulation d_m(n) = sum_delta D_m[delta + 2] exp(-2 pi i (delta1 n1 / K1 + delta2 n2 / K2)):
+    a convolution in the grid is a product in the image.  A centred delta
+    kernel leaves G unchanged; the DDE operator keeps the adjoint identity."""
+    ny, nx, M = 12, 16, 25
+    geom = nf.Geometry(ny, nx)
+    om = _uv(M, 21)
+    rng = np.random.default_rng(7)
+    dde = rng.standard_normal((M, 5, 5)) + 1j * rng.standard_normal((M, 5, 5))
+    op = nf.Operator(om[None], np.zeros((1, M)), np.array([1.3]), geom)
+    opd = nf.Operator(om[None], np.zeros((1, M)), np.array([1.3]), geom, dde=dde[None])
+    x = rng.standard_normal((ny, nx))
+    got = opd.forward(x, 0)
+    n1 = (np.arange(ny) - ny // 2)[:, None]
+    n2 = (np.arange(nx) - nx // 2)[None, :]
+    for m in range(M):
+        d = sum(dde[m, a, b] * np.exp(-2j * np.pi * ((a - 2) * n1 / geom.K1 + (b - 2) * n2 / geom.K2))
+                for a in range(5) for b in range(5))
+        ref = op.forward(d * x, 0)[m]
+        assert abs(got[m] - ref) < 1e-12 * max(1.0, abs(ref))
+    delta = np.zeros((1, M, 5, 5), dtype=np.complex128)
+    delta[:, :, 2, 2] = 1.0
+    op1 = nf.Operator(om[None], np.zeros((1, M)), np.array([1.3]), geom, dde=delta)
+    assert abs(op1.G[0] - op.G[0]).max() < 1e-15
+    v = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+    assert abs(np.vdot(v, opd.forward(x, 0)).real - np.vdot(opd.adjoint(v, 0), x).real) < 1e-12 * np.linalg.norm(v) * np.linalg.norm(got)
