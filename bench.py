@@ -145,8 +145,14 @@ def run_gpu(args):
     fhs.load_library()
     t0 = time.time()
     P = synth.make_problem(args.workload)
-    gen_s = time.time() - t0
     L, M = P.omega.shape[:2]
+    dde = None
+    if args.dde:
+        # 5x5 DDE kernels per visibility (Sec. 3.1); w halved so that the w-kernels add at most
+        # 2 taps per side and every box stays within 16 taps
+        P.w *= 0.5
+        dde = synth.random_dde(L, M, 7604 + 100 * synth.WORKLOADS[args.workload]["config_id"] + 99)
+    gen_s = time.time() - t0
     Mtot = L * M
     stream = torch.cuda.current_stream()
 
@@ -163,13 +169,16 @@ def run_gpu(args):
     e2e_iters = args.e2e_iters
     img_host = torch.empty((L, P.ny, P.nx), dtype=torch.float32, pin_memory=True)
     t_e2e = time.perf_counter()
-    prob = fhs.Problem(params, omega, wv, yv, P.sigma, vis_off, P.block_offsets)
+    prob = fhs.Problem(params, omega, wv, yv, P.sigma, vis_off, P.block_offsets, dde=dde)
     setup_s = time.perf_counter() - t_e2e
     prob.solve(e2e_iters, 0.0, n_reweight=1 if e2e_iters >= 2 else 0, check_every=max(1, e2e_iters))
     img_host.copy_(prob.image(), non_blocking=True)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t_e2e
     h2d = omega.nbytes + wv.nbytes + yv.nbytes + P.sigma.nbytes + vis_off.nbytes + P.block_offsets.nbytes
+    if dde is not None:
+        h2d += dde.nbytes
+        del dde
     d2h = img_host.numel() * 4
     info = prob.info
 
@@ -235,7 +244,7 @@ def run_gpu(args):
     k_ms = phases["degrid_grid"] / max(n_prof, 1)
     achieved = kbytes / (k_ms * 1e-3) / 1e9
     traffic, limiter = _profile_traffic("k_binned.cu")
-    if args.workload != WORKLOAD:
+    if args.workload != WORKLOAD or args.dde:
         traffic = None          # the committed capture is scaled to the default workload only
     # visibilities through Phi and Phi^H per second inside the PDFB iteration
     vis_s = Mtot / (ms_step * 1e-3)
@@ -258,7 +267,8 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (G factors alone %.1f GB per iteration)" % (info.n_gfac * 8 / 1e9),
                    "mu": MU, "mu_bar": MU_BAR, "gram": args.gram,
                    "bins": {"dense_min": info.bin_dense_min, "split": info.bin_split,
-                            "autotuned": bool(args.autotune)}},
+                            "autotuned": bool(args.autotune)},
+                   "dde": "5x5 kernel per visibility, w halved" if args.dde else None},
         "vis_per_s": ws * vis_s,
         "phi_vis_per_s": ws * Mtot / (phi_ms * 1e-3),
         "phi_adjoint_vis_per_s": ws * Mtot / (phit_ms * 1e-3),
@@ -276,7 +286,7 @@ def run_gpu(args):
         "device_bytes": info.device_bytes,
         "generate_seconds": gen_s,
     }
-    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+    if rank == 0 and not args.no_cpu_baseline and ws == 1 and not args.dde:
         out["cpu_baseline"] = cpu_baseline(P, info)
     prob.close()
     if ws > 1:
@@ -458,6 +468,8 @@ def main():
                     help="measure candidate tile binnings of the pass over G before timing")
     ap.add_argument("--gram", default="fp32", choices=["fp32", "tf32", "bf16", "fp64"],
                     help="arithmetic of the nuclear facet Gram (tf32/bf16: tensor cores)")
+    ap.add_argument("--dde", action="store_true",
+                    help="fold seeded 5x5 DDE kernels into G (w halved to keep boxes within 16 taps)")
     ap.add_argument("--mode", default="pdfb", choices=["pdfb", "serve"])
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=4.0)

@@ -120,6 +120,25 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
                               const int64_t *block_offsets, const double *eps, void *stream,
                               fhs_problem **out);
 
+/*
+ * fhs_create_problem with direction-dependent effects folded into G
+ * (Sec. 3.1: each row of G is its interpolation kernel convolved with the
+ * Fourier kernel of the DDEs of its antenna pair).
+ *  dde  host, [M_tot][5][5] complex as interleaved float64 (re, im), in the
+ *       order of omega: the DDE kernel of each visibility on the oversampled
+ *       grid, tap [j1][j2] at grid offset (j1 - 2, j2 - 2) along (y, x).
+ * Every row's box grows to T + 4 taps per axis (its corner moves by -2) and
+ * the row is stored as the sum of 5 separable terms, which represents the
+ * 2-D convolution exactly; the factors take 5x the storage of a row without
+ * DDEs.  Boxes must stay within 16 taps: with J = 7 the w-kernels may add at
+ * most 2 taps per side, otherwise FHS_ERR_ARG.  dde NULL: FHS_ERR_ARG.
+ * fhs_estimate_bytes does not count the DDE factors.
+ */
+fhs_status fhs_create_problem_dde(const fhs_params *params, const double *omega, const double *w,
+                                  const double *y, const double *sigma, const int64_t *vis_offsets,
+                                  const int64_t *block_offsets, const double *eps, const double *dde,
+                                  void *stream, fhs_problem **out);
+
 /* Release every device and host resource of the problem (NULL is a no-op). */
 void fhs_destroy_problem(fhs_problem *prob);
 

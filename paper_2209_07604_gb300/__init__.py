@@ -19,7 +19,7 @@ FHS_OK, FHS_ERR_ARG, FHS_ERR_OOM, FHS_ERR_CUDA, FHS_ERR_TIMEOUT, FHS_ERR_STATE =
 STATE_IMAGE, STATE_DUAL_DATA, STATE_DUAL_SARA, STATE_DUAL_NUCLEAR, STATE_WEIGHTS_SARA, STATE_WEIGHTS_NUC = range(6)
 
 EXPORTED = [
-    "fhs_default_params", "fhs_create_problem", "fhs_destroy_problem", "fhs_get_info", "fhs_measure",
+    "fhs_default_params", "fhs_create_problem", "fhs_create_problem_dde", "fhs_destroy_problem", "fhs_get_info", "fhs_measure",
     "fhs_adjoint", "fhs_sara_analysis", "fhs_sara_synthesis", "fhs_pdfb_step", "fhs_reweight", "fhs_solve",
     "fhs_state_size", "fhs_get_state", "fhs_set_state", "fhs_operator_norms", "fhs_daubechies_filter",
     "fhs_last_error", "fhs_profile_enable", "fhs_profile_read", "fhs_kernel_launches",
@@ -91,6 +91,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     sig = {
         "fhs_default_params": (None, [P(fhs_params)]),
         "fhs_create_problem": (C.c_int, [P(fhs_params), vp, vp, vp, vp, vp, vp, vp, vp, P(vp)]),
+        "fhs_create_problem_dde": (C.c_int, [P(fhs_params), vp, vp, vp, vp, vp, vp, vp, vp, vp, P(vp)]),
         "fhs_destroy_problem": (None, [vp]),
         "fhs_get_info": (C.c_int, [vp, P(fhs_info)]),
         "fhs_measure": (C.c_int, [vp, vp, vp, vp]),
@@ -171,7 +172,10 @@ def default_params(**kw) -> fhs_params:
 
 # --- entry points (same names as the C ABI) ---------------------------------
 
-def fhs_create_problem(params: fhs_params, omega, w, y, sigma, vis_offsets, block_offsets, eps=None, stream=None):
+def fhs_create_problem(params: fhs_params, omega, w, y, sigma, vis_offsets, block_offsets, eps=None, stream=None,
+                       dde=None):
+    """Without ``dde`` calls fhs_create_problem; with ``dde`` ([M_tot][5][5]
+    complex, the DDE kernel of every visibility) fhs_create_problem_dde."""
     omega = np.ascontiguousarray(omega, dtype=np.float64)
     w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
     yc = np.ascontiguousarray(y)
@@ -184,9 +188,18 @@ def fhs_create_problem(params: fhs_params, omega, w, y, sigma, vis_offsets, bloc
     block_offsets = np.ascontiguousarray(block_offsets, dtype=np.int64)
     eps = None if eps is None else np.ascontiguousarray(eps, dtype=np.float64)
     h = C.c_void_p()
-    _check(load_library().fhs_create_problem(C.byref(params), _ptr(omega), _ptr(w), _ptr(yc), _ptr(sigma),
-                                             _ptr(vis_offsets), _ptr(block_offsets), _ptr(eps), _stream(stream),
-                                             C.byref(h)))
+    if dde is None:
+        _check(load_library().fhs_create_problem(C.byref(params), _ptr(omega), _ptr(w), _ptr(yc), _ptr(sigma),
+                                                 _ptr(vis_offsets), _ptr(block_offsets), _ptr(eps), _stream(stream),
+                                                 C.byref(h)))
+    else:
+        d = np.asarray(dde, dtype=np.complex128).reshape(-1, 5, 5)
+        if d.shape[0] != omega.shape[0]:
+            raise ValueError(f"dde holds {d.shape[0]} kernels for {omega.shape[0]} visibilities")
+        dd = np.ascontiguousarray(np.stack([d.real, d.imag], axis=-1), dtype=np.float64)
+        _check(load_library().fhs_create_problem_dde(C.byref(params), _ptr(omega), _ptr(w), _ptr(yc), _ptr(sigma),
+                                                     _ptr(vis_offsets), _ptr(block_offsets), _ptr(eps), _ptr(dd),
+                                                     _stream(stream), C.byref(h)))
     return h
 
 
@@ -400,16 +413,18 @@ class Server:
 class Problem:
     """Owns one libfhs problem built from host arrays; device tensors via torch."""
 
-    def __init__(self, params: fhs_params, omega, w, y, sigma, vis_offsets, block_offsets, eps=None, stream=None):
+    def __init__(self, params: fhs_params, omega, w, y, sigma, vis_offsets, block_offsets, eps=None, stream=None,
+                 dde=None):
         self.params = params
         self.L = int(params.n_channels)
         self.ny, self.nx = int(params.ny), int(params.nx)
-        self.handle = fhs_create_problem(params, omega, w, y, sigma, vis_offsets, block_offsets, eps, stream)
+        self.handle = fhs_create_problem(params, omega, w, y, sigma, vis_offsets, block_offsets, eps, stream, dde)
         self.info = fhs_get_info(self.handle)
 
     @classmethod
-    def from_synth(cls, prob, mu, mu_bar, stream=None, **kw):
-        """Build from a ``synth.Problem`` (all channels share one visibility count)."""
+    def from_synth(cls, prob, mu, mu_bar, stream=None, dde=None, **kw):
+        """Build from a ``synth.Problem`` (all channels share one visibility count);
+        ``dde`` (L, M, 5, 5) complex folds DDE kernels into G."""
         L, M = prob.omega.shape[:2]
         params = default_params(ny=prob.ny, nx=prob.nx, n_channels=L, n_subcubes=prob.C, n_blocks=prob.B,
                                 qy=prob.qy, qx=prob.qx, facet_overlap=prob.overlap, w_max=prob.w_max,
@@ -418,7 +433,7 @@ class Problem:
             setattr(params, k, v)
         vis_off = np.arange(L + 1, dtype=np.int64) * M
         return cls(params, prob.omega.reshape(-1, 2), prob.w.reshape(-1), prob.y.reshape(-1), prob.sigma,
-                   vis_off, prob.block_offsets, None, stream)
+                   vis_off, prob.block_offsets, None, stream, dde)
 
     def close(self):
         if self.handle:

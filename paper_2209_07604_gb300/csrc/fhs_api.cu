@@ -643,9 +643,11 @@ fhs_status fhs_daubechies_filter(int32_t p, double *h_out) {
     return FHS_OK;
 }
 
-fhs_status fhs_create_problem(const fhs_params *params, const double *omega, const double *w, const double *y,
+// Problem set-up shared by fhs_create_problem and fhs_create_problem_dde (dde: NULL, or
+// [M_tot][5][5] complex DDE kernels in the caller's visibility order).
+static fhs_status create_impl(const fhs_params *params, const double *omega, const double *w, const double *y,
                               const double *sigma, const int64_t *vis_offsets, const int64_t *block_offsets,
-                              const double *eps_in, void *stream, fhs_problem **out) {
+                              const double *eps_in, const double *dde, void *stream, fhs_problem **out) {
     g_err.clear();
     if (!out) return fail(FHS_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -719,6 +721,11 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
     const double dw = q.w_max > 0.0 ? q.w_max / P1 : 0.0;
     const int ntx = (K2 + kTile - 1) / kTile, nty = (K1 + kTile - 1) / kTile;
     std::vector<int> key(Mtot), pl(Mtot), corner1(Mtot), corner2(Mtot), Tv(Mtot);
+    // with DDE kernels every box grows by kDdeTaps - 1 (half on each side) and a row is the
+    // sum of kDdeTaps separable terms (see build_g_kernel)
+    const int ext = dde ? kDdeTaps - 1 : 0, hx = ext / 2;
+    p->rank = dde ? kDdeTaps : 1;
+    std::atomic<int> box_too_big{0};
     parallel_for(Mtot, [&](long long i0, long long i1) {
     for (long long i = i0; i < i1; ++i) {
         const double k1 = omega[2 * i] * K1 / (2.0 * M_PI);
@@ -733,13 +740,19 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
             pv = int(wv < 0 ? -pa : pa);
             h = (8 * std::abs(pv) + P1) / (2 * P1);
         }
-        const int T = J + 2 * h;
-        long long c1 = (p01 - h) % K1; if (c1 < 0) c1 += K1;
-        long long c2 = (p02 - h) % K2; if (c2 < 0) c2 += K2;
+        const int T = J + 2 * h + ext;
+        if (T > 16) box_too_big.store(1, std::memory_order_relaxed);
+        long long c1 = (p01 - h - hx) % K1; if (c1 < 0) c1 += K1;
+        long long c2 = (p02 - h - hx) % K2; if (c2 < 0) c2 += K2;
         corner1[i] = int(c1); corner2[i] = int(c2); Tv[i] = T; pl[i] = pv + P1;
         key[i] = (int(c1 / kTile) * ntx + int(c2 / kTile)) * 17 + T;   // tile, then box side
     }
     });
+    if (box_too_big.load()) {
+        delete p;
+        return fail(FHS_ERR_ARG, "DDE kernels widen the G boxes past 16 taps: with DDEs the w-kernels may "
+                                 "add at most %d taps per side (w_max too large for this pixel size)", (16 - J - ext) / 2);
+    }
     const int nkeys = nty * ntx * 17;
     std::vector<long long> perm(Mtot);
     // counting sort by tile key, segments in parallel (each segment is stable)
@@ -765,7 +778,7 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
             while (v >= vis_offsets[l + 1]) ++l;
             const long long i = perm[v];
             meta[v] = make_int2(corner1[i] | (corner2[i] << 16), Tv[i]);
-            fptr[v + 1] = 2LL * Tv[i];
+            fptr[v + 1] = 2LL * p->rank * Tv[i];
             kap[v] = make_double2(omega[2 * i] * K1 / (2.0 * M_PI), omega[2 * i + 1] * K2 / (2.0 * M_PI));
             plane[v] = short(pl[i]);
             yw[v] = make_float2(float(y[2 * i] / sigma[l]), float(y[2 * i + 1] / sigma[l]));
@@ -773,8 +786,20 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
     });
     p->nnz = 0;
     for (long long v = 0; v < Mtot; ++v) {
-        p->nnz += (fptr[v + 1] / 2) * (fptr[v + 1] / 2);
+        p->nnz += (long long)meta[v].y * meta[v].y;
         fptr[v + 1] += fptr[v];
+    }
+    std::vector<double2> dde_sorted;
+    if (dde) {
+        dde_sorted.resize((size_t)Mtot * kDdeTaps * kDdeTaps);
+        parallel_for(Mtot, [&](long long v0, long long v1) {
+            for (long long v = v0; v < v1; ++v) {
+                const long long i = perm[v];
+                for (int j = 0; j < kDdeTaps * kDdeTaps; ++j)
+                    dde_sorted[(size_t)v * kDdeTaps * kDdeTaps + j] =
+                        make_double2(dde[2 * (i * kDdeTaps * kDdeTaps + j)], dde[2 * (i * kDdeTaps * kDdeTaps + j) + 1]);
+            }
+        });
     }
     p->n_fac = fptr[Mtot];
     { std::vector<int> t; t.swap(key); } { std::vector<int> t; t.swap(corner1); } { std::vector<int> t; t.swap(corner2); }
@@ -858,6 +883,11 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
     if ((st = guard(dev_alloc(p, &d_plane, Mtot, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &d_wk, wk.size(), false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &d_isg, p->n_seg, false))) != FHS_OK) return st;
+    double2 *d_dde = nullptr;
+    if (dde) {
+        if ((st = guard(dev_alloc(p, &d_dde, dde_sorted.size(), false))) != FHS_OK) return st;
+        if ((st = guard(upload(d_dde, dde_sorted.data(), dde_sorted.size(), s))) != FHS_OK) return st;
+    }
     std::vector<float> ones(p->n_seg, 1.0f);
     if ((st = guard(upload(p->meta, meta.data(), Mtot, s))) != FHS_OK) return st;
     if ((st = guard(upload(p->fptr, fptr.data(), Mtot + 1, s))) != FHS_OK) return st;
@@ -876,9 +906,14 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
     if ((st = guard(upload(d_wk, wk.data(), wk.size(), s))) != FHS_OK) return st;
     if ((st = guard(upload(d_isg, inv_sig.data(), p->n_seg, s))) != FHS_OK) return st;
     {
-        cudaError_t e = launch_build_g(p, d_kap, d_plane, d_wk, nullptr, n_planes, d_isg, s);
+        cudaError_t e = launch_build_g(p, d_kap, d_plane, d_wk, d_dde, ext, d_isg, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return guard(fail(FHS_ERR_CUDA, "G build failed: %s", cudaGetErrorString(e)));
+        if (d_dde) {
+            dev_free(p, d_dde);
+            p->bytes -= sizeof(double2) * dde_sorted.size();
+            std::vector<double2>().swap(dde_sorted);
+        }
     }
 
     // scaling of Z
@@ -1034,6 +1069,19 @@ fhs_status fhs_create_problem(const fhs_params *params, const double *omega, con
     p->bytes -= sizeof(double2) * Mtot + sizeof(short) * Mtot + sizeof(double2) * wk.size() + sizeof(double) * p->n_seg;
     *out = p;
     return FHS_OK;
+}
+
+fhs_status fhs_create_problem(const fhs_params *params, const double *omega, const double *w, const double *y,
+                              const double *sigma, const int64_t *vis_offsets, const int64_t *block_offsets,
+                              const double *eps_in, void *stream, fhs_problem **out) {
+    return create_impl(params, omega, w, y, sigma, vis_offsets, block_offsets, eps_in, nullptr, stream, out);
+}
+
+fhs_status fhs_create_problem_dde(const fhs_params *params, const double *omega, const double *w, const double *y,
+                                  const double *sigma, const int64_t *vis_offsets, const int64_t *block_offsets,
+                                  const double *eps_in, const double *dde, void *stream, fhs_problem **out) {
+    if (!dde) return fail(FHS_ERR_ARG, "dde is NULL (use fhs_create_problem without DDE kernels)");
+    return create_impl(params, omega, w, y, sigma, vis_offsets, block_offsets, eps_in, dde, stream, out);
 }
 
 void fhs_destroy_problem(fhs_problem *p) {

@@ -20,6 +20,7 @@ constexpr int kMaxF = 16;          // taps of db8
 constexpr int kMaxLc = 32;         // channels per sub-cube supported
 constexpr int kMaxWHalf = 4;       // largest w-kernel half-width h
 constexpr int kTile = 32;
+constexpr int kDdeTaps = 5;        // DDE kernels: kDdeTaps x kDdeTaps grid taps, centred
 #ifndef FHS_BIN_MAX
 #define FHS_BIN_MAX 384
 #endif
@@ -70,6 +71,7 @@ struct Facet {
 struct fhs_problem {
     fhs_params prm;
     int L = 0, C = 0, Lc = 0, B = 0, ny = 0, nx = 0, K1 = 0, K2 = 0, J = 7;
+    int rank = 1;                             // separable terms per row of G (kDdeTaps with DDE kernels)
     long long N = 0, K = 0;                   // pixels and grid cells per channel
     long long Mtot = 0, nnz = 0, n_fac = 0;   // nnz: entries of G (sum T^2); n_fac: stored factors (sum 2T)
     std::vector<long long> vis_off;           // [L+1]
@@ -174,9 +176,9 @@ void destroy_on_stream(fhs_problem *p, cudaStream_t s);
 
 // kernel launchers --------------------------------------------------------
 // k_nufft.cu
+// dde: NULL, or [Mtot][kDdeTaps^2] DDE kernels in sorted order; ext = kDdeTaps - 1 with DDEs, else 0.
 cudaError_t launch_build_g(fhs_problem *p, const double2 *kap, const short *plane, const double2 *wk_table,
-                           const int *wk_half, int n_planes_total, const double *inv_sigma_seg,
-                           cudaStream_t s);
+                           const double2 *dde, int ext, const double *inv_sigma_seg, cudaStream_t s);
 cudaError_t launch_zpad(fhs_problem *p, const float *x, float2 *grid, cudaStream_t s);
 cudaError_t launch_degrid(fhs_problem *p, const float2 *grid, float2 *vis_sorted, cudaStream_t s);
 cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s);

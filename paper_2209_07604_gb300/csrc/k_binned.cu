@@ -169,6 +169,63 @@ __device__ __forceinline__ void bin_rows(int i0, int nv, int lane, const int2 *s
     }
 }
 
+// Scatter of rows with R > 1 separable terms (DDE rows, see k_nufft.cu): one
+// row per warp as in bin_rows; each lane sums conj(A_r[t1]) conj(B_r[col]) d
+// over the terms in registers and adds each of its cells once.
+template <bool DENSE>
+__device__ __forceinline__ void scatter_rows_rank(int i0, int nv, int lane, int R, const int2 *s_meta,
+                                                  const int *s_off, const float2 *s_d,
+                                                  const float2 *__restrict__ fbin, float *s_re, float *s_im,
+                                                  int wy0, int wx0, float2 *__restrict__ gb, int K1, int K2) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int half = lane >> 4, col = lane & 15;
+    for (int i = i0; i < nv; i += kWarps) {
+        const int2 m = s_meta[i];
+        const int T = m.y;
+        const int c1 = m.x & 0xffff, c2 = (int)((unsigned)m.x >> 16);
+        const bool cin = col < T;
+        const float dr = s_d[i].x, di = s_d[i].y;
+        float accr[8], acci[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) accr[k] = acci[k] = 0.f;
+        for (int r = 0; r < R; ++r) {
+            const float2 fac = load_factors(fbin + s_off[i] + r * 2 * T, T, lane);
+            const float g2x = __shfl_sync(FULL, fac.x, 16 + col), g2y = __shfl_sync(FULL, fac.y, 16 + col);
+            const float er = fmaf(g2x, dr, g2y * di), ei = fmaf(g2x, di, -g2y * dr);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (2 * k >= T) break;
+                const int t1 = 2 * k + half;
+                const float g1x = __shfl_sync(FULL, fac.x, t1), g1y = __shfl_sync(FULL, fac.y, t1);
+                accr[k] = fmaf(g1x, er, fmaf(g1y, ei, accr[k]));
+                acci[k] = fmaf(g1x, ei, fmaf(-g1y, er, acci[k]));
+            }
+        }
+        int ib = 0, k1 = 0, k2 = 0;
+        if (DENSE) {
+            ib = (c1 - wy0 + half) * kWin + (c2 - wx0 + col);
+        } else {
+            k1 = c1 + half;
+            k2 = c2 + col;
+            k2 -= (k2 >= K2) ? K2 : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (2 * k >= T) break;
+            if (cin && 2 * k + half < T) {
+                if (DENSE) {
+                    atomicAdd(s_re + ib + 2 * k * kWin, accr[k]);
+                    atomicAdd(s_im + ib + 2 * k * kWin, acci[k]);
+                } else {
+                    int kk = k1 + 2 * k;
+                    kk -= (kk >= K1) ? K1 : 0;
+                    red_add_f2(gb + (long long)kk * K2 + k2, make_float2(accr[k], acci[k]));
+                }
+            }
+        }
+    }
+}
+
 // Columns [C0, C0 + CW) of the gather of one row by one lane:
 // sum_t1 g1[t1] sum_t2 g2[t2] X[c1+t1][c2+t2], with g2 of those columns in
 // registers (zero beyond T).
@@ -233,12 +290,26 @@ __device__ __forceinline__ float2 gather_lane(const float2 *__restrict__ f, int 
     return make_float2(ar, ai);
 }
 
+// Gather of a row with R separable terms (term r at offset 2 T r).
+template <int TT, bool DENSE>
+__device__ __forceinline__ float2 gather_terms(const float2 *__restrict__ f, int T, int R, int c1, int c2,
+                                               const float2 *s_grid, int wy0, int wx0,
+                                               const float2 *__restrict__ gl, int K1, int K2) {
+    float2 phi = gather_lane<TT, DENSE>(f, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
+    for (int r = 1; r < R; ++r) {
+        const float2 t = gather_lane<TT, DENSE>(f + r * 2 * T, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
+        phi.x += t.x;
+        phi.y += t.y;
+    }
+    return phi;
+}
+
 // Phase 1 of a bin: one row per thread (rows are sorted by T inside each tile
 // run, so a warp's rows mostly share T).  kFused: the data-dual pre-update
 // d = s_b d + sigma2 (phi - y) into s_d, the bin's output and the block norm;
 // kGather: phi to the output; kNormal: phi into s_d for the scatter.
 template <int MODE, bool DENSE>
-__device__ __forceinline__ void gather_phase(int nv, const int2 *s_meta, const int *s_off, const float2 *s_y,
+__device__ __forceinline__ void gather_phase(int nv, int R, const int2 *s_meta, const int *s_off, const float2 *s_y,
                                              float2 *s_d, const float2 *__restrict__ fbin, const float2 *s_grid,
                                              int wy0, int wx0, const float2 *__restrict__ gl, int K1, int K2,
                                              float sc, float sigma2, float2 *__restrict__ dvis_bin, Kahan &nrm) {
@@ -256,12 +327,12 @@ __device__ __forceinline__ void gather_phase(int nv, const int2 *s_meta, const i
         }
         const int tm = __reduce_max_sync(0xffffffffu, T);
         float2 phi;
-        if (tm <= 4) phi = gather_lane<4, DENSE>(f, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
-        else if (tm <= 7) phi = gather_lane<7, DENSE>(f, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
-        else if (tm <= 9) phi = gather_lane<9, DENSE>(f, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
-        else if (tm <= 11) phi = gather_lane<11, DENSE>(f, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
-        else if (tm <= 13) phi = gather_lane<13, DENSE>(f, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
-        else phi = gather_lane<16, DENSE>(f, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
+        if (tm <= 4) phi = gather_terms<4, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
+        else if (tm <= 7) phi = gather_terms<7, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
+        else if (tm <= 9) phi = gather_terms<9, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
+        else if (tm <= 11) phi = gather_terms<11, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
+        else if (tm <= 13) phi = gather_terms<13, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
+        else phi = gather_terms<16, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
         if (!valid) continue;
         if (MODE == kFused) {
             const float2 dold = s_d[i];
@@ -289,13 +360,16 @@ __device__ __forceinline__ void gather_phase(int nv, const int2 *s_meta, const i
 // the forward grid.  kScatter: dvis holds the visibilities, grid_blk the
 // per-channel output grids (indexed by channel instead of segment).  kNormal:
 // grid is the forward grid, grid_blk the per-channel output grids, dvis unused.
-template <int MODE>
+// MULTI: rows of R > 1 separable terms (DDE rows); otherwise R is 1 and the
+// term loops compile away.
+template <int MODE, bool MULTI>
 __global__ void __launch_bounds__(256, FHS_FUSED_MIN_BLOCKS) degrid_grid_binned_kernel(
     const int2 *__restrict__ meta, const long long *__restrict__ fptr, const float2 *__restrict__ gfac,
     const float2 *__restrict__ y, float2 *__restrict__ dvis, const long long *__restrict__ bin_start,
     const int *__restrict__ bin_seg, const int *__restrict__ bin_tile, int ntx, int B,
     const float *__restrict__ blk_scale, double *__restrict__ blk_norm2, const float2 *__restrict__ grid,
-    float2 *__restrict__ grid_blk, long long K, int K1, int K2, float sigma2) {
+    float2 *__restrict__ grid_blk, long long K, int K1, int K2, float sigma2, int R_) {
+    const int R = MULTI ? R_ : 1;
     __shared__ float2 s_grid[kWin * kWin];
     __shared__ float s_re[kWin * kWin];
     __shared__ float s_im[kWin * kWin];
@@ -348,17 +422,23 @@ __global__ void __launch_bounds__(256, FHS_FUSED_MIN_BLOCKS) degrid_grid_binned_
     // phase 1: gathers, one row per thread
     if (MODE != kScatter) {
         if (dense)
-            gather_phase<MODE, true>(nv, s_meta, s_off, s_y, s_d, fbin, s_grid, wy0, wx0, gl, K1, K2, sc, sigma2,
+            gather_phase<MODE, true>(nv, R, s_meta, s_off, s_y, s_d, fbin, s_grid, wy0, wx0, gl, K1, K2, sc, sigma2,
                                      dvis + v0, nrm);
         else
-            gather_phase<MODE, false>(nv, s_meta, s_off, s_y, s_d, fbin, s_grid, wy0, wx0, gl, K1, K2, sc, sigma2,
+            gather_phase<MODE, false>(nv, R, s_meta, s_off, s_y, s_d, fbin, s_grid, wy0, wx0, gl, K1, K2, sc, sigma2,
                                       dvis + v0, nrm);
     }
     // phase 2: scatters of conj(G_i) s_d[i], one row per warp
     if (MODE != kGather) {
         if (MODE != kScatter) __syncthreads();       // s_d holds the new values
         Kahan unused;
-        if (dense)
+        if (MULTI) {
+            if (dense)
+                scatter_rows_rank<true>(warp, nv, lane, R, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1, K2);
+            else
+                scatter_rows_rank<false>(warp, nv, lane, R, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1,
+                                         K2);
+        } else if (dense)
             bin_rows<kScatter, true>(warp, nv, lane, s_meta, s_off, s_y, s_d, fbin, s_grid, s_re, s_im, wy0, wx0,
                                      gl, gb, K1, K2, sc, sigma2, dvis + v0, unused);
         else
@@ -413,37 +493,37 @@ __global__ void __launch_bounds__(256, FHS_FUSED_MIN_BLOCKS) degrid_grid_binned_
 
 cudaError_t launch_degrid(fhs_problem *p, const float2 *grid, float2 *vis_sorted, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
-    degrid_grid_binned_kernel<kGather><<<p->n_bin, 256, 0, s>>>(
+    (p->rank > 1 ? degrid_grid_binned_kernel<kGather, true> : degrid_grid_binned_kernel<kGather, false>)<<<p->n_bin, 256, 0, s>>>(
         p->meta, p->fptr, p->gfac, nullptr, vis_sorted, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B,
-        nullptr, nullptr, grid, nullptr, p->K, p->K1, p->K2, 0.f);
+        nullptr, nullptr, grid, nullptr, p->K, p->K1, p->K2, 0.f, p->rank);
     p->n_launch += 1;
     return cudaGetLastError();
 }
 
 cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
-    degrid_grid_binned_kernel<kScatter><<<p->n_bin, 256, 0, s>>>(
+    (p->rank > 1 ? degrid_grid_binned_kernel<kScatter, true> : degrid_grid_binned_kernel<kScatter, false>)<<<p->n_bin, 256, 0, s>>>(
         p->meta, p->fptr, p->gfac, nullptr, const_cast<float2 *>(vis_sorted), p->bin_start, p->bin_seg,
-        p->bin_tile, p->ntx, p->B, nullptr, nullptr, nullptr, grid, p->K, p->K1, p->K2, 0.f);
+        p->bin_tile, p->ntx, p->B, nullptr, nullptr, nullptr, grid, p->K, p->K1, p->K2, 0.f, p->rank);
     p->n_launch += 1;
     return cudaGetLastError();
 }
 
 cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
-    degrid_grid_binned_kernel<kNormal><<<p->n_bin, 256, 0, s>>>(
+    (p->rank > 1 ? degrid_grid_binned_kernel<kNormal, true> : degrid_grid_binned_kernel<kNormal, false>)<<<p->n_bin, 256, 0, s>>>(
         p->meta, p->fptr, p->gfac, nullptr, nullptr, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B, nullptr,
-        nullptr, grid, grid_out, p->K, p->K1, p->K2, 0.f);
+        nullptr, grid, grid_out, p->K, p->K1, p->K2, 0.f, p->rank);
     p->n_launch += 1;
     return cudaGetLastError();
 }
 
 cudaError_t launch_degrid_grid_fused(fhs_problem *p, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
-    degrid_grid_binned_kernel<kFused><<<p->n_bin, 256, 0, s>>>(p->meta, p->fptr, p->gfac, p->y, p->dvis, p->bin_start,
+    (p->rank > 1 ? degrid_grid_binned_kernel<kFused, true> : degrid_grid_binned_kernel<kFused, false>)<<<p->n_bin, 256, 0, s>>>(p->meta, p->fptr, p->gfac, p->y, p->dvis, p->bin_start,
                                                        p->bin_seg, p->bin_tile, p->ntx, p->B, p->blk_scale,
                                                        p->blk_norm2, p->grid_work, p->grid_blk, p->K, p->K1, p->K2,
-                                                       float(p->sigma2));
+                                                       float(p->sigma2), p->rank);
     p->n_launch += 1;
     return cudaGetLastError();
 }

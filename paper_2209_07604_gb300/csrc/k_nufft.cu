@@ -51,12 +51,22 @@ __device__ __forceinline__ int seg_of(const long long *seg_off, int n_seg, long 
 // the w-kernel of the row's plane, whitening; the row of G is the outer
 // product g1 (x) g2 of the two 1-D factors, stored as T values of g1 (times
 // 1/sigma) followed by T values of g2, in FP32.
+//
+// With DDE kernels (dde != NULL, ext = kDdeTaps - 1) the row is the 2-D
+// convolution of that outer product (Tb = T - ext taps per axis) with the
+// row's kDdeTaps x kDdeTaps DDE kernel D (Sec. 3.1).  Splitting the
+// convolution over the first DDE axis makes it exact with kDdeTaps separable
+// terms: G[a][b] = sum_r A_r[a] B_r[b], A_r[a] = g1[a - r],
+// B_r[b] = sum_j D[r][j] g2[b - j] (out-of-range taps zero).  Term r is
+// stored at offset 2 T r as T values of A_r followed by T values of B_r.
 __global__ void __launch_bounds__(256) build_g_kernel(
     const int2 *__restrict__ meta, const long long *__restrict__ fptr, float2 *__restrict__ gfac,
     const double2 *__restrict__ kap, const short *__restrict__ plane, const double2 *__restrict__ wk,
+    const double2 *__restrict__ dde, int ext,
     const long long *__restrict__ seg_off, int n_seg, const double *__restrict__ inv_sigma_seg,
     long long Mtot, int J, double beta, double inv_i0b) {
     __shared__ double s_kb[kWarps][2][16];
+    __shared__ double2 s_g[kWarps][2][16];
     __shared__ double s_c[kI0Terms];          // 1 / (k!)^2
     if (threadIdx.x == 0) {
         double ck = 1.0;
@@ -70,7 +80,8 @@ __global__ void __launch_bounds__(256) build_g_kernel(
     const long long stride = (long long)gridDim.x * kWarps;
     for (long long v = (long long)blockIdx.x * kWarps + warp; v < Mtot; v += stride) {
         const int T = meta[v].y;
-        const int h = (T - J) / 2;
+        const int Tb = T - ext;
+        const int h = (Tb - J) / 2;
         const int S = 2 * h + 1;
         const double2 kp = kap[v];
         const int dim = lane >> 4, i = lane & 15;
@@ -79,7 +90,7 @@ __global__ void __launch_bounds__(256) build_g_kernel(
         if (i < J) s_kb[warp][dim][i] = kb_eval(kd - double(p0 + i), J, beta, inv_i0b, s_c);
         __syncwarp();
         const int pl = plane[v];
-        if (i < T) {
+        if (i < Tb) {
             double2 acc = make_double2(0.0, 0.0);
             for (int jj = 0; jj < S; ++jj) {
                 const int ti = i + jj - (S - 1);
@@ -90,7 +101,32 @@ __global__ void __launch_bounds__(256) build_g_kernel(
                 acc.y += c.y * k;
             }
             const double f = dim ? 1.0 : inv_sigma_seg[seg_of(seg_off, n_seg, v)];
-            gfac[fptr[v] + dim * T + i] = make_float2(float(acc.x * f), float(acc.y * f));
+            acc.x *= f;
+            acc.y *= f;
+            if (dde) s_g[warp][dim][i] = acc;
+            else gfac[fptr[v] + dim * T + i] = make_float2(float(acc.x), float(acc.y));
+        }
+        if (dde) {
+            __syncwarp();
+            const double2 *D = dde + v * (kDdeTaps * kDdeTaps);
+            for (int e = lane; e < 2 * kDdeTaps * T; e += 32) {
+                const int r = e / (2 * T), q = e - r * 2 * T;
+                double2 val = make_double2(0.0, 0.0);
+                if (q < T) {
+                    const int a = q - r;
+                    if (a >= 0 && a < Tb) val = s_g[warp][0][a];
+                } else {
+                    const int bq = q - T;
+                    for (int j = 0; j < kDdeTaps; ++j) {
+                        const int b = bq - j;
+                        if (b < 0 || b >= Tb) continue;
+                        const double2 d = D[r * kDdeTaps + j], g = s_g[warp][1][b];
+                        val.x += d.x * g.x - d.y * g.y;
+                        val.y += d.x * g.y + d.y * g.x;
+                    }
+                }
+                gfac[fptr[v] + e] = make_float2(float(val.x), float(val.y));
+            }
         }
         __syncwarp();
     }
@@ -299,12 +335,11 @@ inline int grid_for(long long n, int threads, int cap = 152 * 16) {
 }  // namespace
 
 cudaError_t launch_build_g(fhs_problem *p, const double2 *kap, const short *plane, const double2 *wk_table,
-                           const int * /*wk_half*/, int /*n_planes_total*/, const double *inv_sigma_seg,
-                           cudaStream_t s) {
+                           const double2 *dde, int ext, const double *inv_sigma_seg, cudaStream_t s) {
     const double beta = kb_beta(p->J, 2.0);
     build_g_kernel<<<grid_for(p->Mtot, kWarps, 152 * 64), 256, 0, s>>>(
-        p->meta, p->fptr, p->gfac, kap, plane, wk_table, p->d_seg_off, p->n_seg, inv_sigma_seg, p->Mtot, p->J,
-        beta, 1.0 / bessel_i0(beta));
+        p->meta, p->fptr, p->gfac, kap, plane, wk_table, dde, ext, p->d_seg_off, p->n_seg, inv_sigma_seg, p->Mtot,
+        p->J, beta, 1.0 / bessel_i0(beta));
     p->n_launch += 1;
     return cudaGetLastError();
 }

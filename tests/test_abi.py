@@ -116,3 +116,25 @@ def test_estimate_bytes_counts_g_factors(lib):
     assert pk0 > r0 and pk1 > r1
     r2, _ = fhs.fhs_estimate_bytes(p, np.zeros(2 * M), 2 * M)
     assert r2 > r0
+
+
+def test_dde_rejections_without_device(lib):
+    """fhs_create_problem_dde refuses a NULL kernel array, and boxes that the 4
+    DDE taps would widen past 16 (w-kernels of 4 extra taps per side at w_max),
+    before touching the device."""
+    p = fhs.default_params(ny=32, nx=32, n_channels=2, n_subcubes=1, n_blocks=2, w_max=2000.0, pixel_size=1e-4)
+    om, y, sig, vo, bo = _args()
+    h = C.c_void_p()
+    st = lib.fhs_create_problem_dde(C.byref(p), om.ctypes.data_as(C.c_void_p), None, y.ctypes.data_as(C.c_void_p),
+                                    sig.ctypes.data_as(C.c_void_p), vo.ctypes.data_as(C.c_void_p),
+                                    bo.ctypes.data_as(C.c_void_p), None, None, None, C.byref(h))
+    assert st == fhs.FHS_ERR_ARG and not h.value
+    dde = np.zeros((len(om), 5, 5), dtype=np.complex128)
+    dde[:, 2, 2] = 1.0
+    w = np.full(len(om), 2000.0)
+    with pytest.raises(fhs.FhsError) as e:
+        fhs.fhs_create_problem(p, om, w, y, sig, vo, bo, dde=dde)
+    assert e.value.status == fhs.FHS_ERR_ARG
+    assert "16 taps" in lib.fhs_last_error().decode()
+    with pytest.raises(ValueError):
+        fhs.fhs_create_problem(p, om, w, y, sig, vo, bo, dde=dde[:3])
