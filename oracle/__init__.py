@@ -19,6 +19,9 @@ matrix-vector products, dense SVD/eigh), written from the paper:
 * ``defaults`` PSF-peak normalisation, residual and dirty image (Sec. 5.3),
                dirty-image defaults of mu and mu_bar (a reading: the paper
                defers the heuristics to Part I).
+* ``reduction`` visibility-gridding data reduction: gridding operator
+               Gamma = Lambda G^H Theta^H, reduced operator Phi' = Lambda H F Z
+               (Sec. 3.4, Eqs. 4-5), the default bound eps' (a reading).
 
 Nothing here is shared with the CUDA library; the two implementations are
 compared in the tests.  Every function states the passage it follows and,

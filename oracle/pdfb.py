@@ -21,7 +21,8 @@ s0 = 1 / max facet coverage (= ||L0||^2), s2 = 1 / max_l ||Phi_l||^2,
 tau = 0.99 / 3.  Start: x = 0, all duals 0, all weights 1.  Reweighting:
 w_r = upsilon / (upsilon + ||(Psi^dagger X)_r||), w_{q,i} = upsilon_bar /
 (upsilon_bar + sigma_i(S_q X)), duals kept.  Channels l of sub-cube c are
-l = c, c + C, ... (channel interleaving, Eq. 3).
+l = c, c + C, ... (channel interleaving, Eq. 3).  With ``reduction`` the data
+term is that of the gridded data (Sec. 3.4, see ``reduction.py``).
 """
 from __future__ import annotations
 
@@ -30,6 +31,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import nufft, prox, wavelets
+from . import reduction as reduction_mod
 
 
 @dataclass
@@ -46,13 +48,23 @@ class FHS:
     def __init__(self, omega, w, y, sigma, block_offsets, ny, nx, C, qy, qx, overlap,
                  mu, mu_bar, upsilon=1e-3, upsilon_bar=1e-3, w_max=0.0, n_wplanes=64,
                  pixel_size=0.0, levels=4, eps=None, steps: Steps | None = None,
-                 faceted_sara: bool = False, sara_q=(1, 1), dde=None):
+                 faceted_sara: bool = False, sara_q=(1, 1), dde=None, reduction: bool = False):
         self.L = omega.shape[0]
         self.ny, self.nx, self.C = ny, nx, C
         self.geom = nufft.Geometry(ny, nx, w_max=w_max, n_wplanes=n_wplanes, pixel_size=pixel_size)
         self.op = nufft.Operator(omega, w, sigma, self.geom, dde=dde)
         self.yw = [y[l] / sigma[l] for l in range(self.L)]                 # Theta_l y_l
         self.bo = np.asarray(block_offsets, dtype=np.int64)
+        # data term: Phi_l on the visibility blocks, or with the data reduction of
+        # Sec. 3.4 Phi'_l on the gridded data y'_l, one block per channel
+        self.data = self.op
+        if reduction:
+            self.red = reduction_mod.Reduced(self.op, self.yw)
+            self.data = self.red
+            self.yw = self.red.y
+            self.bo = np.array([[0, self.red.m_red(l)] for l in range(self.L)], dtype=np.int64)
+            if eps is None:
+                eps = self.red.eps_default()
         B = self.bo.shape[1] - 1
         if eps is None:
             eps = np.stack([prox.eps_blocks(len(self.yw[l]), np.diff(self.bo[l])) for l in range(self.L)])
@@ -64,7 +76,7 @@ class FHS:
         self.upsilon, self.upsilon_bar = float(upsilon), float(upsilon_bar)
         self.chans = [list(range(c, self.L, C)) for c in range(C)]
         if steps is None:
-            nrm = max(self.op.norm2(l) for l in range(self.L))
+            nrm = max(self.data.norm2(l) for l in range(self.L))
             cov = prox.facet_coverage(ny, nx, self.facets).max()
             steps = Steps(tau=0.99 / 3.0, sigma0=1.0 / cov, sigma1=1.0, sigma2=1.0 / nrm)
         self.steps = steps
@@ -89,12 +101,12 @@ class FHS:
         Xb = 2.0 * Xp - X
         # data fidelity: l2 balls per block, then the adjoint Re(Phi_l^H v_l)
         for l in range(self.L):
-            phix = self.op.forward(Xb[l], l)
+            phix = self.data.forward(Xb[l], l)
             for b in range(self.bo.shape[1] - 1):
                 s0, s1 = self.bo[l, b], self.bo[l, b + 1]
                 self.v[l][s0:s1] = prox.l2ball_dual(self.v[l][s0:s1], phix[s0:s1],
                                                     self.yw[l][s0:s1], self.eps[l, b], st.sigma2)
-            self.A_data[l] = self.op.adjoint(self.v[l], l)
+            self.A_data[l] = self.data.adjoint(self.v[l], l)
         # average joint sparsity: weighted l21 over each sub-cube
         for c, ch in enumerate(self.chans):
             Aw = self.sara.analysis(Xb[ch])
@@ -142,7 +154,7 @@ class FHS:
         """||Phi_{l,b} x_l - y_{l,b}|| for every block (feasibility check)."""
         out = np.zeros(self.eps.shape)
         for l in range(self.L):
-            r = self.op.forward(self.X[l], l) - self.yw[l]
+            r = self.data.forward(self.X[l], l) - self.yw[l]
             for b in range(self.bo.shape[1] - 1):
                 out[l, b] = np.linalg.norm(r[self.bo[l, b]:self.bo[l, b + 1]])
         return out
