@@ -165,7 +165,7 @@ def run_gpu(args):
     gram = {"fp32": fhs.GRAM_FP32, "tf32": fhs.GRAM_TF32, "bf16": fhs.GRAM_BF16, "fp64": fhs.GRAM_FP64}[args.gram]
     params = fhs.default_params(ny=P.ny, nx=P.nx, n_channels=L, n_subcubes=P.C, n_blocks=P.B, qy=P.qy, qx=P.qx,
                                 facet_overlap=P.overlap, w_max=P.w_max, pixel_size=P.pixel_size, mu=MU,
-                                mu_bar=MU_BAR, gram_precision=gram)
+                                mu_bar=MU_BAR, gram_precision=gram, data_reduction=int(args.reduction))
     e2e_iters = args.e2e_iters
     img_host = torch.empty((L, P.ny, P.nx), dtype=torch.float32, pin_memory=True)
     t_e2e = time.perf_counter()
@@ -241,10 +241,14 @@ def run_gpu(args):
     K = 4 * P.ny * P.nx
     peak, peak_kind = _peaks()
     kbytes = fused_kernel_bytes(info, L, P.B, K, Mtot)
+    if args.reduction:
+        # two normal-mode passes per iteration (H Xhat, then H Lambda v): factors, row meta and
+        # offsets, the input grid read and the output grid written once each per pass
+        kbytes = 2 * (info.n_gfac * 8 + Mtot * 16 + 2 * L * K * 8)
     k_ms = phases["degrid_grid"] / max(n_prof, 1)
     achieved = kbytes / (k_ms * 1e-3) / 1e9
     traffic, limiter = _profile_traffic("k_binned.cu")
-    if args.workload != WORKLOAD or args.dde:
+    if args.workload != WORKLOAD or args.dde or args.reduction:
         traffic = None          # the committed capture is scaled to the default workload only
     # visibilities through Phi and Phi^H per second inside the PDFB iteration
     vis_s = Mtot / (ms_step * 1e-3)
@@ -268,7 +272,9 @@ def run_gpu(args):
                    "mu": MU, "mu_bar": MU_BAR, "gram": args.gram,
                    "bins": {"dense_min": info.bin_dense_min, "split": info.bin_split,
                             "autotuned": bool(args.autotune)},
-                   "dde": "5x5 kernel per visibility, w halved" if args.dde else None},
+                   "dde": "5x5 kernel per visibility, w halved" if args.dde else None,
+                   "data_reduction": ({"gridded_points": int(info.n_red), "visibilities": int(Mtot)}
+                                      if args.reduction else None)},
         "vis_per_s": ws * vis_s,
         "phi_vis_per_s": ws * Mtot / (phi_ms * 1e-3),
         "phi_adjoint_vis_per_s": ws * Mtot / (phit_ms * 1e-3),
@@ -286,7 +292,7 @@ def run_gpu(args):
         "device_bytes": info.device_bytes,
         "generate_seconds": gen_s,
     }
-    if rank == 0 and not args.no_cpu_baseline and ws == 1 and not args.dde:
+    if rank == 0 and not args.no_cpu_baseline and ws == 1 and not args.dde and not args.reduction:
         out["cpu_baseline"] = cpu_baseline(P, info)
     prob.close()
     if ws > 1:
@@ -470,6 +476,8 @@ def main():
                     help="arithmetic of the nuclear facet Gram (tf32/bf16: tensor cores)")
     ap.add_argument("--dde", action="store_true",
                     help="fold seeded 5x5 DDE kernels into G (w halved to keep boxes within 16 taps)")
+    ap.add_argument("--reduction", action="store_true",
+                    help="visibility-gridding data reduction: Phi' = Lambda H F Z, one l2 ball per channel")
     ap.add_argument("--mode", default="pdfb", choices=["pdfb", "serve"])
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=4.0)

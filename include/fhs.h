@@ -80,7 +80,26 @@ typedef struct fhs_params {
     int32_t power_iters;     /* Lanczos steps for ||Phi_l||^2 (default 100)        */
     double  power_tol;       /* relative change of the estimate that stops them    */
     int32_t gram_precision;  /* facet Gram of the nuclear dual step, fhs_gram_precision */
+    int32_t data_reduction;  /* 1: visibility-gridding data reduction (Sec. 3.4), see below */
 } fhs_params;
+
+/* Data reduction (data_reduction = 1, Sec. 3.4, Eqs. 4-5).  Each channel's
+ * visibilities are gridded, y'_l = Lambda_l (Theta_l G_l)^H y_l, and the data
+ * term becomes one l2 ball per channel (all blocks aggregated) around y'_l for
+ * Phi'_l = Lambda_l H_l F Z, H_l = (Theta_l G_l)^H (Theta_l G_l), Lambda_l =
+ * diag(H_l)^(-1/2) on the M'_l grid cells some visibility reaches (0 elsewhere).
+ * H_l is applied as a pass over G (it is not stored), so an iteration makes two
+ * passes over G instead of one.  With data reduction:
+ *  - eps (fhs_create_problem) is [L]: eps'_l; NULL selects
+ *    eps'_l = sqrt(M'_l + 2 sqrt(M'_l)) (Eq. 2's bound for M'_l unit-variance
+ *    values: E||Gamma n||^2 = M'_l for whitened noise n);
+ *  - sigma2 <= 0 selects 1 / max_l ||Phi'_l||^2, the PSF normalisation and the
+ *    dirty image of the mu / mu_bar defaults use Phi'_l, and fhs_residual
+ *    returns eta'_l Re Phi'^H_l (y'_l - Phi'_l x_l);
+ *  - the data dual (FHS_STATE_DUAL_DATA) is [L][2N_y][2N_x] complex on the
+ *    oversampled grid (zero off the gridded cells);
+ *  - fhs_measure and fhs_adjoint still apply Phi_l and Phi_l^H of the
+ *    visibilities. */
 
 /* Arithmetic of the facet Gram G_q = Z_q^T Z_q in the nuclear dual step
  * (Sec. 2.2.2).  FP32: FP32 products on the CUDA cores, FP64 sums across
@@ -157,6 +176,7 @@ typedef struct fhs_info {
     int32_t bin_dense_min;   /* binning of the pass over G (fhs_autotune_bins)     */
     int32_t bin_split;
     double  mu, mu_bar;      /* regularisation in use (the defaults once computed) */
+    int64_t n_red;           /* gridded data points sum_l M'_l (0 without data reduction) */
 } fhs_info;
 
 fhs_status fhs_get_info(const fhs_problem *prob, fhs_info *info);
@@ -172,6 +192,21 @@ fhs_status fhs_measure(fhs_problem *prob, const float *x_dev, float *vis_dev, vo
  * for x = 0, which gives the dirty image.  Asynchronous; uses the problem's
  * scratch (not the PDFB state). */
 fhs_status fhs_residual(fhs_problem *prob, const float *x_dev, float *r_dev, void *stream);
+
+/* Noise levels and l2 bounds from a model cube x0_dev ([L][ny][nx] float32,
+ * device), as the paper sets them from the model image of a calibration step
+ * (Sec. 3.3 (i), Sec. 5): with the whitened residual visibilities
+ * r_{l,b} = Theta_l (y_{l,b} - Phi_{l,b} x0_l),
+ *   sigma_out[l*B + b] = sigma_l * (sample standard deviation of r_{l,b},
+ *                        complex, mean removed, M_{l,b} - 1 degrees of freedom)
+ *   eps_out[l*B + b]   = ||r_{l,b}||_2.
+ * With data reduction both are [L]: eps_out[l] = ||y'_l - Phi'_l x0_l||_2 (Sec.
+ * 5.2, with the model visibilities Phi_l x0_l) and sigma_out[l] = eps_out[l] /
+ * sqrt(M'_l).  sigma_out / eps_out (host) may be NULL.  apply != 0 makes
+ * eps_out the problem's l2 bounds for the following iterations.  Synchronises
+ * `stream`. */
+fhs_status fhs_noise_from_model(fhs_problem *prob, const float *x0_dev, int32_t apply, double *sigma_out,
+                                double *eps_out, void *stream);
 
 /* x_dev[L][ny][nx] = Re(Phi_l^H v_l), the adjoint of fhs_measure for real
  * images.  vis_dev: [M_tot] complex in the caller's order.  Asynchronous. */

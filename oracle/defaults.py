@@ -13,6 +13,14 @@ CPU-baseline leg of the benchmark.
   mu_bar = 1 / sum_{c,q} ||S_q X_c||_* (facet nuclear norms of every
   sub-cube, D_q = 1) and mu = 1 / sum_c ||Psi^dagger X_c||_{2,1} (rows over
   the sub-cube's channels).  Sub-cube c holds channels c, c + C, ... (Eq. 3).
+* Noise statistics and l2 bounds from a model image (Sec. 3.3 (i), Sec. 5.1
+  and the pre-processing paragraph of Sec. 5): with the residual visibilities
+  r_{l,b} = Theta_l (y_{l,b} - Phi_{l,b} x0_l) of a model cube x0, the noise
+  level of block (l, b) is sigma_l times the standard deviation of r_{l,b}
+  (complex sample standard deviation, mean removed, M_{l,b} - 1 degrees of
+  freedom) and its l2 bound is ||r_{l,b}||_2.  With data reduction the bound
+  of channel l is ||y'_l - Phi'_l x0_l||_2 (Sec. 5.2, with the model
+  visibilities Phi_l x0_l), and its noise level eps'_l / sqrt(M'_l).
 """
 from __future__ import annotations
 
@@ -52,3 +60,27 @@ def default_regularisation(Xd: np.ndarray, C: int, facets, sara) -> tuple:
         A = np.stack([sara.analysis(Xd[l]) for l in ch])
         l21 += float(np.sqrt((A ** 2).sum(axis=0)).sum())
     return 1.0 / l21, 1.0 / nuc
+
+
+def noise_from_model(op, yw, sigma, block_offsets, X0: np.ndarray) -> tuple:
+    """(sigma_hat (L, B), eps (L, B)) from the model cube X0 (L, ny, nx); yw the
+    whitened data per channel, sigma the per-channel whitening."""
+    bo = np.asarray(block_offsets)
+    L, B = bo.shape[0], bo.shape[1] - 1
+    sig = np.zeros((L, B))
+    eps = np.zeros((L, B))
+    for l in range(L):
+        r = yw[l] - op.forward(X0[l], l)
+        for b in range(B):
+            rb = r[bo[l, b]:bo[l, b + 1]]
+            eps[l, b] = np.linalg.norm(rb)
+            if len(rb) > 1:
+                sig[l, b] = sigma[l] * np.sqrt(np.sum(np.abs(rb - rb.mean()) ** 2) / (len(rb) - 1))
+    return sig, eps
+
+
+def reduced_bounds(red, X0: np.ndarray) -> tuple:
+    """(sigma_hat (L,), eps' (L,)) of the reduced data (``reduction.Reduced``)."""
+    eps = np.array([np.linalg.norm(red.y[l] - red.forward(X0[l], l)) for l in range(red.L)])
+    m = np.array([red.m_red(l) for l in range(red.L)], dtype=np.float64)
+    return np.where(m > 0, eps / np.sqrt(np.maximum(m, 1.0)), 0.0), eps

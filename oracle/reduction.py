@@ -72,6 +72,19 @@ class Reduced:
         return np.array([prox.eps_blocks(self.m_red(l), np.array([self.m_red(l)]))[0] if self.m_red(l) else 0.0
                          for l in range(self.L)])
 
+    def norm2_eigsh(self, l: int, tol: float = 1e-12) -> float:
+        """||Phi'_l||^2 as the largest eigenvalue of Re(Phi'_l^H Phi'_l) by ARPACK's
+        implicitly restarted Lanczos (scipy ``eigsh``)."""
+        from scipy.sparse.linalg import LinearOperator, eigsh
+        ny, nx = self.op.geom.ny, self.op.geom.nx
+
+        def mv(x):
+            return np.asarray(self.adjoint(self.forward(np.asarray(x).reshape(ny, nx), l), l)).ravel()
+
+        A = LinearOperator((ny * nx, ny * nx), matvec=mv, dtype=np.float64)
+        v0 = np.random.default_rng(0).standard_normal(ny * nx)
+        return float(eigsh(A, k=1, which="LA", tol=tol, v0=v0, return_eigenvectors=False)[0])
+
     def norm2(self, l: int, n_iter: int = 200, tol: float = 1e-10, seed: int = 0) -> float:
         """||Phi'_l||^2 by power iteration on Re(Phi'_l^H Phi'_l)."""
         rng = np.random.default_rng(seed)

@@ -19,7 +19,7 @@ FHS_OK, FHS_ERR_ARG, FHS_ERR_OOM, FHS_ERR_CUDA, FHS_ERR_TIMEOUT, FHS_ERR_STATE =
 STATE_IMAGE, STATE_DUAL_DATA, STATE_DUAL_SARA, STATE_DUAL_NUCLEAR, STATE_WEIGHTS_SARA, STATE_WEIGHTS_NUC = range(6)
 
 EXPORTED = [
-    "fhs_default_params", "fhs_create_problem", "fhs_create_problem_dde", "fhs_destroy_problem", "fhs_get_info", "fhs_measure",
+    "fhs_default_params", "fhs_create_problem", "fhs_create_problem_dde", "fhs_noise_from_model", "fhs_destroy_problem", "fhs_get_info", "fhs_measure",
     "fhs_adjoint", "fhs_sara_analysis", "fhs_sara_synthesis", "fhs_pdfb_step", "fhs_reweight", "fhs_solve",
     "fhs_state_size", "fhs_get_state", "fhs_set_state", "fhs_operator_norms", "fhs_daubechies_filter",
     "fhs_last_error", "fhs_profile_enable", "fhs_profile_read", "fhs_kernel_launches",
@@ -46,7 +46,7 @@ class fhs_params(C.Structure):
         ("pixel_size", C.c_double), ("mu", C.c_double), ("mu_bar", C.c_double), ("upsilon", C.c_double),
         ("upsilon_bar", C.c_double), ("tau", C.c_double), ("sigma0", C.c_double), ("sigma1", C.c_double),
         ("sigma2", C.c_double), ("power_iters", C.c_int32), ("power_tol", C.c_double),
-        ("gram_precision", C.c_int32),
+        ("gram_precision", C.c_int32), ("data_reduction", C.c_int32),
     ]
 
 
@@ -56,7 +56,7 @@ class fhs_info(C.Structure):
         ("device_bytes", C.c_int64), ("n_facets", C.c_int32), ("iteration", C.c_int32), ("tau", C.c_double),
         ("sigma0", C.c_double), ("sigma1", C.c_double), ("sigma2", C.c_double), ("phi_norm2_max", C.c_double),
         ("n_gfac", C.c_int64), ("bin_dense_min", C.c_int32), ("bin_split", C.c_int32),
-        ("mu", C.c_double), ("mu_bar", C.c_double),
+        ("mu", C.c_double), ("mu_bar", C.c_double), ("n_red", C.c_int64),
     ]
 
 
@@ -92,6 +92,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fhs_default_params": (None, [P(fhs_params)]),
         "fhs_create_problem": (C.c_int, [P(fhs_params), vp, vp, vp, vp, vp, vp, vp, vp, P(vp)]),
         "fhs_create_problem_dde": (C.c_int, [P(fhs_params), vp, vp, vp, vp, vp, vp, vp, vp, vp, P(vp)]),
+        "fhs_noise_from_model": (C.c_int, [vp, vp, C.c_int32, vp, vp, vp]),
         "fhs_destroy_problem": (None, [vp]),
         "fhs_get_info": (C.c_int, [vp, P(fhs_info)]),
         "fhs_measure": (C.c_int, [vp, vp, vp, vp]),
@@ -225,6 +226,16 @@ def fhs_residual(prob, x, r, stream=None):
     """r = eta Re Phi^H (y - Phi x); x None gives the dirty image."""
     xp = C.c_void_p(None) if x is None else _dev(x, "float32")
     _check(load_library().fhs_residual(prob, xp, _dev(r, "float32"), _stream(stream)))
+
+
+def fhs_noise_from_model(prob, x0, n_out, apply=False, stream=None):
+    """(sigma, eps) float64 arrays of n_out values (blocks, or channels with data
+    reduction) from the model cube x0; apply=True makes eps the l2 bounds."""
+    sig = np.zeros(n_out)
+    eps = np.zeros(n_out)
+    _check(load_library().fhs_noise_from_model(prob, _dev(x0, "float32"), int(bool(apply)), _ptr(sig), _ptr(eps),
+                                               _stream(stream)))
+    return sig, eps
 
 
 def fhs_sara_analysis(prob, x, coef, stream=None):
@@ -466,6 +477,12 @@ class Problem:
         r = self._img()
         fhs_residual(self.handle, x, r)
         return r
+
+    def noise_from_model(self, x0, apply=False):
+        """Noise levels and l2 bounds from a model cube (per block; per channel with
+        data reduction)."""
+        n = self.L if int(self.params.data_reduction) else self.L * int(self.params.n_blocks)
+        return fhs_noise_from_model(self.handle, x0, n, apply)
 
     def sara_analysis(self, x):
         import torch

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfhs.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 CUDA_SOURCES = ["fhs_api.cu", "fhs_server.cu", "k_binned.cu", "k_gram_tc.cu", "k_nufft.cu", "k_sara.cu", "k_nuclear.cu",
-                "k_pdfb.cu"]
+                "k_pdfb.cu", "k_reduce.cu"]
 CXX_SOURCES = ["host_math.cpp"]
 
 

@@ -202,6 +202,7 @@ fhs_status check_params(const fhs_params *q) {
     if (!(q->upsilon > 0.0) || !(q->upsilon_bar > 0.0)) return fail(FHS_ERR_ARG, "upsilon and upsilon_bar must be > 0");
     if (q->gram_precision < FHS_GRAM_FP32 || q->gram_precision > FHS_GRAM_FP64)
         return fail(FHS_ERR_ARG, "gram_precision must be one of FHS_GRAM_FP32, _TF32, _BF16, _FP64");
+    if (q->data_reduction != 0 && q->data_reduction != 1) return fail(FHS_ERR_ARG, "data_reduction must be 0 or 1");
     return FHS_OK;
 }
 
@@ -237,14 +238,36 @@ fhs_status adjoint_to_image(fhs_problem *p, const float2 *vis_sorted, float *x, 
 // keeps its zero padding (Z writes the image cells only) and grid_work (Phi^H
 // of the data dual) is iteration state, so the adjoint grids go to the first
 // L grids of grid_blk, which are zero between iterations and zero again after.
+//
+// With data reduction, y = Re(Phi'^H Phi') v = Re Z^T F^H H Lambda^2 H F Z v:
+// two passes over G with the Lambda^2 weighting between them (dr_u and dr_w
+// are zero / free between iterations).
 fhs_status apply_normal(fhs_problem *p, const float *v, float *y, cudaStream_t s) {
     float2 *scratch = p->grid_blk;
     CU(launch_zpad(p, v, p->grid_in, s));
     TRY(fft(p, p->grid_in, p->grid_aux, CUFFT_FORWARD, s));
-    CU(launch_normal(p, p->grid_aux, scratch, s));
+    if (p->dr) {
+        CU(launch_normal(p, p->grid_aux, p->dr_u, s));
+        CU(launch_dr_combine(p, p->dr_u, 0.f, 1.f, p->dr_w, s));
+        CU(launch_normal(p, p->dr_w, scratch, s));
+    } else {
+        CU(launch_normal(p, p->grid_aux, scratch, s));
+    }
     TRY(fft(p, scratch, scratch, CUFFT_INVERSE, s));
     CU(launch_crop(p, scratch, y, s));
     CU(cudaMemsetAsync(scratch, 0, sizeof(float2) * p->K * p->L, s));
+    return FHS_OK;
+}
+
+// x = Re Phi^H y (the dirty image before the PSF normalisation); with data
+// reduction Re Phi'^H y' = Re Z^T F^H H Lambda y'.
+fhs_status dirty_image(fhs_problem *p, float *x, cudaStream_t s) {
+    if (!p->dr) return adjoint_to_image(p, p->y, x, s);
+    CU(launch_dr_combine(p, nullptr, 1.f, 0.f, p->dr_w, s));
+    CU(cudaMemsetAsync(p->grid_aux, 0, sizeof(float2) * p->K * p->L, s));
+    CU(launch_normal(p, p->dr_w, p->grid_aux, s));
+    TRY(fft(p, p->grid_aux, p->grid_aux, CUFFT_INVERSE, s));
+    CU(launch_crop(p, p->grid_aux, x, s));
     return FHS_OK;
 }
 
@@ -313,7 +336,7 @@ fhs_status default_regularisation(fhs_problem *p, cudaStream_t s) {
     if (!want_mu && !want_mu_bar) return FHS_OK;
     const long long LN = (long long)p->L * p->N;
     float *X = p->A_sara;
-    TRY(adjoint_to_image(p, p->y, X, s));
+    TRY(dirty_image(p, X, s));
     CU(launch_chan_scale(p, X, p->eta, s));
     double *tmp = nullptr;
     const size_t n_tmp = (size_t)p->C * p->Q * p->Lc + p->C;
@@ -493,14 +516,24 @@ fhs_status one_iteration(fhs_problem *p, cudaStream_t s) {
     }
     {
         Phase ph(p, s, FHS_PHASE_DEGRID_GRID);
-        CU(launch_degrid_grid_fused(p, s));
+        if (p->dr) CU(launch_normal(p, p->grid_work, p->dr_u, s));     // H Xhat
+        else CU(launch_degrid_grid_fused(p, s));
     }
     if (fork) {
         CU(cudaEventRecord(p->ev_fork, s));
         CU(cudaStreamWaitEvent(p->s_sara, p->ev_fork, 0));
         CU(cudaStreamWaitEvent(p->s_nuc, p->ev_fork, 0));
     }
-    {
+    if (p->dr) {
+        // reduced l2 balls, then the adjoint pass H Lambda v into grid_work
+        {
+            Phase ph(p, s, FHS_PHASE_L2BALL);
+            CU(launch_dr_dual(p, s));
+            CU(launch_dr_finalize(p, s));
+        }
+        Phase ph(p, s, FHS_PHASE_DEGRID_GRID);
+        CU(launch_normal(p, p->dr_w, p->grid_work, s));
+    } else {
         Phase ph(p, s, FHS_PHASE_L2BALL);
         CU(launch_block_finalize(p, s));
         CU(launch_combine(p, s));
@@ -634,6 +667,7 @@ void fhs_default_params(fhs_params *p) {
     p->power_iters = 100;
     p->power_tol = 1e-7;
     p->gram_precision = FHS_GRAM_FP32;
+    p->data_reduction = 0;
 }
 
 fhs_status fhs_daubechies_filter(int32_t p, double *h_out) {
@@ -703,12 +737,14 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
     };
     p->prm = q;
     p->home = s;
+    p->dr = q.data_reduction != 0;
     p->L = L; p->C = q.n_subcubes; p->Lc = L / q.n_subcubes; p->B = B; p->J = J;
     p->ny = q.ny; p->nx = q.nx; p->K1 = 2 * q.ny; p->K2 = 2 * q.nx;
     p->N = (long long)q.ny * q.nx;
     p->K = (long long)p->K1 * p->K2;
     p->Mtot = Mtot;
     p->vis_off.assign(vis_offsets, vis_offsets + L + 1);
+    p->sigma_l.assign(sigma, sigma + L);
     p->n_seg = L * B;
     p->seg_off.resize(p->n_seg + 1);
     for (int l = 0; l < L; ++l)
@@ -852,7 +888,7 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
         const double Ml = double(vis_offsets[l + 1] - vis_offsets[l]);
         for (int b = 0; b < B; ++b) {
             const double Mb = double(block_offsets[(int64_t)l * (B + 1) + b + 1] - block_offsets[(int64_t)l * (B + 1) + b]);
-            eps[l * B + b] = eps_in ? eps_in[l * B + b]
+            eps[l * B + b] = (eps_in && !q.data_reduction) ? eps_in[l * B + b]
                                     : (Ml > 0 ? std::sqrt((Ml + 2.0 * std::sqrt(Ml)) * Mb / Ml) : 0.0);
             inv_sig[l * B + b] = 1.0 / sigma[l];
         }
@@ -939,6 +975,39 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
     if ((st = guard(dev_alloc(p, &p->grid_work, p->K * L))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->grid_aux, p->K * L))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->grid_blk, p->K * L * B))) != FHS_OK) return st;
+    if (p->dr) {
+        // gridding (Sec. 3.4): diag(H_l) by one pass over the rows, Lambda_l, y'_l, M'_l
+        const size_t LK = (size_t)p->K * L;
+        if ((st = guard(dev_alloc(p, &p->dr_lam, LK, false))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &p->dr_y, LK, false))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &p->dr_v, LK))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &p->dr_u, LK))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &p->dr_w, LK))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &p->dr_norm2, L))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &p->dr_eps, L, false))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &p->dr_scale, L))) != FHS_OK) return st;
+        double *diag = nullptr;
+        unsigned long long *cnt = nullptr;
+        if ((st = guard(dev_alloc(p, &diag, LK))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &cnt, L))) != FHS_OK) return st;
+        std::vector<unsigned long long> hc(L);
+        cudaError_t e = launch_dr_diag(p, diag, s);
+        if (e == cudaSuccess) e = launch_grid(p, p->y, p->dr_u, s);
+        if (e == cudaSuccess) e = launch_dr_setup(p, diag, p->dr_u, cnt, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), cnt, sizeof(unsigned long long) * L, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return guard(fail(FHS_ERR_CUDA, "data reduction set-up failed: %s", cudaGetErrorString(e)));
+        dev_free(p, diag);
+        dev_free(p, cnt);
+        p->bytes -= sizeof(double) * LK + sizeof(unsigned long long) * L;
+        p->dr_m.assign(hc.begin(), hc.end());
+        std::vector<double> de(L);
+        for (int l = 0; l < L; ++l) {
+            const double m = double(p->dr_m[l]);
+            de[l] = eps_in ? eps_in[l] : (m > 0 ? std::sqrt(m + 2.0 * std::sqrt(m)) : 0.0);
+        }
+        if ((st = guard(upload(p->dr_eps, de.data(), L, s))) != FHS_OK) return st;
+    }
 
     // ---- image domain
     if ((st = guard(dev_alloc(p, &p->X, p->N * L))) != FHS_OK) return st;
@@ -1153,8 +1222,9 @@ fhs_status fhs_estimate_bytes(const fhs_params *params, const double *w, int64_t
     r += 16 * Q + 8 * C * Q + 4 * nuc + 12 * C * Q * Lc * Lc + 4 * C * Q * Lc + 4 * (q.ny + q.nx);
     r += 8 * C * Q * ne * ne;                                        // eigenvector warm starts
     r += (long long)cufft_workspace(2 * q.ny, 2 * q.nx, int(L));
+    if (q.data_reduction) r += 36 * K * L + 20 * L;                  // Lambda, y', v', u, w; norms, eps', scales
     const long long n_planes = q.w_max > 0.0 ? 2LL * (q.n_wplanes - 1) + 1 : 1;
-    const long long peak = r + 16 * M + 2 * M + 16 * n_planes * 2 * (2 * kMaxWHalf + 1) + 8 * nseg;
+    const long long peak = r + (q.data_reduction ? 8 * K * L : 0) + 16 * M + 2 * M + 16 * n_planes * 2 * (2 * kMaxWHalf + 1) + 8 * nseg;
     if (resident_out) *resident_out = r;
     if (peak_out) *peak_out = peak;
     return FHS_OK;
@@ -1225,6 +1295,9 @@ fhs_status fhs_get_info(const fhs_problem *p, fhs_info *info) {
     info->bin_split = p->bin_split;
     info->mu = p->prm.mu;
     info->mu_bar = p->prm.mu_bar;
+    long long nr = 0;
+    for (long long m : p->dr_m) nr += m;
+    info->n_red = nr;
     return FHS_OK;
 }
 
@@ -1247,6 +1320,23 @@ fhs_status fhs_adjoint(fhs_problem *p, const float *vis_dev, float *x_dev, void 
 fhs_status fhs_residual(fhs_problem *p, const float *x_dev, float *r_dev, void *stream) {
     if (!p || !r_dev) return fail(FHS_ERR_ARG, "NULL argument");
     cudaStream_t s = S(stream);
+    if (p->dr) {
+        // eta' Re Phi'^H (y' - Phi' x) = eta' Re Z^T F^H H Lambda (y' - Lambda H F Z x)
+        float2 *u = nullptr;
+        if (x_dev) {
+            CU(launch_zpad(p, x_dev, p->grid_in, s));
+            TRY(fft(p, p->grid_in, p->grid_aux, CUFFT_FORWARD, s));
+            CU(launch_normal(p, p->grid_aux, p->dr_u, s));
+            u = p->dr_u;
+        }
+        CU(launch_dr_combine(p, u, 1.f, -1.f, p->dr_w, s));
+        CU(cudaMemsetAsync(p->grid_aux, 0, sizeof(float2) * p->K * p->L, s));
+        CU(launch_normal(p, p->dr_w, p->grid_aux, s));
+        TRY(fft(p, p->grid_aux, p->grid_aux, CUFFT_INVERSE, s));
+        CU(launch_crop(p, p->grid_aux, r_dev, s));
+        CU(launch_chan_scale(p, r_dev, p->eta, s));
+        return FHS_OK;
+    }
     if (x_dev) {
         TRY(forward_from_image(p, x_dev, p->vis_tmp, s));
         CU(launch_vis_residual(p, p->vis_tmp, p->vis_tmp, s));
@@ -1255,6 +1345,54 @@ fhs_status fhs_residual(fhs_problem *p, const float *x_dev, float *r_dev, void *
     }
     TRY(adjoint_to_image(p, p->vis_tmp, r_dev, s));
     CU(launch_chan_scale(p, r_dev, p->eta, s));
+    return FHS_OK;
+}
+
+fhs_status fhs_noise_from_model(fhs_problem *p, const float *x0_dev, int32_t apply, double *sigma_out,
+                                double *eps_out, void *stream) {
+    if (!p || !x0_dev) return fail(FHS_ERR_ARG, "NULL argument");
+    cudaStream_t s = S(stream);
+    const int n = p->dr ? p->L : p->n_seg;
+    const size_t n_st = p->dr ? (size_t)p->L : 3 * (size_t)p->n_seg;
+    double *st = nullptr;
+    CU(cudaMallocAsync(reinterpret_cast<void **>(&st), sizeof(double) * n_st, s));
+    std::vector<double> h(n_st), sig(n), eps(n);
+    auto run = [&]() -> fhs_status {
+        CU(cudaMemsetAsync(st, 0, sizeof(double) * n_st, s));
+        if (p->dr) {
+            CU(launch_zpad(p, x0_dev, p->grid_in, s));
+            TRY(fft(p, p->grid_in, p->grid_aux, CUFFT_FORWARD, s));
+            CU(launch_normal(p, p->grid_aux, p->dr_u, s));
+            CU(launch_dr_resid_norm(p, st, s));
+        } else {
+            TRY(forward_from_image(p, x0_dev, p->vis_tmp, s));
+            CU(launch_seg_stats(p, p->vis_tmp, st, s));
+        }
+        CU(cudaMemcpyAsync(h.data(), st, sizeof(double) * n_st, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        return FHS_OK;
+    };
+    const fhs_status rs = run();
+    cudaFreeAsync(st, s);
+    if (rs != FHS_OK) return rs;
+    for (int i = 0; i < n; ++i) {
+        if (p->dr) {
+            eps[i] = std::sqrt(h[i]);
+            sig[i] = p->dr_m[i] > 0 ? eps[i] / std::sqrt(double(p->dr_m[i])) : 0.0;
+        } else {
+            const double m = double(p->seg_off[i + 1] - p->seg_off[i]);
+            const double sr = h[3 * i], si = h[3 * i + 1], s2 = h[3 * i + 2];
+            eps[i] = std::sqrt(s2);
+            const double var = m > 1 ? (s2 - (sr * sr + si * si) / m) / (m - 1) : 0.0;
+            sig[i] = p->sigma_l[i / p->B] * std::sqrt(std::max(var, 0.0));
+        }
+    }
+    if (sigma_out) std::copy(sig.begin(), sig.end(), sigma_out);
+    if (eps_out) std::copy(eps.begin(), eps.end(), eps_out);
+    if (apply) {
+        CU(cudaMemcpyAsync(p->dr ? p->dr_eps : p->eps, eps.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        CU(cudaStreamSynchronize(s));
+    }
     return FHS_OK;
 }
 
@@ -1323,7 +1461,7 @@ fhs_status fhs_state_size(const fhs_problem *p, int32_t part, int64_t *n) {
     if (!p || !n) return fail(FHS_ERR_ARG, "NULL argument");
     switch (part) {
         case FHS_STATE_IMAGE: *n = p->N * p->L; break;
-        case FHS_STATE_DUAL_DATA: *n = 2 * p->Mtot; break;
+        case FHS_STATE_DUAL_DATA: *n = p->dr ? 2 * p->K * p->L : 2 * p->Mtot; break;
         case FHS_STATE_DUAL_SARA: *n = p->sara.n_coef * p->L; break;
         case FHS_STATE_DUAL_NUCLEAR: *n = p->nuc_size; break;
         case FHS_STATE_WEIGHTS_SARA: *n = p->sara.n_coef * p->C; break;
@@ -1342,7 +1480,8 @@ fhs_status fhs_get_state(fhs_problem *p, int32_t part, float *dst, void *stream)
     switch (part) {
         case FHS_STATE_IMAGE: CU(cudaMemcpyAsync(dst, p->X, b, cudaMemcpyDeviceToDevice, s)); break;
         case FHS_STATE_DUAL_DATA:
-            CU(launch_permute_to_caller(p, p->dvis, reinterpret_cast<float2 *>(dst), p->blk_scale, s));
+            if (p->dr) CU(cudaMemcpyAsync(dst, p->dr_v, b, cudaMemcpyDeviceToDevice, s));
+            else CU(launch_permute_to_caller(p, p->dvis, reinterpret_cast<float2 *>(dst), p->blk_scale, s));
             break;
         case FHS_STATE_DUAL_SARA: CU(cudaMemcpyAsync(dst, p->W, b, cudaMemcpyDeviceToDevice, s)); break;
         case FHS_STATE_DUAL_NUCLEAR: CU(cudaMemcpyAsync(dst, p->P, b, cudaMemcpyDeviceToDevice, s)); break;
@@ -1361,6 +1500,16 @@ fhs_status fhs_set_state(fhs_problem *p, int32_t part, const float *src, void *s
     switch (part) {
         case FHS_STATE_IMAGE: CU(cudaMemcpyAsync(p->X, src, b, cudaMemcpyDeviceToDevice, s)); break;
         case FHS_STATE_DUAL_DATA: {
+            if (p->dr) {
+                // the reduced dual and its adjoint grid F^H H Lambda v (what the next primal step reads)
+                CU(cudaMemcpyAsync(p->dr_v, src, b, cudaMemcpyDeviceToDevice, s));
+                CU(launch_dr_weight(p, s));
+                CU(cudaMemsetAsync(p->grid_work, 0, sizeof(float2) * p->K * p->L, s));
+                CU(launch_normal(p, p->dr_w, p->grid_work, s));
+                TRY(fft(p, p->grid_work, p->grid_work, CUFFT_INVERSE, s));
+                CU(cudaStreamSynchronize(s));
+                break;
+            }
             CU(launch_permute_from_caller(p, reinterpret_cast<const float2 *>(src), p->dvis, s));
             std::vector<float> ones(p->n_seg, 1.0f);
             CU(cudaMemcpyAsync(p->blk_scale, ones.data(), sizeof(float) * p->n_seg, cudaMemcpyHostToDevice, s));

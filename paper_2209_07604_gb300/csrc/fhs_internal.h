@@ -75,6 +75,7 @@ struct fhs_problem {
     long long N = 0, K = 0;                   // pixels and grid cells per channel
     long long Mtot = 0, nnz = 0, n_fac = 0;   // nnz: entries of G (sum T^2); n_fac: stored factors (sum 2T)
     std::vector<long long> vis_off;           // [L+1]
+    std::vector<double> sigma_l;              // [L] whitening of each channel (Theta_l = 1 / sigma_l)
     std::vector<long long> seg_off;           // [L*B+1] sorted-order offsets of (l,b) segments
     int n_seg = 0;
 
@@ -106,6 +107,18 @@ struct fhs_problem {
     float2 *grid_work = nullptr;              // [L][K] FFT output / data adjoint grid
     float2 *grid_blk = nullptr;               // [L][B][K] per-block adjoint grids
     float2 *grid_aux = nullptr;               // [L][K] scratch for measure/adjoint
+
+    // data reduction (Sec. 3.4): grids [L][K], zero off the gridded cells
+    bool dr = false;
+    float *dr_lam = nullptr;                  // Lambda_l
+    float2 *dr_y = nullptr;                   // y'_l
+    float2 *dr_v = nullptr;                   // reduced data dual
+    float2 *dr_u = nullptr;                   // H Xhat (zero between uses)
+    float2 *dr_w = nullptr;                   // Lambda v, input of the adjoint pass
+    double *dr_norm2 = nullptr;               // [L]
+    double *dr_eps = nullptr;                 // [L] eps'_l
+    float *dr_scale = nullptr;                // [L]
+    std::vector<long long> dr_m;              // M'_l
 
     // image domain
     float *X = nullptr, *Xbar = nullptr, *A_sara = nullptr;
@@ -209,6 +222,15 @@ cudaError_t launch_nuclear_svals(fhs_problem *p, double *svals, cudaStream_t s);
 cudaError_t launch_l21_norm(fhs_problem *p, const float *A, double *out, cudaStream_t s);
 cudaError_t launch_vis_residual(fhs_problem *p, const float2 *phi, float2 *r, cudaStream_t s);
 cudaError_t launch_chan_scale(fhs_problem *p, float *x, const float *f, cudaStream_t s);
+// data reduction (k_reduce.cu)
+cudaError_t launch_dr_diag(fhs_problem *p, double *diag, cudaStream_t s);
+cudaError_t launch_dr_setup(fhs_problem *p, const double *diag, float2 *ghy, unsigned long long *cnt, cudaStream_t s);
+cudaError_t launch_dr_dual(fhs_problem *p, cudaStream_t s);
+cudaError_t launch_dr_finalize(fhs_problem *p, cudaStream_t s);
+cudaError_t launch_dr_weight(fhs_problem *p, cudaStream_t s);      // dr_w = Lambda dr_v
+cudaError_t launch_dr_resid_norm(fhs_problem *p, double *out, cudaStream_t s);   // out[l] += ||y' - Lambda dr_u||^2
+cudaError_t launch_seg_stats(fhs_problem *p, const float2 *phi, double *stats, cudaStream_t s);
+cudaError_t launch_dr_combine(fhs_problem *p, float2 *u, float a, float b, float2 *w, cudaStream_t s);
 cudaError_t launch_nuclear_apply(fhs_problem *p, cudaStream_t s);
 // Tensor-core Gram of the dual step (precision FHS_GRAM_TF32 or FHS_GRAM_BF16).
 cudaError_t launch_nuclear_gram_tc(fhs_problem *p, int precision, cudaStream_t s);

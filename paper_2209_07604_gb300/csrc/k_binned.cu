@@ -230,7 +230,7 @@ __device__ __forceinline__ void scatter_rows_rank(int i0, int nv, int lane, int 
 // sum_t1 g1[t1] sum_t2 g2[t2] X[c1+t1][c2+t2], with g2 of those columns in
 // registers (zero beyond T).
 template <int C0, int CW, bool DENSE>
-__device__ __forceinline__ void gather_cols(const float2 *__restrict__ f, int T, int c1, int c2,
+__device__ __forceinline__ void gather_cols(const float2 *__restrict__ f, int T, int t_lo, int t_hi, int c1, int c2,
                                             const float2 *s_grid, int wy0, int wx0,
                                             const float2 *__restrict__ gl, int K1, int K2, float &ar, float &ai) {
     float2 g2[CW];
@@ -244,7 +244,7 @@ __device__ __forceinline__ void gather_cols(const float2 *__restrict__ f, int T,
             k2[t] -= (k2[t] >= K2) ? K2 : 0;
         }
     }
-    for (int t1 = 0; t1 < T; ++t1) {
+    for (int t1 = t_lo; t1 < t_hi; ++t1) {
         const float2 a = __ldg(f + t1);
         float br = 0.f, bi = 0.f;
         if (DENSE) {
@@ -271,33 +271,39 @@ __device__ __forceinline__ void gather_cols(const float2 *__restrict__ f, int T,
     }
 }
 
-// Gather of one row by one lane: phi = sum_t1 g1[t1] sum_t2 g2[t2] X[c1+t1][c2+t2].
-// TT >= T is the warp's largest side rounded to a compiled size; each entry
-// costs one load of X and four FMAs with every lane busy and no reduction
-// across lanes.  Sides above 8 take two passes over the rows (8 columns of
-// g2 in registers at a time, under the 64-register cap).
+// Gather of one row by one lane: phi = sum_t1 g1[t1] sum_t2 g2[t2] X[c1+t1][c2+t2],
+// rows t1 in [t_lo, t_hi) (g1 is zero outside).  TT >= T is the warp's
+// largest side rounded to a compiled size; each entry costs one load of X and
+// four FMAs with every lane busy and no reduction across lanes.  Sides above 8
+// take two passes over the rows (8 columns of g2 in registers at a time, under
+// the 64-register cap).
 template <int TT, bool DENSE>
-__device__ __forceinline__ float2 gather_lane(const float2 *__restrict__ f, int T, int c1, int c2,
-                                              const float2 *s_grid, int wy0, int wx0,
+__device__ __forceinline__ float2 gather_lane(const float2 *__restrict__ f, int T, int t_lo, int t_hi, int c1,
+                                              int c2, const float2 *s_grid, int wy0, int wx0,
                                               const float2 *__restrict__ gl, int K1, int K2) {
     float ar = 0.f, ai = 0.f;
     if (TT <= 8) {
-        gather_cols<0, TT, DENSE>(f, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2, ar, ai);
+        gather_cols<0, TT, DENSE>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, gl, K1, K2, ar, ai);
     } else {
-        gather_cols<0, 8, DENSE>(f, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2, ar, ai);
-        gather_cols<8, (TT > 8 ? TT - 8 : 1), DENSE>(f, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2, ar, ai);
+        gather_cols<0, 8, DENSE>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, gl, K1, K2, ar, ai);
+        gather_cols<8, (TT > 8 ? TT - 8 : 1), DENSE>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, gl, K1, K2, ar,
+                                                     ai);
     }
     return make_float2(ar, ai);
 }
 
-// Gather of a row with R separable terms (term r at offset 2 T r).
+// Gather of a row with R separable terms (term r at offset 2 T r).  With
+// R > 1 (DDE rows) the first factor of term r is the base factor shifted by
+// r, nonzero only on rows [r, r + T - R + 1), so the other rows are skipped.
 template <int TT, bool DENSE>
 __device__ __forceinline__ float2 gather_terms(const float2 *__restrict__ f, int T, int R, int c1, int c2,
                                                const float2 *s_grid, int wy0, int wx0,
                                                const float2 *__restrict__ gl, int K1, int K2) {
-    float2 phi = gather_lane<TT, DENSE>(f, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
-    for (int r = 1; r < R; ++r) {
-        const float2 t = gather_lane<TT, DENSE>(f + r * 2 * T, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
+    if (R == 1) return gather_lane<TT, DENSE>(f, T, 0, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
+    const int Tb = T - R + 1;
+    float2 phi = make_float2(0.f, 0.f);
+    for (int r = 0; r < R; ++r) {
+        const float2 t = gather_lane<TT, DENSE>(f + r * 2 * T, T, r, r + Tb, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
         phi.x += t.x;
         phi.y += t.y;
     }

@@ -317,6 +317,44 @@ __global__ void vis_residual_kernel(const float2 *__restrict__ y, const float2 *
     }
 }
 
+// Residual statistics per (channel, block) segment of sorted visibilities:
+// stats[3 s] += sum Re r, stats[3 s + 1] += sum Im r, stats[3 s + 2] += sum |r|^2
+// with r = y - phi.  Each thread takes a contiguous run of kRun visibilities
+// and flushes its FP64 sums whenever the segment changes.
+constexpr int kRun = 64;
+__global__ void seg_stats_kernel(const float2 *__restrict__ y, const float2 *__restrict__ phi,
+                                 const long long *__restrict__ seg_off, int n_seg, long long M,
+                                 double *__restrict__ stats) {
+    const long long nrun = (M + kRun - 1) / kRun;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nrun;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long m0 = t * kRun, m1 = m0 + kRun < M ? m0 + kRun : M;
+        int sg = seg_of(seg_off, n_seg, m0);
+        double sr = 0.0, si = 0.0, s2 = 0.0;
+        for (long long m = m0; m < m1; ++m) {
+            while (m >= seg_off[sg + 1]) {
+                if (s2 != 0.0 || sr != 0.0 || si != 0.0) {
+                    atomicAdd(stats + 3 * sg, sr);
+                    atomicAdd(stats + 3 * sg + 1, si);
+                    atomicAdd(stats + 3 * sg + 2, s2);
+                }
+                sr = si = s2 = 0.0;
+                ++sg;
+            }
+            const float2 a = y[m], b = phi[m];
+            const double rr = double(a.x) - b.x, ri = double(a.y) - b.y;
+            sr += rr;
+            si += ri;
+            s2 += rr * rr + ri * ri;
+        }
+        if (s2 != 0.0 || sr != 0.0 || si != 0.0) {
+            atomicAdd(stats + 3 * sg, sr);
+            atomicAdd(stats + 3 * sg + 1, si);
+            atomicAdd(stats + 3 * sg + 2, s2);
+        }
+    }
+}
+
 // x_l *= f_l on every pixel of channel l (blockIdx.y = channel).
 __global__ void chan_scale_kernel(float *__restrict__ x, long long N, const float *__restrict__ f) {
     const int l = blockIdx.y;
@@ -411,6 +449,14 @@ cudaError_t launch_power_scale(fhs_problem *p, const float *y, float *x, const d
 cudaError_t launch_vis_residual(fhs_problem *p, const float2 *phi, float2 *r, cudaStream_t s) {
     if (p->Mtot == 0) return cudaSuccess;
     vis_residual_kernel<<<grid_for(p->Mtot, 256), 256, 0, s>>>(p->y, phi, r, p->Mtot);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seg_stats(fhs_problem *p, const float2 *phi, double *stats, cudaStream_t s) {
+    if (p->Mtot == 0) return cudaSuccess;
+    seg_stats_kernel<<<grid_for((p->Mtot + kRun - 1) / kRun, 256), 256, 0, s>>>(p->y, phi, p->d_seg_off, p->n_seg,
+                                                                               p->Mtot, stats);
     p->n_launch += 1;
     return cudaGetLastError();
 }

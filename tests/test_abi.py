@@ -58,7 +58,7 @@ def _args(L=2, M=10, B=2):
 
 @pytest.mark.parametrize("field,value", [("ny", 15), ("nx", 8), ("n_subcubes", 3), ("n_blocks", 0),
                                          ("facet_overlap", 1.0), ("wavelet_levels", 9), ("mu", float("nan")),
-                                         ("upsilon", 0.0), ("qy", 0)])
+                                         ("upsilon", 0.0), ("qy", 0), ("data_reduction", 2)])
 def test_invalid_params_rejected_without_device(lib, field, value):
     p = fhs.default_params(ny=32, nx=32, n_channels=2, n_subcubes=1, n_blocks=2, mu=0.1, mu_bar=0.1)
     setattr(p, field, value)
@@ -94,8 +94,8 @@ def test_params_struct_layout(lib):
     p = fhs.default_params()
     assert p.kb_taps == 7 and p.wavelet_levels == 4 and p.n_wplanes == 64 and p.power_iters == 100
     assert abs(p.upsilon - 1e-3) < 1e-18 and abs(p.power_tol - 1e-7) < 1e-20
-    assert p.gram_precision == fhs.GRAM_FP32
-    # 7 int32 + pad, double, 2 int32, double, int32 + pad, 9 doubles, int32 + pad, double, int32 + pad
+    assert p.gram_precision == fhs.GRAM_FP32 and p.data_reduction == 0
+    # 7 int32 + pad, double, 2 int32, double, int32 + pad, 9 doubles, int32 + pad, double, 2 int32
     assert C.sizeof(fhs.fhs_params) == 160
 
 
@@ -116,6 +116,11 @@ def test_estimate_bytes_counts_g_factors(lib):
     assert pk0 > r0 and pk1 > r1
     r2, _ = fhs.fhs_estimate_bytes(p, np.zeros(2 * M), 2 * M)
     assert r2 > r0
+    # data reduction keeps Lambda, y', the reduced dual and two work grids per channel
+    p.data_reduction = 1
+    r3, pk3 = fhs.fhs_estimate_bytes(p, np.zeros(M), M)
+    K, L = 4 * 64 * 64, 2
+    assert r3 - r0 == 36 * K * L + 20 * L and pk3 - pk0 == r3 - r0 + 8 * K * L
 
 
 def test_dde_rejections_without_device(lib):

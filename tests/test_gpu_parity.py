@@ -236,7 +236,7 @@ def test_default_regularisation(name):
 
 def test_relative_change_and_nonnegativity():
     P = synth.make_problem("tiny")
-    prob = fhs.Problem.from_synth(P, mu=0.02, mu_bar=0.3, sigma2=1e-3)
+    prob = fhs.Problem.from_synth(P, mu=0.02, mu_bar=0.3, sigma2=5e-6)
     prob.step(3)
     Xa = prob.image().cpu().numpy().astype(np.float64)
     r = prob.step(1, want_rel=True)
@@ -248,7 +248,7 @@ def test_relative_change_and_nonnegativity():
 
 def test_checkpoint_resume():
     P = synth.make_problem("mid_w")
-    prob = fhs.Problem.from_synth(P, mu=0.05, mu_bar=0.5, sigma2=1e-4)
+    prob = fhs.Problem.from_synth(P, mu=0.05, mu_bar=0.5, sigma2=1e-7)
     prob.step(4)
     prob.reweight()
     prob.step(2)
@@ -257,7 +257,7 @@ def test_checkpoint_resume():
     saved = {k: prob.get_state(k).clone() for k in parts}
     prob.step(5)
     Xa = prob.image().cpu().numpy()
-    other = fhs.Problem.from_synth(P, mu=0.05, mu_bar=0.5, sigma2=1e-4)
+    other = fhs.Problem.from_synth(P, mu=0.05, mu_bar=0.5, sigma2=1e-7)
     for k in parts:
         other.set_state(k, saved[k])
     other.step(5)
@@ -269,10 +269,10 @@ def test_checkpoint_resume():
 
 def test_solve_matches_step_schedule():
     P = synth.make_problem("tiny")
-    a = fhs.Problem.from_synth(P, mu=0.02, mu_bar=0.3, sigma2=1e-3)
+    a = fhs.Problem.from_synth(P, mu=0.02, mu_bar=0.3, sigma2=5e-6)
     n = a.solve(12, 0.0, n_reweight=1, check_every=4)
     assert n == 12
-    b = fhs.Problem.from_synth(P, mu=0.02, mu_bar=0.3, sigma2=1e-3)
+    b = fhs.Problem.from_synth(P, mu=0.02, mu_bar=0.3, sigma2=5e-6)
     b.step(6)
     b.reweight()
     b.step(6)
@@ -293,7 +293,7 @@ def test_empty_block_and_uneven_channels():
     vo = np.array([0, M, M + cut], dtype=np.int64)
     bo = np.array([[0, M // 2, M], [0, 0, cut]], dtype=np.int64)
     params = fhs.default_params(ny=P.ny, nx=P.nx, n_channels=2, n_subcubes=1, n_blocks=2, qy=P.qy, qx=P.qx,
-                                facet_overlap=P.overlap, mu=0.02, mu_bar=0.3, sigma2=1e-3)
+                                facet_overlap=P.overlap, mu=0.02, mu_bar=0.3, sigma2=5e-6)
     prob = fhs.Problem(params, omega, w, y, P.sigma, vo, bo)
     prob.step(6)
     X = prob.image().cpu().numpy()
@@ -301,7 +301,7 @@ def test_empty_block_and_uneven_channels():
     geom = onf.Geometry(P.ny, P.nx)
     from oracle import prox as oprox
     ref = opdfb.FHS(P.omega, P.w, P.y, P.sigma, P.block_offsets, P.ny, P.nx, 1, P.qy, P.qx, P.overlap,
-                    mu=0.02, mu_bar=0.3, steps=_steps_from(prob, 1e-3))
+                    mu=0.02, mu_bar=0.3, steps=_steps_from(prob, 5e-6))
     ref.op.G[1] = onf.build_G(P.omega[1, :cut], P.w[1, :cut], P.sigma[1], geom)
     ref.yw[1] = P.y[1, :cut] / P.sigma[1]
     ref.v[1] = np.zeros(cut, dtype=np.complex128)
@@ -338,13 +338,13 @@ def test_empty_channel():
     vo = np.array([0, M, M], dtype=np.int64)
     bo = np.array([[0, M // 2, M], [0, 0, 0]], dtype=np.int64)
     params = fhs.default_params(ny=P.ny, nx=P.nx, n_channels=2, n_subcubes=1, n_blocks=2, qy=P.qy, qx=P.qx,
-                                facet_overlap=P.overlap, mu=0.02, mu_bar=0.3, sigma2=1e-3)
+                                facet_overlap=P.overlap, mu=0.02, mu_bar=0.3, sigma2=5e-6)
     prob = fhs.Problem(params, omega, w, y, P.sigma, vo, bo)
     prob.step(6)
     X = prob.image().cpu().numpy()
     from oracle import prox as oprox
     ref = opdfb.FHS(P.omega, P.w, P.y, P.sigma, P.block_offsets, P.ny, P.nx, 1, P.qy, P.qx, P.overlap,
-                    mu=0.02, mu_bar=0.3, steps=_steps_from(prob, 1e-3))
+                    mu=0.02, mu_bar=0.3, steps=_steps_from(prob, 5e-6))
     geom = onf.Geometry(P.ny, P.nx)
     ref.op.G[1] = sp.csr_matrix((0, geom.K1 * geom.K2), dtype=np.complex128)
     ref.yw[1] = np.zeros(0, dtype=np.complex128)

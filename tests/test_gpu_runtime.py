@@ -41,8 +41,8 @@ def test_graph_replay_matches_plain_launches():
     P = synth.make_problem("mid_w")
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
-        a = fhs.Problem.from_synth(P, mu=0.05, mu_bar=0.5, sigma2=1e-4)
-        b = fhs.Problem.from_synth(P, mu=0.05, mu_bar=0.5, sigma2=1e-4)
+        a = fhs.Problem.from_synth(P, mu=0.05, mu_bar=0.5, sigma2=1e-7)
+        b = fhs.Problem.from_synth(P, mu=0.05, mu_bar=0.5, sigma2=1e-7)
         fhs.fhs_use_graphs(b.handle, False)
         n0a, n0b = fhs.fhs_kernel_launches(a.handle), fhs.fhs_kernel_launches(b.handle)
         a.step(7)

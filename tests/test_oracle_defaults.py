@@ -7,6 +7,7 @@ import numpy as np
 
 from oracle import defaults as od
 from oracle import nufft as nf
+from paper_2209_07604_gb300 import synth
 from oracle import prox, wavelets
 
 
@@ -52,3 +53,30 @@ def test_default_regularisation_closed_forms():
     assert abs(mu - 1.0 / l21) < 1e-12 / l21
     mu2, mu_bar2 = od.default_regularisation(2.0 * Xd, C, facets, sara)
     assert abs(mu2 - mu / 2) < 1e-12 * mu and abs(mu_bar2 - mu_bar / 2) < 1e-12 * mu_bar
+
+
+def test_noise_from_true_model_recovers_the_added_noise():
+    """Data made as Phi x_true + s n (whitened, n i.i.d. CN(0, 1)): the residual
+    of the true model is exactly s n, so the block bounds are ||s n_b|| and the
+    noise levels estimate sigma_l s (4 standard errors); the reduced bound is
+    ||Gamma_l (s n_l)|| (Sec. 3.3, 3.4, 5.1)."""
+    from oracle import reduction as ored
+    P = synth.make_problem("tiny")
+    geom = nf.Geometry(P.ny, P.nx)
+    op = nf.Operator(P.omega, P.w, P.sigma, geom)
+    x = np.clip(synth.random_image((P.L, P.ny, P.nx), 21), 0, None)
+    rng = np.random.default_rng(22)
+    s = 3.0
+    n = [(rng.standard_normal(P.M) + 1j * rng.standard_normal(P.M)) / np.sqrt(2.0) for _ in range(P.L)]
+    yw = [op.forward(x[l], l) + s * n[l] for l in range(P.L)]
+    sig, eps = od.noise_from_model(op, yw, P.sigma, P.block_offsets, x)
+    for l in range(P.L):
+        for b in range(P.B):
+            nb = n[l][P.block_offsets[l, b]:P.block_offsets[l, b + 1]]
+            assert abs(eps[l, b] - s * np.linalg.norm(nb)) < 1e-9 * eps[l, b]
+            assert abs(sig[l, b] / (P.sigma[l] * s) - 1.0) < 4.0 / (2.0 * np.sqrt(len(nb)))
+    red = ored.Reduced(op, yw)
+    _, epr = od.reduced_bounds(red, x)
+    for l in range(P.L):
+        ref = np.linalg.norm(red.gamma(s * n[l], l))
+        assert abs(epr[l] - ref) < 1e-9 * ref

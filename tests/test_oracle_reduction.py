@@ -81,6 +81,13 @@ def test_gridded_noise_norm_statistics():
     np.testing.assert_allclose(red.eps_default()[0] ** 2, red.m_red(0) + 2 * np.sqrt(red.m_red(0)))
 
 
+def test_norm_by_lanczos_matches_power_iteration():
+    P, op, yw, red = _setup()
+    a = red.norm2_eigsh(0)
+    b = red.norm2(0, n_iter=5000, tol=1e-13)
+    assert abs(a - b) < 1e-6 * a
+
+
 def test_noise_free_data_lies_in_the_reduced_model():
     P, op, _, _ = _setup()
     x = synth.random_image((P.L, P.ny, P.nx), 8)
