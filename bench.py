@@ -461,6 +461,78 @@ def run_serve(args):
         serial["images_per_hour"], "data": "synthetic"}))
 
 
+def run_batch(args):
+    """Batched uneven problems: N seeded problems with image sizes from {256^2, 512^2,
+    1024^2, 1536x1024}, L in {4, 8, 16}, M per channel log-uniform on [1e5, 2e6],
+    w-terms up to 2000 wavelengths (7-15 taps), facet grids 2x2 to 6x6 with 10-20 %
+    overlap.  All problems step together (one stream each, iterations submitted
+    round-robin, each a replayed CUDA graph) against the same problems stepped one
+    after another; the metric is problem-iterations and visibilities per second."""
+    import torch
+    import paper_2209_07604_gb300 as fhs
+    from paper_2209_07604_gb300 import synth
+    torch.cuda.set_device(0)
+    fhs.load_library()
+    rng = np.random.Generator(np.random.Philox(7604 + 100 * 4))
+    sizes = [(256, 256), (512, 512), (1024, 1024), (1536, 1024)]
+    specs = []
+    for k in range(args.batch_problems):
+        ny, nx = sizes[rng.integers(len(sizes))]
+        L = int(rng.choice([4, 8, 16]))
+        M = int(np.exp(rng.uniform(np.log(1e5), np.log(2e6))))
+        q = int(rng.integers(2, 7))
+        specs.append(dict(ny=ny, nx=nx, L=L, C=max(1, L // 8), M=M, B=2, qy=q, qx=q,
+                          overlap=float(rng.uniform(0.1, 0.2)), w_max=2000.0))
+    t0 = time.time()
+    probs, streams = [], []
+    n_vis = 0
+    for k, sp in enumerate(specs):
+        P = synth.make_problem("vla_1024", trial=100 + k, **sp)
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            probs.append(fhs.Problem.from_synth(P, mu=MU, mu_bar=MU_BAR, stream=st))
+        streams.append(st)
+        n_vis += P.L * P.M
+        del P
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    handles = [p.handle for p in probs]
+    fhs.fhs_pdfb_step_batch(handles, args.warmup, streams)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with ClockSampler(0) as clk:
+        ev[0].record()
+        for st in streams:                      # start after everything queued so far
+            torch.cuda.current_stream().wait_stream(st)
+        fhs.fhs_pdfb_step_batch(handles, args.steps, streams)
+        for st in streams:
+            torch.cuda.current_stream().wait_stream(st)
+        ev[1].record()
+        torch.cuda.synchronize()
+    batched_s = ev[0].elapsed_time(ev[1]) * 1e-3
+    serial_s = 0.0
+    for p, st in zip(probs, streams):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            e0.record(st)
+            p.step(args.steps)
+            e1.record(st)
+        st.synchronize()
+        serial_s += e0.elapsed_time(e1) * 1e-3
+    dev_bytes = sum(p.info.device_bytes for p in probs)
+    for p in probs:
+        p.close()
+    it = args.batch_problems * args.steps
+    print(json.dumps({
+        "mode": "batch", "metric": "batched uneven problems: problem-iterations/s and visibilities/s",
+        "unit": "problem-iter/s", "problems": args.batch_problems, "steps": args.steps, "warmup": args.warmup,
+        "value": it / batched_s, "vis_per_s": n_vis * args.steps / batched_s,
+        "one_at_a_time": {"value": it / serial_s, "vis_per_s": n_vis * args.steps / serial_s},
+        "speedup": serial_s / batched_s, "visibilities": n_vis, "device_bytes": dev_bytes,
+        "setup_seconds": setup_s, "clocks": clk.summary(),
+        "config": {"specs": specs}, "data": "synthetic"}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -478,7 +550,8 @@ def main():
                     help="fold seeded 5x5 DDE kernels into G (w halved to keep boxes within 16 taps)")
     ap.add_argument("--reduction", action="store_true",
                     help="visibility-gridding data reduction: Phi' = Lambda H F Z, one l2 ball per channel")
-    ap.add_argument("--mode", default="pdfb", choices=["pdfb", "serve"])
+    ap.add_argument("--mode", default="pdfb", choices=["pdfb", "serve", "batch"])
+    ap.add_argument("--batch-problems", type=int, default=24)
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=4.0)
     ap.add_argument("--serve-iters", type=int, default=200)
@@ -491,6 +564,8 @@ def main():
         run_reference(args)
     elif args.mode == "serve":
         run_serve(args)
+    elif args.mode == "batch":
+        run_batch(args)
     else:
         run_gpu(args)
 

@@ -188,6 +188,7 @@ __device__ __forceinline__ void scatter_rows_rank(int i0, int nv, int lane, int 
         float accr[8], acci[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) accr[k] = acci[k] = 0.f;
+#pragma unroll 1
         for (int r = 0; r < R; ++r) {
             const float2 fac = load_factors(fbin + s_off[i] + r * 2 * T, T, lane);
             const float g2x = __shfl_sync(FULL, fac.x, 16 + col), g2y = __shfl_sync(FULL, fac.y, 16 + col);
@@ -302,6 +303,7 @@ __device__ __forceinline__ float2 gather_terms(const float2 *__restrict__ f, int
     if (R == 1) return gather_lane<TT, DENSE>(f, T, 0, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
     const int Tb = T - R + 1;
     float2 phi = make_float2(0.f, 0.f);
+#pragma unroll 1
     for (int r = 0; r < R; ++r) {
         const float2 t = gather_lane<TT, DENSE>(f + r * 2 * T, T, r, r + Tb, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
         phi.x += t.x;
@@ -367,9 +369,10 @@ __device__ __forceinline__ void gather_phase(int nv, int R, const int2 *s_meta, 
 // per-channel output grids (indexed by channel instead of segment).  kNormal:
 // grid is the forward grid, grid_blk the per-channel output grids, dvis unused.
 // MULTI: rows of R > 1 separable terms (DDE rows); otherwise R is 1 and the
-// term loops compile away.
+// term loops compile away.  Multi-term rows keep 3 CTAs per SM (80 registers:
+// their term accumulators spill under the 64-register cap).
 template <int MODE, bool MULTI>
-__global__ void __launch_bounds__(256, FHS_FUSED_MIN_BLOCKS) degrid_grid_binned_kernel(
+__global__ void __launch_bounds__(256, MULTI ? 3 : FHS_FUSED_MIN_BLOCKS) degrid_grid_binned_kernel(
     const int2 *__restrict__ meta, const long long *__restrict__ fptr, const float2 *__restrict__ gfac,
     const float2 *__restrict__ y, float2 *__restrict__ dvis, const long long *__restrict__ bin_start,
     const int *__restrict__ bin_seg, const int *__restrict__ bin_tile, int ntx, int B,

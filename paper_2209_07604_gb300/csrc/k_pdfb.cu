@@ -22,43 +22,54 @@ __global__ void __launch_bounds__(256) primal_kernel(
     const int l = blockIdx.y;
     const int c = l % C, j = l / C;
     const long long N = (long long)ny * nx;
+    // channel bases once; row offsets hoisted out of the column loop
+    float *Xl = X + (long long)l * N, *Xbl = Xbar + (long long)l * N;
+    const float *Al = A_sara + (long long)l * N;
+    const float2 *gal = grid_adj + (long long)l * K;
+    float2 *gil = grid_in + (long long)l * K;
     // compensated FP32 per thread, FP64 across threads
     float num = 0.f, cnum = 0.f, den = 0.f, cden = 0.f;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-        const int i1 = int(p / nx), i2 = int(p - (long long)i1 * nx);
-        int k1 = i1 - ny / 2; k1 += (k1 < 0) ? K1 : 0;
-        int k2 = i2 - nx / 2; k2 += (k2 < 0) ? K2 : 0;
-        const long long gk = (long long)l * K + (long long)k1 * K2 + k2;
-        const float sc = s1[i1] * s2[i2];
-        float a = grid_adj[gk].x * sc;
-        const long long o = (long long)l * N + p;
-        if (use_sara) a += A_sara[o];
-        if (use_nuc) {
-            const int r0 = rf[i1], nr = rc[i1], c0 = cf[i2], ncol = cc[i2];
-            for (int ry = 0; ry < nr; ++ry)
-                for (int rx = 0; rx < ncol; ++rx) {
-                    const int q = (r0 + ry) * qx + (c0 + rx);
-                    const int4 f = facets[q];
-                    const long long wpx = (long long)(f.y - f.x) * (f.w - f.z);
-                    a += P[nuc_off[c * Q + q] + (long long)j * wpx + (long long)(i1 - f.x) * (f.w - f.z) + (i2 - f.z)];
-                }
-        }
-        const float x = X[o];
-        const float xp = fmaxf(0.f, fmaf(-tau, a, x));
-        const float xb = 2.f * xp - x;
-        X[o] = xp;
-        Xbar[o] = xb;
-        grid_in[gk] = make_float2(xb * sc, 0.f);
-        const float dx = xp - x;
-        {
-            const float yv = fmaf(dx, dx, -cnum), t = num + yv;
-            cnum = (t - num) - yv;
-            num = t;
-        }
-        {
-            const float yv = fmaf(xp, xp, -cden), t = den + yv;
-            cden = (t - den) - yv;
-            den = t;
+    // one image row per CTA step (row-uniform terms hoisted), columns over the threads
+    for (int i1 = blockIdx.x; i1 < ny; i1 += gridDim.x) {
+        int k1 = i1 - ny / 2;
+        k1 += (k1 < 0) ? K1 : 0;
+        const float s1r = s1[i1];
+        const int r0 = use_nuc ? rf[i1] : 0, nr = use_nuc ? rc[i1] : 0;
+        const long long grow = (long long)k1 * K2, irow = (long long)i1 * nx;
+        for (int i2 = threadIdx.x; i2 < nx; i2 += blockDim.x) {
+            int k2 = i2 - nx / 2;
+            k2 += (k2 < 0) ? K2 : 0;
+            const float sc = s1r * s2[i2];
+            float a = gal[grow + k2].x * sc;
+            const long long o = irow + i2;
+            if (use_sara) a += Al[o];
+            if (use_nuc) {
+                const int c0 = cf[i2], ncol = cc[i2];
+                for (int ry = 0; ry < nr; ++ry)
+                    for (int rx = 0; rx < ncol; ++rx) {
+                        const int q = (r0 + ry) * qx + (c0 + rx);
+                        const int4 f = facets[q];
+                        const int fw = f.w - f.z;
+                        a += P[nuc_off[c * Q + q] + (long long)j * ((f.y - f.x) * fw) + (i1 - f.x) * fw + (i2 - f.z)];
+                    }
+            }
+            const float x = Xl[o];
+            const float xp = fmaxf(0.f, fmaf(-tau, a, x));
+            const float xb = 2.f * xp - x;
+            Xl[o] = xp;
+            Xbl[o] = xb;
+            gil[grow + k2] = make_float2(xb * sc, 0.f);
+            const float dx = xp - x;
+            {
+                const float yv = fmaf(dx, dx, -cnum), t = num + yv;
+                cnum = (t - num) - yv;
+                num = t;
+            }
+            {
+                const float yv = fmaf(xp, xp, -cden), t = den + yv;
+                cden = (t - den) - yv;
+                den = t;
+            }
         }
     }
     double dn = double(num) - double(cnum), dd = double(den) - double(cden);
@@ -79,7 +90,7 @@ __global__ void __launch_bounds__(256) primal_kernel(
 }  // namespace
 
 cudaError_t launch_primal(fhs_problem *p, cudaStream_t s) {
-    long long g = (p->N + 255) / 256;
+    long long g = p->ny;                 // one row per CTA (rows of a channel are independent)
     if (g > 1024) g = 1024;
     const bool use_sara = p->prm.mu > 0.0;
     const bool use_nuc = p->prm.mu_bar > 0.0;

@@ -19,6 +19,11 @@ namespace {
 
 constexpr int kWarps = 8;
 
+// two complex cells as one float4, two Lambda values as one float2
+inline float4 *f4(float2 *p) { return reinterpret_cast<float4 *>(p); }
+inline const float4 *f4(const float2 *p) { return reinterpret_cast<const float4 *>(p); }
+inline const float2 *f2(const float *p) { return reinterpret_cast<const float2 *>(p); }
+
 __device__ __forceinline__ int chan_of(const long long *seg_off, int n_seg, int B, long long v) {
     int lo = 0, hi = n_seg - 1;
     while (lo < hi) {
@@ -85,34 +90,45 @@ __global__ void dr_setup_kernel(const double *__restrict__ diag, float2 *__restr
     if ((threadIdx.x & 31) == 0 && n) atomicAdd(cnt + l, n);
 }
 
-// Reduced dual pre-update: r = v + sigma2 Lambda (H Xhat) - sigma2 y' on the
-// gridded points (r replaces v), ||r||^2 per channel; the normal-pass output u
-// and the next pass's output grid `out` are zeroed on the way.
-__global__ void __launch_bounds__(256) dr_dual_kernel(float2 *__restrict__ u, float2 *__restrict__ out,
-                                                      float2 *__restrict__ v, const float2 *__restrict__ yred,
-                                                      const float *__restrict__ lam, float sigma2,
-                                                      double *__restrict__ norm2, long long K) {
+// The elementwise kernels below take two grid cells per thread and step
+// (float4 of complex values, float2 of Lambda; K is even, so every channel's
+// grid starts 16-byte aligned) and read every operand unconditionally: off
+// the gridded points v', y' and Lambda are zero, so the formulas give zero
+// there without a branch, and all loads of a step are independent.
+
+// Reduced dual pre-update: r = v + sigma2 Lambda (H Xhat) - sigma2 y' (r
+// replaces v), ||r||^2 per channel; the normal-pass output u and the next
+// pass's output grid `out` are zeroed on the way.
+__global__ void __launch_bounds__(256) dr_dual_kernel(float4 *__restrict__ u, float4 *__restrict__ out,
+                                                      float4 *__restrict__ v, const float4 *__restrict__ yred,
+                                                      const float2 *__restrict__ lam, float sigma2,
+                                                      double *__restrict__ norm2, long long K2h) {
     __shared__ double s_red[8];
     const int l = blockIdx.y;
-    const long long base = (long long)l * K;
-    double acc = 0.0;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < K; k += (long long)gridDim.x * blockDim.x) {
+    const long long base = (long long)l * K2h;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float acc = 0.f, cmp = 0.f;                     // compensated FP32 per thread, FP64 across threads
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < K2h; k += (long long)gridDim.x * blockDim.x) {
         const long long i = base + k;
-        const float2 uu = u[i];
-        u[i] = make_float2(0.f, 0.f);
-        out[i] = make_float2(0.f, 0.f);
-        const float lk = lam[i];
-        if (lk > 0.f) {
-            const float2 vv = v[i], yy = yred[i];
-            const float sl = sigma2 * lk;
-            const float rr = fmaf(sl, uu.x, fmaf(-sigma2, yy.x, vv.x));
-            const float ri = fmaf(sl, uu.y, fmaf(-sigma2, yy.y, vv.y));
-            v[i] = make_float2(rr, ri);
-            acc += double(fmaf(rr, rr, ri * ri));
-        }
+        const float4 uu = u[i], vv = v[i], yy = yred[i];
+        const float2 lk = lam[i];
+        u[i] = z4;
+        out[i] = z4;
+        const float sa = sigma2 * lk.x, sb = sigma2 * lk.y;
+        float4 r;
+        r.x = fmaf(sa, uu.x, fmaf(-sigma2, yy.x, vv.x));
+        r.y = fmaf(sa, uu.y, fmaf(-sigma2, yy.y, vv.y));
+        r.z = fmaf(sb, uu.z, fmaf(-sigma2, yy.z, vv.z));
+        r.w = fmaf(sb, uu.w, fmaf(-sigma2, yy.w, vv.w));
+        v[i] = r;
+        const float q = fmaf(r.x, r.x, fmaf(r.y, r.y, fmaf(r.z, r.z, r.w * r.w)));
+        const float yv = q - cmp, t = acc + yv;
+        cmp = (t - acc) - yv;
+        acc = t;
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+    double d = double(acc) - double(cmp);
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = d;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
@@ -132,68 +148,60 @@ __global__ void dr_scale_kernel(double *norm2, const double *eps, float *scale, 
 }
 
 // v = scale_l r; w = Lambda v (the input of the adjoint pass); scale NULL: 1.
-__global__ void __launch_bounds__(256) dr_apply_kernel(float2 *__restrict__ v, const float *__restrict__ lam,
-                                                       const float *__restrict__ scale, float2 *__restrict__ w,
-                                                       long long K) {
+__global__ void __launch_bounds__(256) dr_apply_kernel(float4 *__restrict__ v, const float2 *__restrict__ lam,
+                                                       const float *__restrict__ scale, float4 *__restrict__ w,
+                                                       long long K2h) {
     const int l = blockIdx.y;
-    const long long base = (long long)l * K;
+    const long long base = (long long)l * K2h;
     const float sc = scale ? scale[l] : 1.f;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < K; k += (long long)gridDim.x * blockDim.x) {
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < K2h; k += (long long)gridDim.x * blockDim.x) {
         const long long i = base + k;
-        const float lk = lam[i];
-        float2 vv = make_float2(0.f, 0.f);
-        if (lk > 0.f) {
-            vv = v[i];
-            vv.x *= sc;
-            vv.y *= sc;
-            v[i] = vv;
-        }
-        w[i] = make_float2(lk * vv.x, lk * vv.y);
+        float4 vv = v[i];
+        const float2 lk = lam[i];
+        vv.x *= sc;
+        vv.y *= sc;
+        vv.z *= sc;
+        vv.w *= sc;
+        if (scale) v[i] = vv;
+        w[i] = make_float4(lk.x * vv.x, lk.x * vv.y, lk.y * vv.z, lk.y * vv.w);
     }
 }
 
 // w = Lambda (a y' + b Lambda u) (u may be NULL; zeroed after it is read).
-__global__ void __launch_bounds__(256) dr_combine_kernel(float2 *__restrict__ u, const float2 *__restrict__ yred,
-                                                         const float *__restrict__ lam, float a, float b,
-                                                         float2 *__restrict__ w, long long K) {
+__global__ void __launch_bounds__(256) dr_combine_kernel(float4 *__restrict__ u, const float4 *__restrict__ yred,
+                                                         const float2 *__restrict__ lam, float a, float b,
+                                                         float4 *__restrict__ w, long long K2h) {
     const int l = blockIdx.y;
-    const long long base = (long long)l * K;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < K; k += (long long)gridDim.x * blockDim.x) {
+    const long long base = (long long)l * K2h;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < K2h; k += (long long)gridDim.x * blockDim.x) {
         const long long i = base + k;
-        const float lk = lam[i];
-        float2 uu = make_float2(0.f, 0.f);
-        if (u) {
-            uu = u[i];
-            u[i] = make_float2(0.f, 0.f);
-        }
-        float2 r = make_float2(0.f, 0.f);
-        if (lk > 0.f) {
-            const float2 yy = a != 0.f ? yred[i] : make_float2(0.f, 0.f);
-            r.x = lk * fmaf(a, yy.x, b * lk * uu.x);
-            r.y = lk * fmaf(a, yy.y, b * lk * uu.y);
-        }
-        w[i] = r;
+        const float2 lk = lam[i];
+        const float4 uu = u ? u[i] : z4;
+        const float4 yy = a != 0.f ? yred[i] : z4;
+        if (u) u[i] = z4;
+        const float ba = b * lk.x, bb = b * lk.y;
+        w[i] = make_float4(lk.x * fmaf(a, yy.x, ba * uu.x), lk.x * fmaf(a, yy.y, ba * uu.y),
+                           lk.y * fmaf(a, yy.z, bb * uu.z), lk.y * fmaf(a, yy.w, bb * uu.w));
     }
 }
 
 // out[l] += sum |y' - Lambda u|^2 over the gridded points (u zeroed after it is read).
-__global__ void __launch_bounds__(256) dr_resid_norm_kernel(float2 *__restrict__ u, const float2 *__restrict__ yred,
-                                                            const float *__restrict__ lam, double *__restrict__ out,
-                                                            long long K) {
+__global__ void __launch_bounds__(256) dr_resid_norm_kernel(float4 *__restrict__ u, const float4 *__restrict__ yred,
+                                                            const float2 *__restrict__ lam, double *__restrict__ out,
+                                                            long long K2h) {
     __shared__ double s_red[8];
     const int l = blockIdx.y;
-    const long long base = (long long)l * K;
+    const long long base = (long long)l * K2h;
     double acc = 0.0;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < K; k += (long long)gridDim.x * blockDim.x) {
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < K2h; k += (long long)gridDim.x * blockDim.x) {
         const long long i = base + k;
-        const float2 uu = u[i];
-        u[i] = make_float2(0.f, 0.f);
-        const float lk = lam[i];
-        if (lk > 0.f) {
-            const float2 yy = yred[i];
-            const double rr = double(yy.x) - double(lk) * uu.x, ri = double(yy.y) - double(lk) * uu.y;
-            acc += rr * rr + ri * ri;
-        }
+        const float4 uu = u[i], yy = yred[i];
+        const float2 lk = lam[i];
+        u[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const double r0 = double(yy.x) - double(lk.x) * uu.x, r1 = double(yy.y) - double(lk.x) * uu.y;
+        const double r2 = double(yy.z) - double(lk.y) * uu.z, r3 = double(yy.w) - double(lk.y) * uu.w;
+        acc += r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3;
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
@@ -205,12 +213,25 @@ __global__ void __launch_bounds__(256) dr_resid_norm_kernel(float2 *__restrict__
     }
 }
 
-dim3 grid_cells(const fhs_problem *p) {
-    long long g = (p->K + 255) / 256;
-    const long long cap = 152LL * 8 / (p->L > 0 ? p->L : 1) + 1;
-    if (g > cap) g = cap;
+// Grid of the elementwise kernels: CTAs per channel for `n` items per
+// channel, capped at whole waves (as many CTAs as the SMs hold at once for
+// this kernel, split evenly over the channels; a partial extra wave would
+// double the time of a bandwidth-bound pass).
+template <typename Kern>
+dim3 grid_cells(const fhs_problem *p, Kern kern, long long n) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        sms = 152;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0) != cudaSuccess || occ < 1) occ = 1;
+    const int L = p->L > 0 ? p->L : 1;
+    long long per = (long long)sms * occ / L;
+    if (per < 1) per = 1;
+    long long g = (n + 255) / 256;
+    if (g > per) g = per;
     if (g < 1) g = 1;
-    return dim3(unsigned(g), unsigned(p->L));
+    return dim3(unsigned(g), unsigned(L));
 }
 
 }  // namespace
@@ -227,39 +248,43 @@ cudaError_t launch_dr_diag(fhs_problem *p, double *diag, cudaStream_t s) {
 
 cudaError_t launch_dr_setup(fhs_problem *p, const double *diag, float2 *ghy, unsigned long long *cnt,
                             cudaStream_t s) {
-    dr_setup_kernel<<<grid_cells(p), 256, 0, s>>>(diag, ghy, p->dr_lam, p->dr_y, cnt, p->K);
+    dr_setup_kernel<<<grid_cells(p, dr_setup_kernel, p->K), 256, 0, s>>>(diag, ghy, p->dr_lam, p->dr_y, cnt, p->K);
     p->n_launch += 1;
     return cudaGetLastError();
 }
 
 cudaError_t launch_dr_dual(fhs_problem *p, cudaStream_t s) {
-    dr_dual_kernel<<<grid_cells(p), 256, 0, s>>>(p->dr_u, p->grid_work, p->dr_v, p->dr_y, p->dr_lam,
-                                                float(p->sigma2), p->dr_norm2, p->K);
+    dr_dual_kernel<<<grid_cells(p, dr_dual_kernel, p->K / 2), 256, 0, s>>>(
+        f4(p->dr_u), f4(p->grid_work), f4(p->dr_v), f4(p->dr_y), f2(p->dr_lam), float(p->sigma2), p->dr_norm2, p->K / 2);
     p->n_launch += 1;
     return cudaGetLastError();
 }
 
 cudaError_t launch_dr_finalize(fhs_problem *p, cudaStream_t s) {
     dr_scale_kernel<<<(p->L + 127) / 128, 128, 0, s>>>(p->dr_norm2, p->dr_eps, p->dr_scale, p->L, p->sigma2);
-    dr_apply_kernel<<<grid_cells(p), 256, 0, s>>>(p->dr_v, p->dr_lam, p->dr_scale, p->dr_w, p->K);
+    dr_apply_kernel<<<grid_cells(p, dr_apply_kernel, p->K / 2), 256, 0, s>>>(f4(p->dr_v), f2(p->dr_lam), p->dr_scale,
+                                                                          f4(p->dr_w), p->K / 2);
     p->n_launch += 2;
     return cudaGetLastError();
 }
 
 cudaError_t launch_dr_weight(fhs_problem *p, cudaStream_t s) {
-    dr_apply_kernel<<<grid_cells(p), 256, 0, s>>>(p->dr_v, p->dr_lam, nullptr, p->dr_w, p->K);
+    dr_apply_kernel<<<grid_cells(p, dr_apply_kernel, p->K / 2), 256, 0, s>>>(f4(p->dr_v), f2(p->dr_lam), nullptr,
+                                                                          f4(p->dr_w), p->K / 2);
     p->n_launch += 1;
     return cudaGetLastError();
 }
 
 cudaError_t launch_dr_resid_norm(fhs_problem *p, double *out, cudaStream_t s) {
-    dr_resid_norm_kernel<<<grid_cells(p), 256, 0, s>>>(p->dr_u, p->dr_y, p->dr_lam, out, p->K);
+    dr_resid_norm_kernel<<<grid_cells(p, dr_resid_norm_kernel, p->K / 2), 256, 0, s>>>(f4(p->dr_u), f4(p->dr_y),
+                                                                                    f2(p->dr_lam), out, p->K / 2);
     p->n_launch += 1;
     return cudaGetLastError();
 }
 
 cudaError_t launch_dr_combine(fhs_problem *p, float2 *u, float a, float b, float2 *w, cudaStream_t s) {
-    dr_combine_kernel<<<grid_cells(p), 256, 0, s>>>(u, p->dr_y, p->dr_lam, a, b, w, p->K);
+    dr_combine_kernel<<<grid_cells(p, dr_combine_kernel, p->K / 2), 256, 0, s>>>(f4(u), f4(p->dr_y), f2(p->dr_lam), a, b,
+                                                                              f4(w), p->K / 2);
     p->n_launch += 1;
     return cudaGetLastError();
 }
