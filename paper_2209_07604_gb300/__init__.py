@@ -136,10 +136,11 @@ def _check(status: int):
 
 
 def _stream(stream):
-    """cudaStream_t handle: the given one, else torch's current stream (NULL, the
-    legacy default stream, when torch sees no CUDA device)."""
+    """cudaStream_t handle: the given one (an integer handle or a torch stream),
+    else torch's current stream (NULL, the legacy default stream, when torch
+    sees no CUDA device)."""
     if stream is not None:
-        return C.c_void_p(int(stream))
+        return C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
     import torch
     if not torch.cuda.is_available():
         return C.c_void_p(0)

@@ -800,6 +800,19 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
             for (long long i = a; i < b; ++i) cnt[key[i] + 1]++;
             for (int k = 0; k < nkeys; ++k) cnt[k + 1] += cnt[k];
             for (long long i = a; i < b; ++i) perm[a + cnt[key[i]]++] = i;
+            // inside each (tile, T) run: by box corner, row-major within the tile, so that
+            // the rows one warp gathers at once read nearby window cells
+            for (long long r0 = a; r0 < b;) {
+                long long r1 = r0 + 1;
+                while (r1 < b && key[perm[r1]] == key[perm[r0]]) ++r1;
+                if (r1 - r0 > 1)
+                    std::sort(perm.begin() + r0, perm.begin() + r1, [&](long long u, long long v) {
+                        const int pu = (corner1[u] % kTile) * kTile + corner2[u] % kTile;
+                        const int pv = (corner1[v] % kTile) * kTile + corner2[v] % kTile;
+                        return pu != pv ? pu < pv : u < v;
+                    });
+                r0 = r1;
+            }
         }
     }, 1);
     std::vector<int2> meta(Mtot);

@@ -97,8 +97,10 @@ __global__ void dr_setup_kernel(const double *__restrict__ diag, float2 *__restr
 // there without a branch, and all loads of a step are independent.
 
 // Reduced dual pre-update: r = v + sigma2 Lambda (H Xhat) - sigma2 y' (r
-// replaces v), ||r||^2 per channel; the normal-pass output u and the next
-// pass's output grid `out` are zeroed on the way.
+// replaces v), ||r||^2 per channel; the next pass's output grid `out` is
+// zeroed on the way.  u (the normal-pass output) is zeroed by dr_apply_kernel:
+// a store that does not wait for the load of the same line stalls the
+// load/store queue behind that line's miss.
 __global__ void __launch_bounds__(256) dr_dual_kernel(float4 *__restrict__ u, float4 *__restrict__ out,
                                                       float4 *__restrict__ v, const float4 *__restrict__ yred,
                                                       const float2 *__restrict__ lam, float sigma2,
@@ -112,7 +114,6 @@ __global__ void __launch_bounds__(256) dr_dual_kernel(float4 *__restrict__ u, fl
         const long long i = base + k;
         const float4 uu = u[i], vv = v[i], yy = yred[i];
         const float2 lk = lam[i];
-        u[i] = z4;
         out[i] = z4;
         const float sa = sigma2 * lk.x, sb = sigma2 * lk.y;
         float4 r;
@@ -148,9 +149,10 @@ __global__ void dr_scale_kernel(double *norm2, const double *eps, float *scale, 
 }
 
 // v = scale_l r; w = Lambda v (the input of the adjoint pass); scale NULL: 1.
+// u (may be NULL) is zeroed.
 __global__ void __launch_bounds__(256) dr_apply_kernel(float4 *__restrict__ v, const float2 *__restrict__ lam,
                                                        const float *__restrict__ scale, float4 *__restrict__ w,
-                                                       long long K2h) {
+                                                       float4 *__restrict__ u, long long K2h) {
     const int l = blockIdx.y;
     const long long base = (long long)l * K2h;
     const float sc = scale ? scale[l] : 1.f;
@@ -164,10 +166,11 @@ __global__ void __launch_bounds__(256) dr_apply_kernel(float4 *__restrict__ v, c
         vv.w *= sc;
         if (scale) v[i] = vv;
         w[i] = make_float4(lk.x * vv.x, lk.x * vv.y, lk.y * vv.z, lk.y * vv.w);
+        if (u) u[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
-// w = Lambda (a y' + b Lambda u) (u may be NULL; zeroed after it is read).
+// w = Lambda (a y' + b Lambda u) (u may be NULL).
 __global__ void __launch_bounds__(256) dr_combine_kernel(float4 *__restrict__ u, const float4 *__restrict__ yred,
                                                          const float2 *__restrict__ lam, float a, float b,
                                                          float4 *__restrict__ w, long long K2h) {
@@ -179,14 +182,13 @@ __global__ void __launch_bounds__(256) dr_combine_kernel(float4 *__restrict__ u,
         const float2 lk = lam[i];
         const float4 uu = u ? u[i] : z4;
         const float4 yy = a != 0.f ? yred[i] : z4;
-        if (u) u[i] = z4;
         const float ba = b * lk.x, bb = b * lk.y;
         w[i] = make_float4(lk.x * fmaf(a, yy.x, ba * uu.x), lk.x * fmaf(a, yy.y, ba * uu.y),
                            lk.y * fmaf(a, yy.z, bb * uu.z), lk.y * fmaf(a, yy.w, bb * uu.w));
     }
 }
 
-// out[l] += sum |y' - Lambda u|^2 over the gridded points (u zeroed after it is read).
+// out[l] += sum |y' - Lambda u|^2 over the gridded points.
 __global__ void __launch_bounds__(256) dr_resid_norm_kernel(float4 *__restrict__ u, const float4 *__restrict__ yred,
                                                             const float2 *__restrict__ lam, double *__restrict__ out,
                                                             long long K2h) {
@@ -198,7 +200,6 @@ __global__ void __launch_bounds__(256) dr_resid_norm_kernel(float4 *__restrict__
         const long long i = base + k;
         const float4 uu = u[i], yy = yred[i];
         const float2 lk = lam[i];
-        u[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         const double r0 = double(yy.x) - double(lk.x) * uu.x, r1 = double(yy.y) - double(lk.x) * uu.y;
         const double r2 = double(yy.z) - double(lk.y) * uu.z, r3 = double(yy.w) - double(lk.y) * uu.w;
         acc += r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3;
@@ -263,30 +264,37 @@ cudaError_t launch_dr_dual(fhs_problem *p, cudaStream_t s) {
 cudaError_t launch_dr_finalize(fhs_problem *p, cudaStream_t s) {
     dr_scale_kernel<<<(p->L + 127) / 128, 128, 0, s>>>(p->dr_norm2, p->dr_eps, p->dr_scale, p->L, p->sigma2);
     dr_apply_kernel<<<grid_cells(p, dr_apply_kernel, p->K / 2), 256, 0, s>>>(f4(p->dr_v), f2(p->dr_lam), p->dr_scale,
-                                                                          f4(p->dr_w), p->K / 2);
+                                                                          f4(p->dr_w), f4(p->dr_u), p->K / 2);
     p->n_launch += 2;
     return cudaGetLastError();
 }
 
 cudaError_t launch_dr_weight(fhs_problem *p, cudaStream_t s) {
     dr_apply_kernel<<<grid_cells(p, dr_apply_kernel, p->K / 2), 256, 0, s>>>(f4(p->dr_v), f2(p->dr_lam), nullptr,
-                                                                          f4(p->dr_w), p->K / 2);
+                                                                          f4(p->dr_w), nullptr, p->K / 2);
     p->n_launch += 1;
     return cudaGetLastError();
 }
 
+// The two launchers below zero u (when given) after the kernel with a memset:
+// zeroing it inside the kernel, right after loading it, stalls the load/store
+// queue (see dr_dual_kernel).
 cudaError_t launch_dr_resid_norm(fhs_problem *p, double *out, cudaStream_t s) {
     dr_resid_norm_kernel<<<grid_cells(p, dr_resid_norm_kernel, p->K / 2), 256, 0, s>>>(f4(p->dr_u), f4(p->dr_y),
                                                                                     f2(p->dr_lam), out, p->K / 2);
     p->n_launch += 1;
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->dr_u, 0, sizeof(float2) * p->K * p->L, s);
+    return e;
 }
 
 cudaError_t launch_dr_combine(fhs_problem *p, float2 *u, float a, float b, float2 *w, cudaStream_t s) {
     dr_combine_kernel<<<grid_cells(p, dr_combine_kernel, p->K / 2), 256, 0, s>>>(f4(u), f4(p->dr_y), f2(p->dr_lam), a, b,
                                                                               f4(w), p->K / 2);
     p->n_launch += 1;
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && u) e = cudaMemsetAsync(u, 0, sizeof(float2) * p->K * p->L, s);
+    return e;
 }
 
 }  // namespace fhs

@@ -28,6 +28,13 @@ constexpr int SB_X = (STX + kMaxF - 2) / 2;         // staged band cols
 // with compile-time filter length F = 2P, writing the four subbands at level
 // j (details to coef, LL to `ll_out`, row stride mx).  The staged input row r
 // holds image row 2 k0y + 2 - kMaxF + r, so output k uses rows 2k+kMaxF-1-i.
+//
+// Register blocking: a thread of the x-filter computes kAnaNX adjacent outputs
+// of one row from 2 (kAnaNX - 1) + F staged inputs held in registers (instead
+// of F loads per output), and the warp's threads take consecutive rows (odd
+// row stride: no bank conflicts); a thread of the y-filter computes kAnaNY
+// outputs of one column the same way.
+constexpr int kAnaNX = 4, kAnaNY = 2;
 template <int P>
 __device__ __forceinline__ void analysis_tile_t(const SaraConst &c, int j, int k0y, int k0x,
                                                 float (*sin_)[AIN_X + 1], float (*slo)[ATX + 1],
@@ -35,6 +42,8 @@ __device__ __forceinline__ void analysis_tile_t(const SaraConst &c, int j, int k
                                                 float ll_scale) {
     constexpr int F = 2 * P;
     constexpr int R0 = kMaxF - F;                    // first staged row this filter reaches
+    constexpr int NR = AIN_Y - R0;                   // staged rows the y-filter reads
+    constexpr int WX = 2 * (kAnaNX - 1) + F, WY = 2 * (kAnaNY - 1) + F;
     float h[F], g[F];
 #pragma unroll
     for (int i = 0; i < F; ++i) {
@@ -42,40 +51,55 @@ __device__ __forceinline__ void analysis_tile_t(const SaraConst &c, int j, int k
         g[i] = c.g[P][i];
     }
     const int my = c.ny[P][j], mx = c.nx[P][j];
-    for (int idx = threadIdx.x; idx < (AIN_Y - R0) * ATX; idx += blockDim.x) {
-        const int r = R0 + idx / ATX, kx = idx % ATX;
-        const float *src = &sin_[r][2 * kx + R0];      // src[F-1-i] = input 2kx+kMaxF-1-i
-        float lo = 0.f, hi = 0.f;
+    for (int idx = threadIdx.x; idx < NR * (ATX / kAnaNX); idx += blockDim.x) {
+        const int r = R0 + idx % NR, kx0 = (idx / NR) * kAnaNX;
+        const float *src = &sin_[r][2 * kx0 + R0];     // src[2n+F-1-i] = input of output kx0+n, tap i
+        float a[WX];
 #pragma unroll
-        for (int i = 0; i < F; ++i) {
-            const float a = src[F - 1 - i];
-            lo = fmaf(h[i], a, lo);
-            hi = fmaf(g[i], a, hi);
+        for (int t = 0; t < WX; ++t) a[t] = src[t];
+#pragma unroll
+        for (int n = 0; n < kAnaNX; ++n) {
+            float lo = 0.f, hi = 0.f;
+#pragma unroll
+            for (int i = 0; i < F; ++i) {
+                lo = fmaf(h[i], a[2 * n + F - 1 - i], lo);
+                hi = fmaf(g[i], a[2 * n + F - 1 - i], hi);
+            }
+            slo[r][kx0 + n] = lo;
+            shi[r][kx0 + n] = hi;
         }
-        slo[r][kx] = lo;
-        shi[r][kx] = hi;
     }
     __syncthreads();
     const long long bs = (long long)my * mx;
-    for (int idx = threadIdx.x; idx < ATY * ATX; idx += blockDim.x) {
-        const int ky = idx / ATX, kx = idx % ATX;
-        const int gy = k0y + ky, gx = k0x + kx;
-        const int r1 = 2 * ky + R0;                    // row of tap i = F-1
-        float ll = 0.f, lh = 0.f, hl = 0.f, hh = 0.f;
+    for (int idx = threadIdx.x; idx < (ATY / kAnaNY) * ATX; idx += blockDim.x) {
+        const int kx = idx % ATX, ky0 = (idx / ATX) * kAnaNY;
+        const int r1 = 2 * ky0 + R0;                   // row of tap i = F-1 of output ky0
+        float lo[WY], hi[WY];
 #pragma unroll
-        for (int i = 0; i < F; ++i) {
-            const float lo = slo[r1 + F - 1 - i][kx], hi = shi[r1 + F - 1 - i][kx];
-            ll = fmaf(h[i], lo, ll);
-            lh = fmaf(h[i], hi, lh);
-            hl = fmaf(g[i], lo, hl);
-            hh = fmaf(g[i], hi, hh);
+        for (int t = 0; t < WY; ++t) {
+            lo[t] = slo[r1 + t][kx];
+            hi[t] = shi[r1 + t][kx];
         }
-        if (gy < my && gx < mx) {
-            float *d = coef_l + c.off_det[P][j] + (long long)gy * mx + gx;
-            d[0] = lh * kSaraScale;
-            d[bs] = hl * kSaraScale;
-            d[2 * bs] = hh * kSaraScale;
-            ll_out[(long long)gy * mx + gx] = ll * ll_scale;
+        const int gx = k0x + kx;
+#pragma unroll
+        for (int m = 0; m < kAnaNY; ++m) {
+            float ll = 0.f, lh = 0.f, hl = 0.f, hh = 0.f;
+#pragma unroll
+            for (int i = 0; i < F; ++i) {
+                const float vl = lo[2 * m + F - 1 - i], vh = hi[2 * m + F - 1 - i];
+                ll = fmaf(h[i], vl, ll);
+                lh = fmaf(h[i], vh, lh);
+                hl = fmaf(g[i], vl, hl);
+                hh = fmaf(g[i], vh, hh);
+            }
+            const int gy = k0y + ky0 + m;
+            if (gy < my && gx < mx) {
+                float *d = coef_l + c.off_det[P][j] + (long long)gy * mx + gx;
+                d[0] = lh * kSaraScale;
+                d[bs] = hl * kSaraScale;
+                d[2 * bs] = hh * kSaraScale;
+                ll_out[(long long)gy * mx + gx] = ll * ll_scale;
+            }
         }
     }
     __syncthreads();
@@ -166,10 +190,16 @@ __global__ void __launch_bounds__(256) analysis_lj_kernel(const __grid_constant_
 // (both even).  Polyphase: outputs 2q and 2q+1 use the same band samples
 // k0 + q + t, t < F/2, with the odd and the even taps respectively
 // (a[m] = sum_k f[2k+1-m] band[k]).  Adds this thread's outputs to acc[8]:
-// pairs idx = tid + 256 s, s < 4, each giving rows 2qy and 2qy+1 of column rx.
+// slot pairs s < 4 give rows 2 qy and 2 qy + 1 of column rx (synth_slot).
+//
+// Register blocking as in the analysis: an x-step thread computes kSynNQ
+// adjacent q of one band row from H + kSynNQ - 1 samples per band (rows
+// taken by consecutive threads, odd row strides), and a y-step thread
+// computes its four adjacent qy of one column from H + 3 samples per array.
+constexpr int kSynNQ = 4;
 template <int P>
 __device__ __forceinline__ void synthesis_tile_t(const SaraConst &c, int j, int m0y, int m0x, const float *coef_l,
-                                                 const float *ll_in, float (*sb)[SB_Y][SB_X + 1],
+                                                 const float *ll_in, float (*sb)[SB_Y][SB_X + 2],
                                                  float (*su)[SB_Y][STX + 1], float *acc) {
     constexpr int F = 2 * P, H = P;
     float h[F], g[F];
@@ -201,43 +231,60 @@ __device__ __forceinline__ void synthesis_tile_t(const SaraConst &c, int j, int 
     }
     __syncthreads();
     // x: u_lo = synth(LL, h) + synth(LH, g); u_hi = synth(HL, h) + synth(HH, g)
-    for (int idx = threadIdx.x; idx < NBY * (STX / 2); idx += blockDim.x) {
-        const int r = idx / (STX / 2), q = idx % (STX / 2);
-        float le = 0.f, lo = 0.f, he = 0.f, ho = 0.f;
+    constexpr int WQ = H + kSynNQ - 1;
+    for (int idx = threadIdx.x; idx < NBY * (STX / 2 / kSynNQ); idx += blockDim.x) {
+        const int r = idx % NBY, q0 = (idx / NBY) * kSynNQ;
+        float a0[WQ], a1[WQ], a2[WQ], a3[WQ];
 #pragma unroll
-        for (int t = 0; t < H; ++t) {
-            const float a0 = sb[0][r][q + t], a1 = sb[1][r][q + t], a2 = sb[2][r][q + t], a3 = sb[3][r][q + t];
-            le = fmaf(h[2 * t + 1], a0, fmaf(g[2 * t + 1], a1, le));
-            lo = fmaf(h[2 * t], a0, fmaf(g[2 * t], a1, lo));
-            he = fmaf(h[2 * t + 1], a2, fmaf(g[2 * t + 1], a3, he));
-            ho = fmaf(h[2 * t], a2, fmaf(g[2 * t], a3, ho));
+        for (int t = 0; t < WQ; ++t) {
+            a0[t] = sb[0][r][q0 + t];
+            a1[t] = sb[1][r][q0 + t];
+            a2[t] = sb[2][r][q0 + t];
+            a3[t] = sb[3][r][q0 + t];
         }
-        su[0][r][2 * q] = le;
-        su[0][r][2 * q + 1] = lo;
-        su[1][r][2 * q] = he;
-        su[1][r][2 * q + 1] = ho;
+#pragma unroll
+        for (int n = 0; n < kSynNQ; ++n) {
+            float le = 0.f, lo = 0.f, he = 0.f, ho = 0.f;
+#pragma unroll
+            for (int t = 0; t < H; ++t) {
+                le = fmaf(h[2 * t + 1], a0[n + t], fmaf(g[2 * t + 1], a1[n + t], le));
+                lo = fmaf(h[2 * t], a0[n + t], fmaf(g[2 * t], a1[n + t], lo));
+                he = fmaf(h[2 * t + 1], a2[n + t], fmaf(g[2 * t + 1], a3[n + t], he));
+                ho = fmaf(h[2 * t], a2[n + t], fmaf(g[2 * t], a3[n + t], ho));
+            }
+            su[0][r][2 * (q0 + n)] = le;
+            su[0][r][2 * (q0 + n) + 1] = lo;
+            su[1][r][2 * (q0 + n)] = he;
+            su[1][r][2 * (q0 + n) + 1] = ho;
+        }
     }
     __syncthreads();
+    {
+        const int rx = threadIdx.x % STX, qy0 = (threadIdx.x / STX) * 4;
+        float ul[H + 3], uh[H + 3];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        const int idx = threadIdx.x + 256 * s;
-        const int qy = idx / STX, rx = idx % STX;
-        float e = 0.f, o = 0.f;
-#pragma unroll
-        for (int t = 0; t < H; ++t) {
-            const float ul = su[0][qy + t][rx], uh = su[1][qy + t][rx];
-            e = fmaf(h[2 * t + 1], ul, fmaf(g[2 * t + 1], uh, e));
-            o = fmaf(h[2 * t], ul, fmaf(g[2 * t], uh, o));
+        for (int t = 0; t < H + 3; ++t) {
+            ul[t] = su[0][qy0 + t][rx];
+            uh[t] = su[1][qy0 + t][rx];
         }
-        acc[2 * s] += e;
-        acc[2 * s + 1] += o;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            float e = 0.f, o = 0.f;
+#pragma unroll
+            for (int t = 0; t < H; ++t) {
+                e = fmaf(h[2 * t + 1], ul[s + t], fmaf(g[2 * t + 1], uh[s + t], e));
+                o = fmaf(h[2 * t], ul[s + t], fmaf(g[2 * t], uh[s + t], o));
+            }
+            acc[2 * s] += e;
+            acc[2 * s + 1] += o;
+        }
     }
     __syncthreads();
 }
 
 __device__ __forceinline__ void synthesis_tile(const SaraConst &c, int p, int j, int m0y, int m0x,
                                                const float *coef_l, const float *ll_in,
-                                               float (*sb)[SB_Y][SB_X + 1], float (*su)[SB_Y][STX + 1],
+                                               float (*sb)[SB_Y][SB_X + 2], float (*su)[SB_Y][STX + 1],
                                                float *acc) {
     switch (p) {
         case 1: synthesis_tile_t<1>(c, j, m0y, m0x, coef_l, ll_in, sb, su, acc); break;
@@ -251,20 +298,21 @@ __device__ __forceinline__ void synthesis_tile(const SaraConst &c, int p, int j,
     }
 }
 
-// Output sample of pair slot s of this thread: (row, col) offsets in the tile.
+// Output sample of slot s of this thread: (row, col) offsets in the tile
+// (column threadIdx % STX, band rows qy0 .. qy0 + 3 with qy0 = 4 (threadIdx / STX),
+// even and odd output row of each).
 __device__ __forceinline__ void synth_slot(int s, int &ry, int &rx) {
-    const int idx = threadIdx.x + 256 * (s >> 1);
-    ry = 2 * (idx / STX) + (s & 1);
-    rx = idx % STX;
+    ry = 2 * ((threadIdx.x / STX) * 4 + (s >> 1)) + (s & 1);
+    rx = threadIdx.x % STX;
 }
 
-// Synthesis kernels run six CTAs per SM (at most 40 registers): the band
-// staging is latency-bound, and occupancy hides it (3.5 % faster than the
-// register-unlimited build at 1024^2 x 8 channels).
+// Synthesis kernels run four CTAs per SM (at most 64 registers: the
+// register-blocked sample windows and the eight accumulators fit without
+// spills; the band staging is latency-bound and the occupancy hides it).
 // Levels j >= 2: reconstruct a_{j-1} of basis p into tmp.
-__global__ void __launch_bounds__(256, 6) synthesis_lj_kernel(const __grid_constant__ SaraConst c, int j,
+__global__ void __launch_bounds__(256, 4) synthesis_lj_kernel(const __grid_constant__ SaraConst c, int j,
                                                            const float *__restrict__ coef, float *__restrict__ tmp) {
-    __shared__ float sb[4][SB_Y][SB_X + 1];
+    __shared__ float sb[4][SB_Y][SB_X + 2];
     __shared__ float su[2][SB_Y][STX + 1];
     const int p = 1 + blockIdx.z % kNumDb;
     const int l = blockIdx.z / kNumDb;
@@ -287,10 +335,10 @@ __global__ void __launch_bounds__(256, 6) synthesis_lj_kernel(const __grid_const
 }
 
 // Level 1 of all bases plus the Dirac basis, summed into the image: x = (1/3) sum.
-__global__ void __launch_bounds__(256, 6) synthesis_l1_kernel(const __grid_constant__ SaraConst c,
+__global__ void __launch_bounds__(256, 4) synthesis_l1_kernel(const __grid_constant__ SaraConst c,
                                                            const float *__restrict__ coef, const float *__restrict__ tmp,
                                                            float *__restrict__ x) {
-    __shared__ float sb[4][SB_Y][SB_X + 1];
+    __shared__ float sb[4][SB_Y][SB_X + 2];
     __shared__ float su[2][SB_Y][STX + 1];
     const int l = blockIdx.z;
     const int m0y = blockIdx.y * STY, m0x = blockIdx.x * STX;
