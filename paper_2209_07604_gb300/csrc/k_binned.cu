@@ -169,9 +169,10 @@ __device__ __forceinline__ void bin_rows(int i0, int nv, int lane, const int2 *s
     }
 }
 
-// Scatter of rows with R > 1 separable terms (DDE rows, see k_nufft.cu): one
-// row per warp as in bin_rows; each lane sums conj(A_r[t1]) conj(B_r[col]) d
-// over the terms in registers and adds each of its cells once.
+// Scatter of rows with 1 < R <= kDdeTaps separable terms (DDE rows, see
+// k_nufft.cu): one row per warp as in bin_rows; each lane sums
+// conj(A_r[t1]) conj(B_r[col]) d over the terms in registers and adds each of
+// its cells once.
 template <bool DENSE>
 __device__ __forceinline__ void scatter_rows_rank(int i0, int nv, int lane, int R, const int2 *s_meta,
                                                   const int *s_off, const float2 *s_d,
@@ -188,9 +189,15 @@ __device__ __forceinline__ void scatter_rows_rank(int i0, int nv, int lane, int 
         float accr[8], acci[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) accr[k] = acci[k] = 0.f;
-#pragma unroll 1
-        for (int r = 0; r < R; ++r) {
-            const float2 fac = load_factors(fbin + s_off[i] + r * 2 * T, T, lane);
+        // all terms' factors are loaded before the first is used (one memory latency per row)
+        float2 facs[kDdeTaps];
+#pragma unroll
+        for (int r = 0; r < kDdeTaps; ++r)
+            facs[r] = r < R ? load_factors(fbin + s_off[i] + r * 2 * T, T, lane) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int r = 0; r < kDdeTaps; ++r) {
+            if (r >= R) break;
+            const float2 fac = facs[r];
             const float g2x = __shfl_sync(FULL, fac.x, 16 + col), g2y = __shfl_sync(FULL, fac.y, 16 + col);
             const float er = fmaf(g2x, dr, g2y * di), ei = fmaf(g2x, di, -g2y * dr);
 #pragma unroll
