@@ -6,6 +6,9 @@
 // corner inside each (channel, block) segment.
 #include "fhs_internal.h"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 namespace fhs {
 
 namespace {
@@ -32,6 +35,8 @@ __device__ __forceinline__ void red_add_f2(float2 *addr, float2 v) {
 // instead of one per G entry).  Bins marked -1 (sparse tiles) take the
 // global path.
 constexpr int kWin = kTile + 15;        // boxes have T <= 16
+constexpr int kWinP = kWin + 1;         // row stride of the staged forward window: a TMA box row
+                                        // must be a multiple of 16 bytes (48 complex values)
 #ifndef FHS_BIN_MAX
 #define FHS_BIN_MAX 384
 #endif
@@ -256,7 +261,7 @@ __device__ __forceinline__ void gather_cols(const float2 *__restrict__ f, int T,
         const float2 a = __ldg(f + t1);
         float br = 0.f, bi = 0.f;
         if (DENSE) {
-            const float2 *row = s_grid + (c1 - wy0 + t1) * kWin + (c2 - wx0 + C0);
+            const float2 *row = s_grid + (c1 - wy0 + t1) * kWinP + (c2 - wx0 + C0);
 #pragma unroll
             for (int t2 = 0; t2 < CW; ++t2) {
                 const float2 x = row[t2];
@@ -365,6 +370,39 @@ __device__ __forceinline__ void gather_phase(int nv, int R, const int2 *s_meta, 
     }
 }
 
+// Window staging by the tensor memory accelerator: one 3-D box (kWinP x kWin
+// cells x 1 channel) of the forward grid into shared memory, completion
+// counted on an mbarrier.  Used for tiles whose window does not wrap around
+// the grid edge (wrapped windows take the per-thread loads).
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void window_tma(float2 *dst, const CUtensorMap *tmap, int x, int y, int z, uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(int(sizeof(float2) * kWin * kWinP))
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Bounded wait for phase 0 of the window barrier; false if it gave up.
+__device__ __forceinline__ bool window_wait(uint64_t *bar) {
+    const uint32_t a = smem_addr(bar);
+    for (int it = 0; it < (1 << 24); ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
 // Four CTAs per SM (64 registers, 46 KB shared each): the kernel is latency
 // bound, and occupancy matters more than the registers the cap takes away.
 #ifndef FHS_FUSED_MIN_BLOCKS
@@ -384,9 +422,11 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : FHS_FUSED_MIN_BLOCKS) degrid_
     const float2 *__restrict__ y, float2 *__restrict__ dvis, const long long *__restrict__ bin_start,
     const int *__restrict__ bin_seg, const int *__restrict__ bin_tile, int ntx, int B,
     const float *__restrict__ blk_scale, double *__restrict__ blk_norm2, const float2 *__restrict__ grid,
-    float2 *__restrict__ grid_blk, long long K, int K1, int K2, float sigma2, int R_) {
+    float2 *__restrict__ grid_blk, long long K, int K1, int K2, float sigma2, int R_,
+    const __grid_constant__ CUtensorMap tmap, int use_tma, int *__restrict__ err) {
     const int R = MULTI ? R_ : 1;
-    __shared__ float2 s_grid[kWin * kWin];
+    __shared__ alignas(128) float2 s_grid[kWin * kWinP];
+    __shared__ alignas(8) uint64_t s_bar;
     __shared__ float s_re[kWin * kWin];
     __shared__ float s_im[kWin * kWin];
     __shared__ int2 s_meta[kBinMax];
@@ -420,18 +460,38 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : FHS_FUSED_MIN_BLOCKS) degrid_
     if (dense) {
         wy0 = (tile / ntx) * kTile;
         wx0 = (tile % ntx) * kTile;
+    }
+    // the window by TMA when it lies inside the grid (x = wx0 is a multiple of 32 cells: 256-byte aligned)
+    const bool tma = MODE != kScatter && use_tma && dense && wy0 + kWin <= K1 && wx0 + kWinP <= K2;
+    if (tma) {
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_bar)) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) window_tma(s_grid, &tmap, wx0, wy0, l, &s_bar);
+    }
+    if (dense) {
         for (int i = threadIdx.x; i < kWin * kWin; i += blockDim.x) {
             const int r = i / kWin, c = i - r * kWin;
-            int k1 = wy0 + r;
-            while (k1 >= K1) k1 -= K1;
-            int k2 = wx0 + c;
-            while (k2 >= K2) k2 -= K2;
-            if (MODE != kScatter) s_grid[i] = gl[(long long)k1 * K2 + k2];
+            if (MODE != kScatter && !tma) {
+                int k1 = wy0 + r;
+                while (k1 >= K1) k1 -= K1;
+                int k2 = wx0 + c;
+                while (k2 >= K2) k2 -= K2;
+                s_grid[r * kWinP + c] = gl[(long long)k1 * K2 + k2];
+            }
             if (MODE != kGather) {
                 s_re[i] = 0.f;
                 s_im[i] = 0.f;
             }
         }
+    }
+    if (tma && !window_wait(&s_bar)) {
+        // the copy did not complete in time: record it, then wait once more (bounded) so that
+        // no copy into this CTA's shared memory is still in flight when it moves on
+        if (threadIdx.x == 0) atomicExch(err, 2);
+        window_wait(&s_bar);
     }
     __syncthreads();
     Kahan nrm;
@@ -507,39 +567,75 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : FHS_FUSED_MIN_BLOCKS) degrid_
 
 }  // namespace
 
+// Tensor map of a [L][K1][K2] complex grid for the window staging (8-byte
+// elements, box kWinP x kWin x 1).  The encoder comes from the driver entry
+// point; ok = 0 (per-thread staging) if it is unavailable or refuses the map.
+struct WindowMap {
+    CUtensorMap map;
+    int ok = 0;
+};
+
+static WindowMap window_map(const fhs_problem *p, const float2 *grid) {
+    static PFN_cuTensorMapEncodeTiled_v12000 enc = [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            fn = nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    WindowMap w{};
+    if (!enc || !grid || p->K1 < kWin || p->K2 < kWinP) return w;
+    const cuuint64_t dims[3] = {cuuint64_t(p->K2), cuuint64_t(p->K1), cuuint64_t(p->L)};
+    const cuuint64_t strides[2] = {cuuint64_t(p->K2) * sizeof(float2), cuuint64_t(p->K) * sizeof(float2)};
+    const cuuint32_t box[3] = {cuuint32_t(kWinP), cuuint32_t(kWin), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    w.ok = enc(&w.map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<float2 *>(grid), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return w;
+}
+
 cudaError_t launch_degrid(fhs_problem *p, const float2 *grid, float2 *vis_sorted, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
+    const WindowMap tm = window_map(p, grid);
     (p->rank > 1 ? degrid_grid_binned_kernel<kGather, true> : degrid_grid_binned_kernel<kGather, false>)<<<p->n_bin, 256, 0, s>>>(
         p->meta, p->fptr, p->gfac, nullptr, vis_sorted, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B,
-        nullptr, nullptr, grid, nullptr, p->K, p->K1, p->K2, 0.f, p->rank);
+        nullptr, nullptr, grid, nullptr, p->K, p->K1, p->K2, 0.f, p->rank, tm.map, tm.ok, p->dev_err);
     p->n_launch += 1;
     return cudaGetLastError();
 }
 
 cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
+    const WindowMap tm{};                        // no forward window to stage
     (p->rank > 1 ? degrid_grid_binned_kernel<kScatter, true> : degrid_grid_binned_kernel<kScatter, false>)<<<p->n_bin, 256, 0, s>>>(
         p->meta, p->fptr, p->gfac, nullptr, const_cast<float2 *>(vis_sorted), p->bin_start, p->bin_seg,
-        p->bin_tile, p->ntx, p->B, nullptr, nullptr, nullptr, grid, p->K, p->K1, p->K2, 0.f, p->rank);
+        p->bin_tile, p->ntx, p->B, nullptr, nullptr, nullptr, grid, p->K, p->K1, p->K2, 0.f, p->rank, tm.map, tm.ok, p->dev_err);
     p->n_launch += 1;
     return cudaGetLastError();
 }
 
 cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
+    const WindowMap tm = window_map(p, grid);
     (p->rank > 1 ? degrid_grid_binned_kernel<kNormal, true> : degrid_grid_binned_kernel<kNormal, false>)<<<p->n_bin, 256, 0, s>>>(
         p->meta, p->fptr, p->gfac, nullptr, nullptr, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B, nullptr,
-        nullptr, grid, grid_out, p->K, p->K1, p->K2, 0.f, p->rank);
+        nullptr, grid, grid_out, p->K, p->K1, p->K2, 0.f, p->rank, tm.map, tm.ok, p->dev_err);
     p->n_launch += 1;
     return cudaGetLastError();
 }
 
 cudaError_t launch_degrid_grid_fused(fhs_problem *p, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
+    const WindowMap tm = window_map(p, p->grid_work);
     (p->rank > 1 ? degrid_grid_binned_kernel<kFused, true> : degrid_grid_binned_kernel<kFused, false>)<<<p->n_bin, 256, 0, s>>>(p->meta, p->fptr, p->gfac, p->y, p->dvis, p->bin_start,
                                                        p->bin_seg, p->bin_tile, p->ntx, p->B, p->blk_scale,
                                                        p->blk_norm2, p->grid_work, p->grid_blk, p->K, p->K1, p->K2,
-                                                       float(p->sigma2), p->rank);
+                                                       float(p->sigma2), p->rank, tm.map, tm.ok, p->dev_err);
     p->n_launch += 1;
     return cudaGetLastError();
 }
