@@ -791,28 +791,23 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
     }
     const int nkeys = nty * ntx * 17;
     std::vector<long long> perm(Mtot);
-    // counting sort by tile key, segments in parallel (each segment is stable)
+    // sort by tile key, then (inside each (tile, T) run) by box corner, row-major within the
+    // tile, so that the rows one warp gathers at once read nearby window cells: two stable
+    // counting sorts per segment (corner position first, then tile key), segments in parallel
     parallel_for(p->n_seg, [&](long long s0, long long s1) {
-        std::vector<long long> cnt(nkeys + 1);
+        std::vector<long long> cnt(nkeys + 1), cpos(kTile * kTile + 1), tmp;
         for (long long sg = s0; sg < s1; ++sg) {
             const long long a = p->seg_off[sg], b = p->seg_off[sg + 1];
+            auto pos = [&](long long i) { return (corner1[i] % kTile) * kTile + corner2[i] % kTile; };
+            tmp.resize(size_t(b - a));
+            std::fill(cpos.begin(), cpos.end(), 0);
+            for (long long i = a; i < b; ++i) cpos[pos(i) + 1]++;
+            for (int k = 0; k < kTile * kTile; ++k) cpos[k + 1] += cpos[k];
+            for (long long i = a; i < b; ++i) tmp[cpos[pos(i)]++] = i;
             std::fill(cnt.begin(), cnt.end(), 0);
             for (long long i = a; i < b; ++i) cnt[key[i] + 1]++;
             for (int k = 0; k < nkeys; ++k) cnt[k + 1] += cnt[k];
-            for (long long i = a; i < b; ++i) perm[a + cnt[key[i]]++] = i;
-            // inside each (tile, T) run: by box corner, row-major within the tile, so that
-            // the rows one warp gathers at once read nearby window cells
-            for (long long r0 = a; r0 < b;) {
-                long long r1 = r0 + 1;
-                while (r1 < b && key[perm[r1]] == key[perm[r0]]) ++r1;
-                if (r1 - r0 > 1)
-                    std::sort(perm.begin() + r0, perm.begin() + r1, [&](long long u, long long v) {
-                        const int pu = (corner1[u] % kTile) * kTile + corner2[u] % kTile;
-                        const int pv = (corner1[v] % kTile) * kTile + corner2[v] % kTile;
-                        return pu != pv ? pu < pv : u < v;
-                    });
-                r0 = r1;
-            }
+            for (const long long i : tmp) perm[a + cnt[key[i]]++] = i;
         }
     }, 1);
     std::vector<int2> meta(Mtot);
