@@ -105,16 +105,16 @@ def _peaks():
 
 
 def _profile_traffic(kernel_file: str):
-    """(dram bytes per launch, limiter) of the fused kernel from the committed
-    ncu summary, valid only while the kernel source is unchanged (sha256
-    recorded there); (None, None) otherwise."""
-    path = os.path.join(ROOT, "profiles", "degrid_grid_fused_vla_1024.md")
+    """(dram bytes per data term, limiter) of the two passes over G from the
+    committed ncu summary, valid only while the kernel source is unchanged
+    (sha256 recorded there); (None, None) otherwise."""
+    path = os.path.join(ROOT, "profiles", "data_term_passes_vla_1024.md")
     src = os.path.join(ROOT, "paper_2209_07604_gb300", "csrc", kernel_file)
     try:
         txt = open(path).read()
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
         m_sha = re.search(r"kernel source sha256:\s*([0-9a-f]{64})", txt)
-        m_tr = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", txt)
+        m_tr = re.search(r"dram bytes per full data term:\s*([0-9.eE+]+)", txt)
         m_lim = re.search(r"^limiter:\s*(.+)$", txt, re.M)
         if m_sha and m_tr and m_sha.group(1) == sha:
             return float(m_tr.group(1)), (m_lim.group(1).strip() if m_lim else None)
@@ -123,13 +123,15 @@ def _profile_traffic(kernel_file: str):
     return None, None
 
 
-def fused_kernel_bytes(info, L, B, K, M):
-    """Algorithmic HBM bytes of one launch of the single-pass data kernel:
-    G factors 8 B per stored value (2T per row); per row meta 8 B + factor
-    offset 8 B; per visibility y 8 B, dual d read 8 B + write 8 B; the forward
-    grid read once (8 B/cell) and every block grid written back once
-    (8 B/cell/block)."""
-    return info.n_gfac * 8 + M * (8 + 8 + 8 + 8 + 8) + L * K * 8 + L * B * K * 8
+def data_term_bytes(info, L, K, M):
+    """Algorithmic HBM bytes of the data term's two passes over G.  Dual pass:
+    G factors 8 B per stored value (2T per row), per row meta 8 B + factor
+    offset 8 B, per visibility y 8 B and the dual d read 8 B + written 8 B,
+    the forward grid read once (8 B/cell).  Scatter pass: the factors, meta and
+    offsets again, d read 8 B, the channel grid written once (8 B/cell)."""
+    dual = info.n_gfac * 8 + M * (8 + 8 + 8 + 8 + 8) + L * K * 8
+    scatter = info.n_gfac * 8 + M * (8 + 8 + 8) + L * K * 8
+    return dual + scatter
 
 
 def run_gpu(args):
@@ -237,10 +239,10 @@ def run_gpu(args):
     phit_ms = e[1].elapsed_time(e[2]) / n_op
     del xs, vis, img
 
-    # roofline of the dominant kernel (single pass over G)
+    # roofline of the dominant kernels: the data term's two passes over G (the degrid_grid phase)
     K = 4 * P.ny * P.nx
     peak, peak_kind = _peaks()
-    kbytes = fused_kernel_bytes(info, L, P.B, K, Mtot)
+    kbytes = data_term_bytes(info, L, K, Mtot)
     if args.reduction:
         # two normal-mode passes per iteration (H Xhat, then H Lambda v): factors, row meta and
         # offsets, the input grid read and the output grid written once each per pass
@@ -285,7 +287,7 @@ def run_gpu(args):
                 "seconds": e2e_s, "setup_seconds": setup_s},
         "gpu_launches": int(launches),
         "phases_ms_per_step": {k: v / max(n_prof, 1) for k, v in phases.items()},
-        "roofline": {"kernel": "degrid_grid_fused", "bound": "hbm", "achieved": achieved, "peak": peak,
+        "roofline": {"kernel": "data term: dual + scatter passes over G", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes": kbytes, "peak_source": peak_kind, "limiter": limiter},
         "clocks": clk.summary(),

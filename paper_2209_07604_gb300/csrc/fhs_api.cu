@@ -237,13 +237,13 @@ fhs_status adjoint_to_image(fhs_problem *p, const float2 *vis_sorted, float *x, 
 // (gather and scatter of each row together) between the two FFTs.  grid_in
 // keeps its zero padding (Z writes the image cells only) and grid_work (Phi^H
 // of the data dual) is iteration state, so the adjoint grids go to the first
-// L grids of grid_blk, which are zero between iterations and zero again after.
+// grids of grid_scr, which are zero between uses and zero again after.
 //
 // With data reduction, y = Re(Phi'^H Phi') v = Re Z^T F^H H Lambda^2 H F Z v:
 // two passes over G with the Lambda^2 weighting between them (dr_u and dr_w
 // are zero / free between iterations).
 fhs_status apply_normal(fhs_problem *p, const float *v, float *y, cudaStream_t s) {
-    float2 *scratch = p->grid_blk;
+    float2 *scratch = p->grid_scr;
     CU(launch_zpad(p, v, p->grid_in, s));
     TRY(fft(p, p->grid_in, p->grid_aux, CUFFT_FORWARD, s));
     if (p->dr) {
@@ -504,12 +504,13 @@ fhs_status one_iteration(fhs_problem *p, cudaStream_t s) {
         Phase ph(p, s, FHS_PHASE_PRIMAL);
         CU(launch_primal(p, s));
     }
-    // the prior branches only read xbar and fork off after the pass over G (they
-    // then overlap the combine and F^H; beside the pass itself they take the
-    // shared memory it needs and cost more than they save); tracing keeps one
-    // stream so that its per-phase event pairs time one phase at a time
+    // the prior branches only read xbar and fork off after the dual pass over G
+    // (they then overlap the l2-ball factors, the scatter pass and F^H; beside
+    // the first pass they take the shared memory it needs and cost more than
+    // they save); tracing keeps one stream so that its per-phase event pairs
+    // time one phase at a time
     const bool fork = !p->prof_on && p->s_sara && p->s_nuc && (sara_active(p) || nuc_active(p));
-    // data fidelity: F, single pass over G, l2-ball factors, combine, F^H
+    // data fidelity: F, dual pass over G, l2-ball factors, scatter pass, F^H
     {
         Phase ph(p, s, FHS_PHASE_FFT_FWD);
         TRY(fft(p, p->grid_in, p->grid_work, CUFFT_FORWARD, s));
@@ -517,7 +518,7 @@ fhs_status one_iteration(fhs_problem *p, cudaStream_t s) {
     {
         Phase ph(p, s, FHS_PHASE_DEGRID_GRID);
         if (p->dr) CU(launch_normal(p, p->grid_work, p->dr_u, s));     // H Xhat
-        else CU(launch_degrid_grid_fused(p, s));
+        else CU(launch_data_dual(p, s));                               // d, block norms
     }
     if (fork) {
         CU(cudaEventRecord(p->ev_fork, s));
@@ -534,9 +535,14 @@ fhs_status one_iteration(fhs_problem *p, cudaStream_t s) {
         Phase ph(p, s, FHS_PHASE_DEGRID_GRID);
         CU(launch_normal(p, p->dr_w, p->grid_work, s));
     } else {
-        Phase ph(p, s, FHS_PHASE_L2BALL);
-        CU(launch_block_finalize(p, s));
-        CU(launch_combine(p, s));
+        // l2-ball factors, then G^H (s_b d) straight into the channel grids
+        {
+            Phase ph(p, s, FHS_PHASE_L2BALL);
+            CU(launch_block_finalize(p, s));
+            CU(cudaMemsetAsync(p->grid_work, 0, sizeof(float2) * p->K * p->L, s));
+        }
+        Phase ph(p, s, FHS_PHASE_DEGRID_GRID);
+        CU(launch_data_scatter(p, s));
     }
     {
         Phase ph(p, s, FHS_PHASE_FFT_INV);
@@ -982,7 +988,7 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
     if ((st = guard(dev_alloc(p, &p->grid_in, p->K * L))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->grid_work, p->K * L))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->grid_aux, p->K * L))) != FHS_OK) return st;
-    if ((st = guard(dev_alloc(p, &p->grid_blk, p->K * L * B))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->grid_scr, p->K * L))) != FHS_OK) return st;
     if (p->dr) {
         // gridding (Sec. 3.4): diag(H_l) by one pass over the rows, Lambda_l, y'_l, M'_l
         const size_t LK = (size_t)p->K * L;
@@ -1223,7 +1229,7 @@ fhs_status fhs_estimate_bytes(const fhs_params *params, const double *w, int64_t
     r += 8 * (nseg + 1) + 8 * nseg + 8 * nseg + 4 * nseg;            // segments, norms, eps, scales
     r += 8 * (nbin + 1) + 8 * nbin + 8 * (nchunk + 1) + 4 * nchunk;  // bins and chunks
     r += 4 * (q.ny + q.nx);                                          // Z scaling
-    r += 8 * K * L * (3 + B);                                        // grids
+    r += 8 * K * L * 4;                                              // grids
     r += 4 * N * L * 3 + 16 + 16 * L + 4 * L;                        // images, reductions, PSF factors
     r += 4 * c.n_coef * L * 2 + 4 * c.n_tmp * L + 4 * c.n_coef * C;  // SARA
     const long long ne = Lc + (Lc & 1);
@@ -1583,9 +1589,9 @@ fhs_status fhs_autotune_bins(fhs_problem *p, void *stream, int32_t *dense_min_ou
         p->bin_seg = b.seg;
         p->bin_tile = b.tile;
         p->n_bin = b.n;
-        CU(launch_normal(p, p->grid_aux, p->grid_blk, s));          // warm-up
+        CU(launch_normal(p, p->grid_aux, p->grid_scr, s));          // warm-up
         CU(cudaEventRecord(e0, s));
-        for (int r = 0; r < 3; ++r) CU(launch_normal(p, p->grid_aux, p->grid_blk, s));
+        for (int r = 0; r < 3; ++r) CU(launch_normal(p, p->grid_aux, p->grid_scr, s));
         CU(cudaEventRecord(e1, s));
         CU(cudaEventSynchronize(e1));
         CU(cudaEventElapsedTime(&ms, e0, e1));
@@ -1661,7 +1667,7 @@ fhs_status fhs_autotune_bins(fhs_problem *p, void *stream, int32_t *dense_min_ou
         cudaGraphExecDestroy(p->gexec);
         p->gexec = nullptr;
     }
-    CU(cudaMemsetAsync(p->grid_blk, 0, sizeof(float2) * p->K * p->L, s));
+    CU(cudaMemsetAsync(p->grid_scr, 0, sizeof(float2) * p->K * p->L, s));
     CU(cudaMemsetAsync(p->coef_tmp, 0, sizeof(float) * LN, s));
     CU(cudaStreamSynchronize(s));
     if (rs != FHS_OK) return rs;

@@ -105,7 +105,7 @@ struct fhs_problem {
     bool plan_ok = false;
     float2 *grid_in = nullptr;                // [L][K] zero-padded input (zeros persist)
     float2 *grid_work = nullptr;              // [L][K] FFT output / data adjoint grid
-    float2 *grid_blk = nullptr;               // [L][B][K] per-block adjoint grids
+    float2 *grid_scr = nullptr;               // [L][K] scratch output grids (zero between uses)
     float2 *grid_aux = nullptr;               // [L][K] scratch for measure/adjoint
 
     // data reduction (Sec. 3.4): grids [L][K], zero off the gridded cells
@@ -196,14 +196,14 @@ cudaError_t launch_zpad(fhs_problem *p, const float *x, float2 *grid, cudaStream
 cudaError_t launch_degrid(fhs_problem *p, const float2 *grid, float2 *vis_sorted, cudaStream_t s);
 cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s);
 cudaError_t launch_crop(fhs_problem *p, const float2 *grid, float *x, cudaStream_t s);
-cudaError_t launch_degrid_grid_fused(fhs_problem *p, cudaStream_t s);
+cudaError_t launch_data_dual(fhs_problem *p, cudaStream_t s);      // dual pre-update + block norms
+cudaError_t launch_data_scatter(fhs_problem *p, cudaStream_t s);   // grid_work += G^H (s_b d)
 cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, cudaStream_t s);
 // One Lanczos step after y = A v: y <- w, vprev <- v_{j+1}; alpha_j[l] and
 // nb2_j[L + l] (= beta_{j+1}^2) accumulate, nb2_j[l] = beta_j^2 is read.
 cudaError_t launch_lanczos_step(fhs_problem *p, float *y, float *vprev, const float *v, double *alpha_j,
                                 double *nb2_j, cudaStream_t s);
 cudaError_t launch_block_finalize(fhs_problem *p, cudaStream_t s);
-cudaError_t launch_combine(fhs_problem *p, cudaStream_t s);
 cudaError_t launch_permute_to_caller(fhs_problem *p, const float2 *sorted, float2 *caller, const float *scale_seg,
                                      cudaStream_t s);
 cudaError_t launch_permute_from_caller(fhs_problem *p, const float2 *caller, float2 *sorted, cudaStream_t s);

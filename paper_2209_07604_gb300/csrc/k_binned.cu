@@ -1,6 +1,6 @@
-// The tile-binned pass over G (Sec. 2.1, Eq. 1) in its four uses: the data
-// term of a PDFB iteration (Eq. 2, gather + dual pre-update + block norms +
-// scatter in one pass), Phi alone, Phi^H alone, and Phi^H Phi for the
+// The tile-binned pass over G (Sec. 2.1, Eq. 1) in its uses: the data term of
+// a PDFB iteration (Eq. 2) as a dual pass (gather + dual pre-update + block
+// norms) and a scatter pass, Phi alone, Phi^H alone, and Phi^H Phi for the
 // operator-norm estimate.  Rows of G are the outer products g1 (x) g2 of two
 // 1-D factors (see k_nufft.cu); rows are sorted by the grid tile of their box
 // corner inside each (channel, block) segment.
@@ -19,21 +19,22 @@ __device__ __forceinline__ void red_add_f2(float2 *addr, float2 v) {
     atomicAdd(addr, v);   // sm_90+: vector float2 reduction (red.global.add.v2.f32)
 }
 
-// The data term of one PDFB iteration in a single pass over G (Eq. 2):
-//   phi  = G_m . Xhat                      (gather from the forward grid)
-//   d_m  = s_b d_m + sigma2 (phi - y_m)    (= z - sigma2 y, z = v + sigma2 Phi xbar)
-//   ||d_b||^2 accumulated per block (compensated FP32, then FP64)
-//   grid_b += conj(G_m) d_m                (scatter into the block's own grid)
-// The block's l2-ball factor (1 - m_b) is known only after the pass; it is
-// applied to grid_b when the block grids are combined, and kept as s_b for d.
-// Tile-binned form of the same pass.  A bin holds visibilities of one
-// (channel, block) segment whose box corners fall in one kTile x kTile grid
-// tile; every box then lies inside the kWin x kWin window at the tile origin.
-// The CTA stages the window of the forward grid in shared memory, gathers
-// from it, accumulates conj(G) d with shared-memory atomics, and adds the
-// window to the block grid once at the end (one global reduction per cell
-// instead of one per G entry).  Bins marked -1 (sparse tiles) take the
-// global path.
+// The data term of one PDFB iteration (Eq. 2) in two passes over G:
+//   dual pass      phi  = G_m . Xhat                    (gather from the forward grid)
+//                  d_m  = s_b d_m + sigma2 (phi - y_m)  (= z - sigma2 y, z = v + sigma2 Phi xbar)
+//                  ||d_b||^2 per block (compensated FP32, then FP64)
+//   (host stream)  s_b = 1 - min(1, sigma2 eps_b / ||d_b||), the block's l2-ball factor
+//   scatter pass   grid_l += conj(G_m) s_b d_m           (v_m = s_b d_m)
+// The dual is kept as d with the factor s_b applied lazily (v = s_b d).  Two
+// passes read G twice but need no per-block adjoint grids and no combine, and
+// each pass runs at the occupancy of its own resources.
+// Tile-binned form.  A bin holds visibilities of one (channel, block) segment
+// whose box corners fall in one kTile x kTile grid tile; every box then lies
+// inside the kWin x kWin window at the tile origin.  The CTA stages the
+// window of the forward grid in shared memory and gathers from it, or
+// accumulates conj(G) v with shared-memory atomics and adds the window to the
+// channel grid once at the end (one global reduction per cell instead of one
+// per G entry).  Bins marked -1 (sparse tiles) take the global path.
 constexpr int kWin = kTile + 15;        // boxes have T <= 16
 constexpr int kWinP = kWin + 1;         // row stride of the staged forward window: a TMA box row
                                         // must be a multiple of 16 bytes (48 complex values)
@@ -63,24 +64,25 @@ struct Kahan {
     }
 };
 
-// Visibilities i = i0, i0 + kWarps, ... of one bin, for one warp.  DENSE: the
-// box lies in the shared window; otherwise gather/scatter in global memory.
-// MODE: kFused (the PDFB data term), kGather (Phi only: vis_bin[i] = G_i . Xhat),
-// kScatter (Phi^H only: grid += conj(G_i) vis_bin[i]) or kNormal (G^H G in one
-// pass: grid += conj(G_i) (G_i . Xhat), for the operator-norm estimate).
+// Modes of the pass: kDual (the data term's dual pass), kGather (Phi only:
+// vis_bin[i] = G_i . Xhat), kScatter (Phi^H only, and the data term's scatter
+// pass: grid += conj(G_i) vis_bin[i]) and kNormal (G^H G in one pass:
+// grid += conj(G_i) (G_i . Xhat), for the operator-norm estimate).
+enum { kDual = 0, kGather = 1, kScatter = 2, kNormal = 3 };
+
+// Scatter of rows i = i0, i0 + kWarps, ... of one bin by one warp,
+// grid += conj(G_i) s_d[i].  DENSE: the box lies in the shared window (shared
+// atomics); otherwise global reductions.
 //
 // Row G_i = g1 (x) g2 over the T x T box: lane (half, col) = (lane / 16,
-// lane % 16) owns box column col and rows t1 = half, half + 2, ...; it forms
-// b = sum_t1 g1[t1] X[t1][col], and the warp reduces g2[col] b over lanes.
-// The scatter adds conj(g1[t1]) (conj(g2[col]) d) to the same cells.
-enum { kFused = 0, kGather = 1, kScatter = 2, kNormal = 3 };
-
-template <int MODE, bool DENSE>
-__device__ __forceinline__ void bin_rows(int i0, int nv, int lane, const int2 *s_meta, const int *s_off,
-                                         const float2 *s_y, const float2 *s_d, const float2 *__restrict__ fbin,
-                                         const float2 *s_grid, float *s_re, float *s_im, int wy0, int wx0,
-                                         const float2 *__restrict__ gl, float2 *__restrict__ gb, int K1, int K2,
-                                         float sc, float sigma2, float2 *__restrict__ dvis_bin, Kahan &nrm) {
+// lane % 16) owns box column col and rows t1 = half, half + 2, ...; it adds
+// conj(g1[t1]) (conj(g2[col]) d) to those cells.  The next row's factors are
+// loaded while the current row is scattered.
+template <bool DENSE>
+__device__ __forceinline__ void scatter_rows(int i0, int nv, int lane, const int2 *s_meta, const int *s_off,
+                                             const float2 *s_d, const float2 *__restrict__ fbin, float *s_re,
+                                             float *s_im, int wy0, int wx0, float2 *__restrict__ gb, int K1,
+                                             int K2) {
     constexpr unsigned FULL = 0xffffffffu;
     const int half = lane >> 4, col = lane & 15;
     float2 fac = make_float2(0.f, 0.f);
@@ -94,7 +96,6 @@ __device__ __forceinline__ void bin_rows(int i0, int nv, int lane, const int2 *s
         const int c1 = m.x & 0xffff, c2 = (int)((unsigned)m.x >> 16);
         const bool cin = col < T;
         const float g2x = __shfl_sync(FULL, fac.x, 16 + col), g2y = __shfl_sync(FULL, fac.y, 16 + col);
-        // this lane's cell in box row t1 = half (rows advance by 2 per step)
         int ib = 0, k1 = 0, k2 = 0;
         if (DENSE) {
             ib = (c1 - wy0 + half) * kWin + (c2 - wx0 + col);
@@ -103,59 +104,12 @@ __device__ __forceinline__ void bin_rows(int i0, int nv, int lane, const int2 *s
             k2 = c2 + col;
             k2 -= (k2 >= K2) ? K2 : 0;
         }
-        float dr = 0.f, di = 0.f;
-        if (MODE != kScatter) {
-            float br = 0.f, bi = 0.f;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                if (2 * k >= T) break;                 // warp-uniform
-                const int t1 = 2 * k + half;
-                const float g1x = __shfl_sync(FULL, fac.x, t1), g1y = __shfl_sync(FULL, fac.y, t1);
-                if (cin && t1 < T) {
-                    float2 x;
-                    if (DENSE) {
-                        x = s_grid[ib + 2 * k * kWin];
-                    } else {
-                        int kk = k1 + 2 * k;
-                        kk -= (kk >= K1) ? K1 : 0;
-                        x = gl[(long long)kk * K2 + k2];
-                    }
-                    br = fmaf(g1x, x.x, fmaf(-g1y, x.y, br));
-                    bi = fmaf(g1x, x.y, fmaf(g1y, x.x, bi));
-                }
-            }
-            float ar = fmaf(br, g2x, -bi * g2y), ai = fmaf(br, g2y, bi * g2x);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                ar += __shfl_xor_sync(FULL, ar, o);
-                ai += __shfl_xor_sync(FULL, ai, o);
-            }
-            if (MODE == kFused) {
-                const float2 dold = s_d[i];
-                const float2 sy = s_y[i];
-                dr = fmaf(sc, dold.x, fmaf(sigma2, ar, -sy.x));
-                di = fmaf(sc, dold.y, fmaf(sigma2, ai, -sy.y));
-                if (lane == 0) {
-                    dvis_bin[i] = make_float2(dr, di);
-                    nrm.add(fmaf(dr, dr, di * di));
-                }
-            } else if (MODE == kGather) {
-                if (lane == 0) dvis_bin[i] = make_float2(ar, ai);
-                fac = fnx;
-                continue;
-            } else {
-                dr = ar;
-                di = ai;
-            }
-        } else {
-            dr = s_d[i].x;
-            di = s_d[i].y;
-        }
+        const float dr = s_d[i].x, di = s_d[i].y;
         // e = conj(g2[col]) d; cell (t1, col) += conj(g1[t1]) e
         const float er = fmaf(g2x, dr, g2y * di), ei = fmaf(g2x, di, -g2y * dr);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            if (2 * k >= T) break;
+            if (2 * k >= T) break;                   // warp-uniform
             const int t1 = 2 * k + half;
             const float g1x = __shfl_sync(FULL, fac.x, t1), g1y = __shfl_sync(FULL, fac.y, t1);
             if (cin && t1 < T) {
@@ -175,7 +129,7 @@ __device__ __forceinline__ void bin_rows(int i0, int nv, int lane, const int2 *s
 }
 
 // Scatter of rows with 1 < R <= kDdeTaps separable terms (DDE rows, see
-// k_nufft.cu): one row per warp as in bin_rows; each lane sums
+// k_nufft.cu): one row per warp as in scatter_rows; each lane sums
 // conj(A_r[t1]) conj(B_r[col]) d over the terms in registers and adds each of
 // its cells once.
 template <bool DENSE>
@@ -325,7 +279,7 @@ __device__ __forceinline__ float2 gather_terms(const float2 *__restrict__ f, int
 }
 
 // Phase 1 of a bin: one row per thread (rows are sorted by T inside each tile
-// run, so a warp's rows mostly share T).  kFused: the data-dual pre-update
+// run, so a warp's rows mostly share T).  kDual: the data-dual pre-update
 // d = s_b d + sigma2 (phi - y) into s_d, the bin's output and the block norm;
 // kGather: phi to the output; kNormal: phi into s_d for the scatter.
 template <int MODE, bool DENSE>
@@ -354,7 +308,7 @@ __device__ __forceinline__ void gather_phase(int nv, int R, const int2 *s_meta, 
         else if (tm <= 13) phi = gather_terms<13, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
         else phi = gather_terms<16, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
         if (!valid) continue;
-        if (MODE == kFused) {
+        if (MODE == kDual) {
             const float2 dold = s_d[i];
             const float2 sy = s_y[i];
             const float dr = fmaf(sc, dold.x, fmaf(sigma2, phi.x, -sy.x));
@@ -408,11 +362,13 @@ __device__ __forceinline__ bool window_wait(uint64_t *bar) {
 #ifndef FHS_FUSED_MIN_BLOCKS
 #define FHS_FUSED_MIN_BLOCKS 4
 #endif
-// MODE kFused: dvis is the data dual (read and written), grid the forward grid,
-// grid_blk the per-block adjoint grids.  kGather: dvis receives Phi x, grid is
-// the forward grid.  kScatter: dvis holds the visibilities, grid_blk the
-// per-channel output grids (indexed by channel instead of segment).  kNormal:
-// grid is the forward grid, grid_blk the per-channel output grids, dvis unused.
+// MODE kDual: dvis is the data dual d (read and written), grid the forward
+// grid, blk_scale the factors s_b of the previous iteration, blk_norm2 receives
+// ||d_b||^2.  kGather: dvis receives Phi x, grid is the forward grid.
+// kScatter: dvis holds the visibilities, scaled by blk_scale[segment] when
+// blk_scale is given (the data term's v = s_b d), grid_out the per-channel
+// output grids.  kNormal: grid is the forward grid, grid_out the per-channel
+// output grids, dvis unused.
 // MULTI: rows of R > 1 separable terms (DDE rows); otherwise R is 1 and the
 // term loops compile away.  Multi-term rows keep 3 CTAs per SM (80 registers:
 // their term accumulators spill under the 64-register cap).
@@ -422,7 +378,7 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : FHS_FUSED_MIN_BLOCKS) degrid_
     const float2 *__restrict__ y, float2 *__restrict__ dvis, const long long *__restrict__ bin_start,
     const int *__restrict__ bin_seg, const int *__restrict__ bin_tile, int ntx, int B,
     const float *__restrict__ blk_scale, double *__restrict__ blk_norm2, const float2 *__restrict__ grid,
-    float2 *__restrict__ grid_blk, long long K, int K1, int K2, float sigma2, int R_,
+    float2 *__restrict__ grid_out, long long K, int K1, int K2, float sigma2, int R_,
     const __grid_constant__ CUtensorMap tmap, int use_tma, int *__restrict__ err) {
     const int R = MULTI ? R_ : 1;
     __shared__ alignas(128) float2 s_grid[kWin * kWinP];
@@ -440,8 +396,9 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : FHS_FUSED_MIN_BLOCKS) degrid_
     const int tile = bin_tile[bin];
     const int l = seg / B;
     const float2 *gl = grid + (long long)l * K;
-    float2 *gb = grid_blk + (long long)((MODE == kScatter || MODE == kNormal) ? l : seg) * K;
-    const float sc = MODE == kFused ? blk_scale[seg] : 0.f;
+    float2 *gb = (MODE == kScatter || MODE == kNormal) ? grid_out + (long long)l * K : nullptr;
+    const float sc = MODE == kDual ? blk_scale[seg] : 0.f;
+    const float vsc = (MODE == kScatter && blk_scale) ? blk_scale[seg] : 1.f;
     const long long v0 = bin_start[bin];
     const int nv = int(bin_start[bin + 1] - v0);
     const long long g0 = fptr[v0];
@@ -449,11 +406,15 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : FHS_FUSED_MIN_BLOCKS) degrid_
     for (int i = threadIdx.x; i < nv; i += blockDim.x) {
         s_meta[i] = meta[v0 + i];
         s_off[i] = int(fptr[v0 + i] - g0);
-        if (MODE == kFused) {
+        if (MODE == kDual) {
             const float2 yy = y[v0 + i];
             s_y[i] = make_float2(sigma2 * yy.x, sigma2 * yy.y);
+            s_d[i] = dvis[v0 + i];
         }
-        if (MODE == kFused || MODE == kScatter) s_d[i] = dvis[v0 + i];
+        if (MODE == kScatter) {
+            const float2 dd = dvis[v0 + i];
+            s_d[i] = make_float2(vsc * dd.x, vsc * dd.y);
+        }
     }
     const bool dense = tile >= 0;
     int wy0 = 0, wx0 = 0;
@@ -481,7 +442,7 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : FHS_FUSED_MIN_BLOCKS) degrid_
                 while (k2 >= K2) k2 -= K2;
                 s_grid[r * kWinP + c] = gl[(long long)k1 * K2 + k2];
             }
-            if (MODE != kGather) {
+            if (MODE != kGather && MODE != kDual) {
                 s_re[i] = 0.f;
                 s_im[i] = 0.f;
             }
@@ -505,9 +466,8 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : FHS_FUSED_MIN_BLOCKS) degrid_
                                       dvis + v0, nrm);
     }
     // phase 2: scatters of conj(G_i) s_d[i], one row per warp
-    if (MODE != kGather) {
-        if (MODE != kScatter) __syncthreads();       // s_d holds the new values
-        Kahan unused;
+    if (MODE == kScatter || MODE == kNormal) {
+        if (MODE == kNormal) __syncthreads();        // s_d holds the gathered values
         if (MULTI) {
             if (dense)
                 scatter_rows_rank<true>(warp, nv, lane, R, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1, K2);
@@ -515,13 +475,11 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : FHS_FUSED_MIN_BLOCKS) degrid_
                 scatter_rows_rank<false>(warp, nv, lane, R, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1,
                                          K2);
         } else if (dense)
-            bin_rows<kScatter, true>(warp, nv, lane, s_meta, s_off, s_y, s_d, fbin, s_grid, s_re, s_im, wy0, wx0,
-                                     gl, gb, K1, K2, sc, sigma2, dvis + v0, unused);
+            scatter_rows<true>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1, K2);
         else
-            bin_rows<kScatter, false>(warp, nv, lane, s_meta, s_off, s_y, s_d, fbin, s_grid, s_re, s_im, wy0, wx0,
-                                      gl, gb, K1, K2, sc, sigma2, dvis + v0, unused);
+            scatter_rows<false>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1, K2);
     }
-    if (MODE != kFused) {
+    if (MODE != kDual) {
         if ((MODE == kScatter || MODE == kNormal) && dense) {
             __syncthreads();
             for (int q = threadIdx.x; q < kWin * kWin; q += blockDim.x) {
@@ -545,19 +503,6 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : FHS_FUSED_MIN_BLOCKS) degrid_
         if (lane == 0) s_red[warp] = v;
     }
     __syncthreads();
-    if (dense) {
-        for (int q = threadIdx.x; q < kWin * kWin; q += blockDim.x) {
-            const float re = s_re[q], im = s_im[q];
-            if (re != 0.f || im != 0.f) {
-                const int r = q / kWin, c = q - r * kWin;
-                int k1 = wy0 + r;
-                while (k1 >= K1) k1 -= K1;
-                int k2 = wx0 + c;
-                while (k2 >= K2) k2 -= K2;
-                red_add_f2(gb + (long long)k1 * K2 + k2, make_float2(re, im));
-            }
-        }
-    }
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < kWarps; ++w) t += s_red[w];
@@ -629,13 +574,27 @@ cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_degrid_grid_fused(fhs_problem *p, cudaStream_t s) {
+// The data term in two passes: the dual pre-update with the block norms
+// (kDual), then, once the l2-ball factors s_b are known, the scatter of
+// s_b d into the channel grids (kScatter with blk_scale), with no per-block
+// grids to combine.
+cudaError_t launch_data_dual(fhs_problem *p, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
     const WindowMap tm = window_map(p, p->grid_work);
-    (p->rank > 1 ? degrid_grid_binned_kernel<kFused, true> : degrid_grid_binned_kernel<kFused, false>)<<<p->n_bin, 256, 0, s>>>(p->meta, p->fptr, p->gfac, p->y, p->dvis, p->bin_start,
-                                                       p->bin_seg, p->bin_tile, p->ntx, p->B, p->blk_scale,
-                                                       p->blk_norm2, p->grid_work, p->grid_blk, p->K, p->K1, p->K2,
-                                                       float(p->sigma2), p->rank, tm.map, tm.ok, p->dev_err);
+    (p->rank > 1 ? degrid_grid_binned_kernel<kDual, true> : degrid_grid_binned_kernel<kDual, false>)<<<p->n_bin, 256, 0, s>>>(
+        p->meta, p->fptr, p->gfac, p->y, p->dvis, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B, p->blk_scale,
+        p->blk_norm2, p->grid_work, nullptr, p->K, p->K1, p->K2, float(p->sigma2), p->rank, tm.map, tm.ok,
+        p->dev_err);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_data_scatter(fhs_problem *p, cudaStream_t s) {
+    if (p->n_bin == 0) return cudaSuccess;
+    const WindowMap tm{};
+    (p->rank > 1 ? degrid_grid_binned_kernel<kScatter, true> : degrid_grid_binned_kernel<kScatter, false>)<<<p->n_bin, 256, 0, s>>>(
+        p->meta, p->fptr, p->gfac, nullptr, p->dvis, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B,
+        p->blk_scale, nullptr, nullptr, p->grid_work, p->K, p->K1, p->K2, 0.f, p->rank, tm.map, tm.ok, p->dev_err);
     p->n_launch += 1;
     return cudaGetLastError();
 }

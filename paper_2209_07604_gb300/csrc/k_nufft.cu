@@ -143,38 +143,6 @@ __global__ void block_finalize_kernel(double *blk_norm2, const double *eps, floa
     blk_norm2[s] = 0.0;
 }
 
-// grid_work[l] = sum_b s_{l,b} grid_blk[l][b]; grid_blk <- 0.  float4 = 2 cells;
-// blockIdx.y is the channel.  All B loads are issued before any store so they
-// overlap (the zero stores would otherwise order them).
-template <int MAXB>
-__global__ void __launch_bounds__(256) combine_kernel(float4 *__restrict__ blk, float4 *__restrict__ out,
-                                                      const float *__restrict__ blk_scale, int B, long long K4) {
-    const int l = blockIdx.y;
-    float sc[MAXB];
-#pragma unroll
-    for (int b = 0; b < MAXB; ++b) sc[b] = (b < B) ? blk_scale[l * B + b] : 0.f;
-    float4 *base = blk + (long long)l * B * K4;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < K4; k += (long long)gridDim.x * blockDim.x) {
-        float4 v[MAXB];
-#pragma unroll
-        for (int b = 0; b < MAXB; ++b)
-            if (b < B) v[b] = __ldcs(base + (long long)b * K4 + k);
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int b = 0; b < MAXB; ++b)
-            if (b < B) {
-                acc.x = fmaf(sc[b], v[b].x, acc.x);
-                acc.y = fmaf(sc[b], v[b].y, acc.y);
-                acc.z = fmaf(sc[b], v[b].z, acc.z);
-                acc.w = fmaf(sc[b], v[b].w, acc.w);
-            }
-        out[(long long)l * K4 + k] = acc;
-#pragma unroll
-        for (int b = 0; b < MAXB; ++b)
-            if (b < B) __stcs(base + (long long)b * K4 + k, make_float4(0.f, 0.f, 0.f, 0.f));
-    }
-}
-
 // Z: grid[(n mod K)] = x_n s1(n1) s2(n2) (zero cells elsewhere are left as is).
 __global__ void zpad_kernel(const float *__restrict__ x, float2 *__restrict__ grid, const float *__restrict__ s1,
                             const float *__restrict__ s2, int ny, int nx, int K1, int K2, long long K) {
@@ -399,19 +367,6 @@ cudaError_t launch_crop(fhs_problem *p, const float2 *grid, float *x, cudaStream
 cudaError_t launch_block_finalize(fhs_problem *p, cudaStream_t s) {
     block_finalize_kernel<<<(p->n_seg + 127) / 128, 128, 0, s>>>(p->blk_norm2, p->eps, p->blk_scale, p->n_seg,
                                                                  p->sigma2);
-    p->n_launch += 1;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_combine(fhs_problem *p, cudaStream_t s) {
-    const long long K4 = p->K / 2;
-    dim3 g(grid_for(K4, 256, 152 * 8 / p->L + 1), p->L);
-    float4 *blk = reinterpret_cast<float4 *>(p->grid_blk), *out = reinterpret_cast<float4 *>(p->grid_work);
-    if (p->B <= 2) combine_kernel<2><<<g, 256, 0, s>>>(blk, out, p->blk_scale, p->B, K4);
-    else if (p->B <= 4) combine_kernel<4><<<g, 256, 0, s>>>(blk, out, p->blk_scale, p->B, K4);
-    else if (p->B <= 8) combine_kernel<8><<<g, 256, 0, s>>>(blk, out, p->blk_scale, p->B, K4);
-    else if (p->B <= 16) combine_kernel<16><<<g, 256, 0, s>>>(blk, out, p->blk_scale, p->B, K4);
-    else return cudaErrorInvalidValue;
     p->n_launch += 1;
     return cudaGetLastError();
 }
