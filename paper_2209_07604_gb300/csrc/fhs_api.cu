@@ -916,6 +916,7 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
     if ((st = guard(dev_alloc(p, &p->meta, Mtot, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->fptr, Mtot + 1, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->gfac, p->n_fac, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->gmax, Mtot, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->y, Mtot, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->dvis, Mtot))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->vis_tmp, Mtot))) != FHS_OK) return st;
@@ -1006,7 +1007,7 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
         if ((st = guard(dev_alloc(p, &cnt, L))) != FHS_OK) return st;
         std::vector<unsigned long long> hc(L);
         cudaError_t e = launch_dr_diag(p, diag, s);
-        if (e == cudaSuccess) e = launch_grid(p, p->y, p->dr_u, s);
+        if (e == cudaSuccess) e = launch_grid(p, p->y, p->dr_u, s, false);
         if (e == cudaSuccess) e = launch_dr_setup(p, diag, p->dr_u, cnt, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), cnt, sizeof(unsigned long long) * L, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1225,7 +1226,8 @@ fhs_status fhs_estimate_bytes(const fhs_params *params, const double *w, int64_t
     nuc *= C;
     const long long Q = (long long)fac.size();
     long long r = 0;
-    r += 8 * M + 8 * (M + 1) + 8 * n_fac + 8 * M * 4;                // meta, factor offsets, G factors, y, d, scratch, perm
+    r += 8 * M + 8 * (M + 1) + 8 * n_fac + 8 * M * 4 + 4 * M;        // meta, factor offsets, G factors, y, d, scratch,
+                                                                     // perm, row bounds
     r += 8 * (nseg + 1) + 8 * nseg + 8 * nseg + 4 * nseg;            // segments, norms, eps, scales
     r += 8 * (nbin + 1) + 8 * nbin + 8 * (nchunk + 1) + 4 * nchunk;  // bins and chunks
     r += 4 * (q.ny + q.nx);                                          // Z scaling

@@ -83,6 +83,7 @@ struct fhs_problem {
     int2 *meta = nullptr;                     // {c1 | c2 << 16, T}
     long long *fptr = nullptr;                // [Mtot+1] offsets of the row factors
     float2 *gfac = nullptr;                   // [n_fac] per row: g1 / sigma (T values), g2 (T values)
+    float *gmax = nullptr;                    // [Mtot] max |g1| max |g2| per single-term row
     float2 *y = nullptr;                      // whitened data
     float2 *dvis = nullptr;                   // data dual storage d (v = scale_b d)
     long long *perm = nullptr;                // sorted -> caller index
@@ -194,7 +195,9 @@ cudaError_t launch_build_g(fhs_problem *p, const double2 *kap, const short *plan
                            const double2 *dde, int ext, const double *inv_sigma_seg, cudaStream_t s);
 cudaError_t launch_zpad(fhs_problem *p, const float *x, float2 *grid, cudaStream_t s);
 cudaError_t launch_degrid(fhs_problem *p, const float2 *grid, float2 *vis_sorted, cudaStream_t s);
-cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s);
+// fixed: dense bins accumulate their window in 32-bit fixed point (see k_binned.cu); false keeps
+// FP32 atomics (the gridding of the data reduction, whose faint cells are weighted up by Lambda).
+cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s, bool fixed = true);
 cudaError_t launch_crop(fhs_problem *p, const float2 *grid, float *x, cudaStream_t s);
 cudaError_t launch_data_dual(fhs_problem *p, cudaStream_t s);      // dual pre-update + block norms
 cudaError_t launch_data_scatter(fhs_problem *p, cudaStream_t s);   // grid_work += G^H (s_b d)

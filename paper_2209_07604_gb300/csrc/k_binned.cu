@@ -70,6 +70,9 @@ struct Kahan {
 // grid += conj(G_i) (G_i . Xhat), for the operator-norm estimate).
 enum { kDual = 0, kGather = 1, kScatter = 2, kNormal = 3 };
 
+constexpr float kFixMagic = 12582912.f;          // 1.5 * 2^23
+constexpr int kFixMagicBits = 0x4B400000;        // its bit pattern
+
 // Scatter of rows i = i0, i0 + kWarps, ... of one bin by one warp,
 // grid += conj(G_i) s_d[i].  DENSE: the box lies in the shared window (shared
 // atomics); otherwise global reductions.
@@ -78,11 +81,19 @@ enum { kDual = 0, kGather = 1, kScatter = 2, kNormal = 3 };
 // lane % 16) owns box column col and rows t1 = half, half + 2, ...; it adds
 // conj(g1[t1]) (conj(g2[col]) d) to those cells.  The next row's factors are
 // loaded while the current row is scattered.
-template <bool DENSE>
+//
+// FIXED (dense bins): the window accumulates in 32-bit fixed point, with
+// native integer shared atomics (a float shared atomic costs about 3.5 times
+// as much).  A contribution c is converted as round(c S) by one FMA with
+// 1.5 * 2^23 (the sum lands in [2^23, 2^24), whose unit is 1, so its low
+// mantissa bits are the integer; valid for |c S| < 2^22).  S = 2^(21 - e)
+// with bound < 2^e, and bound >= |every contribution of the bin|, so |c S| <
+// 2^21 and a cell's sum of at most kBinMax contributions stays below 2^30.
+template <bool DENSE, bool FIXED>
 __device__ __forceinline__ void scatter_rows(int i0, int nv, int lane, const int2 *s_meta, const int *s_off,
                                              const float2 *s_d, const float2 *__restrict__ fbin, float *s_re,
                                              float *s_im, int wy0, int wx0, float2 *__restrict__ gb, int K1,
-                                             int K2) {
+                                             int K2, float fs) {
     constexpr unsigned FULL = 0xffffffffu;
     const int half = lane >> 4, col = lane & 15;
     float2 fac = make_float2(0.f, 0.f);
@@ -114,7 +125,12 @@ __device__ __forceinline__ void scatter_rows(int i0, int nv, int lane, const int
             const float g1x = __shfl_sync(FULL, fac.x, t1), g1y = __shfl_sync(FULL, fac.y, t1);
             if (cin && t1 < T) {
                 const float pr = fmaf(g1x, er, g1y * ei), pi = fmaf(g1x, ei, -g1y * er);
-                if (DENSE) {
+                if (DENSE && FIXED) {
+                    atomicAdd(reinterpret_cast<int *>(s_re) + ib + 2 * k * kWin,
+                              __float_as_int(fmaf(pr, fs, kFixMagic)) - kFixMagicBits);
+                    atomicAdd(reinterpret_cast<int *>(s_im) + ib + 2 * k * kWin,
+                              __float_as_int(fmaf(pi, fs, kFixMagic)) - kFixMagicBits);
+                } else if (DENSE) {
                     atomicAdd(s_re + ib + 2 * k * kWin, pr);
                     atomicAdd(s_im + ib + 2 * k * kWin, pi);
                 } else {
@@ -381,7 +397,8 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : FHS_F
     const int *__restrict__ bin_seg, const int *__restrict__ bin_tile, int ntx, int B,
     const float *__restrict__ blk_scale, double *__restrict__ blk_norm2, const float2 *__restrict__ grid,
     float2 *__restrict__ grid_out, long long K, int K1, int K2, float sigma2, int R_,
-    const __grid_constant__ CUtensorMap tmap, int use_tma, int *__restrict__ err) {
+    const __grid_constant__ CUtensorMap tmap, int use_tma, const float *__restrict__ gmax, int allow_fixed,
+    int *__restrict__ err) {
     const int R = MULTI ? R_ : 1;
     __shared__ alignas(128) float2 s_grid[kWin * kWinP];
     __shared__ alignas(8) uint64_t s_bar;
@@ -392,6 +409,7 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : FHS_F
     __shared__ float2 s_y[kBinMax];       // sigma2 * y
     __shared__ float2 s_d[kBinMax];
     __shared__ double s_red[kWarps];
+    __shared__ int s_bound, s_bad;        // fixed-point scatter: bin bound (float bits), non-finite flag
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bin = blockIdx.x;
     const int seg = bin_seg[bin];
@@ -417,6 +435,10 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : FHS_F
             const float2 dd = dvis[v0 + i];
             s_d[i] = make_float2(vsc * dd.x, vsc * dd.y);
         }
+    }
+    if (threadIdx.x == 0) {
+        s_bound = 0;
+        s_bad = 0;
     }
     const bool dense = tile >= 0;
     int wy0 = 0, wx0 = 0;
@@ -468,24 +490,60 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : FHS_F
                                       dvis + v0, nrm);
     }
     // phase 2: scatters of conj(G_i) s_d[i], one row per warp
+    bool fixed = false;
+    float fs = 1.f, finv = 1.f;
     if (MODE == kScatter || MODE == kNormal) {
         if (MODE == kNormal) __syncthreads();        // s_d holds the gathered values
+        // fixed point in the scatter (Phi^H and the data term's scatter pass) when allowed; the
+        // normal-mode pass and the gridding of the data reduction keep the float atomics: their
+        // output is weighted by Lambda and the faint, sparsely covered cells need their own
+        // relative precision, which a quantum set by the bin's brightest contribution does not give
+        if (!MULTI && dense && MODE == kScatter && allow_fixed) {
+            // the bin's bound of |contribution|: max_i |s_d[i]| max|g1_i| max|g2_i|
+            float m = 0.f;
+            bool bad = false;
+            for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+                const float2 d = s_d[i];
+                bad |= !(isfinite(d.x) && isfinite(d.y));
+                m = fmaxf(m, sqrtf(fmaf(d.x, d.x, d.y * d.y)) * gmax[v0 + i]);
+            }
+            if (m > 0.f) atomicMax(&s_bound, __float_as_int(m));   // non-negative floats order as integers
+            if (bad) s_bad = 1;
+            __syncthreads();
+            const float bound = __int_as_float(s_bound);
+            int e = 0;
+            if (bound > 0.f) frexpf(bound, &e);             // bound < 2^e
+            // fixed point unless a value is not finite or the bin is so faint (bound < 2^-100)
+            // that 2^(21 - e) would overflow: those bins keep the float atomics
+            if (!s_bad && isfinite(bound) && e >= -100) {
+                fixed = true;
+                fs = ldexpf(1.f, 21 - e);
+                finv = ldexpf(1.f, e - 21);
+            }
+        }
         if (MULTI) {
             if (dense)
                 scatter_rows_rank<true>(warp, nv, lane, R, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1, K2);
             else
                 scatter_rows_rank<false>(warp, nv, lane, R, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1,
                                          K2);
-        } else if (dense)
-            scatter_rows<true>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1, K2);
+        } else if (dense && fixed)
+            scatter_rows<true, true>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1, K2, fs);
+        else if (dense)
+            scatter_rows<true, false>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1, K2, fs);
         else
-            scatter_rows<false>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1, K2);
+            scatter_rows<false, false>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1, K2,
+                                       fs);
     }
     if (MODE != kDual) {
         if ((MODE == kScatter || MODE == kNormal) && dense) {
             __syncthreads();
             for (int q = threadIdx.x; q < kWin * kWin; q += blockDim.x) {
-                const float re = s_re[q], im = s_im[q];
+                float re = s_re[q], im = s_im[q];
+                if (fixed) {
+                    re = float(__float_as_int(re)) * finv;     // exact scaling by a power of two
+                    im = float(__float_as_int(im)) * finv;
+                }
                 if (re != 0.f || im != 0.f) {
                     const int r = q / kWin, c = q - r * kWin;
                     int k1 = wy0 + r;
@@ -551,17 +609,17 @@ cudaError_t launch_degrid(fhs_problem *p, const float2 *grid, float2 *vis_sorted
     const WindowMap tm = window_map(p, grid);
     (p->rank > 1 ? degrid_grid_binned_kernel<kGather, true> : degrid_grid_binned_kernel<kGather, false>)<<<p->n_bin, 256, 0, s>>>(
         p->meta, p->fptr, p->gfac, nullptr, vis_sorted, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B,
-        nullptr, nullptr, grid, nullptr, p->K, p->K1, p->K2, 0.f, p->rank, tm.map, tm.ok, p->dev_err);
+        nullptr, nullptr, grid, nullptr, p->K, p->K1, p->K2, 0.f, p->rank, tm.map, tm.ok, p->gmax, 0, p->dev_err);
     p->n_launch += 1;
     return cudaGetLastError();
 }
 
-cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s) {
+cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s, bool fixed) {
     if (p->n_bin == 0) return cudaSuccess;
     const WindowMap tm{};                        // no forward window to stage
     (p->rank > 1 ? degrid_grid_binned_kernel<kScatter, true> : degrid_grid_binned_kernel<kScatter, false>)<<<p->n_bin, 256, 0, s>>>(
         p->meta, p->fptr, p->gfac, nullptr, const_cast<float2 *>(vis_sorted), p->bin_start, p->bin_seg,
-        p->bin_tile, p->ntx, p->B, nullptr, nullptr, nullptr, grid, p->K, p->K1, p->K2, 0.f, p->rank, tm.map, tm.ok, p->dev_err);
+        p->bin_tile, p->ntx, p->B, nullptr, nullptr, nullptr, grid, p->K, p->K1, p->K2, 0.f, p->rank, tm.map, tm.ok, p->gmax, fixed ? 1 : 0, p->dev_err);
     p->n_launch += 1;
     return cudaGetLastError();
 }
@@ -571,7 +629,7 @@ cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, 
     const WindowMap tm = window_map(p, grid);
     (p->rank > 1 ? degrid_grid_binned_kernel<kNormal, true> : degrid_grid_binned_kernel<kNormal, false>)<<<p->n_bin, 256, 0, s>>>(
         p->meta, p->fptr, p->gfac, nullptr, nullptr, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B, nullptr,
-        nullptr, grid, grid_out, p->K, p->K1, p->K2, 0.f, p->rank, tm.map, tm.ok, p->dev_err);
+        nullptr, grid, grid_out, p->K, p->K1, p->K2, 0.f, p->rank, tm.map, tm.ok, p->gmax, 0, p->dev_err);
     p->n_launch += 1;
     return cudaGetLastError();
 }
@@ -586,7 +644,7 @@ cudaError_t launch_data_dual(fhs_problem *p, cudaStream_t s) {
     (p->rank > 1 ? degrid_grid_binned_kernel<kDual, true> : degrid_grid_binned_kernel<kDual, false>)<<<p->n_bin, 256, 0, s>>>(
         p->meta, p->fptr, p->gfac, p->y, p->dvis, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B, p->blk_scale,
         p->blk_norm2, p->grid_work, nullptr, p->K, p->K1, p->K2, float(p->sigma2), p->rank, tm.map, tm.ok,
-        p->dev_err);
+        p->gmax, 0, p->dev_err);
     p->n_launch += 1;
     return cudaGetLastError();
 }
@@ -596,7 +654,7 @@ cudaError_t launch_data_scatter(fhs_problem *p, cudaStream_t s) {
     const WindowMap tm{};
     (p->rank > 1 ? degrid_grid_binned_kernel<kScatter, true> : degrid_grid_binned_kernel<kScatter, false>)<<<p->n_bin, 256, 0, s>>>(
         p->meta, p->fptr, p->gfac, nullptr, p->dvis, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B,
-        p->blk_scale, nullptr, nullptr, p->grid_work, p->K, p->K1, p->K2, 0.f, p->rank, tm.map, tm.ok, p->dev_err);
+        p->blk_scale, nullptr, nullptr, p->grid_work, p->K, p->K1, p->K2, 0.f, p->rank, tm.map, tm.ok, p->gmax, 1, p->dev_err);
     p->n_launch += 1;
     return cudaGetLastError();
 }

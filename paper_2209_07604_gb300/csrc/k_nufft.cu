@@ -59,12 +59,14 @@ __device__ __forceinline__ int seg_of(const long long *seg_off, int n_seg, long 
 // terms: G[a][b] = sum_r A_r[a] B_r[b], A_r[a] = g1[a - r],
 // B_r[b] = sum_j D[r][j] g2[b - j] (out-of-range taps zero).  Term r is
 // stored at offset 2 T r as T values of A_r followed by T values of B_r.
+// gmax[v] = max |g1| max |g2| of a single-term row (an upper bound of its
+// entries, for the fixed-point scatter; 0 for DDE rows).
 __global__ void __launch_bounds__(256) build_g_kernel(
     const int2 *__restrict__ meta, const long long *__restrict__ fptr, float2 *__restrict__ gfac,
     const double2 *__restrict__ kap, const short *__restrict__ plane, const double2 *__restrict__ wk,
     const double2 *__restrict__ dde, int ext,
     const long long *__restrict__ seg_off, int n_seg, const double *__restrict__ inv_sigma_seg,
-    long long Mtot, int J, double beta, double inv_i0b) {
+    long long Mtot, int J, double beta, double inv_i0b, float *__restrict__ gmax) {
     __shared__ double s_kb[kWarps][2][16];
     __shared__ double2 s_g[kWarps][2][16];
     __shared__ double s_c[kI0Terms];          // 1 / (k!)^2
@@ -90,6 +92,7 @@ __global__ void __launch_bounds__(256) build_g_kernel(
         if (i < J) s_kb[warp][dim][i] = kb_eval(kd - double(p0 + i), J, beta, inv_i0b, s_c);
         __syncwarp();
         const int pl = plane[v];
+        float gm = 0.f;                          // |factor value| as stored (FP32)
         if (i < Tb) {
             double2 acc = make_double2(0.0, 0.0);
             for (int jj = 0; jj < S; ++jj) {
@@ -103,9 +106,18 @@ __global__ void __launch_bounds__(256) build_g_kernel(
             const double f = dim ? 1.0 : inv_sigma_seg[seg_of(seg_off, n_seg, v)];
             acc.x *= f;
             acc.y *= f;
-            if (dde) s_g[warp][dim][i] = acc;
-            else gfac[fptr[v] + dim * T + i] = make_float2(float(acc.x), float(acc.y));
+            if (dde) {
+                s_g[warp][dim][i] = acc;
+            } else {
+                const float2 g = make_float2(float(acc.x), float(acc.y));
+                gfac[fptr[v] + dim * T + i] = g;
+                gm = sqrtf(fmaf(g.x, g.x, g.y * g.y));
+            }
         }
+        // bound of every entry of a single-term row: max |g1| max |g2| (lanes 0-15: g1, 16-31: g2)
+        for (int o = 8; o > 0; o >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+        const float gm2 = __shfl_sync(0xffffffffu, gm, 16);
+        if (lane == 0) gmax[v] = dde ? 0.f : gm * gm2;
         if (dde) {
             __syncwarp();
             const double2 *D = dde + v * (kDdeTaps * kDdeTaps);
@@ -345,7 +357,7 @@ cudaError_t launch_build_g(fhs_problem *p, const double2 *kap, const short *plan
     const double beta = kb_beta(p->J, 2.0);
     build_g_kernel<<<grid_for(p->Mtot, kWarps, 152 * 64), 256, 0, s>>>(
         p->meta, p->fptr, p->gfac, kap, plane, wk_table, dde, ext, p->d_seg_off, p->n_seg, inv_sigma_seg, p->Mtot,
-        p->J, beta, 1.0 / bessel_i0(beta));
+        p->J, beta, 1.0 / bessel_i0(beta), p->gmax);
     p->n_launch += 1;
     return cudaGetLastError();
 }
