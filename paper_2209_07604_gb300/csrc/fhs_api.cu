@@ -247,11 +247,11 @@ fhs_status apply_normal(fhs_problem *p, const float *v, float *y, cudaStream_t s
     CU(launch_zpad(p, v, p->grid_in, s));
     TRY(fft(p, p->grid_in, p->grid_aux, CUFFT_FORWARD, s));
     if (p->dr) {
-        CU(launch_normal(p, p->grid_aux, p->dr_u, s));
+        CU(launch_normal(p, p->grid_aux, p->dr_u, s, false));
         CU(launch_dr_combine(p, p->dr_u, 0.f, 1.f, p->dr_w, s));
-        CU(launch_normal(p, p->dr_w, scratch, s));
+        CU(launch_normal(p, p->dr_w, scratch, s, false));
     } else {
-        CU(launch_normal(p, p->grid_aux, scratch, s));
+        CU(launch_normal(p, p->grid_aux, scratch, s, true));
     }
     TRY(fft(p, scratch, scratch, CUFFT_INVERSE, s));
     CU(launch_crop(p, scratch, y, s));
@@ -265,7 +265,7 @@ fhs_status dirty_image(fhs_problem *p, float *x, cudaStream_t s) {
     if (!p->dr) return adjoint_to_image(p, p->y, x, s);
     CU(launch_dr_combine(p, nullptr, 1.f, 0.f, p->dr_w, s));
     CU(cudaMemsetAsync(p->grid_aux, 0, sizeof(float2) * p->K * p->L, s));
-    CU(launch_normal(p, p->dr_w, p->grid_aux, s));
+    CU(launch_normal(p, p->dr_w, p->grid_aux, s, false));
     TRY(fft(p, p->grid_aux, p->grid_aux, CUFFT_INVERSE, s));
     CU(launch_crop(p, p->grid_aux, x, s));
     return FHS_OK;
@@ -517,7 +517,7 @@ fhs_status one_iteration(fhs_problem *p, cudaStream_t s) {
     }
     {
         Phase ph(p, s, FHS_PHASE_DEGRID_GRID);
-        if (p->dr) CU(launch_normal(p, p->grid_work, p->dr_u, s));     // H Xhat
+        if (p->dr) CU(launch_normal(p, p->grid_work, p->dr_u, s, false));     // H Xhat
         else CU(launch_data_dual(p, s));                               // d, block norms
     }
     if (fork) {
@@ -533,7 +533,7 @@ fhs_status one_iteration(fhs_problem *p, cudaStream_t s) {
             CU(launch_dr_finalize(p, s));
         }
         Phase ph(p, s, FHS_PHASE_DEGRID_GRID);
-        CU(launch_normal(p, p->dr_w, p->grid_work, s));
+        CU(launch_normal(p, p->dr_w, p->grid_work, s, false));
     } else {
         // l2-ball factors, then G^H (s_b d) straight into the channel grids
         {
@@ -1342,12 +1342,12 @@ fhs_status fhs_residual(fhs_problem *p, const float *x_dev, float *r_dev, void *
         if (x_dev) {
             CU(launch_zpad(p, x_dev, p->grid_in, s));
             TRY(fft(p, p->grid_in, p->grid_aux, CUFFT_FORWARD, s));
-            CU(launch_normal(p, p->grid_aux, p->dr_u, s));
+            CU(launch_normal(p, p->grid_aux, p->dr_u, s, false));
             u = p->dr_u;
         }
         CU(launch_dr_combine(p, u, 1.f, -1.f, p->dr_w, s));
         CU(cudaMemsetAsync(p->grid_aux, 0, sizeof(float2) * p->K * p->L, s));
-        CU(launch_normal(p, p->dr_w, p->grid_aux, s));
+        CU(launch_normal(p, p->dr_w, p->grid_aux, s, false));
         TRY(fft(p, p->grid_aux, p->grid_aux, CUFFT_INVERSE, s));
         CU(launch_crop(p, p->grid_aux, r_dev, s));
         CU(launch_chan_scale(p, r_dev, p->eta, s));
@@ -1378,7 +1378,7 @@ fhs_status fhs_noise_from_model(fhs_problem *p, const float *x0_dev, int32_t app
         if (p->dr) {
             CU(launch_zpad(p, x0_dev, p->grid_in, s));
             TRY(fft(p, p->grid_in, p->grid_aux, CUFFT_FORWARD, s));
-            CU(launch_normal(p, p->grid_aux, p->dr_u, s));
+            CU(launch_normal(p, p->grid_aux, p->dr_u, s, false));
             CU(launch_dr_resid_norm(p, st, s));
         } else {
             TRY(forward_from_image(p, x0_dev, p->vis_tmp, s));
@@ -1521,7 +1521,7 @@ fhs_status fhs_set_state(fhs_problem *p, int32_t part, const float *src, void *s
                 CU(cudaMemcpyAsync(p->dr_v, src, b, cudaMemcpyDeviceToDevice, s));
                 CU(launch_dr_weight(p, s));
                 CU(cudaMemsetAsync(p->grid_work, 0, sizeof(float2) * p->K * p->L, s));
-                CU(launch_normal(p, p->dr_w, p->grid_work, s));
+                CU(launch_normal(p, p->dr_w, p->grid_work, s, false));
                 TRY(fft(p, p->grid_work, p->grid_work, CUFFT_INVERSE, s));
                 CU(cudaStreamSynchronize(s));
                 break;
@@ -1591,9 +1591,9 @@ fhs_status fhs_autotune_bins(fhs_problem *p, void *stream, int32_t *dense_min_ou
         p->bin_seg = b.seg;
         p->bin_tile = b.tile;
         p->n_bin = b.n;
-        CU(launch_normal(p, p->grid_aux, p->grid_scr, s));          // warm-up
+        CU(launch_normal(p, p->grid_aux, p->grid_scr, s, !p->dr));          // warm-up
         CU(cudaEventRecord(e0, s));
-        for (int r = 0; r < 3; ++r) CU(launch_normal(p, p->grid_aux, p->grid_scr, s));
+        for (int r = 0; r < 3; ++r) CU(launch_normal(p, p->grid_aux, p->grid_scr, s, !p->dr));
         CU(cudaEventRecord(e1, s));
         CU(cudaEventSynchronize(e1));
         CU(cudaEventElapsedTime(&ms, e0, e1));

@@ -201,7 +201,8 @@ cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, 
 cudaError_t launch_crop(fhs_problem *p, const float2 *grid, float *x, cudaStream_t s);
 cudaError_t launch_data_dual(fhs_problem *p, cudaStream_t s);      // dual pre-update + block norms
 cudaError_t launch_data_scatter(fhs_problem *p, cudaStream_t s);   // grid_work += G^H (s_b d)
-cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, cudaStream_t s);
+// fixed: as for launch_grid; the passes of the data reduction use false.
+cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, cudaStream_t s, bool fixed);
 // One Lanczos step after y = A v: y <- w, vprev <- v_{j+1}; alpha_j[l] and
 // nb2_j[L + l] (= beta_{j+1}^2) accumulate, nb2_j[l] = beta_j^2 is read.
 cudaError_t launch_lanczos_step(fhs_problem *p, float *y, float *vprev, const float *v, double *alpha_j,

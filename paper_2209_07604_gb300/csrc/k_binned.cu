@@ -494,11 +494,12 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : FHS_F
     float fs = 1.f, finv = 1.f;
     if (MODE == kScatter || MODE == kNormal) {
         if (MODE == kNormal) __syncthreads();        // s_d holds the gathered values
-        // fixed point in the scatter (Phi^H and the data term's scatter pass) when allowed; the
-        // normal-mode pass and the gridding of the data reduction keep the float atomics: their
-        // output is weighted by Lambda and the faint, sparsely covered cells need their own
-        // relative precision, which a quantum set by the bin's brightest contribution does not give
-        if (!MULTI && dense && MODE == kScatter && allow_fixed) {
+        // fixed point in the scatter when the caller allows it (Phi^H, the data term's scatter pass,
+        // the normal-mode pass of the norm estimate); the passes of the data reduction keep the
+        // float atomics: their output is weighted by Lambda and the faint, sparsely covered cells
+        // need their own relative precision, which a quantum set by the bin's brightest
+        // contribution does not give
+        if (!MULTI && dense && allow_fixed) {
             // the bin's bound of |contribution|: max_i |s_d[i]| max|g1_i| max|g2_i|
             float m = 0.f;
             bool bad = false;
@@ -624,12 +625,12 @@ cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, cudaStream_t s) {
+cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, cudaStream_t s, bool fixed) {
     if (p->n_bin == 0) return cudaSuccess;
     const WindowMap tm = window_map(p, grid);
     (p->rank > 1 ? degrid_grid_binned_kernel<kNormal, true> : degrid_grid_binned_kernel<kNormal, false>)<<<p->n_bin, 256, 0, s>>>(
         p->meta, p->fptr, p->gfac, nullptr, nullptr, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B, nullptr,
-        nullptr, grid, grid_out, p->K, p->K1, p->K2, 0.f, p->rank, tm.map, tm.ok, p->gmax, 0, p->dev_err);
+        nullptr, grid, grid_out, p->K, p->K1, p->K2, 0.f, p->rank, tm.map, tm.ok, p->gmax, fixed ? 1 : 0, p->dev_err);
     p->n_launch += 1;
     return cudaGetLastError();
 }
