@@ -373,11 +373,10 @@ __device__ __forceinline__ bool window_wait(uint64_t *bar) {
     return false;
 }
 
-// Four CTAs per SM (64 registers, 46 KB shared each): the kernel is latency
-// bound, and occupancy matters more than the registers the cap takes away.
-#ifndef FHS_FUSED_MIN_BLOCKS
-#define FHS_FUSED_MIN_BLOCKS 4
-#endif
+// Four CTAs per SM for the gathering passes (64 registers; their per-thread
+// gathers spill below that): the passes are latency bound, and occupancy
+// matters more than the registers the cap takes away.
+constexpr int kGatherMinBlocks = 4;
 // MODE kDual: dvis is the data dual d (read and written), grid the forward
 // grid, blk_scale the factors s_b of the previous iteration, blk_norm2 receives
 // ||d_b||^2.  kGather: dvis receives Phi x, grid is the forward grid.
@@ -391,7 +390,7 @@ __device__ __forceinline__ bool window_wait(uint64_t *bar) {
 // scatter pass runs 6 CTAs per SM (40 registers, no spills: 3.5 % faster than
 // 5, while 8 spills).
 template <int MODE, bool MULTI>
-__global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : FHS_FUSED_MIN_BLOCKS)) degrid_grid_binned_kernel(
+__global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGatherMinBlocks)) degrid_grid_binned_kernel(
     const int2 *__restrict__ meta, const long long *__restrict__ fptr, const float2 *__restrict__ gfac,
     const float2 *__restrict__ y, float2 *__restrict__ dvis, const long long *__restrict__ bin_start,
     const int *__restrict__ bin_seg, const int *__restrict__ bin_tile, int ntx, int B,
