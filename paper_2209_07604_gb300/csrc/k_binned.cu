@@ -148,11 +148,12 @@ __device__ __forceinline__ void scatter_rows(int i0, int nv, int lane, const int
 // k_nufft.cu): one row per warp as in scatter_rows; each lane sums
 // conj(A_r[t1]) conj(B_r[col]) d over the terms in registers and adds each of
 // its cells once.
-template <bool DENSE>
+template <bool DENSE, bool FIXED>
 __device__ __forceinline__ void scatter_rows_rank(int i0, int nv, int lane, int R, const int2 *s_meta,
                                                   const int *s_off, const float2 *s_d,
                                                   const float2 *__restrict__ fbin, float *s_re, float *s_im,
-                                                  int wy0, int wx0, float2 *__restrict__ gb, int K1, int K2) {
+                                                  int wy0, int wx0, float2 *__restrict__ gb, int K1, int K2,
+                                                  float fs) {
     constexpr unsigned FULL = 0xffffffffu;
     const int half = lane >> 4, col = lane & 15;
     for (int i = i0; i < nv; i += kWarps) {
@@ -196,7 +197,12 @@ __device__ __forceinline__ void scatter_rows_rank(int i0, int nv, int lane, int 
         for (int k = 0; k < 8; ++k) {
             if (2 * k >= T) break;
             if (cin && 2 * k + half < T) {
-                if (DENSE) {
+                if (DENSE && FIXED) {
+                    atomicAdd(reinterpret_cast<int *>(s_re) + ib + 2 * k * kWin,
+                              __float_as_int(fmaf(accr[k], fs, kFixMagic)) - kFixMagicBits);
+                    atomicAdd(reinterpret_cast<int *>(s_im) + ib + 2 * k * kWin,
+                              __float_as_int(fmaf(acci[k], fs, kFixMagic)) - kFixMagicBits);
+                } else if (DENSE) {
                     atomicAdd(s_re + ib + 2 * k * kWin, accr[k]);
                     atomicAdd(s_im + ib + 2 * k * kWin, acci[k]);
                 } else {
@@ -498,7 +504,7 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
         // float atomics: their output is weighted by Lambda and the faint, sparsely covered cells
         // need their own relative precision, which a quantum set by the bin's brightest
         // contribution does not give
-        if (!MULTI && dense && allow_fixed) {
+        if (dense && allow_fixed) {
             // the bin's bound of |contribution|: max_i |s_d[i]| max|g1_i| max|g2_i|
             float m = 0.f;
             bool bad = false;
@@ -522,11 +528,15 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
             }
         }
         if (MULTI) {
-            if (dense)
-                scatter_rows_rank<true>(warp, nv, lane, R, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1, K2);
+            if (dense && fixed)
+                scatter_rows_rank<true, true>(warp, nv, lane, R, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb,
+                                              K1, K2, fs);
+            else if (dense)
+                scatter_rows_rank<true, false>(warp, nv, lane, R, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb,
+                                               K1, K2, fs);
             else
-                scatter_rows_rank<false>(warp, nv, lane, R, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1,
-                                         K2);
+                scatter_rows_rank<false, false>(warp, nv, lane, R, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb,
+                                                K1, K2, fs);
         } else if (dense && fixed)
             scatter_rows<true, true>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1, K2, fs);
         else if (dense)

@@ -59,8 +59,8 @@ __device__ __forceinline__ int seg_of(const long long *seg_off, int n_seg, long 
 // terms: G[a][b] = sum_r A_r[a] B_r[b], A_r[a] = g1[a - r],
 // B_r[b] = sum_j D[r][j] g2[b - j] (out-of-range taps zero).  Term r is
 // stored at offset 2 T r as T values of A_r followed by T values of B_r.
-// gmax[v] = max |g1| max |g2| of a single-term row (an upper bound of its
-// entries, for the fixed-point scatter; 0 for DDE rows).
+// gmax[v] bounds the row's entries for the fixed-point scatter: max |g1| max |g2|
+// of a single-term row, sum_r max |A_r| max |B_r| of a DDE row.
 __global__ void __launch_bounds__(256) build_g_kernel(
     const int2 *__restrict__ meta, const long long *__restrict__ fptr, float2 *__restrict__ gfac,
     const double2 *__restrict__ kap, const short *__restrict__ plane, const double2 *__restrict__ wk,
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256) build_g_kernel(
         // bound of every entry of a single-term row: max |g1| max |g2| (lanes 0-15: g1, 16-31: g2)
         for (int o = 8; o > 0; o >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
         const float gm2 = __shfl_sync(0xffffffffu, gm, 16);
-        if (lane == 0) gmax[v] = dde ? 0.f : gm * gm2;
+        if (lane == 0 && !dde) gmax[v] = gm * gm2;
         if (dde) {
             __syncwarp();
             const double2 *D = dde + v * (kDdeTaps * kDdeTaps);
@@ -139,6 +139,20 @@ __global__ void __launch_bounds__(256) build_g_kernel(
                 }
                 gfac[fptr[v] + e] = make_float2(float(val.x), float(val.y));
             }
+            // bound of every entry of the row: sum_r max |A_r| max |B_r| (lane r < kDdeTaps)
+            __syncwarp();
+            float bt = 0.f;
+            if (lane < kDdeTaps) {
+                const float2 *f = gfac + fptr[v] + lane * 2 * T;
+                float ma = 0.f, mb = 0.f;
+                for (int q = 0; q < T; ++q) {
+                    ma = fmaxf(ma, sqrtf(fmaf(f[q].x, f[q].x, f[q].y * f[q].y)));
+                    mb = fmaxf(mb, sqrtf(fmaf(f[T + q].x, f[T + q].x, f[T + q].y * f[T + q].y)));
+                }
+                bt = ma * mb;
+            }
+            for (int o = 4; o > 0; o >>= 1) bt += __shfl_xor_sync(0xffffffffu, bt, o);
+            if (lane == 0) gmax[v] = bt;
         }
         __syncwarp();
     }
