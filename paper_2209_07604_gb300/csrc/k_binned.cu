@@ -14,6 +14,14 @@ namespace fhs {
 namespace {
 
 constexpr int kWarps = 8;               // warps per CTA
+// Columns of g2 a gathering thread holds in registers, and the CTAs per SM of
+// the gathering passes.  Measured at 1024^2 x 16 channels: 8 and 4 (64
+// registers) beat 4 and 5 (48 registers: 9 % slower) and 3 and 6 (40: 21 %):
+// narrower chunks pass over the box rows more often than the extra warps hide.
+#ifndef FHS_GATHER_COLS
+#define FHS_GATHER_COLS 8
+#endif
+constexpr int kGatherCols = FHS_GATHER_COLS;
 
 __device__ __forceinline__ void red_add_f2(float2 *addr, float2 v) {
     atomicAdd(addr, v);   // sm_90+: vector float2 reduction (red.global.add.v2.f32)
@@ -266,18 +274,22 @@ __device__ __forceinline__ void gather_cols(const float2 *__restrict__ f, int T,
 // four FMAs with every lane busy and no reduction across lanes.  Sides above 8
 // take two passes over the rows (8 columns of g2 in registers at a time, under
 // the 64-register cap).
+template <int C0, int TT, bool DENSE>
+__device__ __forceinline__ void gather_chunks(const float2 *__restrict__ f, int T, int t_lo, int t_hi, int c1,
+                                              int c2, const float2 *s_grid, int wy0, int wx0,
+                                              const float2 *__restrict__ gl, int K1, int K2, float &ar, float &ai) {
+    constexpr int CW = (TT - C0 < kGatherCols) ? TT - C0 : kGatherCols;
+    gather_cols<C0, CW, DENSE>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, gl, K1, K2, ar, ai);
+    if constexpr (C0 + CW < TT)
+        gather_chunks<C0 + CW, TT, DENSE>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, gl, K1, K2, ar, ai);
+}
+
 template <int TT, bool DENSE>
 __device__ __forceinline__ float2 gather_lane(const float2 *__restrict__ f, int T, int t_lo, int t_hi, int c1,
                                               int c2, const float2 *s_grid, int wy0, int wx0,
                                               const float2 *__restrict__ gl, int K1, int K2) {
     float ar = 0.f, ai = 0.f;
-    if (TT <= 8) {
-        gather_cols<0, TT, DENSE>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, gl, K1, K2, ar, ai);
-    } else {
-        gather_cols<0, 8, DENSE>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, gl, K1, K2, ar, ai);
-        gather_cols<8, (TT > 8 ? TT - 8 : 1), DENSE>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, gl, K1, K2, ar,
-                                                     ai);
-    }
+    gather_chunks<0, TT, DENSE>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, gl, K1, K2, ar, ai);
     return make_float2(ar, ai);
 }
 
@@ -382,7 +394,10 @@ __device__ __forceinline__ bool window_wait(uint64_t *bar) {
 // Four CTAs per SM for the gathering passes (64 registers; their per-thread
 // gathers spill below that): the passes are latency bound, and occupancy
 // matters more than the registers the cap takes away.
-constexpr int kGatherMinBlocks = 4;
+#ifndef FHS_GATHER_MIN_BLOCKS
+#define FHS_GATHER_MIN_BLOCKS 4
+#endif
+constexpr int kGatherMinBlocks = FHS_GATHER_MIN_BLOCKS;
 // MODE kDual: dvis is the data dual d (read and written), grid the forward
 // grid, blk_scale the factors s_b of the previous iteration, blk_norm2 receives
 // ||d_b||^2.  kGather: dvis receives Phi x, grid is the forward grid.
