@@ -391,9 +391,8 @@ __device__ __forceinline__ bool window_wait(uint64_t *bar) {
     return false;
 }
 
-// Four CTAs per SM for the gathering passes (64 registers; their per-thread
-// gathers spill below that): the passes are latency bound, and occupancy
-// matters more than the registers the cap takes away.
+// CTAs per SM of the gathering passes (4: 64 registers, what the 8-column
+// chunks need without spills).
 #ifndef FHS_GATHER_MIN_BLOCKS
 #define FHS_GATHER_MIN_BLOCKS 4
 #endif
