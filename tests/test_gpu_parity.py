@@ -372,3 +372,18 @@ def test_adjoint_precision_of_fixed_point_scatter(name):
     img = prob.adjoint(torch.tensor(np.concatenate(yw).astype(np.complex64), device="cuda")).cpu().numpy()
     assert rel(img, op.adjoint_all(yw)) < 5e-6
     prob.close()
+
+
+@pytest.mark.parametrize("scale", [1e-34, 1e-20, 1e20])
+def test_adjoint_scales_linearly_across_the_fixed_point_range(scale):
+    """Phi^H (s v) = s Phi^H v for scales that send the bins' bounds far from 1:
+    the fixed-point windows rescale per bin (2^(21 - e)), and bins fainter than
+    2^-100 fall back to FP32 atomics; both agree with the unscaled result."""
+    P = synth.make_problem("small_128")
+    prob = fhs.Problem.from_synth(P, mu=0.0, mu_bar=0.0, sigma2=1.0)
+    v = synth.random_vis((P.L, P.M), 3).reshape(-1)
+    ref = prob.adjoint(torch.tensor(v, dtype=torch.complex64, device="cuda")).cpu().numpy().astype(np.float64)
+    got = prob.adjoint(torch.tensor(v * scale, dtype=torch.complex64, device="cuda")).cpu().numpy()
+    assert np.all(np.isfinite(got))
+    assert rel(got / scale, ref) < 2e-6
+    prob.close()
