@@ -197,17 +197,22 @@ __global__ void __launch_bounds__(256) analysis_lj_kernel(const __grid_constant_
 // taken by consecutive threads, odd row strides), and a y-step thread
 // computes its four adjacent qy of one column from H + 3 samples per array.
 constexpr int kSynNQ = 4;
-template <int P>
-__device__ __forceinline__ void synthesis_tile_t(const SaraConst &c, int j, int m0y, int m0x, const float *coef_l,
-                                                 const float *ll_in, float (*sb)[SB_Y][SB_X + 2],
-                                                 float (*su)[SB_Y][STX + 1], float *acc) {
-    constexpr int F = 2 * P, H = P;
-    float h[F], g[F];
-#pragma unroll
-    for (int i = 0; i < F; ++i) {
-        h[i] = c.h[P][i];
-        g[i] = c.g[P][i];
-    }
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid) {
+    // 4-byte asynchronous copy to shared memory; zero-filled when !valid (nothing is read)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(static_cast<uint32_t>(
+                     __cvta_generic_to_shared(dst))),
+                 "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+
+// Stage the four level-j bands of db_P that an STY x STX output tile at
+// (m0y, m0x) reaches into sb (zero outside the band).  ASYNC: by cp.async
+// (the caller commits and waits), otherwise by plain loads.
+template <int P, bool ASYNC>
+__device__ __forceinline__ void synthesis_stage_t(const SaraConst &c, int j, int m0y, int m0x, const float *coef_l,
+                                                  const float *ll_in, float (*sb)[SB_Y][SB_X + 2]) {
+    constexpr int H = P;
     const int my = c.ny[P][j], mx = c.nx[P][j];
     const long long bs = (long long)my * mx;
     const int k0y = m0y / 2, k0x = m0x / 2;
@@ -216,20 +221,43 @@ __device__ __forceinline__ void synthesis_tile_t(const SaraConst &c, int j, int 
     for (int idx = threadIdx.x; idx < NBY * NBX; idx += blockDim.x) {
         const int r = idx / NBX, cc = idx - r * NBX;
         const int ky = k0y + r, kx = k0x + cc;
-        float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
-        if (ky < my && kx < mx) {
-            const long long o = (long long)ky * mx + kx;
-            v0 = ll_in[o];
-            v1 = det[o];
-            v2 = det[bs + o];
-            v3 = det[2 * bs + o];
+        const bool in = ky < my && kx < mx;
+        const long long o = in ? (long long)ky * mx + kx : 0;
+        if (ASYNC) {
+            cp_async4(&sb[0][r][cc], ll_in + o, in);    // LL  (y lo, x lo)
+            cp_async4(&sb[1][r][cc], det + o, in);      // LH  (y lo, x hi)
+            cp_async4(&sb[2][r][cc], det + bs + o, in); // HL  (y hi, x lo)
+            cp_async4(&sb[3][r][cc], det + 2 * bs + o, in);
+        } else {
+            sb[0][r][cc] = in ? ll_in[o] : 0.f;
+            sb[1][r][cc] = in ? det[o] : 0.f;
+            sb[2][r][cc] = in ? det[bs + o] : 0.f;
+            sb[3][r][cc] = in ? det[2 * bs + o] : 0.f;
         }
-        sb[0][r][cc] = v0;   // LL  (y lo, x lo)
-        sb[1][r][cc] = v1;   // LH  (y lo, x hi)
-        sb[2][r][cc] = v2;   // HL  (y hi, x lo)
-        sb[3][r][cc] = v3;   // HH  (y hi, x hi)
     }
-    __syncthreads();
+}
+
+// Adjoint of one level of db_P for an STY x STX tile of a_{j-1} from the
+// staged bands sb.  Polyphase: outputs 2q and 2q+1 use the same band samples
+// k0 + q + t, t < F/2, with the odd and the even taps respectively
+// (a[m] = sum_k f[2k+1-m] band[k]).  Adds this thread's outputs to acc[8]:
+// slot pairs s < 4 give rows 2 qy and 2 qy + 1 of column rx (synth_slot).
+//
+// Register blocking as in the analysis: an x-step thread computes kSynNQ
+// adjacent q of one band row from H + kSynNQ - 1 samples per band (rows
+// taken by consecutive threads, odd row strides), and a y-step thread
+// computes its four adjacent qy of one column from H + 3 samples per array.
+template <int P>
+__device__ __forceinline__ void synthesis_compute_t(const SaraConst &c, float (*sb)[SB_Y][SB_X + 2],
+                                                    float (*su)[SB_Y][STX + 1], float *acc) {
+    constexpr int F = 2 * P, H = P;
+    constexpr int NBY = STY / 2 + H - 1;
+    float h[F], g[F];
+#pragma unroll
+    for (int i = 0; i < F; ++i) {
+        h[i] = c.h[P][i];
+        g[i] = c.g[P][i];
+    }
     // x: u_lo = synth(LL, h) + synth(LH, g); u_hi = synth(HL, h) + synth(HH, g)
     constexpr int WQ = H + kSynNQ - 1;
     for (int idx = threadIdx.x; idx < NBY * (STX / 2 / kSynNQ); idx += blockDim.x) {
@@ -280,6 +308,16 @@ __device__ __forceinline__ void synthesis_tile_t(const SaraConst &c, int j, int 
         }
     }
     __syncthreads();
+}
+
+
+template <int P>
+__device__ __forceinline__ void synthesis_tile_t(const SaraConst &c, int j, int m0y, int m0x, const float *coef_l,
+                                                 const float *ll_in, float (*sb)[SB_Y][SB_X + 2],
+                                                 float (*su)[SB_Y][STX + 1], float *acc) {
+    synthesis_stage_t<P, false>(c, j, m0y, m0x, coef_l, ll_in, sb);
+    __syncthreads();
+    synthesis_compute_t<P>(c, sb, su, acc);
 }
 
 __device__ __forceinline__ void synthesis_tile(const SaraConst &c, int p, int j, int m0y, int m0x,
@@ -335,29 +373,41 @@ __global__ void __launch_bounds__(256, 4) synthesis_lj_kernel(const __grid_const
 }
 
 // Level 1 of all bases plus the Dirac basis, summed into the image: x = (1/3) sum.
+// The bands of basis P + 1 are staged by cp.async into the second buffer
+// while basis P is synthesised from the first.
 __global__ void __launch_bounds__(256, 4) synthesis_l1_kernel(const __grid_constant__ SaraConst c,
                                                            const float *__restrict__ coef, const float *__restrict__ tmp,
                                                            float *__restrict__ x) {
-    __shared__ float sb[4][SB_Y][SB_X + 2];
+    __shared__ float sb[2][4][SB_Y][SB_X + 2];
     __shared__ float su[2][SB_Y][STX + 1];
     const int l = blockIdx.z;
     const int m0y = blockIdx.y * STY, m0x = blockIdx.x * STX;
     const int ny = c.img_ny, nx = c.img_nx;
     const float *coef_l = coef + (long long)l * c.n_coef;
     float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#define FHS_SYN_L1(P)                                                                                      \
-    synthesis_tile_t<P>(c, 1, m0y, m0x, coef_l,                                                           \
-                        (c.levels == 1) ? coef_l + c.off_ll[P] : tmp + (long long)l * c.n_tmp + c.off_tmp[P][1], \
-                        sb, su, acc)
-    FHS_SYN_L1(1);
-    FHS_SYN_L1(2);
-    FHS_SYN_L1(3);
-    FHS_SYN_L1(4);
-    FHS_SYN_L1(5);
-    FHS_SYN_L1(6);
-    FHS_SYN_L1(7);
-    FHS_SYN_L1(8);
-#undef FHS_SYN_L1
+#define FHS_SYN_LL(P) ((c.levels == 1) ? coef_l + c.off_ll[P] : tmp + (long long)l * c.n_tmp + c.off_tmp[P][1])
+#define FHS_SYN_STAGE(P)                                                                                   \
+    synthesis_stage_t<P, true>(c, 1, m0y, m0x, coef_l, FHS_SYN_LL(P), sb[(P) & 1]);                         \
+    asm volatile("cp.async.commit_group;" ::: "memory")
+#define FHS_SYN_STEP(P)                                                                                    \
+    asm volatile("cp.async.wait_group 0;" ::: "memory");                                                   \
+    __syncthreads();                                                                                       \
+    FHS_SYN_STAGE(P + 1);                                                                                  \
+    synthesis_compute_t<P>(c, sb[(P) & 1], su, acc)
+    FHS_SYN_STAGE(1);
+    FHS_SYN_STEP(1);
+    FHS_SYN_STEP(2);
+    FHS_SYN_STEP(3);
+    FHS_SYN_STEP(4);
+    FHS_SYN_STEP(5);
+    FHS_SYN_STEP(6);
+    FHS_SYN_STEP(7);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    synthesis_compute_t<8>(c, sb[0], su, acc);
+#undef FHS_SYN_STEP
+#undef FHS_SYN_STAGE
+#undef FHS_SYN_LL
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
         int ry, rx;
