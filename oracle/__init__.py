@@ -22,6 +22,9 @@ matrix-vector products, dense SVD/eigh), written from the paper:
 * ``reduction`` visibility-gridding data reduction: gridding operator
                Gamma = Lambda G^H Theta^H, reduced operator Phi' = Lambda H F Z
                (Sec. 3.4, Eqs. 4-5), the default bound eps' (a reading).
+* ``adaptive`` adaptive estimation of the effective noise level during the
+               first PDFB iterations (Sec. 3.3 (ii); the schedule is a
+               reading built from the Sec. 3.3 (i) estimator and Eq. 2).
 
 Nothing here is shared with the CUDA library; the two implementations are
 compared in the tests.  Every function states the passage it follows and,
