@@ -208,6 +208,48 @@ fhs_status fhs_residual(fhs_problem *prob, const float *x_dev, float *r_dev, voi
 fhs_status fhs_noise_from_model(fhs_problem *prob, const float *x0_dev, int32_t apply, double *sigma_out,
                                 double *eps_out, void *stream);
 
+/* Schedule of the adaptive noise estimation (fhs_adaptive_noise). */
+typedef struct fhs_adaptive_params {
+    int32_t max_iter;      /* PDFB iterations of the phase at most (>= 0)                       */
+    int32_t check_every;   /* PDFB iterations between checks (>= 1)                             */
+    double  settle_tol;    /* a check acts only when the relative change ||x+ - x|| / ||x+|| of
+                              the last iteration is below settle_tol (> 0; INFINITY: always)    */
+} fhs_adaptive_params;
+
+typedef struct fhs_adaptive_result {
+    int32_t iterations;    /* PDFB iterations run                                             */
+    int32_t n_checks;      /* checks that acted                                               */
+    int32_t n_updates;     /* checks that re-estimated the bounds                             */
+    int32_t satisfied;     /* 1 when the last check found every l2 bound satisfied            */
+} fhs_adaptive_result;
+
+/* Adaptive estimation of the effective noise level during the first PDFB
+ * iterations (Sec. 3.3 (ii)).  The paper gives the outline: image priors
+ * inactive at first, noise estimates and l2 bounds updated while the
+ * iteration runs, and fixed once the bounds hold.  The schedule here is a
+ * reading of it built from the paper's own estimator and bound:
+ *  - mu = mu_bar = 0 for the phase (SARA and nuclear steps skipped), the
+ *    bounds the problem holds at the start;
+ *  - every check_every iterations, if the last relative change is below
+ *    settle_tol, a check takes the Sec. 3.3 (i) estimates of the current
+ *    iterate (residual norms rho and noise levels, as fhs_noise_from_model);
+ *    if rho <= eps for every block (every channel with data reduction) the
+ *    bounds hold: the phase ends with them fixed.  Otherwise every bound is
+ *    re-estimated as eps = s * eps0, with eps0 the bound of unit whitened
+ *    noise (the default of fhs_create_problem: Eq. 2 with
+ *    eps0^2 = (M_l + 2 sqrt(M_l)) M_{l,b} / M_l; with data reduction
+ *    M'_l + 2 sqrt(M'_l)) and s the estimated whitened noise level
+ *    (sigma_hat_{l,b} / sigma_l; with data reduction sigma_hat'_l);
+ *  - the phase ends after max_iter iterations otherwise; mu and mu_bar are
+ *    then restored (the iteration count goes on from the phase).
+ * The phase starts the run: a problem that has iterated already gives
+ * FHS_ERR_STATE.  sigma_out / eps_out (host, [L*B], or [L] with data
+ * reduction; may be NULL) receive the noise levels of the final iterate's
+ * residual and the bounds in force; res_out (may be NULL) the counts.
+ * Synchronises `stream`. */
+fhs_status fhs_adaptive_noise(fhs_problem *prob, const fhs_adaptive_params *params, double *sigma_out,
+                              double *eps_out, fhs_adaptive_result *res_out, void *stream);
+
 /* x_dev[L][ny][nx] = Re(Phi_l^H v_l), the adjoint of fhs_measure for real
  * images.  vis_dev: [M_tot] complex in the caller's order.  Asynchronous.
  * The gridding accumulates each tile of the oversampled grid in 32-bit fixed

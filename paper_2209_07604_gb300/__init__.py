@@ -25,7 +25,7 @@ EXPORTED = [
     "fhs_last_error", "fhs_profile_enable", "fhs_profile_read", "fhs_kernel_launches",
     "fhs_sara_analysis_noalloc", "fhs_pdfb_step_batch", "fhs_use_graphs", "fhs_estimate_bytes",
     "fhs_server_create", "fhs_server_submit", "fhs_server_query", "fhs_server_wait", "fhs_server_stats",
-    "fhs_server_destroy", "fhs_device_status", "fhs_autotune_bins", "fhs_residual",
+    "fhs_server_destroy", "fhs_device_status", "fhs_autotune_bins", "fhs_residual", "fhs_adaptive_noise",
 ]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 GRAM_FP32, GRAM_TF32, GRAM_BF16, GRAM_FP64 = range(4)
@@ -58,6 +58,15 @@ class fhs_info(C.Structure):
         ("n_gfac", C.c_int64), ("bin_dense_min", C.c_int32), ("bin_split", C.c_int32),
         ("mu", C.c_double), ("mu_bar", C.c_double), ("n_red", C.c_int64),
     ]
+
+
+class fhs_adaptive_params(C.Structure):
+    _fields_ = [("max_iter", C.c_int32), ("check_every", C.c_int32), ("settle_tol", C.c_double)]
+
+
+class fhs_adaptive_result(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("n_checks", C.c_int32), ("n_updates", C.c_int32),
+                ("satisfied", C.c_int32)]
 
 
 class fhs_request(C.Structure):
@@ -93,6 +102,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fhs_create_problem": (C.c_int, [P(fhs_params), vp, vp, vp, vp, vp, vp, vp, vp, P(vp)]),
         "fhs_create_problem_dde": (C.c_int, [P(fhs_params), vp, vp, vp, vp, vp, vp, vp, vp, vp, P(vp)]),
         "fhs_noise_from_model": (C.c_int, [vp, vp, C.c_int32, vp, vp, vp]),
+        "fhs_adaptive_noise": (C.c_int, [vp, P(fhs_adaptive_params), vp, vp, P(fhs_adaptive_result), vp]),
         "fhs_destroy_problem": (None, [vp]),
         "fhs_get_info": (C.c_int, [vp, P(fhs_info)]),
         "fhs_measure": (C.c_int, [vp, vp, vp, vp]),
@@ -237,6 +247,19 @@ def fhs_noise_from_model(prob, x0, n_out, apply=False, stream=None):
     _check(load_library().fhs_noise_from_model(prob, _dev(x0, "float32"), int(bool(apply)), _ptr(sig), _ptr(eps),
                                                _stream(stream)))
     return sig, eps
+
+
+def fhs_adaptive_noise(prob, n_out, max_iter, check_every=10, settle_tol=1e-3, stream=None):
+    """Adaptive noise estimation (Sec. 3.3 (ii)) on a problem that has not
+    iterated: (sigma, eps, result) with n_out values each (blocks, or channels
+    with data reduction) and result a dict of the counts."""
+    ap = fhs_adaptive_params(int(max_iter), int(check_every), float(settle_tol))
+    res = fhs_adaptive_result()
+    sig = np.zeros(n_out)
+    eps = np.zeros(n_out)
+    _check(load_library().fhs_adaptive_noise(prob, C.byref(ap), _ptr(sig), _ptr(eps), C.byref(res),
+                                             _stream(stream)))
+    return sig, eps, {k: int(getattr(res, k)) for k, _ in fhs_adaptive_result._fields_}
 
 
 def fhs_sara_analysis(prob, x, coef, stream=None):
@@ -484,6 +507,13 @@ class Problem:
         data reduction)."""
         n = self.L if int(self.params.data_reduction) else self.L * int(self.params.n_blocks)
         return fhs_noise_from_model(self.handle, x0, n, apply)
+
+    def adaptive_noise(self, max_iter, check_every=10, settle_tol=1e-3):
+        """Adaptive noise estimation (Sec. 3.3 (ii)) before the run: (sigma, eps, counts)."""
+        n = self.L if int(self.params.data_reduction) else self.L * int(self.params.n_blocks)
+        out = fhs_adaptive_noise(self.handle, n, max_iter, check_every, settle_tol)
+        self.info = fhs_get_info(self.handle)
+        return out
 
     def sara_analysis(self, x):
         import torch

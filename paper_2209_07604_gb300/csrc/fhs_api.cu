@@ -1412,6 +1412,88 @@ fhs_status fhs_noise_from_model(fhs_problem *p, const float *x0_dev, int32_t app
     return FHS_OK;
 }
 
+// Adaptive noise estimation (Sec. 3.3 (ii)): PDFB iterations with the priors
+// inactive, the l2 bounds re-estimated from the current iterate's residual
+// (the Sec. 3.3 (i) estimator) until they hold.
+fhs_status fhs_adaptive_noise(fhs_problem *p, const fhs_adaptive_params *ap, double *sigma_out, double *eps_out,
+                              fhs_adaptive_result *res_out, void *stream) {
+    if (!p || !ap) return fail(FHS_ERR_ARG, "NULL argument");
+    if (ap->max_iter < 0 || ap->check_every < 1)
+        return fail(FHS_ERR_ARG, "max_iter must be >= 0 and check_every >= 1");
+    if (!(ap->settle_tol > 0.0)) return fail(FHS_ERR_ARG, "settle_tol must be > 0 (INFINITY: every check acts)");
+    if (p->iteration != 0)
+        return fail(FHS_ERR_STATE, "the adaptive phase starts the run: the problem has iterated already");
+    cudaStream_t s = S(stream);
+    const int n = p->dr ? p->L : p->n_seg;
+    double *eps_dev = p->dr ? p->dr_eps : p->eps;
+    // eps0: the bounds of unit-variance whitened noise (the default rule of the set-up)
+    std::vector<double> eps0(n), cur(n), sig(n), rho(n), scale(n);
+    for (int i = 0; i < n; ++i) {
+        if (p->dr) {
+            const double m = double(p->dr_m[i]);
+            eps0[i] = m > 0 ? std::sqrt(m + 2.0 * std::sqrt(m)) : 0.0;
+            scale[i] = 1.0;
+        } else {
+            const int l = i / p->B;
+            const double Ml = double(p->seg_off[(l + 1) * p->B] - p->seg_off[l * p->B]);
+            const double Mb = double(p->seg_off[i + 1] - p->seg_off[i]);
+            eps0[i] = Ml > 0 ? std::sqrt((Ml + 2.0 * std::sqrt(Ml)) * Mb / Ml) : 0.0;
+            scale[i] = 1.0 / p->sigma_l[l];
+        }
+    }
+    CU(cudaMemcpyAsync(cur.data(), eps_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    // the captured iteration holds the regularisation: capture it again on each side of the phase
+    auto drop_graph = [&]() {
+        if (p->gexec) {
+            cudaGraphExecDestroy(p->gexec);
+            p->gexec = nullptr;
+        }
+    };
+    const double mu = p->prm.mu, mu_bar = p->prm.mu_bar;
+    drop_graph();
+    p->prm.mu = 0.0;
+    p->prm.mu_bar = 0.0;
+    int it = 0, n_chk = 0, n_up = 0, sat = 0;
+    fhs_status st = FHS_OK;
+    while (it < ap->max_iter) {
+        const int k = std::min(ap->check_every, ap->max_iter - it);
+        double rel = INFINITY;
+        if ((st = fhs_pdfb_step(p, k, &rel, stream)) != FHS_OK) break;
+        it += k;
+        if (!(rel < ap->settle_tol)) continue;
+        if ((st = fhs_noise_from_model(p, p->X, 0, sig.data(), rho.data(), stream)) != FHS_OK) break;
+        ++n_chk;
+        bool hold = true;
+        for (int i = 0; i < n; ++i) hold = hold && rho[i] <= cur[i];
+        if (hold) {
+            sat = 1;
+            break;
+        }
+        for (int i = 0; i < n; ++i) cur[i] = sig[i] * scale[i] * eps0[i];
+        if (cudaMemcpyAsync(eps_dev, cur.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            st = fail(FHS_ERR_CUDA, "%s", cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
+        ++n_up;
+    }
+    cudaStreamSynchronize(s);
+    drop_graph();
+    p->prm.mu = mu;
+    p->prm.mu_bar = mu_bar;
+    if (st != FHS_OK) return st;
+    if (sigma_out) TRY(fhs_noise_from_model(p, p->X, 0, sigma_out, nullptr, stream));
+    if (eps_out) std::copy(cur.begin(), cur.end(), eps_out);
+    if (res_out) {
+        res_out->iterations = it;
+        res_out->n_checks = n_chk;
+        res_out->n_updates = n_up;
+        res_out->satisfied = sat;
+    }
+    return FHS_OK;
+}
+
 fhs_status fhs_sara_analysis(fhs_problem *p, const float *x_dev, float *coef_dev, void *stream) {
     if (!p || !x_dev || !coef_dev) return fail(FHS_ERR_ARG, "NULL argument");
     CU(launch_sara_analysis(p, x_dev, coef_dev, S(stream)));

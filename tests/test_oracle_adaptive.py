@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from paper_2209_07604_gb300 import synth
-from oracle import adaptive as oad, nufft as onf, pdfb as opdfb, prox
+from oracle import adaptive as oad, nufft as onf, pdfb as opdfb
 
 
 S_EFF = 2.5
@@ -88,3 +88,22 @@ def test_every_check_acts_with_an_infinite_tolerance():
     assert r.checks[0][0] == 20 and r.n_updates >= 1
     assert np.any(r.checks[0][1] > r.checks[0][2])
     assert len(r.checks) == r.n_updates + (1 if r.satisfied else 0)
+
+
+def _pin_holds(P, ref, eps):
+    Mb = np.diff(P.block_offsets, axis=1).astype(np.float64)
+    return bool(np.all(np.abs(eps / (S_EFF * oad.unit_bounds(ref)) - 1.0) < 4.0 / (2.0 * np.sqrt(Mb)) + 1e-3))
+
+
+def test_mutations_of_the_bound_rule_fail_the_pin():
+    """Plausible mistakes in the bound rule, planted on the CPU: the noise level
+    left unwhitened (sigma_hat instead of sigma_hat / sigma_l), the variance in
+    place of the standard deviation, and the residual norm in place of the
+    noise level: each fails the closed-form pin that the rule itself passes."""
+    P, x, ref, _ = _data(S_EFF)
+    sig, rho, s = oad.estimate(ref, P.sigma, x)
+    eps0 = oad.unit_bounds(ref)
+    assert _pin_holds(P, ref, s * eps0)
+    assert not _pin_holds(P, ref, sig * eps0)
+    assert not _pin_holds(P, ref, s ** 2 * eps0)
+    assert not _pin_holds(P, ref, rho * eps0)
