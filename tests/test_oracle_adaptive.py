@@ -107,3 +107,32 @@ def test_mutations_of_the_bound_rule_fail_the_pin():
     assert not _pin_holds(P, ref, sig * eps0)
     assert not _pin_holds(P, ref, s ** 2 * eps0)
     assert not _pin_holds(P, ref, rho * eps0)
+
+
+def test_bound_rule_with_data_reduction_at_the_true_model():
+    """Gridded data (Sec. 3.4): at x = x_true the reduced residual is exactly
+    Gamma_l (s n_l), and the re-estimated bound is s eps0'_l within four
+    standard errors. ||Gamma_l n_l||^2 has mean trace(A) = M'_l and variance
+    ||A||_F^2 with A = Lambda_l H_l Lambda_l, for circular complex Gaussian
+    noise of unit variance."""
+    P = synth.make_problem("tiny", M=6000)
+    op = onf.Operator(P.omega, P.w, P.sigma, onf.Geometry(P.ny, P.nx))
+    x = np.clip(synth.random_image((P.L, P.ny, P.nx), 43), 0, None)
+    rng = np.random.default_rng(44)
+    n = (rng.standard_normal((P.L, P.M)) + 1j * rng.standard_normal((P.L, P.M))) / np.sqrt(2.0)
+    y = np.stack([(op.forward(x[l], l) + S_EFF * n[l]) * P.sigma[l] for l in range(P.L)])
+    ref = opdfb.FHS(P.omega, P.w, y, P.sigma, P.block_offsets, P.ny, P.nx, P.C, P.qy, P.qx, P.overlap,
+                    mu=0.0, mu_bar=0.0, reduction=True)
+    red = ref.red
+    np.testing.assert_array_equal(oad.unit_bounds(ref).ravel(), red.eps_default())
+    sig, rho, s = oad.estimate(ref, P.sigma, x)
+    eps = oad.updated_bounds(ref, P.sigma, x)
+    for l in range(P.L):
+        m = red.m_red(l)
+        gn = np.linalg.norm(red.gamma(S_EFF * n[l], l))
+        assert abs(rho[l, 0] - gn) <= 1e-9 * gn
+        A = red.Hr[l][:, red.rows[l]].multiply(np.outer(red.lam[l], red.lam[l]))
+        assert abs(np.real(A.diagonal()).sum() - m) < 1e-9 * m
+        se = 0.5 * np.sqrt(np.real(A.multiply(A.conj()).sum())) / m
+        assert abs(eps[l, 0] / (S_EFF * red.eps_default()[l]) - 1.0) < 4.0 * se + 1e-3
+        assert abs(s[l, 0] / S_EFF - 1.0) < 4.0 * se + 1e-3
