@@ -80,6 +80,8 @@ def updated_bounds(fhs, sigma, X) -> np.ndarray:
 def adaptive_noise(fhs, sigma, max_iter: int, check_every: int = 10, settle_tol: float = 1e-3) -> AdaptiveResult:
     """Run the adaptive phase on the oracle problem ``fhs`` (``pdfb.FHS``, fresh:
     no iteration done) with the channel whitening ``sigma``."""
+    if fhs.n_done != 0:
+        raise ValueError("the adaptive phase starts the run: the problem has iterated already")
     mu, mu_bar = fhs.mu, fhs.mu_bar
     fhs.mu, fhs.mu_bar = 0.0, 0.0
     eps0 = unit_bounds(fhs)

@@ -80,6 +80,13 @@ def test_no_check_before_the_iterate_settles():
     np.testing.assert_array_equal(r.eps, eps0)
 
 
+def test_the_phase_starts_the_run():
+    P, _, ref, _ = _data(S_EFF)
+    ref.step()
+    with pytest.raises(ValueError):
+        oad.adaptive_noise(ref, P.sigma, max_iter=10)
+
+
 def test_every_check_acts_with_an_infinite_tolerance():
     """settle_tol = inf: a check every check_every iterations; the first one
     (residual far above the nominal bounds) re-estimates them."""
