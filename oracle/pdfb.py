@@ -128,14 +128,10 @@ class FHS:
     # -- outer reweighting ---------------------------------------------------
     def reweight(self):
         for c, ch in enumerate(self.chans):
-            Aw = self.sara.analysis(self.X[ch])
-            self.w21[c] = self.upsilon / (self.upsilon + np.sqrt(np.sum(Aw * Aw, axis=0)))
+            self.w21[c] = prox.l21_weights(self.sara.analysis(self.X[ch]), self.upsilon)
             for q, (y0, y1, x0, x1) in enumerate(self.facets):
                 Z = self.X[ch, y0:y1, x0:x1].reshape(len(ch), -1).T
-                S = np.linalg.svd(Z, compute_uv=False)
-                wq = np.ones(len(ch))
-                wq[: len(S)] = self.upsilon_bar / (self.upsilon_bar + S)
-                self.wnuc[c][q] = wq
+                self.wnuc[c][q] = prox.nuclear_weights(Z, self.upsilon_bar, len(ch))
 
     def run(self, n_iter: int, n_reweight: int = 0) -> list:
         """n_reweight + 1 inner runs of n_iter // (n_reweight + 1) iterations

@@ -66,6 +66,25 @@ def nuclear_dual(P: np.ndarray, Xq: np.ndarray, s: float, mu_bar: float, weights
     return out.T.reshape(P.shape)
 
 
+def l21_weights(A: np.ndarray, upsilon: float) -> np.ndarray:
+    """Log-sum reweighting of the l21 rows (Sec. 2.2.3; Candes et al. 2008): the
+    weight of row r is upsilon / (upsilon + ||A_r||_2), where A is (L_c, n_coef)
+    and row r is column r, one coefficient across the sub-cube's channels."""
+    return upsilon / (upsilon + np.sqrt(np.sum(A * A, axis=0)))
+
+
+def nuclear_weights(Z: np.ndarray, upsilon_bar: float, L: int) -> np.ndarray:
+    """Log-sum reweighting of one facet's singular values (Sec. 2.2.3): Z is the
+    (pixels x L) facet matrix; weight i is upsilon_bar / (upsilon_bar + sigma_i)
+    with sigma_i the i-th largest singular value, and 1 beyond the rank bound
+    min(pixels, L).  The weights come out non-decreasing, as the weighted SVT
+    of ``svt`` expects."""
+    S = np.linalg.svd(Z, compute_uv=False)          # descending
+    w = np.ones(L)
+    w[: len(S)] = upsilon_bar / (upsilon_bar + S)
+    return w
+
+
 def nuclear_facets(ny: int, nx: int, qy: int, qx: int, overlap: float):
     """Facet windows [(y0, y1, x0, x1)] of the faceted low-rankness prior:
     tiles at floor(i n / Q) extended on their low side by ceil(overlap * tile),
