@@ -1,11 +1,13 @@
 """Benchmark: Faceted HyperSARA PDFB iterations/s on one GB300 (libfhs).
 
-One step = one PDFB iteration of the whole hot path (primal step, F, the
-single pass over G with the l2-ball dual step, F^H, SARA analysis + weighted
-l21 dual + synthesis, per-facet Gram + FP64 eig + SVT dual) over the
-1024x1024, 16-channel, 16e6-visibility workload with w-projection.
-Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
-bounded sample of the same workload instead.
+One step = one PDFB iteration of the whole hot path (primal step, F, the dual
+pass over G with the data-dual update, the l2-ball factors, the scatter pass
+over G, F^H, SARA analysis + weighted l21 dual + synthesis, per-facet Gram +
+FP64 eig + SVT dual) over the workload, by default the 2048 x 2048,
+32-channel, 1.28e8-visibility imaging configuration (4 spectral sub-cubes,
+8 x 8 facets, 8 blocks).  Prints one JSON line.  ``--impl reference`` times
+the FP64 CPU oracle on a bounded sample of the same workload instead, on all
+host cores.
 """
 from __future__ import annotations
 
@@ -25,8 +27,16 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "vla_1024"
-METRIC = "PDFB iter/s (1024^2 x 16 ch, 16e6 vis, w-projection); Phi/Phi^H vis/s alongside"
+WORKLOAD = "vla_2048"
+
+
+def _metric(workload: str) -> str:
+    from paper_2209_07604_gb300 import synth
+    sp = synth.WORKLOADS[workload]
+    w = ", w-projection" if sp["w_max"] > 0 else ""
+    return ("PDFB iter/s (%d^2 x %d ch, %.3g vis%s); Phi/Phi^H vis/s alongside"
+            % (sp["ny"], sp["L"], sp["L"] * sp["M"], w))
+
 MU, MU_BAR = 1e-2, 1e-1            # regularisation used for timing (cost does not depend on it)
 
 
@@ -104,34 +114,61 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _profile_traffic(kernel_file: str):
-    """(dram bytes per data term, limiter) of the two passes over G from the
-    committed ncu summary, valid only while the kernel source is unchanged
-    (sha256 recorded there); (None, None) otherwise."""
-    path = os.path.join(ROOT, "profiles", "data_term_passes_vla_1024.md")
+def _profile_traffic(workload: str, kernel_file: str):
+    """DRAM bytes per full launch of the dual and the scatter pass over G at
+    the workload, and the limiter line, from the committed ncu summary
+    profiles/data_term_passes_<workload>.md; valid only while the kernel
+    source is unchanged (its sha256 is recorded there).  None otherwise."""
+    path = os.path.join(ROOT, "profiles", "data_term_passes_%s.md" % workload)
     src = os.path.join(ROOT, "paper_2209_07604_gb300", "csrc", kernel_file)
     try:
         txt = open(path).read()
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        m_sha = re.search(r"kernel source sha256:\s*([0-9a-f]{64})", txt)
-        m_tr = re.search(r"dram bytes per full data term:\s*([0-9.eE+]+)", txt)
-        m_lim = re.search(r"^limiter:\s*(.+)$", txt, re.M)
-        if m_sha and m_tr and m_sha.group(1) == sha:
-            return float(m_tr.group(1)), (m_lim.group(1).strip() if m_lim else None)
     except OSError:
-        pass
-    return None, None
+        return None
+    m_sha = re.search(r"kernel source sha256:\s*([0-9a-f]{64})", txt)
+    if not m_sha or m_sha.group(1) != sha:
+        return None
+    out = {}
+    for key in ("dual", "scatter"):
+        m = re.search(r"^%s pass dram bytes per full launch:\s*([0-9.eE+]+)" % key, txt, re.M)
+        out[key] = float(m.group(1)) if m else None
+    for key in ("dual", "scatter"):
+        m = re.search(r"^%s pass limiter:\s*(.+)$" % key, txt, re.M)
+        out[key + "_limiter"] = m.group(1).strip() if m else None
+    return out
 
 
 def data_term_bytes(info, L, K, M):
-    """Algorithmic HBM bytes of the data term's two passes over G.  Dual pass:
-    G factors 8 B per stored value (2T per row), per row meta 8 B + factor
-    offset 8 B, per visibility y 8 B and the dual d read 8 B + written 8 B,
-    the forward grid read once (8 B/cell).  Scatter pass: the factors, meta and
-    offsets again, d read 8 B, the channel grid written once (8 B/cell)."""
+    """Algorithmic HBM bytes of the data term's two passes over G, (dual,
+    scatter).  Dual pass: G factors 8 B per stored value (2T per row), per row
+    meta 8 B + factor offset 8 B, per visibility y 8 B and the dual d read
+    8 B + written 8 B, the forward grid read once (8 B/cell).  Scatter pass:
+    the factors, meta and offsets again, d read 8 B, the channel grid written
+    once (8 B/cell)."""
     dual = info.n_gfac * 8 + M * (8 + 8 + 8 + 8 + 8) + L * K * 8
     scatter = info.n_gfac * 8 + M * (8 + 8 + 8) + L * K * 8
-    return dual + scatter
+    return dual, scatter
+
+
+def phase_bytes(info, P, L, K, M):
+    """Algorithmic HBM bytes per iteration of every phase of the PDFB
+    iteration (the least traffic each phase's result needs):
+    primal      37 B per pixel-channel: x, the SARA adjoint, the nuclear dual
+                over the facet cover (1.2 on average) read, the data adjoint
+                read from the grid (8 B), x, xbar and the zero-padded grid
+                (8 B) written;
+    fft_fwd/inv the channel grids read and written once (2 x 8 B per cell);
+    dual        G factors, row data, y, d read and written, forward grid;
+    scatter     G factors, row data, d read, channel grids written;
+    sara        the dual W read and written, the weights read (one per
+                coefficient row), xbar read and the adjoint term written;
+    nuclear     the facet duals P read and written, xbar over the facets read."""
+    N = P.ny * P.nx
+    dual, scatter = data_term_bytes(info, L, K, M)
+    return {"primal": 37 * N * L, "fft_fwd": 16 * L * K, "fft_inv": 16 * L * K, "degrid_grid": dual,
+            "scatter": scatter, "sara": (2 * L + P.C) * info.n_coef * 4 + 2 * N * L * 4,
+            "nuclear": 3 * info.nuclear_size * 4}
 
 
 def run_gpu(args):
@@ -171,12 +208,14 @@ def run_gpu(args):
     params = fhs.default_params(ny=P.ny, nx=P.nx, n_channels=L, n_subcubes=P.C, n_blocks=P.B, qy=P.qy, qx=P.qx,
                                 facet_overlap=P.overlap, w_max=P.w_max, pixel_size=P.pixel_size, mu=MU,
                                 mu_bar=MU_BAR, gram_precision=gram, data_reduction=int(args.reduction))
-    e2e_iters = args.e2e_iters
+    spec = synth.WORKLOADS[args.workload]
+    e2e_iters = args.e2e_iters if args.e2e_iters > 0 else max(int(spec["n_iter"]), 2)
+    e2e_rw = int(spec["n_reweight"]) if args.e2e_iters <= 0 else (1 if e2e_iters >= 2 else 0)
     img_host = torch.empty((L, P.ny, P.nx), dtype=torch.float32, pin_memory=True)
     t_e2e = time.perf_counter()
     prob = fhs.Problem(params, omega, wv, yv, P.sigma, vis_off, P.block_offsets, dde=dde)
     setup_s = time.perf_counter() - t_e2e
-    prob.solve(e2e_iters, 0.0, n_reweight=1 if e2e_iters >= 2 else 0, check_every=max(1, e2e_iters))
+    prob.solve(e2e_iters, 0.0, n_reweight=e2e_rw, check_every=max(1, e2e_iters))
     img_host.copy_(prob.image(), non_blocking=True)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t_e2e
@@ -242,23 +281,31 @@ def run_gpu(args):
     phit_ms = e[1].elapsed_time(e[2]) / n_op
     del xs, vis, img
 
-    # roofline of the dominant kernels: the data term's two passes over G (the degrid_grid phase)
+    # rooflines: every phase of the iteration against its algorithmic bytes; the dominant
+    # kernel is the longer of the two passes over G
     K = 4 * P.ny * P.nx
     peak, peak_kind = _peaks()
-    kbytes = data_term_bytes(info, L, K, Mtot)
+    pbytes = phase_bytes(info, P, L, K, Mtot)
     if args.reduction:
         # two normal-mode passes per iteration (H Xhat, then H Lambda v): factors, row meta and
         # offsets, the input grid read and the output grid written once each per pass
-        kbytes = 2 * (info.n_gfac * 8 + Mtot * 16 + 2 * L * K * 8)
-    k_ms = phases["degrid_grid"] / max(n_prof, 1)
-    achieved = kbytes / (k_ms * 1e-3) / 1e9
-    traffic, limiter = _profile_traffic("k_binned.cu")
-    if args.workload != WORKLOAD or args.dde or args.reduction:
-        traffic = None          # the committed capture is scaled to the default workload only
+        pbytes["degrid_grid"] = pbytes["scatter"] = info.n_gfac * 8 + Mtot * 16 + 2 * L * K * 8
+    pms = {k: v / max(n_prof, 1) for k, v in phases.items()}
+    rl_phases = {}
+    for k, b in pbytes.items():
+        if pms.get(k, 0.0) > 0:
+            a = b / (pms[k] * 1e-3) / 1e9
+            rl_phases[k] = {"ms": pms[k], "algorithmic_bytes": int(b), "achieved": a, "frac": a / peak}
+    dom = "degrid_grid" if pms["degrid_grid"] >= pms["scatter"] else "scatter"
+    prof = _profile_traffic(args.workload, "k_binned.cu")
+    if prof is None or args.dde or args.reduction:
+        prof = {}
+    pkey = "dual" if dom == "degrid_grid" else "scatter"
+    achieved = rl_phases[dom]["achieved"]
     # visibilities through Phi and Phi^H per second inside the PDFB iteration
     vis_s = Mtot / (ms_step * 1e-3)
     out = {
-        "metric": METRIC,
+        "metric": _metric(args.workload),
         "value": ws * 1e3 / ms_step,
         "unit": "iter/s",
         "n_gpus": ws,
@@ -285,20 +332,23 @@ def run_gpu(args):
         "phi_adjoint_vis_per_s": ws * Mtot / (phit_ms * 1e-3),
         "e2e": {"value": ws * e2e_iters / e2e_s, "unit": "iter/s", "h2d_bytes_per_step": h2d / e2e_iters,
                 "d2h_bytes_per_step": d2h / e2e_iters,
-                "what": "create from host arrays (sort, G build, Lanczos norm estimate) + %d iterations with one "
-                        "reweighting + image to pinned host" % e2e_iters,
+                "what": "create from host arrays (sort, G build, Lanczos norm estimate) + %d iterations with %d "
+                        "reweighting(s) + image to pinned host" % (e2e_iters, e2e_rw),
                 "seconds": e2e_s, "setup_seconds": setup_s},
         "gpu_launches": int(launches),
         "phases_ms_per_step": {k: v / max(n_prof, 1) for k, v in phases.items()},
-        "roofline": {"kernel": "data term: dual + scatter passes over G", "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                     "algorithmic_bytes": kbytes, "peak_source": peak_kind, "limiter": limiter},
+        "roofline": {"kernel": ("degrid_grid_binned_kernel<kDual>: dual pass over G" if dom == "degrid_grid"
+                                else "degrid_grid_binned_kernel<kScatter>: scatter pass over G"),
+                     "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": prof.get(pkey), "algorithmic_bytes": int(pbytes[dom]), "peak_source": peak_kind,
+                     "limiter": prof.get(pkey + "_limiter")},
+        "roofline_phases": rl_phases,
         "clocks": clk.summary(),
         "device_bytes": info.device_bytes,
         "generate_seconds": gen_s,
     }
     if rank == 0 and not args.no_cpu_baseline and ws == 1 and not args.dde and not args.reduction:
-        out["cpu_baseline"] = cpu_baseline(P, info)
+        out["cpu_baseline"] = cpu_baseline(args.workload)
     prob.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -306,100 +356,218 @@ def run_gpu(args):
         print(json.dumps(out))
 
 
-def _oracle_sample(P, n_vis: int, sara_side: int, n_facets: int):
-    """Time the oracle's own pieces of one PDFB iteration on a bounded sample
-    of the workload and return seconds per unit of work:
-    data term per stored entry of G (2 channels x n_vis visibilities),
-    SARA analysis + l21 + synthesis per pixel-channel (one channel, a
-    sara_side^2 crop), nuclear dual per facet-pixel-channel (n_facets facets
-    of one sub-cube)."""
+# ---------------------------------------------------------------------------
+# The FP64 oracle on the host cores (cpu_baseline of the GPU arm, and the
+# reference arm): a bounded sample of the workload, timed in one process per
+# core at the same time, scaled per unit of work to one full iteration.
+# ---------------------------------------------------------------------------
+ORACLE_SAMPLE = dict(n_vis=20_000, sara_side=384)     # per worker; the same in both arms
+
+
+def _host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+_WORKER_CACHE = {}
+
+
+def _oracle_worker(args):
+    """One worker's share of the sample (a spawned process with one thread):
+    the oracle's own operations of one PDFB iteration on a piece of the
+    workload, each timed.  Returns per-unit seconds.  The sample's inputs (a
+    problem of n_vis visibilities per channel with the workload's geometry and
+    its G rows for one channel) are built on a worker's first round only."""
+    workload, wid, n_vis, side = args
+    from paper_2209_07604_gb300 import synth
     from oracle import nufft as onf, prox as oprox, wavelets as owv
-    Lc = P.omega.shape[0] // P.C
-    ch = [0, P.C]
-    geom = onf.Geometry(P.ny, P.nx, w_max=P.w_max, n_wplanes=64, pixel_size=P.pixel_size)
-    op = onf.Operator(P.omega[ch, :n_vis], P.w[ch, :n_vis], P.sigma[ch], geom)
-    nnz = sum(G.nnz for G in op.G)
-    rng = np.random.default_rng(0)
-    X = rng.uniform(0, 1, (Lc, P.ny, P.nx))
+    key = (workload, n_vis)
+    if key not in _WORKER_CACHE:
+        _WORKER_CACHE.clear()
+        # same geometry and distributions as the workload, n_vis visibilities per channel
+        _WORKER_CACHE[key] = {"P": synth.make_problem(workload, M=n_vis)}
+    cache = _WORKER_CACHE[key]
+    P = cache["P"]
+    l = wid % P.L
+    if l not in cache:
+        geom = onf.Geometry(P.ny, P.nx, w_max=P.w_max, n_wplanes=64, pixel_size=P.pixel_size)
+        cache[l] = onf.Operator(P.omega[l:l + 1], P.w[l:l + 1], P.sigma[l:l + 1], geom)
+    op = cache[l]
+    L, Lc = P.L, P.L // P.C
+    nnz = op.G[0].nnz
+    rng = np.random.default_rng(wid)
+    x = rng.uniform(0, 1, (P.ny, P.nx))
+    out = {}
+    # per channel: Z, F, F^H, Z^H (zero-pad + scaling, two FFTs on the K grid)
     t0 = time.perf_counter()
-    for j in range(2):
-        yw = P.y[ch[j], :n_vis] / P.sigma[ch[j]]
-        eps = oprox.eps_blocks(n_vis, [n_vis])[0]
-        v = oprox.l2ball_dual(np.zeros(n_vis, complex), op.forward(X[j], j), yw, eps, 1e-6)
-        op.adjoint(v, j)
-    t_data = (time.perf_counter() - t0) / nnz
-    side = min(sara_side, P.ny, P.nx)
-    S = owv.Sara(side, side)
+    g = op.fzx(x)
+    op.zf_adj(g)
+    out["fft_channel"] = time.perf_counter() - t0
+    # per entry of G: Phi's G, the block l2-ball dual steps, G^H
+    yw = P.y[l] / P.sigma[l]
+    bo = P.block_offsets[l]
+    eps = oprox.eps_blocks(n_vis, np.diff(bo))
     t0 = time.perf_counter()
-    A = S.analysis(X[:1, :side, :side])
+    phix = op.G[0] @ g.ravel()
+    v = np.zeros(n_vis, complex)
+    for b in range(len(bo) - 1):
+        v[bo[b]:bo[b + 1]] = oprox.l2ball_dual(v[bo[b]:bo[b + 1]], phix[bo[b]:bo[b + 1]], yw[bo[b]:bo[b + 1]],
+                                               eps[b], 1e-6)
+    (op.G[0].conj().T @ v)
+    out["g_entry"] = (time.perf_counter() - t0) / nnz
+    out["row_nnz"] = nnz / n_vis
+    # per pixel-channel: SARA analysis, weighted l21 dual, synthesis (one channel, a side^2 crop)
+    sd = min(side, P.ny, P.nx)
+    S = owv.Sara(sd, sd)
+    xs = x[None, :sd, :sd]
+    t0 = time.perf_counter()
+    A = S.analysis(xs)
     W = oprox.l21_dual(np.zeros_like(A), A, 1.0, MU, np.ones(A.shape[1]))
     S.synthesis(W)
-    t_sara = (time.perf_counter() - t0) / (side * side)
-    facets = oprox.nuclear_facets(P.ny, P.nx, P.qy, P.qx, P.overlap)[:n_facets]
-    npx = 0
+    out["sara_px"] = (time.perf_counter() - t0) / (sd * sd)
+    # per facet-pixel-channel: the nuclear dual step of one facet of a sub-cube
+    facets = oprox.nuclear_facets(P.ny, P.nx, P.qy, P.qx, P.overlap)
+    y0, y1, x0, x1 = facets[wid % len(facets)]
+    Xq = rng.uniform(0, 1, (Lc, y1 - y0, x1 - x0))
     t0 = time.perf_counter()
-    for (y0, y1, x0, x1) in facets:
-        oprox.nuclear_dual(np.zeros((Lc, y1 - y0, x1 - x0)), X[:, y0:y1, x0:x1], 0.25, MU_BAR, np.ones(Lc))
-        npx += (y1 - y0) * (x1 - x0) * Lc
-    t_nuc = (time.perf_counter() - t0) / npx
-    return t_data, t_sara, t_nuc
+    oprox.nuclear_dual(np.zeros_like(Xq), Xq, 0.25, MU_BAR, np.ones(Lc))
+    out["nuc_px"] = (time.perf_counter() - t0) / Xq.size
+    # per pixel-channel: the primal step (projection, extrapolation, relative change)
+    Xa, Aa = rng.uniform(0, 1, (3, P.ny, P.nx)), rng.uniform(-1, 1, (3, P.ny, P.nx))
+    t0 = time.perf_counter()
+    Xp = np.maximum(0.0, Xa - 0.33 * (Aa + Aa + Aa))
+    Xb = 2.0 * Xp - Xa
+    np.linalg.norm(Xp - Xa), np.linalg.norm(Xp), Xb.sum()
+    out["primal_px"] = (time.perf_counter() - t0) / Xa.size
+    return out
 
 
-def _full_units(P, nnz_full):
+class OracleTimer:
+    """A pool of spawned single-thread processes, one per host core, that
+    time the oracle's sample together (rounds of ORACLE_SAMPLE)."""
+
+    def __init__(self, workload: str):
+        import multiprocessing as mp
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[k] = "1"
+        self.workload = workload
+        self.n = _host_cores()
+        self.pool = mp.get_context("spawn").Pool(self.n)
+
+    def round(self):
+        """One round: every worker times its share; returns (per-unit medians, wall seconds)."""
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_worker, [(self.workload, w, ORACLE_SAMPLE["n_vis"], ORACLE_SAMPLE["sara_side"])
+                                             for w in range(self.n)])
+        wall = time.perf_counter() - t0
+        return {k: float(np.median([r[k] for r in res])) for k in res[0]}, wall
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def oracle_seconds_per_iter(workload: str, u: dict, cores: int) -> float:
+    """One PDFB iteration of the full workload on `cores` cores from per-unit
+    costs measured with every core busy: channels x (zero-pad, FFT, FFT^H,
+    crop) + G entries x (G, l2 ball, G^H) + pixel-channels x (SARA + primal) +
+    facet-pixel-channels x nuclear dual, divided by the cores (the sub-cubes,
+    channels and facets of an iteration are independent pieces of work)."""
+    from paper_2209_07604_gb300 import synth
     from oracle import prox as oprox
-    L = P.omega.shape[0]
-    fac = oprox.nuclear_facets(P.ny, P.nx, P.qy, P.qx, P.overlap)
-    nuc = sum((y1 - y0) * (x1 - x0) for (y0, y1, x0, x1) in fac) * L
-    return nnz_full, P.ny * P.nx * L, nuc
+    spec = synth.WORKLOADS[workload]
+    L, M, ny, nx = spec["L"], spec["M"], spec["ny"], spec["nx"]
+    fac = oprox.nuclear_facets(ny, nx, spec["qy"], spec["qx"], spec["overlap"])
+    nuc_units = sum((y1 - y0) * (x1 - x0) for (y0, y1, x0, x1) in fac) * L
+    serial = (L * u["fft_channel"] + u["row_nnz"] * L * M * u["g_entry"]
+              + ny * nx * L * (u["sara_px"] + u["primal_px"]) + nuc_units * u["nuc_px"])
+    return serial / cores
 
 
-def _estimate(P, nnz_full, t_data, t_sara, t_nuc):
-    u_data, u_sara, u_nuc = _full_units(P, nnz_full)
-    return t_data * u_data + t_sara * u_sara + t_nuc * u_nuc
+def oracle_config1_run():
+    """The oracle as it stands, one core, on the whole 128^2 x 4-channel
+    problem of 2e4 visibilities per channel: 50 PDFB iterations (no
+    extrapolation); returns the per-iteration times."""
+    from paper_2209_07604_gb300 import synth
+    from oracle import pdfb
+    P = synth.make_problem("small_128")
+    steps = pdfb.Steps(tau=0.99 / 3.0, sigma0=0.25, sigma1=1.0, sigma2=1e-6)
+    o = pdfb.FHS(P.omega, P.w, P.y, P.sigma, P.block_offsets, P.ny, P.nx, P.C, P.qy, P.qx, P.overlap,
+                 mu=MU, mu_bar=MU_BAR, steps=steps)
+    ts = []
+    for _ in range(P.n_iter):
+        t0 = time.perf_counter()
+        o.step()
+        ts.append(time.perf_counter() - t0)
+    return ts
 
 
-def cpu_baseline(P, info):
-    """Oracle seconds per PDFB iteration of the full workload, from a bounded
-    sample (about 20 s of host work) scaled per unit of work."""
-    n_vis, side, nf = min(P.M, 100_000), 512, 4
-    t_data, t_sara, t_nuc = _oracle_sample(P, n_vis, side, nf)
-    t_full = _estimate(P, info.nnz, t_data, t_sara, t_nuc)
-    return {"value": 1.0 / t_full, "unit": "iter/s", "cores": 1, "kind": "oracle",
-            "sample": ("data term on 2 channels x %d visibilities, SARA on one %dx%d channel crop, nuclear "
-                       "dual on %d facets of one sub-cube; each scaled per unit (G entry, pixel-channel, "
-                       "facet-pixel-channel) to the full workload" % (n_vis, side, side, nf)),
-            "seconds_per_iter": t_full}
+def _config1_summary(ts):
+    return {"workload": "small_128 (128^2, 4 channels, 2e4 visibilities per channel, 2x2 facets)",
+            "iterations": len(ts), "wall_s": float(np.sum(ts)),
+            "s_per_iter_median3": float(np.median(ts[1:4])), "cores": 1,
+            "what": "the whole problem, no extrapolation; median of iterations 2-4 after one warm-up"}
+
+
+def _sample_text(n):
+    return ("per core (%d single-thread processes at once): one channel's zero-pad + FFT + FFT^H + crop on the "
+            "full oversampled grid, G, l2-ball duals and G^H of %d visibilities, SARA analysis + l21 dual + "
+            "synthesis on a %d^2 crop of one channel, the nuclear dual of one facet of a sub-cube, the primal "
+            "step on 3 channels; per-unit costs (channel, G entry, pixel-channel, facet-pixel-channel) scaled to "
+            "one full iteration and divided by the cores" % (n, ORACLE_SAMPLE["n_vis"], ORACLE_SAMPLE["sara_side"]))
+
+
+def cpu_baseline(workload):
+    """Oracle iterations/s on the host cores for the workload: one warm-up
+    round and one timed round of the sample, plus the real 50-iteration run of
+    the 128^2 configuration on one core."""
+    tm = OracleTimer(workload)
+    try:
+        tm.round()
+        u, wall = tm.round()
+    finally:
+        tm.close()
+    spi = oracle_seconds_per_iter(workload, u, tm.n)
+    c1 = _config1_summary(oracle_config1_run())
+    return {"value": 1.0 / spi, "unit": "iter/s", "cores": tm.n, "kind": "oracle", "extrapolated": True,
+            "sample": _sample_text(tm.n), "seconds_per_iter": spi, "sample_wall_s": wall, "per_unit_s": u,
+            "config1": c1}
 
 
 def run_reference(args):
-    """The oracle as the reference arm (rank 0 only; other ranks exit)."""
+    """The oracle as the reference arm (rank 0 only; other ranks exit): each
+    step is one round of the same sample as the GPU arm's cpu_baseline."""
     ws, rank, local = _dist()
     if rank != 0:
         return
-    from paper_2209_07604_gb300 import synth
-    from oracle import nufft as onf
-    P = synth.make_problem(args.workload)
-    geom = onf.Geometry(P.ny, P.nx, w_max=P.w_max, n_wplanes=64, pixel_size=P.pixel_size)
-    _, _, h = onf.wplane(P.w.reshape(-1), geom)
-    nnz_full = float(np.sum((geom.J + 2 * h) ** 2))
-    n_vis, side, nf = min(P.M, 20_000), 128, 1
-    per = []
-    for i in range(args.warmup + args.steps):
-        t = _oracle_sample(P, n_vis, side, nf)
-        if i >= args.warmup:
-            per.append(_estimate(P, nnz_full, *t))
+    tm = OracleTimer(args.workload)
+    per, walls, units = [], [], []
+    try:
+        for i in range(args.warmup + args.steps):
+            u, wall = tm.round()
+            if i >= args.warmup:
+                per.append(oracle_seconds_per_iter(args.workload, u, tm.n))
+                walls.append(wall)
+                units.append(u)
+    finally:
+        tm.close()
     s_step = float(np.median(per))
     val = 1.0 / s_step
+    c1 = _config1_summary(oracle_config1_run())
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": val, "unit": "iter/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": s_step * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "impl": "reference", "metric": _metric(args.workload), "value": val, "unit": "iter/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.median(walls)) * 1e3,
+        "seconds_per_iter_estimate": s_step,
+        "note": "value = one full iteration of the workload estimated from each step's bounded sample (all host "
+                "cores); ms_per_step = the wall time of one sample round, what each step actually ran",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded VLA-like uv/w, Gaussian-blob sky, 40 dB)",
         "config": {"workload": args.workload},
-        "cpu_baseline": {"value": val, "unit": "iter/s", "cores": 1, "kind": "oracle",
-                         "sample": ("each step: data term on 2 channels x %d visibilities, SARA on one %dx%d "
-                                    "crop, nuclear dual on %d facet; scaled per unit of work to the full "
-                                    "workload" % (n_vis, side, side, nf))},
+        "cpu_baseline": {"value": val, "unit": "iter/s", "cores": tm.n, "kind": "oracle", "extrapolated": True,
+                         "sample": "each step: " + _sample_text(tm.n), "sample_wall_s_median": float(np.median(walls)),
+                         "config1": c1},
         "e2e": {"value": val, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -609,7 +777,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="fhs", choices=["fhs", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--e2e-iters", type=int, default=200)
+    ap.add_argument("--e2e-iters", type=int, default=0,
+                    help="iterations of the end-to-end run (0: the workload's own, with its reweightings)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true",
                     help="measure candidate tile binnings of the pass over G before timing")

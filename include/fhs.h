@@ -204,7 +204,8 @@ fhs_status fhs_residual(fhs_problem *prob, const float *x_dev, float *r_dev, voi
  * 5.2, with the model visibilities Phi_l x0_l) and sigma_out[l] = eps_out[l] /
  * sqrt(M'_l).  sigma_out / eps_out (host) may be NULL.  apply != 0 makes
  * eps_out the problem's l2 bounds for the following iterations.  Synchronises
- * `stream`. */
+ * `stream`; FHS_ERR_TIMEOUT if a bounded device wait gave up before (see
+ * fhs_device_status). */
 fhs_status fhs_noise_from_model(fhs_problem *prob, const float *x0_dev, int32_t apply, double *sigma_out,
                                 double *eps_out, void *stream);
 
@@ -278,7 +279,10 @@ fhs_status fhs_sara_analysis(fhs_problem *prob, const float *x_dev, float *coef_
  * needing more scratch than that (about 1.4e6 pixels at 4 levels) are rejected
  * with FHS_ERR_ARG.  The first call on a device looks up the array's address
  * on that device (it must be the current device); make that first call before
- * any stream capture.  Every call shares the one array, so calls that overlap
+ * any stream capture.  The address is cached per device for the life of the
+ * process: after cudaDeviceReset the module is loaded afresh and the cached
+ * address may no longer be valid, so do not call this entry point after a
+ * device reset.  Every call shares the one array, so calls that overlap
  * on the GPU (other streams, other threads) race: order them.  The scratch
  * needs no clearing (every value read was written earlier in the same call).
  * Asynchronous on `stream`. */
@@ -294,7 +298,8 @@ fhs_status fhs_sara_synthesis(fhs_problem *prob, const float *coef_dev, float *x
  *   W   <- Z min(1, mu w_r / ||Z_r||), Z = W + sigma1 Psi^dagger xbar (rows over channels)
  *   v_b <- (Z - sigma2 y_b)(1 - min(1, sigma2 eps_b / ||Z - sigma2 y_b||)), Z = v_b + sigma2 Phi_b xbar.
  * rel_change_out (host, may be NULL): ||x+ - x|| / ||x+|| of the last
- * iteration; when non-NULL the call synchronises `stream`.            */
+ * iteration; when non-NULL the call synchronises `stream` and returns
+ * FHS_ERR_TIMEOUT if a bounded device wait gave up (see fhs_device_status). */
 fhs_status fhs_pdfb_step(fhs_problem *prob, int32_t n_iter, double *rel_change_out, void *stream);
 
 /* n_iter PDFB iterations of each of n_prob problems, problem k on
@@ -318,15 +323,23 @@ fhs_status fhs_use_graphs(fhs_problem *prob, int32_t on);
 fhs_status fhs_estimate_bytes(const fhs_params *params, const double *w, int64_t n_vis, int64_t *resident_out,
                               int64_t *peak_out);
 
+/* The admission query of the serving path under the name of the boundary
+ * table: identical to fhs_estimate_bytes (same arguments, same results). */
+fhs_status fhs_workspace_bytes(const fhs_params *params, const double *w, int64_t n_vis, int64_t *resident_out,
+                               int64_t *peak_out);
+
 /* Log-sum reweighting (Sec. 2.2.3): w_r = upsilon/(upsilon + ||(Psi^dagger X)_r||),
  * w_{q,i} = upsilon_bar/(upsilon_bar + sigma_i(S_q X)); duals are kept. Async. */
 fhs_status fhs_reweight(fhs_problem *prob, void *stream);
 
-/* Outer reweighting loop around PDFB: n_reweight+1 inner runs of at most
+/* The reweighting scheme of Sec. 2.2.3: log-sum priors handled by an outer
+ * reweighting loop around PDFB.  n_reweight+1 inner runs of at most
  * max_iter/(n_reweight+1) iterations each (remainder in the last), an inner
  * run stopping early once ||x+ - x||/||x+|| < rel_tol (tested every
- * `check_every` iterations; <= 0 means 10), reweighting between runs.
- * iters_out (host, may be NULL) receives the iterations done.  Synchronises. */
+ * `check_every` iterations; <= 0 means 10), fhs_reweight between runs.
+ * iters_out (host, may be NULL) receives the iterations done.  Synchronises;
+ * returns FHS_ERR_TIMEOUT if a bounded device wait gave up during the run
+ * (the image is then not to be trusted). */
 fhs_status fhs_solve(fhs_problem *prob, int32_t max_iter, double rel_tol, int32_t n_reweight,
                      int32_t check_every, int32_t *iters_out, void *stream);
 
@@ -346,6 +359,9 @@ typedef enum {
  * followed by set_state of every part resumes the iteration exactly. */
 fhs_status fhs_state_size(const fhs_problem *prob, int32_t part, int64_t *n_floats);
 fhs_status fhs_get_state(fhs_problem *prob, int32_t part, float *dst_dev, void *stream);
+/* The current image X (the iterate x of Eq. 3's PDFB, [L][ny][nx] float32)
+ * into x_dev; the same as fhs_get_state(prob, FHS_STATE_IMAGE, ...).  Async. */
+fhs_status fhs_get_image(fhs_problem *prob, float *x_dev, void *stream);
 fhs_status fhs_set_state(fhs_problem *prob, int32_t part, const float *src_dev, void *stream);
 
 /* Pick the tile binning of the pass over G by measurement (a layout choice of
@@ -372,12 +388,15 @@ fhs_status fhs_operator_norms(fhs_problem *prob, int32_t n_iter, double *norms, 
 typedef enum {
     FHS_PHASE_PRIMAL = 0,        /* primal step + adjoint gathers + zero-pad     */
     FHS_PHASE_FFT_FWD = 1,       /* F (cuFFT)                                    */
-    FHS_PHASE_DEGRID_GRID = 2,   /* single pass over G: Phi xbar, dual, G^H      */
-    FHS_PHASE_L2BALL = 3,        /* block l2-ball factors + block-grid combine   */
+    FHS_PHASE_DEGRID_GRID = 2,   /* dual pass over G: Phi xbar, data-dual update,
+                                    block norms (data reduction: H Xhat)        */
+    FHS_PHASE_L2BALL = 3,        /* block l2-ball factors, clearing of the grids */
     FHS_PHASE_FFT_INV = 4,       /* F^H (cuFFT)                                  */
     FHS_PHASE_SARA = 5,          /* Psi^dagger, weighted l21 dual, Psi           */
     FHS_PHASE_NUCLEAR = 6,       /* facet Grams, FP64 eig, SVT dual              */
-    FHS_N_PHASES = 7
+    FHS_PHASE_SCATTER = 7,       /* scatter pass over G: G^H of the data dual
+                                    (data reduction: H Lambda v)                */
+    FHS_N_PHASES = 8
 } fhs_phase;
 
 /* on != 0 starts recording (and clears the totals); 0 stops. */
@@ -391,10 +410,26 @@ fhs_status fhs_profile_read(fhs_problem *prob, double *ms_out, int64_t *iters_ou
 fhs_status fhs_kernel_launches(const fhs_problem *prob, int64_t *count_out);
 
 /* Device-side status of the problem's kernels: FHS_ERR_TIMEOUT if a bounded
- * wait inside a kernel gave up since the last call (the tensor-core Gram's
- * mbarrier waits), FHS_OK otherwise; the flag is cleared.  Synchronises the
- * stream. */
+ * wait inside a kernel gave up since the flag was last read, FHS_OK
+ * otherwise; the flag is cleared.  The bounded waits are the tensor-core
+ * Gram's stage mbarriers (code 1: the kernel skips its remaining stages and
+ * still releases its tensor memory) and the pass over G's wait for the TMA
+ * copy of its window (code 2: it waits once more, bounded, so that no copy
+ * into its shared memory is in flight when it goes on).  fhs_solve,
+ * fhs_pdfb_step with rel_change_out, fhs_noise_from_model and the server's
+ * per-request checks read the same flag and fail with FHS_ERR_TIMEOUT (the
+ * server marks the request FHS_REQ_FAILED).  Synchronises the stream. */
 fhs_status fhs_device_status(fhs_problem *prob, void *stream);
+
+/* Test aid for the failure path (the paper has no counterpart): launches one
+ * CTA whose thread waits, with the same bounded wait as the pass over G's
+ * window copy, on an mbarrier that nothing arrives at.  After max_polls polls
+ * (1 .. 2^24; each poll may suspend the thread for a hardware-defined
+ * interval, well below a millisecond) the wait gives up, records code 2 in
+ * the problem's device flag and the kernel returns.  The next synchronising
+ * call then reports FHS_ERR_TIMEOUT, as after a real timeout; nothing else of
+ * the problem changes.  Asynchronous. */
+fhs_status fhs_debug_unsatisfied_wait(fhs_problem *prob, int32_t max_polls, void *stream);
 
 /* ------------------------------------------------------------------------
  * Serving: imaging requests solved concurrently on one GPU.  Requests are

@@ -26,10 +26,11 @@ EXPORTED = [
     "fhs_sara_analysis_noalloc", "fhs_pdfb_step_batch", "fhs_use_graphs", "fhs_estimate_bytes",
     "fhs_server_create", "fhs_server_submit", "fhs_server_query", "fhs_server_wait", "fhs_server_stats",
     "fhs_server_destroy", "fhs_device_status", "fhs_autotune_bins", "fhs_residual", "fhs_adaptive_noise",
+    "fhs_get_image", "fhs_workspace_bytes", "fhs_debug_unsatisfied_wait",
 ]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
 GRAM_FP32, GRAM_TF32, GRAM_BF16, GRAM_FP64 = range(4)
-PHASES = ["primal", "fft_fwd", "degrid_grid", "l2ball", "fft_inv", "sara", "nuclear"]
+PHASES = ["primal", "fft_fwd", "degrid_grid", "l2ball", "fft_inv", "sara", "nuclear", "scatter"]
 
 
 class FhsError(RuntimeError):
@@ -125,6 +126,10 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "fhs_pdfb_step_batch": (C.c_int, [vp, i32, i32, vp, vp]),
         "fhs_use_graphs": (C.c_int, [vp, i32]),
         "fhs_estimate_bytes": (C.c_int, [P(fhs_params), vp, i64, P(i64), P(i64)]),
+        "fhs_workspace_bytes": (C.c_int, [P(fhs_params), vp, i64, P(i64), P(i64)]),
+        "fhs_get_image": (C.c_int, [vp, vp, vp]),
+        "fhs_device_status": (C.c_int, [vp, vp]),
+        "fhs_debug_unsatisfied_wait": (C.c_int, [vp, i32, vp]),
         "fhs_server_create": (C.c_int, [i64, i32, i32, P(vp)]),
         "fhs_server_submit": (C.c_int, [vp, P(fhs_request), P(i64)]),
         "fhs_server_query": (C.c_int, [vp, i64, P(fhs_request_result)]),
@@ -266,11 +271,33 @@ def fhs_sara_analysis(prob, x, coef, stream=None):
     _check(load_library().fhs_sara_analysis(prob, _dev(x, "float32"), _dev(coef, "float32"), _stream(stream)))
 
 
+def sara_coefficient_count(ny, nx, levels, n_db=8):
+    """Coefficients per image of fhs_sara_analysis: the Dirac block plus, per
+    basis db_p (filter length 2p), the three detail bands of every level and
+    the last approximation, level sides n_{j+1} = floor((n_j + 2p - 1) / 2)."""
+    n = int(ny) * int(nx)
+    for p in range(1, n_db + 1):
+        a, b = int(ny), int(nx)
+        for _ in range(int(levels)):
+            a, b = (a + 2 * p - 1) // 2, (b + 2 * p - 1) // 2
+            n += 3 * a * b
+        n += a * b
+    return n
+
+
 def fhs_sara_analysis_noalloc(ny, nx, n_images, levels, x, coef, stream=None):
     """SARA analysis for callers that cannot allocate device memory (static
-    16 MiB scratch shared by all calls; overlapping calls race)."""
-    _check(load_library().fhs_sara_analysis_noalloc(int(ny), int(nx), int(n_images), int(levels),
-                                                    _dev(x, "float32"), _dev(coef, "float32"), _stream(stream)))
+    16 MiB scratch shared by all calls; overlapping calls race).  The tensors
+    are checked against the sizes first: the C entry point cannot see how
+    large the buffers behind its pointers are."""
+    ny, nx, n_images, levels = int(ny), int(nx), int(n_images), int(levels)
+    need_x = n_images * ny * nx
+    need_c = n_images * sara_coefficient_count(ny, nx, levels) if ny > 0 and nx > 0 and levels > 0 else 0
+    if x.numel() < need_x or coef.numel() < need_c:
+        raise FhsError(FHS_ERR_ARG, "fhs_sara_analysis_noalloc: x holds %d of %d floats, coef %d of %d"
+                       % (x.numel(), need_x, coef.numel(), need_c))
+    _check(load_library().fhs_sara_analysis_noalloc(ny, nx, n_images, levels, _dev(x, "float32"),
+                                                    _dev(coef, "float32"), _stream(stream)))
 
 
 def fhs_sara_synthesis(prob, coef, x, stream=None):
@@ -302,6 +329,10 @@ def fhs_state_size(prob, part) -> int:
 
 def fhs_get_state(prob, part, dst, stream=None):
     _check(load_library().fhs_get_state(prob, int(part), _dev(dst, "float32"), _stream(stream)))
+
+
+def fhs_get_image(prob, x, stream=None):
+    _check(load_library().fhs_get_image(prob, _dev(x, "float32"), _stream(stream)))
 
 
 def fhs_set_state(prob, part, src, stream=None):
@@ -344,6 +375,14 @@ def fhs_estimate_bytes(params: fhs_params, w, n_vis: int):
     return r.value, pk.value
 
 
+def fhs_workspace_bytes(params: fhs_params, w, n_vis: int):
+    """(resident, peak) device bytes; the same query as fhs_estimate_bytes."""
+    w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+    r, pk = C.c_int64(0), C.c_int64(0)
+    _check(load_library().fhs_workspace_bytes(C.byref(params), _ptr(w), int(n_vis), C.byref(r), C.byref(pk)))
+    return r.value, pk.value
+
+
 def fhs_profile_enable(prob, on: bool):
     _check(load_library().fhs_profile_enable(prob, 1 if on else 0))
 
@@ -359,6 +398,11 @@ def fhs_profile_read(prob):
 def fhs_device_status(prob, stream=None):
     """Raise FhsError(FHS_ERR_TIMEOUT) if a bounded device wait gave up."""
     _check(load_library().fhs_device_status(prob, _stream(stream)))
+
+
+def fhs_debug_unsatisfied_wait(prob, max_polls, stream=None):
+    """Test aid: a device wait that runs out and records a timeout in the problem's flag."""
+    _check(load_library().fhs_debug_unsatisfied_wait(prob, int(max_polls), _stream(stream)))
 
 
 def fhs_autotune_bins(prob, stream=None):
@@ -545,7 +589,9 @@ class Problem:
         fhs_set_state(self.handle, part, t)
 
     def image(self):
-        return self.get_state(STATE_IMAGE).reshape(self.L, self.ny, self.nx)
+        x = self._img()
+        fhs_get_image(self.handle, x)
+        return x
 
     def operator_norms(self, n_iter=100):
         return fhs_operator_norms(self.handle, n_iter, self.L)

@@ -180,6 +180,26 @@ void make_bins(const int2 *meta, const std::vector<long long> &seg_off, int n_se
     }
 }
 
+// The device-side error flag, already copied to the host as h after a
+// synchronisation of s: FHS_OK when clear; otherwise FHS_ERR_TIMEOUT, with the
+// flag cleared on s so that the next check starts afresh.  Codes: 1 the
+// tensor-core Gram's mbarrier wait, 2 the pass over G's window wait.
+fhs_status take_device_error(fhs_problem *p, int h, cudaStream_t s) {
+    if (h == 0) return FHS_OK;
+    CU(cudaMemsetAsync(p->dev_err, 0, sizeof(int), s));
+    return fail(FHS_ERR_TIMEOUT, "a bounded wait in a device kernel gave up (code %d: %s)", h,
+                h == 1 ? "tensor-core Gram stage barrier" : "window copy of the pass over G");
+}
+
+// Copies the device-side error flag to the host, synchronises s and returns
+// take_device_error's verdict.
+fhs_status device_error(fhs_problem *p, cudaStream_t s) {
+    int h = 0;
+    CU(cudaMemcpyAsync(&h, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    return take_device_error(p, h, s);
+}
+
 fhs_status check_params(const fhs_params *q) {
     if (!q) return fail(FHS_ERR_ARG, "params is NULL");
     if (q->ny < 16 || q->nx < 16 || (q->ny & 1) || (q->nx & 1))
@@ -532,7 +552,7 @@ fhs_status one_iteration(fhs_problem *p, cudaStream_t s) {
             CU(launch_dr_dual(p, s));
             CU(launch_dr_finalize(p, s));
         }
-        Phase ph(p, s, FHS_PHASE_DEGRID_GRID);
+        Phase ph(p, s, FHS_PHASE_SCATTER);
         CU(launch_normal(p, p->dr_w, p->grid_work, s, false));
     } else {
         // l2-ball factors, then G^H (s_b d) straight into the channel grids
@@ -541,7 +561,7 @@ fhs_status one_iteration(fhs_problem *p, cudaStream_t s) {
             CU(launch_block_finalize(p, s));
             CU(cudaMemsetAsync(p->grid_work, 0, sizeof(float2) * p->K * p->L, s));
         }
-        Phase ph(p, s, FHS_PHASE_DEGRID_GRID);
+        Phase ph(p, s, FHS_PHASE_SCATTER);
         CU(launch_data_scatter(p, s));
     }
     {
@@ -1246,6 +1266,15 @@ fhs_status fhs_estimate_bytes(const fhs_params *params, const double *w, int64_t
     return FHS_OK;
 }
 
+fhs_status fhs_workspace_bytes(const fhs_params *params, const double *w, int64_t n_vis, int64_t *resident_out,
+                               int64_t *peak_out) {
+    return fhs_estimate_bytes(params, w, n_vis, resident_out, peak_out);
+}
+
+fhs_status fhs_get_image(fhs_problem *p, float *x_dev, void *stream) {
+    return fhs_get_state(p, FHS_STATE_IMAGE, x_dev, stream);
+}
+
 fhs_status fhs_profile_enable(fhs_problem *p, int32_t on) {
     if (!p) return fail(FHS_ERR_ARG, "NULL problem");
     if (on) {
@@ -1287,9 +1316,14 @@ fhs_status fhs_device_status(fhs_problem *p, void *stream) {
     int h = 0;
     CU(cudaMemcpyAsync(&h, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    if (h == 0) return FHS_OK;
-    CU(cudaMemsetAsync(p->dev_err, 0, sizeof(int), s));
-    return fail(FHS_ERR_TIMEOUT, "a bounded wait in a device kernel gave up (code %d)", h);
+    return take_device_error(p, h, s);
+}
+
+fhs_status fhs_debug_unsatisfied_wait(fhs_problem *p, int32_t max_polls, void *stream) {
+    if (!p) return fail(FHS_ERR_ARG, "NULL problem");
+    if (max_polls < 1 || max_polls > (1 << 24)) return fail(FHS_ERR_ARG, "max_polls must be in [1, 2^24]");
+    CU(launch_unsatisfied_wait(p, max_polls, S(stream)));
+    return FHS_OK;
 }
 
 fhs_status fhs_get_info(const fhs_problem *p, fhs_info *info) {
@@ -1391,6 +1425,7 @@ fhs_status fhs_noise_from_model(fhs_problem *p, const float *x0_dev, int32_t app
     const fhs_status rs = run();
     cudaFreeAsync(st, s);
     if (rs != FHS_OK) return rs;
+    TRY(device_error(p, s));
     for (int i = 0; i < n; ++i) {
         if (p->dr) {
             eps[i] = std::sqrt(h[i]);
@@ -1512,9 +1547,14 @@ fhs_status fhs_pdfb_step(fhs_problem *p, int32_t n_iter, double *rel_change_out,
     cudaStream_t s = S(stream);
     TRY(run_iterations(p, n_iter, s));
     if (rel_change_out) {
+        // the relative change and the device error flag in one synchronisation: an iteration
+        // whose bounded wait gave up must not be reported as a good one
         double h[2] = {0, 0};
+        int herr = 0;
         CU(cudaMemcpyAsync(h, p->red, sizeof h, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(&herr, p->dev_err, sizeof herr, cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
+        TRY(take_device_error(p, herr, s));
         *rel_change_out = h[1] > 0 ? std::sqrt(h[0] / h[1]) : INFINITY;
     }
     return FHS_OK;
@@ -1550,9 +1590,8 @@ fhs_status fhs_solve(fhs_problem *p, int32_t max_iter, double rel_tol, int32_t n
         done += it;
         if (r < n_reweight) TRY(fhs_reweight(p, stream));
     }
-    CU(cudaStreamSynchronize(S(stream)));
     if (iters_out) *iters_out = done;
-    return FHS_OK;
+    return device_error(p, S(stream));     // synchronises; FHS_ERR_TIMEOUT if a device wait gave up
 }
 
 fhs_status fhs_state_size(const fhs_problem *p, int32_t part, int64_t *n) {

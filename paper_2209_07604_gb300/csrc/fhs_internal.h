@@ -195,6 +195,8 @@ cudaError_t launch_build_g(fhs_problem *p, const double2 *kap, const short *plan
                            const double2 *dde, int ext, const double *inv_sigma_seg, cudaStream_t s);
 cudaError_t launch_zpad(fhs_problem *p, const float *x, float2 *grid, cudaStream_t s);
 cudaError_t launch_degrid(fhs_problem *p, const float2 *grid, float2 *vis_sorted, cudaStream_t s);
+// test aid: a bounded wait on an mbarrier nothing arrives at, which records a timeout in p->dev_err
+cudaError_t launch_unsatisfied_wait(fhs_problem *p, int max_polls, cudaStream_t s);
 // fixed: dense bins accumulate their window in 32-bit fixed point (see k_binned.cu); false keeps
 // FP32 atomics (the gridding of the data reduction, whose faint cells are weighted up by Lambda).
 cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s, bool fixed = true);

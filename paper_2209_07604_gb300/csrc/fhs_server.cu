@@ -45,7 +45,7 @@ struct Req {
     fhs_problem *prob = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
-    double *h_red = nullptr;                    // pinned [2]
+    double *h_red = nullptr;                    // pinned [3]: the two reductions, then the device error flag
     bool in_flight = false;
     int stage = 0, stage_iters = 0, per_stage = 0;
 };
@@ -129,7 +129,7 @@ void setup_loop(fhs_server *sv) {
         fhs_status st = FHS_OK;
         if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess ||
-            cudaMallocHost(&r->h_red, 2 * sizeof(double)) != cudaSuccess) {
+            cudaMallocHost(&r->h_red, 3 * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
             st = FHS_ERR_CUDA;
         }
@@ -174,6 +174,14 @@ bool step_one(fhs_server *sv, std::shared_ptr<Req> &r) {
             cudaGetLastError();
             release(r);
             finish(sv, r, FHS_REQ_FAILED, FHS_ERR_CUDA);
+            return true;
+        }
+        int dev_err = 0;
+        std::memcpy(&dev_err, r->h_red + 2, sizeof dev_err);
+        if (dev_err != 0) {
+            // a bounded device wait gave up during these iterations: the iterate is not to be trusted
+            release(r);
+            finish(sv, r, FHS_REQ_FAILED, FHS_ERR_TIMEOUT);
             return true;
         }
         const double rel = r->h_red[1] > 0 ? std::sqrt(r->h_red[0] / r->h_red[1]) : INFINITY;
@@ -221,6 +229,7 @@ bool step_one(fhs_server *sv, std::shared_ptr<Req> &r) {
     }
     // relative change of the last iteration, read back without blocking
     if (cudaMemcpyAsync(r->h_red, r->prob->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+        cudaMemcpyAsync(r->h_red + 2, r->prob->dev_err, sizeof(int), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
         cudaEventRecord(r->ev, r->stream) != cudaSuccess) {
         cudaGetLastError();
         release(r);

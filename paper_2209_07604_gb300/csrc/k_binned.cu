@@ -50,6 +50,10 @@ constexpr int kWinP = kWin + 1;         // row stride of the staged forward wind
 #define FHS_BIN_MAX 384
 #endif
 constexpr int kBinMax = FHS_BIN_MAX;    // visibilities per bin (host splits longer runs)
+// The fixed-point scatter window (below) converts each contribution to an
+// integer of magnitude below 2^21 and adds at most kBinMax of them to a cell;
+// the sum stays inside int32 only while kBinMax <= 1024.
+static_assert(kBinMax <= 1024, "the fixed-point scatter window overflows int32 for bins above 1024 rows");
 
 // Factors of one row for one warp: lane t < T holds g1[t], lane 16 + t holds
 // g2[t]; the other lanes hold 0.
@@ -376,10 +380,13 @@ __device__ __forceinline__ void window_tma(float2 *dst, const CUtensorMap *tmap,
         : "memory");
 }
 
-// Bounded wait for phase 0 of the window barrier; false if it gave up.
-__device__ __forceinline__ bool window_wait(uint64_t *bar) {
+// Bounded wait for phase 0 of the window barrier: at most max_polls polls
+// (each try_wait may suspend the thread for a hardware-defined interval);
+// false if it gave up.
+constexpr int kWindowPolls = 1 << 24;
+__device__ __forceinline__ bool window_wait(uint64_t *bar, int max_polls = kWindowPolls) {
     const uint32_t a = smem_addr(bar);
-    for (int it = 0; it < (1 << 24); ++it) {
+    for (int it = 0; it < max_polls; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -594,7 +601,28 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
     }
 }
 
+// Test aid for the failure path: one thread waits, with the window wait of
+// the pass over G, on an mbarrier that expects one arrival that never comes.
+// The wait gives up after max_polls polls and records the code a timed-out
+// window copy records (2); the kernel then returns.  Nothing is copied, so no
+// transfer can be in flight when the CTA exits.
+__global__ void unsatisfied_wait_kernel(int max_polls, int *__restrict__ err) {
+    __shared__ alignas(8) uint64_t s_bar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !window_wait(&s_bar, max_polls)) atomicExch(err, 2);
+}
+
 }  // namespace
+
+cudaError_t launch_unsatisfied_wait(fhs_problem *p, int max_polls, cudaStream_t s) {
+    unsatisfied_wait_kernel<<<1, 32, 0, s>>>(max_polls, p->dev_err);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
 
 // Tensor map of a [L][K1][K2] complex grid for the window staging (8-byte
 // elements, box kWinP x kWin x 1).  The encoder comes from the driver entry

@@ -653,6 +653,14 @@ extern "C" fhs_status fhs_sara_analysis_noalloc(int32_t ny, int32_t nx, int32_t 
         }
         scratch = g_noalloc_ptr[dev];
     }
+    // an error left pending by an earlier CUDA call of this thread would otherwise be read back
+    // below as a failure of these launches: report it as what it is
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_last_error(std::string("fhs_sara_analysis_noalloc: a CUDA error was pending from an earlier call: ") +
+                       cudaGetErrorString(e));
+        return FHS_ERR_CUDA;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int my = 0, mx = 0;
     for (int b = 1; b <= kNumDb; ++b) { my = max(my, c.ny[b][1]); mx = max(mx, c.nx[b][1]); }

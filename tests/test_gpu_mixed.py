@@ -6,8 +6,10 @@ number of iterations.  The bounds follow from the rounding: TF32 keeps 10
 mantissa bits and BF16 7, so Gram entries carry relative errors of order 2^-11
 and 2^-8; any Gram in FP32 arithmetic resolves the singular values of Z only
 down to about sqrt(eps) of the largest, and the SVT weights of the ones near
-the threshold inherit that.  Only the FP64 Gram is held to the 1e-4 iterate
-tolerance."""
+the threshold inherit that.  Every mode is held to the 1e-4 image tolerance
+after the fixed iteration count; the nuclear dual itself, which carries the
+SVT of the singular values nearest the threshold, is held to 1e-4 with the
+FP64 Gram and to the rounding bounds below with the others."""
 import numpy as np
 import pytest
 
@@ -16,10 +18,12 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import paper_2209_07604_gb300 as fhs
+from parity import rel
 from paper_2209_07604_gb300 import synth
 from oracle import nufft as onf, pdfb as opdfb
 
-# relative error bound per precision after the runs below
+# error bounds after the runs below: the image (every precision) and the nuclear dual (per precision)
+BOUND_IMG = 1e-4
 BOUND = {fhs.GRAM_FP64: 1e-4, fhs.GRAM_FP32: 1e-2, fhs.GRAM_TF32: 1e-2, fhs.GRAM_BF16: 3e-2}
 NAMES = {fhs.GRAM_FP64: "fp64", fhs.GRAM_FP32: "fp32", fhs.GRAM_TF32: "tf32", fhs.GRAM_BF16: "bf16"}
 
@@ -33,9 +37,6 @@ def _lib():
     fhs.load_library()
 
 
-def rel(a, b):
-    a = np.asarray(a, dtype=np.complex128 if np.iscomplexobj(a) else np.float64)
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 _REF = {}
@@ -78,14 +79,14 @@ def _errors(name, n_iter, mu, mu_bar, precision, **over):
 @pytest.mark.parametrize("precision", [fhs.GRAM_FP64, fhs.GRAM_FP32, fhs.GRAM_TF32, fhs.GRAM_BF16])
 def test_gram_precision_mid_w(precision):
     e_img, e_nuc = _errors("mid_w", 20, 0.05, 0.5, precision)
-    assert e_img < BOUND[precision] and e_nuc < BOUND[precision]
+    assert e_img < BOUND_IMG and e_nuc < BOUND[precision]
 
 
 @pytest.mark.parametrize("precision", [fhs.GRAM_FP64, fhs.GRAM_FP32, fhs.GRAM_TF32, fhs.GRAM_BF16])
 def test_gram_precision_32_channels(precision):
     """32 channels per sub-cube: the full N = 32 of the tensor-core tile."""
     e_img, e_nuc = _errors("tiny", 8, 0.02, 0.3, precision, L=32, C=1)
-    assert e_img < BOUND[precision] and e_nuc < BOUND[precision]
+    assert e_img < BOUND_IMG and e_nuc < BOUND[precision]
 
 
 def test_tensor_gram_close_to_fp32_gram():

@@ -9,12 +9,11 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import paper_2209_07604_gb300 as fhs
+from parity import rel
 from paper_2209_07604_gb300 import synth
 from oracle import defaults as od, nufft as onf, pdfb as opdfb, reduction as ored
 
 
-def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
 
 
 @pytest.fixture(scope="module", autouse=True)

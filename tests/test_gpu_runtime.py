@@ -10,11 +10,10 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import paper_2209_07604_gb300 as fhs
+from parity import rel
 from paper_2209_07604_gb300 import synth
 
 
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -107,3 +106,58 @@ def test_autotune_bins_changes_layout_only(name):
         assert rel(pb, pa) < 1e-4, part
     a.close()
     b.close()
+
+
+def test_device_wait_that_runs_out_is_reported():
+    """Failure detection without a fault: a kernel waits, with the bounded wait
+    of the pass over G's window copy, on an mbarrier that nothing arrives at.
+    The wait gives up, the kernel records a timeout and returns, and every
+    synchronising call that reads the flag reports FHS_ERR_TIMEOUT once; the
+    problem stays usable afterwards."""
+    import time
+    P = synth.make_problem("tiny")
+    prob = fhs.Problem.from_synth(P, mu=0.02, mu_bar=0.3, sigma2=5e-6)
+    prob.step(2)
+    fhs.fhs_device_status(prob.handle)                    # healthy
+    t0 = time.perf_counter()
+    fhs.fhs_debug_unsatisfied_wait(prob.handle, 1000)
+    with pytest.raises(fhs.FhsError) as e:
+        fhs.fhs_device_status(prob.handle)
+    assert time.perf_counter() - t0 < 30.0                 # the wait is bounded
+    assert e.value.status == fhs.FHS_ERR_TIMEOUT
+    assert "window copy" in str(e.value)
+    fhs.fhs_device_status(prob.handle)                    # read once, then clear
+    # the iteration's own synchronising calls read the same flag
+    fhs.fhs_debug_unsatisfied_wait(prob.handle, 1000)
+    with pytest.raises(fhs.FhsError) as e:
+        prob.step(1, want_rel=True)
+    assert e.value.status == fhs.FHS_ERR_TIMEOUT
+    fhs.fhs_debug_unsatisfied_wait(prob.handle, 1000)
+    with pytest.raises(fhs.FhsError) as e:
+        prob.solve(4, 0.0, n_reweight=1, check_every=2)
+    assert e.value.status == fhs.FHS_ERR_TIMEOUT
+    fhs.fhs_debug_unsatisfied_wait(prob.handle, 1000)
+    with pytest.raises(fhs.FhsError) as e:
+        prob.noise_from_model(prob.image())
+    assert e.value.status == fhs.FHS_ERR_TIMEOUT
+    r = prob.step(1, want_rel=True)
+    assert np.isfinite(r)
+    with pytest.raises(fhs.FhsError) as e:
+        fhs.fhs_debug_unsatisfied_wait(prob.handle, 0)
+    assert e.value.status == fhs.FHS_ERR_ARG
+    prob.close()
+
+
+def test_get_image_and_workspace_names():
+    """fhs_get_image is the image part of the state transfer and
+    fhs_workspace_bytes the footprint query under the boundary's names."""
+    P = synth.make_problem("tiny")
+    prob = fhs.Problem.from_synth(P, mu=0.02, mu_bar=0.3, sigma2=5e-6)
+    prob.step(3)
+    a = prob.get_state(fhs.STATE_IMAGE).cpu().numpy()
+    x = torch.empty((P.L, P.ny, P.nx), dtype=torch.float32, device="cuda")
+    fhs.fhs_get_image(prob.handle, x)
+    np.testing.assert_array_equal(x.cpu().numpy().ravel(), a)
+    assert fhs.fhs_workspace_bytes(prob.params, P.w.reshape(-1), P.L * P.M) == \
+        fhs.fhs_estimate_bytes(prob.params, P.w.reshape(-1), P.L * P.M)
+    prob.close()

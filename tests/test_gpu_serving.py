@@ -13,14 +13,13 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import paper_2209_07604_gb300 as fhs
+from parity import rel
 from paper_2209_07604_gb300 import synth
 
 MIX = [("tiny", {}), ("mid_w", {}), ("small_128", {}), ("tiny", dict(L=3, C=1, trial=1))]
 KW = dict(mu=0.05, mu_bar=0.5, max_iter=30, rel_tol=1e-3, n_reweight=1, check_every=5)
 
 
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 @pytest.fixture(scope="module", autouse=True)
