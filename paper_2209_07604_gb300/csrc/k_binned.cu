@@ -46,6 +46,12 @@ __device__ __forceinline__ void red_add_f2(float2 *addr, float2 v) {
 constexpr int kWin = kTile + 15;        // boxes have T <= 16
 constexpr int kWinP = kWin + 1;         // row stride of the staged forward window: a TMA box row
                                         // must be a multiple of 16 bytes (48 complex values)
+// Row stride (in 32-bit words) of the adjoint window planes.  56 = 24 mod 32:
+// box rows 1, 2 and 3 below a row start 24, 16 and 8 banks further on, so
+// four rows of at most 8 adjacent cells, or two rows 2 apart of at most 16
+// adjacent cells, fall in disjoint banks (the scatter's lane mappings).
+constexpr int kAdjS = 56;
+static_assert(kAdjS >= kWin && kAdjS % 32 == 24, "adjoint window stride");
 #ifndef FHS_BIN_MAX
 #define FHS_BIN_MAX 384
 #endif
@@ -89,10 +95,16 @@ constexpr int kFixMagicBits = 0x4B400000;        // its bit pattern
 // grid += conj(G_i) s_d[i].  DENSE: the box lies in the shared window (shared
 // atomics); otherwise global reductions.
 //
-// Row G_i = g1 (x) g2 over the T x T box: lane (half, col) = (lane / 16,
-// lane % 16) owns box column col and rows t1 = half, half + 2, ...; it adds
-// conj(g1[t1]) (conj(g2[col]) d) to those cells.  The next row's factors are
-// loaded while the current row is scattered.
+// Row G_i = g1 (x) g2 over the T x T box; lane t < T holds g1[t] and lane
+// 16 + t holds g2[t].  A lane adds conj(g1[t1]) (conj(g2[col]) d) to cell
+// (t1, col) of the box for the box rows t1 of its mapping:
+//  - T <= 8: lane (g, col) = (lane / 8, lane % 8) takes rows t1 = g, g + 4:
+//    four box rows per step, ceil(T / 4) steps;
+//  - T > 8: lane (h, col) = (lane / 16, lane % 16) takes rows
+//    t1 = 4 j + 2 h + e at step 2 j + e: two box rows 2 apart per step.
+// With the window's row stride kAdjS both mappings touch 32 distinct banks
+// per step.  The next row's factors are loaded while the current row is
+// scattered.
 //
 // FIXED (dense bins): the window accumulates in 32-bit fixed point, with
 // native integer shared atomics (a float shared atomic costs about 3.5 times
@@ -100,14 +112,27 @@ constexpr int kFixMagicBits = 0x4B400000;        // its bit pattern
 // 1.5 * 2^23 (the sum lands in [2^23, 2^24), whose unit is 1, so its low
 // mantissa bits are the integer; valid for |c S| < 2^22).  S = 2^(21 - e)
 // with bound < 2^e, and bound >= |every contribution of the bin|, so |c S| <
-// 2^21 and a cell's sum of at most kBinMax contributions stays below 2^30.
+// 2^21 and a cell's sum of at most kBinMax contributions stays below 2^31.
+template <bool DENSE, bool FIXED>
+__device__ __forceinline__ void scatter_cell(float *s_re, float *s_im, int ib, float2 *__restrict__ gb,
+                                             long long gidx, float pr, float pi, float fs) {
+    if (DENSE && FIXED) {
+        atomicAdd(reinterpret_cast<int *>(s_re) + ib, __float_as_int(fmaf(pr, fs, kFixMagic)) - kFixMagicBits);
+        atomicAdd(reinterpret_cast<int *>(s_im) + ib, __float_as_int(fmaf(pi, fs, kFixMagic)) - kFixMagicBits);
+    } else if (DENSE) {
+        atomicAdd(s_re + ib, pr);
+        atomicAdd(s_im + ib, pi);
+    } else {
+        red_add_f2(gb + gidx, make_float2(pr, pi));
+    }
+}
+
 template <bool DENSE, bool FIXED>
 __device__ __forceinline__ void scatter_rows(int i0, int nv, int lane, const int2 *s_meta, const int *s_off,
                                              const float2 *s_d, const float2 *__restrict__ fbin, float *s_re,
                                              float *s_im, int wy0, int wx0, float2 *__restrict__ gb, int K1,
                                              int K2, float fs) {
     constexpr unsigned FULL = 0xffffffffu;
-    const int half = lane >> 4, col = lane & 15;
     float2 fac = make_float2(0.f, 0.f);
     if (i0 < nv) fac = load_factors(fbin + s_off[i0], s_meta[i0].y, lane);
     for (int i = i0; i < nv; i += kWarps) {
@@ -117,38 +142,65 @@ __device__ __forceinline__ void scatter_rows(int i0, int nv, int lane, const int
         const int2 m = s_meta[i];
         const int T = m.y;
         const int c1 = m.x & 0xffff, c2 = (int)((unsigned)m.x >> 16);
-        const bool cin = col < T;
-        const float g2x = __shfl_sync(FULL, fac.x, 16 + col), g2y = __shfl_sync(FULL, fac.y, 16 + col);
-        int ib = 0, k1 = 0, k2 = 0;
-        if (DENSE) {
-            ib = (c1 - wy0 + half) * kWin + (c2 - wx0 + col);
-        } else {
-            k1 = c1 + half;
-            k2 = c2 + col;
-            k2 -= (k2 >= K2) ? K2 : 0;
-        }
         const float dr = s_d[i].x, di = s_d[i].y;
-        // e = conj(g2[col]) d; cell (t1, col) += conj(g1[t1]) e
-        const float er = fmaf(g2x, dr, g2y * di), ei = fmaf(g2x, di, -g2y * dr);
+        if (T <= 8) {                                // warp-uniform: one row per warp
+            const int g = lane >> 3, col = lane & 7;
+            const bool cin = col < T;
+            const float g2x = __shfl_sync(FULL, fac.x, 16 + col), g2y = __shfl_sync(FULL, fac.y, 16 + col);
+            // e = conj(g2[col]) d; cell (t1, col) += conj(g1[t1]) e
+            const float er = fmaf(g2x, dr, g2y * di), ei = fmaf(g2x, di, -g2y * dr);
+            int ib = 0, k2 = 0;
+            if (DENSE) {
+                ib = (c1 - wy0 + g) * kAdjS + (c2 - wx0 + col);
+            } else {
+                k2 = c2 + col;
+                k2 -= (k2 >= K2) ? K2 : 0;
+            }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            if (2 * k >= T) break;                   // warp-uniform
-            const int t1 = 2 * k + half;
-            const float g1x = __shfl_sync(FULL, fac.x, t1), g1y = __shfl_sync(FULL, fac.y, t1);
-            if (cin && t1 < T) {
-                const float pr = fmaf(g1x, er, g1y * ei), pi = fmaf(g1x, ei, -g1y * er);
-                if (DENSE && FIXED) {
-                    atomicAdd(reinterpret_cast<int *>(s_re) + ib + 2 * k * kWin,
-                              __float_as_int(fmaf(pr, fs, kFixMagic)) - kFixMagicBits);
-                    atomicAdd(reinterpret_cast<int *>(s_im) + ib + 2 * k * kWin,
-                              __float_as_int(fmaf(pi, fs, kFixMagic)) - kFixMagicBits);
-                } else if (DENSE) {
-                    atomicAdd(s_re + ib + 2 * k * kWin, pr);
-                    atomicAdd(s_im + ib + 2 * k * kWin, pi);
-                } else {
-                    int kk = k1 + 2 * k;
-                    kk -= (kk >= K1) ? K1 : 0;
-                    red_add_f2(gb + (long long)kk * K2 + k2, make_float2(pr, pi));
+            for (int k = 0; k < 2; ++k) {
+                if (4 * k >= T) break;                   // warp-uniform
+                const int t1 = 4 * k + g;
+                const float g1x = __shfl_sync(FULL, fac.x, t1), g1y = __shfl_sync(FULL, fac.y, t1);
+                if (cin && t1 < T) {
+                    const float pr = fmaf(g1x, er, g1y * ei), pi = fmaf(g1x, ei, -g1y * er);
+                    long long gidx = 0;
+                    if (!DENSE) {
+                        int kk = c1 + t1;
+                        kk -= (kk >= K1) ? K1 : 0;
+                        gidx = (long long)kk * K2 + k2;
+                    }
+                    scatter_cell<DENSE, FIXED>(s_re, s_im, ib + 4 * k * kAdjS, gb, gidx, pr, pi, fs);
+                }
+            }
+        } else {
+            const int half = lane >> 4, col = lane & 15;
+            const bool cin = col < T;
+            const float g2x = __shfl_sync(FULL, fac.x, 16 + col), g2y = __shfl_sync(FULL, fac.y, 16 + col);
+            const float er = fmaf(g2x, dr, g2y * di), ei = fmaf(g2x, di, -g2y * dr);
+            int ib = 0, k2 = 0;
+            if (DENSE) {
+                ib = (c1 - wy0 + 2 * half) * kAdjS + (c2 - wx0 + col);
+            } else {
+                k2 = c2 + col;
+                k2 -= (k2 >= K2) ? K2 : 0;
+            }
+            // steps: two per complete block of 4 box rows, then 1 or 2 for the remainder
+            const int n = 2 * (T >> 2) + min(T & 3, 2);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (k >= n) break;                       // warp-uniform
+                const int dt = 4 * (k >> 1) + (k & 1);   // t1 = dt + 2 half
+                const int t1 = dt + 2 * half;
+                const float g1x = __shfl_sync(FULL, fac.x, t1), g1y = __shfl_sync(FULL, fac.y, t1);
+                if (cin && t1 < T) {
+                    const float pr = fmaf(g1x, er, g1y * ei), pi = fmaf(g1x, ei, -g1y * er);
+                    long long gidx = 0;
+                    if (!DENSE) {
+                        int kk = c1 + t1;
+                        kk -= (kk >= K1) ? K1 : 0;
+                        gidx = (long long)kk * K2 + k2;
+                    }
+                    scatter_cell<DENSE, FIXED>(s_re, s_im, ib + dt * kAdjS, gb, gidx, pr, pi, fs);
                 }
             }
         }
@@ -173,6 +225,7 @@ __device__ __forceinline__ void scatter_rows_rank(int i0, int nv, int lane, int 
         const int T = m.y;
         const int c1 = m.x & 0xffff, c2 = (int)((unsigned)m.x >> 16);
         const bool cin = col < T;
+        const int n = 2 * (T >> 2) + min(T & 3, 2);      // steps over the box rows (as in scatter_rows)
         const float dr = s_d[i].x, di = s_d[i].y;
         float accr[8], acci[8];
 #pragma unroll
@@ -190,38 +243,33 @@ __device__ __forceinline__ void scatter_rows_rank(int i0, int nv, int lane, int 
             const float er = fmaf(g2x, dr, g2y * di), ei = fmaf(g2x, di, -g2y * dr);
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                if (2 * k >= T) break;
-                const int t1 = 2 * k + half;
+                if (k >= n) break;
+                const int t1 = 4 * (k >> 1) + (k & 1) + 2 * half;
                 const float g1x = __shfl_sync(FULL, fac.x, t1), g1y = __shfl_sync(FULL, fac.y, t1);
                 accr[k] = fmaf(g1x, er, fmaf(g1y, ei, accr[k]));
                 acci[k] = fmaf(g1x, ei, fmaf(-g1y, er, acci[k]));
             }
         }
-        int ib = 0, k1 = 0, k2 = 0;
-        if (DENSE) {
-            ib = (c1 - wy0 + half) * kWin + (c2 - wx0 + col);
-        } else {
-            k1 = c1 + half;
+        int k2 = 0;
+        if (!DENSE) {
             k2 = c2 + col;
             k2 -= (k2 >= K2) ? K2 : 0;
         }
+        // accumulator k holds box row 4 (k / 2) + k % 2 + 2 half: the two halves' rows of one step
+        // are 2 apart, 16 banks at the window's row stride kAdjS (no conflicts)
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            if (2 * k >= T) break;
-            if (cin && 2 * k + half < T) {
-                if (DENSE && FIXED) {
-                    atomicAdd(reinterpret_cast<int *>(s_re) + ib + 2 * k * kWin,
-                              __float_as_int(fmaf(accr[k], fs, kFixMagic)) - kFixMagicBits);
-                    atomicAdd(reinterpret_cast<int *>(s_im) + ib + 2 * k * kWin,
-                              __float_as_int(fmaf(acci[k], fs, kFixMagic)) - kFixMagicBits);
-                } else if (DENSE) {
-                    atomicAdd(s_re + ib + 2 * k * kWin, accr[k]);
-                    atomicAdd(s_im + ib + 2 * k * kWin, acci[k]);
-                } else {
-                    int kk = k1 + 2 * k;
+            if (k >= n) break;
+            const int t1 = 4 * (k >> 1) + (k & 1) + 2 * half;
+            if (cin && t1 < T) {
+                long long gidx = 0;
+                if (!DENSE) {
+                    int kk = c1 + t1;
                     kk -= (kk >= K1) ? K1 : 0;
-                    red_add_f2(gb + (long long)kk * K2 + k2, make_float2(accr[k], acci[k]));
+                    gidx = (long long)kk * K2 + k2;
                 }
+                const int ib = DENSE ? (c1 - wy0 + t1) * kAdjS + (c2 - wx0 + col) : 0;
+                scatter_cell<DENSE, FIXED>(s_re, s_im, ib, gb, gidx, accr[k], acci[k], fs);
             }
         }
     }
@@ -428,8 +476,8 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
     const int R = MULTI ? R_ : 1;
     __shared__ alignas(128) float2 s_grid[kWin * kWinP];
     __shared__ alignas(8) uint64_t s_bar;
-    __shared__ float s_re[kWin * kWin];
-    __shared__ float s_im[kWin * kWin];
+    __shared__ float s_re[kWin * kAdjS];     // adjoint window planes, row stride kAdjS
+    __shared__ float s_im[kWin * kAdjS];
     __shared__ int2 s_meta[kBinMax];
     __shared__ int s_off[kBinMax];        // factor offset relative to the bin's first row
     __shared__ float2 s_y[kBinMax];       // sigma2 * y
@@ -493,8 +541,8 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
                 s_grid[r * kWinP + c] = gl[(long long)k1 * K2 + k2];
             }
             if (MODE != kGather && MODE != kDual) {
-                s_re[i] = 0.f;
-                s_im[i] = 0.f;
+                s_re[r * kAdjS + c] = 0.f;
+                s_im[r * kAdjS + c] = 0.f;
             }
         }
     }
@@ -570,13 +618,13 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
         if ((MODE == kScatter || MODE == kNormal) && dense) {
             __syncthreads();
             for (int q = threadIdx.x; q < kWin * kWin; q += blockDim.x) {
-                float re = s_re[q], im = s_im[q];
+                const int r = q / kWin, c = q - r * kWin;
+                float re = s_re[r * kAdjS + c], im = s_im[r * kAdjS + c];
                 if (fixed) {
                     re = float(__float_as_int(re)) * finv;     // exact scaling by a power of two
                     im = float(__float_as_int(im)) * finv;
                 }
                 if (re != 0.f || im != 0.f) {
-                    const int r = q / kWin, c = q - r * kWin;
                     int k1 = wy0 + r;
                     while (k1 >= K1) k1 -= K1;
                     int k2 = wx0 + c;

@@ -42,6 +42,11 @@ WORKLOADS = {
     # 5e5 visibilities/channel with w-terms; ~6 GB on the device, inputs > L2.
     "prof_1024": dict(config_id=4, ny=1024, nx=1024, L=8, M=500_000, B=4, C=1,
                       qy=4, qx=4, overlap=0.1, w_max=2000.0, n_iter=20, n_reweight=0),
+    # Profiling case of the 2048x2048 configuration: its per-channel density
+    # (4e6 visibilities per channel in 8 blocks over a 4096^2 grid, no w-term)
+    # on 4 channels of one sub-cube; about 8 GB on the device.
+    "prof_2048": dict(config_id=5, ny=2048, nx=2048, L=4, M=4_000_000, B=8, C=1,
+                      qy=8, qx=8, overlap=0.1, w_max=0.0, n_iter=20, n_reweight=0),
     # Parity-test shapes: several tiles, ragged sizes, w-terms, two sub-cubes.
     "mid_w": dict(config_id=11, ny=96, nx=160, L=4, M=12000, B=3, C=2,
                   qy=3, qx=2, overlap=0.15, w_max=2000.0, n_iter=20, n_reweight=1),
