@@ -5,6 +5,7 @@
 #include "fhs_internal.h"
 
 #include <algorithm>
+#include <climits>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -137,47 +138,164 @@ inline cudaStream_t S(void *s) { return static_cast<cudaStream_t>(s); }
 // parts of at most `split` rows (equal parts when `even`, else full parts and
 // a remainder); shorter runs are packed in order into sparse bins of at most
 // sparse_max rows, which take the global-memory path.
-void make_bins(const int2 *meta, const std::vector<long long> &seg_off, int n_seg, int ntx, long long dense_min,
-               long long split, bool even, long long sparse_max, std::vector<long long> &bstart,
-               std::vector<int> &bseg, std::vector<int> &btile) {
-    bstart.clear();
-    bseg.clear();
-    btile.clear();
+// Tile bins of the pass over G.  A channel's rows are sorted, inside each
+// data block's segment, by the grid tile of their box corner.  For every tile,
+// the runs of all B blocks together form dense bins when they hold at least
+// dense_min rows: the runs are the bin's pieces (one block each, in block
+// order), cut into parts of at most `split` rows (`even`: parts of about equal
+// size).  The rows of tiles below dense_min are sparse: consecutive ones of a
+// block form sparse bins (tile -1) of one piece of at most sparse_max rows.
+// With B > kBinMaxPieces every block is binned on its own (tile bins of one
+// piece).
+struct BinList {
+    std::vector<int> pptr, chan, tile, plen, pblk;
+    std::vector<long long> pstart, fbase;
+    void clear() {
+        pptr.assign(1, 0);
+        fbase.clear();
+        chan.clear();
+        tile.clear();
+        plen.clear();
+        pblk.clear();
+        pstart.clear();
+    }
+    void piece(long long start, long long len, int blk) {
+        pstart.push_back(start);
+        plen.push_back(int(len));
+        pblk.push_back(blk);
+    }
+    void close(int l, int k) {
+        fbase.push_back(pstart[pptr.back()]);    // the bin's first row (its factor offset is filled in later)
+        chan.push_back(l);
+        tile.push_back(k);
+        pptr.push_back(int(pstart.size()));
+    }
+    int n_bin() const { return int(chan.size()); }
+};
+
+void make_bins(const int2 *meta, const long long *fptr, const std::vector<long long> &seg_off, int L, int B, int ntx,
+               long long dense_min, long long split, bool even, long long sparse_max, BinList &out) {
+    out.clear();
     auto key = [&](long long i) {
         return (meta[i].x & 0xffff) / kTile * ntx + (int)((unsigned)meta[i].x >> 16) / kTile;
     };
-    for (int sg = 0; sg < n_seg; ++sg) {
-        const long long a = seg_off[sg], b = seg_off[sg + 1];
-        long long sp0 = -1;                          // open sparse run start
-        auto flush_sparse = [&](long long end) {
-            for (long long q = sp0; q < end; q += sparse_max) {
-                bstart.push_back(q);
-                bseg.push_back(sg);
-                btile.push_back(-1);
+    // blocks share bins while a bin's factor offsets stay 32-bit (rows of one channel span less
+    // than 2^31 factor values)
+    bool merge = B <= kBinMaxPieces;
+    for (int l = 0; l < L && merge; ++l)
+        merge = fptr[seg_off[(l + 1) * B]] - fptr[seg_off[l * B]] < INT_MAX;
+    const int G = merge ? B : 1;                     // blocks binned together
+    struct Run { long long a, e; };
+    for (int l = 0; l < L; ++l) {
+        for (int b0 = 0; b0 < B; b0 += G) {
+            std::vector<long long> pos(G), end(G), sp_a(G, -1), sp_e(G, -1);
+            for (int g = 0; g < G; ++g) {
+                pos[g] = seg_off[l * B + b0 + g];
+                end[g] = seg_off[l * B + b0 + g + 1];
             }
-            sp0 = -1;
-        };
-        long long i = a;
-        while (i < b) {
-            const int k = key(i);
-            long long j = i + 1;
-            while (j < b && key(j) == k) ++j;
-            if (j - i >= dense_min) {
-                if (sp0 >= 0) flush_sparse(i);
-                const long long n = j - i;
-                const long long parts = (n + split - 1) / split;
-                for (long long t = 0; t < parts; ++t) {
-                    bstart.push_back(even ? i + n * t / parts : i + t * split);
-                    bseg.push_back(sg);
-                    btile.push_back(k);
+            auto flush_sparse = [&](int g) {
+                for (long long q = sp_a[g]; q < sp_e[g]; q += sparse_max) {
+                    out.piece(q, std::min(sparse_max, sp_e[g] - q), b0 + g);
+                    out.close(l, -1);
                 }
-            } else if (sp0 < 0) {
-                sp0 = i;
+                sp_a[g] = sp_e[g] = -1;
+            };
+            std::vector<Run> runs(G);
+            for (;;) {
+                // the smallest tile key among the blocks' next runs
+                int k = INT_MAX;
+                for (int g = 0; g < G; ++g)
+                    if (pos[g] < end[g]) k = std::min(k, key(pos[g]));
+                if (k == INT_MAX) break;
+                long long n = 0;
+                for (int g = 0; g < G; ++g) {
+                    runs[g] = {pos[g], pos[g]};
+                    if (pos[g] < end[g] && key(pos[g]) == k) {
+                        long long e = pos[g] + 1;
+                        while (e < end[g] && key(e) == k) ++e;
+                        runs[g].e = e;
+                        n += e - pos[g];
+                        pos[g] = e;
+                    }
+                }
+                if (n >= dense_min) {
+                    const long long parts = (n + split - 1) / split;
+                    const long long cap = even ? (n + parts - 1) / parts : split;
+                    // a block's pending sparse rows end where its run of this tile starts
+                    for (int g = 0; g < G; ++g)
+                        if (runs[g].e > runs[g].a && sp_a[g] >= 0) flush_sparse(g);
+                    long long room = cap;
+                    bool open = false;
+                    for (int g = 0; g < G; ++g) {
+                        long long a = runs[g].a;
+                        while (a < runs[g].e) {
+                            const long long take = std::min(room, runs[g].e - a);
+                            out.piece(a, take, b0 + g);
+                            open = true;
+                            a += take;
+                            room -= take;
+                            if (room == 0) {
+                                out.close(l, k);
+                                open = false;
+                                room = cap;
+                            }
+                        }
+                    }
+                    if (open) out.close(l, k);
+                } else {
+                    for (int g = 0; g < G; ++g) {
+                        if (runs[g].e == runs[g].a) continue;
+                        if (sp_e[g] != runs[g].a && sp_a[g] >= 0) flush_sparse(g);
+                        if (sp_a[g] < 0) sp_a[g] = runs[g].a;
+                        sp_e[g] = runs[g].e;
+                    }
+                }
             }
-            i = j;
+            for (int g = 0; g < G; ++g)
+                if (sp_a[g] >= 0) flush_sparse(g);
         }
-        if (sp0 >= 0) flush_sparse(b);
     }
+    for (long long &f : out.fbase) f = fptr[f];
+}
+
+// A bin list on the device (the arrays the pass over G reads) and its bytes.
+struct DevBins {
+    int *pptr = nullptr, *chan = nullptr, *tile = nullptr, *plen = nullptr, *pblk = nullptr;
+    long long *pstart = nullptr, *fbase = nullptr;
+    int n_bin = 0, n_piece = 0, dense_min = 0, split = 0;
+    size_t bytes = 0;
+};
+
+DevBins current_bins(const fhs_problem *p) {
+    DevBins d;
+    d.pptr = p->bin_pptr;
+    d.fbase = p->bin_fbase;
+    d.chan = p->bin_chan;
+    d.tile = p->bin_tile;
+    d.pstart = p->piece_start;
+    d.plen = p->piece_len;
+    d.pblk = p->piece_blk;
+    d.n_bin = p->n_bin;
+    d.n_piece = p->n_piece;
+    d.dense_min = p->bin_dense_min;
+    d.split = p->bin_split;
+    d.bytes = sizeof(int) * (3 * size_t(p->n_bin) + 1 + 2 * size_t(p->n_piece)) +
+              sizeof(long long) * (size_t(p->n_piece) + p->n_bin);
+    return d;
+}
+
+void use_bins(fhs_problem *p, const DevBins &d) {
+    p->bin_pptr = d.pptr;
+    p->bin_fbase = d.fbase;
+    p->bin_chan = d.chan;
+    p->bin_tile = d.tile;
+    p->piece_start = d.pstart;
+    p->piece_len = d.plen;
+    p->piece_blk = d.pblk;
+    p->n_bin = d.n_bin;
+    p->n_piece = d.n_piece;
+    p->bin_dense_min = d.dense_min;
+    p->bin_split = d.split;
 }
 
 // The device-side error flag, already copied to the host as h after a
@@ -907,15 +1025,13 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
 
     // ---- tile bins for the single-pass data kernel (make_bins); fhs_autotune_bins
     // may replace them with a measured choice
-    std::vector<long long> bstart;
-    std::vector<int> bseg, btile;
+    BinList bins;
     p->ntx = ntx;
-    make_bins(meta.data(), p->seg_off, p->n_seg, ntx, kBinDenseMin, kBinSplitMax, false, kBinSplitMax, bstart, bseg,
-              btile);
+    make_bins(meta.data(), fptr.data(), p->seg_off, L, B, ntx, kBinDenseMin, kBinSplitMax, false, kBinSplitMax, bins);
     p->bin_dense_min = int(kBinDenseMin);
     p->bin_split = int(kBinSplitMax);
-    p->n_bin = int(bseg.size());
-    bstart.push_back(Mtot);
+    p->n_bin = bins.n_bin();
+    p->n_piece = int(bins.pstart.size());
 
     std::vector<double> eps(p->n_seg), inv_sig(p->n_seg);
     for (int l = 0; l < L; ++l) {
@@ -945,9 +1061,13 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
     if ((st = guard(dev_alloc(p, &p->blk_norm2, p->n_seg))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->eps, p->n_seg, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->blk_scale, p->n_seg, false))) != FHS_OK) return st;
-    if ((st = guard(dev_alloc(p, &p->bin_start, p->n_bin + 1, false))) != FHS_OK) return st;
-    if ((st = guard(dev_alloc(p, &p->bin_seg, p->n_bin, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->bin_pptr, p->n_bin + 1, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->bin_fbase, p->n_bin, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->bin_chan, p->n_bin, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->bin_tile, p->n_bin, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->piece_start, p->n_piece, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->piece_len, p->n_piece, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->piece_blk, p->n_piece, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->chunk_start, p->n_chunk + 1, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->chunk_seg, p->n_chunk, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &d_kap, Mtot, false))) != FHS_OK) return st;
@@ -967,9 +1087,13 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
     if ((st = guard(upload(p->d_seg_off, p->seg_off.data(), p->n_seg + 1, s))) != FHS_OK) return st;
     if ((st = guard(upload(p->eps, eps.data(), p->n_seg, s))) != FHS_OK) return st;
     if ((st = guard(upload(p->blk_scale, ones.data(), p->n_seg, s))) != FHS_OK) return st;
-    if ((st = guard(upload(p->bin_start, bstart.data(), bstart.size(), s))) != FHS_OK) return st;
-    if ((st = guard(upload(p->bin_seg, bseg.data(), bseg.size(), s))) != FHS_OK) return st;
-    if ((st = guard(upload(p->bin_tile, btile.data(), btile.size(), s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->bin_pptr, bins.pptr.data(), bins.pptr.size(), s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->bin_fbase, bins.fbase.data(), bins.fbase.size(), s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->bin_chan, bins.chan.data(), bins.chan.size(), s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->bin_tile, bins.tile.data(), bins.tile.size(), s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->piece_start, bins.pstart.data(), bins.pstart.size(), s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->piece_len, bins.plen.data(), bins.plen.size(), s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->piece_blk, bins.pblk.data(), bins.pblk.size(), s))) != FHS_OK) return st;
     if ((st = guard(upload(p->chunk_start, cstart.data(), cstart.size(), s))) != FHS_OK) return st;
     if ((st = guard(upload(p->chunk_seg, cseg.data(), cseg.size(), s))) != FHS_OK) return st;
     if ((st = guard(upload(d_kap, kap.data(), Mtot, s))) != FHS_OK) return st;
@@ -1249,7 +1373,11 @@ fhs_status fhs_estimate_bytes(const fhs_params *params, const double *w, int64_t
     r += 8 * M + 8 * (M + 1) + 8 * n_fac + 8 * M * 4 + 4 * M;        // meta, factor offsets, G factors, y, d, scratch,
                                                                      // perm, row bounds
     r += 8 * (nseg + 1) + 8 * nseg + 8 * nseg + 4 * nseg;            // segments, norms, eps, scales
-    r += 8 * (nbin + 1) + 8 * nbin + 8 * (nchunk + 1) + 4 * nchunk;  // bins and chunks
+    // bins (first piece, channel, tile) and their pieces (start, length, block): a piece is a run of one
+    // block inside one tile, or a sparse run, so there are at most bins + (segments x tiles) of them
+    const long long ntiles = (long long)((2 * q.ny + kTile - 1) / kTile) * ((2 * q.nx + kTile - 1) / kTile);
+    const long long npiece = nbin + std::min(M, nseg * ntiles);
+    r += 4 * (nbin + 1) + 16 * nbin + 16 * npiece + 8 * (nchunk + 1) + 4 * nchunk;
     r += 4 * (q.ny + q.nx);                                          // Z scaling
     r += 8 * K * L * 4;                                              // grids
     r += 4 * N * L * 3 + 16 + 16 * L + 4 * L;                        // images, reductions, PSF factors
@@ -1681,7 +1809,9 @@ fhs_status fhs_autotune_bins(fhs_problem *p, void *stream, int32_t *dense_min_ou
     }
     CU(cudaStreamSynchronize(s));
     std::vector<int2> meta(p->Mtot);
+    std::vector<long long> fptr(p->Mtot + 1);
     CU(cudaMemcpyAsync(meta.data(), p->meta, sizeof(int2) * p->Mtot, cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(fptr.data(), p->fptr, sizeof(long long) * (p->Mtot + 1), cudaMemcpyDeviceToHost, s));
     // a forward grid of a random image (scratch: coef_tmp, grid_in, grid_aux); the
     // normal-mode pass accumulates into the first L block grids, zero again after
     const long long LN = (long long)p->L * p->N;
@@ -1695,23 +1825,23 @@ fhs_status fhs_autotune_bins(fhs_problem *p, void *stream, int32_t *dense_min_ou
     CU(launch_zpad(p, p->coef_tmp, p->grid_in, s));
     TRY(fft(p, p->grid_in, p->grid_aux, CUFFT_FORWARD, s));
 
-    struct Bins {
-        long long *start = nullptr;
-        int *seg = nullptr, *tile = nullptr;
-        int n = 0, dense_min = 0, split = 0;
-        size_t bytes = 0;
-    };
-    Bins cur{p->bin_start, p->bin_seg, p->bin_tile, p->n_bin, p->bin_dense_min, p->bin_split,
-             sizeof(long long) * (p->n_bin + 1) + 2 * sizeof(int) * p->n_bin};
+    const DevBins cur = current_bins(p);
     cudaStream_t home = p->home;
     p->home = s;                                       // candidate arrays live on this call's stream
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     fhs_status rs = FHS_OK;
-    auto time_bins = [&](const Bins &b, float &ms) -> fhs_status {
-        p->bin_start = b.start;
-        p->bin_seg = b.seg;
-        p->bin_tile = b.tile;
-        p->n_bin = b.n;
+    auto release = [&](const DevBins &b) {
+        dev_free(p, b.pptr);
+        dev_free(p, b.fbase);
+        dev_free(p, b.chan);
+        dev_free(p, b.tile);
+        dev_free(p, b.pstart);
+        dev_free(p, b.plen);
+        dev_free(p, b.pblk);
+        p->bytes -= b.bytes;
+    };
+    auto time_bins = [&](const DevBins &b, float &ms) -> fhs_status {
+        use_bins(p, b);
         CU(launch_normal(p, p->grid_aux, p->grid_scr, s, !p->dr));          // warm-up
         CU(cudaEventRecord(e0, s));
         for (int r = 0; r < 3; ++r) CU(launch_normal(p, p->grid_aux, p->grid_scr, s, !p->dr));
@@ -1720,7 +1850,7 @@ fhs_status fhs_autotune_bins(fhs_problem *p, void *stream, int32_t *dense_min_ou
         CU(cudaEventElapsedTime(&ms, e0, e1));
         return FHS_OK;
     };
-    Bins best = cur;
+    DevBins best = cur;
     float best_ms = 0.f;
     auto run = [&]() -> fhs_status {
         CU(cudaEventCreate(&e0));
@@ -1728,61 +1858,51 @@ fhs_status fhs_autotune_bins(fhs_problem *p, void *stream, int32_t *dense_min_ou
         TRY(time_bins(cur, best_ms));
         const long long dmins[] = {16, 32, 48, 96};
         const long long splits[] = {192, 288, kBinSplitMax};
-        std::vector<long long> bstart;
-        std::vector<int> bseg, btile;
+        BinList bl;
         for (long long dm : dmins)
             for (long long sp : splits) {
                 if (sp > kBinSplitMax) continue;
-                make_bins(meta.data(), p->seg_off, p->n_seg, p->ntx, dm, sp, true, kBinSplitMax, bstart, bseg, btile);
-                Bins c;
-                c.n = int(bseg.size());
+                make_bins(meta.data(), fptr.data(), p->seg_off, p->L, p->B, p->ntx, dm, sp, true, kBinSplitMax, bl);
+                DevBins c;
+                c.n_bin = bl.n_bin();
+                c.n_piece = int(bl.pstart.size());
                 c.dense_min = int(dm);
                 c.split = int(sp);
-                bstart.push_back(p->Mtot);
-                TRY(dev_alloc(p, &c.start, bstart.size(), false));
-                TRY(dev_alloc(p, &c.seg, bseg.size(), false));
-                TRY(dev_alloc(p, &c.tile, btile.size(), false));
-                c.bytes = sizeof(long long) * bstart.size() + sizeof(int) * (bseg.size() + btile.size());
-                TRY(upload(c.start, bstart.data(), bstart.size(), s));
-                TRY(upload(c.seg, bseg.data(), bseg.size(), s));
-                TRY(upload(c.tile, btile.data(), btile.size(), s));
+                TRY(dev_alloc(p, &c.pptr, bl.pptr.size(), false));
+                TRY(dev_alloc(p, &c.fbase, bl.fbase.size(), false));
+                TRY(dev_alloc(p, &c.chan, bl.chan.size(), false));
+                TRY(dev_alloc(p, &c.tile, bl.tile.size(), false));
+                TRY(dev_alloc(p, &c.pstart, bl.pstart.size(), false));
+                TRY(dev_alloc(p, &c.plen, bl.plen.size(), false));
+                TRY(dev_alloc(p, &c.pblk, bl.pblk.size(), false));
+                c.bytes = sizeof(int) * (bl.pptr.size() + bl.chan.size() + bl.tile.size() + bl.plen.size() +
+                                         bl.pblk.size()) + sizeof(long long) * (bl.pstart.size() + bl.fbase.size());
+                TRY(upload(c.pptr, bl.pptr.data(), bl.pptr.size(), s));
+                TRY(upload(c.fbase, bl.fbase.data(), bl.fbase.size(), s));
+                TRY(upload(c.chan, bl.chan.data(), bl.chan.size(), s));
+                TRY(upload(c.tile, bl.tile.data(), bl.tile.size(), s));
+                TRY(upload(c.pstart, bl.pstart.data(), bl.pstart.size(), s));
+                TRY(upload(c.plen, bl.plen.data(), bl.plen.size(), s));
+                TRY(upload(c.pblk, bl.pblk.data(), bl.pblk.size(), s));
                 float ms = 0.f;
                 TRY(time_bins(c, ms));
-                Bins loser = c;
+                DevBins loser = c;
                 if (ms < 0.97f * best_ms) {            // keep a candidate only for a clear gain
                     loser = best;
                     best = c;
                     best_ms = ms;
                 }
-                if (loser.start != cur.start) {
-                    dev_free(p, loser.start);
-                    dev_free(p, loser.seg);
-                    dev_free(p, loser.tile);
-                    p->bytes -= loser.bytes;
-                }
+                if (loser.pptr != cur.pptr) release(loser);
             }
         return FHS_OK;
     };
     rs = run();
-    if (rs != FHS_OK && best.start != cur.start) {      // a failed search keeps the original bins
-        dev_free(p, best.start);
-        dev_free(p, best.seg);
-        dev_free(p, best.tile);
-        p->bytes -= best.bytes;
+    if (rs != FHS_OK && best.pptr != cur.pptr) {        // a failed search keeps the original bins
+        release(best);
         best = cur;
     }
-    p->bin_start = best.start;
-    p->bin_seg = best.seg;
-    p->bin_tile = best.tile;
-    p->n_bin = best.n;
-    p->bin_dense_min = best.dense_min;
-    p->bin_split = best.split;
-    if (best.start != cur.start) {
-        dev_free(p, cur.start);
-        dev_free(p, cur.seg);
-        dev_free(p, cur.tile);
-        p->bytes -= cur.bytes;
-    }
+    use_bins(p, best);
+    if (best.pptr != cur.pptr) release(cur);
     p->home = home;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);

@@ -26,7 +26,11 @@ constexpr int kDdeTaps = 5;        // DDE kernels: kDdeTaps x kDdeTaps grid taps
 #endif
 // Rows per bin of the data kernel: at most kBinSplitMax (its shared-memory
 // staging capacity); tile runs shorter than kBinDenseMin go to sparse bins.
-constexpr long long kBinSplitMax = FHS_BIN_MAX, kBinDenseMin = 48;          // grid tile (cells) used to sort visibilities
+constexpr long long kBinSplitMax = FHS_BIN_MAX, kBinDenseMin = 48;
+// Pieces (runs of one data block each) a bin may hold: the blocks of a channel
+// share tile bins while B <= kBinMaxPieces (otherwise every bin holds rows of
+// one block, as one piece).
+constexpr long long kBinMaxPieces = 16;          // grid tile (cells) used to sort visibilities
 constexpr float kSaraScale = 1.0f / 3.0f;   // 1/sqrt(9 bases)
 
 // ---------------------------------------------------------------------------
@@ -95,9 +99,16 @@ struct fhs_problem {
     float *blk_scale = nullptr;               // [n_seg]  (1 - m_b)
     int n_bin = 0, ntx = 0;                   // tile bins of the single-pass data kernel
     int bin_dense_min = 0, bin_split = 0;     // binning in use (defaults or fhs_autotune_bins)
-    long long *bin_start = nullptr;           // [n_bin+1]
-    int *bin_seg = nullptr;                   // [n_bin]
+    // a bin is a list of pieces: runs of sorted rows of one data block each (the rows of all
+    // blocks of a channel whose boxes start in one grid tile, or a run of sparse rows of one block)
+    int n_piece = 0;
+    int *bin_pptr = nullptr;                  // [n_bin+1] first piece of each bin
+    long long *bin_fbase = nullptr;           // [n_bin] factor offset (fptr) of each bin's first row
+    int *bin_chan = nullptr;                  // [n_bin] channel
     int *bin_tile = nullptr;                  // [n_bin] tile key, -1 = sparse (global path)
+    long long *piece_start = nullptr;         // [n_piece] first row (sorted order)
+    int *piece_len = nullptr;                 // [n_piece] rows
+    int *piece_blk = nullptr;                 // [n_piece] block b of the channel
     int n_chunk = 0;
     long long *chunk_start = nullptr;         // [n_chunk+1]
     int *chunk_seg = nullptr;                 // [n_chunk]

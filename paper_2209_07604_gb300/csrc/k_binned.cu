@@ -60,6 +60,11 @@ constexpr int kBinMax = FHS_BIN_MAX;    // visibilities per bin (host splits lon
 // integer of magnitude below 2^21 and adds at most kBinMax of them to a cell;
 // the sum stays inside int32 only while kBinMax <= 1024.
 static_assert(kBinMax <= 1024, "the fixed-point scatter window overflows int32 for bins above 1024 rows");
+static_assert(kBinMax <= 65536, "row offsets of a bin");
+// Pieces of a bin: runs of rows of one data block each (a tile's rows of all
+// blocks of a channel share one bin); the host merges blocks only while B <= kMaxPieces.
+constexpr int kMaxPieces = int(kBinMaxPieces);
+static_assert(kMaxPieces <= 256, "piece index of a row is one byte");
 
 // Factors of one row for one warp: lane t < T holds g1[t], lane 16 + t holds
 // g2[t]; the other lanes hold 0.
@@ -69,18 +74,6 @@ __device__ __forceinline__ float2 load_factors(const float2 *__restrict__ f, int
     if (col < T) r = __ldcs(f + half * T + col);
     return r;
 }
-
-// Compensated (Kahan) FP32 accumulation for the block norms: a warp sums at
-// most kBinMax / kWarps visibilities this way; warps and CTAs combine in FP64.
-struct Kahan {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float x) {
-        const float y = x - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-};
 
 // Modes of the pass: kDual (the data term's dual pass), kGather (Phi only:
 // vis_bin[i] = G_i . Xhat), kScatter (Phi^H only, and the data term's scatter
@@ -366,13 +359,17 @@ __device__ __forceinline__ float2 gather_terms(const float2 *__restrict__ f, int
 
 // Phase 1 of a bin: one row per thread (rows are sorted by T inside each tile
 // run, so a warp's rows mostly share T).  kDual: the data-dual pre-update
-// d = s_b d + sigma2 (phi - y) into s_d, the bin's output and the block norm;
-// kGather: phi to the output; kNormal: phi into s_d for the scatter.
+// d = s_b d + sigma2 (phi - y) (s_b of the row's block) into s_d and the
+// output, |d|^2 into s_n2 for the block norms; kGather: phi to the output;
+// kNormal: phi into s_d for the scatter.  s_off: each row's factor offset
+// from fbin, s_v: its visibility index, s_pc: its piece (block) in the bin.
 template <int MODE, bool DENSE>
-__device__ __forceinline__ void gather_phase(int nv, int R, const int2 *s_meta, const int *s_off, const float2 *s_y,
-                                             float2 *s_d, const float2 *__restrict__ fbin, const float2 *s_grid,
+__device__ __forceinline__ void gather_phase(int nv, int R, const int2 *s_meta, const int *s_off,
+                                             const long long *s_v, const unsigned char *s_pc, const float *s_psc,
+                                             const float2 *s_y, float2 *s_d, float *s_n2,
+                                             const float2 *__restrict__ fbin, const float2 *s_grid,
                                              int wy0, int wx0, const float2 *__restrict__ gl, int K1, int K2,
-                                             float sc, float sigma2, float2 *__restrict__ dvis_bin, Kahan &nrm) {
+                                             float sigma2, float2 *__restrict__ dvis) {
     const int nvr = (nv + 31) & ~31;                 // whole warps: the max below takes every lane
     for (int i = threadIdx.x; i < nvr; i += blockDim.x) {
         const bool valid = i < nv;
@@ -397,13 +394,14 @@ __device__ __forceinline__ void gather_phase(int nv, int R, const int2 *s_meta, 
         if (MODE == kDual) {
             const float2 dold = s_d[i];
             const float2 sy = s_y[i];
+            const float sc = s_psc[s_pc[i]];
             const float dr = fmaf(sc, dold.x, fmaf(sigma2, phi.x, -sy.x));
             const float di = fmaf(sc, dold.y, fmaf(sigma2, phi.y, -sy.y));
-            dvis_bin[i] = make_float2(dr, di);
+            dvis[s_v[i]] = make_float2(dr, di);
             s_d[i] = make_float2(dr, di);
-            nrm.add(fmaf(dr, dr, di * di));
+            s_n2[i] = fmaf(dr, dr, di * di);
         } else if (MODE == kGather) {
-            dvis_bin[i] = phi;
+            dvis[s_v[i]] = phi;
         } else {
             s_d[i] = phi;
         }
@@ -430,11 +428,14 @@ __device__ __forceinline__ void window_tma(float2 *dst, const CUtensorMap *tmap,
 
 // Bounded wait for phase 0 of the window barrier: at most max_polls polls
 // (each try_wait may suspend the thread for a hardware-defined interval);
-// false if it gave up.
+// false if it gave up.  With `err` given it also gives up once another CTA
+// has recorded a timeout there (checked every 4096 polls), so that a failure
+// costs the launch one wait limit, not one per CTA.
 constexpr int kWindowPolls = 1 << 24;
-__device__ __forceinline__ bool window_wait(uint64_t *bar, int max_polls = kWindowPolls) {
+__device__ __forceinline__ bool window_wait(uint64_t *bar, int max_polls = kWindowPolls, const int *err = nullptr) {
     const uint32_t a = smem_addr(bar);
     for (int it = 0; it < max_polls; ++it) {
+        if (err && (it & 4095) == 4095 && *reinterpret_cast<const volatile int *>(err) != 0) return false;
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -467,8 +468,9 @@ constexpr int kGatherMinBlocks = FHS_GATHER_MIN_BLOCKS;
 template <int MODE, bool MULTI>
 __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGatherMinBlocks)) degrid_grid_binned_kernel(
     const int2 *__restrict__ meta, const long long *__restrict__ fptr, const float2 *__restrict__ gfac,
-    const float2 *__restrict__ y, float2 *__restrict__ dvis, const long long *__restrict__ bin_start,
-    const int *__restrict__ bin_seg, const int *__restrict__ bin_tile, int ntx, int B,
+    const float2 *__restrict__ y, float2 *__restrict__ dvis, const int *__restrict__ bin_pptr,
+    const long long *__restrict__ bin_fbase, const long long *__restrict__ piece_start, const int *__restrict__ piece_len, const int *__restrict__ piece_blk,
+    const int *__restrict__ bin_chan, const int *__restrict__ bin_tile, int ntx, int B,
     const float *__restrict__ blk_scale, double *__restrict__ blk_norm2, const float2 *__restrict__ grid,
     float2 *__restrict__ grid_out, long long K, int K1, int K2, float sigma2, int R_,
     const __grid_constant__ CUtensorMap tmap, int use_tma, const float *__restrict__ gmax, int allow_fixed,
@@ -479,56 +481,80 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
     __shared__ float s_re[kWin * kAdjS];     // adjoint window planes, row stride kAdjS
     __shared__ float s_im[kWin * kAdjS];
     __shared__ int2 s_meta[kBinMax];
-    __shared__ int s_off[kBinMax];        // factor offset relative to the bin's first row
+    __shared__ int s_off[kBinMax];        // factor offset of each row from the bin's base
+    __shared__ long long s_v[kBinMax];    // visibility (sorted) index of each row
+    __shared__ unsigned char s_pc[kBinMax];  // piece of the bin each row belongs to
     __shared__ float2 s_y[kBinMax];       // sigma2 * y
     __shared__ float2 s_d[kBinMax];
-    __shared__ double s_red[kWarps];
+    __shared__ float s_n2[kBinMax];       // |d|^2 of each row (block norms)
+    __shared__ long long s_pstart[kMaxPieces];
+    __shared__ int s_pcum[kMaxPieces + 1];
+    __shared__ int s_pblk[kMaxPieces];
+    __shared__ float s_psc[kMaxPieces];   // block factor s_b of each piece
+    __shared__ double s_pnb[kMaxPieces];  // block norm of each piece
     __shared__ int s_bound, s_bad;        // fixed-point scatter: bin bound (float bits), non-finite flag
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bin = blockIdx.x;
-    const int seg = bin_seg[bin];
+    const int l = bin_chan[bin];
     const int tile = bin_tile[bin];
-    const int l = seg / B;
     const float2 *gl = grid + (long long)l * K;
     float2 *gb = (MODE == kScatter || MODE == kNormal) ? grid_out + (long long)l * K : nullptr;
-    const float sc = MODE == kDual ? blk_scale[seg] : 0.f;
-    const float vsc = (MODE == kScatter && blk_scale) ? blk_scale[seg] : 1.f;
-    const long long v0 = bin_start[bin];
-    const int nv = int(bin_start[bin + 1] - v0);
-    const long long g0 = fptr[v0];
-    const float2 *fbin = gfac + g0;
-    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-        s_meta[i] = meta[v0 + i];
-        s_off[i] = int(fptr[v0 + i] - g0);
-        if (MODE == kDual) {
-            const float2 yy = y[v0 + i];
-            s_y[i] = make_float2(sigma2 * yy.x, sigma2 * yy.y);
-            s_d[i] = dvis[v0 + i];
-        }
-        if (MODE == kScatter) {
-            const float2 dd = dvis[v0 + i];
-            s_d[i] = make_float2(vsc * dd.x, vsc * dd.y);
-        }
-    }
-    if (threadIdx.x == 0) {
-        s_bound = 0;
-        s_bad = 0;
-    }
     const bool dense = tile >= 0;
     int wy0 = 0, wx0 = 0;
     if (dense) {
         wy0 = (tile / ntx) * kTile;
         wx0 = (tile % ntx) * kTile;
     }
-    // the window by TMA when it lies inside the grid (x = wx0 is a multiple of 32 cells: 256-byte aligned)
+    // the window by TMA when it lies inside the grid (x = wx0 is a multiple of 32 cells: 256-byte
+    // aligned), issued first so that it overlaps the staging of the rows
     const bool tma = MODE != kScatter && use_tma && dense && wy0 + kWin <= K1 && wx0 + kWinP <= K2;
-    if (tma) {
-        if (threadIdx.x == 0) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_bar)) : "memory");
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (tma && threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        window_tma(s_grid, &tmap, wx0, wy0, l, &s_bar);
+    }
+    // the bin's pieces: runs of rows of one block each, in the order of their blocks
+    const int pp0 = bin_pptr[bin];
+    const long long fb = bin_fbase[bin];       // factor offset of the bin's first row (the smallest)
+    const int np = bin_pptr[bin + 1] - pp0;
+    if (threadIdx.x < np) {
+        const int b = piece_blk[pp0 + threadIdx.x];
+        s_pstart[threadIdx.x] = piece_start[pp0 + threadIdx.x];
+        s_pcum[threadIdx.x + 1] = piece_len[pp0 + threadIdx.x];
+        s_pblk[threadIdx.x] = b;
+        s_psc[threadIdx.x] = blk_scale ? blk_scale[l * B + b] : 1.f;
+        s_pnb[threadIdx.x] = 0.0;
+    }
+    if (threadIdx.x == 0) {
+        s_bound = 0;
+        s_bad = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_pcum[0] = 0;
+        for (int q = 0; q < np; ++q) s_pcum[q + 1] += s_pcum[q];
+    }
+    __syncthreads();
+    const int nv = s_pcum[np];
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+        int q = 0;
+        while (i >= s_pcum[q + 1]) ++q;
+        const long long v = s_pstart[q] + (i - s_pcum[q]);
+        s_meta[i] = meta[v];
+        s_off[i] = int(fptr[v] - fb);
+        s_pc[i] = (unsigned char)q;
+        if (MODE == kDual || MODE == kGather) s_v[i] = v;
+        if (MODE == kDual) {
+            const float2 yy = y[v];
+            s_y[i] = make_float2(sigma2 * yy.x, sigma2 * yy.y);
+            s_d[i] = dvis[v];
         }
-        __syncthreads();
-        if (threadIdx.x == 0) window_tma(s_grid, &tmap, wx0, wy0, l, &s_bar);
+        if (MODE == kScatter) {
+            const float2 dd = dvis[v];
+            const float vsc = s_psc[q];
+            s_d[i] = make_float2(vsc * dd.x, vsc * dd.y);
+        }
+        if ((MODE == kScatter || MODE == kNormal) && dense && allow_fixed) s_n2[i] = gmax[v];
     }
     if (dense) {
         for (int i = threadIdx.x; i < kWin * kWin; i += blockDim.x) {
@@ -546,22 +572,22 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
             }
         }
     }
-    if (tma && !window_wait(&s_bar)) {
+    __syncthreads();                     // the barrier's initialisation is visible from here on
+    if (tma && !window_wait(&s_bar, kWindowPolls, err)) {
         // the copy did not complete in time: record it, then wait once more (bounded) so that
         // no copy into this CTA's shared memory is still in flight when it moves on
         if (threadIdx.x == 0) atomicExch(err, 2);
-        window_wait(&s_bar);
+        window_wait(&s_bar, kWindowPolls, err);
     }
-    __syncthreads();
-    Kahan nrm;
+    const float2 *fbin = gfac + fb;
     // phase 1: gathers, one row per thread
     if (MODE != kScatter) {
         if (dense)
-            gather_phase<MODE, true>(nv, R, s_meta, s_off, s_y, s_d, fbin, s_grid, wy0, wx0, gl, K1, K2, sc, sigma2,
-                                     dvis + v0, nrm);
+            gather_phase<MODE, true>(nv, R, s_meta, s_off, s_v, s_pc, s_psc, s_y, s_d, s_n2, fbin, s_grid, wy0, wx0,
+                                     gl, K1, K2, sigma2, dvis);
         else
-            gather_phase<MODE, false>(nv, R, s_meta, s_off, s_y, s_d, fbin, s_grid, wy0, wx0, gl, K1, K2, sc, sigma2,
-                                      dvis + v0, nrm);
+            gather_phase<MODE, false>(nv, R, s_meta, s_off, s_v, s_pc, s_psc, s_y, s_d, s_n2, fbin, s_grid, wy0, wx0,
+                                      gl, K1, K2, sigma2, dvis);
     }
     // phase 2: scatters of conj(G_i) s_d[i], one row per warp
     bool fixed = false;
@@ -580,7 +606,7 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
             for (int i = threadIdx.x; i < nv; i += blockDim.x) {
                 const float2 d = s_d[i];
                 bad |= !(isfinite(d.x) && isfinite(d.y));
-                m = fmaxf(m, sqrtf(fmaf(d.x, d.x, d.y * d.y)) * gmax[v0 + i]);
+                m = fmaxf(m, sqrtf(fmaf(d.x, d.x, d.y * d.y)) * s_n2[i]);    // s_n2: the rows' bounds here
             }
             if (m > 0.f) atomicMax(&s_bound, __float_as_int(m));   // non-negative floats order as integers
             if (bad) s_bad = 1;
@@ -635,18 +661,26 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
         }
         return;
     }
-    {
-        double v = double(nrm.s) - double(nrm.c);
+    // block norms ||d_b||^2: the rows are ordered by piece (one block each), so every 32 rows
+    // reduce in FP32 per piece (segmented, towards the first row of each piece), then in FP64
+    __syncthreads();
+    for (int base = warp * 32; base < nv; base += blockDim.x) {
+        const int i = base + lane;
+        const bool ok = i < nv;
+        float v = ok ? s_n2[i] : 0.f;
+        const int pc = ok ? int(s_pc[i]) : -1;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) s_red[warp] = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const float t = __shfl_down_sync(0xffffffffu, v, o);
+            const int q = __shfl_down_sync(0xffffffffu, pc, o);
+            if (lane + o < 32 && q == pc) v += t;
+        }
+        const int prev = __shfl_up_sync(0xffffffffu, pc, 1);
+        if (ok && (lane == 0 || prev != pc)) atomicAdd(&s_pnb[pc], double(v));
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < kWarps; ++w) t += s_red[w];
-        atomicAdd(blk_norm2 + seg, t);
-    }
+    if (threadIdx.x < np && s_pnb[threadIdx.x] != 0.0)
+        atomicAdd(blk_norm2 + l * B + s_pblk[threadIdx.x], s_pnb[threadIdx.x]);
 }
 
 // Test aid for the failure path: one thread waits, with the window wait of
@@ -704,34 +738,36 @@ static WindowMap window_map(const fhs_problem *p, const float2 *grid) {
     return w;
 }
 
-cudaError_t launch_degrid(fhs_problem *p, const float2 *grid, float2 *vis_sorted, cudaStream_t s) {
+// One launch of the pass over G in mode MODE, one CTA per bin.
+template <int MODE>
+cudaError_t launch_pass(fhs_problem *p, const float2 *y, float2 *dvis, const float *blk_scale, double *blk_norm2,
+                        const float2 *grid, float2 *grid_out, float sigma2, const WindowMap &tm, int allow_fixed,
+                        cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
-    const WindowMap tm = window_map(p, grid);
-    (p->rank > 1 ? degrid_grid_binned_kernel<kGather, true> : degrid_grid_binned_kernel<kGather, false>)<<<p->n_bin, 256, 0, s>>>(
-        p->meta, p->fptr, p->gfac, nullptr, vis_sorted, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B,
-        nullptr, nullptr, grid, nullptr, p->K, p->K1, p->K2, 0.f, p->rank, tm.map, tm.ok, p->gmax, 0, p->dev_err);
+    (p->rank > 1 ? degrid_grid_binned_kernel<MODE, true> : degrid_grid_binned_kernel<MODE, false>)<<<p->n_bin, 256, 0, s>>>(
+        p->meta, p->fptr, p->gfac, y, dvis, p->bin_pptr, p->bin_fbase, p->piece_start, p->piece_len, p->piece_blk,
+        p->bin_chan,
+        p->bin_tile, p->ntx, p->B, blk_scale, blk_norm2, grid, grid_out, p->K, p->K1, p->K2, sigma2, p->rank, tm.map,
+        tm.ok, p->gmax, allow_fixed, p->dev_err);
     p->n_launch += 1;
     return cudaGetLastError();
 }
 
-cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s, bool fixed) {
+cudaError_t launch_degrid(fhs_problem *p, const float2 *grid, float2 *vis_sorted, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
-    const WindowMap tm{};                        // no forward window to stage
-    (p->rank > 1 ? degrid_grid_binned_kernel<kScatter, true> : degrid_grid_binned_kernel<kScatter, false>)<<<p->n_bin, 256, 0, s>>>(
-        p->meta, p->fptr, p->gfac, nullptr, const_cast<float2 *>(vis_sorted), p->bin_start, p->bin_seg,
-        p->bin_tile, p->ntx, p->B, nullptr, nullptr, nullptr, grid, p->K, p->K1, p->K2, 0.f, p->rank, tm.map, tm.ok, p->gmax, fixed ? 1 : 0, p->dev_err);
-    p->n_launch += 1;
-    return cudaGetLastError();
+    return launch_pass<kGather>(p, nullptr, vis_sorted, nullptr, nullptr, grid, nullptr, 0.f, window_map(p, grid), 0,
+                                s);
+}
+
+cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s, bool fixed) {
+    return launch_pass<kScatter>(p, nullptr, const_cast<float2 *>(vis_sorted), nullptr, nullptr, nullptr, grid, 0.f,
+                                 WindowMap{}, fixed ? 1 : 0, s);
 }
 
 cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, cudaStream_t s, bool fixed) {
     if (p->n_bin == 0) return cudaSuccess;
-    const WindowMap tm = window_map(p, grid);
-    (p->rank > 1 ? degrid_grid_binned_kernel<kNormal, true> : degrid_grid_binned_kernel<kNormal, false>)<<<p->n_bin, 256, 0, s>>>(
-        p->meta, p->fptr, p->gfac, nullptr, nullptr, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B, nullptr,
-        nullptr, grid, grid_out, p->K, p->K1, p->K2, 0.f, p->rank, tm.map, tm.ok, p->gmax, fixed ? 1 : 0, p->dev_err);
-    p->n_launch += 1;
-    return cudaGetLastError();
+    return launch_pass<kNormal>(p, nullptr, nullptr, nullptr, nullptr, grid, grid_out, 0.f, window_map(p, grid),
+                                fixed ? 1 : 0, s);
 }
 
 // The data term in two passes: the dual pre-update with the block norms
@@ -740,23 +776,13 @@ cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, 
 // grids to combine.
 cudaError_t launch_data_dual(fhs_problem *p, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
-    const WindowMap tm = window_map(p, p->grid_work);
-    (p->rank > 1 ? degrid_grid_binned_kernel<kDual, true> : degrid_grid_binned_kernel<kDual, false>)<<<p->n_bin, 256, 0, s>>>(
-        p->meta, p->fptr, p->gfac, p->y, p->dvis, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B, p->blk_scale,
-        p->blk_norm2, p->grid_work, nullptr, p->K, p->K1, p->K2, float(p->sigma2), p->rank, tm.map, tm.ok,
-        p->gmax, 0, p->dev_err);
-    p->n_launch += 1;
-    return cudaGetLastError();
+    return launch_pass<kDual>(p, p->y, p->dvis, p->blk_scale, p->blk_norm2, p->grid_work, nullptr, float(p->sigma2),
+                              window_map(p, p->grid_work), 0, s);
 }
 
 cudaError_t launch_data_scatter(fhs_problem *p, cudaStream_t s) {
-    if (p->n_bin == 0) return cudaSuccess;
-    const WindowMap tm{};
-    (p->rank > 1 ? degrid_grid_binned_kernel<kScatter, true> : degrid_grid_binned_kernel<kScatter, false>)<<<p->n_bin, 256, 0, s>>>(
-        p->meta, p->fptr, p->gfac, nullptr, p->dvis, p->bin_start, p->bin_seg, p->bin_tile, p->ntx, p->B,
-        p->blk_scale, nullptr, nullptr, p->grid_work, p->K, p->K1, p->K2, 0.f, p->rank, tm.map, tm.ok, p->gmax, 1, p->dev_err);
-    p->n_launch += 1;
-    return cudaGetLastError();
+    return launch_pass<kScatter>(p, nullptr, p->dvis, p->blk_scale, nullptr, nullptr, p->grid_work, 0.f, WindowMap{},
+                                 1, s);
 }
 
 }  // namespace fhs
