@@ -201,6 +201,76 @@ __device__ __forceinline__ void scatter_rows(int i0, int nv, int lane, const int
     }
 }
 
+// Scatter of the rows of a bin whose rows all have at most 8 taps, two rows
+// per warp step: the warp's rows i0, i0 + kWarps, ... are taken in pairs
+// (i, i + kWarps); half v = lane / 16 takes row i + v kWarps, lane
+// (g, col) = ((lane / 8) % 2, lane % 8) its cells (t1, col) for box rows
+// t1 = g, g + 2, ...  Lanes 16 v + t hold g1[t] and lanes 16 v + 8 + t hold
+// g2[t] of the half's row.  The two box rows of a half's step lie 24 banks
+// apart (rows of 8 cells, no conflict); the two halves' rows are unrelated
+// (at most 2-way conflicts).  Per row, half the per-row work of scatter_rows.
+template <bool DENSE, bool FIXED>
+__device__ __forceinline__ void scatter_pairs(int i0, int nv, int lane, const int2 *s_meta, const int *s_off,
+                                              const float2 *s_d, const float2 *__restrict__ fbin, float *s_re,
+                                              float *s_im, int wy0, int wx0, float2 *__restrict__ gb, int K1,
+                                              int K2, float fs) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int v = lane >> 4, g = (lane >> 3) & 1, col = lane & 7, hi = g;
+    auto load = [&](int r) -> float2 {
+        float2 x = make_float2(0.f, 0.f);
+        if (r < nv) {
+            const int T = s_meta[r].y;
+            if (col < T) x = __ldcs(fbin + s_off[r] + hi * T + col);
+        }
+        return x;
+    };
+    float2 fac = load(i0 + v * kWarps);
+    for (int i = i0; i < nv; i += 2 * kWarps) {
+        const int r = i + v * kWarps;                // this half's row (may be past the end)
+        const float2 fnx = load(r + 2 * kWarps);
+        int T = 0, c1 = 0, c2 = 0;
+        float dr = 0.f, di = 0.f;
+        if (r < nv) {
+            const int2 m = s_meta[r];
+            T = m.y;
+            c1 = m.x & 0xffff;
+            c2 = (int)((unsigned)m.x >> 16);
+            dr = s_d[r].x;
+            di = s_d[r].y;
+        }
+        const bool cin = col < T;
+        const int Tm = __reduce_max_sync(FULL, T);
+        const float g2x = __shfl_sync(FULL, fac.x, 16 * v + 8 + col);
+        const float g2y = __shfl_sync(FULL, fac.y, 16 * v + 8 + col);
+        // e = conj(g2[col]) d; cell (t1, col) += conj(g1[t1]) e
+        const float er = fmaf(g2x, dr, g2y * di), ei = fmaf(g2x, di, -g2y * dr);
+        int ib = 0, k2 = 0;
+        if (DENSE) {
+            ib = (c1 - wy0 + g) * kAdjS + (c2 - wx0 + col);
+        } else {
+            k2 = c2 + col;
+            k2 -= (k2 >= K2) ? K2 : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (2 * k >= Tm) break;                      // warp-uniform
+            const int t1 = 2 * k + g;
+            const float g1x = __shfl_sync(FULL, fac.x, 16 * v + t1), g1y = __shfl_sync(FULL, fac.y, 16 * v + t1);
+            if (cin && t1 < T) {
+                const float pr = fmaf(g1x, er, g1y * ei), pi = fmaf(g1x, ei, -g1y * er);
+                long long gidx = 0;
+                if (!DENSE) {
+                    int kk = c1 + t1;
+                    kk -= (kk >= K1) ? K1 : 0;
+                    gidx = (long long)kk * K2 + k2;
+                }
+                scatter_cell<DENSE, FIXED>(s_re, s_im, ib + 2 * k * kAdjS, gb, gidx, pr, pi, fs);
+            }
+        }
+        fac = fnx;
+    }
+}
+
 // Scatter of rows with 1 < R <= kDdeTaps separable terms (DDE rows, see
 // k_nufft.cu): one row per warp as in scatter_rows; each lane sums
 // conj(A_r[t1]) conj(B_r[col]) d over the terms in registers and adds each of
@@ -493,6 +563,7 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
     __shared__ float s_psc[kMaxPieces];   // block factor s_b of each piece
     __shared__ double s_pnb[kMaxPieces];  // block norm of each piece
     __shared__ int s_bound, s_bad;        // fixed-point scatter: bin bound (float bits), non-finite flag
+    __shared__ int s_tmax;                // largest box side of the bin (scatter)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bin = blockIdx.x;
     const int l = bin_chan[bin];
@@ -528,6 +599,7 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
     if (threadIdx.x == 0) {
         s_bound = 0;
         s_bad = 0;
+        s_tmax = 0;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -536,11 +608,14 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
     }
     __syncthreads();
     const int nv = s_pcum[np];
+    int tmax = 0;                        // largest box side among this thread's rows
     for (int i = threadIdx.x; i < nv; i += blockDim.x) {
         int q = 0;
         while (i >= s_pcum[q + 1]) ++q;
         const long long v = s_pstart[q] + (i - s_pcum[q]);
-        s_meta[i] = meta[v];
+        const int2 mv = meta[v];
+        s_meta[i] = mv;
+        tmax = max(tmax, mv.y);
         s_off[i] = int(fptr[v] - fb);
         s_pc[i] = (unsigned char)q;
         if (MODE == kDual || MODE == kGather) s_v[i] = v;
@@ -555,6 +630,10 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
             s_d[i] = make_float2(vsc * dd.x, vsc * dd.y);
         }
         if ((MODE == kScatter || MODE == kNormal) && dense && allow_fixed) s_n2[i] = gmax[v];
+    }
+    if (MODE == kScatter || MODE == kNormal) {
+        tmax = __reduce_max_sync(0xffffffffu, tmax);
+        if (lane == 0 && tmax > 0) atomicMax(&s_tmax, tmax);
     }
     if (dense) {
         for (int i = threadIdx.x; i < kWin * kWin; i += blockDim.x) {
@@ -632,6 +711,17 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
             else
                 scatter_rows_rank<false, false>(warp, nv, lane, R, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb,
                                                 K1, K2, fs);
+        } else if (s_tmax <= 8) {
+            // every row of the bin has at most 8 taps: two rows per warp step
+            if (dense && fixed)
+                scatter_pairs<true, true>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1, K2,
+                                          fs);
+            else if (dense)
+                scatter_pairs<true, false>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1, K2,
+                                           fs);
+            else
+                scatter_pairs<false, false>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1,
+                                            K2, fs);
         } else if (dense && fixed)
             scatter_rows<true, true>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1, K2, fs);
         else if (dense)
