@@ -260,15 +260,41 @@ void make_bins(const int2 *meta, const long long *fptr, const std::vector<long l
 
 // A bin list on the device (the arrays the pass over G reads) and its bytes.
 struct DevBins {
-    int *pptr = nullptr, *chan = nullptr, *tile = nullptr, *plen = nullptr, *pblk = nullptr;
+    int *chan = nullptr, *tile = nullptr, *plen = nullptr, *pblk = nullptr;
     long long *pstart = nullptr, *fbase = nullptr;
-    int n_bin = 0, n_piece = 0, dense_min = 0, split = 0;
+    int n_bin = 0, slots = 1, dense_min = 0, split = 0;
     size_t bytes = 0;
 };
 
+// A bin list in the device layout: every bin has `slots` piece slots (the
+// most pieces any bin holds), unused ones of length 0, so that a CTA loads its
+// bin's pieces in the same round trip as the bin's channel and tile.
+struct SlotBins {
+    int slots = 1;
+    std::vector<long long> pstart;
+    std::vector<int> plen, pblk;
+};
+
+SlotBins to_slots(const BinList &b) {
+    SlotBins o;
+    for (int k = 0; k < b.n_bin(); ++k) o.slots = std::max(o.slots, b.pptr[k + 1] - b.pptr[k]);
+    const size_t n = size_t(b.n_bin()) * o.slots;
+    o.pstart.assign(n, 0);
+    o.plen.assign(n, 0);
+    o.pblk.assign(n, 0);
+    for (int k = 0; k < b.n_bin(); ++k)
+        for (int q = b.pptr[k]; q < b.pptr[k + 1]; ++q) {
+            const size_t d = size_t(k) * o.slots + (q - b.pptr[k]);
+            o.pstart[d] = b.pstart[q];
+            o.plen[d] = b.plen[q];
+            o.pblk[d] = b.pblk[q];
+        }
+    return o;
+}
+
 DevBins current_bins(const fhs_problem *p) {
     DevBins d;
-    d.pptr = p->bin_pptr;
+    d.slots = p->bin_slots;
     d.fbase = p->bin_fbase;
     d.chan = p->bin_chan;
     d.tile = p->bin_tile;
@@ -276,16 +302,16 @@ DevBins current_bins(const fhs_problem *p) {
     d.plen = p->piece_len;
     d.pblk = p->piece_blk;
     d.n_bin = p->n_bin;
-    d.n_piece = p->n_piece;
+
     d.dense_min = p->bin_dense_min;
     d.split = p->bin_split;
-    d.bytes = sizeof(int) * (3 * size_t(p->n_bin) + 1 + 2 * size_t(p->n_piece)) +
-              sizeof(long long) * (size_t(p->n_piece) + p->n_bin);
+    const size_t np = size_t(p->n_bin) * p->bin_slots;
+    d.bytes = sizeof(int) * (2 * size_t(p->n_bin) + 2 * np) + sizeof(long long) * (np + p->n_bin);
     return d;
 }
 
 void use_bins(fhs_problem *p, const DevBins &d) {
-    p->bin_pptr = d.pptr;
+    p->bin_slots = d.slots;
     p->bin_fbase = d.fbase;
     p->bin_chan = d.chan;
     p->bin_tile = d.tile;
@@ -293,7 +319,7 @@ void use_bins(fhs_problem *p, const DevBins &d) {
     p->piece_len = d.plen;
     p->piece_blk = d.pblk;
     p->n_bin = d.n_bin;
-    p->n_piece = d.n_piece;
+
     p->bin_dense_min = d.dense_min;
     p->bin_split = d.split;
 }
@@ -1031,7 +1057,9 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
     p->bin_dense_min = int(kBinDenseMin);
     p->bin_split = int(kBinSplitMax);
     p->n_bin = bins.n_bin();
-    p->n_piece = int(bins.pstart.size());
+    const SlotBins sb = to_slots(bins);
+    p->bin_slots = sb.slots;
+    const size_t n_slot = sb.pstart.size();
 
     std::vector<double> eps(p->n_seg), inv_sig(p->n_seg);
     for (int l = 0; l < L; ++l) {
@@ -1061,13 +1089,12 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
     if ((st = guard(dev_alloc(p, &p->blk_norm2, p->n_seg))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->eps, p->n_seg, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->blk_scale, p->n_seg, false))) != FHS_OK) return st;
-    if ((st = guard(dev_alloc(p, &p->bin_pptr, p->n_bin + 1, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->bin_fbase, p->n_bin, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->bin_chan, p->n_bin, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->bin_tile, p->n_bin, false))) != FHS_OK) return st;
-    if ((st = guard(dev_alloc(p, &p->piece_start, p->n_piece, false))) != FHS_OK) return st;
-    if ((st = guard(dev_alloc(p, &p->piece_len, p->n_piece, false))) != FHS_OK) return st;
-    if ((st = guard(dev_alloc(p, &p->piece_blk, p->n_piece, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->piece_start, n_slot, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->piece_len, n_slot, false))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->piece_blk, n_slot, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->chunk_start, p->n_chunk + 1, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->chunk_seg, p->n_chunk, false))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &d_kap, Mtot, false))) != FHS_OK) return st;
@@ -1087,13 +1114,12 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
     if ((st = guard(upload(p->d_seg_off, p->seg_off.data(), p->n_seg + 1, s))) != FHS_OK) return st;
     if ((st = guard(upload(p->eps, eps.data(), p->n_seg, s))) != FHS_OK) return st;
     if ((st = guard(upload(p->blk_scale, ones.data(), p->n_seg, s))) != FHS_OK) return st;
-    if ((st = guard(upload(p->bin_pptr, bins.pptr.data(), bins.pptr.size(), s))) != FHS_OK) return st;
     if ((st = guard(upload(p->bin_fbase, bins.fbase.data(), bins.fbase.size(), s))) != FHS_OK) return st;
     if ((st = guard(upload(p->bin_chan, bins.chan.data(), bins.chan.size(), s))) != FHS_OK) return st;
     if ((st = guard(upload(p->bin_tile, bins.tile.data(), bins.tile.size(), s))) != FHS_OK) return st;
-    if ((st = guard(upload(p->piece_start, bins.pstart.data(), bins.pstart.size(), s))) != FHS_OK) return st;
-    if ((st = guard(upload(p->piece_len, bins.plen.data(), bins.plen.size(), s))) != FHS_OK) return st;
-    if ((st = guard(upload(p->piece_blk, bins.pblk.data(), bins.pblk.size(), s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->piece_start, sb.pstart.data(), n_slot, s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->piece_len, sb.plen.data(), n_slot, s))) != FHS_OK) return st;
+    if ((st = guard(upload(p->piece_blk, sb.pblk.data(), n_slot, s))) != FHS_OK) return st;
     if ((st = guard(upload(p->chunk_start, cstart.data(), cstart.size(), s))) != FHS_OK) return st;
     if ((st = guard(upload(p->chunk_seg, cseg.data(), cseg.size(), s))) != FHS_OK) return st;
     if ((st = guard(upload(d_kap, kap.data(), Mtot, s))) != FHS_OK) return st;
@@ -1376,8 +1402,9 @@ fhs_status fhs_estimate_bytes(const fhs_params *params, const double *w, int64_t
     // bins (first piece, channel, tile) and their pieces (start, length, block): a piece is a run of one
     // block inside one tile, or a sparse run, so there are at most bins + (segments x tiles) of them
     const long long ntiles = (long long)((2 * q.ny + kTile - 1) / kTile) * ((2 * q.nx + kTile - 1) / kTile);
-    const long long npiece = nbin + std::min(M, nseg * ntiles);
-    r += 4 * (nbin + 1) + 16 * nbin + 16 * npiece + 8 * (nchunk + 1) + 4 * nchunk;
+    (void)ntiles;
+    const long long npiece = nbin * std::min<long long>(B <= kBinMaxPieces ? B : 1, kBinMaxPieces);
+    r += 16 * nbin + 16 * npiece + 8 * (nchunk + 1) + 4 * nchunk;
     r += 4 * (q.ny + q.nx);                                          // Z scaling
     r += 8 * K * L * 4;                                              // grids
     r += 4 * N * L * 3 + 16 + 16 * L + 4 * L;                        // images, reductions, PSF factors
@@ -1831,7 +1858,6 @@ fhs_status fhs_autotune_bins(fhs_problem *p, void *stream, int32_t *dense_min_ou
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     fhs_status rs = FHS_OK;
     auto release = [&](const DevBins &b) {
-        dev_free(p, b.pptr);
         dev_free(p, b.fbase);
         dev_free(p, b.chan);
         dev_free(p, b.tile);
@@ -1865,25 +1891,24 @@ fhs_status fhs_autotune_bins(fhs_problem *p, void *stream, int32_t *dense_min_ou
                 make_bins(meta.data(), fptr.data(), p->seg_off, p->L, p->B, p->ntx, dm, sp, true, kBinSplitMax, bl);
                 DevBins c;
                 c.n_bin = bl.n_bin();
-                c.n_piece = int(bl.pstart.size());
+                const SlotBins sl = to_slots(bl);
+                c.slots = sl.slots;
                 c.dense_min = int(dm);
                 c.split = int(sp);
-                TRY(dev_alloc(p, &c.pptr, bl.pptr.size(), false));
                 TRY(dev_alloc(p, &c.fbase, bl.fbase.size(), false));
                 TRY(dev_alloc(p, &c.chan, bl.chan.size(), false));
                 TRY(dev_alloc(p, &c.tile, bl.tile.size(), false));
-                TRY(dev_alloc(p, &c.pstart, bl.pstart.size(), false));
-                TRY(dev_alloc(p, &c.plen, bl.plen.size(), false));
-                TRY(dev_alloc(p, &c.pblk, bl.pblk.size(), false));
-                c.bytes = sizeof(int) * (bl.pptr.size() + bl.chan.size() + bl.tile.size() + bl.plen.size() +
-                                         bl.pblk.size()) + sizeof(long long) * (bl.pstart.size() + bl.fbase.size());
-                TRY(upload(c.pptr, bl.pptr.data(), bl.pptr.size(), s));
+                TRY(dev_alloc(p, &c.pstart, sl.pstart.size(), false));
+                TRY(dev_alloc(p, &c.plen, sl.plen.size(), false));
+                TRY(dev_alloc(p, &c.pblk, sl.pblk.size(), false));
+                c.bytes = sizeof(int) * (bl.chan.size() + bl.tile.size() + sl.plen.size() + sl.pblk.size()) +
+                          sizeof(long long) * (sl.pstart.size() + bl.fbase.size());
                 TRY(upload(c.fbase, bl.fbase.data(), bl.fbase.size(), s));
                 TRY(upload(c.chan, bl.chan.data(), bl.chan.size(), s));
                 TRY(upload(c.tile, bl.tile.data(), bl.tile.size(), s));
-                TRY(upload(c.pstart, bl.pstart.data(), bl.pstart.size(), s));
-                TRY(upload(c.plen, bl.plen.data(), bl.plen.size(), s));
-                TRY(upload(c.pblk, bl.pblk.data(), bl.pblk.size(), s));
+                TRY(upload(c.pstart, sl.pstart.data(), sl.pstart.size(), s));
+                TRY(upload(c.plen, sl.plen.data(), sl.plen.size(), s));
+                TRY(upload(c.pblk, sl.pblk.data(), sl.pblk.size(), s));
                 float ms = 0.f;
                 TRY(time_bins(c, ms));
                 DevBins loser = c;
@@ -1892,17 +1917,17 @@ fhs_status fhs_autotune_bins(fhs_problem *p, void *stream, int32_t *dense_min_ou
                     best = c;
                     best_ms = ms;
                 }
-                if (loser.pptr != cur.pptr) release(loser);
+                if (loser.chan != cur.chan) release(loser);
             }
         return FHS_OK;
     };
     rs = run();
-    if (rs != FHS_OK && best.pptr != cur.pptr) {        // a failed search keeps the original bins
+    if (rs != FHS_OK && best.chan != cur.chan) {        // a failed search keeps the original bins
         release(best);
         best = cur;
     }
     use_bins(p, best);
-    if (best.pptr != cur.pptr) release(cur);
+    if (best.chan != cur.chan) release(cur);
     p->home = home;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);

@@ -101,14 +101,13 @@ struct fhs_problem {
     int bin_dense_min = 0, bin_split = 0;     // binning in use (defaults or fhs_autotune_bins)
     // a bin is a list of pieces: runs of sorted rows of one data block each (the rows of all
     // blocks of a channel whose boxes start in one grid tile, or a run of sparse rows of one block)
-    int n_piece = 0;
-    int *bin_pptr = nullptr;                  // [n_bin+1] first piece of each bin
+    int bin_slots = 1;                        // piece slots per bin (unused ones have length 0)
     long long *bin_fbase = nullptr;           // [n_bin] factor offset (fptr) of each bin's first row
     int *bin_chan = nullptr;                  // [n_bin] channel
     int *bin_tile = nullptr;                  // [n_bin] tile key, -1 = sparse (global path)
-    long long *piece_start = nullptr;         // [n_piece] first row (sorted order)
-    int *piece_len = nullptr;                 // [n_piece] rows
-    int *piece_blk = nullptr;                 // [n_piece] block b of the channel
+    long long *piece_start = nullptr;         // [n_bin][bin_slots] first row (sorted order)
+    int *piece_len = nullptr;                 // [n_bin][bin_slots] rows
+    int *piece_blk = nullptr;                 // [n_bin][bin_slots] block b of the channel
     int n_chunk = 0;
     long long *chunk_start = nullptr;         // [n_chunk+1]
     int *chunk_seg = nullptr;                 // [n_chunk]

@@ -538,7 +538,7 @@ constexpr int kGatherMinBlocks = FHS_GATHER_MIN_BLOCKS;
 template <int MODE, bool MULTI>
 __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGatherMinBlocks)) degrid_grid_binned_kernel(
     const int2 *__restrict__ meta, const long long *__restrict__ fptr, const float2 *__restrict__ gfac,
-    const float2 *__restrict__ y, float2 *__restrict__ dvis, const int *__restrict__ bin_pptr,
+    const float2 *__restrict__ y, float2 *__restrict__ dvis, int slots,
     const long long *__restrict__ bin_fbase, const long long *__restrict__ piece_start, const int *__restrict__ piece_len, const int *__restrict__ piece_blk,
     const int *__restrict__ bin_chan, const int *__restrict__ bin_tile, int ntx, int B,
     const float *__restrict__ blk_scale, double *__restrict__ blk_norm2, const float2 *__restrict__ grid,
@@ -585,9 +585,9 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
         window_tma(s_grid, &tmap, wx0, wy0, l, &s_bar);
     }
     // the bin's pieces: runs of rows of one block each, in the order of their blocks
-    const int pp0 = bin_pptr[bin];
+    const long long pp0 = (long long)bin * slots;
     const long long fb = bin_fbase[bin];       // factor offset of the bin's first row (the smallest)
-    const int np = bin_pptr[bin + 1] - pp0;
+    const int np = slots;                     // pieces of length 0 in unused slots
     if (threadIdx.x < np) {
         const int b = piece_blk[pp0 + threadIdx.x];
         s_pstart[threadIdx.x] = piece_start[pp0 + threadIdx.x];
@@ -835,7 +835,7 @@ cudaError_t launch_pass(fhs_problem *p, const float2 *y, float2 *dvis, const flo
                         cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
     (p->rank > 1 ? degrid_grid_binned_kernel<MODE, true> : degrid_grid_binned_kernel<MODE, false>)<<<p->n_bin, 256, 0, s>>>(
-        p->meta, p->fptr, p->gfac, y, dvis, p->bin_pptr, p->bin_fbase, p->piece_start, p->piece_len, p->piece_blk,
+        p->meta, p->fptr, p->gfac, y, dvis, p->bin_slots, p->bin_fbase, p->piece_start, p->piece_len, p->piece_blk,
         p->bin_chan,
         p->bin_tile, p->ntx, p->B, blk_scale, blk_norm2, grid, grid_out, p->K, p->K1, p->K2, sigma2, p->rank, tm.map,
         tm.ok, p->gmax, allow_fixed, p->dev_err);

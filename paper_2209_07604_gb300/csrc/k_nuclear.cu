@@ -75,8 +75,8 @@ __global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ P, 
 
 // L_c in (16, 32]: the per-thread triangle no longer fits in registers.  The
 // CTA stages kSub pixels x L_c channels of Z in shared memory (loads coalesced
-// along pixels); lane i of each warp then accumulates row i of the Gram over
-// the warp's pixels, reading Z[j][p] as a shared-memory broadcast.
+// along pixels); every lane of a warp then accumulates a 4 x 8 block of the
+// 32 x 32 Gram over the warp's pixels.
 constexpr int kSub = 128;
 
 template <typename AccT>
@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(256) gram32_kernel(const float *__restrict__ P
                                                      double *__restrict__ gram) {
     __shared__ float s_z[32][kSub + 1];
     __shared__ double s_red[32 * 32];
+    __shared__ long long s_o[kSub];           // image offset of each pixel of the sub-chunk
     const int cq = blockIdx.y;
     const int c = cq / Q, q = cq - c * Q;
     const int4 f = facets[q];
@@ -98,33 +99,50 @@ __global__ void __launch_bounds__(256) gram32_kernel(const float *__restrict__ P
     const float *Pq = P + nuc_off[cq];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) s_red[e] = 0.0;
-    AccT acc[32];
+    // lane (bi, bj) = (lane / 4, lane % 4) accumulates rows 4 bi .. 4 bi + 3 and columns
+    // 8 bj .. 8 bj + 7 of the Gram: 12 shared loads (conflict-free: the row stride kSub + 1
+    // puts channel j of pixel t in bank (j + t) % 32) for 32 products per pixel
+    const int bi = lane >> 2, bj = lane & 3;
+    AccT acc[4][8];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) acc[j] = AccT(0);
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[r][q] = AccT(0);
     for (long long sb = p0; sb < p1; sb += kSub) {
         const int nsub = int(min((long long)kSub, p1 - sb));
         __syncthreads();                         // the previous sub-chunk is consumed
+        if (threadIdx.x < kSub) {
+            const long long pp = sb + threadIdx.x;
+            const int py = int(pp / wx), px = int(pp - (long long)py * wx);
+            s_o[threadIdx.x] = (long long)(f.x + py) * nx + (f.z + px);
+        }
+        __syncthreads();
         for (int e = threadIdx.x; e < 32 * kSub; e += blockDim.x) {
             const int j = e / kSub, t = e - j * kSub;
             float v = 0.f;
             if (j < Lc && t < nsub) {
-                const long long pp = sb + t;
-                const int py = int(pp / wx), px = int(pp - (long long)py * wx);
-                const long long o = (long long)(f.x + py) * nx + (f.z + px);
-                const float xv = img[(long long)(c + j * C) * N + o];
-                v = with_dual ? fmaf(s, xv, Pq[(long long)j * npix + pp]) : xv;
+                const float xv = img[(long long)(c + j * C) * N + s_o[t]];
+                v = with_dual ? fmaf(s, xv, Pq[(long long)j * npix + sb + t]) : xv;
             }
             s_z[j][t] = v;
         }
         __syncthreads();
         for (int t = warp; t < nsub; t += blockDim.x >> 5) {
-            const AccT zi = AccT(s_z[lane][t]);
+            AccT zr[4], zc[8];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) acc[j] = fma(zi, AccT(s_z[j][t]), acc[j]);
+            for (int r = 0; r < 4; ++r) zr[r] = AccT(s_z[4 * bi + r][t]);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) zc[q] = AccT(s_z[8 * bj + q][t]);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[r][q] = fma(zr[r], zc[q], acc[r][q]);
         }
     }
 #pragma unroll
-    for (int j = 0; j < 32; ++j) atomicAdd(&s_red[lane * 32 + j], double(acc[j]));
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) atomicAdd(&s_red[(4 * bi + r) * 32 + 8 * bj + q], double(acc[r][q]));
     __syncthreads();
     double *G = gram + (long long)cq * Lc * Lc;
     for (int e = threadIdx.x; e < Lc * Lc; e += blockDim.x) {
@@ -332,6 +350,56 @@ __global__ void __launch_bounds__(256) apply_kernel(float *__restrict__ P, const
     }
 }
 
+// P_q <- (P_q + sigma0 S_q xbar) M_q for more than 8 channels: a thread
+// accumulates its pixel's (at most 32) outputs, taking z_i one channel at a
+// time and adding z_i times row i of M (padded to 32 columns: eight 16-byte
+// shared loads per 32 products).  The per-output form above takes 128-254
+// registers at 16-32 channels.
+__global__ void __launch_bounds__(256, 3) apply_wide_kernel(float *__restrict__ P, const float *__restrict__ img,
+                                                            const int4 *__restrict__ facets,
+                                                            const long long *__restrict__ nuc_off,
+                                                            const float *__restrict__ mix, int Q, int C, int Lc,
+                                                            int nx, long long N, float s) {
+    __shared__ __align__(16) float sM[32 * 32];
+    const int cq = blockIdx.y;
+    const int c = cq / Q, q = cq - c * Q;
+    const int4 f = facets[q];
+    const int wy = f.y - f.x, wx = f.w - f.z;
+    const long long npix = (long long)wy * wx;
+    const long long p0 = (long long)blockIdx.x * kPix;
+    if (p0 >= npix) return;
+    const long long p1 = min(npix, p0 + kPix);
+    for (int k = threadIdx.x; k < 32 * 32; k += blockDim.x) {
+        const int i = k >> 5, j = k & 31;
+        sM[k] = (i < Lc && j < Lc) ? mix[(long long)cq * Lc * Lc + i * Lc + j] : 0.f;
+    }
+    __syncthreads();
+    float *Pq = P + nuc_off[cq];
+    for (long long pp = p0 + threadIdx.x; pp < p1; pp += blockDim.x) {
+        const int py = int(pp / wx), px = int(pp - (long long)py * wx);
+        const long long o = (long long)(f.x + py) * nx + (f.z + px);
+        float acc[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+#pragma unroll 2
+        for (int i = 0; i < Lc; ++i) {
+            const float zi = fmaf(s, img[(long long)(c + i * C) * N + o], Pq[(long long)i * npix + pp]);
+            const float4 *mr = reinterpret_cast<const float4 *>(&sM[i * 32]);
+#pragma unroll
+            for (int jq = 0; jq < 8; ++jq) {
+                const float4 m = mr[jq];
+                acc[4 * jq] = fmaf(zi, m.x, acc[4 * jq]);
+                acc[4 * jq + 1] = fmaf(zi, m.y, acc[4 * jq + 1]);
+                acc[4 * jq + 2] = fmaf(zi, m.z, acc[4 * jq + 2]);
+                acc[4 * jq + 3] = fmaf(zi, m.w, acc[4 * jq + 3]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (j < Lc) Pq[(long long)j * npix + pp] = acc[j];
+    }
+}
+
 }  // namespace
 
 template <typename AccT>
@@ -395,10 +463,9 @@ cudaError_t launch_nuclear_apply(fhs_problem *p, cudaStream_t s) {
         apply_kernel<4><<<g, 256, 0, s>>>(p->P, p->Xbar, p->d_facets, p->nuc_off, p->mix, p->Q, p->C, p->Lc, p->nx, p->N, s0);
     else if (p->Lc <= 8)
         apply_kernel<8><<<g, 256, 0, s>>>(p->P, p->Xbar, p->d_facets, p->nuc_off, p->mix, p->Q, p->C, p->Lc, p->nx, p->N, s0);
-    else if (p->Lc <= 16)
-        apply_kernel<16><<<g, 256, 0, s>>>(p->P, p->Xbar, p->d_facets, p->nuc_off, p->mix, p->Q, p->C, p->Lc, p->nx, p->N, s0);
     else if (p->Lc <= 32)
-        apply_kernel<32><<<g, 256, 0, s>>>(p->P, p->Xbar, p->d_facets, p->nuc_off, p->mix, p->Q, p->C, p->Lc, p->nx, p->N, s0);
+        apply_wide_kernel<<<g, 256, 0, s>>>(p->P, p->Xbar, p->d_facets, p->nuc_off, p->mix, p->Q, p->C, p->Lc, p->nx,
+                                             p->N, s0);
     else
         return cudaErrorInvalidValue;
     p->n_launch += 1;

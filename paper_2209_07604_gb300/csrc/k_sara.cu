@@ -448,6 +448,35 @@ __global__ void __launch_bounds__(256) l21_dual_kernel(float *__restrict__ W, co
     }
 }
 
+// The same step for sub-cubes of more than 8 channels, without holding the
+// row in registers: a first sweep over the channels forms ||z||^2, a second
+// forms z again (its loads hit the caches) and writes z min(1, mu w / ||z||).
+// Holding the row took 128 registers a thread at 16 channels and 254 at 32
+// (16 and 8 warps per SM).
+__global__ void __launch_bounds__(256) l21_dual_wide_kernel(float *__restrict__ W, const float *__restrict__ A,
+                                                            const float *__restrict__ w21, long long n_coef, int C,
+                                                            int Lc, float sigma1, float mu) {
+    const int c = blockIdx.y;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n_coef;
+         r += (long long)gridDim.x * blockDim.x) {
+        float n2 = 0.f;
+#pragma unroll 8
+        for (int jj = 0; jj < Lc; ++jj) {
+            const long long o = (long long)(c + jj * C) * n_coef + r;
+            const float z = fmaf(sigma1, A[o], W[o]);
+            n2 = fmaf(z, z, n2);
+        }
+        const float thr = mu * w21[(long long)c * n_coef + r];
+        const float nr = sqrtf(n2);
+        const float f = (nr > thr) ? thr / nr : 1.f;
+#pragma unroll 8
+        for (int jj = 0; jj < Lc; ++jj) {
+            const long long o = (long long)(c + jj * C) * n_coef + r;
+            W[o] = fmaf(sigma1, A[o], W[o]) * f;
+        }
+    }
+}
+
 // Log-sum weights w_r = upsilon / (upsilon + ||(Psi^dagger X)_r||) per sub-cube.
 __global__ void __launch_bounds__(256) l21_reweight_kernel(const float *__restrict__ A, float *__restrict__ w21,
                                                            long long n_coef, int C, int Lc, double upsilon) {
@@ -566,8 +595,7 @@ cudaError_t launch_l21_dual(fhs_problem *p, cudaStream_t s) {
     if (p->Lc <= 2) l21_dual_kernel<2><<<g, 256, 0, s>>>(p->W, p->coef_tmp, p->w21, n, p->C, p->Lc, s1, mu);
     else if (p->Lc <= 4) l21_dual_kernel<4><<<g, 256, 0, s>>>(p->W, p->coef_tmp, p->w21, n, p->C, p->Lc, s1, mu);
     else if (p->Lc <= 8) l21_dual_kernel<8><<<g, 256, 0, s>>>(p->W, p->coef_tmp, p->w21, n, p->C, p->Lc, s1, mu);
-    else if (p->Lc <= 16) l21_dual_kernel<16><<<g, 256, 0, s>>>(p->W, p->coef_tmp, p->w21, n, p->C, p->Lc, s1, mu);
-    else l21_dual_kernel<32><<<g, 256, 0, s>>>(p->W, p->coef_tmp, p->w21, n, p->C, p->Lc, s1, mu);
+    else l21_dual_wide_kernel<<<g, 256, 0, s>>>(p->W, p->coef_tmp, p->w21, n, p->C, p->Lc, s1, mu);
     p->n_launch += 1;
     return cudaGetLastError();
 }
