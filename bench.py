@@ -572,14 +572,27 @@ def run_reference(args):
     }))
 
 
-SERVE_MIX = [  # (ny, nx, L, C, M per channel, B, facets, w_max)
-    (256, 256, 4, 1, 100_000, 2, 2, 2000.0),
-    (512, 512, 8, 2, 200_000, 2, 2, 2000.0),
-    (256, 256, 8, 1, 400_000, 4, 2, 0.0),
-    (1024, 1024, 4, 1, 300_000, 4, 4, 2000.0),
-    (512, 512, 4, 2, 1_000_000, 4, 2, 2000.0),
-    (1536, 1024, 4, 1, 200_000, 2, 4, 0.0),
-]
+SERVE_MIXES = {  # (ny, nx, L, C, M per channel, B, facets, w_max)
+    # the serving configuration: images 256^2 to 4096^2, 4 to 64 channels (at most 32 per
+    # sub-cube), 1e5 to 2e7 visibilities per channel; the largest request holds about 40 GB
+    "config5": [
+        (256, 256, 4, 1, 100_000, 2, 2, 2000.0),
+        (512, 512, 16, 2, 500_000, 4, 2, 2000.0),
+        (1024, 1024, 64, 2, 100_000, 4, 4, 2000.0),
+        (1024, 1024, 8, 2, 2_000_000, 4, 4, 2000.0),
+        (2048, 2048, 16, 2, 2_000_000, 8, 8, 0.0),
+        (4096, 4096, 6, 1, 20_000_000, 8, 8, 0.0),
+    ],
+    # a small mix (images up to 1536 x 1024, up to 8 channels, up to 1e6 visibilities per channel)
+    "small": [
+        (256, 256, 4, 1, 100_000, 2, 2, 2000.0),
+        (512, 512, 8, 2, 200_000, 2, 2, 2000.0),
+        (256, 256, 8, 1, 400_000, 4, 2, 0.0),
+        (1024, 1024, 4, 1, 300_000, 4, 4, 2000.0),
+        (512, 512, 4, 2, 1_000_000, 4, 2, 2000.0),
+        (1536, 1024, 4, 1, 200_000, 2, 4, 0.0),
+    ],
+}
 
 
 def _serve_pass(reqs, arrivals, max_active, budget, check_every):
@@ -611,10 +624,15 @@ def run_serve(args):
     from paper_2209_07604_gb300 import synth
     torch.cuda.set_device(0)
     fhs.load_library()
-    pool = []
-    for k, (ny, nx, L, C, M, B, Q, wmax) in enumerate(SERVE_MIX):
-        pool.append(synth.make_problem("vla_1024", trial=k, ny=ny, nx=nx, L=L, C=C, M=M, B=B, qy=Q, qx=Q,
-                                       w_max=wmax))
+    mix = SERVE_MIXES[args.serve_mix]
+    pool, sizes = [], []
+    for k, (ny, nx, L, C, M, B, Q, wmax) in enumerate(mix):
+        P = synth.make_problem("vla_1024", trial=k, ny=ny, nx=nx, L=L, C=C, M=M, B=B, qy=Q, qx=Q, w_max=wmax)
+        params = fhs.default_params(ny=ny, nx=nx, n_channels=L, n_subcubes=C, n_blocks=B, qy=Q, qx=Q,
+                                    facet_overlap=P.overlap, w_max=P.w_max, pixel_size=P.pixel_size, mu=MU,
+                                    mu_bar=MU_BAR)
+        sizes.append(fhs.fhs_estimate_bytes(params, P.w.reshape(-1), L * M))
+        pool.append(P)
     rng = np.random.default_rng(7604)
     n = args.serve_requests
     reqs = [(pool[rng.integers(len(pool))], dict(mu=MU, mu_bar=MU_BAR, max_iter=args.serve_iters,
@@ -627,7 +645,9 @@ def run_serve(args):
     print(json.dumps({
         "mode": "serve", "metric": "imaging requests: p50/p99 time to image, images/hour, visibilities/s",
         "unit": "s", "requests": n, "arrival_rate_per_s": args.serve_rate,
-        "mix": [dict(zip(["ny", "nx", "L", "C", "M_per_channel", "B", "facets", "w_max"], m)) for m in SERVE_MIX],
+        "mix": [dict(zip(["ny", "nx", "L", "C", "M_per_channel", "B", "facets", "w_max"], m),
+                     resident_gb=sz[0] / 1e9, peak_gb=sz[1] / 1e9) for m, sz in zip(mix, sizes)],
+        "mix_name": args.serve_mix,
         "iterations_per_request": args.serve_iters, "hbm_budget_gb": args.serve_budget_gb,
         "continuous_batching": batched, "one_at_a_time": serial,
         "speedup_p99": serial["p99_s"] / batched["p99_s"], "speedup_throughput": batched["images_per_hour"] /
@@ -792,6 +812,7 @@ def main():
     ap.add_argument("--adaptive-settle", type=float, default=3e-3,
                     help="--mode adaptive: relative change below which a check acts")
     ap.add_argument("--batch-problems", type=int, default=24)
+    ap.add_argument("--serve-mix", default="config5", choices=sorted(SERVE_MIXES))
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=4.0)
     ap.add_argument("--serve-iters", type=int, default=200)

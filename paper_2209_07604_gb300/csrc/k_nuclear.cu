@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ P, 
 #pragma unroll
     for (int k = 0; k < NP; ++k) acc[k] = AccT(0);
     for (long long pp = p0 + threadIdx.x; pp < p1; pp += blockDim.x) {
-        const int py = int(pp / wx), px = int(pp - (long long)py * wx);
+        const int py = int(pp) / wx, px = int(pp) - py * wx;     // 32-bit division: facets hold < 2^31 pixels
         const long long o = (long long)(f.x + py) * nx + (f.z + px);
         AccT z[MAXLC];
 #pragma unroll
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(256) gram32_kernel(const float *__restrict__ P
         __syncthreads();                         // the previous sub-chunk is consumed
         if (threadIdx.x < kSub) {
             const long long pp = sb + threadIdx.x;
-            const int py = int(pp / wx), px = int(pp - (long long)py * wx);
+            const int py = int(pp) / wx, px = int(pp) - py * wx;     // 32-bit division: facets hold < 2^31 pixels
             s_o[threadIdx.x] = (long long)(f.x + py) * nx + (f.z + px);
         }
         __syncthreads();
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(256) apply_kernel(float *__restrict__ P, const
     __syncthreads();
     float *Pq = P + nuc_off[cq];
     for (long long pp = p0 + threadIdx.x; pp < p1; pp += blockDim.x) {
-        const int py = int(pp / wx), px = int(pp - (long long)py * wx);
+        const int py = int(pp) / wx, px = int(pp) - py * wx;     // 32-bit division: facets hold < 2^31 pixels
         const long long o = (long long)(f.x + py) * nx + (f.z + px);
         float z[MAXLC];
 #pragma unroll
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(256, 3) apply_wide_kernel(float *__restrict__ 
     __syncthreads();
     float *Pq = P + nuc_off[cq];
     for (long long pp = p0 + threadIdx.x; pp < p1; pp += blockDim.x) {
-        const int py = int(pp / wx), px = int(pp - (long long)py * wx);
+        const int py = int(pp) / wx, px = int(pp) - py * wx;     // 32-bit division: facets hold < 2^31 pixels
         const long long o = (long long)(f.x + py) * nx + (f.z + px);
         float acc[32];
 #pragma unroll

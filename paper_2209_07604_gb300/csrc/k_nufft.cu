@@ -175,7 +175,7 @@ __global__ void zpad_kernel(const float *__restrict__ x, float2 *__restrict__ gr
     const int l = blockIdx.y;
     const long long N = (long long)ny * nx;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-        const int i1 = int(p / nx), i2 = int(p - (long long)i1 * nx);
+        const int i1 = int(p) / nx, i2 = int(p) - i1 * nx;      // 32-bit division: images hold < 2^31 pixels
         int k1 = i1 - ny / 2; k1 += (k1 < 0) ? K1 : 0;
         int k2 = i2 - nx / 2; k2 += (k2 < 0) ? K2 : 0;
         grid[(long long)l * K + (long long)k1 * K2 + k2] = make_float2(x[(long long)l * N + p] * s1[i1] * s2[i2], 0.f);
@@ -188,7 +188,7 @@ __global__ void crop_kernel(const float2 *__restrict__ grid, float *__restrict__
     const int l = blockIdx.y;
     const long long N = (long long)ny * nx;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (long long)gridDim.x * blockDim.x) {
-        const int i1 = int(p / nx), i2 = int(p - (long long)i1 * nx);
+        const int i1 = int(p) / nx, i2 = int(p) - i1 * nx;      // 32-bit division: images hold < 2^31 pixels
         int k1 = i1 - ny / 2; k1 += (k1 < 0) ? K1 : 0;
         int k2 = i2 - nx / 2; k2 += (k2 < 0) ? K2 : 0;
         x[(long long)l * N + p] = grid[(long long)l * K + (long long)k1 * K2 + k2].x * s1[i1] * s2[i2];
