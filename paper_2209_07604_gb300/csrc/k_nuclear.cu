@@ -156,7 +156,8 @@ __global__ void __launch_bounds__(256) gram32_kernel(const float *__restrict__ P
 // rotations at once (columns first, then rows: disjoint Givens rotations
 // commute).  Bounded sweeps.  Then either the SVT mixing matrix
 // M = V diag(min(1, mu_bar w_i / s_i)) V^T or the reweighting weights.
-// NMAX = 16: four warps (four matrices) per CTA; NMAX = 32: one.
+// Four warps (four matrices of at most 16 x 16) per CTA; larger matrices go
+// to eig32_kernel.
 // eigv (n x n per matrix, n = L_c rounded up to even), when not NULL, holds
 // the eigenvectors found at the previous call and receives the new ones: the
 // sweeps start from V0^T G V0, which is nearly diagonal when the facet changes
@@ -312,6 +313,163 @@ __global__ void __launch_bounds__(NMAX == 16 ? 128 : 32) eig_kernel(double *__re
     }
 }
 
+// The same eigen-decomposition for 16 < L_c <= 32 by a CTA of kEig32Threads
+// threads per matrix (one warp took 1.7 ms for 64 matrices of 32 x 32: each
+// round's dependent FP64 updates ran 16 deep per lane).  Same rotations, same
+// order, same outputs as eig_kernel<32>.
+constexpr int kEig32Threads = 128;
+
+__global__ void __launch_bounds__(kEig32Threads) eig32_kernel(double *__restrict__ gram, float *__restrict__ mix,
+                                                              float *__restrict__ wnuc, int n_mat, int Lc,
+                                                              double mu_bar, double upsilon_bar, bool reweight,
+                                                              double *__restrict__ eigv, double *__restrict__ svals) {
+    constexpr int NMAX = 32, NT = kEig32Threads;
+    __shared__ double a[NMAX][NMAX + 1];
+    __shared__ double V[NMAX][NMAX + 1];
+    __shared__ double Tm[NMAX][NMAX + 1];
+    __shared__ double s_cs[NMAX / 2], s_sn[NMAX / 2];
+    __shared__ int s_p[NMAX / 2], s_q[NMAX / 2];
+    __shared__ int s_ord[NMAX];
+    __shared__ double s_red[2][NT / 32];
+    __shared__ double s_f[NMAX];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int cq = blockIdx.x;
+    if (cq >= n_mat) return;
+    double *G = gram + (long long)cq * Lc * Lc;
+    const int n = Lc + (Lc & 1);
+    for (int e = t; e < n * n; e += NT) {
+        const int i = e / n, j = e - (e / n) * n;
+        double v = 0.0;
+        if (i < Lc && j < Lc) v = (j >= i) ? G[i * Lc + j] : G[j * Lc + i];
+        a[i][j] = v;
+        V[i][j] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int e = t; e < Lc * Lc; e += NT) G[e] = 0.0;   // ready for the next accumulation
+    double *Vg = eigv ? eigv + (long long)cq * n * n : nullptr;
+    if (Vg) {
+        for (int e = t; e < n * n; e += NT) V[e / n][e % n] = Vg[e];
+        __syncthreads();
+        for (int e = t; e < n * n; e += NT) {
+            const int i = e / n, j = e - (e / n) * n;
+            double x = 0.0;
+            for (int k = 0; k < n; ++k) x = fma(a[i][k], V[k][j], x);
+            Tm[i][j] = x;
+        }
+        __syncthreads();
+        for (int e = t; e < n * n; e += NT) {
+            const int i = e / n, j = e - (e / n) * n;
+            double x = 0.0;
+            for (int k = 0; k < n; ++k) x = fma(V[k][i], Tm[k][j], x);
+            a[i][j] = x;
+        }
+        __syncthreads();
+    }
+    const int half = n / 2;
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        double off = 0.0, dia = 0.0;
+        for (int e = t; e < n * n; e += NT) {
+            const int i = e / n, j = e - (e / n) * n;
+            const double x = a[i][j];
+            if (i == j) dia += x * x; else off += x * x;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            dia += __shfl_xor_sync(0xffffffffu, dia, o);
+        }
+        if (lane == 0) {
+            s_red[0][w] = off;
+            s_red[1][w] = dia;
+        }
+        __syncthreads();
+        off = dia = 0.0;
+        for (int k = 0; k < NT / 32; ++k) {
+            off += s_red[0][k];
+            dia += s_red[1][k];
+        }
+        __syncthreads();                          // s_red is rewritten by the next sweep
+        if (off <= 1e-28 * dia || off == 0.0) break;
+        for (int round = 0; round < n - 1; ++round) {
+            if (t < half) {
+                const int k = t;
+                int pa = (k == 0) ? 0 : 1 + (k - 1 + round) % (n - 1);
+                int pb = 1 + (n - 2 - k + round) % (n - 1);
+                const int p = min(pa, pb), q = max(pa, pb);
+                const double apq = a[p][q];
+                double cs = 1.0, sn = 0.0;
+                if (apq != 0.0) {
+                    const double theta = (a[q][q] - a[p][p]) / (2.0 * apq);
+                    const double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                    cs = 1.0 / sqrt(tt * tt + 1.0);
+                    sn = tt * cs;
+                }
+                s_p[k] = p;
+                s_q[k] = q;
+                s_cs[k] = cs;
+                s_sn[k] = sn;
+            }
+            __syncthreads();
+            for (int e = t; e < half * n; e += NT) {        // columns: A <- A J, V <- V J
+                const int k = e / n, r = e - k * n;
+                const int p = s_p[k], q = s_q[k];
+                const double cs = s_cs[k], sn = s_sn[k];
+                const double arp = a[r][p], arq = a[r][q];
+                a[r][p] = cs * arp - sn * arq;
+                a[r][q] = sn * arp + cs * arq;
+                const double vrp = V[r][p], vrq = V[r][q];
+                V[r][p] = cs * vrp - sn * vrq;
+                V[r][q] = sn * vrp + cs * vrq;
+            }
+            __syncthreads();
+            for (int e = t; e < half * n; e += NT) {        // rows: A <- J^T A
+                const int k = e / n, c = e - k * n;
+                const int p = s_p[k], q = s_q[k];
+                const double cs = s_cs[k], sn = s_sn[k];
+                const double apc = a[p][c], aqc = a[q][c];
+                a[p][c] = cs * apc - sn * aqc;
+                a[q][c] = sn * apc + cs * aqc;
+            }
+            __syncthreads();
+        }
+    }
+    if (Vg)
+        for (int e = t; e < n * n; e += NT) Vg[e] = V[e / n][e % n];
+    if (t == 0) {                             // eigenvalues descending (padding excluded)
+        for (int i = 0; i < Lc; ++i) s_ord[i] = i;
+        for (int i = 0; i < Lc; ++i)
+            for (int j = i + 1; j < Lc; ++j)
+                if (a[s_ord[j]][s_ord[j]] > a[s_ord[i]][s_ord[i]]) {
+                    const int x = s_ord[i]; s_ord[i] = s_ord[j]; s_ord[j] = x;
+                }
+    }
+    __syncthreads();
+    float *wv = wnuc + (long long)cq * Lc;
+    if (svals) {                              // singular values only, descending
+        if (t < Lc) svals[(long long)cq * Lc + t] = sqrt(fmax(a[s_ord[t]][s_ord[t]], 0.0));
+        return;
+    }
+    if (reweight) {
+        if (t < Lc) {
+            const double sv = sqrt(fmax(a[s_ord[t]][s_ord[t]], 0.0));
+            wv[t] = float(upsilon_bar / (upsilon_bar + sv));
+        }
+        return;
+    }
+    if (t < Lc) {
+        const double sv = sqrt(fmax(a[s_ord[t]][s_ord[t]], 0.0));
+        const double thr = mu_bar * double(wv[t]);
+        s_f[t] = (sv > thr) ? thr / sv : 1.0;
+    }
+    __syncthreads();
+    float *M = mix + (long long)cq * Lc * Lc;
+    for (int e = t; e < Lc * Lc; e += NT) {
+        const int i = e / Lc, j = e - (e / Lc) * Lc;
+        double m = 0.0;
+        for (int k = 0; k < Lc; ++k) m += V[i][s_ord[k]] * s_f[k] * V[j][s_ord[k]];
+        M[e] = float(m);
+    }
+}
+
 // P_q <- (P_q + sigma0 S_q xbar) M_q, one thread per facet pixel.
 template <int MAXLC>
 __global__ void __launch_bounds__(256) apply_kernel(float *__restrict__ P, const float *__restrict__ img,
@@ -435,8 +593,8 @@ cudaError_t launch_nuclear_eig(fhs_problem *p, bool reweight, cudaStream_t s) {
         eig_kernel<16><<<(n + 3) / 4, 128, 0, s>>>(p->gram, p->mix, p->wnuc, n, p->Lc, p->prm.mu_bar,
                                                   p->prm.upsilon_bar, reweight, v0, nullptr);
     else
-        eig_kernel<32><<<n, 32, 0, s>>>(p->gram, p->mix, p->wnuc, n, p->Lc, p->prm.mu_bar, p->prm.upsilon_bar,
-                                         reweight, v0, nullptr);
+        eig32_kernel<<<n, kEig32Threads, 0, s>>>(p->gram, p->mix, p->wnuc, n, p->Lc, p->prm.mu_bar,
+                                                 p->prm.upsilon_bar, reweight, v0, nullptr);
     p->n_launch += 1;
     return cudaGetLastError();
 }
@@ -447,7 +605,7 @@ cudaError_t launch_nuclear_svals(fhs_problem *p, double *svals, cudaStream_t s) 
         eig_kernel<16><<<(n + 3) / 4, 128, 0, s>>>(p->gram, p->mix, p->wnuc, n, p->Lc, 0.0, 1.0, true, nullptr,
                                                   svals);
     else
-        eig_kernel<32><<<n, 32, 0, s>>>(p->gram, p->mix, p->wnuc, n, p->Lc, 0.0, 1.0, true, nullptr, svals);
+        eig32_kernel<<<n, kEig32Threads, 0, s>>>(p->gram, p->mix, p->wnuc, n, p->Lc, 0.0, 1.0, true, nullptr, svals);
     p->n_launch += 1;
     return cudaGetLastError();
 }
