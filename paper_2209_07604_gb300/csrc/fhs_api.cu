@@ -5,11 +5,13 @@
 #include "fhs_internal.h"
 
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <numeric>
@@ -540,7 +542,8 @@ fhs_status default_regularisation(fhs_problem *p, cudaStream_t s) {
     return rs;
 }
 
-fhs_status norm_estimate(fhs_problem *p, int n_iter, double tol, std::vector<double> &lam, cudaStream_t s) {
+fhs_status norm_estimate(fhs_problem *p, int n_iter, double tol, std::vector<double> &lam, cudaStream_t s,
+                         int *steps_taken = nullptr) {
     const long long LN = (long long)p->L * p->N;
     const int L = p->L;
     std::vector<float> x0(LN);
@@ -551,6 +554,7 @@ fhs_status norm_estimate(fhs_problem *p, int n_iter, double tol, std::vector<dou
     }
     double *norms = p->pnorms;
     float *vprev = p->Xbar, *v = p->A_sara, *y = p->coef_tmp;
+    const bool trace = std::getenv("FHS_TRACE_SETUP") != nullptr;
     double *coef = nullptr;                     // alpha[n_iter][L] then nb2[n_iter + 1][L]
     const size_t n_coef = (size_t)(2 * n_iter + 1) * L;
     CU(cudaMallocAsync(reinterpret_cast<void **>(&coef), sizeof(double) * n_coef, s));
@@ -569,6 +573,7 @@ fhs_status norm_estimate(fhs_problem *p, int n_iter, double tol, std::vector<dou
             TRY(apply_normal(p, v, y, s));
             CU(launch_lanczos_step(p, y, vprev, v, alpha + (size_t)j * L, nb2 + (size_t)j * L, s));
             std::swap(vprev, v);
+            if (steps_taken) *steps_taken = j + 1;
             const bool last = j + 1 == n_iter;
             if (!last && !(tol > 0.0 && (j + 1) % 5 == 0)) continue;
             const int m = j + 1;
@@ -589,6 +594,7 @@ fhs_status norm_estimate(fhs_problem *p, int n_iter, double tol, std::vector<dou
                 worst = std::max(worst, std::fabs(lam[l] - prev[l]) / std::max(std::fabs(lam[l]), 1e-300));
                 prev[l] = lam[l];
             }
+            if (trace) std::fprintf(stderr, "fhs set-up: Lanczos step %3d: largest relative change %.3e\n", m, worst);
             if (tol > 0.0 && worst < tol) break;
         }
         return FHS_OK;
@@ -847,6 +853,22 @@ fhs_status fhs_daubechies_filter(int32_t p, double *h_out) {
     return FHS_OK;
 }
 
+// Wall time of the stages of the problem set-up, printed to stderr when the
+// environment variable FHS_TRACE_SETUP is set (each mark waits for the stream,
+// so that device work is charged to its own stage).
+struct SetupTrace {
+    bool on = std::getenv("FHS_TRACE_SETUP") != nullptr;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now(), t = t0;
+    void mark(const char *stage, cudaStream_t s) {
+        if (!on) return;
+        cudaStreamSynchronize(s);
+        const auto n = std::chrono::steady_clock::now();
+        std::fprintf(stderr, "fhs set-up: %-34s %8.3f s (total %8.3f s)\n", stage,
+                     std::chrono::duration<double>(n - t).count(), std::chrono::duration<double>(n - t0).count());
+        t = n;
+    }
+};
+
 // Problem set-up shared by fhs_create_problem and fhs_create_problem_dde (dde: NULL, or
 // [M_tot][5][5] complex DDE kernels in the caller's visibility order).
 static fhs_status create_impl(const fhs_params *params, const double *omega, const double *w, const double *y,
@@ -856,6 +878,7 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
     if (!out) return fail(FHS_ERR_ARG, "out is NULL");
     *out = nullptr;
     TRY(check_params(params));
+    SetupTrace trace;
     if (!omega || !y || !sigma || !vis_offsets || !block_offsets) return fail(FHS_ERR_ARG, "NULL input array");
     const fhs_params &q = *params;
     const int L = q.n_channels, B = q.n_blocks, J = q.kb_taps;
@@ -894,6 +917,7 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
         }
     }
     cudaStream_t s = S(stream);
+    trace.mark("input checks", s);
 
     fhs_problem *p = new (std::nothrow) fhs_problem();
     if (!p) return fail(FHS_ERR_OOM, "host allocation failed");
@@ -959,6 +983,7 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
         return fail(FHS_ERR_ARG, "DDE kernels widen the G boxes past 16 taps: with DDEs the w-kernels may "
                                  "add at most %d taps per side (w_max too large for this pixel size)", (16 - J - ext) / 2);
     }
+    trace.mark("host geometry (boxes, planes, keys)", s);
     const int nkeys = nty * ntx * 17;
     std::vector<long long> perm(Mtot);
     // sort by tile key, then (inside each (tile, T) run) by box corner, row-major within the
@@ -980,6 +1005,7 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
             for (const long long i : tmp) perm[a + cnt[key[i]]++] = i;
         }
     }, 1);
+    trace.mark("host sort by tile", s);
     std::vector<int2> meta(Mtot);
     std::vector<long long> fptr(Mtot + 1);
     std::vector<double2> kap(Mtot);
@@ -998,10 +1024,37 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
             yw[v] = make_float2(float(y[2 * i] / sigma[l]), float(y[2 * i + 1] / sigma[l]));
         }
     });
-    p->nnz = 0;
-    for (long long v = 0; v < Mtot; ++v) {
-        p->nnz += (long long)meta[v].y * meta[v].y;
-        fptr[v + 1] += fptr[v];
+    trace.mark("host rows (meta, data)", s);
+    {
+        // fptr[v + 1] holds row v's factor count: prefix sums (and nnz) over fixed blocks of rows,
+        // block totals first, then each block from its offset
+        const long long nblk = 64, bl = (Mtot + nblk - 1) / nblk;
+        std::vector<long long> bsum(nblk + 1, 0), bnnz(nblk, 0);
+        parallel_for(nblk, [&](long long b0, long long b1) {
+            for (long long b = b0; b < b1; ++b) {
+                long long t = 0, z = 0;
+                for (long long v = b * bl; v < std::min(Mtot, (b + 1) * bl); ++v) {
+                    t += fptr[v + 1];
+                    z += (long long)meta[v].y * meta[v].y;
+                }
+                bsum[b + 1] = t;
+                bnnz[b] = z;
+            }
+        }, 1);
+        p->nnz = 0;
+        for (long long b = 0; b < nblk; ++b) {
+            bsum[b + 1] += bsum[b];
+            p->nnz += bnnz[b];
+        }
+        parallel_for(nblk, [&](long long b0, long long b1) {
+            for (long long b = b0; b < b1; ++b) {
+                long long run = bsum[b];
+                for (long long v = b * bl; v < std::min(Mtot, (b + 1) * bl); ++v) {
+                    run += fptr[v + 1];
+                    fptr[v + 1] = run;
+                }
+            }
+        }, 1);
     }
     std::vector<double2> dde_sorted;
     if (dde) {
@@ -1018,6 +1071,7 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
     p->n_fac = fptr[Mtot];
     { std::vector<int> t; t.swap(key); } { std::vector<int> t; t.swap(corner1); } { std::vector<int> t; t.swap(corner2); }
 
+    trace.mark("host row offsets (prefix sums)", s);
     // ---- w-kernel table: planes -P1..P1, per axis up to 2*kMaxWHalf+1 taps
     const int n_planes = 2 * P1 + 1;
     std::vector<char> used(n_planes, 0);
@@ -1061,6 +1115,7 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
     p->bin_slots = sb.slots;
     const size_t n_slot = sb.pstart.size();
 
+    trace.mark("host w-kernels, chunks, bins", s);
     std::vector<double> eps(p->n_seg), inv_sig(p->n_seg);
     for (int l = 0; l < L; ++l) {
         const double Ml = double(vis_offsets[l + 1] - vis_offsets[l]);
@@ -1126,6 +1181,7 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
     if ((st = guard(upload(d_plane, plane.data(), Mtot, s))) != FHS_OK) return st;
     if ((st = guard(upload(d_wk, wk.data(), wk.size(), s))) != FHS_OK) return st;
     if ((st = guard(upload(d_isg, inv_sig.data(), p->n_seg, s))) != FHS_OK) return st;
+    trace.mark("device allocation and upload", s);
     {
         cudaError_t e = launch_build_g(p, d_kap, d_plane, d_wk, d_dde, ext, d_isg, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1296,6 +1352,7 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
         cudaEventCreateWithFlags(&p->ev_nuc, cudaEventDisableTiming) != cudaSuccess)
         return guard(fail(FHS_ERR_CUDA, "stream/event creation failed"));
 
+    trace.mark("G build and the other device state", s);
     // ---- step sizes (Condat-Vu: tau * sum_i sigma_i ||L_i||^2 < 1)
     p->tau = q.tau > 0 ? q.tau : 0.99 / 3.0;
     p->sigma1 = q.sigma1 > 0 ? q.sigma1 : 1.0;
@@ -1306,7 +1363,11 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
         std::vector<double> lam;
         const int n_it = q.power_iters > 0 ? q.power_iters : 100;
         const double tol = q.power_tol > 0 ? q.power_tol : 1e-7;
-        if ((st = guard(norm_estimate(p, n_it, tol, lam, s))) != FHS_OK) return st;
+        int steps = 0;
+        if ((st = guard(norm_estimate(p, n_it, tol, lam, s, &steps))) != FHS_OK) return st;
+        char what[64];
+        std::snprintf(what, sizeof what, "operator norms (%d Lanczos steps)", steps);
+        trace.mark(what, s);
         p->phi_norm2_max = *std::max_element(lam.begin(), lam.end());
         if (!(p->phi_norm2_max > 0)) return guard(fail(FHS_ERR_ARG, "operator norm is zero (no visibilities?)"));
         p->sigma2 = 1.0 / p->phi_norm2_max;
@@ -1314,6 +1375,7 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
     if ((st = guard(dev_alloc(p, &p->eta, L, false))) != FHS_OK) return st;
     if ((st = guard(psf_factors(p, s))) != FHS_OK) return st;
     if ((st = guard(default_regularisation(p, s))) != FHS_OK) return st;
+    trace.mark("PSF peaks, default regularisation", s);
     {
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return guard(fail(FHS_ERR_CUDA, "set-up failed: %s", cudaGetErrorString(e)));

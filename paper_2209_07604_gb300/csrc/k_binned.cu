@@ -56,10 +56,10 @@ static_assert(kAdjS >= kWin && kAdjS % 32 == 24, "adjoint window stride");
 #define FHS_BIN_MAX 384
 #endif
 constexpr int kBinMax = FHS_BIN_MAX;    // visibilities per bin (host splits longer runs)
-// The fixed-point scatter window (below) converts each contribution to an
-// integer of magnitude below 2^21 and adds at most kBinMax of them to a cell;
-// the sum stays inside int32 only while kBinMax <= 1024.
-static_assert(kBinMax <= 1024, "the fixed-point scatter window overflows int32 for bins above 1024 rows");
+// The fixed-point scatter window (below) converts each part of a contribution
+// to an integer of magnitude at most 2^22 and adds at most kBinMax of them to a
+// cell; the sum stays inside int32 only while kBinMax <= 511.
+static_assert(kBinMax <= 511, "the fixed-point scatter window overflows int32 for bins above 511 rows");
 static_assert(kBinMax <= 65536, "row offsets of a bin");
 // Pieces of a bin: runs of rows of one data block each (a tile's rows of all
 // blocks of a channel share one bin); the host merges blocks only while B <= kMaxPieces.
@@ -82,7 +82,8 @@ __device__ __forceinline__ float2 load_factors(const float2 *__restrict__ f, int
 enum { kDual = 0, kGather = 1, kScatter = 2, kNormal = 3 };
 
 constexpr float kFixMagic = 12582912.f;          // 1.5 * 2^23
-constexpr int kFixMagicBits = 0x4B400000;        // its bit pattern
+constexpr unsigned kFixMagicBits = 0x4B400000u;  // its bit pattern
+constexpr int kFixBits = 22;                     // contributions are scaled below 2^22
 
 // Scatter of rows i = i0, i0 + kWarps, ... of one bin by one warp,
 // grid += conj(G_i) s_d[i].  DENSE: the box lies in the shared window (shared
@@ -101,20 +102,57 @@ constexpr int kFixMagicBits = 0x4B400000;        // its bit pattern
 //
 // FIXED (dense bins): the window accumulates in 32-bit fixed point, with
 // native integer shared atomics (a float shared atomic costs about 3.5 times
-// as much).  A contribution c is converted as round(c S) by one FMA with
-// 1.5 * 2^23 (the sum lands in [2^23, 2^24), whose unit is 1, so its low
-// mantissa bits are the integer; valid for |c S| < 2^22).  S = 2^(21 - e)
-// with bound < 2^e, and bound >= |every contribution of the bin|, so |c S| <
-// 2^21 and a cell's sum of at most kBinMax contributions stays below 2^31.
+// as much).  With e = S conj(g2[col]) d formed once per row, the real part
+// of S conj(g1) e is rounded to an integer by two FMAs on 1.5 * 2^23:
+// fma(g1x, er, fma(g1y, ei, 1.5 * 2^23)) lands in [2^23, 2^24], whose unit is
+// 1, so the low mantissa bits hold the integer (each FMA rounds once: at most
+// one unit of error), and the bit pattern less the magic's is the integer;
+// likewise the imaginary part.  S = 2^(22 - e) with bound < 2^e and bound >=
+// |every contribution of the bin|, so each part is at most 2^22 in magnitude
+// and a cell's sums of at most kBinMax of them stay inside int32.  (Packing
+// both parts in one 64-bit atomic, im 2^32 + re, halves the atomics but was
+// measured 20-30 % slower.)  A lane whose cell lies outside its row's box
+// (t1 >= T or col >= T) holds a zero factor, so in fixed point it adds
+// exactly 0 to a cell that still lies in the window (corner offsets below
+// kTile = 32, t1 and col below 16: both below kWin = 47) instead of branching
+// around the atomics.
+
+// cell ib += conj(g1) e, with e = conj(g2) d already formed (and scaled by S
+// in fixed point).  The window is two planes (real, imaginary) of kWin x kAdjS
+// 32-bit words: integers in fixed point, floats otherwise.
 template <bool DENSE, bool FIXED>
-__device__ __forceinline__ void scatter_cell(float *s_re, float *s_im, int ib, float2 *__restrict__ gb,
-                                             long long gidx, float pr, float pi, float fs) {
+__device__ __forceinline__ void scatter_cell(int *s_win, int ib, float2 *__restrict__ gb,
+                                             long long gidx, float g1x, float g1y, float er, float ei) {
     if (DENSE && FIXED) {
-        atomicAdd(reinterpret_cast<int *>(s_re) + ib, __float_as_int(fmaf(pr, fs, kFixMagic)) - kFixMagicBits);
-        atomicAdd(reinterpret_cast<int *>(s_im) + ib, __float_as_int(fmaf(pi, fs, kFixMagic)) - kFixMagicBits);
+        const float re = fmaf(g1x, er, fmaf(g1y, ei, kFixMagic));
+        const float im = fmaf(g1x, ei, fmaf(-g1y, er, kFixMagic));
+        atomicAdd(s_win + ib, int(__float_as_uint(re) - kFixMagicBits));
+        atomicAdd(s_win + kWin * kAdjS + ib, int(__float_as_uint(im) - kFixMagicBits));
+    } else {
+        const float pr = fmaf(g1x, er, g1y * ei), pi = fmaf(g1x, ei, -g1y * er);
+        if (DENSE) {
+            float *s_re = reinterpret_cast<float *>(s_win);
+            atomicAdd(s_re + ib, pr);
+            atomicAdd(s_re + kWin * kAdjS + ib, pi);
+        } else {
+            red_add_f2(gb + gidx, make_float2(pr, pi));
+        }
+    }
+}
+
+// cell ib += (pr, pi), a contribution already formed (scaled by fs in fixed
+// point here: one rounding).
+template <bool DENSE, bool FIXED>
+__device__ __forceinline__ void scatter_value(int *s_win, int ib, float2 *__restrict__ gb,
+                                              long long gidx, float pr, float pi, float fs) {
+    if (DENSE && FIXED) {
+        const float re = fmaf(pr, fs, kFixMagic), im = fmaf(pi, fs, kFixMagic);
+        atomicAdd(s_win + ib, int(__float_as_uint(re) - kFixMagicBits));
+        atomicAdd(s_win + kWin * kAdjS + ib, int(__float_as_uint(im) - kFixMagicBits));
     } else if (DENSE) {
+        float *s_re = reinterpret_cast<float *>(s_win);
         atomicAdd(s_re + ib, pr);
-        atomicAdd(s_im + ib, pi);
+        atomicAdd(s_re + kWin * kAdjS + ib, pi);
     } else {
         red_add_f2(gb + gidx, make_float2(pr, pi));
     }
@@ -122,9 +160,8 @@ __device__ __forceinline__ void scatter_cell(float *s_re, float *s_im, int ib, f
 
 template <bool DENSE, bool FIXED>
 __device__ __forceinline__ void scatter_rows(int i0, int nv, int lane, const int2 *s_meta, const int *s_off,
-                                             const float2 *s_d, const float2 *__restrict__ fbin, float *s_re,
-                                             float *s_im, int wy0, int wx0, float2 *__restrict__ gb, int K1,
-                                             int K2, float fs) {
+                                             const float2 *s_d, const float2 *__restrict__ fbin, int *s_win,
+                                             int wy0, int wx0, float2 *__restrict__ gb, int K1, int K2, float fs) {
     constexpr unsigned FULL = 0xffffffffu;
     float2 fac = make_float2(0.f, 0.f);
     if (i0 < nv) fac = load_factors(fbin + s_off[i0], s_meta[i0].y, lane);
@@ -141,7 +178,11 @@ __device__ __forceinline__ void scatter_rows(int i0, int nv, int lane, const int
             const bool cin = col < T;
             const float g2x = __shfl_sync(FULL, fac.x, 16 + col), g2y = __shfl_sync(FULL, fac.y, 16 + col);
             // e = conj(g2[col]) d; cell (t1, col) += conj(g1[t1]) e
-            const float er = fmaf(g2x, dr, g2y * di), ei = fmaf(g2x, di, -g2y * dr);
+            float er = fmaf(g2x, dr, g2y * di), ei = fmaf(g2x, di, -g2y * dr);
+            if (FIXED) {
+                er *= fs;
+                ei *= fs;
+            }
             int ib = 0, k2 = 0;
             if (DENSE) {
                 ib = (c1 - wy0 + g) * kAdjS + (c2 - wx0 + col);
@@ -154,22 +195,25 @@ __device__ __forceinline__ void scatter_rows(int i0, int nv, int lane, const int
                 if (4 * k >= T) break;                   // warp-uniform
                 const int t1 = 4 * k + g;
                 const float g1x = __shfl_sync(FULL, fac.x, t1), g1y = __shfl_sync(FULL, fac.y, t1);
-                if (cin && t1 < T) {
-                    const float pr = fmaf(g1x, er, g1y * ei), pi = fmaf(g1x, ei, -g1y * er);
+                if ((DENSE && FIXED) || (cin && t1 < T)) {   // fixed point: the other cells add 0
                     long long gidx = 0;
                     if (!DENSE) {
                         int kk = c1 + t1;
                         kk -= (kk >= K1) ? K1 : 0;
                         gidx = (long long)kk * K2 + k2;
                     }
-                    scatter_cell<DENSE, FIXED>(s_re, s_im, ib + 4 * k * kAdjS, gb, gidx, pr, pi, fs);
+                    scatter_cell<DENSE, FIXED>(s_win, ib + 4 * k * kAdjS, gb, gidx, g1x, g1y, er, ei);
                 }
             }
         } else {
             const int half = lane >> 4, col = lane & 15;
             const bool cin = col < T;
             const float g2x = __shfl_sync(FULL, fac.x, 16 + col), g2y = __shfl_sync(FULL, fac.y, 16 + col);
-            const float er = fmaf(g2x, dr, g2y * di), ei = fmaf(g2x, di, -g2y * dr);
+            float er = fmaf(g2x, dr, g2y * di), ei = fmaf(g2x, di, -g2y * dr);
+            if (FIXED) {
+                er *= fs;
+                ei *= fs;
+            }
             int ib = 0, k2 = 0;
             if (DENSE) {
                 ib = (c1 - wy0 + 2 * half) * kAdjS + (c2 - wx0 + col);
@@ -185,15 +229,14 @@ __device__ __forceinline__ void scatter_rows(int i0, int nv, int lane, const int
                 const int dt = 4 * (k >> 1) + (k & 1);   // t1 = dt + 2 half
                 const int t1 = dt + 2 * half;
                 const float g1x = __shfl_sync(FULL, fac.x, t1), g1y = __shfl_sync(FULL, fac.y, t1);
-                if (cin && t1 < T) {
-                    const float pr = fmaf(g1x, er, g1y * ei), pi = fmaf(g1x, ei, -g1y * er);
+                if ((DENSE && FIXED) || (cin && t1 < T)) {   // fixed point: the other cells add 0
                     long long gidx = 0;
                     if (!DENSE) {
                         int kk = c1 + t1;
                         kk -= (kk >= K1) ? K1 : 0;
                         gidx = (long long)kk * K2 + k2;
                     }
-                    scatter_cell<DENSE, FIXED>(s_re, s_im, ib + dt * kAdjS, gb, gidx, pr, pi, fs);
+                    scatter_cell<DENSE, FIXED>(s_win, ib + dt * kAdjS, gb, gidx, g1x, g1y, er, ei);
                 }
             }
         }
@@ -211,9 +254,8 @@ __device__ __forceinline__ void scatter_rows(int i0, int nv, int lane, const int
 // (at most 2-way conflicts).  Per row, half the per-row work of scatter_rows.
 template <bool DENSE, bool FIXED>
 __device__ __forceinline__ void scatter_pairs(int i0, int nv, int lane, const int2 *s_meta, const int *s_off,
-                                              const float2 *s_d, const float2 *__restrict__ fbin, float *s_re,
-                                              float *s_im, int wy0, int wx0, float2 *__restrict__ gb, int K1,
-                                              int K2, float fs) {
+                                              const float2 *s_d, const float2 *__restrict__ fbin, int *s_win,
+                                              int wy0, int wx0, float2 *__restrict__ gb, int K1, int K2, float fs) {
     constexpr unsigned FULL = 0xffffffffu;
     const int v = lane >> 4, g = (lane >> 3) & 1, col = lane & 7, hi = g;
     auto load = [&](int r) -> float2 {
@@ -228,7 +270,7 @@ __device__ __forceinline__ void scatter_pairs(int i0, int nv, int lane, const in
     for (int i = i0; i < nv; i += 2 * kWarps) {
         const int r = i + v * kWarps;                // this half's row (may be past the end)
         const float2 fnx = load(r + 2 * kWarps);
-        int T = 0, c1 = 0, c2 = 0;
+        int T = 0, c1 = wy0, c2 = wx0;              // past the end: cells of the window, adding 0
         float dr = 0.f, di = 0.f;
         if (r < nv) {
             const int2 m = s_meta[r];
@@ -243,7 +285,11 @@ __device__ __forceinline__ void scatter_pairs(int i0, int nv, int lane, const in
         const float g2x = __shfl_sync(FULL, fac.x, 16 * v + 8 + col);
         const float g2y = __shfl_sync(FULL, fac.y, 16 * v + 8 + col);
         // e = conj(g2[col]) d; cell (t1, col) += conj(g1[t1]) e
-        const float er = fmaf(g2x, dr, g2y * di), ei = fmaf(g2x, di, -g2y * dr);
+        float er = fmaf(g2x, dr, g2y * di), ei = fmaf(g2x, di, -g2y * dr);
+        if (FIXED) {
+            er *= fs;
+            ei *= fs;
+        }
         int ib = 0, k2 = 0;
         if (DENSE) {
             ib = (c1 - wy0 + g) * kAdjS + (c2 - wx0 + col);
@@ -256,15 +302,14 @@ __device__ __forceinline__ void scatter_pairs(int i0, int nv, int lane, const in
             if (2 * k >= Tm) break;                      // warp-uniform
             const int t1 = 2 * k + g;
             const float g1x = __shfl_sync(FULL, fac.x, 16 * v + t1), g1y = __shfl_sync(FULL, fac.y, 16 * v + t1);
-            if (cin && t1 < T) {
-                const float pr = fmaf(g1x, er, g1y * ei), pi = fmaf(g1x, ei, -g1y * er);
+            if ((DENSE && FIXED) || (cin && t1 < T)) {   // fixed point: the other cells add 0
                 long long gidx = 0;
                 if (!DENSE) {
                     int kk = c1 + t1;
                     kk -= (kk >= K1) ? K1 : 0;
                     gidx = (long long)kk * K2 + k2;
                 }
-                scatter_cell<DENSE, FIXED>(s_re, s_im, ib + 2 * k * kAdjS, gb, gidx, pr, pi, fs);
+                scatter_cell<DENSE, FIXED>(s_win, ib + 2 * k * kAdjS, gb, gidx, g1x, g1y, er, ei);
             }
         }
         fac = fnx;
@@ -278,7 +323,7 @@ __device__ __forceinline__ void scatter_pairs(int i0, int nv, int lane, const in
 template <bool DENSE, bool FIXED>
 __device__ __forceinline__ void scatter_rows_rank(int i0, int nv, int lane, int R, const int2 *s_meta,
                                                   const int *s_off, const float2 *s_d,
-                                                  const float2 *__restrict__ fbin, float *s_re, float *s_im,
+                                                  const float2 *__restrict__ fbin, int *s_win,
                                                   int wy0, int wx0, float2 *__restrict__ gb, int K1, int K2,
                                                   float fs) {
     constexpr unsigned FULL = 0xffffffffu;
@@ -324,7 +369,7 @@ __device__ __forceinline__ void scatter_rows_rank(int i0, int nv, int lane, int 
         for (int k = 0; k < 8; ++k) {
             if (k >= n) break;
             const int t1 = 4 * (k >> 1) + (k & 1) + 2 * half;
-            if (cin && t1 < T) {
+            if ((DENSE && FIXED) || (cin && t1 < T)) {   // fixed point: the other cells add 0
                 long long gidx = 0;
                 if (!DENSE) {
                     int kk = c1 + t1;
@@ -332,7 +377,7 @@ __device__ __forceinline__ void scatter_rows_rank(int i0, int nv, int lane, int 
                     gidx = (long long)kk * K2 + k2;
                 }
                 const int ib = DENSE ? (c1 - wy0 + t1) * kAdjS + (c2 - wx0 + col) : 0;
-                scatter_cell<DENSE, FIXED>(s_re, s_im, ib, gb, gidx, accr[k], acci[k], fs);
+                scatter_value<DENSE, FIXED>(s_win, ib, gb, gidx, accr[k], acci[k], fs);
             }
         }
     }
@@ -548,8 +593,7 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
     const int R = MULTI ? R_ : 1;
     __shared__ alignas(128) float2 s_grid[kWin * kWinP];
     __shared__ alignas(8) uint64_t s_bar;
-    __shared__ float s_re[kWin * kAdjS];     // adjoint window planes, row stride kAdjS
-    __shared__ float s_im[kWin * kAdjS];
+    __shared__ alignas(16) int s_win[2 * kWin * kAdjS];   // adjoint window planes, row stride kAdjS
     __shared__ int2 s_meta[kBinMax];
     __shared__ int s_off[kBinMax];        // factor offset of each row from the bin's base
     __shared__ long long s_v[kBinMax];    // visibility (sorted) index of each row
@@ -645,11 +689,9 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
                 while (k2 >= K2) k2 -= K2;
                 s_grid[r * kWinP + c] = gl[(long long)k1 * K2 + k2];
             }
-            if (MODE != kGather && MODE != kDual) {
-                s_re[r * kAdjS + c] = 0.f;
-                s_im[r * kAdjS + c] = 0.f;
-            }
         }
+        if (MODE != kGather && MODE != kDual)
+            for (int i = threadIdx.x; i < 2 * kWin * kAdjS; i += blockDim.x) s_win[i] = 0;
     }
     __syncthreads();                     // the barrier's initialisation is visible from here on
     if (tma && !window_wait(&s_bar, kWindowPolls, err)) {
@@ -694,40 +736,40 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
             int e = 0;
             if (bound > 0.f) frexpf(bound, &e);             // bound < 2^e
             // fixed point unless a value is not finite or the bin is so faint (bound < 2^-100)
-            // that 2^(21 - e) would overflow: those bins keep the float atomics
+            // that 2^(22 - e) would overflow: those bins keep the float atomics
             if (!s_bad && isfinite(bound) && e >= -100) {
                 fixed = true;
-                fs = ldexpf(1.f, 21 - e);
-                finv = ldexpf(1.f, e - 21);
+                fs = ldexpf(1.f, kFixBits - e);
+                finv = ldexpf(1.f, e - kFixBits);
             }
         }
         if (MULTI) {
             if (dense && fixed)
-                scatter_rows_rank<true, true>(warp, nv, lane, R, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb,
+                scatter_rows_rank<true, true>(warp, nv, lane, R, s_meta, s_off, s_d, fbin, s_win, wy0, wx0, gb,
                                               K1, K2, fs);
             else if (dense)
-                scatter_rows_rank<true, false>(warp, nv, lane, R, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb,
+                scatter_rows_rank<true, false>(warp, nv, lane, R, s_meta, s_off, s_d, fbin, s_win, wy0, wx0, gb,
                                                K1, K2, fs);
             else
-                scatter_rows_rank<false, false>(warp, nv, lane, R, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb,
+                scatter_rows_rank<false, false>(warp, nv, lane, R, s_meta, s_off, s_d, fbin, s_win, wy0, wx0, gb,
                                                 K1, K2, fs);
         } else if (s_tmax <= 8) {
             // every row of the bin has at most 8 taps: two rows per warp step
             if (dense && fixed)
-                scatter_pairs<true, true>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1, K2,
+                scatter_pairs<true, true>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_win, wy0, wx0, gb, K1, K2,
                                           fs);
             else if (dense)
-                scatter_pairs<true, false>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1, K2,
+                scatter_pairs<true, false>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_win, wy0, wx0, gb, K1, K2,
                                            fs);
             else
-                scatter_pairs<false, false>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1,
+                scatter_pairs<false, false>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_win, wy0, wx0, gb, K1,
                                             K2, fs);
         } else if (dense && fixed)
-            scatter_rows<true, true>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1, K2, fs);
+            scatter_rows<true, true>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_win, wy0, wx0, gb, K1, K2, fs);
         else if (dense)
-            scatter_rows<true, false>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1, K2, fs);
+            scatter_rows<true, false>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_win, wy0, wx0, gb, K1, K2, fs);
         else
-            scatter_rows<false, false>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_re, s_im, wy0, wx0, gb, K1, K2,
+            scatter_rows<false, false>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_win, wy0, wx0, gb, K1, K2,
                                        fs);
     }
     if (MODE != kDual) {
@@ -735,10 +777,16 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
             __syncthreads();
             for (int q = threadIdx.x; q < kWin * kWin; q += blockDim.x) {
                 const int r = q / kWin, c = q - r * kWin;
-                float re = s_re[r * kAdjS + c], im = s_im[r * kAdjS + c];
+                float re, im;
                 if (fixed) {
-                    re = float(__float_as_int(re)) * finv;     // exact scaling by a power of two
-                    im = float(__float_as_int(im)) * finv;
+                    // im 2^32 + re: the low word is re (signed); the rest, less re, is im 2^32
+                    const int ir = s_win[r * kAdjS + c], ii = s_win[kWin * kAdjS + r * kAdjS + c];
+                    re = float(ir) * finv;                    // exact scaling by a power of two
+                    im = float(ii) * finv;
+                } else {
+                    const float *s_re = reinterpret_cast<const float *>(s_win);
+                    re = s_re[r * kAdjS + c];
+                    im = s_re[kWin * kAdjS + r * kAdjS + c];
                 }
                 if (re != 0.f || im != 0.f) {
                     int k1 = wy0 + r;
