@@ -444,6 +444,42 @@ __device__ __forceinline__ void gather_chunks(const float2 *__restrict__ f, int 
         gather_chunks<C0 + CW, TT, DENSE>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, gl, K1, K2, ar, ai);
 }
 
+// Gather of a row whose side is exactly TT (at most 8) from the shared
+// window: the row's 2 TT factors are loaded at once, two per 16-byte load (a
+// row's factors start on a 16-byte boundary: offsets are multiples of 2 T
+// values of 8 bytes), and every loop is unrolled, so the row waits for one
+// memory latency.
+template <int TT>
+__device__ __forceinline__ float2 gather_exact(const float2 *__restrict__ f, int c1, int c2, const float2 *s_grid,
+                                               int wy0, int wx0) {
+    static_assert(TT <= 8, "exact-side gather");
+    float2 g[2 * TT];
+    const float4 *f4 = reinterpret_cast<const float4 *>(f);
+#pragma unroll
+    for (int k = 0; k < TT; ++k) {
+        const float4 q = __ldg(f4 + k);
+        g[2 * k] = make_float2(q.x, q.y);
+        g[2 * k + 1] = make_float2(q.z, q.w);
+    }
+    float ar = 0.f, ai = 0.f;
+    const float2 *row = s_grid + (c1 - wy0) * kWinP + (c2 - wx0);
+#pragma unroll
+    for (int t1 = 0; t1 < TT; ++t1) {
+        float br = 0.f, bi = 0.f;
+#pragma unroll
+        for (int t2 = 0; t2 < TT; ++t2) {
+            const float2 x = row[t1 * kWinP + t2];
+            const float2 b = g[TT + t2];
+            br = fmaf(b.x, x.x, fmaf(-b.y, x.y, br));
+            bi = fmaf(b.x, x.y, fmaf(b.y, x.x, bi));
+        }
+        const float2 a = g[t1];
+        ar = fmaf(a.x, br, fmaf(-a.y, bi, ar));
+        ai = fmaf(a.x, bi, fmaf(a.y, br, ai));
+    }
+    return make_float2(ar, ai);
+}
+
 template <int TT, bool DENSE>
 __device__ __forceinline__ float2 gather_lane(const float2 *__restrict__ f, int T, int t_lo, int t_hi, int c1,
                                               int c2, const float2 *s_grid, int wy0, int wx0,
@@ -488,7 +524,7 @@ __device__ __forceinline__ void gather_phase(int nv, int R, const int2 *s_meta, 
     const int nvr = (nv + 31) & ~31;                 // whole warps: the max below takes every lane
     for (int i = threadIdx.x; i < nvr; i += blockDim.x) {
         const bool valid = i < nv;
-        int T = 0, c1 = 0, c2 = 0;
+        int T = 0, c1 = wy0, c2 = wx0;                   // past the end: the window origin, nothing read
         const float2 *f = fbin;
         if (valid) {
             const int2 m = s_meta[i];
@@ -498,8 +534,18 @@ __device__ __forceinline__ void gather_phase(int nv, int R, const int2 *s_meta, 
             f = fbin + s_off[i];
         }
         const int tm = __reduce_max_sync(0xffffffffu, T);
+        // every valid row of the warp has side tm (7 or 8), one term, window in shared memory
+        const bool exact = DENSE && R == 1 && (tm == 7 || tm == 8) &&
+                           __reduce_min_sync(0xffffffffu, valid ? T : 16) == tm;
         float2 phi;
-        if (tm <= 4) phi = gather_terms<4, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
+        if (exact) {
+            // rows past the end take no part (the exact gather reads every cell of its box)
+            phi = make_float2(0.f, 0.f);
+            if (valid)
+                phi = tm == 7 ? gather_exact<7>(f, c1, c2, s_grid, wy0, wx0)
+                              : gather_exact<8>(f, c1, c2, s_grid, wy0, wx0);
+        }
+        else if (tm <= 4) phi = gather_terms<4, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
         else if (tm <= 7) phi = gather_terms<7, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
         else if (tm <= 9) phi = gather_terms<9, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
         else if (tm <= 11) phi = gather_terms<11, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
