@@ -124,7 +124,10 @@ void free_all(fhs_problem *p) {
     for (void *q : p->allocs) cudaFreeAsync(q, p->home);
     p->allocs.clear();
     cudaStreamSynchronize(p->home);
-    if (p->plan_ok) cufftDestroy(p->plan);
+    if (p->plan_ok) {
+        cufftDestroy(p->plan_r2c);
+        cufftDestroy(p->plan_c2r);
+    }
     p->plan_ok = false;
     for (cudaStream_t *t : {&p->s_sara, &p->s_nuc})
         if (*t) { cudaStreamDestroy(*t); *t = nullptr; }
@@ -372,38 +375,56 @@ fhs_status check_params(const fhs_params *q) {
     return FHS_OK;
 }
 
-fhs_status fft(fhs_problem *p, float2 *in, float2 *out, int dir, cudaStream_t s) {
-    CUFFT(cufftSetStream(p->plan, s));
-    CUFFT(cufftExecC2C(p->plan, reinterpret_cast<cufftComplex *>(in), reinterpret_cast<cufftComplex *>(out), dir));
+// F of a real zero-padded grid: R2C into columns 0..K2/2 of `out` (row stride K2), then the
+// other columns by Hermitian symmetry, so that the passes over G read a full spectrum.
+fhs_status fft_forward(fhs_problem *p, const float *in, float2 *out, cudaStream_t s) {
+    CUFFT(cufftSetStream(p->plan_r2c, s));
+    CUFFT(cufftExecR2C(p->plan_r2c, const_cast<cufftReal *>(in), reinterpret_cast<cufftComplex *>(out)));
+    CU(launch_expand(p, out, s));
     return FHS_OK;
 }
 
-// Phi^H applied to sorted visibilities `vis`, result as an inverse-FFT'd grid in `grid`.
-fhs_status adjoint_to_grid(fhs_problem *p, const float2 *vis, float2 *grid, cudaStream_t s) {
-    CU(cudaMemsetAsync(grid, 0, sizeof(float2) * p->K * p->L, s));
-    CU(launch_grid(p, vis, grid, s));
-    TRY(fft(p, grid, grid, CUFFT_INVERSE, s));
+// Re F^H g from the Hermitian part of g held in columns 0..K2/2 of `in` (the folded adjoint):
+// C2R into the real grid `out`.  The transform overwrites `in`.
+fhs_status fft_inverse(fhs_problem *p, float2 *in, float *out, cudaStream_t s) {
+    CUFFT(cufftSetStream(p->plan_c2r, s));
+    CUFFT(cufftExecC2R(p->plan_c2r, reinterpret_cast<cufftComplex *>(in), reinterpret_cast<cufftReal *>(out)));
+    return FHS_OK;
+}
+
+// Zeroes the columns 0..K2/2 of every row of L grids: all that a folded scatter writes.
+fhs_status zero_half(fhs_problem *p, float2 *grid, cudaStream_t s) {
+    CU(cudaMemset2DAsync(grid, sizeof(float2) * p->K2, 0, sizeof(float2) * (p->K2 / 2 + 1),
+                         (size_t)p->K1 * p->L, s));
+    return FHS_OK;
+}
+
+// Re F^H G^H of sorted visibilities `vis` into the real grid `out` (grid: scratch).
+fhs_status adjoint_to_real(fhs_problem *p, const float2 *vis, float2 *grid, float *out, cudaStream_t s) {
+    TRY(zero_half(p, grid, s));
+    CU(launch_grid(p, vis, grid, s, true, true));
+    TRY(fft_inverse(p, grid, out, s));
     return FHS_OK;
 }
 
 fhs_status forward_from_image(fhs_problem *p, const float *x, float2 *vis_sorted, cudaStream_t s) {
     CU(launch_zpad(p, x, p->grid_in, s));
-    TRY(fft(p, p->grid_in, p->grid_aux, CUFFT_FORWARD, s));
+    TRY(fft_forward(p, p->grid_in, p->grid_aux, s));
     CU(launch_degrid(p, p->grid_aux, vis_sorted, s));
     return FHS_OK;
 }
 
 fhs_status adjoint_to_image(fhs_problem *p, const float2 *vis_sorted, float *x, cudaStream_t s) {
-    TRY(adjoint_to_grid(p, vis_sorted, p->grid_aux, s));
-    CU(launch_crop(p, p->grid_aux, x, s));
+    TRY(adjoint_to_real(p, vis_sorted, p->grid_aux, p->real_scr, s));
+    CU(launch_crop(p, p->real_scr, x, s));
     return FHS_OK;
 }
 
 // y = Re(Phi^H Phi) v for every channel: one pass over G in the normal mode
 // (gather and scatter of each row together) between the two FFTs.  grid_in
-// keeps its zero padding (Z writes the image cells only) and grid_work (Phi^H
-// of the data dual) is iteration state, so the adjoint grids go to the first
-// grids of grid_scr, which are zero between uses and zero again after.
+// keeps its zero padding (Z writes the image cells only) and grid_work and
+// adj_real (Phi^H of the data dual) are iteration state, so the adjoint grids
+// go to grid_scr and real_scr.
 //
 // With data reduction, y = Re(Phi'^H Phi') v = Re Z^T F^H H Lambda^2 H F Z v:
 // two passes over G with the Lambda^2 weighting between them (dr_u and dr_w
@@ -411,17 +432,17 @@ fhs_status adjoint_to_image(fhs_problem *p, const float2 *vis_sorted, float *x, 
 fhs_status apply_normal(fhs_problem *p, const float *v, float *y, cudaStream_t s) {
     float2 *scratch = p->grid_scr;
     CU(launch_zpad(p, v, p->grid_in, s));
-    TRY(fft(p, p->grid_in, p->grid_aux, CUFFT_FORWARD, s));
+    TRY(fft_forward(p, p->grid_in, p->grid_aux, s));
+    TRY(zero_half(p, scratch, s));
     if (p->dr) {
-        CU(launch_normal(p, p->grid_aux, p->dr_u, s, false));
+        CU(launch_normal(p, p->grid_aux, p->dr_u, s, false, false));
         CU(launch_dr_combine(p, p->dr_u, 0.f, 1.f, p->dr_w, s));
-        CU(launch_normal(p, p->dr_w, scratch, s, false));
+        CU(launch_normal(p, p->dr_w, scratch, s, false, true));
     } else {
-        CU(launch_normal(p, p->grid_aux, scratch, s, true));
+        CU(launch_normal(p, p->grid_aux, scratch, s, true, true));
     }
-    TRY(fft(p, scratch, scratch, CUFFT_INVERSE, s));
-    CU(launch_crop(p, scratch, y, s));
-    CU(cudaMemsetAsync(scratch, 0, sizeof(float2) * p->K * p->L, s));
+    TRY(fft_inverse(p, scratch, p->real_scr, s));
+    CU(launch_crop(p, p->real_scr, y, s));
     return FHS_OK;
 }
 
@@ -430,10 +451,10 @@ fhs_status apply_normal(fhs_problem *p, const float *v, float *y, cudaStream_t s
 fhs_status dirty_image(fhs_problem *p, float *x, cudaStream_t s) {
     if (!p->dr) return adjoint_to_image(p, p->y, x, s);
     CU(launch_dr_combine(p, nullptr, 1.f, 0.f, p->dr_w, s));
-    CU(cudaMemsetAsync(p->grid_aux, 0, sizeof(float2) * p->K * p->L, s));
-    CU(launch_normal(p, p->dr_w, p->grid_aux, s, false));
-    TRY(fft(p, p->grid_aux, p->grid_aux, CUFFT_INVERSE, s));
-    CU(launch_crop(p, p->grid_aux, x, s));
+    TRY(zero_half(p, p->grid_aux, s));
+    CU(launch_normal(p, p->dr_w, p->grid_aux, s, false, true));
+    TRY(fft_inverse(p, p->grid_aux, p->real_scr, s));
+    CU(launch_crop(p, p->real_scr, x, s));
     return FHS_OK;
 }
 
@@ -683,11 +704,11 @@ fhs_status one_iteration(fhs_problem *p, cudaStream_t s) {
     // data fidelity: F, dual pass over G, l2-ball factors, scatter pass, F^H
     {
         Phase ph(p, s, FHS_PHASE_FFT_FWD);
-        TRY(fft(p, p->grid_in, p->grid_work, CUFFT_FORWARD, s));
+        TRY(fft_forward(p, p->grid_in, p->grid_work, s));
     }
     {
         Phase ph(p, s, FHS_PHASE_DEGRID_GRID);
-        if (p->dr) CU(launch_normal(p, p->grid_work, p->dr_u, s, false));     // H Xhat
+        if (p->dr) CU(launch_normal(p, p->grid_work, p->dr_u, s, false, false));     // H Xhat
         else CU(launch_data_dual(p, s));                               // d, block norms
     }
     if (fork) {
@@ -703,20 +724,20 @@ fhs_status one_iteration(fhs_problem *p, cudaStream_t s) {
             CU(launch_dr_finalize(p, s));
         }
         Phase ph(p, s, FHS_PHASE_SCATTER);
-        CU(launch_normal(p, p->dr_w, p->grid_work, s, false));
+        CU(launch_normal(p, p->dr_w, p->grid_work, s, false, true));
     } else {
         // l2-ball factors, then G^H (s_b d) straight into the channel grids
         {
             Phase ph(p, s, FHS_PHASE_L2BALL);
             CU(launch_block_finalize(p, s));
-            CU(cudaMemsetAsync(p->grid_work, 0, sizeof(float2) * p->K * p->L, s));
+            TRY(zero_half(p, p->grid_work, s));
         }
         Phase ph(p, s, FHS_PHASE_SCATTER);
         CU(launch_data_scatter(p, s));
     }
     {
         Phase ph(p, s, FHS_PHASE_FFT_INV);
-        TRY(fft(p, p->grid_work, p->grid_work, CUFFT_INVERSE, s));
+        TRY(fft_inverse(p, p->grid_work, p->adj_real, s));
     }
     // average joint sparsity
     if (sara_active(p)) {
@@ -794,12 +815,13 @@ fhs_status run_iterations(fhs_problem *p, int n, cudaStream_t s) {
     return FHS_OK;
 }
 
+// Work area of the R2C and C2R plans (one shared area: the larger of the two).
 size_t cufft_workspace(int K1, int K2, int L) {
-    int n[2] = {K1, K2};
-    size_t ws = 0;
-    if (cufftEstimateMany(2, n, nullptr, 1, K1 * K2, nullptr, 1, K1 * K2, CUFFT_C2C, L, &ws) != CUFFT_SUCCESS)
-        return 0;
-    return ws;
+    int n[2] = {K1, K2}, emb[2] = {K1, K2};
+    size_t wf = 0, wi = 0;
+    if (cufftEstimateMany(2, n, emb, 1, K1 * K2, emb, 1, K1 * K2, CUFFT_R2C, L, &wf) != CUFFT_SUCCESS) wf = 0;
+    if (cufftEstimateMany(2, n, emb, 1, K1 * K2, emb, 1, K1 * K2, CUFFT_C2R, L, &wi) != CUFFT_SUCCESS) wi = 0;
+    return std::max(wf, wi);
 }
 
 }  // namespace
@@ -1205,17 +1227,37 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
         if ((st = guard(upload(p->s2, s2.data(), q.nx, s))) != FHS_OK) return st;
     }
     {
-        int n[2] = {K1, K2};
-        if (cufftPlanMany(&p->plan, 2, n, nullptr, 1, int(p->K), nullptr, 1, int(p->K), CUFFT_C2C, L) != CUFFT_SUCCESS)
-            return guard(fail(FHS_ERR_CUDA, "cufftPlanMany failed"));
+        // R2C: real [L][K1][K2] -> complex columns 0..K2/2 of [L][K1][K2]; C2R the reverse.  One
+        // work area serves both (they never run at the same time on a problem's streams).
+        int n[2] = {K1, K2}, emb[2] = {K1, K2};
+        size_t ws_f = 0, ws_i = 0;
+        if (cufftCreate(&p->plan_r2c) != CUFFT_SUCCESS) return guard(fail(FHS_ERR_CUDA, "cufftCreate failed"));
+        if (cufftCreate(&p->plan_c2r) != CUFFT_SUCCESS) {
+            cufftDestroy(p->plan_r2c);
+            return guard(fail(FHS_ERR_CUDA, "cufftCreate failed"));
+        }
         p->plan_ok = true;
-        size_t ws = 0;
-        if (cufftGetSize(p->plan, &ws) == CUFFT_SUCCESS) p->bytes += ws;
+        if (cufftSetAutoAllocation(p->plan_r2c, 0) != CUFFT_SUCCESS ||
+            cufftSetAutoAllocation(p->plan_c2r, 0) != CUFFT_SUCCESS ||
+            cufftMakePlanMany(p->plan_r2c, 2, n, emb, 1, int(p->K), emb, 1, int(p->K), CUFFT_R2C, L, &ws_f) !=
+                CUFFT_SUCCESS ||
+            cufftMakePlanMany(p->plan_c2r, 2, n, emb, 1, int(p->K), emb, 1, int(p->K), CUFFT_C2R, L, &ws_i) !=
+                CUFFT_SUCCESS)
+            return guard(fail(FHS_ERR_CUDA, "cuFFT plan set-up failed"));
+        const size_t ws = std::max<size_t>(std::max(ws_f, ws_i), 1);
+        char *w = nullptr;
+        if ((st = guard(dev_alloc(p, &w, ws, false))) != FHS_OK) return st;
+        p->fft_ws = w;
+        if (cufftSetWorkArea(p->plan_r2c, p->fft_ws) != CUFFT_SUCCESS ||
+            cufftSetWorkArea(p->plan_c2r, p->fft_ws) != CUFFT_SUCCESS)
+            return guard(fail(FHS_ERR_CUDA, "cufftSetWorkArea failed"));
     }
     if ((st = guard(dev_alloc(p, &p->grid_in, p->K * L))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->grid_work, p->K * L))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->grid_aux, p->K * L))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->grid_scr, p->K * L))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->adj_real, p->K * L))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->real_scr, p->K * L, false))) != FHS_OK) return st;
     if (p->dr) {
         // gridding (Sec. 3.4): diag(H_l) by one pass over the rows, Lambda_l, y'_l, M'_l
         const size_t LK = (size_t)p->K * L;
@@ -1233,7 +1275,7 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
         if ((st = guard(dev_alloc(p, &cnt, L))) != FHS_OK) return st;
         std::vector<unsigned long long> hc(L);
         cudaError_t e = launch_dr_diag(p, diag, s);
-        if (e == cudaSuccess) e = launch_grid(p, p->y, p->dr_u, s, false);
+        if (e == cudaSuccess) e = launch_grid(p, p->y, p->dr_u, s, false, false);
         if (e == cudaSuccess) e = launch_dr_setup(p, diag, p->dr_u, cnt, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), cnt, sizeof(unsigned long long) * L, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1468,7 +1510,7 @@ fhs_status fhs_estimate_bytes(const fhs_params *params, const double *w, int64_t
     const long long npiece = nbin * std::min<long long>(B <= kBinMaxPieces ? B : 1, kBinMaxPieces);
     r += 16 * nbin + 16 * npiece + 8 * (nchunk + 1) + 4 * nchunk;
     r += 4 * (q.ny + q.nx);                                          // Z scaling
-    r += 8 * K * L * 4;                                              // grids
+    r += 8 * K * L * 3 + 4 * K * L * 3;                              // complex grids, real grids
     r += 4 * N * L * 3 + 16 + 16 * L + 4 * L;                        // images, reductions, PSF factors
     r += 4 * c.n_coef * L * 2 + 4 * c.n_tmp * L + 4 * c.n_coef * C;  // SARA
     const long long ne = Lc + (Lc & 1);
@@ -1592,15 +1634,15 @@ fhs_status fhs_residual(fhs_problem *p, const float *x_dev, float *r_dev, void *
         float2 *u = nullptr;
         if (x_dev) {
             CU(launch_zpad(p, x_dev, p->grid_in, s));
-            TRY(fft(p, p->grid_in, p->grid_aux, CUFFT_FORWARD, s));
-            CU(launch_normal(p, p->grid_aux, p->dr_u, s, false));
+            TRY(fft_forward(p, p->grid_in, p->grid_aux, s));
+            CU(launch_normal(p, p->grid_aux, p->dr_u, s, false, false));
             u = p->dr_u;
         }
         CU(launch_dr_combine(p, u, 1.f, -1.f, p->dr_w, s));
-        CU(cudaMemsetAsync(p->grid_aux, 0, sizeof(float2) * p->K * p->L, s));
-        CU(launch_normal(p, p->dr_w, p->grid_aux, s, false));
-        TRY(fft(p, p->grid_aux, p->grid_aux, CUFFT_INVERSE, s));
-        CU(launch_crop(p, p->grid_aux, r_dev, s));
+        TRY(zero_half(p, p->grid_aux, s));
+        CU(launch_normal(p, p->dr_w, p->grid_aux, s, false, true));
+        TRY(fft_inverse(p, p->grid_aux, p->real_scr, s));
+        CU(launch_crop(p, p->real_scr, r_dev, s));
         CU(launch_chan_scale(p, r_dev, p->eta, s));
         return FHS_OK;
     }
@@ -1628,8 +1670,8 @@ fhs_status fhs_noise_from_model(fhs_problem *p, const float *x0_dev, int32_t app
         CU(cudaMemsetAsync(st, 0, sizeof(double) * n_st, s));
         if (p->dr) {
             CU(launch_zpad(p, x0_dev, p->grid_in, s));
-            TRY(fft(p, p->grid_in, p->grid_aux, CUFFT_FORWARD, s));
-            CU(launch_normal(p, p->grid_aux, p->dr_u, s, false));
+            TRY(fft_forward(p, p->grid_in, p->grid_aux, s));
+            CU(launch_normal(p, p->grid_aux, p->dr_u, s, false, false));
             CU(launch_dr_resid_norm(p, st, s));
         } else {
             TRY(forward_from_image(p, x0_dev, p->vis_tmp, s));
@@ -1858,16 +1900,16 @@ fhs_status fhs_set_state(fhs_problem *p, int32_t part, const float *src, void *s
                 // the reduced dual and its adjoint grid F^H H Lambda v (what the next primal step reads)
                 CU(cudaMemcpyAsync(p->dr_v, src, b, cudaMemcpyDeviceToDevice, s));
                 CU(launch_dr_weight(p, s));
-                CU(cudaMemsetAsync(p->grid_work, 0, sizeof(float2) * p->K * p->L, s));
-                CU(launch_normal(p, p->dr_w, p->grid_work, s, false));
-                TRY(fft(p, p->grid_work, p->grid_work, CUFFT_INVERSE, s));
+                TRY(zero_half(p, p->grid_work, s));
+                CU(launch_normal(p, p->dr_w, p->grid_work, s, false, true));
+                TRY(fft_inverse(p, p->grid_work, p->adj_real, s));
                 CU(cudaStreamSynchronize(s));
                 break;
             }
             CU(launch_permute_from_caller(p, reinterpret_cast<const float2 *>(src), p->dvis, s));
             std::vector<float> ones(p->n_seg, 1.0f);
             CU(cudaMemcpyAsync(p->blk_scale, ones.data(), sizeof(float) * p->n_seg, cudaMemcpyHostToDevice, s));
-            TRY(adjoint_to_grid(p, p->dvis, p->grid_work, s));
+            TRY(adjoint_to_real(p, p->dvis, p->grid_work, p->adj_real, s));
             CU(cudaStreamSynchronize(s));
             break;
         }
@@ -1912,7 +1954,7 @@ fhs_status fhs_autotune_bins(fhs_problem *p, void *stream, int32_t *dense_min_ou
     }
     TRY(upload(p->coef_tmp, x0.data(), LN, s));
     CU(launch_zpad(p, p->coef_tmp, p->grid_in, s));
-    TRY(fft(p, p->grid_in, p->grid_aux, CUFFT_FORWARD, s));
+    TRY(fft_forward(p, p->grid_in, p->grid_aux, s));
 
     const DevBins cur = current_bins(p);
     cudaStream_t home = p->home;
@@ -1930,9 +1972,9 @@ fhs_status fhs_autotune_bins(fhs_problem *p, void *stream, int32_t *dense_min_ou
     };
     auto time_bins = [&](const DevBins &b, float &ms) -> fhs_status {
         use_bins(p, b);
-        CU(launch_normal(p, p->grid_aux, p->grid_scr, s, !p->dr));          // warm-up
+        CU(launch_normal(p, p->grid_aux, p->grid_scr, s, !p->dr, true));    // warm-up
         CU(cudaEventRecord(e0, s));
-        for (int r = 0; r < 3; ++r) CU(launch_normal(p, p->grid_aux, p->grid_scr, s, !p->dr));
+        for (int r = 0; r < 3; ++r) CU(launch_normal(p, p->grid_aux, p->grid_scr, s, !p->dr, true));
         CU(cudaEventRecord(e1, s));
         CU(cudaEventSynchronize(e1));
         CU(cudaEventElapsedTime(&ms, e0, e1));

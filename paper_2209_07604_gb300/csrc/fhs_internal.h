@@ -112,12 +112,18 @@ struct fhs_problem {
     long long *chunk_start = nullptr;         // [n_chunk+1]
     int *chunk_seg = nullptr;                 // [n_chunk]
     float *s1 = nullptr, *s2 = nullptr;       // Z scaling per axis
-    cufftHandle plan = 0;
+    // F on real images: R2C of the zero-padded image into the lower half of a full grid (columns
+    // 0..K2/2, row stride K2), the upper half filled by Hermitian symmetry; F^H through C2R from
+    // the lower half of a grid that holds the Hermitian part of the adjoint (the scatter folds)
+    cufftHandle plan_r2c = 0, plan_c2r = 0;
     bool plan_ok = false;
-    float2 *grid_in = nullptr;                // [L][K] zero-padded input (zeros persist)
-    float2 *grid_work = nullptr;              // [L][K] FFT output / data adjoint grid
-    float2 *grid_scr = nullptr;               // [L][K] scratch output grids (zero between uses)
+    void *fft_ws = nullptr;                   // work area shared by both plans
+    float *grid_in = nullptr;                 // [L][K] real zero-padded input (zeros persist)
+    float2 *grid_work = nullptr;              // [L][K] forward spectrum / folded data adjoint grid
+    float2 *grid_scr = nullptr;               // [L][K] scratch output grids
     float2 *grid_aux = nullptr;               // [L][K] scratch for measure/adjoint
+    float *adj_real = nullptr;                // [L][K] F^H of the data adjoint grid (iteration state)
+    float *real_scr = nullptr;                // [L][K] F^H output of the other calls
 
     // data reduction (Sec. 3.4): grids [L][K], zero off the gridded cells
     bool dr = false;
@@ -203,18 +209,24 @@ void destroy_on_stream(fhs_problem *p, cudaStream_t s);
 // dde: NULL, or [Mtot][kDdeTaps^2] DDE kernels in sorted order; ext = kDdeTaps - 1 with DDEs, else 0.
 cudaError_t launch_build_g(fhs_problem *p, const double2 *kap, const short *plane, const double2 *wk_table,
                            const double2 *dde, int ext, const double *inv_sigma_seg, cudaStream_t s);
-cudaError_t launch_zpad(fhs_problem *p, const float *x, float2 *grid, cudaStream_t s);
+cudaError_t launch_zpad(fhs_problem *p, const float *x, float *grid, cudaStream_t s);
+// the upper half (columns K2/2+1..K2-1) of an R2C output grid from Hermitian symmetry
+cudaError_t launch_expand(fhs_problem *p, float2 *grid, cudaStream_t s);
 cudaError_t launch_degrid(fhs_problem *p, const float2 *grid, float2 *vis_sorted, cudaStream_t s);
 // test aid: a bounded wait on an mbarrier nothing arrives at, which records a timeout in p->dev_err
 cudaError_t launch_unsatisfied_wait(fhs_problem *p, int max_polls, cudaStream_t s);
 // fixed: dense bins accumulate their window in 32-bit fixed point (see k_binned.cu); false keeps
 // FP32 atomics (the gridding of the data reduction, whose faint cells are weighted up by Lambda).
-cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s, bool fixed = true);
-cudaError_t launch_crop(fhs_problem *p, const float2 *grid, float *x, cudaStream_t s);
+// fold: the output grid receives the Hermitian part (g(k) + conj g(-k)) / 2 of the adjoint in its
+// lower half (columns 0..K2/2; the rest untouched), the input of the C2R transform; without fold
+// the full grid g (outputs that stay in the frequency domain).
+cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s, bool fixed, bool fold);
+cudaError_t launch_crop(fhs_problem *p, const float *grid, float *x, cudaStream_t s);
 cudaError_t launch_data_dual(fhs_problem *p, cudaStream_t s);      // dual pre-update + block norms
-cudaError_t launch_data_scatter(fhs_problem *p, cudaStream_t s);   // grid_work += G^H (s_b d)
-// fixed: as for launch_grid; the passes of the data reduction use false.
-cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, cudaStream_t s, bool fixed);
+cudaError_t launch_data_scatter(fhs_problem *p, cudaStream_t s);   // grid_work += G^H (s_b d), folded
+// fixed, fold: as for launch_grid; the passes of the data reduction use fixed = false.
+cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, cudaStream_t s, bool fixed,
+                          bool fold);
 // One Lanczos step after y = A v: y <- w, vprev <- v_{j+1}; alpha_j[l] and
 // nb2_j[L + l] (= beta_{j+1}^2) accumulate, nb2_j[l] = beta_j^2 is read.
 cudaError_t launch_lanczos_step(fhs_problem *p, float *y, float *vprev, const float *v, double *alpha_j,

@@ -27,6 +27,24 @@ __device__ __forceinline__ void red_add_f2(float2 *addr, float2 v) {
     atomicAdd(addr, v);   // sm_90+: vector float2 reduction (red.global.add.v2.f32)
 }
 
+// grid(k1, k2) += c.  fold: the grid holds, in columns 0..K2/2, the Hermitian
+// part h(k) = (g(k) + conj g(-k)) / 2 of the sum g, which is what the C2R
+// transform needs for Re F^H g: c adds c / 2 at k when k2 <= K2/2 and
+// conj(c) / 2 at -k when -k2 mod K2 <= K2/2 (both for k2 = 0 and k2 = K2/2).
+__device__ __forceinline__ void red_grid(float2 *__restrict__ gb, int k1, int k2, int K1, int K2, float re,
+                                         float im, bool fold) {
+    if (!fold) {
+        red_add_f2(gb + (long long)k1 * K2 + k2, make_float2(re, im));
+        return;
+    }
+    const int h = K2 >> 1;
+    if (k2 <= h) red_add_f2(gb + (long long)k1 * K2 + k2, make_float2(0.5f * re, 0.5f * im));
+    if (k2 == 0 || k2 >= h) {
+        const int m1 = k1 ? K1 - k1 : 0, m2 = k2 ? K2 - k2 : 0;
+        red_add_f2(gb + (long long)m1 * K2 + m2, make_float2(0.5f * re, -0.5f * im));
+    }
+}
+
 // The data term of one PDFB iteration (Eq. 2) in two passes over G:
 //   dual pass      phi  = G_m . Xhat                    (gather from the forward grid)
 //                  d_m  = s_b d_m + sigma2 (phi - y_m)  (= z - sigma2 y, z = v + sigma2 Phi xbar)
@@ -122,7 +140,8 @@ constexpr int kFixBits = 22;                     // contributions are scaled bel
 // 32-bit words: integers in fixed point, floats otherwise.
 template <bool DENSE, bool FIXED>
 __device__ __forceinline__ void scatter_cell(int *s_win, int ib, float2 *__restrict__ gb,
-                                             long long gidx, float g1x, float g1y, float er, float ei) {
+                                             int gk1, int gk2, int K1, int K2, bool fold, float g1x, float g1y,
+                                             float er, float ei) {
     if (DENSE && FIXED) {
         const float re = fmaf(g1x, er, fmaf(g1y, ei, kFixMagic));
         const float im = fmaf(g1x, ei, fmaf(-g1y, er, kFixMagic));
@@ -135,7 +154,7 @@ __device__ __forceinline__ void scatter_cell(int *s_win, int ib, float2 *__restr
             atomicAdd(s_re + ib, pr);
             atomicAdd(s_re + kWin * kAdjS + ib, pi);
         } else {
-            red_add_f2(gb + gidx, make_float2(pr, pi));
+            red_grid(gb, gk1, gk2, K1, K2, pr, pi, fold);
         }
     }
 }
@@ -144,7 +163,8 @@ __device__ __forceinline__ void scatter_cell(int *s_win, int ib, float2 *__restr
 // point here: one rounding).
 template <bool DENSE, bool FIXED>
 __device__ __forceinline__ void scatter_value(int *s_win, int ib, float2 *__restrict__ gb,
-                                              long long gidx, float pr, float pi, float fs) {
+                                              int gk1, int gk2, int K1, int K2, bool fold, float pr, float pi,
+                                              float fs) {
     if (DENSE && FIXED) {
         const float re = fmaf(pr, fs, kFixMagic), im = fmaf(pi, fs, kFixMagic);
         atomicAdd(s_win + ib, int(__float_as_uint(re) - kFixMagicBits));
@@ -154,14 +174,15 @@ __device__ __forceinline__ void scatter_value(int *s_win, int ib, float2 *__rest
         atomicAdd(s_re + ib, pr);
         atomicAdd(s_re + kWin * kAdjS + ib, pi);
     } else {
-        red_add_f2(gb + gidx, make_float2(pr, pi));
+        red_grid(gb, gk1, gk2, K1, K2, pr, pi, fold);
     }
 }
 
 template <bool DENSE, bool FIXED>
 __device__ __forceinline__ void scatter_rows(int i0, int nv, int lane, const int2 *s_meta, const int *s_off,
                                              const float2 *s_d, const float2 *__restrict__ fbin, int *s_win,
-                                             int wy0, int wx0, float2 *__restrict__ gb, int K1, int K2, float fs) {
+                                             int wy0, int wx0, float2 *__restrict__ gb, int K1, int K2, float fs,
+                                             bool fold) {
     constexpr unsigned FULL = 0xffffffffu;
     float2 fac = make_float2(0.f, 0.f);
     if (i0 < nv) fac = load_factors(fbin + s_off[i0], s_meta[i0].y, lane);
@@ -196,13 +217,13 @@ __device__ __forceinline__ void scatter_rows(int i0, int nv, int lane, const int
                 const int t1 = 4 * k + g;
                 const float g1x = __shfl_sync(FULL, fac.x, t1), g1y = __shfl_sync(FULL, fac.y, t1);
                 if ((DENSE && FIXED) || (cin && t1 < T)) {   // fixed point: the other cells add 0
-                    long long gidx = 0;
+                    int kk = 0;
                     if (!DENSE) {
-                        int kk = c1 + t1;
+                        kk = c1 + t1;
                         kk -= (kk >= K1) ? K1 : 0;
-                        gidx = (long long)kk * K2 + k2;
                     }
-                    scatter_cell<DENSE, FIXED>(s_win, ib + 4 * k * kAdjS, gb, gidx, g1x, g1y, er, ei);
+                    scatter_cell<DENSE, FIXED>(s_win, ib + 4 * k * kAdjS, gb, kk, k2, K1, K2, fold, g1x, g1y, er,
+                                               ei);
                 }
             }
         } else {
@@ -230,13 +251,13 @@ __device__ __forceinline__ void scatter_rows(int i0, int nv, int lane, const int
                 const int t1 = dt + 2 * half;
                 const float g1x = __shfl_sync(FULL, fac.x, t1), g1y = __shfl_sync(FULL, fac.y, t1);
                 if ((DENSE && FIXED) || (cin && t1 < T)) {   // fixed point: the other cells add 0
-                    long long gidx = 0;
+                    int kk = 0;
                     if (!DENSE) {
-                        int kk = c1 + t1;
+                        kk = c1 + t1;
                         kk -= (kk >= K1) ? K1 : 0;
-                        gidx = (long long)kk * K2 + k2;
                     }
-                    scatter_cell<DENSE, FIXED>(s_win, ib + dt * kAdjS, gb, gidx, g1x, g1y, er, ei);
+                    scatter_cell<DENSE, FIXED>(s_win, ib + dt * kAdjS, gb, kk, k2, K1, K2, fold, g1x, g1y, er,
+                                               ei);
                 }
             }
         }
@@ -255,7 +276,8 @@ __device__ __forceinline__ void scatter_rows(int i0, int nv, int lane, const int
 template <bool DENSE, bool FIXED>
 __device__ __forceinline__ void scatter_pairs(int i0, int nv, int lane, const int2 *s_meta, const int *s_off,
                                               const float2 *s_d, const float2 *__restrict__ fbin, int *s_win,
-                                              int wy0, int wx0, float2 *__restrict__ gb, int K1, int K2, float fs) {
+                                              int wy0, int wx0, float2 *__restrict__ gb, int K1, int K2, float fs,
+                                              bool fold) {
     constexpr unsigned FULL = 0xffffffffu;
     const int v = lane >> 4, g = (lane >> 3) & 1, col = lane & 7, hi = g;
     auto load = [&](int r) -> float2 {
@@ -303,13 +325,13 @@ __device__ __forceinline__ void scatter_pairs(int i0, int nv, int lane, const in
             const int t1 = 2 * k + g;
             const float g1x = __shfl_sync(FULL, fac.x, 16 * v + t1), g1y = __shfl_sync(FULL, fac.y, 16 * v + t1);
             if ((DENSE && FIXED) || (cin && t1 < T)) {   // fixed point: the other cells add 0
-                long long gidx = 0;
+                int kk = 0;
                 if (!DENSE) {
-                    int kk = c1 + t1;
+                    kk = c1 + t1;
                     kk -= (kk >= K1) ? K1 : 0;
-                    gidx = (long long)kk * K2 + k2;
                 }
-                scatter_cell<DENSE, FIXED>(s_win, ib + 2 * k * kAdjS, gb, gidx, g1x, g1y, er, ei);
+                scatter_cell<DENSE, FIXED>(s_win, ib + 2 * k * kAdjS, gb, kk, k2, K1, K2, fold, g1x, g1y, er,
+                                           ei);
             }
         }
         fac = fnx;
@@ -325,7 +347,7 @@ __device__ __forceinline__ void scatter_rows_rank(int i0, int nv, int lane, int 
                                                   const int *s_off, const float2 *s_d,
                                                   const float2 *__restrict__ fbin, int *s_win,
                                                   int wy0, int wx0, float2 *__restrict__ gb, int K1, int K2,
-                                                  float fs) {
+                                                  float fs, bool fold) {
     constexpr unsigned FULL = 0xffffffffu;
     const int half = lane >> 4, col = lane & 15;
     for (int i = i0; i < nv; i += kWarps) {
@@ -370,14 +392,13 @@ __device__ __forceinline__ void scatter_rows_rank(int i0, int nv, int lane, int 
             if (k >= n) break;
             const int t1 = 4 * (k >> 1) + (k & 1) + 2 * half;
             if ((DENSE && FIXED) || (cin && t1 < T)) {   // fixed point: the other cells add 0
-                long long gidx = 0;
+                int kk = 0;
                 if (!DENSE) {
-                    int kk = c1 + t1;
+                    kk = c1 + t1;
                     kk -= (kk >= K1) ? K1 : 0;
-                    gidx = (long long)kk * K2 + k2;
                 }
                 const int ib = DENSE ? (c1 - wy0 + t1) * kAdjS + (c2 - wx0 + col) : 0;
-                scatter_value<DENSE, FIXED>(s_win, ib, gb, gidx, accr[k], acci[k], fs);
+                scatter_value<DENSE, FIXED>(s_win, ib, gb, kk, k2, K1, K2, fold, accr[k], acci[k], fs);
             }
         }
     }
@@ -635,7 +656,7 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
     const float *__restrict__ blk_scale, double *__restrict__ blk_norm2, const float2 *__restrict__ grid,
     float2 *__restrict__ grid_out, long long K, int K1, int K2, float sigma2, int R_,
     const __grid_constant__ CUtensorMap tmap, int use_tma, const float *__restrict__ gmax, int allow_fixed,
-    int *__restrict__ err) {
+    int fold_out, int *__restrict__ err) {
     const int R = MULTI ? R_ : 1;
     __shared__ alignas(128) float2 s_grid[kWin * kWinP];
     __shared__ alignas(8) uint64_t s_bar;
@@ -759,6 +780,7 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
     // phase 2: scatters of conj(G_i) s_d[i], one row per warp
     bool fixed = false;
     float fs = 1.f, finv = 1.f;
+    const bool fold = fold_out != 0;
     if (MODE == kScatter || MODE == kNormal) {
         if (MODE == kNormal) __syncthreads();        // s_d holds the gathered values
         // fixed point in the scatter when the caller allows it (Phi^H, the data term's scatter pass,
@@ -792,31 +814,31 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
         if (MULTI) {
             if (dense && fixed)
                 scatter_rows_rank<true, true>(warp, nv, lane, R, s_meta, s_off, s_d, fbin, s_win, wy0, wx0, gb,
-                                              K1, K2, fs);
+                                              K1, K2, fs, fold);
             else if (dense)
                 scatter_rows_rank<true, false>(warp, nv, lane, R, s_meta, s_off, s_d, fbin, s_win, wy0, wx0, gb,
-                                               K1, K2, fs);
+                                               K1, K2, fs, fold);
             else
                 scatter_rows_rank<false, false>(warp, nv, lane, R, s_meta, s_off, s_d, fbin, s_win, wy0, wx0, gb,
-                                                K1, K2, fs);
+                                                K1, K2, fs, fold);
         } else if (s_tmax <= 8) {
             // every row of the bin has at most 8 taps: two rows per warp step
             if (dense && fixed)
                 scatter_pairs<true, true>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_win, wy0, wx0, gb, K1, K2,
-                                          fs);
+                                          fs, fold);
             else if (dense)
                 scatter_pairs<true, false>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_win, wy0, wx0, gb, K1, K2,
-                                           fs);
+                                           fs, fold);
             else
                 scatter_pairs<false, false>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_win, wy0, wx0, gb, K1,
-                                            K2, fs);
+                                            K2, fs, fold);
         } else if (dense && fixed)
-            scatter_rows<true, true>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_win, wy0, wx0, gb, K1, K2, fs);
+            scatter_rows<true, true>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_win, wy0, wx0, gb, K1, K2, fs, fold);
         else if (dense)
-            scatter_rows<true, false>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_win, wy0, wx0, gb, K1, K2, fs);
+            scatter_rows<true, false>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_win, wy0, wx0, gb, K1, K2, fs, fold);
         else
             scatter_rows<false, false>(warp, nv, lane, s_meta, s_off, s_d, fbin, s_win, wy0, wx0, gb, K1, K2,
-                                       fs);
+                                       fs, fold);
     }
     if (MODE != kDual) {
         if ((MODE == kScatter || MODE == kNormal) && dense) {
@@ -839,7 +861,7 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
                     while (k1 >= K1) k1 -= K1;
                     int k2 = wx0 + c;
                     while (k2 >= K2) k2 -= K2;
-                    red_add_f2(gb + (long long)k1 * K2 + k2, make_float2(re, im));
+                    red_grid(gb, k1, k2, K1, K2, re, im, fold);
                 }
             }
         }
@@ -926,13 +948,13 @@ static WindowMap window_map(const fhs_problem *p, const float2 *grid) {
 template <int MODE>
 cudaError_t launch_pass(fhs_problem *p, const float2 *y, float2 *dvis, const float *blk_scale, double *blk_norm2,
                         const float2 *grid, float2 *grid_out, float sigma2, const WindowMap &tm, int allow_fixed,
-                        cudaStream_t s) {
+                        int fold, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
     (p->rank > 1 ? degrid_grid_binned_kernel<MODE, true> : degrid_grid_binned_kernel<MODE, false>)<<<p->n_bin, 256, 0, s>>>(
         p->meta, p->fptr, p->gfac, y, dvis, p->bin_slots, p->bin_fbase, p->piece_start, p->piece_len, p->piece_blk,
         p->bin_chan,
         p->bin_tile, p->ntx, p->B, blk_scale, blk_norm2, grid, grid_out, p->K, p->K1, p->K2, sigma2, p->rank, tm.map,
-        tm.ok, p->gmax, allow_fixed, p->dev_err);
+        tm.ok, p->gmax, allow_fixed, fold, p->dev_err);
     p->n_launch += 1;
     return cudaGetLastError();
 }
@@ -940,18 +962,20 @@ cudaError_t launch_pass(fhs_problem *p, const float2 *y, float2 *dvis, const flo
 cudaError_t launch_degrid(fhs_problem *p, const float2 *grid, float2 *vis_sorted, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
     return launch_pass<kGather>(p, nullptr, vis_sorted, nullptr, nullptr, grid, nullptr, 0.f, window_map(p, grid), 0,
-                                s);
+                                0, s);
 }
 
-cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s, bool fixed) {
+cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s, bool fixed,
+                        bool fold) {
     return launch_pass<kScatter>(p, nullptr, const_cast<float2 *>(vis_sorted), nullptr, nullptr, nullptr, grid, 0.f,
-                                 WindowMap{}, fixed ? 1 : 0, s);
+                                 WindowMap{}, fixed ? 1 : 0, fold ? 1 : 0, s);
 }
 
-cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, cudaStream_t s, bool fixed) {
+cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, cudaStream_t s, bool fixed,
+                          bool fold) {
     if (p->n_bin == 0) return cudaSuccess;
     return launch_pass<kNormal>(p, nullptr, nullptr, nullptr, nullptr, grid, grid_out, 0.f, window_map(p, grid),
-                                fixed ? 1 : 0, s);
+                                fixed ? 1 : 0, fold ? 1 : 0, s);
 }
 
 // The data term in two passes: the dual pre-update with the block norms
@@ -961,12 +985,12 @@ cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, 
 cudaError_t launch_data_dual(fhs_problem *p, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
     return launch_pass<kDual>(p, p->y, p->dvis, p->blk_scale, p->blk_norm2, p->grid_work, nullptr, float(p->sigma2),
-                              window_map(p, p->grid_work), 0, s);
+                              window_map(p, p->grid_work), 0, 0, s);
 }
 
 cudaError_t launch_data_scatter(fhs_problem *p, cudaStream_t s) {
     return launch_pass<kScatter>(p, nullptr, p->dvis, p->blk_scale, nullptr, nullptr, p->grid_work, 0.f, WindowMap{},
-                                 1, s);
+                                 1, 1, s);
 }
 
 }  // namespace fhs

@@ -169,8 +169,8 @@ __global__ void block_finalize_kernel(double *blk_norm2, const double *eps, floa
     blk_norm2[s] = 0.0;
 }
 
-// Z: grid[(n mod K)] = x_n s1(n1) s2(n2) (zero cells elsewhere are left as is).
-__global__ void zpad_kernel(const float *__restrict__ x, float2 *__restrict__ grid, const float *__restrict__ s1,
+// Z: grid[(n mod K)] = x_n s1(n1) s2(n2), a real grid (zero cells elsewhere are left as is).
+__global__ void zpad_kernel(const float *__restrict__ x, float *__restrict__ grid, const float *__restrict__ s1,
                             const float *__restrict__ s2, int ny, int nx, int K1, int K2, long long K) {
     const int l = blockIdx.y;
     const long long N = (long long)ny * nx;
@@ -178,12 +178,12 @@ __global__ void zpad_kernel(const float *__restrict__ x, float2 *__restrict__ gr
         const int i1 = int(p) / nx, i2 = int(p) - i1 * nx;      // 32-bit division: images hold < 2^31 pixels
         int k1 = i1 - ny / 2; k1 += (k1 < 0) ? K1 : 0;
         int k2 = i2 - nx / 2; k2 += (k2 < 0) ? K2 : 0;
-        grid[(long long)l * K + (long long)k1 * K2 + k2] = make_float2(x[(long long)l * N + p] * s1[i1] * s2[i2], 0.f);
+        grid[(long long)l * K + (long long)k1 * K2 + k2] = x[(long long)l * N + p] * s1[i1] * s2[i2];
     }
 }
 
-// Z^T, real part: x_n = Re(grid[(n mod K)]) s1(n1) s2(n2).
-__global__ void crop_kernel(const float2 *__restrict__ grid, float *__restrict__ x, const float *__restrict__ s1,
+// Z^T of a real grid (the C2R output, Re F^H g): x_n = grid[(n mod K)] s1(n1) s2(n2).
+__global__ void crop_kernel(const float *__restrict__ grid, float *__restrict__ x, const float *__restrict__ s1,
                             const float *__restrict__ s2, int ny, int nx, int K1, int K2, long long K) {
     const int l = blockIdx.y;
     const long long N = (long long)ny * nx;
@@ -191,7 +191,25 @@ __global__ void crop_kernel(const float2 *__restrict__ grid, float *__restrict__
         const int i1 = int(p) / nx, i2 = int(p) - i1 * nx;      // 32-bit division: images hold < 2^31 pixels
         int k1 = i1 - ny / 2; k1 += (k1 < 0) ? K1 : 0;
         int k2 = i2 - nx / 2; k2 += (k2 < 0) ? K2 : 0;
-        x[(long long)l * N + p] = grid[(long long)l * K + (long long)k1 * K2 + k2].x * s1[i1] * s2[i2];
+        x[(long long)l * N + p] = grid[(long long)l * K + (long long)k1 * K2 + k2] * s1[i1] * s2[i2];
+    }
+}
+
+// The spectrum of a real grid is Hermitian: X(k) = conj X(-k).  The R2C
+// transform writes columns 0..K2/2 of each row; this fills columns
+// K2/2+1..K2-1 from them, X[k1][k2] = conj X[(K1 - k1) mod K1][K2 - k2], one
+// row per CTA step (reads and writes are contiguous, the reads in reverse).
+__global__ void expand_kernel(float2 *__restrict__ grid, int K1, int K2, int rows) {
+    const int h = K2 >> 1;
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int l = r / K1, k1 = r - l * K1;
+        const int m1 = k1 ? K1 - k1 : 0;
+        float2 *dst = grid + (long long)r * K2;
+        const float2 *src = grid + ((long long)l * K1 + m1) * K2;
+        for (int k2 = h + 1 + threadIdx.x; k2 < K2; k2 += blockDim.x) {
+            const float2 v = src[K2 - k2];
+            dst[k2] = make_float2(v.x, -v.y);
+        }
     }
 }
 
@@ -376,16 +394,24 @@ cudaError_t launch_build_g(fhs_problem *p, const double2 *kap, const short *plan
     return cudaGetLastError();
 }
 
-cudaError_t launch_zpad(fhs_problem *p, const float *x, float2 *grid, cudaStream_t s) {
+cudaError_t launch_zpad(fhs_problem *p, const float *x, float *grid, cudaStream_t s) {
     dim3 g(grid_for(p->N, 256, 512), p->L);
     zpad_kernel<<<g, 256, 0, s>>>(x, grid, p->s1, p->s2, p->ny, p->nx, p->K1, p->K2, p->K);
     p->n_launch += 1;
     return cudaGetLastError();
 }
 
-cudaError_t launch_crop(fhs_problem *p, const float2 *grid, float *x, cudaStream_t s) {
+cudaError_t launch_crop(fhs_problem *p, const float *grid, float *x, cudaStream_t s) {
     dim3 g(grid_for(p->N, 256, 512), p->L);
     crop_kernel<<<g, 256, 0, s>>>(grid, x, p->s1, p->s2, p->ny, p->nx, p->K1, p->K2, p->K);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expand(fhs_problem *p, float2 *grid, cudaStream_t s) {
+    const long long rows = (long long)p->L * p->K1;
+    if (rows == 0 || p->K2 < 4) return cudaSuccess;
+    expand_kernel<<<grid_for(rows, 1, 152 * 16), 256, 0, s>>>(grid, p->K1, p->K2, int(rows));
     p->n_launch += 1;
     return cudaGetLastError();
 }

@@ -2,6 +2,7 @@
 // the three adjoint terms and the zero-padding of the next forward FFT:
 //
 //   a    = Re(Z^T F^H g_data) + A_sara + sum_{q covering n} P_q(n)
+//          (Re F^H g_data is the C2R transform of the folded adjoint grid)
 //   x+   = max(0, x - tau a)             (non-negativity, Eq. 2)
 //   xbar = 2 x+ - x,   grid_in[(n mod K)] = xbar s1 s2   (Z for the next F)
 //   ||x+ - x||^2 and ||x+||^2 in FP64 for the relative-change test.
@@ -13,7 +14,7 @@ namespace {
 
 __global__ void __launch_bounds__(256) primal_kernel(
     float *__restrict__ X, float *__restrict__ Xbar, const float *__restrict__ A_sara,
-    const float2 *__restrict__ grid_adj, float2 *__restrict__ grid_in, const float *__restrict__ s1,
+    const float *__restrict__ grid_adj, float *__restrict__ grid_in, const float *__restrict__ s1,
     const float *__restrict__ s2, const float *__restrict__ P, const int4 *__restrict__ facets,
     const long long *__restrict__ nuc_off, const short *__restrict__ rf, const short *__restrict__ rc,
     const short *__restrict__ cf, const short *__restrict__ cc, int qx, int Q, int C, int ny, int nx, int K1,
@@ -25,8 +26,8 @@ __global__ void __launch_bounds__(256) primal_kernel(
     // channel bases once; row offsets hoisted out of the column loop
     float *Xl = X + (long long)l * N, *Xbl = Xbar + (long long)l * N;
     const float *Al = A_sara + (long long)l * N;
-    const float2 *gal = grid_adj + (long long)l * K;
-    float2 *gil = grid_in + (long long)l * K;
+    const float *gal = grid_adj + (long long)l * K;
+    float *gil = grid_in + (long long)l * K;
     // compensated FP32 per thread, FP64 across threads
     float num = 0.f, cnum = 0.f, den = 0.f, cden = 0.f;
     // one image row per CTA step (row-uniform terms hoisted), columns over the threads
@@ -40,7 +41,7 @@ __global__ void __launch_bounds__(256) primal_kernel(
             int k2 = i2 - nx / 2;
             k2 += (k2 < 0) ? K2 : 0;
             const float sc = s1r * s2[i2];
-            float a = gal[grow + k2].x * sc;
+            float a = gal[grow + k2] * sc;
             const long long o = irow + i2;
             if (use_sara) a += Al[o];
             if (use_nuc) {
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(256) primal_kernel(
             const float xb = 2.f * xp - x;
             Xl[o] = xp;
             Xbl[o] = xb;
-            gil[grow + k2] = make_float2(xb * sc, 0.f);
+            gil[grow + k2] = xb * sc;
             const float dx = xp - x;
             {
                 const float yv = fmaf(dx, dx, -cnum), t = num + yv;
@@ -95,7 +96,7 @@ cudaError_t launch_primal(fhs_problem *p, cudaStream_t s) {
     const bool use_sara = p->prm.mu > 0.0;
     const bool use_nuc = p->prm.mu_bar > 0.0;
     primal_kernel<<<dim3(int(g), p->L), 256, 0, s>>>(
-        p->X, p->Xbar, p->A_sara, p->grid_work, p->grid_in, p->s1, p->s2, p->P, p->d_facets, p->nuc_off,
+        p->X, p->Xbar, p->A_sara, p->adj_real, p->grid_in, p->s1, p->s2, p->P, p->d_facets, p->nuc_off,
         p->cov_row_first, p->cov_row_cnt, p->cov_col_first, p->cov_col_cnt, p->prm.qx, p->Q, p->C, p->ny, p->nx,
         p->K1, p->K2, p->K, float(p->tau), use_sara, use_nuc, p->red);
     p->n_launch += 1;
