@@ -375,27 +375,25 @@ fhs_status check_params(const fhs_params *q) {
     return FHS_OK;
 }
 
-// F of a real zero-padded grid: R2C into columns 0..K2/2 of `out` (row stride K2), then the
-// other columns by Hermitian symmetry, so that the passes over G read a full spectrum.
+// F of a real zero-padded grid: R2C into the half grid `out` (columns 0..K2/2, row stride HS);
+// the passes over G read the other columns as X(k) = conj X(-k).
 fhs_status fft_forward(fhs_problem *p, const float *in, float2 *out, cudaStream_t s) {
     CUFFT(cufftSetStream(p->plan_r2c, s));
     CUFFT(cufftExecR2C(p->plan_r2c, const_cast<cufftReal *>(in), reinterpret_cast<cufftComplex *>(out)));
-    CU(launch_expand(p, out, s));
     return FHS_OK;
 }
 
-// Re F^H g from the Hermitian part of g held in columns 0..K2/2 of `in` (the folded adjoint):
-// C2R into the real grid `out`.  The transform overwrites `in`.
+// Re F^H g from the half grid `in` holding the Hermitian part of g (the folded adjoint): C2R into
+// the real grid `out`.  The transform overwrites `in`.
 fhs_status fft_inverse(fhs_problem *p, float2 *in, float *out, cudaStream_t s) {
     CUFFT(cufftSetStream(p->plan_c2r, s));
     CUFFT(cufftExecC2R(p->plan_c2r, reinterpret_cast<cufftComplex *>(in), reinterpret_cast<cufftReal *>(out)));
     return FHS_OK;
 }
 
-// Zeroes the columns 0..K2/2 of every row of L grids: all that a folded scatter writes.
+// Zeroes L half grids (the target of a folded scatter).
 fhs_status zero_half(fhs_problem *p, float2 *grid, cudaStream_t s) {
-    CU(cudaMemset2DAsync(grid, sizeof(float2) * p->K2, 0, sizeof(float2) * (p->K2 / 2 + 1),
-                         (size_t)p->K1 * p->L, s));
+    CU(cudaMemsetAsync(grid, 0, sizeof(float2) * p->KH * p->L, s));
     return FHS_OK;
 }
 
@@ -435,11 +433,11 @@ fhs_status apply_normal(fhs_problem *p, const float *v, float *y, cudaStream_t s
     TRY(fft_forward(p, p->grid_in, p->grid_aux, s));
     TRY(zero_half(p, scratch, s));
     if (p->dr) {
-        CU(launch_normal(p, p->grid_aux, p->dr_u, s, false, false));
+        CU(launch_normal(p, p->grid_aux, true, p->dr_u, s, false, false));
         CU(launch_dr_combine(p, p->dr_u, 0.f, 1.f, p->dr_w, s));
-        CU(launch_normal(p, p->dr_w, scratch, s, false, true));
+        CU(launch_normal(p, p->dr_w, false, scratch, s, false, true));
     } else {
-        CU(launch_normal(p, p->grid_aux, scratch, s, true, true));
+        CU(launch_normal(p, p->grid_aux, true, scratch, s, true, true));
     }
     TRY(fft_inverse(p, scratch, p->real_scr, s));
     CU(launch_crop(p, p->real_scr, y, s));
@@ -452,7 +450,7 @@ fhs_status dirty_image(fhs_problem *p, float *x, cudaStream_t s) {
     if (!p->dr) return adjoint_to_image(p, p->y, x, s);
     CU(launch_dr_combine(p, nullptr, 1.f, 0.f, p->dr_w, s));
     TRY(zero_half(p, p->grid_aux, s));
-    CU(launch_normal(p, p->dr_w, p->grid_aux, s, false, true));
+    CU(launch_normal(p, p->dr_w, false, p->grid_aux, s, false, true));
     TRY(fft_inverse(p, p->grid_aux, p->real_scr, s));
     CU(launch_crop(p, p->real_scr, x, s));
     return FHS_OK;
@@ -708,7 +706,7 @@ fhs_status one_iteration(fhs_problem *p, cudaStream_t s) {
     }
     {
         Phase ph(p, s, FHS_PHASE_DEGRID_GRID);
-        if (p->dr) CU(launch_normal(p, p->grid_work, p->dr_u, s, false, false));     // H Xhat
+        if (p->dr) CU(launch_normal(p, p->grid_work, true, p->dr_u, s, false, false));     // H Xhat
         else CU(launch_data_dual(p, s));                               // d, block norms
     }
     if (fork) {
@@ -722,9 +720,10 @@ fhs_status one_iteration(fhs_problem *p, cudaStream_t s) {
             Phase ph(p, s, FHS_PHASE_L2BALL);
             CU(launch_dr_dual(p, s));
             CU(launch_dr_finalize(p, s));
+            TRY(zero_half(p, p->grid_work, s));
         }
         Phase ph(p, s, FHS_PHASE_SCATTER);
-        CU(launch_normal(p, p->dr_w, p->grid_work, s, false, true));
+        CU(launch_normal(p, p->dr_w, false, p->grid_work, s, false, true));
     } else {
         // l2-ball factors, then G^H (s_b d) straight into the channel grids
         {
@@ -817,10 +816,11 @@ fhs_status run_iterations(fhs_problem *p, int n, cudaStream_t s) {
 
 // Work area of the R2C and C2R plans (one shared area: the larger of the two).
 size_t cufft_workspace(int K1, int K2, int L) {
-    int n[2] = {K1, K2}, emb[2] = {K1, K2};
+    const int hs = K2 / 2 + 1;
+    int n[2] = {K1, K2}, emb[2] = {K1, K2}, hemb[2] = {K1, hs};
     size_t wf = 0, wi = 0;
-    if (cufftEstimateMany(2, n, emb, 1, K1 * K2, emb, 1, K1 * K2, CUFFT_R2C, L, &wf) != CUFFT_SUCCESS) wf = 0;
-    if (cufftEstimateMany(2, n, emb, 1, K1 * K2, emb, 1, K1 * K2, CUFFT_C2R, L, &wi) != CUFFT_SUCCESS) wi = 0;
+    if (cufftEstimateMany(2, n, emb, 1, K1 * K2, hemb, 1, K1 * hs, CUFFT_R2C, L, &wf) != CUFFT_SUCCESS) wf = 0;
+    if (cufftEstimateMany(2, n, hemb, 1, K1 * hs, emb, 1, K1 * K2, CUFFT_C2R, L, &wi) != CUFFT_SUCCESS) wi = 0;
     return std::max(wf, wi);
 }
 
@@ -958,6 +958,8 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
     p->ny = q.ny; p->nx = q.nx; p->K1 = 2 * q.ny; p->K2 = 2 * q.nx;
     p->N = (long long)q.ny * q.nx;
     p->K = (long long)p->K1 * p->K2;
+    p->HS = p->K2 / 2 + 1;
+    p->KH = (long long)p->K1 * p->HS;
     p->Mtot = Mtot;
     p->vis_off.assign(vis_offsets, vis_offsets + L + 1);
     p->sigma_l.assign(sigma, sigma + L);
@@ -1227,9 +1229,9 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
         if ((st = guard(upload(p->s2, s2.data(), q.nx, s))) != FHS_OK) return st;
     }
     {
-        // R2C: real [L][K1][K2] -> complex columns 0..K2/2 of [L][K1][K2]; C2R the reverse.  One
-        // work area serves both (they never run at the same time on a problem's streams).
-        int n[2] = {K1, K2}, emb[2] = {K1, K2};
+        // R2C: real [L][K1][K2] -> half grids [L][K1][HS]; C2R the reverse.  One work area serves
+        // both (they never run at the same time on a problem's streams).
+        int n[2] = {K1, K2}, emb[2] = {K1, K2}, hemb[2] = {K1, p->HS};
         size_t ws_f = 0, ws_i = 0;
         if (cufftCreate(&p->plan_r2c) != CUFFT_SUCCESS) return guard(fail(FHS_ERR_CUDA, "cufftCreate failed"));
         if (cufftCreate(&p->plan_c2r) != CUFFT_SUCCESS) {
@@ -1239,9 +1241,9 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
         p->plan_ok = true;
         if (cufftSetAutoAllocation(p->plan_r2c, 0) != CUFFT_SUCCESS ||
             cufftSetAutoAllocation(p->plan_c2r, 0) != CUFFT_SUCCESS ||
-            cufftMakePlanMany(p->plan_r2c, 2, n, emb, 1, int(p->K), emb, 1, int(p->K), CUFFT_R2C, L, &ws_f) !=
+            cufftMakePlanMany(p->plan_r2c, 2, n, emb, 1, int(p->K), hemb, 1, int(p->KH), CUFFT_R2C, L, &ws_f) !=
                 CUFFT_SUCCESS ||
-            cufftMakePlanMany(p->plan_c2r, 2, n, emb, 1, int(p->K), emb, 1, int(p->K), CUFFT_C2R, L, &ws_i) !=
+            cufftMakePlanMany(p->plan_c2r, 2, n, hemb, 1, int(p->KH), emb, 1, int(p->K), CUFFT_C2R, L, &ws_i) !=
                 CUFFT_SUCCESS)
             return guard(fail(FHS_ERR_CUDA, "cuFFT plan set-up failed"));
         const size_t ws = std::max<size_t>(std::max(ws_f, ws_i), 1);
@@ -1253,9 +1255,9 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
             return guard(fail(FHS_ERR_CUDA, "cufftSetWorkArea failed"));
     }
     if ((st = guard(dev_alloc(p, &p->grid_in, p->K * L))) != FHS_OK) return st;
-    if ((st = guard(dev_alloc(p, &p->grid_work, p->K * L))) != FHS_OK) return st;
-    if ((st = guard(dev_alloc(p, &p->grid_aux, p->K * L))) != FHS_OK) return st;
-    if ((st = guard(dev_alloc(p, &p->grid_scr, p->K * L))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->grid_work, p->KH * L))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->grid_aux, p->KH * L))) != FHS_OK) return st;
+    if ((st = guard(dev_alloc(p, &p->grid_scr, p->KH * L))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->adj_real, p->K * L))) != FHS_OK) return st;
     if ((st = guard(dev_alloc(p, &p->real_scr, p->K * L, false))) != FHS_OK) return st;
     if (p->dr) {
@@ -1510,7 +1512,8 @@ fhs_status fhs_estimate_bytes(const fhs_params *params, const double *w, int64_t
     const long long npiece = nbin * std::min<long long>(B <= kBinMaxPieces ? B : 1, kBinMaxPieces);
     r += 16 * nbin + 16 * npiece + 8 * (nchunk + 1) + 4 * nchunk;
     r += 4 * (q.ny + q.nx);                                          // Z scaling
-    r += 8 * K * L * 3 + 4 * K * L * 3;                              // complex grids, real grids
+    const long long KH = (long long)(2 * q.ny) * (q.nx + 1);         // half-grid cells: K1 x HS
+    r += 8 * KH * L * 3 + 4 * K * L * 3;                             // half grids, real grids
     r += 4 * N * L * 3 + 16 + 16 * L + 4 * L;                        // images, reductions, PSF factors
     r += 4 * c.n_coef * L * 2 + 4 * c.n_tmp * L + 4 * c.n_coef * C;  // SARA
     const long long ne = Lc + (Lc & 1);
@@ -1635,12 +1638,12 @@ fhs_status fhs_residual(fhs_problem *p, const float *x_dev, float *r_dev, void *
         if (x_dev) {
             CU(launch_zpad(p, x_dev, p->grid_in, s));
             TRY(fft_forward(p, p->grid_in, p->grid_aux, s));
-            CU(launch_normal(p, p->grid_aux, p->dr_u, s, false, false));
+            CU(launch_normal(p, p->grid_aux, true, p->dr_u, s, false, false));
             u = p->dr_u;
         }
         CU(launch_dr_combine(p, u, 1.f, -1.f, p->dr_w, s));
         TRY(zero_half(p, p->grid_aux, s));
-        CU(launch_normal(p, p->dr_w, p->grid_aux, s, false, true));
+        CU(launch_normal(p, p->dr_w, false, p->grid_aux, s, false, true));
         TRY(fft_inverse(p, p->grid_aux, p->real_scr, s));
         CU(launch_crop(p, p->real_scr, r_dev, s));
         CU(launch_chan_scale(p, r_dev, p->eta, s));
@@ -1671,7 +1674,7 @@ fhs_status fhs_noise_from_model(fhs_problem *p, const float *x0_dev, int32_t app
         if (p->dr) {
             CU(launch_zpad(p, x0_dev, p->grid_in, s));
             TRY(fft_forward(p, p->grid_in, p->grid_aux, s));
-            CU(launch_normal(p, p->grid_aux, p->dr_u, s, false, false));
+            CU(launch_normal(p, p->grid_aux, true, p->dr_u, s, false, false));
             CU(launch_dr_resid_norm(p, st, s));
         } else {
             TRY(forward_from_image(p, x0_dev, p->vis_tmp, s));
@@ -1901,7 +1904,7 @@ fhs_status fhs_set_state(fhs_problem *p, int32_t part, const float *src, void *s
                 CU(cudaMemcpyAsync(p->dr_v, src, b, cudaMemcpyDeviceToDevice, s));
                 CU(launch_dr_weight(p, s));
                 TRY(zero_half(p, p->grid_work, s));
-                CU(launch_normal(p, p->dr_w, p->grid_work, s, false, true));
+                CU(launch_normal(p, p->dr_w, false, p->grid_work, s, false, true));
                 TRY(fft_inverse(p, p->grid_work, p->adj_real, s));
                 CU(cudaStreamSynchronize(s));
                 break;
@@ -1972,9 +1975,9 @@ fhs_status fhs_autotune_bins(fhs_problem *p, void *stream, int32_t *dense_min_ou
     };
     auto time_bins = [&](const DevBins &b, float &ms) -> fhs_status {
         use_bins(p, b);
-        CU(launch_normal(p, p->grid_aux, p->grid_scr, s, !p->dr, true));    // warm-up
+        CU(launch_normal(p, p->grid_aux, true, p->grid_scr, s, !p->dr, true));    // warm-up
         CU(cudaEventRecord(e0, s));
-        for (int r = 0; r < 3; ++r) CU(launch_normal(p, p->grid_aux, p->grid_scr, s, !p->dr, true));
+        for (int r = 0; r < 3; ++r) CU(launch_normal(p, p->grid_aux, true, p->grid_scr, s, !p->dr, true));
         CU(cudaEventRecord(e1, s));
         CU(cudaEventSynchronize(e1));
         CU(cudaEventElapsedTime(&ms, e0, e1));
@@ -2039,7 +2042,7 @@ fhs_status fhs_autotune_bins(fhs_problem *p, void *stream, int32_t *dense_min_ou
         cudaGraphExecDestroy(p->gexec);
         p->gexec = nullptr;
     }
-    CU(cudaMemsetAsync(p->grid_scr, 0, sizeof(float2) * p->K * p->L, s));
+    TRY(zero_half(p, p->grid_scr, s));
     CU(cudaMemsetAsync(p->coef_tmp, 0, sizeof(float) * LN, s));
     CU(cudaStreamSynchronize(s));
     if (rs != FHS_OK) return rs;

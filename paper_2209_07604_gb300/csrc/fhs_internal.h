@@ -112,16 +112,19 @@ struct fhs_problem {
     long long *chunk_start = nullptr;         // [n_chunk+1]
     int *chunk_seg = nullptr;                 // [n_chunk]
     float *s1 = nullptr, *s2 = nullptr;       // Z scaling per axis
-    // F on real images: R2C of the zero-padded image into the lower half of a full grid (columns
-    // 0..K2/2, row stride K2), the upper half filled by Hermitian symmetry; F^H through C2R from
-    // the lower half of a grid that holds the Hermitian part of the adjoint (the scatter folds)
+    // F on real images: R2C of the zero-padded image into a half grid (columns 0..K2/2 of each
+    // row, row stride HS), which the passes over G read with X(k) = conj X(-k) for the other
+    // columns; F^H through C2R from a half grid holding the Hermitian part of the adjoint (the
+    // scatter folds it there)
+    int HS = 0;                               // half-grid row stride: K2/2 + 1
+    long long KH = 0;                         // half-grid cells per channel, K1 * HS
     cufftHandle plan_r2c = 0, plan_c2r = 0;
     bool plan_ok = false;
     void *fft_ws = nullptr;                   // work area shared by both plans
     float *grid_in = nullptr;                 // [L][K] real zero-padded input (zeros persist)
-    float2 *grid_work = nullptr;              // [L][K] forward spectrum / folded data adjoint grid
-    float2 *grid_scr = nullptr;               // [L][K] scratch output grids
-    float2 *grid_aux = nullptr;               // [L][K] scratch for measure/adjoint
+    float2 *grid_work = nullptr;              // [L][KH] forward spectrum / folded data adjoint
+    float2 *grid_scr = nullptr;               // [L][KH] scratch output grids
+    float2 *grid_aux = nullptr;               // [L][KH] scratch for measure/adjoint
     float *adj_real = nullptr;                // [L][K] F^H of the data adjoint grid (iteration state)
     float *real_scr = nullptr;                // [L][K] F^H output of the other calls
 
@@ -210,23 +213,22 @@ void destroy_on_stream(fhs_problem *p, cudaStream_t s);
 cudaError_t launch_build_g(fhs_problem *p, const double2 *kap, const short *plane, const double2 *wk_table,
                            const double2 *dde, int ext, const double *inv_sigma_seg, cudaStream_t s);
 cudaError_t launch_zpad(fhs_problem *p, const float *x, float *grid, cudaStream_t s);
-// the upper half (columns K2/2+1..K2-1) of an R2C output grid from Hermitian symmetry
-cudaError_t launch_expand(fhs_problem *p, float2 *grid, cudaStream_t s);
 cudaError_t launch_degrid(fhs_problem *p, const float2 *grid, float2 *vis_sorted, cudaStream_t s);
 // test aid: a bounded wait on an mbarrier nothing arrives at, which records a timeout in p->dev_err
 cudaError_t launch_unsatisfied_wait(fhs_problem *p, int max_polls, cudaStream_t s);
 // fixed: dense bins accumulate their window in 32-bit fixed point (see k_binned.cu); false keeps
 // FP32 atomics (the gridding of the data reduction, whose faint cells are weighted up by Lambda).
-// fold: the output grid receives the Hermitian part (g(k) + conj g(-k)) / 2 of the adjoint in its
-// lower half (columns 0..K2/2; the rest untouched), the input of the C2R transform; without fold
-// the full grid g (outputs that stay in the frequency domain).
+// fold: the output is a half grid that receives the Hermitian part (g(k) + conj g(-k)) / 2 of the
+// adjoint, the input of the C2R transform; without fold a full grid receives g (outputs that stay
+// in the frequency domain).  Gathering passes read half grids (forward spectra) unless stated.
 cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s, bool fixed, bool fold);
 cudaError_t launch_crop(fhs_problem *p, const float *grid, float *x, cudaStream_t s);
 cudaError_t launch_data_dual(fhs_problem *p, cudaStream_t s);      // dual pre-update + block norms
 cudaError_t launch_data_scatter(fhs_problem *p, cudaStream_t s);   // grid_work += G^H (s_b d), folded
-// fixed, fold: as for launch_grid; the passes of the data reduction use fixed = false.
-cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, cudaStream_t s, bool fixed,
-                          bool fold);
+// fixed, fold: as for launch_grid; the passes of the data reduction use fixed = false.  in_half:
+// the input is a half grid (a forward spectrum), else a full grid.
+cudaError_t launch_normal(fhs_problem *p, const float2 *grid, bool in_half, float2 *grid_out, cudaStream_t s,
+                          bool fixed, bool fold);
 // One Lanczos step after y = A v: y <- w, vprev <- v_{j+1}; alpha_j[l] and
 // nb2_j[L + l] (= beta_{j+1}^2) accumulate, nb2_j[l] = beta_j^2 is read.
 cudaError_t launch_lanczos_step(fhs_problem *p, float *y, float *vprev, const float *v, double *alpha_j,

@@ -27,22 +27,39 @@ __device__ __forceinline__ void red_add_f2(float2 *addr, float2 v) {
     atomicAdd(addr, v);   // sm_90+: vector float2 reduction (red.global.add.v2.f32)
 }
 
-// grid(k1, k2) += c.  fold: the grid holds, in columns 0..K2/2, the Hermitian
-// part h(k) = (g(k) + conj g(-k)) / 2 of the sum g, which is what the C2R
-// transform needs for Re F^H g: c adds c / 2 at k when k2 <= K2/2 and
-// conj(c) / 2 at -k when -k2 mod K2 <= K2/2 (both for k2 = 0 and k2 = K2/2).
+// Grid layouts.  Full: [K1][K2] complex.  Half (hs > 0): columns 0..K2/2 of
+// each row at a row stride of hs = K2/2 + 1, the layout of the R2C output
+// and of the C2R input (cuFFT runs these about 35 % slower with a padded
+// row stride, so half grids are not TMA-aligned and their windows are staged
+// by per-thread asynchronous copies).
+//
+// grid(k1, k2) += c.  fold = 0: a full grid.  fold = hs > 0: the half grid
+// holds the Hermitian part h(k) = (g(k) + conj g(-k)) / 2 of the sum g, which
+// is what the C2R transform needs for Re F^H g: c adds c / 2 at k when
+// k2 <= K2/2 and conj(c) / 2 at -k when -k2 mod K2 <= K2/2 (both for k2 = 0
+// and k2 = K2/2).
 __device__ __forceinline__ void red_grid(float2 *__restrict__ gb, int k1, int k2, int K1, int K2, float re,
-                                         float im, bool fold) {
+                                         float im, int fold) {
     if (!fold) {
         red_add_f2(gb + (long long)k1 * K2 + k2, make_float2(re, im));
         return;
     }
     const int h = K2 >> 1;
-    if (k2 <= h) red_add_f2(gb + (long long)k1 * K2 + k2, make_float2(0.5f * re, 0.5f * im));
+    if (k2 <= h) red_add_f2(gb + (long long)k1 * fold + k2, make_float2(0.5f * re, 0.5f * im));
     if (k2 == 0 || k2 >= h) {
         const int m1 = k1 ? K1 - k1 : 0, m2 = k2 ? K2 - k2 : 0;
-        red_add_f2(gb + (long long)m1 * K2 + m2, make_float2(0.5f * re, -0.5f * im));
+        red_add_f2(gb + (long long)m1 * fold + m2, make_float2(0.5f * re, -0.5f * im));
     }
+}
+
+// X(k1, k2) of a spectrum.  hs = 0: a full grid.  hs > 0: a half grid of a
+// real image's spectrum, whose other half follows from X(k) = conj X(-k).
+__device__ __forceinline__ float2 spec_at(const float2 *__restrict__ gl, int k1, int k2, int K1, int K2, int hs) {
+    if (!hs) return gl[(long long)k1 * K2 + k2];
+    if (k2 <= (K2 >> 1)) return gl[(long long)k1 * hs + k2];
+    const int m1 = k1 ? K1 - k1 : 0;
+    const float2 v = gl[(long long)m1 * hs + (K2 - k2)];
+    return make_float2(v.x, -v.y);
 }
 
 // The data term of one PDFB iteration (Eq. 2) in two passes over G:
@@ -140,7 +157,7 @@ constexpr int kFixBits = 22;                     // contributions are scaled bel
 // 32-bit words: integers in fixed point, floats otherwise.
 template <bool DENSE, bool FIXED>
 __device__ __forceinline__ void scatter_cell(int *s_win, int ib, float2 *__restrict__ gb,
-                                             int gk1, int gk2, int K1, int K2, bool fold, float g1x, float g1y,
+                                             int gk1, int gk2, int K1, int K2, int fold, float g1x, float g1y,
                                              float er, float ei) {
     if (DENSE && FIXED) {
         const float re = fmaf(g1x, er, fmaf(g1y, ei, kFixMagic));
@@ -163,7 +180,7 @@ __device__ __forceinline__ void scatter_cell(int *s_win, int ib, float2 *__restr
 // point here: one rounding).
 template <bool DENSE, bool FIXED>
 __device__ __forceinline__ void scatter_value(int *s_win, int ib, float2 *__restrict__ gb,
-                                              int gk1, int gk2, int K1, int K2, bool fold, float pr, float pi,
+                                              int gk1, int gk2, int K1, int K2, int fold, float pr, float pi,
                                               float fs) {
     if (DENSE && FIXED) {
         const float re = fmaf(pr, fs, kFixMagic), im = fmaf(pi, fs, kFixMagic);
@@ -182,7 +199,7 @@ template <bool DENSE, bool FIXED>
 __device__ __forceinline__ void scatter_rows(int i0, int nv, int lane, const int2 *s_meta, const int *s_off,
                                              const float2 *s_d, const float2 *__restrict__ fbin, int *s_win,
                                              int wy0, int wx0, float2 *__restrict__ gb, int K1, int K2, float fs,
-                                             bool fold) {
+                                             int fold) {
     constexpr unsigned FULL = 0xffffffffu;
     float2 fac = make_float2(0.f, 0.f);
     if (i0 < nv) fac = load_factors(fbin + s_off[i0], s_meta[i0].y, lane);
@@ -277,7 +294,7 @@ template <bool DENSE, bool FIXED>
 __device__ __forceinline__ void scatter_pairs(int i0, int nv, int lane, const int2 *s_meta, const int *s_off,
                                               const float2 *s_d, const float2 *__restrict__ fbin, int *s_win,
                                               int wy0, int wx0, float2 *__restrict__ gb, int K1, int K2, float fs,
-                                              bool fold) {
+                                              int fold) {
     constexpr unsigned FULL = 0xffffffffu;
     const int v = lane >> 4, g = (lane >> 3) & 1, col = lane & 7, hi = g;
     auto load = [&](int r) -> float2 {
@@ -347,7 +364,7 @@ __device__ __forceinline__ void scatter_rows_rank(int i0, int nv, int lane, int 
                                                   const int *s_off, const float2 *s_d,
                                                   const float2 *__restrict__ fbin, int *s_win,
                                                   int wy0, int wx0, float2 *__restrict__ gb, int K1, int K2,
-                                                  float fs, bool fold) {
+                                                  float fs, int fold) {
     constexpr unsigned FULL = 0xffffffffu;
     const int half = lane >> 4, col = lane & 15;
     for (int i = i0; i < nv; i += kWarps) {
@@ -410,7 +427,8 @@ __device__ __forceinline__ void scatter_rows_rank(int i0, int nv, int lane, int 
 template <int C0, int CW, bool DENSE>
 __device__ __forceinline__ void gather_cols(const float2 *__restrict__ f, int T, int t_lo, int t_hi, int c1, int c2,
                                             const float2 *s_grid, int wy0, int wx0,
-                                            const float2 *__restrict__ gl, int K1, int K2, float &ar, float &ai) {
+                                            const float2 *__restrict__ gl, int K1, int K2, int hs, float &ar,
+                                            float &ai) {
     float2 g2[CW];
 #pragma unroll
     for (int t = 0; t < CW; ++t) g2[t] = (C0 + t < T) ? __ldg(f + T + C0 + t) : make_float2(0.f, 0.f);
@@ -436,10 +454,9 @@ __device__ __forceinline__ void gather_cols(const float2 *__restrict__ f, int T,
         } else {
             int k1 = c1 + t1;
             k1 -= (k1 >= K1) ? K1 : 0;
-            const float2 *row = gl + (long long)k1 * K2;
 #pragma unroll
             for (int t2 = 0; t2 < CW; ++t2) {
-                const float2 x = row[k2[t2]];
+                const float2 x = spec_at(gl, k1, k2[t2], K1, K2, hs);
                 br = fmaf(g2[t2].x, x.x, fmaf(-g2[t2].y, x.y, br));
                 bi = fmaf(g2[t2].x, x.y, fmaf(g2[t2].y, x.x, bi));
             }
@@ -458,11 +475,12 @@ __device__ __forceinline__ void gather_cols(const float2 *__restrict__ f, int T,
 template <int C0, int TT, bool DENSE>
 __device__ __forceinline__ void gather_chunks(const float2 *__restrict__ f, int T, int t_lo, int t_hi, int c1,
                                               int c2, const float2 *s_grid, int wy0, int wx0,
-                                              const float2 *__restrict__ gl, int K1, int K2, float &ar, float &ai) {
+                                              const float2 *__restrict__ gl, int K1, int K2, int hs, float &ar,
+                                              float &ai) {
     constexpr int CW = (TT - C0 < kGatherCols) ? TT - C0 : kGatherCols;
-    gather_cols<C0, CW, DENSE>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, gl, K1, K2, ar, ai);
+    gather_cols<C0, CW, DENSE>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs, ar, ai);
     if constexpr (C0 + CW < TT)
-        gather_chunks<C0 + CW, TT, DENSE>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, gl, K1, K2, ar, ai);
+        gather_chunks<C0 + CW, TT, DENSE>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs, ar, ai);
 }
 
 // Gather of a row whose side is exactly TT (at most 8) from the shared
@@ -504,9 +522,9 @@ __device__ __forceinline__ float2 gather_exact(const float2 *__restrict__ f, int
 template <int TT, bool DENSE>
 __device__ __forceinline__ float2 gather_lane(const float2 *__restrict__ f, int T, int t_lo, int t_hi, int c1,
                                               int c2, const float2 *s_grid, int wy0, int wx0,
-                                              const float2 *__restrict__ gl, int K1, int K2) {
+                                              const float2 *__restrict__ gl, int K1, int K2, int hs) {
     float ar = 0.f, ai = 0.f;
-    gather_chunks<0, TT, DENSE>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, gl, K1, K2, ar, ai);
+    gather_chunks<0, TT, DENSE>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs, ar, ai);
     return make_float2(ar, ai);
 }
 
@@ -516,13 +534,14 @@ __device__ __forceinline__ float2 gather_lane(const float2 *__restrict__ f, int 
 template <int TT, bool DENSE>
 __device__ __forceinline__ float2 gather_terms(const float2 *__restrict__ f, int T, int R, int c1, int c2,
                                                const float2 *s_grid, int wy0, int wx0,
-                                               const float2 *__restrict__ gl, int K1, int K2) {
-    if (R == 1) return gather_lane<TT, DENSE>(f, T, 0, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
+                                               const float2 *__restrict__ gl, int K1, int K2, int hs) {
+    if (R == 1) return gather_lane<TT, DENSE>(f, T, 0, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs);
     const int Tb = T - R + 1;
     float2 phi = make_float2(0.f, 0.f);
 #pragma unroll 1
     for (int r = 0; r < R; ++r) {
-        const float2 t = gather_lane<TT, DENSE>(f + r * 2 * T, T, r, r + Tb, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
+        const float2 t =
+            gather_lane<TT, DENSE>(f + r * 2 * T, T, r, r + Tb, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs);
         phi.x += t.x;
         phi.y += t.y;
     }
@@ -540,7 +559,7 @@ __device__ __forceinline__ void gather_phase(int nv, int R, const int2 *s_meta, 
                                              const long long *s_v, const unsigned char *s_pc, const float *s_psc,
                                              const float2 *s_y, float2 *s_d, float *s_n2,
                                              const float2 *__restrict__ fbin, const float2 *s_grid,
-                                             int wy0, int wx0, const float2 *__restrict__ gl, int K1, int K2,
+                                             int wy0, int wx0, const float2 *__restrict__ gl, int K1, int K2, int hs,
                                              float sigma2, float2 *__restrict__ dvis) {
     const int nvr = (nv + 31) & ~31;                 // whole warps: the max below takes every lane
     for (int i = threadIdx.x; i < nvr; i += blockDim.x) {
@@ -566,12 +585,12 @@ __device__ __forceinline__ void gather_phase(int nv, int R, const int2 *s_meta, 
                 phi = tm == 7 ? gather_exact<7>(f, c1, c2, s_grid, wy0, wx0)
                               : gather_exact<8>(f, c1, c2, s_grid, wy0, wx0);
         }
-        else if (tm <= 4) phi = gather_terms<4, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
-        else if (tm <= 7) phi = gather_terms<7, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
-        else if (tm <= 9) phi = gather_terms<9, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
-        else if (tm <= 11) phi = gather_terms<11, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
-        else if (tm <= 13) phi = gather_terms<13, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
-        else phi = gather_terms<16, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2);
+        else if (tm <= 4) phi = gather_terms<4, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs);
+        else if (tm <= 7) phi = gather_terms<7, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs);
+        else if (tm <= 9) phi = gather_terms<9, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs);
+        else if (tm <= 11) phi = gather_terms<11, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs);
+        else if (tm <= 13) phi = gather_terms<13, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs);
+        else phi = gather_terms<16, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs);
         if (!valid) continue;
         if (MODE == kDual) {
             const float2 dold = s_d[i];
@@ -654,9 +673,9 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
     const long long *__restrict__ bin_fbase, const long long *__restrict__ piece_start, const int *__restrict__ piece_len, const int *__restrict__ piece_blk,
     const int *__restrict__ bin_chan, const int *__restrict__ bin_tile, int ntx, int B,
     const float *__restrict__ blk_scale, double *__restrict__ blk_norm2, const float2 *__restrict__ grid,
-    float2 *__restrict__ grid_out, long long K, int K1, int K2, float sigma2, int R_,
-    const __grid_constant__ CUtensorMap tmap, int use_tma, const float *__restrict__ gmax, int allow_fixed,
-    int fold_out, int *__restrict__ err) {
+    float2 *__restrict__ grid_out, long long in_cs, int in_hs, long long out_cs, int K1, int K2, float sigma2,
+    int R_, const __grid_constant__ CUtensorMap tmap, int use_tma, const float *__restrict__ gmax, int allow_fixed,
+    int fold, int *__restrict__ err) {
     const int R = MULTI ? R_ : 1;
     __shared__ alignas(128) float2 s_grid[kWin * kWinP];
     __shared__ alignas(8) uint64_t s_bar;
@@ -679,21 +698,46 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
     const int bin = blockIdx.x;
     const int l = bin_chan[bin];
     const int tile = bin_tile[bin];
-    const float2 *gl = grid + (long long)l * K;
-    float2 *gb = (MODE == kScatter || MODE == kNormal) ? grid_out + (long long)l * K : nullptr;
+    // input grid: channel stride in_cs, full (in_hs = 0) or half layout; output grid: channel stride
+    // out_cs, full, or half with the folded adjoint (fold = its row stride)
+    const float2 *gl = grid + (long long)l * in_cs;
+    float2 *gb = (MODE == kScatter || MODE == kNormal) ? grid_out + (long long)l * out_cs : nullptr;
     const bool dense = tile >= 0;
     int wy0 = 0, wx0 = 0;
     if (dense) {
         wy0 = (tile / ntx) * kTile;
         wx0 = (tile % ntx) * kTile;
     }
-    // the window by TMA when it lies inside the grid (x = wx0 is a multiple of 32 cells: 256-byte
-    // aligned), issued first so that it overlaps the staging of the rows
-    const bool tma = MODE != kScatter && use_tma && dense && wy0 + kWin <= K1 && wx0 + kWinP <= K2;
+    // the window by TMA when it lies inside the stored grid (x = wx0 is a multiple of 32 cells:
+    // 256-byte aligned; a half grid stores columns 0..K2/2), issued first so that it overlaps the
+    // staging of the rows
+    const bool tma = MODE != kScatter && use_tma && dense && wy0 + kWin <= K1 &&
+                     wx0 + kWinP <= (in_hs ? (K2 >> 1) + 1 : K2);
     if (tma && threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         window_tma(s_grid, &tmap, wx0, wy0, l, &s_bar);
+    }
+    // otherwise by per-thread asynchronous 8-byte copies, issued now for the same overlap; cells of
+    // a half grid's other half come from -k (conjugated once they have arrived)
+    const bool acopy = MODE != kScatter && dense && !tma;
+    if (acopy) {
+        // one window row per warp step, its cells over the lanes (row terms computed once)
+        const int h = K2 >> 1;
+        for (int r = warp; r < kWin; r += kWarps) {
+            int k1 = wy0 + r;
+            while (k1 >= K1) k1 -= K1;
+            const float2 *rd = gl + (long long)k1 * (in_hs ? in_hs : K2);          // row k1
+            const float2 *rm = gl + (long long)(k1 ? K1 - k1 : 0) * in_hs + K2;    // row -k1, + K2
+            const uint32_t dst = smem_addr(&s_grid[r * kWinP]);
+            for (int c = lane; c < kWin; c += 32) {
+                int k2 = wx0 + c;
+                while (k2 >= K2) k2 -= K2;
+                const float2 *src = (!in_hs || k2 <= h) ? rd + k2 : rm - k2;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst + 8u * c), "l"(src) : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
     }
     // the bin's pieces: runs of rows of one block each, in the order of their blocks
     const long long pp0 = (long long)bin * slots;
@@ -746,41 +790,39 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
         tmax = __reduce_max_sync(0xffffffffu, tmax);
         if (lane == 0 && tmax > 0) atomicMax(&s_tmax, tmax);
     }
-    if (dense) {
-        for (int i = threadIdx.x; i < kWin * kWin; i += blockDim.x) {
-            const int r = i / kWin, c = i - r * kWin;
-            if (MODE != kScatter && !tma) {
-                int k1 = wy0 + r;
-                while (k1 >= K1) k1 -= K1;
-                int k2 = wx0 + c;
-                while (k2 >= K2) k2 -= K2;
-                s_grid[r * kWinP + c] = gl[(long long)k1 * K2 + k2];
-            }
-        }
-        if (MODE != kGather && MODE != kDual)
-            for (int i = threadIdx.x; i < 2 * kWin * kAdjS; i += blockDim.x) s_win[i] = 0;
-    }
-    __syncthreads();                     // the barrier's initialisation is visible from here on
+    if (dense && MODE != kGather && MODE != kDual)
+        for (int i = threadIdx.x; i < 2 * kWin * kAdjS; i += blockDim.x) s_win[i] = 0;
+    if (acopy) asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();                     // the barrier's initialisation (and the copies) visible from here on
     if (tma && !window_wait(&s_bar, kWindowPolls, err)) {
         // the copy did not complete in time: record it, then wait once more (bounded) so that
         // no copy into this CTA's shared memory is still in flight when it moves on
         if (threadIdx.x == 0) atomicExch(err, 2);
         window_wait(&s_bar, kWindowPolls, err);
     }
+    // conjugate the window's cells that came from -k (columns past K2/2 of a half grid)
+    if (acopy && in_hs && wx0 + kWin - 1 > (K2 >> 1)) {
+        for (int r = warp; r < kWin; r += kWarps)
+            for (int c = lane; c < kWin; c += 32) {
+                int k2 = wx0 + c;
+                while (k2 >= K2) k2 -= K2;
+                if (k2 > (K2 >> 1)) s_grid[r * kWinP + c].y = -s_grid[r * kWinP + c].y;
+            }
+        __syncthreads();
+    }
     const float2 *fbin = gfac + fb;
     // phase 1: gathers, one row per thread
     if (MODE != kScatter) {
         if (dense)
             gather_phase<MODE, true>(nv, R, s_meta, s_off, s_v, s_pc, s_psc, s_y, s_d, s_n2, fbin, s_grid, wy0, wx0,
-                                     gl, K1, K2, sigma2, dvis);
+                                     gl, K1, K2, in_hs, sigma2, dvis);
         else
             gather_phase<MODE, false>(nv, R, s_meta, s_off, s_v, s_pc, s_psc, s_y, s_d, s_n2, fbin, s_grid, wy0, wx0,
-                                      gl, K1, K2, sigma2, dvis);
+                                      gl, K1, K2, in_hs, sigma2, dvis);
     }
     // phase 2: scatters of conj(G_i) s_d[i], one row per warp
     bool fixed = false;
     float fs = 1.f, finv = 1.f;
-    const bool fold = fold_out != 0;
     if (MODE == kScatter || MODE == kNormal) {
         if (MODE == kNormal) __syncthreads();        // s_d holds the gathered values
         // fixed point in the scatter when the caller allows it (Phi^H, the data term's scatter pass,
@@ -912,15 +954,16 @@ cudaError_t launch_unsatisfied_wait(fhs_problem *p, int max_polls, cudaStream_t 
     return cudaGetLastError();
 }
 
-// Tensor map of a [L][K1][K2] complex grid for the window staging (8-byte
-// elements, box kWinP x kWin x 1).  The encoder comes from the driver entry
-// point; ok = 0 (per-thread staging) if it is unavailable or refuses the map.
+// Tensor map of a [L][K1][row stride] complex grid (full: K2, half: hs) for
+// the window staging (8-byte elements, box kWinP x kWin x 1).  The encoder
+// comes from the driver entry point; ok = 0 (per-thread staging) if it is
+// unavailable or refuses the map.
 struct WindowMap {
     CUtensorMap map;
     int ok = 0;
 };
 
-static WindowMap window_map(const fhs_problem *p, const float2 *grid) {
+static WindowMap window_map(const fhs_problem *p, const float2 *grid, bool half) {
     static PFN_cuTensorMapEncodeTiled_v12000 enc = [] {
         void *fn = nullptr;
         cudaDriverEntryPointQueryResult q;
@@ -933,9 +976,12 @@ static WindowMap window_map(const fhs_problem *p, const float2 *grid) {
         return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }();
     WindowMap w{};
-    if (!enc || !grid || p->K1 < kWin || p->K2 < kWinP) return w;
-    const cuuint64_t dims[3] = {cuuint64_t(p->K2), cuuint64_t(p->K1), cuuint64_t(p->L)};
-    const cuuint64_t strides[2] = {cuuint64_t(p->K2) * sizeof(float2), cuuint64_t(p->K) * sizeof(float2)};
+    // a half grid's row stride (K2/2 + 1 complex values) is not a multiple of 16 bytes unless
+    // K2/2 is odd; the encoder would refuse it anyway
+    const int rs = half ? p->HS : p->K2;
+    if (!enc || !grid || p->K1 < kWin || rs < kWinP || (rs * sizeof(float2)) % 16 != 0) return w;
+    const cuuint64_t dims[3] = {cuuint64_t(rs), cuuint64_t(p->K1), cuuint64_t(p->L)};
+    const cuuint64_t strides[2] = {cuuint64_t(rs) * sizeof(float2), cuuint64_t(p->K1) * rs * sizeof(float2)};
     const cuuint32_t box[3] = {cuuint32_t(kWinP), cuuint32_t(kWin), 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     w.ok = enc(&w.map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<float2 *>(grid), dims, strides, box, estr,
@@ -946,36 +992,39 @@ static WindowMap window_map(const fhs_problem *p, const float2 *grid) {
 
 // One launch of the pass over G in mode MODE, one CTA per bin.
 template <int MODE>
+// in_half: the input grid is a half grid (a forward spectrum); fold: the output is the folded
+// adjoint in a half grid (otherwise a full grid).
 cudaError_t launch_pass(fhs_problem *p, const float2 *y, float2 *dvis, const float *blk_scale, double *blk_norm2,
-                        const float2 *grid, float2 *grid_out, float sigma2, const WindowMap &tm, int allow_fixed,
-                        int fold, cudaStream_t s) {
+                        const float2 *grid, bool in_half, float2 *grid_out, bool fold, float sigma2,
+                        const WindowMap &tm, int allow_fixed, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
-    (p->rank > 1 ? degrid_grid_binned_kernel<MODE, true> : degrid_grid_binned_kernel<MODE, false>)<<<p->n_bin, 256, 0, s>>>(
+    const long long in_cs = in_half ? p->KH : p->K, out_cs = fold ? p->KH : p->K;
+    (p->rank > 1 ? degrid_grid_binned_kernel<MODE, true>
+                 : degrid_grid_binned_kernel<MODE, false>)<<<p->n_bin, 256, 0, s>>>(
         p->meta, p->fptr, p->gfac, y, dvis, p->bin_slots, p->bin_fbase, p->piece_start, p->piece_len, p->piece_blk,
-        p->bin_chan,
-        p->bin_tile, p->ntx, p->B, blk_scale, blk_norm2, grid, grid_out, p->K, p->K1, p->K2, sigma2, p->rank, tm.map,
-        tm.ok, p->gmax, allow_fixed, fold, p->dev_err);
+        p->bin_chan, p->bin_tile, p->ntx, p->B, blk_scale, blk_norm2, grid, grid_out, in_cs, in_half ? p->HS : 0,
+        out_cs, p->K1, p->K2, sigma2, p->rank, tm.map, tm.ok, p->gmax, allow_fixed, fold ? p->HS : 0, p->dev_err);
     p->n_launch += 1;
     return cudaGetLastError();
 }
 
 cudaError_t launch_degrid(fhs_problem *p, const float2 *grid, float2 *vis_sorted, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
-    return launch_pass<kGather>(p, nullptr, vis_sorted, nullptr, nullptr, grid, nullptr, 0.f, window_map(p, grid), 0,
-                                0, s);
+    return launch_pass<kGather>(p, nullptr, vis_sorted, nullptr, nullptr, grid, true, nullptr, false, 0.f,
+                                window_map(p, grid, true), 0, s);
 }
 
 cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, cudaStream_t s, bool fixed,
                         bool fold) {
-    return launch_pass<kScatter>(p, nullptr, const_cast<float2 *>(vis_sorted), nullptr, nullptr, nullptr, grid, 0.f,
-                                 WindowMap{}, fixed ? 1 : 0, fold ? 1 : 0, s);
+    return launch_pass<kScatter>(p, nullptr, const_cast<float2 *>(vis_sorted), nullptr, nullptr, nullptr, false,
+                                 grid, fold, 0.f, WindowMap{}, fixed ? 1 : 0, s);
 }
 
-cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, cudaStream_t s, bool fixed,
-                          bool fold) {
+cudaError_t launch_normal(fhs_problem *p, const float2 *grid, bool in_half, float2 *grid_out, cudaStream_t s,
+                          bool fixed, bool fold) {
     if (p->n_bin == 0) return cudaSuccess;
-    return launch_pass<kNormal>(p, nullptr, nullptr, nullptr, nullptr, grid, grid_out, 0.f, window_map(p, grid),
-                                fixed ? 1 : 0, fold ? 1 : 0, s);
+    return launch_pass<kNormal>(p, nullptr, nullptr, nullptr, nullptr, grid, in_half, grid_out, fold, 0.f,
+                                window_map(p, grid, in_half), fixed ? 1 : 0, s);
 }
 
 // The data term in two passes: the dual pre-update with the block norms
@@ -984,13 +1033,13 @@ cudaError_t launch_normal(fhs_problem *p, const float2 *grid, float2 *grid_out, 
 // grids to combine.
 cudaError_t launch_data_dual(fhs_problem *p, cudaStream_t s) {
     if (p->n_bin == 0) return cudaSuccess;
-    return launch_pass<kDual>(p, p->y, p->dvis, p->blk_scale, p->blk_norm2, p->grid_work, nullptr, float(p->sigma2),
-                              window_map(p, p->grid_work), 0, 0, s);
+    return launch_pass<kDual>(p, p->y, p->dvis, p->blk_scale, p->blk_norm2, p->grid_work, true, nullptr, false,
+                              float(p->sigma2), window_map(p, p->grid_work, true), 0, s);
 }
 
 cudaError_t launch_data_scatter(fhs_problem *p, cudaStream_t s) {
-    return launch_pass<kScatter>(p, nullptr, p->dvis, p->blk_scale, nullptr, nullptr, p->grid_work, 0.f, WindowMap{},
-                                 1, 1, s);
+    return launch_pass<kScatter>(p, nullptr, p->dvis, p->blk_scale, nullptr, nullptr, false, p->grid_work, true, 0.f,
+                                 WindowMap{}, 1, s);
 }
 
 }  // namespace fhs

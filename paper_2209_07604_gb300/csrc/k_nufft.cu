@@ -195,24 +195,6 @@ __global__ void crop_kernel(const float *__restrict__ grid, float *__restrict__ 
     }
 }
 
-// The spectrum of a real grid is Hermitian: X(k) = conj X(-k).  The R2C
-// transform writes columns 0..K2/2 of each row; this fills columns
-// K2/2+1..K2-1 from them, X[k1][k2] = conj X[(K1 - k1) mod K1][K2 - k2], one
-// row per CTA step (reads and writes are contiguous, the reads in reverse).
-__global__ void expand_kernel(float2 *__restrict__ grid, int K1, int K2, int rows) {
-    const int h = K2 >> 1;
-    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
-        const int l = r / K1, k1 = r - l * K1;
-        const int m1 = k1 ? K1 - k1 : 0;
-        float2 *dst = grid + (long long)r * K2;
-        const float2 *src = grid + ((long long)l * K1 + m1) * K2;
-        for (int k2 = h + 1 + threadIdx.x; k2 < K2; k2 += blockDim.x) {
-            const float2 v = src[K2 - k2];
-            dst[k2] = make_float2(v.x, -v.y);
-        }
-    }
-}
-
 __global__ void permute_to_caller_kernel(const float2 *__restrict__ sorted, float2 *__restrict__ caller,
                                          const long long *__restrict__ perm, const long long *__restrict__ chunk_start,
                                          const int *__restrict__ chunk_seg, const float *__restrict__ scale_seg) {
@@ -404,14 +386,6 @@ cudaError_t launch_zpad(fhs_problem *p, const float *x, float *grid, cudaStream_
 cudaError_t launch_crop(fhs_problem *p, const float *grid, float *x, cudaStream_t s) {
     dim3 g(grid_for(p->N, 256, 512), p->L);
     crop_kernel<<<g, 256, 0, s>>>(grid, x, p->s1, p->s2, p->ny, p->nx, p->K1, p->K2, p->K);
-    p->n_launch += 1;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_expand(fhs_problem *p, float2 *grid, cudaStream_t s) {
-    const long long rows = (long long)p->L * p->K1;
-    if (rows == 0 || p->K2 < 4) return cudaSuccess;
-    expand_kernel<<<grid_for(rows, 1, 152 * 16), 256, 0, s>>>(grid, p->K1, p->K2, int(rows));
     p->n_launch += 1;
     return cudaGetLastError();
 }

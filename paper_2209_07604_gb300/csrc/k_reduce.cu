@@ -97,24 +97,21 @@ __global__ void dr_setup_kernel(const double *__restrict__ diag, float2 *__restr
 // there without a branch, and all loads of a step are independent.
 
 // Reduced dual pre-update: r = v + sigma2 Lambda (H Xhat) - sigma2 y' (r
-// replaces v), ||r||^2 per channel; the next pass's output grid `out` is
-// zeroed on the way.  u (the normal-pass output) is zeroed by dr_apply_kernel:
-// a store that does not wait for the load of the same line stalls the
-// load/store queue behind that line's miss.
-__global__ void __launch_bounds__(256) dr_dual_kernel(float4 *__restrict__ u, float4 *__restrict__ out,
+// replaces v), ||r||^2 per channel.  u (the normal-pass output) is zeroed by
+// dr_apply_kernel: a store that does not wait for the load of the same line
+// stalls the load/store queue behind that line's miss.
+__global__ void __launch_bounds__(256) dr_dual_kernel(const float4 *__restrict__ u,
                                                       float4 *__restrict__ v, const float4 *__restrict__ yred,
                                                       const float2 *__restrict__ lam, float sigma2,
                                                       double *__restrict__ norm2, long long K2h) {
     __shared__ double s_red[8];
     const int l = blockIdx.y;
     const long long base = (long long)l * K2h;
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     float acc = 0.f, cmp = 0.f;                     // compensated FP32 per thread, FP64 across threads
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < K2h; k += (long long)gridDim.x * blockDim.x) {
         const long long i = base + k;
         const float4 uu = u[i], vv = v[i], yy = yred[i];
         const float2 lk = lam[i];
-        out[i] = z4;
         const float sa = sigma2 * lk.x, sb = sigma2 * lk.y;
         float4 r;
         r.x = fmaf(sa, uu.x, fmaf(-sigma2, yy.x, vv.x));
@@ -256,7 +253,7 @@ cudaError_t launch_dr_setup(fhs_problem *p, const double *diag, float2 *ghy, uns
 
 cudaError_t launch_dr_dual(fhs_problem *p, cudaStream_t s) {
     dr_dual_kernel<<<grid_cells(p, dr_dual_kernel, p->K / 2), 256, 0, s>>>(
-        f4(p->dr_u), f4(p->grid_work), f4(p->dr_v), f4(p->dr_y), f2(p->dr_lam), float(p->sigma2), p->dr_norm2, p->K / 2);
+        f4(p->dr_u), f4(p->dr_v), f4(p->dr_y), f2(p->dr_lam), float(p->sigma2), p->dr_norm2, p->K / 2);
     p->n_launch += 1;
     return cudaGetLastError();
 }
