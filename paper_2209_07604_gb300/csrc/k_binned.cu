@@ -79,8 +79,33 @@ __device__ __forceinline__ float2 spec_at(const float2 *__restrict__ gl, int k1,
 // channel grid once at the end (one global reduction per cell instead of one
 // per G entry).  Bins marked -1 (sparse tiles) take the global path.
 constexpr int kWin = kTile + 15;        // boxes have T <= 16
-constexpr int kWinP = kWin + 1;         // row stride of the staged forward window: a TMA box row
-                                        // must be a multiple of 16 bytes (48 complex values)
+// The staged forward window holds its even and its odd rows in two boxes of
+// kBoxH rows x kBoxW cells (a TMA box row must be a multiple of 16 bytes):
+// grids are read as rows of pairs of rows, whose stride is a multiple of 16
+// bytes even when a row's is not (a half grid's K2/2 + 1 cells).
+constexpr int kBoxW = 48;
+constexpr int kBoxH = (kWin + 1) / 2;
+constexpr int kBoxCells = kBoxW * kBoxH;
+static_assert(kBoxW >= kWin + 1 && kBoxW % 2 == 0, "window box width");
+// Window cell (rr, cc), rows and columns relative to the tile origin.  Direct
+// (MIR = false): cell (rr, cc) of the grid, the odd rows shifted right by sh
+// (the odd box starts one cell early when the grid's row stride is odd).
+// MIR: the window lies in the half of a Hermitian spectrum that is not
+// stored, and the boxes hold the conjugate-symmetric block, cell (rr, cc) at
+// row kBoxH - 1 - rr / 2 and column kWin - 1 + sh (rr odd) - cc of its box: the
+// gather reads such a window's rows backwards and conjugated.
+template <bool MIR>
+__device__ __forceinline__ const float2 *win_cell(const float2 *s_grid, int rr, int cc, int sh) {
+    const int p = rr & 1, j = rr >> 1;
+    if (!MIR) return s_grid + p * kBoxCells + j * kBoxW + cc + sh * p;
+    return s_grid + p * kBoxCells + (kBoxH - 1 - j) * kBoxW + (kWin - 1 + sh * p) - cc;
+}
+template <bool MIR>
+__device__ __forceinline__ float2 win_ld(const float2 *q, int t) {
+    if (!MIR) return q[t];
+    const float2 v = q[-t];
+    return make_float2(v.x, -v.y);
+}
 // Row stride (in 32-bit words) of the adjoint window planes.  56 = 24 mod 32:
 // box rows 1, 2 and 3 below a row start 24, 16 and 8 banks further on, so
 // four rows of at most 8 adjacent cells, or two rows 2 apart of at most 16
@@ -424,9 +449,9 @@ __device__ __forceinline__ void scatter_rows_rank(int i0, int nv, int lane, int 
 // Columns [C0, C0 + CW) of the gather of one row by one lane:
 // sum_t1 g1[t1] sum_t2 g2[t2] X[c1+t1][c2+t2], with g2 of those columns in
 // registers (zero beyond T).
-template <int C0, int CW, bool DENSE>
+template <int C0, int CW, bool DENSE, bool MIR>
 __device__ __forceinline__ void gather_cols(const float2 *__restrict__ f, int T, int t_lo, int t_hi, int c1, int c2,
-                                            const float2 *s_grid, int wy0, int wx0,
+                                            const float2 *s_grid, int wy0, int wx0, int sh,
                                             const float2 *__restrict__ gl, int K1, int K2, int hs, float &ar,
                                             float &ai) {
     float2 g2[CW];
@@ -444,10 +469,10 @@ __device__ __forceinline__ void gather_cols(const float2 *__restrict__ f, int T,
         const float2 a = __ldg(f + t1);
         float br = 0.f, bi = 0.f;
         if (DENSE) {
-            const float2 *row = s_grid + (c1 - wy0 + t1) * kWinP + (c2 - wx0 + C0);
+            const float2 *row = win_cell<MIR>(s_grid, c1 - wy0 + t1, c2 - wx0 + C0, sh);
 #pragma unroll
             for (int t2 = 0; t2 < CW; ++t2) {
-                const float2 x = row[t2];
+                const float2 x = win_ld<MIR>(row, t2);
                 br = fmaf(g2[t2].x, x.x, fmaf(-g2[t2].y, x.y, br));
                 bi = fmaf(g2[t2].x, x.y, fmaf(g2[t2].y, x.x, bi));
             }
@@ -472,15 +497,16 @@ __device__ __forceinline__ void gather_cols(const float2 *__restrict__ f, int T,
 // four FMAs with every lane busy and no reduction across lanes.  Sides above 8
 // take two passes over the rows (8 columns of g2 in registers at a time, under
 // the 64-register cap).
-template <int C0, int TT, bool DENSE>
+template <int C0, int TT, bool DENSE, bool MIR>
 __device__ __forceinline__ void gather_chunks(const float2 *__restrict__ f, int T, int t_lo, int t_hi, int c1,
-                                              int c2, const float2 *s_grid, int wy0, int wx0,
+                                              int c2, const float2 *s_grid, int wy0, int wx0, int sh,
                                               const float2 *__restrict__ gl, int K1, int K2, int hs, float &ar,
                                               float &ai) {
     constexpr int CW = (TT - C0 < kGatherCols) ? TT - C0 : kGatherCols;
-    gather_cols<C0, CW, DENSE>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs, ar, ai);
+    gather_cols<C0, CW, DENSE, MIR>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, sh, gl, K1, K2, hs, ar, ai);
     if constexpr (C0 + CW < TT)
-        gather_chunks<C0 + CW, TT, DENSE>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs, ar, ai);
+        gather_chunks<C0 + CW, TT, DENSE, MIR>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, sh, gl, K1, K2, hs, ar,
+                                               ai);
 }
 
 // Gather of a row whose side is exactly TT (at most 8) from the shared
@@ -488,9 +514,9 @@ __device__ __forceinline__ void gather_chunks(const float2 *__restrict__ f, int 
 // row's factors start on a 16-byte boundary: offsets are multiples of 2 T
 // values of 8 bytes), and every loop is unrolled, so the row waits for one
 // memory latency.
-template <int TT>
+template <int TT, bool MIR>
 __device__ __forceinline__ float2 gather_exact(const float2 *__restrict__ f, int c1, int c2, const float2 *s_grid,
-                                               int wy0, int wx0) {
+                                               int wy0, int wx0, int sh) {
     static_assert(TT <= 8, "exact-side gather");
     float2 g[2 * TT];
     const float4 *f4 = reinterpret_cast<const float4 *>(f);
@@ -501,13 +527,13 @@ __device__ __forceinline__ float2 gather_exact(const float2 *__restrict__ f, int
         g[2 * k + 1] = make_float2(q.z, q.w);
     }
     float ar = 0.f, ai = 0.f;
-    const float2 *row = s_grid + (c1 - wy0) * kWinP + (c2 - wx0);
 #pragma unroll
     for (int t1 = 0; t1 < TT; ++t1) {
+        const float2 *row = win_cell<MIR>(s_grid, c1 - wy0 + t1, c2 - wx0, sh);
         float br = 0.f, bi = 0.f;
 #pragma unroll
         for (int t2 = 0; t2 < TT; ++t2) {
-            const float2 x = row[t1 * kWinP + t2];
+            const float2 x = win_ld<MIR>(row, t2);
             const float2 b = g[TT + t2];
             br = fmaf(b.x, x.x, fmaf(-b.y, x.y, br));
             bi = fmaf(b.x, x.y, fmaf(b.y, x.x, bi));
@@ -519,29 +545,29 @@ __device__ __forceinline__ float2 gather_exact(const float2 *__restrict__ f, int
     return make_float2(ar, ai);
 }
 
-template <int TT, bool DENSE>
+template <int TT, bool DENSE, bool MIR>
 __device__ __forceinline__ float2 gather_lane(const float2 *__restrict__ f, int T, int t_lo, int t_hi, int c1,
-                                              int c2, const float2 *s_grid, int wy0, int wx0,
+                                              int c2, const float2 *s_grid, int wy0, int wx0, int sh,
                                               const float2 *__restrict__ gl, int K1, int K2, int hs) {
     float ar = 0.f, ai = 0.f;
-    gather_chunks<0, TT, DENSE>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs, ar, ai);
+    gather_chunks<0, TT, DENSE, MIR>(f, T, t_lo, t_hi, c1, c2, s_grid, wy0, wx0, sh, gl, K1, K2, hs, ar, ai);
     return make_float2(ar, ai);
 }
 
 // Gather of a row with R separable terms (term r at offset 2 T r).  With
 // R > 1 (DDE rows) the first factor of term r is the base factor shifted by
 // r, nonzero only on rows [r, r + T - R + 1), so the other rows are skipped.
-template <int TT, bool DENSE>
+template <int TT, bool DENSE, bool MIR>
 __device__ __forceinline__ float2 gather_terms(const float2 *__restrict__ f, int T, int R, int c1, int c2,
-                                               const float2 *s_grid, int wy0, int wx0,
+                                               const float2 *s_grid, int wy0, int wx0, int sh,
                                                const float2 *__restrict__ gl, int K1, int K2, int hs) {
-    if (R == 1) return gather_lane<TT, DENSE>(f, T, 0, T, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs);
+    if (R == 1) return gather_lane<TT, DENSE, MIR>(f, T, 0, T, c1, c2, s_grid, wy0, wx0, sh, gl, K1, K2, hs);
     const int Tb = T - R + 1;
     float2 phi = make_float2(0.f, 0.f);
 #pragma unroll 1
     for (int r = 0; r < R; ++r) {
         const float2 t =
-            gather_lane<TT, DENSE>(f + r * 2 * T, T, r, r + Tb, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs);
+            gather_lane<TT, DENSE, MIR>(f + r * 2 * T, T, r, r + Tb, c1, c2, s_grid, wy0, wx0, sh, gl, K1, K2, hs);
         phi.x += t.x;
         phi.y += t.y;
     }
@@ -554,12 +580,13 @@ __device__ __forceinline__ float2 gather_terms(const float2 *__restrict__ f, int
 // output, |d|^2 into s_n2 for the block norms; kGather: phi to the output;
 // kNormal: phi into s_d for the scatter.  s_off: each row's factor offset
 // from fbin, s_v: its visibility index, s_pc: its piece (block) in the bin.
-template <int MODE, bool DENSE>
+template <int MODE, bool DENSE, bool MIR>
 __device__ __forceinline__ void gather_phase(int nv, int R, const int2 *s_meta, const int *s_off,
                                              const long long *s_v, const unsigned char *s_pc, const float *s_psc,
                                              const float2 *s_y, float2 *s_d, float *s_n2,
                                              const float2 *__restrict__ fbin, const float2 *s_grid,
-                                             int wy0, int wx0, const float2 *__restrict__ gl, int K1, int K2, int hs,
+                                             int wy0, int wx0, int sh, const float2 *__restrict__ gl, int K1, int K2,
+                                             int hs,
                                              float sigma2, float2 *__restrict__ dvis) {
     const int nvr = (nv + 31) & ~31;                 // whole warps: the max below takes every lane
     for (int i = threadIdx.x; i < nvr; i += blockDim.x) {
@@ -582,15 +609,15 @@ __device__ __forceinline__ void gather_phase(int nv, int R, const int2 *s_meta, 
             // rows past the end take no part (the exact gather reads every cell of its box)
             phi = make_float2(0.f, 0.f);
             if (valid)
-                phi = tm == 7 ? gather_exact<7>(f, c1, c2, s_grid, wy0, wx0)
-                              : gather_exact<8>(f, c1, c2, s_grid, wy0, wx0);
+                phi = tm == 7 ? gather_exact<7, MIR>(f, c1, c2, s_grid, wy0, wx0, sh)
+                              : gather_exact<8, MIR>(f, c1, c2, s_grid, wy0, wx0, sh);
         }
-        else if (tm <= 4) phi = gather_terms<4, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs);
-        else if (tm <= 7) phi = gather_terms<7, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs);
-        else if (tm <= 9) phi = gather_terms<9, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs);
-        else if (tm <= 11) phi = gather_terms<11, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs);
-        else if (tm <= 13) phi = gather_terms<13, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs);
-        else phi = gather_terms<16, DENSE>(f, T, R, c1, c2, s_grid, wy0, wx0, gl, K1, K2, hs);
+        else if (tm <= 4) phi = gather_terms<4, DENSE, MIR>(f, T, R, c1, c2, s_grid, wy0, wx0, sh, gl, K1, K2, hs);
+        else if (tm <= 7) phi = gather_terms<7, DENSE, MIR>(f, T, R, c1, c2, s_grid, wy0, wx0, sh, gl, K1, K2, hs);
+        else if (tm <= 9) phi = gather_terms<9, DENSE, MIR>(f, T, R, c1, c2, s_grid, wy0, wx0, sh, gl, K1, K2, hs);
+        else if (tm <= 11) phi = gather_terms<11, DENSE, MIR>(f, T, R, c1, c2, s_grid, wy0, wx0, sh, gl, K1, K2, hs);
+        else if (tm <= 13) phi = gather_terms<13, DENSE, MIR>(f, T, R, c1, c2, s_grid, wy0, wx0, sh, gl, K1, K2, hs);
+        else phi = gather_terms<16, DENSE, MIR>(f, T, R, c1, c2, s_grid, wy0, wx0, sh, gl, K1, K2, hs);
         if (!valid) continue;
         if (MODE == kDual) {
             const float2 dold = s_d[i];
@@ -609,21 +636,29 @@ __device__ __forceinline__ void gather_phase(int nv, int R, const int2 *s_meta, 
     }
 }
 
-// Window staging by the tensor memory accelerator: one 3-D box (kWinP x kWin
-// cells x 1 channel) of the forward grid into shared memory, completion
-// counted on an mbarrier.  Used for tiles whose window does not wrap around
-// the grid edge (wrapped windows take the per-thread loads).
+// Window staging by the tensor memory accelerator: two 3-D boxes (kBoxW x
+// kBoxH row pairs x 1 channel: the window's even rows and its odd rows) of
+// the forward grid into shared memory, completion counted on one mbarrier.
+// Used for windows that do not wrap around the grid edge (wrapped windows,
+// and those that straddle the stored half of a half grid, take per-thread
+// copies).
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ void window_tma(float2 *dst, const CUtensorMap *tmap, int x, int y, int z, uint64_t *bar) {
+__device__ __forceinline__ void window_tma(float2 *dst, const CUtensorMap *tmap, int x0, int y0, int x1, int y1,
+                                           int z, uint64_t *bar) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(int(sizeof(float2) * kWin * kWinP))
+                 "r"(int(sizeof(float2) * 2 * kBoxCells))
                  : "memory");
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x0), "r"(y0), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_addr(dst + kBoxCells)), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x1), "r"(y1), "r"(z),
+          "r"(smem_addr(bar))
         : "memory");
 }
 
@@ -677,7 +712,7 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
     int R_, const __grid_constant__ CUtensorMap tmap, int use_tma, const float *__restrict__ gmax, int allow_fixed,
     int fold, int *__restrict__ err) {
     const int R = MULTI ? R_ : 1;
-    __shared__ alignas(128) float2 s_grid[kWin * kWinP];
+    __shared__ alignas(128) float2 s_grid[2 * kBoxCells];   // forward window: even rows, then odd rows
     __shared__ alignas(8) uint64_t s_bar;
     __shared__ alignas(16) int s_win[2 * kWin * kAdjS];   // adjoint window planes, row stride kAdjS
     __shared__ int2 s_meta[kBinMax];
@@ -708,15 +743,34 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
         wy0 = (tile / ntx) * kTile;
         wx0 = (tile % ntx) * kTile;
     }
-    // the window by TMA when it lies inside the stored grid (x = wx0 is a multiple of 32 cells:
-    // 256-byte aligned; a half grid stores columns 0..K2/2), issued first so that it overlaps the
-    // staging of the rows
-    const bool tma = MODE != kScatter && use_tma && dense && wy0 + kWin <= K1 &&
-                     wx0 + kWinP <= (in_hs ? (K2 >> 1) + 1 : K2);
+    // the window by TMA, issued first so that it overlaps the staging of the rows, when it does not
+    // wrap: directly when it lies in the stored columns, or (half grids) as the conjugate-symmetric
+    // block when it lies wholly in the other half.  The grid is read as rows of pairs of rows (row
+    // stride rs, 2 rs per pair): the even rows' box at column x0, the odd rows' at rs + x0 less sh
+    // (x coordinates even: 16-byte aligned).
+    const int rs = in_hs ? in_hs : K2, sh = rs & 1, hcol = K2 >> 1;
+    bool tma = false, mir = false;
+    int bx0 = 0, by0 = 0, bx1 = 0, by1 = 0;
+    if (MODE != kScatter && use_tma && dense && wy0 + kWin <= K1) {
+        if (wx0 + kWin - 1 <= (in_hs ? hcol : K2 - 1)) {
+            tma = true;
+            bx0 = wx0;
+            bx1 = rs + wx0 - sh;
+            by0 = by1 = wy0 >> 1;
+        } else if (in_hs && wx0 > hcol && wx0 + kWin <= K2 && wy0 > 0) {
+            // rows K1 - wy0 - rr, columns K2 - wx0 - cc: both in range, no wrap
+            tma = mir = true;
+            bx0 = K2 - wx0 - (kWin - 1);
+            bx1 = rs + K2 - wx0 - (kWin - 1) - sh;
+            by0 = ((K1 - wy0) >> 1) - (kBoxH - 1);
+            by1 = ((K1 - wy0) >> 1) - kBoxH;
+        }
+    }
+    const int wsh = tma ? sh : 0;                  // odd-row shift of the window layout
     if (tma && threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        window_tma(s_grid, &tmap, wx0, wy0, l, &s_bar);
+        window_tma(s_grid, &tmap, bx0, by0, bx1, by1, l, &s_bar);
     }
     // otherwise by per-thread asynchronous 8-byte copies, issued now for the same overlap; cells of
     // a half grid's other half come from -k (conjugated once they have arrived)
@@ -729,7 +783,7 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
             while (k1 >= K1) k1 -= K1;
             const float2 *rd = gl + (long long)k1 * (in_hs ? in_hs : K2);          // row k1
             const float2 *rm = gl + (long long)(k1 ? K1 - k1 : 0) * in_hs + K2;    // row -k1, + K2
-            const uint32_t dst = smem_addr(&s_grid[r * kWinP]);
+            const uint32_t dst = smem_addr(&s_grid[(r & 1) * kBoxCells + (r >> 1) * kBoxW]);
             for (int c = lane; c < kWin; c += 32) {
                 int k2 = wx0 + c;
                 while (k2 >= K2) k2 -= K2;
@@ -806,19 +860,23 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
             for (int c = lane; c < kWin; c += 32) {
                 int k2 = wx0 + c;
                 while (k2 >= K2) k2 -= K2;
-                if (k2 > (K2 >> 1)) s_grid[r * kWinP + c].y = -s_grid[r * kWinP + c].y;
+                float2 &x = s_grid[(r & 1) * kBoxCells + (r >> 1) * kBoxW + c];
+                if (k2 > (K2 >> 1)) x.y = -x.y;
             }
         __syncthreads();
     }
     const float2 *fbin = gfac + fb;
     // phase 1: gathers, one row per thread
     if (MODE != kScatter) {
-        if (dense)
-            gather_phase<MODE, true>(nv, R, s_meta, s_off, s_v, s_pc, s_psc, s_y, s_d, s_n2, fbin, s_grid, wy0, wx0,
-                                     gl, K1, K2, in_hs, sigma2, dvis);
+        if (dense && mir)
+            gather_phase<MODE, true, true>(nv, R, s_meta, s_off, s_v, s_pc, s_psc, s_y, s_d, s_n2, fbin, s_grid, wy0,
+                                           wx0, wsh, gl, K1, K2, in_hs, sigma2, dvis);
+        else if (dense)
+            gather_phase<MODE, true, false>(nv, R, s_meta, s_off, s_v, s_pc, s_psc, s_y, s_d, s_n2, fbin, s_grid, wy0,
+                                            wx0, wsh, gl, K1, K2, in_hs, sigma2, dvis);
         else
-            gather_phase<MODE, false>(nv, R, s_meta, s_off, s_v, s_pc, s_psc, s_y, s_d, s_n2, fbin, s_grid, wy0, wx0,
-                                      gl, K1, K2, in_hs, sigma2, dvis);
+            gather_phase<MODE, false, false>(nv, R, s_meta, s_off, s_v, s_pc, s_psc, s_y, s_d, s_n2, fbin, s_grid,
+                                             wy0, wx0, wsh, gl, K1, K2, in_hs, sigma2, dvis);
     }
     // phase 2: scatters of conj(G_i) s_d[i], one row per warp
     bool fixed = false;
@@ -955,9 +1013,10 @@ cudaError_t launch_unsatisfied_wait(fhs_problem *p, int max_polls, cudaStream_t 
 }
 
 // Tensor map of a [L][K1][row stride] complex grid (full: K2, half: hs) for
-// the window staging (8-byte elements, box kWinP x kWin x 1).  The encoder
-// comes from the driver entry point; ok = 0 (per-thread staging) if it is
-// unavailable or refuses the map.
+// the window staging, viewed as [L][K1 / 2][2 x row stride] (pairs of rows:
+// the pair stride is a multiple of 16 bytes); 8-byte elements, box kBoxW x
+// kBoxH x 1.  The encoder comes from the driver entry point; ok = 0
+// (per-thread staging) if it is unavailable or refuses the map.
 struct WindowMap {
     CUtensorMap map;
     int ok = 0;
@@ -976,13 +1035,11 @@ static WindowMap window_map(const fhs_problem *p, const float2 *grid, bool half)
         return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }();
     WindowMap w{};
-    // a half grid's row stride (K2/2 + 1 complex values) is not a multiple of 16 bytes unless
-    // K2/2 is odd; the encoder would refuse it anyway
     const int rs = half ? p->HS : p->K2;
-    if (!enc || !grid || p->K1 < kWin || rs < kWinP || (rs * sizeof(float2)) % 16 != 0) return w;
-    const cuuint64_t dims[3] = {cuuint64_t(rs), cuuint64_t(p->K1), cuuint64_t(p->L)};
-    const cuuint64_t strides[2] = {cuuint64_t(rs) * sizeof(float2), cuuint64_t(p->K1) * rs * sizeof(float2)};
-    const cuuint32_t box[3] = {cuuint32_t(kWinP), cuuint32_t(kWin), 1};
+    if (!enc || !grid || p->K1 < kWin || p->K1 % 2 != 0 || 2 * rs < kBoxW) return w;
+    const cuuint64_t dims[3] = {cuuint64_t(2) * rs, cuuint64_t(p->K1 / 2), cuuint64_t(p->L)};
+    const cuuint64_t strides[2] = {cuuint64_t(2) * rs * sizeof(float2), cuuint64_t(p->K1) * rs * sizeof(float2)};
+    const cuuint32_t box[3] = {cuuint32_t(kBoxW), cuuint32_t(kBoxH), 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     w.ok = enc(&w.map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<float2 *>(grid), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
