@@ -139,34 +139,37 @@ def _profile_traffic(workload: str, kernel_file: str):
     return out
 
 
-def data_term_bytes(info, L, K, M):
+def data_term_bytes(info, L, KH, M):
     """Algorithmic HBM bytes of the data term's two passes over G, (dual,
     scatter).  Dual pass: G factors 8 B per stored value (2T per row), per row
     meta 8 B + factor offset 8 B, per visibility y 8 B and the dual d read
-    8 B + written 8 B, the forward grid read once (8 B/cell).  Scatter pass:
-    the factors, meta and offsets again, d read 8 B, the channel grid written
-    once (8 B/cell)."""
-    dual = info.n_gfac * 8 + M * (8 + 8 + 8 + 8 + 8) + L * K * 8
-    scatter = info.n_gfac * 8 + M * (8 + 8 + 8) + L * K * 8
+    8 B + written 8 B, the forward spectrum read once (its stored half: KH
+    complex cells per channel).  Scatter pass: the factors, meta and offsets
+    again, d read 8 B, the folded adjoint written once (KH cells)."""
+    dual = info.n_gfac * 8 + M * (8 + 8 + 8 + 8 + 8) + L * KH * 8
+    scatter = info.n_gfac * 8 + M * (8 + 8 + 8) + L * KH * 8
     return dual, scatter
 
 
 def phase_bytes(info, P, L, K, M):
     """Algorithmic HBM bytes per iteration of every phase of the PDFB
     iteration (the least traffic each phase's result needs):
-    primal      37 B per pixel-channel: x, the SARA adjoint, the nuclear dual
-                over the facet cover (1.2 on average) read, the data adjoint
-                read from the grid (8 B), x, xbar and the zero-padded grid
-                (8 B) written;
-    fft_fwd/inv the channel grids read and written once (2 x 8 B per cell);
+    primal      29 B per pixel-channel: x, the SARA adjoint, the nuclear dual
+                over the facet cover (1.2 on average) and the data adjoint
+                (the real C2R output) read, x, xbar and the real zero-padded
+                grid written;
+    fft_fwd/inv R2C / C2R: the real grid (4 B per cell) and the half
+                spectrum (8 B per stored cell) read or written once;
     dual        G factors, row data, y, d read and written, forward grid;
     scatter     G factors, row data, d read, channel grids written;
     sara        the dual W read and written, the weights read (one per
                 coefficient row), xbar read and the adjoint term written;
     nuclear     the facet duals P read and written, xbar over the facets read."""
     N = P.ny * P.nx
-    dual, scatter = data_term_bytes(info, L, K, M)
-    return {"primal": 37 * N * L, "fft_fwd": 16 * L * K, "fft_inv": 16 * L * K, "degrid_grid": dual,
+    KH = 2 * P.ny * (P.nx + 1)                 # half-spectrum cells per channel: K1 x (K2/2 + 1)
+    dual, scatter = data_term_bytes(info, L, KH, M)
+    fft = L * (4 * K + 8 * KH)
+    return {"primal": 29 * N * L, "fft_fwd": fft, "fft_inv": fft, "degrid_grid": dual,
             "scatter": scatter, "sara": (2 * L + P.C) * info.n_coef * 4 + 2 * N * L * 4,
             "nuclear": 3 * info.nuclear_size * 4}
 
