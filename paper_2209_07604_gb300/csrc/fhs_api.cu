@@ -602,6 +602,7 @@ fhs_status norm_estimate(fhs_problem *p, int n_iter, double tol, std::vector<dou
             CU(cudaMemcpyAsync(hb.data(), nb2 + L, sizeof(double) * m * L, cudaMemcpyDeviceToHost, s));
             CU(cudaStreamSynchronize(s));
             double worst = 0.0;
+            int open = 0;
             al.resize(m);
             bl.resize(m);
             for (int l = 0; l < L; ++l) {
@@ -610,10 +611,14 @@ fhs_status norm_estimate(fhs_problem *p, int n_iter, double tol, std::vector<dou
                     bl[i] = hb[(size_t)i * L + l];
                 }
                 lam[l] = tridiag_max_eig(al.data(), bl.data(), m);
-                worst = std::max(worst, std::fabs(lam[l] - prev[l]) / std::max(std::fabs(lam[l]), 1e-300));
+                const double ch = std::fabs(lam[l] - prev[l]) / std::max(std::fabs(lam[l]), 1e-300);
+                worst = std::max(worst, ch);
+                open += ch >= tol;
                 prev[l] = lam[l];
             }
-            if (trace) std::fprintf(stderr, "fhs set-up: Lanczos step %3d: largest relative change %.3e\n", m, worst);
+            if (trace)
+                std::fprintf(stderr, "fhs set-up: Lanczos step %3d: largest relative change %.3e, %d of %d channels above %.0e\n",
+                             m, worst, open, L, tol);
             if (tol > 0.0 && worst < tol) break;
         }
         return FHS_OK;
