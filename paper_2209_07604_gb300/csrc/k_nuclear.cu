@@ -14,7 +14,11 @@ namespace fhs {
 
 namespace {
 
-constexpr int kPix = 2048;          // facet pixels per CTA in the Gram / apply kernels
+constexpr int kPix = 2048;          // facet pixels per CTA in the apply kernels and the 32-channel Gram
+// Facet pixels per CTA of the register-triangle Gram (L_c <= 16): 32 per thread, so that the
+// reduction of the triangle across the CTA (warp shuffles and FP64 atomics) is amortised over
+// enough pixels.
+constexpr int kGramPix = 8192;
 
 // AccT = float in the iteration (FP32 products, FP64 across threads: small
 // singular values are not needed accurately there, they pass the SVT
@@ -32,9 +36,9 @@ __global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ P, 
     const int4 f = facets[q];
     const int wy = f.y - f.x, wx = f.w - f.z;
     const long long npix = (long long)wy * wx;
-    const long long p0 = (long long)blockIdx.x * kPix;
+    const long long p0 = (long long)blockIdx.x * kGramPix;
     if (p0 >= npix) return;
-    const long long p1 = min(npix, p0 + kPix);
+    const long long p1 = min(npix, p0 + kGramPix);
     const float *Pq = P + nuc_off[cq];
     AccT acc[NP];
 #pragma unroll
@@ -565,8 +569,9 @@ static cudaError_t gram_dispatch(fhs_problem *p, const float *img, bool with_dua
     long long maxpix = 0;
     for (const Facet &f : p->facets) maxpix = std::max<long long>(maxpix, (long long)(f.y1 - f.y0) * (f.x1 - f.x0));
     dim3 g(int((maxpix + kPix - 1) / kPix), p->C * p->Q);
+    const dim3 gt(int((maxpix + kGramPix - 1) / kGramPix), p->C * p->Q);
     const float s0 = with_dual ? float(p->sigma0) : 1.f;
-#define FHS_GRAM(M) gram_kernel<M, AccT><<<g, 256, 0, s>>>(p->P, img, p->d_facets, p->nuc_off, p->Q, p->C, p->Lc, \
+#define FHS_GRAM(M) gram_kernel<M, AccT><<<gt, 256, 0, s>>>(p->P, img, p->d_facets, p->nuc_off, p->Q, p->C, p->Lc, \
                                                            p->nx, p->N, s0, with_dual, p->gram)
     if (p->Lc <= 2) FHS_GRAM(2);
     else if (p->Lc <= 4) FHS_GRAM(4);
