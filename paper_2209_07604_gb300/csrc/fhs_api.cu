@@ -561,6 +561,60 @@ fhs_status default_regularisation(fhs_problem *p, cudaStream_t s) {
     return rs;
 }
 
+// y = Re(Phi_l^H Phi_l) v for the channels `chans` alone (other channels of y are left as they
+// are): per channel Z, R2C by the batch-1 plan f1, the normal-mode pass over the channel's bins
+// [bfirst[l], bfirst[l] + bcount[l]), C2R by i1, Z^T.
+fhs_status apply_normal_channels(fhs_problem *p, const float *v, float *y, const std::vector<int> &chans,
+                                 const std::vector<int> &bfirst, const std::vector<int> &bcount, cufftHandle f1,
+                                 cufftHandle i1, cudaStream_t s) {
+    CUFFT(cufftSetStream(f1, s));
+    CUFFT(cufftSetStream(i1, s));
+    for (const int l : chans) {
+        CU(launch_zpad_channel(p, v, p->grid_in, l, s));
+        CUFFT(cufftExecR2C(f1, p->grid_in + (long long)l * p->K,
+                           reinterpret_cast<cufftComplex *>(p->grid_aux + (long long)l * p->KH)));
+        CU(cudaMemsetAsync(p->grid_scr + (long long)l * p->KH, 0, sizeof(float2) * p->KH, s));
+        CU(launch_normal(p, p->grid_aux, true, p->grid_scr, s, true, true, bfirst[l], bcount[l]));
+        CUFFT(cufftExecC2R(i1, reinterpret_cast<cufftComplex *>(p->grid_scr + (long long)l * p->KH),
+                           p->real_scr + (long long)l * p->K));
+        CU(launch_crop_channel(p, p->real_scr, y, l, s));
+    }
+    return FHS_OK;
+}
+
+// Batch-1 R2C / C2R plans on the problem's work area (for apply_normal_channels); false if they
+// cannot be made or need more work area than the batched plans have.
+bool channel_plans(fhs_problem *p, cufftHandle *f1, cufftHandle *i1) {
+    int n[2] = {p->K1, p->K2}, emb[2] = {p->K1, p->K2}, hemb[2] = {p->K1, p->HS};
+    size_t wf = 0, wi = 0;
+    *f1 = *i1 = 0;
+    if (cufftCreate(f1) != CUFFT_SUCCESS) return false;
+    if (cufftCreate(i1) != CUFFT_SUCCESS) {
+        cufftDestroy(*f1);
+        return false;
+    }
+    const bool ok = cufftSetAutoAllocation(*f1, 0) == CUFFT_SUCCESS && cufftSetAutoAllocation(*i1, 0) == CUFFT_SUCCESS &&
+                    cufftMakePlanMany(*f1, 2, n, emb, 1, int(p->K), hemb, 1, int(p->KH), CUFFT_R2C, 1, &wf) ==
+                        CUFFT_SUCCESS &&
+                    cufftMakePlanMany(*i1, 2, n, hemb, 1, int(p->KH), emb, 1, int(p->K), CUFFT_C2R, 1, &wi) ==
+                        CUFFT_SUCCESS &&
+                    std::max(wf, wi) <= p->fft_ws_bytes && cufftSetWorkArea(*f1, p->fft_ws) == CUFFT_SUCCESS &&
+                    cufftSetWorkArea(*i1, p->fft_ws) == CUFFT_SUCCESS;
+    if (!ok) {
+        cufftDestroy(*f1);
+        cufftDestroy(*i1);
+        *f1 = *i1 = 0;
+    }
+    return ok;
+}
+
+// ||Phi_l||^2 for every channel by Lanczos (see above).  Only the largest value sets the data
+// step, so once every estimate changes by less than kNarrowTol over 5 steps, the steps go on
+// only for the channels within kNarrowMargin of the largest estimate (Ritz values rise
+// monotonically to lambda_max, and these have all but stopped rising); the others keep their
+// last estimate.
+constexpr double kNarrowTol = 1e-4, kNarrowMargin = 0.1;
+
 fhs_status norm_estimate(fhs_problem *p, int n_iter, double tol, std::vector<double> &lam, cudaStream_t s,
                          int *steps_taken = nullptr) {
     const long long LN = (long long)p->L * p->N;
@@ -578,6 +632,24 @@ fhs_status norm_estimate(fhs_problem *p, int n_iter, double tol, std::vector<dou
     const size_t n_coef = (size_t)(2 * n_iter + 1) * L;
     CU(cudaMallocAsync(reinterpret_cast<void **>(&coef), sizeof(double) * n_coef, s));
     fhs_status rs = FHS_OK;
+    std::vector<int> chans, bfirst, bcount;
+    // the channels' bin ranges (bins are ordered by channel), for the narrowed steps
+    cufftHandle f1 = 0, i1 = 0;
+    bool can_narrow = !p->dr && L > 1 && p->n_bin > 0;
+    if (can_narrow) {
+        std::vector<int> bc(p->n_bin);
+        if (cudaMemcpyAsync(bc.data(), p->bin_chan, sizeof(int) * p->n_bin, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            can_narrow = false;
+        }
+        bfirst.assign(L, 0);
+        bcount.assign(L, 0);
+        for (int b = 0; can_narrow && b < p->n_bin; ++b) {
+            if (b > 0 && bc[b] < bc[b - 1]) can_narrow = false;
+            else if (bcount[bc[b]]++ == 0) bfirst[bc[b]] = b;
+        }
+    }
     auto run = [&]() -> fhs_status {
         double *alpha = coef, *nb2 = coef + (size_t)n_iter * L;
         CU(cudaMemsetAsync(coef, 0, sizeof(double) * n_coef, s));
@@ -588,8 +660,10 @@ fhs_status norm_estimate(fhs_problem *p, int n_iter, double tol, std::vector<dou
         CU(launch_power_scale(p, v, v, norms, s));
         lam.assign(L, 0.0);
         std::vector<double> ha, hb, prev(L, -1.0), al, bl;
+        bool narrow = false;
         for (int j = 0; j < n_iter; ++j) {
-            TRY(apply_normal(p, v, y, s));
+            if (narrow) TRY(apply_normal_channels(p, v, y, chans, bfirst, bcount, f1, i1, s));
+            else TRY(apply_normal(p, v, y, s));
             CU(launch_lanczos_step(p, y, vprev, v, alpha + (size_t)j * L, nb2 + (size_t)j * L, s));
             std::swap(vprev, v);
             if (steps_taken) *steps_taken = j + 1;
@@ -606,6 +680,7 @@ fhs_status norm_estimate(fhs_problem *p, int n_iter, double tol, std::vector<dou
             al.resize(m);
             bl.resize(m);
             for (int l = 0; l < L; ++l) {
+                if (narrow && !std::binary_search(chans.begin(), chans.end(), l)) continue;
                 for (int i = 0; i < m; ++i) {
                     al[i] = ha[(size_t)i * L + l];
                     bl[i] = hb[(size_t)i * L + l];
@@ -618,12 +693,26 @@ fhs_status norm_estimate(fhs_problem *p, int n_iter, double tol, std::vector<dou
             }
             if (trace)
                 std::fprintf(stderr, "fhs set-up: Lanczos step %3d: largest relative change %.3e, %d of %d channels above %.0e\n",
-                             m, worst, open, L, tol);
+                             m, worst, open, narrow ? int(chans.size()) : L, tol);
             if (tol > 0.0 && worst < tol) break;
+            if (!narrow && tol > 0.0 && worst < kNarrowTol && can_narrow) {
+                const double top = *std::max_element(lam.begin(), lam.end());
+                chans.clear();
+                for (int l = 0; l < L; ++l)
+                    if (lam[l] >= (1.0 - kNarrowMargin) * top) chans.push_back(l);
+                if (2 * chans.size() <= size_t(L) && channel_plans(p, &f1, &i1)) {
+                    narrow = true;
+                    if (trace)
+                        std::fprintf(stderr, "fhs set-up: Lanczos from step %d on %d of %d channels\n", m,
+                                     int(chans.size()), L);
+                }
+            }
         }
         return FHS_OK;
     };
     rs = run();
+    if (f1) cufftDestroy(f1);
+    if (i1) cufftDestroy(i1);
     cudaFreeAsync(coef, s);
     if (rs != FHS_OK) return rs;
     CU(cudaMemsetAsync(p->Xbar, 0, sizeof(float) * LN, s));
@@ -979,13 +1068,21 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
     const int P1 = q.w_max > 0.0 ? q.n_wplanes - 1 : 0;
     const double dw = q.w_max > 0.0 ? q.w_max / P1 : 0.0;
     const int ntx = (K2 + kTile - 1) / kTile, nty = (K1 + kTile - 1) / kTile;
-    std::vector<int> key(Mtot), pl(Mtot), corner1(Mtot), corner2(Mtot), Tv(Mtot);
+    // per visibility (caller's order) its row meta (corner c1 | c2 << 16, side T) and w-plane:
+    // the sorted rows are gathered from these two and from omega and y
+    std::vector<int> key(Mtot);
+    std::vector<int2> cmeta(Mtot);
+    std::vector<short> cplane(Mtot);
+    const int n_planes = 2 * P1 + 1;
+    std::vector<std::atomic<unsigned char>> used(n_planes);
+    for (auto &u : used) u.store(0, std::memory_order_relaxed);
     // with DDE kernels every box grows by kDdeTaps - 1 (half on each side) and a row is the
     // sum of kDdeTaps separable terms (see build_g_kernel)
     const int ext = dde ? kDdeTaps - 1 : 0, hx = ext / 2;
     p->rank = dde ? kDdeTaps : 1;
     std::atomic<int> box_too_big{0};
     parallel_for(Mtot, [&](long long i0, long long i1) {
+    std::vector<unsigned char> seen(n_planes, 0);
     for (long long i = i0; i < i1; ++i) {
         const double k1 = omega[2 * i] * K1 / (2.0 * M_PI);
         const double k2 = omega[2 * i + 1] * K2 / (2.0 * M_PI);
@@ -1003,9 +1100,13 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
         if (T > 16) box_too_big.store(1, std::memory_order_relaxed);
         long long c1 = (p01 - h - hx) % K1; if (c1 < 0) c1 += K1;
         long long c2 = (p02 - h - hx) % K2; if (c2 < 0) c2 += K2;
-        corner1[i] = int(c1); corner2[i] = int(c2); Tv[i] = T; pl[i] = pv + P1;
+        cmeta[i] = make_int2(int(c1) | (int(c2) << 16), T);
+        cplane[i] = short(pv + P1);
+        seen[pv + P1] = 1;
         key[i] = (int(c1 / kTile) * ntx + int(c2 / kTile)) * 17 + T;   // tile, then box side
     }
+    for (int k = 0; k < n_planes; ++k)
+        if (seen[k]) used[k].store(1, std::memory_order_relaxed);
     });
     if (box_too_big.load()) {
         delete p;
@@ -1022,7 +1123,10 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
         std::vector<long long> cnt(nkeys + 1), cpos(kTile * kTile + 1), tmp;
         for (long long sg = s0; sg < s1; ++sg) {
             const long long a = p->seg_off[sg], b = p->seg_off[sg + 1];
-            auto pos = [&](long long i) { return (corner1[i] % kTile) * kTile + corner2[i] % kTile; };
+            auto pos = [&](long long i) {
+                const int cc = cmeta[i].x;
+                return ((cc & 0xffff) % kTile) * kTile + int((unsigned)cc >> 16) % kTile;
+            };
             tmp.resize(size_t(b - a));
             std::fill(cpos.begin(), cpos.end(), 0);
             for (long long i = a; i < b; ++i) cpos[pos(i) + 1]++;
@@ -1046,10 +1150,11 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
         for (long long v = v0; v < v1; ++v) {
             while (v >= vis_offsets[l + 1]) ++l;
             const long long i = perm[v];
-            meta[v] = make_int2(corner1[i] | (corner2[i] << 16), Tv[i]);
-            fptr[v + 1] = 2LL * p->rank * Tv[i];
+            const int2 m = cmeta[i];
+            meta[v] = m;
+            fptr[v + 1] = 2LL * p->rank * m.y;
             kap[v] = make_double2(omega[2 * i] * K1 / (2.0 * M_PI), omega[2 * i + 1] * K2 / (2.0 * M_PI));
-            plane[v] = short(pl[i]);
+            plane[v] = cplane[i];
             yw[v] = make_float2(float(y[2 * i] / sigma[l]), float(y[2 * i + 1] / sigma[l]));
         }
     });
@@ -1098,16 +1203,14 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
         });
     }
     p->n_fac = fptr[Mtot];
-    { std::vector<int> t; t.swap(key); } { std::vector<int> t; t.swap(corner1); } { std::vector<int> t; t.swap(corner2); }
+    { std::vector<int> t; t.swap(key); }
 
     trace.mark("host row offsets (prefix sums)", s);
-    // ---- w-kernel table: planes -P1..P1, per axis up to 2*kMaxWHalf+1 taps
-    const int n_planes = 2 * P1 + 1;
-    std::vector<char> used(n_planes, 0);
-    for (long long i = 0; i < Mtot; ++i) used[pl[i]] = 1;
+    // ---- w-kernel table: planes -P1..P1, per axis up to 2*kMaxWHalf+1 taps (those in use)
+    { std::vector<int2> t; t.swap(cmeta); } { std::vector<short> t; t.swap(cplane); }
     std::vector<double2> wk((size_t)n_planes * 2 * (2 * kMaxWHalf + 1), make_double2(0.0, 0.0));
     for (int pi = 0; pi < n_planes; ++pi) {
-        if (!used[pi]) continue;
+        if (!used[pi].load(std::memory_order_relaxed)) continue;
         const int pv = pi - P1;
         const int h = P1 > 0 ? (8 * std::abs(pv) + P1) / (2 * P1) : 0;
         const double wp = pv * dw;
@@ -1255,6 +1358,7 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
         char *w = nullptr;
         if ((st = guard(dev_alloc(p, &w, ws, false))) != FHS_OK) return st;
         p->fft_ws = w;
+        p->fft_ws_bytes = ws;
         if (cufftSetWorkArea(p->plan_r2c, p->fft_ws) != CUFFT_SUCCESS ||
             cufftSetWorkArea(p->plan_c2r, p->fft_ws) != CUFFT_SUCCESS)
             return guard(fail(FHS_ERR_CUDA, "cufftSetWorkArea failed"));

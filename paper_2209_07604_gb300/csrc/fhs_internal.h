@@ -121,6 +121,7 @@ struct fhs_problem {
     cufftHandle plan_r2c = 0, plan_c2r = 0;
     bool plan_ok = false;
     void *fft_ws = nullptr;                   // work area shared by both plans
+    size_t fft_ws_bytes = 0;
     float *grid_in = nullptr;                 // [L][K] real zero-padded input (zeros persist)
     float2 *grid_work = nullptr;              // [L][KH] forward spectrum / folded data adjoint
     float2 *grid_scr = nullptr;               // [L][KH] scratch output grids
@@ -213,6 +214,9 @@ void destroy_on_stream(fhs_problem *p, cudaStream_t s);
 cudaError_t launch_build_g(fhs_problem *p, const double2 *kap, const short *plane, const double2 *wk_table,
                            const double2 *dde, int ext, const double *inv_sigma_seg, cudaStream_t s);
 cudaError_t launch_zpad(fhs_problem *p, const float *x, float *grid, cudaStream_t s);
+// Z and Z^T of channel l alone (x and grid point at the channel-0 images and grids)
+cudaError_t launch_zpad_channel(fhs_problem *p, const float *x, float *grid, int l, cudaStream_t s);
+cudaError_t launch_crop_channel(fhs_problem *p, const float *grid, float *x, int l, cudaStream_t s);
 cudaError_t launch_degrid(fhs_problem *p, const float2 *grid, float2 *vis_sorted, cudaStream_t s);
 // test aid: a bounded wait on an mbarrier nothing arrives at, which records a timeout in p->dev_err
 cudaError_t launch_unsatisfied_wait(fhs_problem *p, int max_polls, cudaStream_t s);
@@ -228,7 +232,7 @@ cudaError_t launch_data_scatter(fhs_problem *p, cudaStream_t s);   // grid_work 
 // fixed, fold: as for launch_grid; the passes of the data reduction use fixed = false.  in_half:
 // the input is a half grid (a forward spectrum), else a full grid.
 cudaError_t launch_normal(fhs_problem *p, const float2 *grid, bool in_half, float2 *grid_out, cudaStream_t s,
-                          bool fixed, bool fold);
+                          bool fixed, bool fold, int bin0 = 0, int nbin = -1);   // bins [bin0, bin0 + nbin)
 // One Lanczos step after y = A v: y <- w, vprev <- v_{j+1}; alpha_j[l] and
 // nb2_j[L + l] (= beta_{j+1}^2) accumulate, nb2_j[l] = beta_j^2 is read.
 cudaError_t launch_lanczos_step(fhs_problem *p, float *y, float *vprev, const float *v, double *alpha_j,

@@ -710,7 +710,7 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
     const float *__restrict__ blk_scale, double *__restrict__ blk_norm2, const float2 *__restrict__ grid,
     float2 *__restrict__ grid_out, long long in_cs, int in_hs, long long out_cs, int K1, int K2, float sigma2,
     int R_, const __grid_constant__ CUtensorMap tmap, int use_tma, const float *__restrict__ gmax, int allow_fixed,
-    int fold, int *__restrict__ err) {
+    int fold, int bin0, int *__restrict__ err) {
     const int R = MULTI ? R_ : 1;
     __shared__ alignas(128) float2 s_grid[2 * kBoxCells];   // forward window: even rows, then odd rows
     __shared__ alignas(8) uint64_t s_bar;
@@ -730,7 +730,7 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
     __shared__ int s_bound, s_bad;        // fixed-point scatter: bin bound (float bits), non-finite flag
     __shared__ int s_tmax;                // largest box side of the bin (scatter)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bin = blockIdx.x;
+    const int bin = bin0 + blockIdx.x;
     const int l = bin_chan[bin];
     const int tile = bin_tile[bin];
     // input grid: channel stride in_cs, full (in_hs = 0) or half layout; output grid: channel stride
@@ -1051,16 +1051,19 @@ static WindowMap window_map(const fhs_problem *p, const float2 *grid, bool half)
 template <int MODE>
 // in_half: the input grid is a half grid (a forward spectrum); fold: the output is the folded
 // adjoint in a half grid (otherwise a full grid).
+// Bins [bin0, bin0 + nbin) (all with nbin < 0).
 cudaError_t launch_pass(fhs_problem *p, const float2 *y, float2 *dvis, const float *blk_scale, double *blk_norm2,
                         const float2 *grid, bool in_half, float2 *grid_out, bool fold, float sigma2,
-                        const WindowMap &tm, int allow_fixed, cudaStream_t s) {
-    if (p->n_bin == 0) return cudaSuccess;
+                        const WindowMap &tm, int allow_fixed, cudaStream_t s, int bin0 = 0, int nbin = -1) {
+    if (nbin < 0) nbin = p->n_bin;
+    if (nbin == 0) return cudaSuccess;
     const long long in_cs = in_half ? p->KH : p->K, out_cs = fold ? p->KH : p->K;
     (p->rank > 1 ? degrid_grid_binned_kernel<MODE, true>
-                 : degrid_grid_binned_kernel<MODE, false>)<<<p->n_bin, 256, 0, s>>>(
+                 : degrid_grid_binned_kernel<MODE, false>)<<<nbin, 256, 0, s>>>(
         p->meta, p->fptr, p->gfac, y, dvis, p->bin_slots, p->bin_fbase, p->piece_start, p->piece_len, p->piece_blk,
         p->bin_chan, p->bin_tile, p->ntx, p->B, blk_scale, blk_norm2, grid, grid_out, in_cs, in_half ? p->HS : 0,
-        out_cs, p->K1, p->K2, sigma2, p->rank, tm.map, tm.ok, p->gmax, allow_fixed, fold ? p->HS : 0, p->dev_err);
+        out_cs, p->K1, p->K2, sigma2, p->rank, tm.map, tm.ok, p->gmax, allow_fixed, fold ? p->HS : 0, bin0,
+        p->dev_err);
     p->n_launch += 1;
     return cudaGetLastError();
 }
@@ -1078,10 +1081,10 @@ cudaError_t launch_grid(fhs_problem *p, const float2 *vis_sorted, float2 *grid, 
 }
 
 cudaError_t launch_normal(fhs_problem *p, const float2 *grid, bool in_half, float2 *grid_out, cudaStream_t s,
-                          bool fixed, bool fold) {
+                          bool fixed, bool fold, int bin0, int nbin) {
     if (p->n_bin == 0) return cudaSuccess;
     return launch_pass<kNormal>(p, nullptr, nullptr, nullptr, nullptr, grid, in_half, grid_out, fold, 0.f,
-                                window_map(p, grid, in_half), fixed ? 1 : 0, s);
+                                window_map(p, grid, in_half), fixed ? 1 : 0, s, bin0, nbin);
 }
 
 // The data term in two passes: the dual pre-update with the block norms

@@ -383,6 +383,20 @@ cudaError_t launch_zpad(fhs_problem *p, const float *x, float *grid, cudaStream_
     return cudaGetLastError();
 }
 
+cudaError_t launch_zpad_channel(fhs_problem *p, const float *x, float *grid, int l, cudaStream_t s) {
+    zpad_kernel<<<dim3(grid_for(p->N, 256, 512), 1), 256, 0, s>>>(x + (long long)l * p->N, grid + (long long)l * p->K,
+                                                                   p->s1, p->s2, p->ny, p->nx, p->K1, p->K2, p->K);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_crop_channel(fhs_problem *p, const float *grid, float *x, int l, cudaStream_t s) {
+    crop_kernel<<<dim3(grid_for(p->N, 256, 512), 1), 256, 0, s>>>(grid + (long long)l * p->K, x + (long long)l * p->N,
+                                                                   p->s1, p->s2, p->ny, p->nx, p->K1, p->K2, p->K);
+    p->n_launch += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_crop(fhs_problem *p, const float *grid, float *x, cudaStream_t s) {
     dim3 g(grid_for(p->N, 256, 512), p->L);
     crop_kernel<<<g, 256, 0, s>>>(grid, x, p->s1, p->s2, p->ny, p->nx, p->K1, p->K2, p->K);
