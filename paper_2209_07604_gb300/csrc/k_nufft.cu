@@ -23,19 +23,24 @@ constexpr int kWarps = 8;               // warps per CTA for visibility kernels
 // J <= 8 at 2x oversampling, where the terms beyond k = 35 are below 1e-18 of
 // the sum.
 constexpr int kI0Terms = 40;
+// Intervals of the tabulated KB window over [-J/2, J/2].
+constexpr int kKbTab = 4096;
 
-// KB window at offset t: I0(beta sqrt(1 - (2t/J)^2)) / I0(beta), with
-// I0(x) = sum_k c_k q^k, c_k = 1/(k!)^2, q = x^2/4, by Horner's rule in FP64
-// (all terms positive: no cancellation; one FMA per term, no division).
-__device__ __forceinline__ double kb_eval(double t, int J, double beta, double inv_i0b, const double *c) {
-    const double u = 2.0 * t / double(J);
-    const double r = 1.0 - u * u;
-    if (r < 0.0) return 0.0;
-    const double q = 0.25 * beta * beta * r;
-    double sum = c[kI0Terms - 1];
-#pragma unroll 8
-    for (int k = kI0Terms - 2; k >= 0; --k) sum = fma(sum, q, c[k]);
-    return sum * inv_i0b;
+// KB window at offset t, phi(t) = I0(beta sqrt(1 - (2t/J)^2)) / I0(beta), 0
+// outside [-J/2, J/2], by cubic Hermite interpolation of a table of its
+// values and slopes (tab[n] = {phi(t_n), h phi'(t_n)}, t_n = -J/2 + n h,
+// h = J / kKbTab; `scale` = 1 / h).  phi is a power series in t^2 (an entire
+// function), so the interpolation error, of order h^4 phi'''' / 384, is about
+// 1e-14 of the peak for J <= 8: FP64 rounding, at ten FP64 operations a tap
+// instead of a 40-term series.
+__device__ __forceinline__ double kb_table(double t, int J, const double2 *__restrict__ tab, double scale) {
+    const double x = (t + 0.5 * J) * scale;
+    if (!(x >= 0.0 && x <= double(kKbTab))) return 0.0;
+    const int n = min(int(x), kKbTab - 1);
+    const double u = x - n, u2 = u * u, u3 = u2 * u;
+    const double2 a = tab[n], b = tab[n + 1];
+    return (2.0 * u3 - 3.0 * u2 + 1.0) * a.x + (u3 - 2.0 * u2 + u) * a.y + (3.0 * u2 - 2.0 * u3) * b.x +
+           (u3 - u2) * b.y;
 }
 
 __device__ __forceinline__ int seg_of(const long long *seg_off, int n_seg, long long v) {
@@ -66,18 +71,9 @@ __global__ void __launch_bounds__(256) build_g_kernel(
     const double2 *__restrict__ kap, const short *__restrict__ plane, const double2 *__restrict__ wk,
     const double2 *__restrict__ dde, int ext,
     const long long *__restrict__ seg_off, int n_seg, const double *__restrict__ inv_sigma_seg,
-    long long Mtot, int J, double beta, double inv_i0b, float *__restrict__ gmax) {
+    long long Mtot, int J, const double2 *__restrict__ kbtab, double kbscale, float *__restrict__ gmax) {
     __shared__ double s_kb[kWarps][2][16];
     __shared__ double2 s_g[kWarps][2][16];
-    __shared__ double s_c[kI0Terms];          // 1 / (k!)^2
-    if (threadIdx.x == 0) {
-        double ck = 1.0;
-        for (int k = 0; k < kI0Terms; ++k) {
-            if (k) ck /= double(k) * double(k);
-            s_c[k] = ck;
-        }
-    }
-    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * kWarps;
     for (long long v = (long long)blockIdx.x * kWarps + warp; v < Mtot; v += stride) {
@@ -89,9 +85,12 @@ __global__ void __launch_bounds__(256) build_g_kernel(
         const int dim = lane >> 4, i = lane & 15;
         const double kd = dim ? kp.y : kp.x;
         const long long p0 = (long long)floor(kd - 0.5 * J) + 1;
-        if (i < J) s_kb[warp][dim][i] = kb_eval(kd - double(p0 + i), J, beta, inv_i0b, s_c);
+        if (i < J) s_kb[warp][dim][i] = kb_table(kd - double(p0 + i), J, kbtab, kbscale);
         __syncwarp();
         const int pl = plane[v];
+        int sg = 0;                              // the row's segment (block), searched once per row
+        if (lane == 0) sg = seg_of(seg_off, n_seg, v);
+        sg = __shfl_sync(0xffffffffu, sg, 0);
         float gm = 0.f;                          // |factor value| as stored (FP32)
         if (i < Tb) {
             double2 acc = make_double2(0.0, 0.0);
@@ -103,7 +102,7 @@ __global__ void __launch_bounds__(256) build_g_kernel(
                 acc.x += c.x * k;
                 acc.y += c.y * k;
             }
-            const double f = dim ? 1.0 : inv_sigma_seg[seg_of(seg_off, n_seg, v)];
+            const double f = dim ? 1.0 : inv_sigma_seg[sg];
             acc.x *= f;
             acc.y *= f;
             if (dde) {
@@ -368,12 +367,38 @@ inline int grid_for(long long n, int threads, int cap = 152 * 16) {
 
 cudaError_t launch_build_g(fhs_problem *p, const double2 *kap, const short *plane, const double2 *wk_table,
                            const double2 *dde, int ext, const double *inv_sigma_seg, cudaStream_t s) {
-    const double beta = kb_beta(p->J, 2.0);
-    build_g_kernel<<<grid_for(p->Mtot, kWarps, 152 * 64), 256, 0, s>>>(
-        p->meta, p->fptr, p->gfac, kap, plane, wk_table, dde, ext, p->d_seg_off, p->n_seg, inv_sigma_seg, p->Mtot,
-        p->J, beta, 1.0 / bessel_i0(beta), p->gmax);
-    p->n_launch += 1;
-    return cudaGetLastError();
+    // the KB table: phi and h phi' at kKbTab + 1 nodes, by the I0 series (in q = (beta/2)^2 (1 - (2t/J)^2),
+    // dq/dt = -2 beta^2 t / J^2), normalised by I0(beta)
+    const int J = p->J;
+    const double beta = kb_beta(J, 2.0), inv_i0b = 1.0 / bessel_i0(beta), h = double(J) / kKbTab;
+    std::vector<double2> tab(kKbTab + 1);
+    for (int n = 0; n <= kKbTab; ++n) {
+        const double t = -0.5 * J + n * h, r = 1.0 - (2.0 * t / J) * (2.0 * t / J);
+        const double q = 0.25 * beta * beta * (r > 0.0 ? r : 0.0);
+        double f = 0.0, df = 0.0, ck = 1.0, qk = 1.0;          // sum c_k q^k, sum k c_k q^(k-1)
+        for (int k = 0; k < kI0Terms; ++k) {
+            if (k) ck /= double(k) * double(k);
+            if (k) df += k * ck * qk;                           // qk = q^(k-1) here
+            f += ck * (k ? qk * q : 1.0);
+            if (k) qk *= q;
+        }
+        tab[n] = make_double2(f * inv_i0b, df * (-2.0 * beta * beta * t / (double(J) * J)) * h * inv_i0b);
+    }
+    double2 *d_tab = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d_tab), sizeof(double2) * tab.size(), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(d_tab, tab.data(), sizeof(double2) * tab.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        build_g_kernel<<<grid_for(p->Mtot, kWarps, 152 * 64), 256, 0, s>>>(
+            p->meta, p->fptr, p->gfac, kap, plane, wk_table, dde, ext, p->d_seg_off, p->n_seg, inv_sigma_seg,
+            p->Mtot, J, d_tab, 1.0 / h, p->gmax);
+        p->n_launch += 1;
+        e = cudaGetLastError();
+    }
+    // the copy's host source must outlive it: wait before tab goes out of scope
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaFreeAsync(d_tab, s);
+    return e != cudaSuccess ? e : e2;
 }
 
 cudaError_t launch_zpad(fhs_problem *p, const float *x, float *grid, cudaStream_t s) {
