@@ -613,7 +613,7 @@ bool channel_plans(fhs_problem *p, cufftHandle *f1, cufftHandle *i1) {
 // only for the channels within kNarrowMargin of the largest estimate (Ritz values rise
 // monotonically to lambda_max, and these have all but stopped rising); the others keep their
 // last estimate.
-constexpr double kNarrowTol = 1e-4, kNarrowMargin = 0.1;
+constexpr double kNarrowTol = 1e-3, kNarrowMargin = 0.1, kNarrowStop = 1e-3;
 
 fhs_status norm_estimate(fhs_problem *p, int n_iter, double tol, std::vector<double> &lam, cudaStream_t s,
                          int *steps_taken = nullptr) {
@@ -694,7 +694,11 @@ fhs_status norm_estimate(fhs_problem *p, int n_iter, double tol, std::vector<dou
             if (trace)
                 std::fprintf(stderr, "fhs set-up: Lanczos step %3d: largest relative change %.3e, %d of %d channels above %.0e\n",
                              m, worst, open, narrow ? int(chans.size()) : L, tol);
-            if (tol > 0.0 && worst < tol) break;
+            // narrowed, the largest estimate alone would decide the stop, and a change below tol
+            // over 5 steps can leave it short of its limit by far more than tol (all channels at
+            // once kept it iterating while the slowest converged): the narrowed channels run on
+            // until they are stationary to rounding, or to the step limit
+            if (tol > 0.0 && worst < (narrow ? kNarrowStop * tol : tol)) break;
             if (!narrow && tol > 0.0 && worst < kNarrowTol && can_narrow) {
                 const double top = *std::max_element(lam.begin(), lam.end());
                 chans.clear();
@@ -1139,26 +1143,19 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
         }
     }, 1);
     trace.mark("host sort by tile", s);
+    // the sorted rows' meta and factor counts here (the bins need them on the host); their grid
+    // coordinates, w-planes and whitened data are gathered on the device (launch_gather_rows)
     std::vector<int2> meta(Mtot);
     std::vector<long long> fptr(Mtot + 1);
-    std::vector<double2> kap(Mtot);
-    std::vector<short> plane(Mtot);
-    std::vector<float2> yw(Mtot);
     fptr[0] = 0;
     parallel_for(Mtot, [&](long long v0, long long v1) {
-        int l = int(std::upper_bound(vis_offsets, vis_offsets + L + 1, (int64_t)v0) - vis_offsets) - 1;
         for (long long v = v0; v < v1; ++v) {
-            while (v >= vis_offsets[l + 1]) ++l;
-            const long long i = perm[v];
-            const int2 m = cmeta[i];
+            const int2 m = cmeta[perm[v]];
             meta[v] = m;
             fptr[v + 1] = 2LL * p->rank * m.y;
-            kap[v] = make_double2(omega[2 * i] * K1 / (2.0 * M_PI), omega[2 * i + 1] * K2 / (2.0 * M_PI));
-            plane[v] = cplane[i];
-            yw[v] = make_float2(float(y[2 * i] / sigma[l]), float(y[2 * i + 1] / sigma[l]));
         }
     });
-    trace.mark("host rows (meta, data)", s);
+    trace.mark("host rows (meta, offsets)", s);
     {
         // fptr[v + 1] holds row v's factor count: prefix sums (and nnz) over fixed blocks of rows,
         // block totals first, then each block from its offset
@@ -1207,7 +1204,7 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
 
     trace.mark("host row offsets (prefix sums)", s);
     // ---- w-kernel table: planes -P1..P1, per axis up to 2*kMaxWHalf+1 taps (those in use)
-    { std::vector<int2> t; t.swap(cmeta); } { std::vector<short> t; t.swap(cplane); }
+    { std::vector<int2> t; t.swap(cmeta); }
     std::vector<double2> wk((size_t)n_planes * 2 * (2 * kMaxWHalf + 1), make_double2(0.0, 0.0));
     for (int pi = 0; pi < n_planes; ++pi) {
         if (!used[pi].load(std::memory_order_relaxed)) continue;
@@ -1296,7 +1293,7 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
     std::vector<float> ones(p->n_seg, 1.0f);
     if ((st = guard(upload(p->meta, meta.data(), Mtot, s))) != FHS_OK) return st;
     if ((st = guard(upload(p->fptr, fptr.data(), Mtot + 1, s))) != FHS_OK) return st;
-    if ((st = guard(upload(p->y, yw.data(), Mtot, s))) != FHS_OK) return st;
+
     if ((st = guard(upload(p->perm, perm.data(), Mtot, s))) != FHS_OK) return st;
     if ((st = guard(upload(p->d_seg_off, p->seg_off.data(), p->n_seg + 1, s))) != FHS_OK) return st;
     if ((st = guard(upload(p->eps, eps.data(), p->n_seg, s))) != FHS_OK) return st;
@@ -1309,8 +1306,30 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
     if ((st = guard(upload(p->piece_blk, sb.pblk.data(), n_slot, s))) != FHS_OK) return st;
     if ((st = guard(upload(p->chunk_start, cstart.data(), cstart.size(), s))) != FHS_OK) return st;
     if ((st = guard(upload(p->chunk_seg, cseg.data(), cseg.size(), s))) != FHS_OK) return st;
-    if ((st = guard(upload(d_kap, kap.data(), Mtot, s))) != FHS_OK) return st;
-    if ((st = guard(upload(d_plane, plane.data(), Mtot, s))) != FHS_OK) return st;
+    {
+        // the caller's omega, y and w-planes in its order, gathered into the sorted order on the device
+        double2 *d_om = nullptr, *d_yc = nullptr;
+        short *d_pc = nullptr;
+        long long *d_vo = nullptr;
+        double *d_sg = nullptr;
+        if ((st = guard(dev_alloc(p, &d_om, Mtot, false))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &d_yc, Mtot, false))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &d_pc, Mtot, false))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &d_vo, L + 1, false))) != FHS_OK) return st;
+        if ((st = guard(dev_alloc(p, &d_sg, L, false))) != FHS_OK) return st;
+        std::vector<long long> vo(vis_offsets, vis_offsets + L + 1);
+        if ((st = guard(upload(d_om, reinterpret_cast<const double2 *>(omega), Mtot, s))) != FHS_OK) return st;
+        if ((st = guard(upload(d_yc, reinterpret_cast<const double2 *>(y), Mtot, s))) != FHS_OK) return st;
+        if ((st = guard(upload(d_pc, cplane.data(), Mtot, s))) != FHS_OK) return st;
+        if ((st = guard(upload(d_vo, vo.data(), L + 1, s))) != FHS_OK) return st;
+        if ((st = guard(upload(d_sg, sigma, L, s))) != FHS_OK) return st;
+        cudaError_t e = launch_gather_rows(p, d_om, d_yc, d_pc, d_vo, d_sg, d_kap, d_plane, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return guard(fail(FHS_ERR_CUDA, "row gather failed: %s", cudaGetErrorString(e)));
+        for (void *t : {(void *)d_om, (void *)d_yc, (void *)d_pc, (void *)d_vo, (void *)d_sg}) dev_free(p, t);
+        p->bytes -= (sizeof(double2) * 2 + sizeof(short)) * Mtot + sizeof(long long) * (L + 1) + sizeof(double) * L;
+        { std::vector<short> t; t.swap(cplane); }
+    }
     if ((st = guard(upload(d_wk, wk.data(), wk.size(), s))) != FHS_OK) return st;
     if ((st = guard(upload(d_isg, inv_sig.data(), p->n_seg, s))) != FHS_OK) return st;
     trace.mark("device allocation and upload", s);
@@ -1631,7 +1650,10 @@ fhs_status fhs_estimate_bytes(const fhs_params *params, const double *w, int64_t
     r += (long long)cufft_workspace(2 * q.ny, 2 * q.nx, int(L));
     if (q.data_reduction) r += 36 * K * L + 20 * L;                  // Lambda, y', v', u, w; norms, eps', scales
     const long long n_planes = q.w_max > 0.0 ? 2LL * (q.n_wplanes - 1) + 1 : 1;
-    const long long peak = r + (q.data_reduction ? 8 * K * L : 0) + 16 * M + 2 * M + 16 * n_planes * 2 * (2 * kMaxWHalf + 1) + 8 * nseg;
+    // set-up temporaries: grid coordinates and w-planes (sorted), and the caller's omega, y and planes
+    // while they are gathered
+    const long long peak = r + (q.data_reduction ? 8 * K * L : 0) + (16 + 2 + 16 + 16 + 2) * M +
+                           16 * n_planes * 2 * (2 * kMaxWHalf + 1) + 8 * nseg;
     if (resident_out) *resident_out = r;
     if (peak_out) *peak_out = peak;
     return FHS_OK;

@@ -214,6 +214,11 @@ void destroy_on_stream(fhs_problem *p, cudaStream_t s);
 cudaError_t launch_build_g(fhs_problem *p, const double2 *kap, const short *plane, const double2 *wk_table,
                            const double2 *dde, int ext, const double *inv_sigma_seg, cudaStream_t s);
 cudaError_t launch_zpad(fhs_problem *p, const float *x, float *grid, cudaStream_t s);
+// Set-up: the sorted rows' grid coordinates (kap), w-planes and whitened data (p->y) from the
+// caller's omega, y and planes through p->perm; vis_off [L+1] and sigma [L] on the device.
+cudaError_t launch_gather_rows(fhs_problem *p, const double2 *omega, const double2 *ycall, const short *cplane,
+                               const long long *vis_off, const double *sigma, double2 *kap, short *plane,
+                               cudaStream_t s);
 // Z and Z^T of channel l alone (x and grid point at the channel-0 images and grids)
 cudaError_t launch_zpad_channel(fhs_problem *p, const float *x, float *grid, int l, cudaStream_t s);
 cudaError_t launch_crop_channel(fhs_problem *p, const float *grid, float *x, int l, cudaStream_t s);

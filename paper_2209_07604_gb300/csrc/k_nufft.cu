@@ -168,6 +168,30 @@ __global__ void block_finalize_kernel(double *blk_norm2, const double *eps, floa
     blk_norm2[s] = 0.0;
 }
 
+// The sorted rows' data from the caller's order: kap[v] = omega[perm[v]] K / (2 pi) (grid
+// coordinates), plane[v] = cplane[perm[v]], y[v] = y_caller[perm[v]] / sigma_l with l the channel
+// of row v (vis_off[l] <= v < vis_off[l + 1]).
+__global__ void gather_rows_kernel(const long long *__restrict__ perm, const double2 *__restrict__ omega,
+                                   const double2 *__restrict__ ycall, const short *__restrict__ cplane,
+                                   const long long *__restrict__ vis_off, int L, const double *__restrict__ sigma,
+                                   long long Mtot, int K1, int K2, double2 *__restrict__ kap,
+                                   short *__restrict__ plane, float2 *__restrict__ yw) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < Mtot;
+         v += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = L - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (vis_off[mid] <= v) lo = mid; else hi = mid - 1;
+        }
+        const long long i = perm[v];
+        const double2 om = omega[i], yy = ycall[i];
+        kap[v] = make_double2(om.x * K1 / (2.0 * M_PI), om.y * K2 / (2.0 * M_PI));
+        plane[v] = cplane[i];
+        const double sg = sigma[lo];
+        yw[v] = make_float2(float(yy.x / sg), float(yy.y / sg));
+    }
+}
+
 // Z: grid[(n mod K)] = x_n s1(n1) s2(n2), a real grid (zero cells elsewhere are left as is).
 __global__ void zpad_kernel(const float *__restrict__ x, float *__restrict__ grid, const float *__restrict__ s1,
                             const float *__restrict__ s2, int ny, int nx, int K1, int K2, long long K) {
@@ -399,6 +423,17 @@ cudaError_t launch_build_g(fhs_problem *p, const double2 *kap, const short *plan
     const cudaError_t e2 = cudaStreamSynchronize(s);
     cudaFreeAsync(d_tab, s);
     return e != cudaSuccess ? e : e2;
+}
+
+cudaError_t launch_gather_rows(fhs_problem *p, const double2 *omega, const double2 *ycall, const short *cplane,
+                               const long long *vis_off, const double *sigma, double2 *kap, short *plane,
+                               cudaStream_t s) {
+    if (p->Mtot == 0) return cudaSuccess;
+    gather_rows_kernel<<<grid_for(p->Mtot, 256, 152 * 32), 256, 0, s>>>(p->perm, omega, ycall, cplane, vis_off, p->L,
+                                                                        sigma, p->Mtot, p->K1, p->K2, kap, plane,
+                                                                        p->y);
+    p->n_launch += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_zpad(fhs_problem *p, const float *x, float *grid, cudaStream_t s) {
