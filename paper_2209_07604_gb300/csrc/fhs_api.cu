@@ -1085,8 +1085,10 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
     const int ext = dde ? kDdeTaps - 1 : 0, hx = ext / 2;
     p->rank = dde ? kDdeTaps : 1;
     std::atomic<int> box_too_big{0};
+    std::atomic<long long> wide_rows{0};
     parallel_for(Mtot, [&](long long i0, long long i1) {
     std::vector<unsigned char> seen(n_planes, 0);
+    long long nwide = 0;
     for (long long i = i0; i < i1; ++i) {
         const double k1 = omega[2 * i] * K1 / (2.0 * M_PI);
         const double k2 = omega[2 * i + 1] * K2 / (2.0 * M_PI);
@@ -1102,6 +1104,7 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
         }
         const int T = J + 2 * h + ext;
         if (T > 16) box_too_big.store(1, std::memory_order_relaxed);
+        nwide += T > 8;
         long long c1 = (p01 - h - hx) % K1; if (c1 < 0) c1 += K1;
         long long c2 = (p02 - h - hx) % K2; if (c2 < 0) c2 += K2;
         cmeta[i] = make_int2(int(c1) | (int(c2) << 16), T);
@@ -1111,7 +1114,9 @@ static fhs_status create_impl(const fhs_params *params, const double *omega, con
     }
     for (int k = 0; k < n_planes; ++k)
         if (seen[k]) used[k].store(1, std::memory_order_relaxed);
+    wide_rows.fetch_add(nwide, std::memory_order_relaxed);
     });
+    p->narrow_rows = p->rank == 1 && 10 * wide_rows.load() <= Mtot;
     if (box_too_big.load()) {
         delete p;
         return fail(FHS_ERR_ARG, "DDE kernels widen the G boxes past 16 taps: with DDEs the w-kernels may "

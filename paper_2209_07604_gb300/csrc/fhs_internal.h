@@ -76,6 +76,7 @@ struct fhs_problem {
     fhs_params prm;
     int L = 0, C = 0, Lc = 0, B = 0, ny = 0, nx = 0, K1 = 0, K2 = 0, J = 7;
     int rank = 1;                             // separable terms per row of G (kDdeTaps with DDE kernels)
+    bool narrow_rows = false;                 // at most 1 row in 10 has more than 8 taps (gathers at 5 CTAs/SM)
     long long N = 0, K = 0;                   // pixels and grid cells per channel
     long long Mtot = 0, nnz = 0, n_fac = 0;   // nnz: entries of G (sum T^2); n_fac: stored factors (sum 2T)
     std::vector<long long> vis_off;           // [L+1]

@@ -124,7 +124,8 @@ static_assert(kBinMax <= 65536, "row offsets of a bin");
 // Pieces of a bin: runs of rows of one data block each (a tile's rows of all
 // blocks of a channel share one bin); the host merges blocks only while B <= kMaxPieces.
 constexpr int kMaxPieces = int(kBinMaxPieces);
-static_assert(kMaxPieces <= 256, "piece index of a row is one byte");
+static_assert(kMaxPieces <= 32, "a bin's pieces are scanned by one warp");
+static_assert((2 * kWin * kAdjS) % 4 == 0 && kWin <= 64, "window zeroed by 16-byte stores, flushed 64 columns per warp step");
 
 // Factors of one row for one warp: lane t < T holds g1[t], lane 16 + t holds
 // g2[t]; the other lanes hold 0.
@@ -361,9 +362,7 @@ __device__ __forceinline__ void scatter_pairs(int i0, int nv, int lane, const in
             k2 = c2 + col;
             k2 -= (k2 >= K2) ? K2 : 0;
         }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (2 * k >= Tm) break;                      // warp-uniform
+        auto step = [&](int k) {
             const int t1 = 2 * k + g;
             const float g1x = __shfl_sync(FULL, fac.x, 16 * v + t1), g1y = __shfl_sync(FULL, fac.y, 16 * v + t1);
             if ((DENSE && FIXED) || (cin && t1 < T)) {   // fixed point: the other cells add 0
@@ -374,6 +373,18 @@ __device__ __forceinline__ void scatter_pairs(int i0, int nv, int lane, const in
                 }
                 scatter_cell<DENSE, FIXED>(s_win, ib + 2 * k * kAdjS, gb, kk, k2, K1, K2, fold, g1x, g1y, er,
                                            ei);
+            }
+        };
+        // warp-uniform: rows of 7 or 8 taps (most rows without w-terms) take all four steps with no
+        // test between them (branches were 13 % of the pass's instructions)
+        if (Tm > 6) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) step(k);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (2 * k >= Tm) break;                  // warp-uniform
+                step(k);
             }
         }
         fac = fnx;
@@ -582,7 +593,7 @@ __device__ __forceinline__ float2 gather_terms(const float2 *__restrict__ f, int
 // from fbin, s_v: its visibility index, s_pc: its piece (block) in the bin.
 template <int MODE, bool DENSE, bool MIR>
 __device__ __forceinline__ void gather_phase(int nv, int R, const int2 *s_meta, const int *s_off,
-                                             const long long *s_v, const unsigned char *s_pc, const float *s_psc,
+                                             const long long *s_v,
                                              const float2 *s_y, float2 *s_d, float *s_n2,
                                              const float2 *__restrict__ fbin, const float2 *s_grid,
                                              int wy0, int wx0, int sh, const float2 *__restrict__ gl, int K1, int K2,
@@ -622,7 +633,7 @@ __device__ __forceinline__ void gather_phase(int nv, int R, const int2 *s_meta, 
         if (MODE == kDual) {
             const float2 dold = s_d[i];
             const float2 sy = s_y[i];
-            const float sc = s_psc[s_pc[i]];
+            const float sc = s_n2[i];                 // the row's block factor s_b, staged by this thread
             const float dr = fmaf(sc, dold.x, fmaf(sigma2, phi.x, -sy.x));
             const float di = fmaf(sc, dold.y, fmaf(sigma2, phi.y, -sy.y));
             dvis[s_v[i]] = make_float2(dr, di);
@@ -684,11 +695,14 @@ __device__ __forceinline__ bool window_wait(uint64_t *bar, int max_polls = kWind
 }
 
 // CTAs per SM of the gathering passes (4: 64 registers, what the 8-column
-// chunks need without spills).
+// chunks need without spills).  Problems whose rows nearly all have at most 8
+// taps (no w-terms) run the dual and gather passes at 5 (48 registers, no
+// spills): 8 % faster there, 10 % slower on rows of up to 16 taps.
 #ifndef FHS_GATHER_MIN_BLOCKS
 #define FHS_GATHER_MIN_BLOCKS 4
 #endif
 constexpr int kGatherMinBlocks = FHS_GATHER_MIN_BLOCKS;
+constexpr int kGatherMinBlocksNarrow = 5;
 // MODE kDual: dvis is the data dual d (read and written), grid the forward
 // grid, blk_scale the factors s_b of the previous iteration, blk_norm2 receives
 // ||d_b||^2.  kGather: dvis receives Phi x, grid is the forward grid.
@@ -701,8 +715,12 @@ constexpr int kGatherMinBlocks = FHS_GATHER_MIN_BLOCKS;
 // their term accumulators spill under the 64-register cap); the single-term
 // scatter pass runs 6 CTAs per SM (40 registers, no spills: 3.5 % faster than
 // 5, while 8 spills).
-template <int MODE, bool MULTI>
-__global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGatherMinBlocks)) degrid_grid_binned_kernel(
+// NARROW: the occupancy of problems whose rows nearly all have at most 8 taps (the same code).
+template <int MODE, bool MULTI, bool NARROW = false>
+__global__ void __launch_bounds__(256, MULTI ? 3
+                                             : (MODE == kScatter ? 6
+                                                                 : (NARROW ? kGatherMinBlocksNarrow : kGatherMinBlocks)))
+    degrid_grid_binned_kernel(
     const int2 *__restrict__ meta, const long long *__restrict__ fptr, const float2 *__restrict__ gfac,
     const float2 *__restrict__ y, float2 *__restrict__ dvis, int slots,
     const long long *__restrict__ bin_fbase, const long long *__restrict__ piece_start, const int *__restrict__ piece_len, const int *__restrict__ piece_blk,
@@ -725,7 +743,6 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
     __shared__ long long s_pstart[kMaxPieces];
     __shared__ int s_pcum[kMaxPieces + 1];
     __shared__ int s_pblk[kMaxPieces];
-    __shared__ float s_psc[kMaxPieces];   // block factor s_b of each piece
     __shared__ double s_pnb[kMaxPieces];  // block norm of each piece
     __shared__ int s_bound, s_bad;        // fixed-point scatter: bin bound (float bits), non-finite flag
     __shared__ int s_tmax;                // largest box side of the bin (scatter)
@@ -793,27 +810,32 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
-    // the bin's pieces: runs of rows of one block each, in the order of their blocks
+    // the bin's pieces: runs of rows of one block each, in the order of their blocks.  Warp 0 loads
+    // the slots and scans their lengths by shuffles (slots <= kMaxPieces <= 32): one barrier
+    // between the slot loads and the rows' loads
     const long long pp0 = (long long)bin * slots;
     const long long fb = bin_fbase[bin];       // factor offset of the bin's first row (the smallest)
     const int np = slots;                     // pieces of length 0 in unused slots
-    if (threadIdx.x < np) {
-        const int b = piece_blk[pp0 + threadIdx.x];
-        s_pstart[threadIdx.x] = piece_start[pp0 + threadIdx.x];
-        s_pcum[threadIdx.x + 1] = piece_len[pp0 + threadIdx.x];
-        s_pblk[threadIdx.x] = b;
-        s_psc[threadIdx.x] = blk_scale ? blk_scale[l * B + b] : 1.f;
-        s_pnb[threadIdx.x] = 0.0;
-    }
-    if (threadIdx.x == 0) {
-        s_bound = 0;
-        s_bad = 0;
-        s_tmax = 0;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        s_pcum[0] = 0;
-        for (int q = 0; q < np; ++q) s_pcum[q + 1] += s_pcum[q];
+    if (warp == 0) {
+        int len = 0;
+        if (lane < np) {
+            s_pstart[lane] = piece_start[pp0 + lane];
+            s_pblk[lane] = piece_blk[pp0 + lane];
+            s_pnb[lane] = 0.0;
+            len = piece_len[pp0 + lane];
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, len, o);
+            if (lane >= o) len += t;
+        }
+        if (lane < np) s_pcum[lane + 1] = len;
+        if (lane == 0) {
+            s_pcum[0] = 0;
+            s_bound = 0;
+            s_bad = 0;
+            s_tmax = 0;
+        }
     }
     __syncthreads();
     const int nv = s_pcum[np];
@@ -828,14 +850,16 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
         s_off[i] = int(fptr[v] - fb);
         s_pc[i] = (unsigned char)q;
         if (MODE == kDual || MODE == kGather) s_v[i] = v;
+        // the block factor s_b of the row's block, loaded with the row (not before the barrier)
+        const float vsc = ((MODE == kDual || MODE == kScatter) && blk_scale) ? blk_scale[l * B + s_pblk[q]] : 1.f;
         if (MODE == kDual) {
             const float2 yy = y[v];
             s_y[i] = make_float2(sigma2 * yy.x, sigma2 * yy.y);
             s_d[i] = dvis[v];
+            s_n2[i] = vsc;                    // read (then replaced by |d|^2) by this thread's gather
         }
         if (MODE == kScatter) {
             const float2 dd = dvis[v];
-            const float vsc = s_psc[q];
             s_d[i] = make_float2(vsc * dd.x, vsc * dd.y);
         }
         if ((MODE == kScatter || MODE == kNormal) && dense && allow_fixed) s_n2[i] = gmax[v];
@@ -844,10 +868,16 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
         tmax = __reduce_max_sync(0xffffffffu, tmax);
         if (lane == 0 && tmax > 0) atomicMax(&s_tmax, tmax);
     }
-    if (dense && MODE != kGather && MODE != kDual)
-        for (int i = threadIdx.x; i < 2 * kWin * kAdjS; i += blockDim.x) s_win[i] = 0;
+    if (dense && MODE != kGather && MODE != kDual) {
+        int4 *w4 = reinterpret_cast<int4 *>(s_win);
+        for (int i = threadIdx.x; i < 2 * kWin * kAdjS / 4; i += blockDim.x) w4[i] = make_int4(0, 0, 0, 0);
+    }
     if (acopy) asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();                     // the barrier's initialisation (and the copies) visible from here on
+    // A thread gathers the rows it staged (row i by thread i mod blockDim), so the gathers wait on no
+    // barrier for them, and the TMA window is waited for on its mbarrier (initialised before the
+    // barrier above).  The scatter's warps take other threads' rows and the zeroed window, and the
+    // per-thread window copies fill cells that other threads read: those wait here.
+    if (MODE == kScatter || acopy) __syncthreads();
     if (tma && !window_wait(&s_bar, kWindowPolls, err)) {
         // the copy did not complete in time: record it, then wait once more (bounded) so that
         // no copy into this CTA's shared memory is still in flight when it moves on
@@ -869,13 +899,13 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
     // phase 1: gathers, one row per thread
     if (MODE != kScatter) {
         if (dense && mir)
-            gather_phase<MODE, true, true>(nv, R, s_meta, s_off, s_v, s_pc, s_psc, s_y, s_d, s_n2, fbin, s_grid, wy0,
+            gather_phase<MODE, true, true>(nv, R, s_meta, s_off, s_v, s_y, s_d, s_n2, fbin, s_grid, wy0,
                                            wx0, wsh, gl, K1, K2, in_hs, sigma2, dvis);
         else if (dense)
-            gather_phase<MODE, true, false>(nv, R, s_meta, s_off, s_v, s_pc, s_psc, s_y, s_d, s_n2, fbin, s_grid, wy0,
+            gather_phase<MODE, true, false>(nv, R, s_meta, s_off, s_v, s_y, s_d, s_n2, fbin, s_grid, wy0,
                                             wx0, wsh, gl, K1, K2, in_hs, sigma2, dvis);
         else
-            gather_phase<MODE, false, false>(nv, R, s_meta, s_off, s_v, s_pc, s_psc, s_y, s_d, s_n2, fbin, s_grid,
+            gather_phase<MODE, false, false>(nv, R, s_meta, s_off, s_v, s_y, s_d, s_n2, fbin, s_grid,
                                              wy0, wx0, wsh, gl, K1, K2, in_hs, sigma2, dvis);
     }
     // phase 2: scatters of conj(G_i) s_d[i], one row per warp
@@ -943,25 +973,31 @@ __global__ void __launch_bounds__(256, MULTI ? 3 : (MODE == kScatter ? 6 : kGath
     if (MODE != kDual) {
         if ((MODE == kScatter || MODE == kNormal) && dense) {
             __syncthreads();
-            for (int q = threadIdx.x; q < kWin * kWin; q += blockDim.x) {
-                const int r = q / kWin, c = q - r * kWin;
-                float re, im;
-                if (fixed) {
-                    // im 2^32 + re: the low word is re (signed); the rest, less re, is im 2^32
-                    const int ir = s_win[r * kAdjS + c], ii = s_win[kWin * kAdjS + r * kAdjS + c];
-                    re = float(ir) * finv;                    // exact scaling by a power of two
-                    im = float(ii) * finv;
-                } else {
-                    const float *s_re = reinterpret_cast<const float *>(s_win);
-                    re = s_re[r * kAdjS + c];
-                    im = s_re[kWin * kAdjS + r * kAdjS + c];
-                }
-                if (re != 0.f || im != 0.f) {
-                    int k1 = wy0 + r;
-                    while (k1 >= K1) k1 -= K1;
-                    int k2 = wx0 + c;
-                    while (k2 >= K2) k2 -= K2;
-                    red_grid(gb, k1, k2, K1, K2, re, im, fold);
+            // a box starts in the tile and spans at most s_tmax cells: only the window's first
+            // kTile + s_tmax - 1 rows and columns can hold a contribution (one window row per warp
+            // step, its cells over the lanes)
+            const int ext = min(kWin, kTile + s_tmax - 1);
+            int k2a = wx0 + lane, k2b = wx0 + lane + 32;
+            while (k2a >= K2) k2a -= K2;
+            while (k2b >= K2) k2b -= K2;
+            for (int r = warp; r < ext; r += kWarps) {
+                int k1 = wy0 + r;
+                while (k1 >= K1) k1 -= K1;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = lane + 32 * h;
+                    if (c >= ext) break;
+                    float re, im;
+                    if (fixed) {
+                        const int ir = s_win[r * kAdjS + c], ii = s_win[kWin * kAdjS + r * kAdjS + c];
+                        re = float(ir) * finv;                    // exact scaling by a power of two
+                        im = float(ii) * finv;
+                    } else {
+                        const float *s_re = reinterpret_cast<const float *>(s_win);
+                        re = s_re[r * kAdjS + c];
+                        im = s_re[kWin * kAdjS + r * kAdjS + c];
+                    }
+                    if (re != 0.f || im != 0.f) red_grid(gb, k1, h ? k2b : k2a, K1, K2, re, im, fold);
                 }
             }
         }
@@ -1058,8 +1094,10 @@ cudaError_t launch_pass(fhs_problem *p, const float2 *y, float2 *dvis, const flo
     if (nbin < 0) nbin = p->n_bin;
     if (nbin == 0) return cudaSuccess;
     const long long in_cs = in_half ? p->KH : p->K, out_cs = fold ? p->KH : p->K;
-    (p->rank > 1 ? degrid_grid_binned_kernel<MODE, true>
-                 : degrid_grid_binned_kernel<MODE, false>)<<<nbin, 256, 0, s>>>(
+    auto kern = p->rank > 1 ? degrid_grid_binned_kernel<MODE, true> : degrid_grid_binned_kernel<MODE, false>;
+    if constexpr (MODE == kDual || MODE == kGather)
+        if (p->rank == 1 && p->narrow_rows) kern = degrid_grid_binned_kernel<MODE, false, true>;
+    kern<<<nbin, 256, 0, s>>>(
         p->meta, p->fptr, p->gfac, y, dvis, p->bin_slots, p->bin_fbase, p->piece_start, p->piece_len, p->piece_blk,
         p->bin_chan, p->bin_tile, p->ntx, p->B, blk_scale, blk_norm2, grid, grid_out, in_cs, in_half ? p->HS : 0,
         out_cs, p->K1, p->K2, sigma2, p->rank, tm.map, tm.ok, p->gmax, allow_fixed, fold ? p->HS : 0, bin0,
