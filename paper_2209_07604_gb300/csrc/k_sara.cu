@@ -151,6 +151,21 @@ __global__ void __launch_bounds__(256) analysis_l1_kernel(const __grid_constant_
     analysis_l1_basis<8>(c, l, k0y, k0x, sin_, slo, shi, coef_l, tmp);
 }
 
+// Staging of a level j >= 2 input tile for db_P: only the rows and columns
+// from kMaxF - 2P on, which its filters reach (zero outside the band).
+template <int P>
+__device__ __forceinline__ void analysis_stage_t(const float *__restrict__ in, int ny, int nx, int r0, int c0,
+                                                 float (*sin_)[AIN_X + 1]) {
+    constexpr int R0 = kMaxF - 2 * P, NY = AIN_Y - R0, NX = AIN_X - R0;
+    for (int idx = threadIdx.x; idx < NY * NX; idx += blockDim.x) {
+        const int r = R0 + idx / NX, cc = R0 + idx % NX;
+        const int gy = r0 + r, gx = c0 + cc;
+        // 32-bit offsets: an approximation band holds well under 2^31 samples
+        sin_[r][cc] = (gy >= 0 && gy < ny && gx >= 0 && gx < nx) ? in[gy * nx + gx] : 0.f;
+    }
+    __syncthreads();
+}
+
 // Level j >= 2 of basis p from its level j-1 approximation.
 __global__ void __launch_bounds__(256) analysis_lj_kernel(const __grid_constant__ SaraConst c, int j,
                                                           float *__restrict__ coef, float *__restrict__ tmp) {
@@ -165,24 +180,42 @@ __global__ void __launch_bounds__(256) analysis_lj_kernel(const __grid_constant_
     const float *in = tmp + (long long)l * c.n_tmp + c.off_tmp[p][j - 1];
     float *coef_l = coef + (long long)l * c.n_coef;
     const int r0 = 2 * k0y + 2 - kMaxF, c0 = 2 * k0x + 2 - kMaxF;
-    for (int idx = threadIdx.x; idx < AIN_Y * AIN_X; idx += blockDim.x) {
-        const int r = idx / AIN_X, cc = idx - r * AIN_X;
-        const int gy = r0 + r, gx = c0 + cc;
-        sin_[r][cc] = (gy >= 0 && gy < ny && gx >= 0 && gx < nx) ? in[(long long)gy * nx + gx] : 0.f;
-    }
-    __syncthreads();
     const bool last = (j == c.levels);
     float *ll_out = last ? coef_l + c.off_ll[p] : tmp + (long long)l * c.n_tmp + c.off_tmp[p][j];
     const float lls = last ? kSaraScale : 1.f;
     switch (p) {
-        case 1: analysis_tile_t<1>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls); break;
-        case 2: analysis_tile_t<2>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls); break;
-        case 3: analysis_tile_t<3>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls); break;
-        case 4: analysis_tile_t<4>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls); break;
-        case 5: analysis_tile_t<5>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls); break;
-        case 6: analysis_tile_t<6>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls); break;
-        case 7: analysis_tile_t<7>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls); break;
-        default: analysis_tile_t<8>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls); break;
+        case 1:
+            analysis_stage_t<1>(in, ny, nx, r0, c0, sin_);
+            analysis_tile_t<1>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls);
+            break;
+        case 2:
+            analysis_stage_t<2>(in, ny, nx, r0, c0, sin_);
+            analysis_tile_t<2>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls);
+            break;
+        case 3:
+            analysis_stage_t<3>(in, ny, nx, r0, c0, sin_);
+            analysis_tile_t<3>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls);
+            break;
+        case 4:
+            analysis_stage_t<4>(in, ny, nx, r0, c0, sin_);
+            analysis_tile_t<4>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls);
+            break;
+        case 5:
+            analysis_stage_t<5>(in, ny, nx, r0, c0, sin_);
+            analysis_tile_t<5>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls);
+            break;
+        case 6:
+            analysis_stage_t<6>(in, ny, nx, r0, c0, sin_);
+            analysis_tile_t<6>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls);
+            break;
+        case 7:
+            analysis_stage_t<7>(in, ny, nx, r0, c0, sin_);
+            analysis_tile_t<7>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls);
+            break;
+        default:
+            analysis_stage_t<8>(in, ny, nx, r0, c0, sin_);
+            analysis_tile_t<8>(c, j, k0y, k0x, sin_, slo, shi, coef_l, ll_out, lls);
+            break;
     }
 }
 
