@@ -613,7 +613,7 @@ bool channel_plans(fhs_problem *p, cufftHandle *f1, cufftHandle *i1) {
 // only for the channels within kNarrowMargin of the largest estimate (Ritz values rise
 // monotonically to lambda_max, and these have all but stopped rising); the others keep their
 // last estimate.
-constexpr double kNarrowTol = 1e-3, kNarrowMargin = 0.1, kNarrowStop = 1e-3;
+constexpr double kNarrowTol = 1e-2, kNarrowMargin = 0.1, kNarrowStop = 1e-3;
 
 fhs_status norm_estimate(fhs_problem *p, int n_iter, double tol, std::vector<double> &lam, cudaStream_t s,
                          int *steps_taken = nullptr) {
