@@ -631,6 +631,12 @@ fhs_status norm_estimate(fhs_problem *p, int n_iter, double tol, std::vector<dou
     double *coef = nullptr;                     // alpha[n_iter][L] then nb2[n_iter + 1][L]
     const size_t n_coef = (size_t)(2 * n_iter + 1) * L;
     CU(cudaMallocAsync(reinterpret_cast<void **>(&coef), sizeof(double) * n_coef, s));
+    int *d_chans = nullptr;                     // the narrowed channels, for the vector steps
+    if (cudaMallocAsync(reinterpret_cast<void **>(&d_chans), sizeof(int) * L, s) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeAsync(coef, s);
+        return fail(FHS_ERR_OOM, "device allocation of the Lanczos channel list failed");
+    }
     fhs_status rs = FHS_OK;
     std::vector<int> chans, bfirst, bcount;
     // the channels' bin ranges (bins are ordered by channel), for the narrowed steps
@@ -664,7 +670,8 @@ fhs_status norm_estimate(fhs_problem *p, int n_iter, double tol, std::vector<dou
         for (int j = 0; j < n_iter; ++j) {
             if (narrow) TRY(apply_normal_channels(p, v, y, chans, bfirst, bcount, f1, i1, s));
             else TRY(apply_normal(p, v, y, s));
-            CU(launch_lanczos_step(p, y, vprev, v, alpha + (size_t)j * L, nb2 + (size_t)j * L, s));
+            CU(launch_lanczos_step(p, y, vprev, v, alpha + (size_t)j * L, nb2 + (size_t)j * L, s,
+                                   narrow ? d_chans : nullptr, int(chans.size())));
             std::swap(vprev, v);
             if (steps_taken) *steps_taken = j + 1;
             const bool last = j + 1 == n_iter;
@@ -705,6 +712,9 @@ fhs_status norm_estimate(fhs_problem *p, int n_iter, double tol, std::vector<dou
                 for (int l = 0; l < L; ++l)
                     if (lam[l] >= (1.0 - kNarrowMargin) * top) chans.push_back(l);
                 if (2 * chans.size() <= size_t(L) && channel_plans(p, &f1, &i1)) {
+                    CU(cudaMemcpyAsync(d_chans, chans.data(), sizeof(int) * chans.size(), cudaMemcpyHostToDevice,
+                                       s));
+                    CU(cudaStreamSynchronize(s));    // chans is host memory of this frame
                     narrow = true;
                     if (trace)
                         std::fprintf(stderr, "fhs set-up: Lanczos from step %d on %d of %d channels\n", m,
@@ -718,6 +728,7 @@ fhs_status norm_estimate(fhs_problem *p, int n_iter, double tol, std::vector<dou
     if (f1) cufftDestroy(f1);
     if (i1) cufftDestroy(i1);
     cudaFreeAsync(coef, s);
+    cudaFreeAsync(d_chans, s);
     if (rs != FHS_OK) return rs;
     CU(cudaMemsetAsync(p->Xbar, 0, sizeof(float) * LN, s));
     CU(cudaMemsetAsync(p->A_sara, 0, sizeof(float) * LN, s));

@@ -241,8 +241,9 @@ cudaError_t launch_normal(fhs_problem *p, const float2 *grid, bool in_half, floa
                           bool fixed, bool fold, int bin0 = 0, int nbin = -1);   // bins [bin0, bin0 + nbin)
 // One Lanczos step after y = A v: y <- w, vprev <- v_{j+1}; alpha_j[l] and
 // nb2_j[L + l] (= beta_{j+1}^2) accumulate, nb2_j[l] = beta_j^2 is read.
+// chans (device, nch entries): the channels to step; nullptr: all L
 cudaError_t launch_lanczos_step(fhs_problem *p, float *y, float *vprev, const float *v, double *alpha_j,
-                                double *nb2_j, cudaStream_t s);
+                                double *nb2_j, cudaStream_t s, const int *chans = nullptr, int nch = 0);
 cudaError_t launch_block_finalize(fhs_problem *p, cudaStream_t s);
 cudaError_t launch_permute_to_caller(fhs_problem *p, const float2 *sorted, float2 *caller, const float *scale_seg,
                                      cudaStream_t s);

@@ -31,16 +31,20 @@ constexpr int kKbTab = 4096;
 // values and slopes (tab[n] = {phi(t_n), h phi'(t_n)}, t_n = -J/2 + n h,
 // h = J / kKbTab; `scale` = 1 / h).  phi is a power series in t^2 (an entire
 // function), so the interpolation error, of order h^4 phi'''' / 384, is about
-// 1e-14 of the peak for J <= 8: FP64 rounding, at ten FP64 operations a tap
-// instead of a 40-term series.
-__device__ __forceinline__ double kb_table(double t, int J, const double2 *__restrict__ tab, double scale) {
+// 1e-14 of the peak for J <= 8; the cubic runs in FP32 on FP32 nodes (about
+// 1e-7 of the peak, the rounding of the stored factors), the position in FP64.
+// GB300's FP64 pipe is narrow: this took the G build from a 40-term FP64
+// series per tap to a few FP64 operations.
+__device__ __forceinline__ double kb_table(double t, int J, const float4 *__restrict__ tab, double scale) {
     const double x = (t + 0.5 * J) * scale;
     if (!(x >= 0.0 && x <= double(kKbTab))) return 0.0;
     const int n = min(int(x), kKbTab - 1);
-    const double u = x - n, u2 = u * u, u3 = u2 * u;
-    const double2 a = tab[n], b = tab[n + 1];
-    return (2.0 * u3 - 3.0 * u2 + 1.0) * a.x + (u3 - 2.0 * u2 + u) * a.y + (3.0 * u2 - 2.0 * u3) * b.x +
-           (u3 - u2) * b.y;
+    // the position in FP64 (t reaches 4096 on the grid), the cubic in FP32: the nodes' values and
+    // slopes are at most 1 and the factors are stored in FP32
+    const float u = float(x - n), u2 = u * u, u3 = u2 * u;
+    const float4 ab = tab[n];                    // {phi_n, h phi'_n, phi_n+1, h phi'_n+1}
+    return double(fmaf(2.f * u3 - 3.f * u2 + 1.f, ab.x,
+                       fmaf(u3 - 2.f * u2 + u, ab.y, fmaf(3.f * u2 - 2.f * u3, ab.z, (u3 - u2) * ab.w))));
 }
 
 __device__ __forceinline__ int seg_of(const long long *seg_off, int n_seg, long long v) {
@@ -71,7 +75,7 @@ __global__ void __launch_bounds__(256) build_g_kernel(
     const double2 *__restrict__ kap, const short *__restrict__ plane, const double2 *__restrict__ wk,
     const double2 *__restrict__ dde, int ext,
     const long long *__restrict__ seg_off, int n_seg, const double *__restrict__ inv_sigma_seg,
-    long long Mtot, int J, const double2 *__restrict__ kbtab, double kbscale, float *__restrict__ gmax) {
+    long long Mtot, int J, const float4 *__restrict__ kbtab, double kbscale, float *__restrict__ gmax) {
     __shared__ double s_kb[kWarps][2][16];
     __shared__ double2 s_g[kWarps][2][16];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -285,11 +289,13 @@ __device__ __forceinline__ void block_add(double v, double *s_part, double *out)
     }
 }
 
+// Lanczos vector steps, one channel per blockIdx.y, or channel chans[blockIdx.y] of a list.
 __global__ void __launch_bounds__(256) lanczos_alpha_kernel(float *__restrict__ y, const float *__restrict__ vprev,
                                                             const float *__restrict__ v, long long N,
-                                                            const double *__restrict__ nb2, double *__restrict__ alpha) {
+                                                            const double *__restrict__ nb2, double *__restrict__ alpha,
+                                                            const int *__restrict__ chans) {
     __shared__ double s_part[8];
-    const int l = blockIdx.y;
+    const int l = chans ? chans[blockIdx.y] : blockIdx.y;
     const float beta = float(sqrt(nb2[l]));
     double a = 0.0;
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
@@ -303,9 +309,9 @@ __global__ void __launch_bounds__(256) lanczos_alpha_kernel(float *__restrict__ 
 
 __global__ void __launch_bounds__(256) lanczos_beta_kernel(float *__restrict__ y, const float *__restrict__ v,
                                                            long long N, const double *__restrict__ alpha,
-                                                           double *__restrict__ nb2_next) {
+                                                           double *__restrict__ nb2_next, const int *__restrict__ chans) {
     __shared__ double s_part[8];
-    const int l = blockIdx.y;
+    const int l = chans ? chans[blockIdx.y] : blockIdx.y;
     const float a = float(alpha[l]);
     double b = 0.0;
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
@@ -318,8 +324,8 @@ __global__ void __launch_bounds__(256) lanczos_beta_kernel(float *__restrict__ y
 }
 
 __global__ void lanczos_next_kernel(const float *__restrict__ y, float *__restrict__ vnext, long long N,
-                                    const double *__restrict__ nb2_next) {
-    const int l = blockIdx.y;
+                                    const double *__restrict__ nb2_next, const int *__restrict__ chans) {
+    const int l = chans ? chans[blockIdx.y] : blockIdx.y;
     const double nb = nb2_next[l];
     const float f = nb > 0.0 ? float(1.0 / sqrt(nb)) : 0.f;
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x)
@@ -408,10 +414,14 @@ cudaError_t launch_build_g(fhs_problem *p, const double2 *kap, const short *plan
         }
         tab[n] = make_double2(f * inv_i0b, df * (-2.0 * beta * beta * t / (double(J) * J)) * h * inv_i0b);
     }
-    double2 *d_tab = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d_tab), sizeof(double2) * tab.size(), s);
+    // interval n as one 16-byte entry: both nodes' values and slopes, in FP32
+    std::vector<float4> tab4(kKbTab);
+    for (int n = 0; n < kKbTab; ++n)
+        tab4[n] = make_float4(float(tab[n].x), float(tab[n].y), float(tab[n + 1].x), float(tab[n + 1].y));
+    float4 *d_tab = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d_tab), sizeof(float4) * tab4.size(), s);
     if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(d_tab, tab.data(), sizeof(double2) * tab.size(), cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(d_tab, tab4.data(), sizeof(float4) * tab4.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
         build_g_kernel<<<grid_for(p->Mtot, kWarps, 152 * 64), 256, 0, s>>>(
             p->meta, p->fptr, p->gfac, kap, plane, wk_table, dde, ext, p->d_seg_off, p->n_seg, inv_sigma_seg,
@@ -524,11 +534,12 @@ cudaError_t launch_chan_scale(fhs_problem *p, float *x, const float *f, cudaStre
 }
 
 cudaError_t launch_lanczos_step(fhs_problem *p, float *y, float *vprev, const float *v, double *alpha_j,
-                                double *nb2_j, cudaStream_t s) {
-    dim3 g(grid_for(p->N, 256, 256), p->L);
-    lanczos_alpha_kernel<<<g, 256, 0, s>>>(y, vprev, v, p->N, nb2_j, alpha_j);
-    lanczos_beta_kernel<<<g, 256, 0, s>>>(y, v, p->N, alpha_j, nb2_j + p->L);
-    lanczos_next_kernel<<<g, 256, 0, s>>>(y, vprev, p->N, nb2_j + p->L);
+                                double *nb2_j, cudaStream_t s, const int *chans, int nch) {
+    dim3 g(grid_for(p->N, 256, 256), chans ? nch : p->L);
+    if (g.y == 0) return cudaSuccess;
+    lanczos_alpha_kernel<<<g, 256, 0, s>>>(y, vprev, v, p->N, nb2_j, alpha_j, chans);
+    lanczos_beta_kernel<<<g, 256, 0, s>>>(y, v, p->N, alpha_j, nb2_j + p->L, chans);
+    lanczos_next_kernel<<<g, 256, 0, s>>>(y, vprev, p->N, nb2_j + p->L, chans);
     p->n_launch += 3;
     return cudaGetLastError();
 }
