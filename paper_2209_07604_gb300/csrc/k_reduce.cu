@@ -21,7 +21,6 @@ constexpr int kWarps = 8;
 
 // two complex cells as one float4, two Lambda values as one float2
 inline float4 *f4(float2 *p) { return reinterpret_cast<float4 *>(p); }
-inline const float4 *f4(const float2 *p) { return reinterpret_cast<const float4 *>(p); }
 inline const float2 *f2(const float *p) { return reinterpret_cast<const float2 *>(p); }
 
 __device__ __forceinline__ int chan_of(const long long *seg_off, int n_seg, int B, long long v) {
