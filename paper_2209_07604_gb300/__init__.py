@@ -529,19 +529,31 @@ class Problem:
         import torch
         return torch.empty((self.L, self.ny, self.nx), dtype=torch.float32, device="cuda")
 
+    @staticmethod
+    def _need(t, n, what):
+        """The C entry points take bare device pointers and cannot see how
+        large the buffers behind them are: a caller's tensor of the wrong size
+        is refused here, before any device work."""
+        if t.numel() != n:
+            raise FhsError(FHS_ERR_ARG, "%s holds %d elements, the problem needs %d" % (what, t.numel(), n))
+
     def measure(self, x):
         import torch
+        self._need(x, self.L * self.ny * self.nx, "image cube x")
         vis = torch.empty(self.info.n_vis, dtype=torch.complex64, device="cuda")
         fhs_measure(self.handle, x, vis)
         return vis
 
     def adjoint(self, vis):
+        self._need(vis, self.info.n_vis, "visibilities vis")
         x = self._img()
         fhs_adjoint(self.handle, vis, x)
         return x
 
     def residual(self, x=None):
         """eta_l Re Phi_l^H (y_l - Phi_l x_l); the dirty image when x is None."""
+        if x is not None:
+            self._need(x, self.L * self.ny * self.nx, "image cube x")
         r = self._img()
         fhs_residual(self.handle, x, r)
         return r
@@ -549,6 +561,7 @@ class Problem:
     def noise_from_model(self, x0, apply=False):
         """Noise levels and l2 bounds from a model cube (per block; per channel with
         data reduction)."""
+        self._need(x0, self.L * self.ny * self.nx, "model cube x0")
         n = self.L if int(self.params.data_reduction) else self.L * int(self.params.n_blocks)
         return fhs_noise_from_model(self.handle, x0, n, apply)
 
@@ -561,11 +574,13 @@ class Problem:
 
     def sara_analysis(self, x):
         import torch
+        self._need(x, self.L * self.ny * self.nx, "image cube x")
         c = torch.empty((self.L, self.info.n_coef), dtype=torch.float32, device="cuda")
         fhs_sara_analysis(self.handle, x, c)
         return c
 
     def sara_synthesis(self, c):
+        self._need(c, self.L * self.info.n_coef, "coefficients c")
         x = self._img()
         fhs_sara_synthesis(self.handle, c, x)
         return x
@@ -586,6 +601,7 @@ class Problem:
         return t
 
     def set_state(self, part, t):
+        self._need(t, fhs_state_size(self.handle, part), "state part %d" % int(part))
         fhs_set_state(self.handle, part, t)
 
     def image(self):

@@ -143,3 +143,23 @@ def test_dde_rejections_without_device(lib):
     assert "16 taps" in lib.fhs_last_error().decode()
     with pytest.raises(ValueError):
         fhs.fhs_create_problem(p, om, w, y, sig, vo, bo, dde=dde[:3])
+
+
+def test_problem_methods_refuse_tensors_of_the_wrong_size():
+    """The C entry points take bare pointers; the Problem methods check the
+    caller's tensors against the problem's sizes first and raise
+    FHS_ERR_ARG before any device work (here with CPU tensors and no
+    problem handle: nothing reaches the library)."""
+    torch = pytest.importorskip("torch")
+    p = fhs.Problem.__new__(fhs.Problem)
+    p.handle, p.L, p.ny, p.nx = None, 2, 16, 24
+    p.params = fhs.fhs_params()
+    p.info = fhs.fhs_info()
+    p.info.n_vis, p.info.n_coef = 100, 1000
+    short_img = torch.zeros(2 * 16 * 24 - 1)
+    for call in (lambda: p.measure(short_img), lambda: p.residual(short_img), lambda: p.sara_analysis(short_img),
+                 lambda: p.noise_from_model(short_img), lambda: p.adjoint(torch.zeros(101, dtype=torch.complex64)),
+                 lambda: p.sara_synthesis(torch.zeros(2 * 1000 + 1))):
+        with pytest.raises(fhs.FhsError) as e:
+            call()
+        assert e.value.status == fhs.FHS_ERR_ARG
