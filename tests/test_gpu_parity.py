@@ -480,19 +480,24 @@ def test_reweight_closed_forms():
     prob.close()
 
 
-_SAMPLES = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fhs_1024_samples.npz")
+_GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
-def test_pdfb_iterates_benchmark_geometry():
-    """The geometry of the 1024 x 16-channel workload (2 sub-cubes of 8
-    channels, 4 x 4 facets with 10 % overlap, w-projection with 7..15 taps, 4
-    blocks) at 3e4 visibilities per channel: 10 PDFB iterations with one
-    reweighting against the FP64 oracle's run, stored as seeded samples of the
-    image, the three duals and the weights by tests/golden/make_fhs_1024_samples.py
-    (which calls only the oracle); every sample compared element by element."""
-    d = np.load(_SAMPLES)
-    P = synth.make_problem(str(d["workload"]), M=int(d["m_per_channel"]))
-    prob = fhs.Problem.from_synth(P, mu=float(d["mu"]), mu_bar=float(d["mu_bar"]), sigma2=float(d["sigma2"]))
+_GEOM_PROBLEMS = {}
+
+# the nuclear dual under the tensor-core Grams: the bounds of the mixed-precision tests (TF32 keeps 10
+# mantissa bits, BF16 7); every other part of the state is held to the image tolerance in every mode
+_NUC_BOUND = {fhs.GRAM_FP32: TOL_IMG, fhs.GRAM_TF32: 1e-2, fhs.GRAM_BF16: 3e-2}
+
+
+def _benchmark_geometry(side, precision):
+    d = np.load(os.path.join(_GOLDEN, "fhs_%s_samples.npz" % side))
+    if side not in _GEOM_PROBLEMS:
+        _GEOM_PROBLEMS.clear()
+        _GEOM_PROBLEMS[side] = synth.make_problem(str(d["workload"]), M=int(d["m_per_channel"]))
+    P = _GEOM_PROBLEMS[side]
+    prob = fhs.Problem.from_synth(P, mu=float(d["mu"]), mu_bar=float(d["mu_bar"]), sigma2=float(d["sigma2"]),
+                                  gram_precision=precision)
     i = prob.info
     for k in ("tau", "sigma0", "sigma1"):
         assert abs(getattr(i, k) - float(d[k])) < 1e-12 * float(d[k]), k
@@ -503,21 +508,50 @@ def test_pdfb_iterates_benchmark_geometry():
         if r < n_rw:
             prob.reweight()
     torch.cuda.synchronize()
+    fhs.fhs_device_status(prob.handle)          # no bounded wait gave up
     X = prob.get_state(fhs.STATE_IMAGE).cpu().numpy()
     v = prob.get_state(fhs.STATE_DUAL_DATA).cpu().numpy().view(np.complex64)
     W = prob.get_state(fhs.STATE_DUAL_SARA).cpu().numpy()
     Pn = prob.get_state(fhs.STATE_DUAL_NUCLEAR).cpu().numpy()
     w21 = prob.get_state(fhs.STATE_WEIGHTS_SARA).cpu().numpy()
     wn = prob.get_state(fhs.STATE_WEIGHTS_NUC).cpu().numpy()
+    prob.close()
     assert W.size == P.L * int(d["n_coef"])
+    tol = {"X": TOL_IMG, "v": TOL_IMG, "W": TOL_IMG, "P": _NUC_BOUND[precision], "w21": TOL_IMG,
+           "wnuc": TOL_IMG}
     errs = {}
     for name, arr in (("X", X), ("v", v), ("W", W), ("P", Pn), ("w21", w21)):
         got = arr[d[name + "_idx"]]
         errs[name] = rel(got, d[name])
         # the element-wise part on the scale of the whole array
-        assert np.abs(got - d[name]).max() <= TOL_IMG * float(d[name + "_absmax"]), name
+        assert np.abs(got - d[name]).max() <= tol[name] * float(d[name + "_absmax"]), name
     errs["wnuc"] = rel(wn, d["wnuc"])
-    print("benchmark geometry, 10 iterations + reweighting:", {k: "%.1e" % e for k, e in errs.items()})
+    print("benchmark geometry %s, %s Gram, %d iterations + %d reweighting:"
+          % (side, {fhs.GRAM_FP32: "fp32", fhs.GRAM_TF32: "tf32", fhs.GRAM_BF16: "bf16"}[precision], n_iter, n_rw),
+          {k: "%.1e" % e for k, e in errs.items()})
     for k, e in errs.items():
-        assert e < TOL_IMG, (k, e)
-    prob.close()
+        assert e < tol[k], (k, e)
+
+
+@pytest.mark.parametrize("side", ["1024", "2048"])
+def test_pdfb_iterates_benchmark_geometry(side):
+    """The geometry of the two imaging workloads at 3e4 visibilities per
+    channel, against the FP64 oracle's run stored as seeded samples of the
+    image, the three duals and the weights by tests/golden/make_fhs_samples.py
+    (which calls only the oracle); every sample compared element by element.
+    1024: 1024 x 1024, 16 channels in 2 sub-cubes, 4 x 4 facets with 10 %
+    overlap, w-projection with 7..15 taps, 4 blocks; 10 PDFB iterations with
+    one reweighting.  2048: 2048 x 2048, 32 channels in 4 sub-cubes, 8 x 8
+    facets with 10 % overlap, 8 blocks; 6 iterations with one reweighting.
+    The facet Gram is the default FP32 one."""
+    _benchmark_geometry(side, fhs.GRAM_FP32)
+
+
+@pytest.mark.parametrize("precision", [fhs.GRAM_TF32, fhs.GRAM_BF16])
+def test_tensor_core_gram_benchmark_geometry(precision):
+    """The 2048 x 2048, 32-channel geometry of the test above with the facet
+    Gram on the tensor cores (TF32 or BF16 inputs): the per-result errors
+    against the same oracle run, printed; the image, the data and SARA duals
+    and the weights held to the image tolerance, the nuclear dual to the
+    rounding bound of its input type."""
+    _benchmark_geometry("2048", precision)
