@@ -222,6 +222,8 @@ def run_gpu(args):
     img_host.copy_(prob.image(), non_blocking=True)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t_e2e
+    if ws > 1:
+        e2e_s = max_over_ranks(e2e_s)          # the job ends with its slowest rank
     h2d = omega.nbytes + wv.nbytes + yv.nbytes + P.sigma.nbytes + vis_off.nbytes + P.block_offsets.nbytes
     if dde is not None:
         h2d += dde.nbytes
