@@ -481,7 +481,10 @@ fhs_status fhs_server_wait(fhs_server *server, int64_t id, double timeout_s, flo
                            fhs_request_result *res_out);
 /* Requests running or being set up, queued, and device bytes admitted. */
 fhs_status fhs_server_stats(fhs_server *server, int64_t *active, int64_t *queued, int64_t *bytes_in_use);
-/* Drop queued requests, finish admitted ones, stop the threads. */
+/* Drop queued requests (their state becomes FAILED with FHS_ERR_STATE), let
+ * admitted ones run to the end, stop the threads and free the server.  Call
+ * it when no other thread is inside a call on this server: a caller that
+ * needs a request's result waits for it first. */
 void fhs_server_destroy(fhs_server *server);
 
 /* Host utility: the library's own db_p low-pass filter (2p taps, minimum

@@ -366,9 +366,16 @@ void fhs_server_destroy(fhs_server *sv) {
     if (!sv) return;
     {
         std::lock_guard<std::mutex> lk(sv->mu);
-        sv->queue.clear();        // queued requests are dropped; admitted ones run to the end
+        // queued requests are dropped (FAILED, FHS_ERR_STATE); admitted ones run to the end
+        for (auto &q : sv->queue) {
+            q->res.state = FHS_REQ_FAILED;
+            q->res.status = FHS_ERR_STATE;
+            q->res.t_done = sv->now();
+        }
+        sv->queue.clear();
         sv->stop = true;
         sv->cv_setup.notify_all();
+        sv->cv_done.notify_all();
     }
     for (auto &t : sv->th_setup) t.join();
     sv->th_step.join();
